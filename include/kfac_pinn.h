@@ -1,0 +1,203 @@
+/*
+ * kfac_pinn.h -- C-ABI of the GB300 (sm_103a) KFAC-for-PINNs hot path.
+ *
+ * One KFAC step for a tanh MLP on a Poisson- or heat-type PINN loss, after
+ * Dangel, Mueller, Zeinhofer, "Kronecker-Factored Approximate Curvature for
+ * Physics-Informed Neural Networks" (NeurIPS 2024):
+ *   - the Taylor-mode forward Laplacian (Sec. 3.1, Eq. 5-6; App. C.2);
+ *   - the per-layer Kronecker factors A_l, B_l of the interior term
+ *     (KFAC-expand, Eq. 8, or KFAC-reduce) and of the boundary term (Eq. 3);
+ *   - the damped Kronecker-sum inverse and the preconditioned update
+ *     (Sec. 3.4; App. B, Algorithm 1).
+ *
+ * Conventions shared by every call
+ *   - Layers l = 1..L, widths h_0 = d, h_1, .., h_L = 1, tanh after every
+ *     layer but the last.  theta packs the augmented weights
+ *     W~_l = (W_l b_l) (h_l x (h_{l-1}+1)) one after another, each stacked
+ *     column by column (first index fastest), as in Sec. 2.  Its length is
+ *     D = sum_l h_l (h_{l-1} + 1)  (kfac_pinn_param_count).
+ *   - Points X are N x d, row-major (point-major), FP64.  f has N entries
+ *     (right-hand side at interior points), g has N_bdy entries (boundary
+ *     data).  For the heat operator coordinate 0 of each point is time.
+ *   - Unless a name ends in _host, every pointer argument is a DEVICE pointer
+ *     on the handle's device, owned by the caller, and must stay valid until
+ *     the work queued on `stream` has finished.  The handle owns only its
+ *     internal buffers (activations, factors, inverses, momentum, scratch).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls queue work asynchronously and return at once; argument
+ *     errors are returned immediately (KFAC_BAD_ARG) and nothing is queued.
+ *   - Errors found on the device (a factor that is not positive definite, a
+ *     non-finite loss, a bounded wait that ran out) are latched in a device
+ *     status word; kfac_pinn_sync_status reads and clears it.  No call traps,
+ *     asserts or aborts on the device.
+ *   - A handle is not thread-safe; calls on one handle must be serialised by
+ *     the caller (they share the handle's buffers).
+ */
+#ifndef KFAC_PINN_H
+#define KFAC_PINN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KFAC_OK = 0,
+    KFAC_BAD_ARG = 1,      /* invalid size, pointer or configuration          */
+    KFAC_NOT_PD = 2,       /* a damped factor failed its Cholesky             */
+    KFAC_NONFINITE = 3,    /* NaN/Inf in the loss or the factors               */
+    KFAC_TIMEOUT = 4,      /* a bounded device-side wait gave up               */
+    KFAC_OOM = 5,          /* cudaMalloc failed in kfac_pinn_create            */
+    KFAC_CUDA_ERROR = 6,   /* a CUDA runtime call or launch failed             */
+    KFAC_NOT_READY = 7     /* precondition/update called before invert         */
+} kfac_status_t;
+
+typedef enum {
+    KFAC_FP64 = 0,         /* every stage in FP64 SIMT arithmetic              */
+    KFAC_MIXED_BF16 = 1    /* tensor-core BF16 (split-BF16 on the value and
+                              Laplacian columns) with FP32 accumulation for the
+                              Taylor pass, adjoint, gradient and Grams; FP64
+                              for loss, factors, Cholesky and eigensolver      */
+} kfac_precision_t;
+
+typedef enum { KFAC_EXPAND = 0, KFAC_REDUCE = 1 } kfac_variant_t;
+
+/* Residual operator of the interior term.
+ * LAPLACE: r = -Laplacian(u) - f   (Eq. 1 with L = -Laplacian)
+ * HEAT:    r = du/dt - kappa * Laplacian_x(u) - f, where the Laplacian runs
+ *          over coordinates 1..d-1 and coordinate 0 is time (App. A.6). */
+typedef enum { KFAC_OP_LAPLACE = 0, KFAC_OP_HEAT = 1 } kfac_operator_t;
+
+/* Factor selector of kfac_pinn_get_factor / kfac_pinn_set_factor. */
+typedef enum { KFAC_A_INT = 0, KFAC_B_INT = 1, KFAC_A_BDY = 2, KFAC_B_BDY = 3 } kfac_factor_t;
+
+#define KFAC_MAX_LAYERS 16
+
+typedef struct {
+    int d;                         /* input dimension h_0 (>= 1)                       */
+    int L;                         /* number of linear layers, 1..KFAC_MAX_LAYERS      */
+    int widths[KFAC_MAX_LAYERS];   /* h_1..h_L, each >= 1, h_L == 1                    */
+    int op;                        /* kfac_operator_t                                  */
+    double kappa;                  /* heat diffusivity (op == HEAT)                    */
+    int precision;                 /* kfac_precision_t                                 */
+    int variant;                   /* kfac_variant_t (interior factors)                */
+    double beta;                   /* EMA factor of the Kronecker factors, [0, 1)      */
+    double lambda;                 /* damping lambda > 0                               */
+    int damping_sqrt;              /* 0: factor + lambda*I (paper); 1: + sqrt(lambda)*I */
+    int factor_init_identity;      /* 0: EMA starts from 0; 1: from the identity      */
+    double lr;                     /* fixed learning rate                              */
+    double momentum;               /* momentum mu on the previous update               */
+    int max_n_int;                 /* capacity: interior points per call (>= 1)        */
+    int max_n_bdy;                 /* capacity: boundary points per call (>= 1)        */
+} kfac_config_t;
+
+typedef struct kfac_pinn_handle* kfac_handle_t;
+
+/* D = sum_l h_l (h_{l-1} + 1), or -1 for an invalid configuration. */
+int64_t kfac_pinn_param_count(const kfac_config_t* cfg);
+
+/* Human-readable name of a status code (static string). */
+const char* kfac_pinn_status_string(kfac_status_t st);
+
+/* Create a handle on the current CUDA device: validates cfg, allocates every
+ * internal buffer for max_n_int / max_n_bdy points, and sets the EMA factors
+ * to their initial value (0 or I), momentum to 0 and the step counter to 0.
+ * Returns KFAC_BAD_ARG (cfg invalid, out NULL), KFAC_OOM or KFAC_CUDA_ERROR;
+ * *out is NULL on failure.  Blocks until the initialisation has finished. */
+kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out);
+
+/* Free every buffer of the handle (synchronises its device first). */
+kfac_status_t kfac_pinn_destroy(kfac_handle_t h);
+
+/* Reset EMA factors to their initial value, momentum to 0, step counter to 0. */
+kfac_status_t kfac_pinn_reset(kfac_handle_t h, void* stream);
+
+/* Forward Laplacian (Sec. 3.1 Eq. 5-6; App. C.2): for each of N points, u,
+ * the d input derivatives and the Laplacian (the partial spatial Laplacian
+ * for the heat operator).  u: N; grad: N x d row-major (may be NULL); lap: N
+ * (may be NULL).  N may exceed max_n_int (processed in chunks). */
+kfac_status_t kfac_pinn_forward_laplacian(kfac_handle_t h, void* stream, const double* theta,
+                                          const double* X, int N,
+                                          double* u, double* grad, double* lap);
+
+/* Curvature and gradient of one batch (App. B, Algorithm 1, steps 1, 2 and
+ * 4): forward Laplacian on the interior points and plain forward pass on the
+ * boundary points, residuals and loss (Eq. 1), one backward pass each for
+ * g^{(l)} (Sec. 3.2), the loss gradient, the Kronecker factors (Eq. 8 or
+ * KFAC-reduce; Eq. 3) and their exponential moving average (Sec. 3.4).
+ * loss: 3 device doubles (L, L_Omega, L_boundary), may be NULL.  The gradient
+ * and the factors stay in the handle.  1 <= N_int <= max_n_int,
+ * 1 <= N_bdy <= max_n_bdy. */
+kfac_status_t kfac_pinn_factors(kfac_handle_t h, void* stream, const double* theta,
+                                const double* X_int, int N_int, const double* f,
+                                const double* X_bdy, int N_bdy, const double* g,
+                                double* loss);
+
+/* Damped inverse of the Kronecker sum (Sec. 3.4; App. B step 3): for every
+ * layer, with A~ = A^ + lambda I (or sqrt(lambda) I), the simultaneous
+ * diagonalisation V^T A~_Omega V = I, V^T A~_bdy V = diag(a) through an FP64
+ * Cholesky of A~_Omega and an FP64 symmetric eigendecomposition of the
+ * whitened A~_bdy; likewise for B.  A factor that is not positive definite
+ * latches KFAC_NOT_PD. */
+kfac_status_t kfac_pinn_invert(kfac_handle_t h, void* stream);
+
+/* direction = -(A~_Omega x B~_Omega + A~_bdy x B~_bdy)^{-1} grad per layer,
+ * i.e. Delta = -V_B [(V_B^T G V_A) / (1 + b a^T)] V_A^T (Sec. 3.4).  grad and
+ * direction are packed like theta (D doubles).  grad == NULL uses the
+ * gradient of the last kfac_pinn_factors call; direction == NULL keeps the
+ * result in the handle for kfac_pinn_update.  KFAC_NOT_READY before the first
+ * kfac_pinn_invert. */
+kfac_status_t kfac_pinn_precondition(kfac_handle_t h, void* stream, const double* grad,
+                                     double* direction);
+
+/* theta += delta with delta = lr (momentum * delta_prev + Delta) (Sec. 3.4,
+ * fixed learning rate), using the handle's last preconditioned direction. */
+kfac_status_t kfac_pinn_update(kfac_handle_t h, void* stream, double* theta);
+
+/* One whole KFAC step: kfac_pinn_factors, kfac_pinn_invert,
+ * kfac_pinn_precondition and kfac_pinn_update, in that order.  theta is
+ * updated in place; loss (3 device doubles, may be NULL) is the loss at the
+ * incoming theta. */
+kfac_status_t kfac_pinn_step(kfac_handle_t h, void* stream, double* theta,
+                             const double* X_int, int N_int, const double* f,
+                             const double* X_bdy, int N_bdy, const double* g,
+                             double* loss);
+
+/* The same step with the batch in HOST memory (pinned memory gives
+ * asynchronous copies): X_int_host, f_host, X_bdy_host, g_host are copied to
+ * the handle's staging buffers on `stream`, the step runs, and the 3 loss
+ * values are copied back to loss_host (may be NULL).  theta is a device
+ * pointer (the parameters stay resident).  Synchronises `stream` before
+ * returning, so loss_host is valid on return. */
+kfac_status_t kfac_pinn_step_host(kfac_handle_t h, void* stream, double* theta,
+                                  const double* X_int_host, int N_int, const double* f_host,
+                                  const double* X_bdy_host, int N_bdy, const double* g_host,
+                                  double* loss_host);
+
+/* Copy the current EMA factor `which` (kfac_factor_t, undamped) of layer
+ * `layer` (1..L) to dst (n x n row-major; n = h_{l-1}+1 for A, h_l for B). */
+kfac_status_t kfac_pinn_get_factor(kfac_handle_t h, void* stream, int layer, int which, double* dst);
+
+/* Overwrite the EMA factor `which` of layer `layer` with src (n x n). */
+kfac_status_t kfac_pinn_set_factor(kfac_handle_t h, void* stream, int layer, int which,
+                                   const double* src);
+
+/* Copy the gradient of the last kfac_pinn_factors call (D doubles). */
+kfac_status_t kfac_pinn_get_gradient(kfac_handle_t h, void* stream, double* dst);
+
+/* Copy the last preconditioned direction Delta (D doubles). */
+kfac_status_t kfac_pinn_get_direction(kfac_handle_t h, void* stream, double* dst);
+
+/* Synchronise the handle's device, then read and clear the device status
+ * word (first error latched since the last read). */
+kfac_status_t kfac_pinn_sync_status(kfac_handle_t h, kfac_status_t* status);
+
+/* Number of kernels this library launched on the handle since creation
+ * (host-side counter; used to report launches per step). */
+int64_t kfac_pinn_launch_count(kfac_handle_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KFAC_PINN_H */

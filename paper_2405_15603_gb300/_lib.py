@@ -1,0 +1,81 @@
+"""ctypes declarations of the C-ABI in include/kfac_pinn.h (marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+KFAC_MAX_LAYERS = 16
+
+STATUS = {0: "KFAC_OK", 1: "KFAC_BAD_ARG", 2: "KFAC_NOT_PD", 3: "KFAC_NONFINITE",
+          4: "KFAC_TIMEOUT", 5: "KFAC_OOM", 6: "KFAC_CUDA_ERROR", 7: "KFAC_NOT_READY"}
+
+EXPORTS = [
+    "kfac_pinn_param_count", "kfac_pinn_status_string", "kfac_pinn_create", "kfac_pinn_destroy",
+    "kfac_pinn_reset", "kfac_pinn_forward_laplacian", "kfac_pinn_factors", "kfac_pinn_invert",
+    "kfac_pinn_precondition", "kfac_pinn_update", "kfac_pinn_step", "kfac_pinn_step_host",
+    "kfac_pinn_get_factor", "kfac_pinn_set_factor", "kfac_pinn_get_gradient",
+    "kfac_pinn_get_direction", "kfac_pinn_sync_status", "kfac_pinn_launch_count",
+]
+
+
+class KfacConfig(C.Structure):
+    _fields_ = [
+        ("d", C.c_int), ("L", C.c_int), ("widths", C.c_int * KFAC_MAX_LAYERS),
+        ("op", C.c_int), ("kappa", C.c_double), ("precision", C.c_int), ("variant", C.c_int),
+        ("beta", C.c_double), ("lambda_", C.c_double), ("damping_sqrt", C.c_int),
+        ("factor_init_identity", C.c_int), ("lr", C.c_double), ("momentum", C.c_double),
+        ("max_n_int", C.c_int), ("max_n_bdy", C.c_int),
+    ]
+
+
+class KfacError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} returned {STATUS.get(code, code)}")
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "libkfacpinn.so")
+
+
+def load() -> C.CDLL:
+    """Load libkfacpinn.so; fails loudly when it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2405_15603_gb300.build.build()")
+    lib = C.CDLL(path)
+    P, I, D, H = C.c_void_p, C.c_int, C.c_double, C.c_void_p
+    st = C.c_int
+    sig = {
+        "kfac_pinn_param_count": (C.c_int64, [C.POINTER(KfacConfig)]),
+        "kfac_pinn_status_string": (C.c_char_p, [I]),
+        "kfac_pinn_create": (st, [C.POINTER(KfacConfig), C.POINTER(H)]),
+        "kfac_pinn_destroy": (st, [H]),
+        "kfac_pinn_reset": (st, [H, P]),
+        "kfac_pinn_forward_laplacian": (st, [H, P, P, P, I, P, P, P]),
+        "kfac_pinn_factors": (st, [H, P, P, P, I, P, P, I, P, P]),
+        "kfac_pinn_invert": (st, [H, P]),
+        "kfac_pinn_precondition": (st, [H, P, P, P]),
+        "kfac_pinn_update": (st, [H, P, P]),
+        "kfac_pinn_step": (st, [H, P, P, P, I, P, P, I, P, P]),
+        "kfac_pinn_step_host": (st, [H, P, P, P, I, P, P, I, P, P]),
+        "kfac_pinn_get_factor": (st, [H, P, I, I, P]),
+        "kfac_pinn_set_factor": (st, [H, P, I, I, P]),
+        "kfac_pinn_get_gradient": (st, [H, P, P]),
+        "kfac_pinn_get_direction": (st, [H, P, P]),
+        "kfac_pinn_sync_status": (st, [H, C.POINTER(C.c_int)]),
+        "kfac_pinn_launch_count": (C.c_int64, [H]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib

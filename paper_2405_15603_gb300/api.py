@@ -1,0 +1,189 @@
+"""Thin Python binding of the C-ABI: argument marshalling only.
+
+torch supplies device memory and the current CUDA stream; every step of the
+KFAC path runs in libkfacpinn.so.  Names follow the C entry points.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import KfacConfig, KfacError
+
+OPS = {"laplace": 0, "heat": 1}
+PRECISIONS = {"fp64": 0, "mixed_bf16": 1}
+VARIANTS = {"expand": 0, "reduce": 1}
+FACTORS = {"A_int": 0, "B_int": 1, "A_bdy": 2, "B_bdy": 3}
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _check(fn: str, code: int):
+    if code != 0:
+        raise KfacError(fn, code)
+
+
+def _dev(x, device) -> torch.Tensor:
+    t = torch.as_tensor(x, dtype=torch.float64, device=device)
+    return t.contiguous()
+
+
+def make_config(d: int, widths: Sequence[int], op: str = "laplace", kappa: float = 0.0,
+                precision: str = "fp64", variant: str = "expand", beta: float = 0.0,
+                lam: float = 1e-3, damping_sqrt: bool = False, init_identity: bool = False,
+                lr: float = 0.1, momentum: float = 0.0, max_n_int: int = 1024,
+                max_n_bdy: int = 1024) -> KfacConfig:
+    cfg = KfacConfig()
+    cfg.d = d
+    cfg.L = len(widths)
+    for i, w in enumerate(widths):
+        cfg.widths[i] = int(w)
+    cfg.op = OPS[op]
+    cfg.kappa = kappa
+    cfg.precision = PRECISIONS[precision]
+    cfg.variant = VARIANTS[variant]
+    cfg.beta = beta
+    cfg.lambda_ = lam
+    cfg.damping_sqrt = int(damping_sqrt)
+    cfg.factor_init_identity = int(init_identity)
+    cfg.lr = lr
+    cfg.momentum = momentum
+    cfg.max_n_int = max_n_int
+    cfg.max_n_bdy = max_n_bdy
+    return cfg
+
+
+def param_count(d: int, widths: Sequence[int]) -> int:
+    lib = _lib.load()
+    return int(lib.kfac_pinn_param_count(C.byref(make_config(d, widths))))
+
+
+class KfacPinn:
+    """One KFAC optimiser state (factors, inverses, momentum) on one GPU."""
+
+    def __init__(self, d: int, widths: Sequence[int], device: str = "cuda", **kw):
+        self.lib = _lib.load()
+        self.device = torch.device(device)
+        self.d = d
+        self.widths = tuple(int(w) for w in widths)
+        self.cfg = make_config(d, widths, **kw)
+        self.h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _check("kfac_pinn_create", self.lib.kfac_pinn_create(C.byref(self.cfg), C.byref(self.h)))
+        self.D = int(self.lib.kfac_pinn_param_count(C.byref(self.cfg)))
+        self._loss = torch.zeros(3, dtype=torch.float64, device=self.device)
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if self.h:
+            self.lib.kfac_pinn_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        _check("kfac_pinn_reset", self.lib.kfac_pinn_reset(self.h, _stream()))
+
+    # -- the hot path -----------------------------------------------------
+    def forward_laplacian(self, theta: torch.Tensor, X) -> Tuple[torch.Tensor, torch.Tensor, torch.Tensor]:
+        X = _dev(X, self.device)
+        N = X.shape[0]
+        u = torch.empty(N, dtype=torch.float64, device=self.device)
+        g = torch.empty(N, self.d, dtype=torch.float64, device=self.device)
+        lap = torch.empty(N, dtype=torch.float64, device=self.device)
+        _check("kfac_pinn_forward_laplacian", self.lib.kfac_pinn_forward_laplacian(
+            self.h, _stream(), _ptr(theta), _ptr(X), N, _ptr(u), _ptr(g), _ptr(lap)))
+        return u, g, lap
+
+    def factors(self, theta, X_int, f, X_bdy, g) -> torch.Tensor:
+        X_int, f, X_bdy, g = (_dev(a, self.device) for a in (X_int, f, X_bdy, g))
+        _check("kfac_pinn_factors", self.lib.kfac_pinn_factors(
+            self.h, _stream(), _ptr(theta), _ptr(X_int), X_int.shape[0], _ptr(f),
+            _ptr(X_bdy), X_bdy.shape[0], _ptr(g), _ptr(self._loss)))
+        return self._loss.clone()
+
+    def invert(self):
+        _check("kfac_pinn_invert", self.lib.kfac_pinn_invert(self.h, _stream()))
+
+    def precondition(self, grad: Optional[torch.Tensor] = None) -> torch.Tensor:
+        out = torch.empty(self.D, dtype=torch.float64, device=self.device)
+        _check("kfac_pinn_precondition", self.lib.kfac_pinn_precondition(
+            self.h, _stream(), _ptr(grad), _ptr(out)))
+        return out
+
+    def update(self, theta: torch.Tensor):
+        _check("kfac_pinn_update", self.lib.kfac_pinn_update(self.h, _stream(), _ptr(theta)))
+
+    def step(self, theta: torch.Tensor, X_int, f, X_bdy, g, loss: Optional[torch.Tensor] = None):
+        """One KFAC step in place on theta; inputs must already be device tensors
+        for the timed path (no copies are made for contiguous FP64 CUDA tensors)."""
+        X_int, f, X_bdy, g = (_dev(a, self.device) for a in (X_int, f, X_bdy, g))
+        out = self._loss if loss is None else loss
+        _check("kfac_pinn_step", self.lib.kfac_pinn_step(
+            self.h, _stream(), _ptr(theta), _ptr(X_int), X_int.shape[0], _ptr(f),
+            _ptr(X_bdy), X_bdy.shape[0], _ptr(g), _ptr(out)))
+        return out
+
+    def step_host(self, theta: torch.Tensor, X_int: np.ndarray, f: np.ndarray, X_bdy: np.ndarray,
+                  g: np.ndarray, loss_host: Optional[np.ndarray] = None) -> np.ndarray:
+        """One KFAC step with the batch in host memory (copied in by the library)."""
+        bufs = [np.ascontiguousarray(a, dtype=np.float64) if not isinstance(a, torch.Tensor) else a
+                for a in (X_int, f, X_bdy, g)]
+        ptrs = [b.ctypes.data if isinstance(b, np.ndarray) else b.data_ptr() for b in bufs]
+        out = np.zeros(3) if loss_host is None else loss_host
+        _check("kfac_pinn_step_host", self.lib.kfac_pinn_step_host(
+            self.h, _stream(), _ptr(theta), ptrs[0], bufs[0].shape[0], ptrs[1], ptrs[2],
+            bufs[2].shape[0], ptrs[3], out.ctypes.data))
+        return out
+
+    # -- inspection -------------------------------------------------------
+    def factor_shape(self, layer: int, which: str) -> int:
+        dims = [self.d] + list(self.widths)
+        return dims[layer - 1] + 1 if which.startswith("A") else dims[layer]
+
+    def get_factor(self, layer: int, which: str) -> torch.Tensor:
+        n = self.factor_shape(layer, which)
+        out = torch.empty(n, n, dtype=torch.float64, device=self.device)
+        _check("kfac_pinn_get_factor", self.lib.kfac_pinn_get_factor(
+            self.h, _stream(), layer, FACTORS[which], _ptr(out)))
+        return out
+
+    def set_factor(self, layer: int, which: str, M):
+        t = _dev(M, self.device)
+        _check("kfac_pinn_set_factor", self.lib.kfac_pinn_set_factor(
+            self.h, _stream(), layer, FACTORS[which], _ptr(t)))
+        torch.cuda.current_stream().synchronize()
+
+    def gradient(self) -> torch.Tensor:
+        out = torch.empty(self.D, dtype=torch.float64, device=self.device)
+        _check("kfac_pinn_get_gradient", self.lib.kfac_pinn_get_gradient(self.h, _stream(), _ptr(out)))
+        return out
+
+    def direction(self) -> torch.Tensor:
+        out = torch.empty(self.D, dtype=torch.float64, device=self.device)
+        _check("kfac_pinn_get_direction", self.lib.kfac_pinn_get_direction(self.h, _stream(), _ptr(out)))
+        return out
+
+    def sync_status(self) -> str:
+        v = C.c_int(0)
+        _check("kfac_pinn_sync_status", self.lib.kfac_pinn_sync_status(self.h, C.byref(v)))
+        return _lib.STATUS.get(v.value, str(v.value))
+
+    def launch_count(self) -> int:
+        return int(self.lib.kfac_pinn_launch_count(self.h))

@@ -1,0 +1,410 @@
+// C-ABI entry points of libkfacpinn.so (declared in include/kfac_pinn.h).
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#include "kfac_internal.cuh"
+#include "tc_path.cuh"
+
+namespace {
+
+bool valid_config(const kfac_config_t* c) {
+    if (!c) return false;
+    if (c->d < 1 || c->L < 1 || c->L > KFAC_MAX_LAYERS) return false;
+    for (int l = 0; l < c->L; l++)
+        if (c->widths[l] < 1 || c->widths[l] > 1023) return false;
+    if (c->widths[c->L - 1] != 1) return false;
+    if (c->d + 1 > 1024) return false;
+    if (c->op != KFAC_OP_LAPLACE && c->op != KFAC_OP_HEAT) return false;
+    if (c->op == KFAC_OP_HEAT && c->d < 2) return false;
+    if (c->precision != KFAC_FP64 && c->precision != KFAC_MIXED_BF16) return false;
+    if (c->variant != KFAC_EXPAND && c->variant != KFAC_REDUCE) return false;
+    if (!(c->beta >= 0.0 && c->beta < 1.0)) return false;
+    if (!(c->lambda > 0.0) || !isfinite(c->lambda)) return false;
+    if (!isfinite(c->lr) || !isfinite(c->momentum) || !isfinite(c->kappa)) return false;
+    if (c->max_n_int < 1 || c->max_n_bdy < 1) return false;
+    long long rows = (long long)(c->d + 2) * c->max_n_int;
+    if (rows > (1LL << 30)) return false;
+    return true;
+}
+
+template <class T>
+kfac_status_t dalloc(T** p, size_t elems) {
+    *p = nullptr;
+    if (elems == 0) elems = 1;
+    cudaError_t e = cudaMalloc((void**)p, elems * sizeof(T));
+    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); *p = nullptr; return KFAC_OOM; }
+    if (e != cudaSuccess) { *p = nullptr; return KFAC_CUDA_ERROR; }
+    return KFAC_OK;
+}
+
+void free_pass(PassBuffers& pb) {
+    for (int l = 0; l < KFAC_MAX_LAYERS; l++) {
+        cudaFree(pb.Z[l]);
+        cudaFree(pb.T[l]);
+        cudaFree(pb.Zb[l]);
+    }
+    cudaFree(pb.r);
+    cudaFree(pb.red_a);
+    cudaFree(pb.red_g);
+}
+
+void free_handle(kfac_pinn_handle* h) {
+    if (!h) return;
+    free_pass(h->in);
+    free_pass(h->bd);
+    tc_free(h);
+    cudaFree(h->grad);
+    cudaFree(h->dir);
+    cudaFree(h->delta_prev);
+    for (int w = 0; w < 4; w++)
+        for (int l = 0; l < KFAC_MAX_LAYERS; l++) cudaFree(h->fac[w][l]);
+    for (int l = 0; l < KFAC_MAX_LAYERS; l++) {
+        cudaFree(h->VA[l]);
+        cudaFree(h->wa[l]);
+        cudaFree(h->VB[l]);
+        cudaFree(h->wb[l]);
+    }
+    cudaFree(h->loss);
+    cudaFree(h->part);
+    cudaFree(h->lin);
+    cudaFree(h->tmp);
+    cudaFree(h->status);
+    cudaFree(h->stage);
+    free(h);
+}
+
+kfac_status_t alloc_pass(kfac_pinn_handle* h, PassBuffers& pb, int N, int S) {
+    pb.N = N;
+    pb.S = S;
+    const int L = h->cfg.L;
+    kfac_status_t st;
+    int maxw = 0;
+    for (int l = 1; l <= L; l++) {
+        size_t e = (size_t)S * N * h->dims[l];
+        if ((st = dalloc(&pb.Z[l - 1], e))) return st;
+        if ((st = dalloc(&pb.Zb[l - 1], e))) return st;
+        if (l < L && (st = dalloc(&pb.T[l - 1], e))) return st;
+        if (h->dims[l] > maxw) maxw = h->dims[l];
+    }
+    if (h->dims[0] + 1 > maxw) maxw = h->dims[0] + 1;
+    for (int l = 0; l < L; l++)
+        if (h->dims[l] + 1 > maxw) maxw = h->dims[l] + 1;
+    if ((st = dalloc(&pb.r, (size_t)N))) return st;
+    if (S > 1 && h->cfg.variant == KFAC_REDUCE) {
+        if ((st = dalloc(&pb.red_a, (size_t)N * maxw))) return st;
+        if ((st = dalloc(&pb.red_g, (size_t)N * maxw))) return st;
+    }
+    return KFAC_OK;
+}
+
+size_t partial_elems_needed(const kfac_pinn_handle* h) {
+    // Enough for the split-K partials of every Gram / weight-gradient GEMM.
+    size_t need = 0;
+    const int S = h->S;
+    for (int l = 1; l <= h->cfg.L; l++) {
+        int nin = h->dims[l - 1] + 1, hout = h->dims[l];
+        int K = S * h->cfg.max_n_int;
+        int dimsP[3] = {hout, nin, hout};
+        int dimsQ[3] = {nin, nin, hout};
+        for (int t = 0; t < 3; t++) {
+            long long tiles = (long long)((dimsP[t] + 63) / 64) * ((dimsQ[t] + 63) / 64);
+            long long want = (2LL * h->sm_count + tiles - 1) / tiles;
+            long long maxs = (K + 511) / 512;
+            if (want > maxs) want = maxs;
+            if (want < 1) want = 1;
+            size_t e = (size_t)want * dimsP[t] * dimsQ[t];
+            if (e > need) need = e;
+        }
+    }
+    return need;
+}
+
+__global__ void k_init_factor(double* M, int n, double diag) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * n) return;
+    M[i] = ((int)(i / n) == (int)(i % n)) ? diag : 0.0;
+}
+
+kfac_status_t reset_state(kfac_pinn_handle* h, cudaStream_t s) {
+    double diag = h->cfg.factor_init_identity ? 1.0 : 0.0;
+    for (int l = 1; l <= h->cfg.L; l++) {
+        int na = h->dims[l - 1] + 1, nb = h->dims[l];
+        for (int w = 0; w < 4; w++) {
+            int n = (w == KFAC_A_INT || w == KFAC_A_BDY) ? na : nb;
+            k_init_factor<<<ceil_div_u((long long)n * n, 256), 256, 0, s>>>(h->fac[w][l - 1], n, diag);
+            KFAC_LAUNCH_CHECK(h);
+        }
+    }
+    KFAC_CUDA_TRY(cudaMemsetAsync(h->delta_prev, 0, h->D * sizeof(double), s));
+    KFAC_CUDA_TRY(cudaMemsetAsync(h->dir, 0, h->D * sizeof(double), s));
+    KFAC_CUDA_TRY(cudaMemsetAsync(h->grad, 0, h->D * sizeof(double), s));
+    h->t = 0;
+    h->have_inverse = 0;
+    h->have_direction = 0;
+    return KFAC_OK;
+}
+
+inline cudaStream_t S_(void* p) { return (cudaStream_t)p; }
+
+kfac_status_t check_batch(kfac_pinn_handle* h, const void* X_int, int N_int, const void* f,
+                          const void* X_bdy, int N_bdy, const void* g) {
+    if (!h) return KFAC_BAD_ARG;
+    if (!X_int || !f || !X_bdy || !g) return KFAC_BAD_ARG;
+    if (N_int < 1 || N_int > h->cfg.max_n_int) return KFAC_BAD_ARG;
+    if (N_bdy < 1 || N_bdy > h->cfg.max_n_bdy) return KFAC_BAD_ARG;
+    return KFAC_OK;
+}
+
+kfac_status_t run_factors(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                          const double* X_int, int N_int, const double* f,
+                          const double* X_bdy, int N_bdy, const double* g, double* loss) {
+    if (h->cfg.precision == KFAC_MIXED_BF16)
+        return tc_factors(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g, loss);
+    kfac_status_t st;
+    const int S = h->S;
+    if ((st = fp64_forward(h, s, theta, X_int, N_int, h->in, S))) return st;
+    if ((st = fp64_residual_and_seed(h, s, h->in, N_int, S, f, true))) return st;
+    if ((st = fp64_backward(h, s, theta, h->in, N_int, S))) return st;
+    if ((st = fp64_forward(h, s, theta, X_bdy, N_bdy, h->bd, 1))) return st;
+    if ((st = fp64_residual_and_seed(h, s, h->bd, N_bdy, 1, g, false))) return st;
+    if ((st = fp64_backward(h, s, theta, h->bd, N_bdy, 1))) return st;
+    if ((st = fp64_loss(h, s, N_int, N_bdy, loss))) return st;
+    if ((st = fp64_grad_and_factors(h, s, X_int, N_int, X_bdy, N_bdy))) return st;
+    return KFAC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t kfac_pinn_param_count(const kfac_config_t* cfg) {
+    if (!valid_config(cfg)) return -1;
+    int64_t D = 0;
+    int prev = cfg->d;
+    for (int l = 0; l < cfg->L; l++) {
+        D += (int64_t)cfg->widths[l] * (prev + 1);
+        prev = cfg->widths[l];
+    }
+    return D;
+}
+
+const char* kfac_pinn_status_string(kfac_status_t st) {
+    switch (st) {
+        case KFAC_OK: return "KFAC_OK";
+        case KFAC_BAD_ARG: return "KFAC_BAD_ARG";
+        case KFAC_NOT_PD: return "KFAC_NOT_PD";
+        case KFAC_NONFINITE: return "KFAC_NONFINITE";
+        case KFAC_TIMEOUT: return "KFAC_TIMEOUT";
+        case KFAC_OOM: return "KFAC_OOM";
+        case KFAC_CUDA_ERROR: return "KFAC_CUDA_ERROR";
+        case KFAC_NOT_READY: return "KFAC_NOT_READY";
+    }
+    return "KFAC_UNKNOWN";
+}
+
+kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out) {
+    if (!out) return KFAC_BAD_ARG;
+    *out = nullptr;
+    if (!valid_config(cfg)) return KFAC_BAD_ARG;
+    kfac_pinn_handle* h = (kfac_pinn_handle*)calloc(1, sizeof(kfac_pinn_handle));
+    if (!h) return KFAC_OOM;
+    h->cfg = *cfg;
+    KFAC_CUDA_TRY(cudaGetDevice(&h->device));
+    KFAC_CUDA_TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
+    h->dims[0] = cfg->d;
+    for (int l = 0; l < cfg->L; l++) h->dims[l + 1] = cfg->widths[l];
+    h->woff[0] = 0;
+    for (int l = 1; l <= cfg->L; l++)
+        h->woff[l] = h->woff[l - 1] + (int64_t)h->dims[l] * (h->dims[l - 1] + 1);
+    h->D = h->woff[cfg->L];
+    h->S = cfg->d + 2;
+
+    kfac_status_t st = KFAC_OK;
+#define TRY(x) do { st = (x); if (st != KFAC_OK) { free_handle(h); return st; } } while (0)
+    TRY(alloc_pass(h, h->in, cfg->max_n_int, h->S));
+    TRY(alloc_pass(h, h->bd, cfg->max_n_bdy, 1));
+    TRY(dalloc(&h->grad, (size_t)h->D));
+    TRY(dalloc(&h->dir, (size_t)h->D));
+    TRY(dalloc(&h->delta_prev, (size_t)h->D));
+    size_t tmp = 0;
+    for (int l = 1; l <= cfg->L; l++) {
+        size_t na = h->dims[l - 1] + 1, nb = h->dims[l];
+        TRY(dalloc(&h->fac[KFAC_A_INT][l - 1], na * na));
+        TRY(dalloc(&h->fac[KFAC_A_BDY][l - 1], na * na));
+        TRY(dalloc(&h->fac[KFAC_B_INT][l - 1], nb * nb));
+        TRY(dalloc(&h->fac[KFAC_B_BDY][l - 1], nb * nb));
+        TRY(dalloc(&h->VA[l - 1], na * na));
+        TRY(dalloc(&h->wa[l - 1], na));
+        TRY(dalloc(&h->VB[l - 1], nb * nb));
+        TRY(dalloc(&h->wb[l - 1], nb));
+        if (2 * na * nb > tmp) tmp = 2 * na * nb;
+    }
+    h->tmp_elems = tmp;
+    TRY(dalloc(&h->tmp, tmp));
+    TRY(dalloc(&h->loss, 3));
+    h->part_elems = partial_elems_needed(h);
+    TRY(dalloc(&h->part, h->part_elems));
+    h->lin_elems = linalg_workspace_elems(h);
+    TRY(dalloc(&h->lin, h->lin_elems));
+    TRY(dalloc(&h->status, 1));
+    h->stage_elems = (size_t)cfg->max_n_int * (cfg->d + 1) + (size_t)cfg->max_n_bdy * (cfg->d + 1) + 8;
+    TRY(dalloc(&h->stage, h->stage_elems));
+    if (cfg->precision == KFAC_MIXED_BF16) TRY(tc_alloc(h));
+    if (cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) { free_handle(h); return KFAC_CUDA_ERROR; }
+    TRY(reset_state(h, 0));
+    if (cudaDeviceSynchronize() != cudaSuccess) { free_handle(h); return KFAC_CUDA_ERROR; }
+#undef TRY
+    *out = h;
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_destroy(kfac_handle_t h) {
+    if (!h) return KFAC_BAD_ARG;
+    cudaDeviceSynchronize();
+    free_handle(h);
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_reset(kfac_handle_t h, void* stream) {
+    if (!h) return KFAC_BAD_ARG;
+    return reset_state(h, S_(stream));
+}
+
+kfac_status_t kfac_pinn_forward_laplacian(kfac_handle_t h, void* stream, const double* theta,
+                                          const double* X, int N, double* u, double* grad,
+                                          double* lap) {
+    if (!h || !theta || !X || !u || N < 0) return KFAC_BAD_ARG;
+    cudaStream_t s = S_(stream);
+    const int S = h->S, d = h->dims[0];
+    for (int off = 0; off < N; off += h->cfg.max_n_int) {
+        int n = N - off < h->cfg.max_n_int ? N - off : h->cfg.max_n_int;
+        kfac_status_t st;
+        if (h->cfg.precision == KFAC_MIXED_BF16) {
+            st = tc_forward_laplacian(h, s, theta, X + (long long)off * d, n, u + off,
+                                      grad ? grad + (long long)off * d : nullptr, lap ? lap + off : nullptr);
+        } else {
+            st = fp64_forward(h, s, theta, X + (long long)off * d, n, h->in, S);
+            if (st == KFAC_OK)
+                st = fp64_extract_outputs(h, s, h->in, n, S, u + off,
+                                          grad ? grad + (long long)off * d : nullptr, lap ? lap + off : nullptr);
+        }
+        if (st) return st;
+    }
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_factors(kfac_handle_t h, void* stream, const double* theta,
+                                const double* X_int, int N_int, const double* f,
+                                const double* X_bdy, int N_bdy, const double* g, double* loss) {
+    kfac_status_t st = check_batch(h, X_int, N_int, f, X_bdy, N_bdy, g);
+    if (st) return st;
+    if (!theta) return KFAC_BAD_ARG;
+    return run_factors(h, S_(stream), theta, X_int, N_int, f, X_bdy, N_bdy, g, loss);
+}
+
+kfac_status_t kfac_pinn_invert(kfac_handle_t h, void* stream) {
+    if (!h) return KFAC_BAD_ARG;
+    kfac_status_t st = linalg_invert(h, S_(stream));
+    if (st == KFAC_OK) h->have_inverse = 1;
+    return st;
+}
+
+kfac_status_t kfac_pinn_precondition(kfac_handle_t h, void* stream, const double* grad, double* direction) {
+    if (!h) return KFAC_BAD_ARG;
+    if (!h->have_inverse) return KFAC_NOT_READY;
+    cudaStream_t s = S_(stream);
+    kfac_status_t st = linalg_precondition(h, s, grad ? grad : h->grad, h->dir);
+    if (st) return st;
+    h->have_direction = 1;
+    if (direction)
+        KFAC_CUDA_TRY(cudaMemcpyAsync(direction, h->dir, h->D * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_update(kfac_handle_t h, void* stream, double* theta) {
+    if (!h || !theta) return KFAC_BAD_ARG;
+    if (!h->have_direction) return KFAC_NOT_READY;
+    kfac_status_t st = linalg_update(h, S_(stream), theta);
+    if (st == KFAC_OK) h->t++;
+    return st;
+}
+
+kfac_status_t kfac_pinn_step(kfac_handle_t h, void* stream, double* theta,
+                             const double* X_int, int N_int, const double* f,
+                             const double* X_bdy, int N_bdy, const double* g, double* loss) {
+    kfac_status_t st = check_batch(h, X_int, N_int, f, X_bdy, N_bdy, g);
+    if (st) return st;
+    if (!theta) return KFAC_BAD_ARG;
+    cudaStream_t s = S_(stream);
+    if ((st = run_factors(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g, loss))) return st;
+    if ((st = kfac_pinn_invert(h, stream))) return st;
+    if ((st = kfac_pinn_precondition(h, stream, nullptr, nullptr))) return st;
+    return kfac_pinn_update(h, stream, theta);
+}
+
+kfac_status_t kfac_pinn_step_host(kfac_handle_t h, void* stream, double* theta,
+                                  const double* X_int_host, int N_int, const double* f_host,
+                                  const double* X_bdy_host, int N_bdy, const double* g_host,
+                                  double* loss_host) {
+    kfac_status_t st = check_batch(h, X_int_host, N_int, f_host, X_bdy_host, N_bdy, g_host);
+    if (st) return st;
+    if (!theta) return KFAC_BAD_ARG;
+    cudaStream_t s = S_(stream);
+    const int d = h->dims[0];
+    double* xi = h->stage;
+    double* fi = xi + (size_t)N_int * d;
+    double* xb = fi + N_int;
+    double* gb = xb + (size_t)N_bdy * d;
+    KFAC_CUDA_TRY(cudaMemcpyAsync(xi, X_int_host, (size_t)N_int * d * sizeof(double), cudaMemcpyHostToDevice, s));
+    KFAC_CUDA_TRY(cudaMemcpyAsync(fi, f_host, (size_t)N_int * sizeof(double), cudaMemcpyHostToDevice, s));
+    KFAC_CUDA_TRY(cudaMemcpyAsync(xb, X_bdy_host, (size_t)N_bdy * d * sizeof(double), cudaMemcpyHostToDevice, s));
+    KFAC_CUDA_TRY(cudaMemcpyAsync(gb, g_host, (size_t)N_bdy * sizeof(double), cudaMemcpyHostToDevice, s));
+    if ((st = kfac_pinn_step(h, stream, theta, xi, N_int, fi, xb, N_bdy, gb, h->loss))) return st;
+    if (loss_host)
+        KFAC_CUDA_TRY(cudaMemcpyAsync(loss_host, h->loss, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KFAC_CUDA_TRY(cudaStreamSynchronize(s));
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_get_factor(kfac_handle_t h, void* stream, int layer, int which, double* dst) {
+    if (!h || !dst || layer < 1 || layer > h->cfg.L || which < 0 || which > 3) return KFAC_BAD_ARG;
+    size_t n = (which == KFAC_A_INT || which == KFAC_A_BDY) ? h->dims[layer - 1] + 1 : h->dims[layer];
+    KFAC_CUDA_TRY(cudaMemcpyAsync(dst, h->fac[which][layer - 1], n * n * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, S_(stream)));
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_set_factor(kfac_handle_t h, void* stream, int layer, int which, const double* src) {
+    if (!h || !src || layer < 1 || layer > h->cfg.L || which < 0 || which > 3) return KFAC_BAD_ARG;
+    size_t n = (which == KFAC_A_INT || which == KFAC_A_BDY) ? h->dims[layer - 1] + 1 : h->dims[layer];
+    KFAC_CUDA_TRY(cudaMemcpyAsync(h->fac[which][layer - 1], src, n * n * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, S_(stream)));
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_get_gradient(kfac_handle_t h, void* stream, double* dst) {
+    if (!h || !dst) return KFAC_BAD_ARG;
+    KFAC_CUDA_TRY(cudaMemcpyAsync(dst, h->grad, h->D * sizeof(double), cudaMemcpyDeviceToDevice, S_(stream)));
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_get_direction(kfac_handle_t h, void* stream, double* dst) {
+    if (!h || !dst) return KFAC_BAD_ARG;
+    KFAC_CUDA_TRY(cudaMemcpyAsync(dst, h->dir, h->D * sizeof(double), cudaMemcpyDeviceToDevice, S_(stream)));
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_sync_status(kfac_handle_t h, kfac_status_t* status) {
+    if (!h || !status) return KFAC_BAD_ARG;
+    KFAC_CUDA_TRY(cudaDeviceSynchronize());
+    int v = 0;
+    KFAC_CUDA_TRY(cudaMemcpy(&v, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    KFAC_CUDA_TRY(cudaMemset(h->status, 0, sizeof(int)));
+    *status = (kfac_status_t)v;
+    return KFAC_OK;
+}
+
+int64_t kfac_pinn_launch_count(kfac_handle_t h) { return h ? h->launches : -1; }
+
+}  // extern "C"

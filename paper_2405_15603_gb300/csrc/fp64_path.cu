@@ -1,0 +1,402 @@
+// FP64 SIMT path: forward Laplacian, residuals, adjoint, gradient and factors.
+//
+// Every stage is FP64.  The layer GEMMs, adjoint GEMMs, weight gradient and
+// factor Grams go through the tiled FP64 GEMM of gemm_fp64.cuh; the tanh
+// Taylor rule and its adjoint are element-wise kernels that walk the S
+// shared columns of one (point, feature) pair.
+#include "kfac_internal.cuh"
+#include "gemm_fp64.cuh"
+
+using namespace kfac;
+
+namespace {
+
+constexpr int EW_THREADS = 256;
+
+// --------------------------------------------------------------------------
+// First layer (Sec. 3.1): the inputs are (x, e_1..e_d, 0), so the tangent
+// columns of Z^{(1)} are the columns of W_1 and its Laplacian column is 0.
+// Writes Z^{(1)} and, when a tanh follows, T^{(1)} by the rule of Eq. 6.
+// --------------------------------------------------------------------------
+__global__ void k_layer1_fwd(const double* __restrict__ W, const double* __restrict__ X,
+                             double* __restrict__ Z, double* __restrict__ T,
+                             int N, int d, int h, int S, int lap_first, int has_act) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * h) return;
+    int n = (int)(idx / h), j = (int)(idx % h);
+    double a0 = W[(long long)j + (long long)h * d];   // bias column
+    for (int k = 0; k < d; k++) a0 = fma(W[j + (long long)h * k], X[(long long)n * d + k], a0);
+    const long long blk = (long long)N * h;
+    const long long o = (long long)n * h + j;
+    Z[o] = a0;
+    if (S > 1) {
+        for (int i = 0; i < d; i++) Z[(1 + i) * blk + o] = W[j + (long long)h * i];
+        Z[(S - 1) * blk + o] = 0.0;
+    }
+    if (!has_act) return;
+    double y = tanh(a0);
+    double s1 = 1.0 - y * y;
+    double s2 = -2.0 * y * s1;
+    T[o] = y;
+    if (S > 1) {
+        double sumsq = 0.0;
+        for (int i = 0; i < d; i++) {
+            double w = W[j + (long long)h * i];
+            T[(1 + i) * blk + o] = s1 * w;
+            if (1 + i >= lap_first) sumsq = fma(w, w, sumsq);
+        }
+        T[(S - 1) * blk + o] = s2 * sumsq;
+    }
+}
+
+// Tanh through the Taylor columns (Eq. 6):
+//   y_0 = tanh(a_0), y_i = s1 a_i, y_D = s1 a_D + s2 sum_{i in C} a_i^2
+// with s1 = 1 - y_0^2 and s2 = -2 y_0 s1; C = tangent columns >= lap_first.
+__global__ void k_act_fwd(const double* __restrict__ Z, double* __restrict__ T,
+                          int N, int S, int h, int lap_first) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long blk = (long long)N * h;
+    if (idx >= blk) return;
+    double a0 = Z[idx];
+    double y = tanh(a0);
+    double s1 = 1.0 - y * y;
+    T[idx] = y;
+    if (S == 1) return;
+    double s2 = -2.0 * y * s1;
+    double sumsq = 0.0;
+    for (int s = 1; s < S - 1; s++) {
+        double a = Z[s * blk + idx];
+        T[s * blk + idx] = s1 * a;
+        if (s >= lap_first) sumsq = fma(a, a, sumsq);
+    }
+    T[(S - 1) * blk + idx] = fma(s1, Z[(S - 1) * blk + idx], s2 * sumsq);
+}
+
+// Adjoint of k_act_fwd, in place on G (incoming ybar -> outgoing abar):
+//   abar_D = s1 ybar_D
+//   abar_i = s1 ybar_i + 2 s2 a_i ybar_D            (i in C)
+//   abar_0 = s1 ybar_0 + s2 sum_i a_i ybar_i + (s2 a_D + s3 sum_C a_i^2) ybar_D
+// with s3 = -2 s1 (1 - 3 y^2).
+__global__ void k_act_bwd(const double* __restrict__ Z, double* __restrict__ G,
+                          int N, int S, int h, int lap_first) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long blk = (long long)N * h;
+    if (idx >= blk) return;
+    double a0 = Z[idx];
+    double y = tanh(a0);
+    double s1 = 1.0 - y * y;
+    if (S == 1) { G[idx] = s1 * G[idx]; return; }
+    double s2 = -2.0 * y * s1;
+    double s3 = -2.0 * s1 * (1.0 - 3.0 * y * y);
+    double yd = G[(S - 1) * blk + idx];
+    double y0 = G[idx];
+    double cross = 0.0, sumsq = 0.0;
+    for (int s = 1; s < S - 1; s++) {
+        double a = Z[s * blk + idx];
+        double yb = G[s * blk + idx];
+        cross = fma(a, yb, cross);
+        double ab = s1 * yb;
+        if (s >= lap_first) {
+            sumsq = fma(a, a, sumsq);
+            ab = fma(2.0 * s2 * a, yd, ab);
+        }
+        G[s * blk + idx] = ab;
+    }
+    double aD = Z[(S - 1) * blk + idx];
+    G[idx] = s1 * y0 + s2 * cross + (s2 * aD + s3 * sumsq) * yd;
+    G[(S - 1) * blk + idx] = s1 * yd;
+}
+
+// Residuals (Eq. 1): interior r = -Lap u - f, or du/dt - kappa Lap_x u - f
+// for the heat operator; boundary r = u - g.  Z_L has one feature per row.
+__global__ void k_residual(const double* __restrict__ ZL, const double* __restrict__ target,
+                           double* __restrict__ r, int N, int S, int interior, int heat,
+                           double kappa) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double v;
+    if (!interior) v = ZL[n] - target[n];
+    else if (heat) v = ZL[N + n] - kappa * ZL[(long long)(S - 1) * N + n] - target[n];
+    else v = -ZL[(long long)(S - 1) * N + n] - target[n];
+    r[n] = v;
+}
+
+// Seed of the backward pass, c = dr/dZ^{(L)} (one row per point).
+__global__ void k_seed(double* __restrict__ ZbL, int N, int S, int interior, int heat, double kappa) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * S) return;
+    int s = (int)(idx / N);
+    double c = 0.0;
+    if (!interior) c = 1.0;
+    else if (heat) c = (s == 1) ? 1.0 : (s == S - 1 ? -kappa : 0.0);
+    else c = (s == S - 1) ? -1.0 : 0.0;
+    ZbL[idx] = c;
+}
+
+// loss[1] = sum r^2 / (2N), loss[2] = sum rb^2 / (2Nb), loss[0] = loss[1] + loss[2].
+__global__ void k_loss(const double* __restrict__ r, int N, const double* __restrict__ rb, int Nb,
+                       double* __restrict__ loss, int* status) {
+    __shared__ double sh[2][32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) a = fma(r[i], r[i], a);
+    for (int i = threadIdx.x; i < Nb; i += blockDim.x) b = fma(rb[i], rb[i], b);
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    int w = threadIdx.x / 32, l = threadIdx.x % 32;
+    if (l == 0) { sh[0][w] = a; sh[1][w] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, B = 0.0;
+        for (int i = 0; i < (int)(blockDim.x / 32); i++) { A += sh[0][i]; B += sh[1][i]; }
+        double li = A / (2.0 * N), lb = B / (2.0 * Nb);
+        loss[0] = li + lb;
+        loss[1] = li;
+        loss[2] = lb;
+        if (!isfinite(li + lb)) latch_status(status, KFAC_NONFINITE);
+    }
+}
+
+// out[p*osp + q*osq] = (accumulate ? out : 0) + scale * sum_z part[z][p][q],
+// or the EMA  out = beta * out + (1 - beta) * scale * sum_z part  when ema.
+__global__ void k_reduce_partials(const double* __restrict__ part, int splits, int P, int Q,
+                                  double scale, double* __restrict__ out, long long osp,
+                                  long long osq, int accumulate, int ema, double beta,
+                                  int* status) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long PQ = (long long)P * Q;
+    if (idx >= PQ) return;
+    double v = 0.0;
+    for (int z = 0; z < splits; z++) v += part[z * PQ + idx];
+    v *= scale;
+    int p = (int)(idx / Q), q = (int)(idx % Q);
+    long long o = (long long)p * osp + (long long)q * osq;
+    if (ema) v = beta * out[o] + (1.0 - beta) * v;
+    else if (accumulate) v += out[o];
+    if (!isfinite(v)) latch_status(status, KFAC_NONFINITE);
+    out[o] = v;
+}
+
+// Per-point sums over the S shared columns (KFAC-reduce reading):
+// out[n*ncols + q] = scale * sum_s R(s*N + n, q).
+template <class R>
+__global__ void k_colsum(R rows, int N, int S, int ncols, double scale, double* __restrict__ out) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * ncols) return;
+    int n = (int)(idx / ncols), q = (int)(idx % ncols);
+    double v = 0.0;
+    for (int s = 0; s < S; s++) v += rows(s * N + n, q);
+    out[idx] = scale * v;
+}
+
+template <class LA, class LB>
+kfac_status_t reduce_gemm(kfac_pinn_handle* h, cudaStream_t s, int P, int Q, int K, LA la, LB lb,
+                          double scale, double* out, long long osp, long long osq, int accumulate,
+                          int ema, double beta) {
+    int splits = choose_splits(P, Q, K, h->sm_count);
+    long long cap = (long long)(h->part_elems / ((size_t)P * Q));
+    if (cap < 1) return KFAC_BAD_ARG;
+    if (splits > cap) splits = (int)cap;
+    int kchunk = (K + splits - 1) / splits;
+    kchunk = ((kchunk + GK - 1) / GK) * GK;
+    if (kchunk < GK) kchunk = GK;
+    splits = (K + kchunk - 1) / kchunk;
+    if (cudaSuccess != launch_dgemm(s, P, Q, K, splits, la, lb, EpPartial{h->part, P, Q}))
+        return KFAC_CUDA_ERROR;
+    h->launches++;
+    long long PQ = (long long)P * Q;
+    k_reduce_partials<<<ceil_div_u(PQ, EW_THREADS), EW_THREADS, 0, s>>>(
+        h->part, splits, P, Q, scale, out, osp, osq, accumulate, ema, beta, h->status);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// Public (library-internal) entry points of the FP64 path
+// --------------------------------------------------------------------------
+kfac_status_t fp64_forward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                           const double* X, int N, PassBuffers& pb, int S) {
+    const int L = h->cfg.L, d = h->dims[0];
+    const int lap_first = (h->cfg.op == KFAC_OP_HEAT) ? 2 : 1;
+    {
+        int h1 = h->dims[1];
+        long long cnt = (long long)N * h1;
+        k_layer1_fwd<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(
+            theta + h->woff[0], X, pb.Z[0], pb.T[0], N, d, h1, S, lap_first, L > 1);
+        KFAC_LAUNCH_CHECK(h);
+    }
+    for (int l = 2; l <= L; l++) {
+        int hin = h->dims[l - 1], hout = h->dims[l];
+        const double* W = theta + h->woff[l - 1];
+        Strided<true> A{pb.T[l - 2], hin, 1};
+        Strided<true> B{W, hout, 1};   // B(k, j) = W~[j, k] = W[j + hout*k]
+        EpStore ep{pb.Z[l - 1], hout, 1, 1.0, 0.0, W + (long long)hout * hin, 1, N};
+        if (cudaSuccess != launch_dgemm(s, S * N, hout, hin, 1, A, B, ep)) return KFAC_CUDA_ERROR;
+        h->launches++;
+        if (l < L) {
+            long long cnt = (long long)N * hout;
+            k_act_fwd<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[l - 1], pb.T[l - 1], N,
+                                                                         S, hout, lap_first);
+            KFAC_LAUNCH_CHECK(h);
+        }
+    }
+    return KFAC_OK;
+}
+
+kfac_status_t fp64_residual_and_seed(kfac_pinn_handle* h, cudaStream_t s, PassBuffers& pb, int N,
+                                     int S, const double* target, bool interior) {
+    const int L = h->cfg.L;
+    const int heat = h->cfg.op == KFAC_OP_HEAT;
+    k_residual<<<ceil_div_u(N, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[L - 1], target, pb.r, N, S,
+                                                                interior, heat, h->cfg.kappa);
+    KFAC_LAUNCH_CHECK(h);
+    k_seed<<<ceil_div_u((long long)N * S, EW_THREADS), EW_THREADS, 0, s>>>(pb.Zb[L - 1], N, S,
+                                                                            interior, heat,
+                                                                            h->cfg.kappa);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+kfac_status_t fp64_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                            PassBuffers& pb, int N, int S) {
+    const int L = h->cfg.L;
+    const int lap_first = (h->cfg.op == KFAC_OP_HEAT) ? 2 : 1;
+    for (int l = L; l >= 2; l--) {
+        int hin = h->dims[l - 1], hout = h->dims[l];
+        const double* W = theta + h->woff[l - 1];
+        // Tbar = Zbar_l W_l (bias column dropped):  (S*N x hout)(hout x hin)
+        Strided<true> A{pb.Zb[l - 1], hout, 1};
+        Strided<false> B{W, 1, hout};  // B(i, q) = W~[i, q] = W[i + hout*q]
+        EpStore ep{pb.Zb[l - 2], hin, 1, 1.0, 0.0, nullptr, 0, 0};
+        if (cudaSuccess != launch_dgemm(s, S * N, hin, hout, 1, A, B, ep)) return KFAC_CUDA_ERROR;
+        h->launches++;
+        long long cnt = (long long)N * hin;
+        k_act_bwd<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[l - 2], pb.Zb[l - 2], N, S,
+                                                                     hin, lap_first);
+        KFAC_LAUNCH_CHECK(h);
+    }
+    return KFAC_OK;
+}
+
+kfac_status_t fp64_loss(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N_bdy, double* loss_out) {
+    k_loss<<<1, 1024, 0, s>>>(h->in.r, N_int, h->bd.r, N_bdy, h->loss, h->status);
+    KFAC_LAUNCH_CHECK(h);
+    if (loss_out && loss_out != h->loss)
+        KFAC_CUDA_TRY(cudaMemcpyAsync(loss_out, h->loss, 3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return KFAC_OK;
+}
+
+namespace {
+
+template <class RowsI, class RowsB>
+kfac_status_t layer_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, int l, RowsI in_i,
+                                     RowsB in_b, int N, int Nb) {
+    const int S = h->S;
+    const int hout = h->dims[l], nin = h->dims[l - 1] + 1;
+    const double beta = h->cfg.beta;
+    double* gW = h->grad + h->woff[l - 1];
+    kfac_status_t st;
+    // Weight gradient: (1/N) sum_rows r_n g_row T^_row^T  +  (1/Nb) sum ...
+    {
+        Transposed<WeightedRows> A{WeightedRows{h->in.Zb[l - 1], hout, N, h->in.r}};
+        st = reduce_gemm(h, s, hout, nin, S * N, A, in_i, 1.0 / N, gW, 1, hout, 0, 0, 0.0);
+        if (st != KFAC_OK) return st;
+        Transposed<WeightedRows> Ab{WeightedRows{h->bd.Zb[l - 1], hout, Nb, h->bd.r}};
+        st = reduce_gemm(h, s, hout, nin, Nb, Ab, in_b, 1.0 / Nb, gW, 1, hout, 1, 0, 0.0);
+        if (st != KFAC_OK) return st;
+    }
+    // Interior factors.
+    if (h->cfg.variant == KFAC_EXPAND) {
+        st = reduce_gemm(h, s, nin, nin, S * N, Transposed<RowsI>{in_i}, in_i, 1.0 / ((double)N * S),
+                         h->fac[KFAC_A_INT][l - 1], nin, 1, 0, 1, beta);
+        if (st != KFAC_OK) return st;
+        WeightedRows G{h->in.Zb[l - 1], hout, N, nullptr};
+        st = reduce_gemm(h, s, hout, hout, S * N, Transposed<WeightedRows>{G}, G, 1.0 / N,
+                         h->fac[KFAC_B_INT][l - 1], hout, 1, 0, 1, beta);
+        if (st != KFAC_OK) return st;
+    } else {
+        // KFAC-reduce: abar_n = (1/S) sum_s T^_{n,s}, gbar_n = sum_s g_{n,s}.
+        k_colsum<<<ceil_div_u((long long)N * nin, EW_THREADS), EW_THREADS, 0, s>>>(
+            in_i, N, S, nin, 1.0 / S, h->in.red_a);
+        KFAC_LAUNCH_CHECK(h);
+        WeightedRows G{h->in.Zb[l - 1], hout, N, nullptr};
+        k_colsum<<<ceil_div_u((long long)N * hout, EW_THREADS), EW_THREADS, 0, s>>>(
+            G, N, S, hout, 1.0, h->in.red_g);
+        KFAC_LAUNCH_CHECK(h);
+        Strided<true> Ra{h->in.red_a, nin, 1};
+        Strided<true> Rg{h->in.red_g, hout, 1};
+        st = reduce_gemm(h, s, nin, nin, N, Strided<false>{h->in.red_a, 1, nin}, Ra, 1.0 / N,
+                         h->fac[KFAC_A_INT][l - 1], nin, 1, 0, 1, beta);
+        if (st != KFAC_OK) return st;
+        st = reduce_gemm(h, s, hout, hout, N, Strided<false>{h->in.red_g, 1, hout}, Rg, 1.0 / N,
+                         h->fac[KFAC_B_INT][l - 1], hout, 1, 0, 1, beta);
+        if (st != KFAC_OK) return st;
+    }
+    // Boundary factors (classic KFAC, S = 1).
+    st = reduce_gemm(h, s, nin, nin, Nb, Transposed<RowsB>{in_b}, in_b, 1.0 / Nb,
+                     h->fac[KFAC_A_BDY][l - 1], nin, 1, 0, 1, beta);
+    if (st != KFAC_OK) return st;
+    WeightedRows Gb{h->bd.Zb[l - 1], hout, Nb, nullptr};
+    st = reduce_gemm(h, s, hout, hout, Nb, Transposed<WeightedRows>{Gb}, Gb, 1.0 / Nb,
+                     h->fac[KFAC_B_BDY][l - 1], hout, 1, 0, 1, beta);
+    return st;
+}
+
+}  // namespace
+
+kfac_status_t fp64_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, const double* X_int,
+                                    int N_int, const double* X_bdy, int N_bdy) {
+    const int L = h->cfg.L, d = h->dims[0];
+    for (int l = 1; l <= L; l++) {
+        kfac_status_t st;
+        if (l == 1) {
+            st = layer_grad_and_factors(h, s, 1, InputRows{X_int, d, N_int}, InputRows{X_bdy, d, N_bdy},
+                                        N_int, N_bdy);
+        } else {
+            int hin = h->dims[l - 1];
+            st = layer_grad_and_factors(h, s, l, ActRows{h->in.T[l - 2], hin, N_int},
+                                        ActRows{h->bd.T[l - 2], hin, N_bdy}, N_int, N_bdy);
+        }
+        if (st != KFAC_OK) return st;
+    }
+    return KFAC_OK;
+}
+
+namespace {
+__global__ void k_extract(const double* __restrict__ ZL, int N, int S, int d, double* u,
+                          double* grad, double* lap) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    if (u) u[n] = ZL[n];
+    if (grad)
+        for (int i = 0; i < d; i++) grad[(long long)n * d + i] = ZL[(long long)(1 + i) * N + n];
+    if (lap) lap[n] = ZL[(long long)(S - 1) * N + n];
+}
+}  // namespace
+
+kfac_status_t fp64_extract_outputs(kfac_pinn_handle* h, cudaStream_t s, PassBuffers& pb, int N,
+                                   int S, double* u, double* grad, double* lap) {
+    k_extract<<<ceil_div_u(N, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[h->cfg.L - 1], N, S, h->dims[0],
+                                                               u, grad, lap);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+// Generic strided FP64 GEMM used by the linear-algebra code.
+kfac_status_t dgemm_strided(kfac_pinn_handle* h, cudaStream_t s, int P, int Q, int K,
+                            const double* A, long long a_sp, long long a_sk,
+                            const double* B, long long b_sk, long long b_sq,
+                            double* C, long long c_sp, long long c_sq, double alpha, double beta) {
+    EpStore ep{C, c_sp, c_sq, alpha, beta, nullptr, 0, 0};
+    cudaError_t e;
+    bool akf = (a_sk == 1), bqf = (b_sq == 1);
+    if (akf && bqf) e = launch_dgemm(s, P, Q, K, 1, Strided<true>{A, a_sp, a_sk}, Strided<true>{B, b_sk, b_sq}, ep);
+    else if (akf) e = launch_dgemm(s, P, Q, K, 1, Strided<true>{A, a_sp, a_sk}, Strided<false>{B, b_sk, b_sq}, ep);
+    else if (bqf) e = launch_dgemm(s, P, Q, K, 1, Strided<false>{A, a_sp, a_sk}, Strided<true>{B, b_sk, b_sq}, ep);
+    else e = launch_dgemm(s, P, Q, K, 1, Strided<false>{A, a_sp, a_sk}, Strided<false>{B, b_sk, b_sq}, ep);
+    h->launches++;
+    return e == cudaSuccess ? KFAC_OK : KFAC_CUDA_ERROR;
+}

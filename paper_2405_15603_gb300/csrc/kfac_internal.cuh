@@ -1,0 +1,131 @@
+// Internal declarations shared by the translation units of libkfacpinn.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/kfac_pinn.h"
+
+#define KFAC_DEV __device__ __forceinline__
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+// Activations of one pass are stored column-block-major: the S Taylor columns
+// of all N points form S consecutive blocks of N rows, each row holding the h
+// features of one (column, point) pair:  X[(s * N + n) * h + j].  A layer's
+// linear map is then one GEMM over M = S*N rows, the value rows are the
+// first block (the only rows that see the bias) and the Laplacian rows the
+// last block.
+struct PassBuffers {
+    int N;           // capacity in points
+    int S;           // shared columns (d + 2 for the interior, 1 for the boundary)
+    double* Z[KFAC_MAX_LAYERS];    // pre-activation outputs Z^{(l)}       (S*N x h_l)
+    double* T[KFAC_MAX_LAYERS];    // post-activation T^{(l)}, l < L       (S*N x h_l)
+    double* Zb[KFAC_MAX_LAYERS];   // adjoints g^{(l)} = dr/dZ^{(l)}       (S*N x h_l)
+    double* r;                     // residuals                            (N)
+    // reduce-variant scratch: per-point column sums (N x max width)
+    double* red_a;
+    double* red_g;
+    // mixed-precision path (bf16 operands, see tc_path.cu)
+    void* mx;
+};
+
+struct kfac_pinn_handle {
+    kfac_config_t cfg;
+    int dims[KFAC_MAX_LAYERS + 1];          // h_0..h_L
+    int64_t woff[KFAC_MAX_LAYERS + 1];      // offset of W~_l in theta (l = 0..L-1), woff[L] = D
+    int64_t D;
+    int S;
+    int device;
+    int sm_count;
+
+    PassBuffers in;   // interior pass
+    PassBuffers bd;   // boundary pass
+
+    double* grad;         // D
+    double* dir;          // D
+    double* delta_prev;   // D
+    double* fac[4][KFAC_MAX_LAYERS];      // EMA factors A_int, B_int, A_bdy, B_bdy (n x n)
+    double* VA[KFAC_MAX_LAYERS];          // generalized eigenvectors (na x na, row-major)
+    double* wa[KFAC_MAX_LAYERS];          // generalized eigenvalues (na)
+    double* VB[KFAC_MAX_LAYERS];
+    double* wb[KFAC_MAX_LAYERS];
+    double* loss;                         // 3 doubles
+    double* part;                         // split-K partial sums
+    size_t part_elems;
+    double* lin;                          // linear-algebra workspace
+    size_t lin_elems;
+    double* tmp;                          // precondition temporaries
+    size_t tmp_elems;
+    int* status;                          // device status word
+    // host staging for kfac_pinn_step_host
+    double* stage;                        // device copy of the host batch
+    size_t stage_elems;
+
+    int t;                 // completed steps
+    int have_inverse;
+    int have_direction;
+    long long launches;    // kernels launched (host counter)
+};
+
+// ---------------------------------------------------------------------------
+// Status helpers
+// ---------------------------------------------------------------------------
+KFAC_DEV void latch_status(int* status, int code) {
+    // first error wins
+    atomicCAS(status, 0, code);
+}
+
+#define KFAC_CUDA_TRY(expr)                                   \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return KFAC_CUDA_ERROR;        \
+    } while (0)
+
+#define KFAC_LAUNCH_CHECK(h)                                  \
+    do {                                                      \
+        (h)->launches++;                                      \
+        cudaError_t _e = cudaGetLastError();                  \
+        if (_e != cudaSuccess) return KFAC_CUDA_ERROR;        \
+    } while (0)
+
+static inline unsigned ceil_div_u(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// FP64 path (fp64_path.cu)
+// ---------------------------------------------------------------------------
+kfac_status_t fp64_forward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                           const double* X, int N, PassBuffers& pb, int S);
+kfac_status_t fp64_residual_and_seed(kfac_pinn_handle* h, cudaStream_t s, PassBuffers& pb, int N,
+                                     int S, const double* target, bool interior);
+kfac_status_t fp64_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                            PassBuffers& pb, int N, int S);
+kfac_status_t fp64_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, const double* X_int,
+                                    int N_int, const double* X_bdy, int N_bdy);
+kfac_status_t fp64_loss(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N_bdy, double* loss_out);
+kfac_status_t fp64_extract_outputs(kfac_pinn_handle* h, cudaStream_t s, PassBuffers& pb, int N,
+                                   int S, double* u, double* grad, double* lap);
+
+// ---------------------------------------------------------------------------
+// Linear algebra (linalg.cu)
+// ---------------------------------------------------------------------------
+size_t linalg_workspace_elems(const kfac_pinn_handle* h);
+kfac_status_t linalg_invert(kfac_pinn_handle* h, cudaStream_t s);
+kfac_status_t linalg_precondition(kfac_pinn_handle* h, cudaStream_t s, const double* grad,
+                                  double* dir);
+kfac_status_t linalg_update(kfac_pinn_handle* h, cudaStream_t s, double* theta);
+
+// ---------------------------------------------------------------------------
+// Generic FP64 GEMM launchers (gemm_fp64.cu)
+// ---------------------------------------------------------------------------
+// C(p, q) = sum_k A(p, k) B(k, q) with strided operands:
+//   A(p, k) = A[p * a_sp + k * a_sk],  B(k, q) = B[k * b_sk + q * b_sq]
+// and C(p, q) written to C[p * c_sp + q * c_sq] as alpha * acc (+ beta * C if
+// beta != 0).  Strides are in elements.
+kfac_status_t dgemm_strided(kfac_pinn_handle* h, cudaStream_t s, int P, int Q, int K,
+                            const double* A, long long a_sp, long long a_sk,
+                            const double* B, long long b_sk, long long b_sq,
+                            double* C, long long c_sp, long long c_sq, double alpha, double beta);

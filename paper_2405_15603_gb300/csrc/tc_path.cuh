@@ -1,0 +1,11 @@
+// Mixed-precision (tcgen05 BF16) path: declarations (implemented in tc_path.cu).
+#pragma once
+#include "kfac_internal.cuh"
+
+kfac_status_t tc_alloc(kfac_pinn_handle* h);
+void tc_free(kfac_pinn_handle* h);
+kfac_status_t tc_factors(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                         const double* X_int, int N_int, const double* f,
+                         const double* X_bdy, int N_bdy, const double* g, double* loss);
+kfac_status_t tc_forward_laplacian(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                                   const double* X, int N, double* u, double* grad, double* lap);
