@@ -1,0 +1,386 @@
+"""Benchmark: KFAC steps/s for the 100-d Poisson PINN (100->768->768->512->512->1).
+
+One step = one whole KFAC step (forward Laplacian on 2048 interior points,
+plain forward on 512 boundary points, residuals and loss, adjoint, gradient,
+Kronecker factors with EMA, FP64 Kronecker-sum inverse, preconditioning,
+update), with the collocation points resampled every step from a seeded
+stream (App. A.5 workload shape; synthetic data).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
+    python bench.py --impl reference ...    # the FP64 CPU oracle, timed on host cores
+
+Prints one JSON line on rank 0.  Under torchrun (N > 1) every rank runs an
+independent replica (the path does not shard across GPUs in this design) and
+the value is the total steps/s of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import inputs as si  # noqa: E402
+
+METRIC = "KFAC steps/s on d=100 MLP vs plain FP64 GPU path at equal L2 error; Gram % peak"
+WORKLOAD = si.WORKLOADS["poisson100d"]
+WORKLOAD_NAME = "poisson100d_100-768-768-512-512-1_2048int_512bdy_resampled"
+# KFAC hyper-parameters of the timed run (identical for every precision).
+HYPER = dict(lam=1e-3, beta=0.95, lr=0.05, momentum=0.0, init_identity=True)
+L2_BYTES = 129 * 1024 * 1024
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return p, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_batches(n, seed_base):
+    prob = WORKLOAD.prob
+    return [si.make_batch(prob, WORKLOAD.n_int, WORKLOAD.n_bdy, seed=seed_base, step=k) for k in range(n)]
+
+
+# ---------------------------------------------------------------------------
+# CUDA arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_2405_15603_gb300 import build as _build
+    _build.build()
+    from paper_2405_15603_gb300.api import KfacPinn
+
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    prob = WORKLOAD.prob
+    widths = WORKLOAD.widths
+    seed = 1000 * rank
+
+    def new_opt(precision):
+        return KfacPinn(prob.d, widths, device=str(dev), precision=precision,
+                        max_n_int=WORKLOAD.n_int, max_n_bdy=WORKLOAD.n_bdy, **HYPER)
+
+    def to_dev(batch):
+        return tuple(torch.tensor(a, device=dev) for a in batch)
+
+    K, W = args.steps, args.warmup
+    host_batches = make_batches(K + W, seed)
+    dev_batches = [to_dev(b) for b in host_batches]
+    theta0 = si.xavier_theta(prob.d, widths, seed)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed_steps(opt, theta, batches, warm, steps, timing=False):
+        for k in range(warm):
+            opt.step(theta, *batches[k])
+        torch.cuda.synchronize()
+        if timing:
+            opt.timing_enable(True)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        launches0 = opt.launch_count()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()                       # evict L2 between steps (outside the events)
+            starts[k].record()
+            opt.step(theta, *batches[warm + k])
+            ends[k].record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if world > 1:
+            torch.distributed.barrier()
+        ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+        launches = opt.launch_count() - launches0
+        tim = opt.timing_read() if timing else None
+        if timing:
+            opt.timing_enable(False)
+        return ms, wall, launches, tim
+
+    # ---- main arm ----------------------------------------------------------
+    opt = new_opt(args.precision)
+    theta = torch.tensor(theta0, device=dev)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ms, wall, launches, tim = timed_steps(opt, theta, dev_batches, W, K, timing=True)
+    clocks = sampler.stop()
+    status = opt.sync_status()
+    print(f"[bench] main arm: {ms / K:.3f} ms/step, status {status}, classes {tim}", file=sys.stderr, flush=True)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * K / (ms_max / 1000.0)
+
+    # ---- end to end through the C-ABI with host buffers -------------------
+    import ctypes
+    pinned = []
+    for b in host_batches:
+        pinned.append(tuple(torch.from_numpy(a).pin_memory() for a in b))
+    theta_e = torch.tensor(theta0, device=dev)
+    opt_e = new_opt(args.precision)
+    loss_host = np.zeros(3)
+    for k in range(W):
+        opt_e.step_host(theta_e, *pinned[k], loss_host=loss_host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K):
+        opt_e.step_host(theta_e, *pinned[W + k], loss_host=loss_host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(a.size * 8 for a in host_batches[0])
+    e2e = {"value": world * K / e2e_s if world == 1 else None, "unit": "steps/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 24}
+    if world > 1:
+        e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(e_t, op=torch.distributed.ReduceOp.MAX)
+        e2e["value"] = world * K / float(e_t.item())
+    opt_e.close()
+
+    # ---- plain FP64 GPU path beside it (same workload, fewer steps) -------
+    fp64 = None
+    if args.precision != "fp64" and args.fp64_steps > 0 and rank == 0:
+        opt64 = new_opt("fp64")
+        th64 = torch.tensor(theta0, device=dev)
+        ms64, _, _, _ = timed_steps(opt64, th64, dev_batches, 1, args.fp64_steps)
+        fp64 = {"value": args.fp64_steps / (ms64 / 1000.0), "unit": "steps/s",
+                "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
+        opt64.close()
+
+    # ---- roofline of the dominant kernel class -----------------------------
+    peaks, peak_kind = load_peaks()
+    dom = max(tim.items(), key=lambda kv: kv[1]["ms"])
+    name, rec = dom
+    per_launch_ms = rec["ms"] / max(rec["launches"], 1)
+    per_launch_work = rec["work"] / max(rec["launches"], 1)
+    if name in ("layer_gemm", "adjoint_gemm", "gram", "precond", "eig"):
+        unit = "TFLOP/s"
+        achieved = per_launch_work / (per_launch_ms / 1e3) / 1e12
+        if args.precision == "fp64" or name in ("eig", "precond"):
+            bound, peak, peak_src = "alu", 1.25, "nominal FP64 rate of the GB300 (1.25 TFLOP/s)"
+        else:
+            bound, peak = "tensor", peaks["bf16_tflops_sustained"]
+            peak_src = f"{peak_kind} bf16 sustained"
+    else:
+        unit, bound = "GB/s", "hbm"
+        achieved = per_launch_work / (per_launch_ms / 1e3) / 1e9
+        peak, peak_src = peaks["hbm_gbs"], f"{peak_kind} hbm copy"
+    roofline = {"bound": bound, "achieved": round(achieved, 4), "peak": peak, "unit": unit,
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel_class": name,
+                "per_launch_ms": round(per_launch_ms, 5), "launches": rec["launches"],
+                "peak_source": peak_src}
+    classes = {k: {"ms_per_step": round(v["ms"] / K, 4), "launches_per_step": v["launches"] / K}
+               for k, v in tim.items()}
+
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "steps/s", "n_gpus": world,
+        "steps": K, "warmup": W, "ms_per_step": round(ms_max / K, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "bf16",
+        "data": "synthetic (seeded uniform collocation points, resampled every step)",
+        "config": {"workload": WORKLOAD_NAME, "d": prob.d, "widths": list(widths),
+                   "n_int": WORKLOAD.n_int, "n_bdy": WORKLOAD.n_bdy, "precision": args.precision,
+                   "variant": "expand", **HYPER, "parallelism": f"replicas{world}",
+                   "l2": "flushed between steps (256 MiB write outside the step events)"},
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+        "kernel_classes": classes, "clocks": clocks, "status": status,
+        "wall_s_timed": round(wall, 3),
+    }
+    if fp64:
+        out["fp64_path"] = fp64
+        out["speedup_vs_fp64_path"] = round(value / world / fp64["value"], 2)
+    opt.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_step_time(n_int, n_bdy, seed=0, step=0):
+    """Wall time of one oracle KFAC step on a sample of the workload: the
+    per-point stages on n_int/n_bdy points, scaled to 2048/512 points, plus the
+    full-size Kronecker-sum inverse (which does not depend on the batch)."""
+    from oracle import kfac_oracle as ko
+    prob = WORKLOAD.prob
+    widths = WORKLOAD.widths
+    th = si.xavier_theta(prob.d, widths, seed)
+    Xi, f, Xb, g = si.make_batch(prob, n_int, n_bdy, seed=seed, step=step)
+    cfg = ko.KfacConfig(d=prob.d, widths=widths, lam=HYPER["lam"], lr=HYPER["lr"])
+    Ws = ko.unpack_theta(th, prob.d, widths)
+    t0 = time.perf_counter()
+    cg = ko.curvature_and_gradient(cfg, Ws, Xi, f, Xb, g)
+    t1 = time.perf_counter()
+    Ai, Bi, Ab, Bb = cg["factors"]
+    for l in range(len(widths)):
+        ko.kron_sum_inverse_apply(Ai[l], Bi[l], Ab[l], Bb[l], cg["grads"][l], cfg.lam)
+    t2 = time.perf_counter()
+    scale = WORKLOAD.n_int / n_int
+    return (t1 - t0) * scale + (t2 - t1), (t1 - t0), (t2 - t1)
+
+
+def cpu_cores():
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count()
+
+
+SAMPLE = (16, 4)
+SAMPLE_DESC = ("oracle (numpy FP64) per-point stages on 16 interior + 4 boundary points of the "
+               "workload, scaled linearly to 2048 + 512 points, plus the full-size FP64 "
+               "Kronecker-sum inverse of all 5 layers")
+
+
+def cpu_baseline(budget_s=20.0):
+    times = []
+    t_start = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t_start < budget_s and k < 8:
+        t, _, _ = oracle_step_time(*SAMPLE, step=k)
+        times.append(t)
+        k += 1
+    per = statistics.median(times)
+    return {"value": round(1.0 / per, 6), "unit": "steps/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": SAMPLE_DESC + f" ({k} samples, median)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    W, K = args.warmup, args.steps
+    for k in range(W):
+        oracle_step_time(*SAMPLE, step=k)
+    tot = 0.0
+    t0 = time.perf_counter()
+    for k in range(K):
+        t, _, _ = oracle_step_time(*SAMPLE, step=W + k)
+        tot += t
+    wall = time.perf_counter() - t0
+    value = K / tot
+    return {
+        "metric": METRIC, "value": round(value, 6), "unit": "steps/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": round(1000 * tot / K, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded uniform collocation points, resampled every step)",
+        "config": {"workload": WORKLOAD_NAME, "d": WORKLOAD.d, "widths": list(WORKLOAD.widths),
+                   "n_int": WORKLOAD.n_int, "n_bdy": WORKLOAD.n_bdy, "precision": "fp64",
+                   **HYPER, "parallelism": "cpu"},
+        "impl": "reference",
+        "cpu_baseline": {"value": round(value, 6), "unit": "steps/s", "cores": cpu_cores(),
+                         "kind": "oracle", "sample": SAMPLE_DESC + " per step"},
+        "e2e": {"value": round(value, 6), "unit": "steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "wall_s_timed": round(wall, 2),
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed_bf16"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 5 if args.precision == "fp64" else 30
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

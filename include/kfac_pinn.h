@@ -197,6 +197,30 @@ kfac_status_t kfac_pinn_sync_status(kfac_handle_t h, kfac_status_t* status);
  * (host-side counter; used to report launches per step). */
 int64_t kfac_pinn_launch_count(kfac_handle_t h);
 
+/* Kernel classes of the device timers. */
+typedef enum {
+    KFAC_KC_LAYER_GEMM = 0,   /* forward layer GEMMs of the Taylor pass       */
+    KFAC_KC_ADJOINT_GEMM = 1, /* adjoint GEMMs (T^bar = Z^bar W)              */
+    KFAC_KC_GRAM = 2,         /* factor Grams and weight-gradient reductions  */
+    KFAC_KC_ELEMENTWISE = 3,  /* tanh Taylor rule, its adjoint, residuals     */
+    KFAC_KC_EIG = 4,          /* Cholesky + generalized eigendecomposition    */
+    KFAC_KC_PRECOND = 5,      /* preconditioning GEMMs and the update         */
+    KFAC_KC_COUNT = 6
+} kfac_kernel_class_t;
+
+/* Enable (1) or disable (0) per-class device timers: while enabled, every
+ * launch of a timed class is bracketed by CUDA events recorded on the
+ * launching stream.  Enabling clears the accumulated timers. */
+kfac_status_t kfac_pinn_timing_enable(kfac_handle_t h, int enable);
+
+/* Synchronise the device and return, for one kernel class, the summed device
+ * time of its recorded launches (ms), the number of launches, and their
+ * summed algorithmic work (FLOPs for contractions, bytes for element-wise
+ * kernels: 2 P Q K per GEMM; bytes read + written per element-wise pass).
+ * Any pointer may be NULL.  The class's timers are cleared. */
+kfac_status_t kfac_pinn_timing_read(kfac_handle_t h, int kernel_class, double* total_ms,
+                                    int64_t* launches, double* work);
+
 #ifdef __cplusplus
 }
 #endif

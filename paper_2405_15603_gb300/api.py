@@ -187,3 +187,16 @@ class KfacPinn:
 
     def launch_count(self) -> int:
         return int(self.lib.kfac_pinn_launch_count(self.h))
+
+    def timing_enable(self, on: bool = True):
+        _check("kfac_pinn_timing_enable", self.lib.kfac_pinn_timing_enable(self.h, int(on)))
+
+    def timing_read(self) -> dict:
+        """Per kernel class: (device ms, launches, algorithmic work) since the last read."""
+        out = {}
+        for cls, name in _lib.KERNEL_CLASSES.items():
+            ms, n, w = C.c_double(), C.c_int64(), C.c_double()
+            _check("kfac_pinn_timing_read", self.lib.kfac_pinn_timing_read(
+                self.h, cls, C.byref(ms), C.byref(n), C.byref(w)))
+            out[name] = {"ms": ms.value, "launches": n.value, "work": w.value}
+        return out

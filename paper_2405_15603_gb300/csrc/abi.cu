@@ -51,6 +51,7 @@ void free_pass(PassBuffers& pb) {
 
 void free_handle(kfac_pinn_handle* h) {
     if (!h) return;
+    timers_free(h);
     free_pass(h->in);
     free_pass(h->bd);
     tc_free(h);
@@ -174,9 +175,87 @@ kfac_status_t run_factors(kfac_pinn_handle* h, cudaStream_t s, const double* the
     return KFAC_OK;
 }
 
+constexpr int TIMER_CAP = 4096;
+
+void timer_fold(kfac_pinn_handle* h, int cls) {
+    auto& t = h->timers[cls];
+    if (t.n == 0) return;
+    cudaEventSynchronize(t.ev[2 * t.n - 1]);
+    for (int i = 0; i < t.n; i++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.ev[2 * i], t.ev[2 * i + 1]) == cudaSuccess) t.ms += ms;
+    }
+    t.n = 0;
+}
+
 }  // namespace
 
+void timer_begin(kfac_pinn_handle* h, int cls, cudaStream_t s) {
+    if (!h->timing) return;
+    auto& t = h->timers[cls];
+    if (t.n >= t.cap) timer_fold(h, cls);
+    cudaEventRecord(t.ev[2 * t.n], s);
+}
+
+void timer_end(kfac_pinn_handle* h, int cls, cudaStream_t s, double work) {
+    if (!h->timing) return;
+    auto& t = h->timers[cls];
+    cudaEventRecord(t.ev[2 * t.n + 1], s);
+    t.n++;
+    t.launches++;
+    t.work += work;
+}
+
+void timers_free(kfac_pinn_handle* h) {
+    for (int c = 0; c < KFAC_KC_COUNT; c++) {
+        auto& t = h->timers[c];
+        if (t.ev) {
+            for (int i = 0; i < 2 * t.cap; i++) cudaEventDestroy(t.ev[i]);
+            free(t.ev);
+        }
+        t.ev = nullptr;
+        t.cap = t.n = 0;
+    }
+}
+
 extern "C" {
+
+kfac_status_t kfac_pinn_timing_enable(kfac_handle_t h, int enable) {
+    if (!h) return KFAC_BAD_ARG;
+    if (enable) {
+        for (int c = 0; c < KFAC_KC_COUNT; c++) {
+            auto& t = h->timers[c];
+            if (!t.ev) {
+                t.ev = (cudaEvent_t*)calloc(2 * TIMER_CAP, sizeof(cudaEvent_t));
+                if (!t.ev) return KFAC_OOM;
+                for (int i = 0; i < 2 * TIMER_CAP; i++)
+                    KFAC_CUDA_TRY(cudaEventCreate(&t.ev[i]));
+                t.cap = TIMER_CAP;
+            }
+            t.n = 0;
+            t.launches = 0;
+            t.work = 0.0;
+            t.ms = 0.0;
+        }
+    }
+    h->timing = enable ? 1 : 0;
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_timing_read(kfac_handle_t h, int kernel_class, double* total_ms,
+                                    int64_t* launches, double* work) {
+    if (!h || kernel_class < 0 || kernel_class >= KFAC_KC_COUNT) return KFAC_BAD_ARG;
+    auto& t = h->timers[kernel_class];
+    if (t.ev) timer_fold(h, kernel_class);
+    if (total_ms) *total_ms = t.ms;
+    if (launches) *launches = t.launches;
+    if (work) *work = t.work;
+    t.ms = 0.0;
+    t.launches = 0;
+    t.work = 0.0;
+    return KFAC_OK;
+}
+
 
 int64_t kfac_pinn_param_count(const kfac_config_t* cfg) {
     if (!valid_config(cfg)) return -1;

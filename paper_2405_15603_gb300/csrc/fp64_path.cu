@@ -202,8 +202,10 @@ kfac_status_t reduce_gemm(kfac_pinn_handle* h, cudaStream_t s, int P, int Q, int
     kchunk = ((kchunk + GK - 1) / GK) * GK;
     if (kchunk < GK) kchunk = GK;
     splits = (K + kchunk - 1) / kchunk;
+    timer_begin(h, KFAC_KC_GRAM, s);
     if (cudaSuccess != launch_dgemm(s, P, Q, K, splits, la, lb, EpPartial{h->part, P, Q}))
         return KFAC_CUDA_ERROR;
+    timer_end(h, KFAC_KC_GRAM, s, 2.0 * P * Q * (double)K);
     h->launches++;
     long long PQ = (long long)P * Q;
     k_reduce_partials<<<ceil_div_u(PQ, EW_THREADS), EW_THREADS, 0, s>>>(
@@ -234,12 +236,16 @@ kfac_status_t fp64_forward(kfac_pinn_handle* h, cudaStream_t s, const double* th
         Strided<true> A{pb.T[l - 2], hin, 1};
         Strided<true> B{W, hout, 1};   // B(k, j) = W~[j, k] = W[j + hout*k]
         EpStore ep{pb.Z[l - 1], hout, 1, 1.0, 0.0, W + (long long)hout * hin, 1, N};
+        timer_begin(h, KFAC_KC_LAYER_GEMM, s);
         if (cudaSuccess != launch_dgemm(s, S * N, hout, hin, 1, A, B, ep)) return KFAC_CUDA_ERROR;
+        timer_end(h, KFAC_KC_LAYER_GEMM, s, 2.0 * S * N * (double)hout * hin);
         h->launches++;
         if (l < L) {
             long long cnt = (long long)N * hout;
+            timer_begin(h, KFAC_KC_ELEMENTWISE, s);
             k_act_fwd<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[l - 1], pb.T[l - 1], N,
                                                                          S, hout, lap_first);
+            timer_end(h, KFAC_KC_ELEMENTWISE, s, 16.0 * S * (double)cnt);
             KFAC_LAUNCH_CHECK(h);
         }
     }
@@ -271,11 +277,15 @@ kfac_status_t fp64_backward(kfac_pinn_handle* h, cudaStream_t s, const double* t
         Strided<true> A{pb.Zb[l - 1], hout, 1};
         Strided<false> B{W, 1, hout};  // B(i, q) = W~[i, q] = W[i + hout*q]
         EpStore ep{pb.Zb[l - 2], hin, 1, 1.0, 0.0, nullptr, 0, 0};
+        timer_begin(h, KFAC_KC_ADJOINT_GEMM, s);
         if (cudaSuccess != launch_dgemm(s, S * N, hin, hout, 1, A, B, ep)) return KFAC_CUDA_ERROR;
+        timer_end(h, KFAC_KC_ADJOINT_GEMM, s, 2.0 * S * N * (double)hin * hout);
         h->launches++;
         long long cnt = (long long)N * hin;
+        timer_begin(h, KFAC_KC_ELEMENTWISE, s);
         k_act_bwd<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[l - 2], pb.Zb[l - 2], N, S,
                                                                      hin, lap_first);
+        timer_end(h, KFAC_KC_ELEMENTWISE, s, 24.0 * S * (double)cnt);
         KFAC_LAUNCH_CHECK(h);
     }
     return KFAC_OK;

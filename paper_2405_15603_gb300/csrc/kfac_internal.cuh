@@ -65,6 +65,16 @@ struct kfac_pinn_handle {
     double* stage;                        // device copy of the host batch
     size_t stage_elems;
 
+    // per-class device timers (kfac_pinn_timing_*)
+    int timing;
+    struct Timer {
+        cudaEvent_t* ev;   // 2 * cap events
+        int cap, n;
+        long long launches;
+        double work;
+        double ms;         // folded-in time of earlier batches
+    } timers[KFAC_KC_COUNT];
+
     int t;                 // completed steps
     int have_inverse;
     int have_direction;
@@ -91,6 +101,11 @@ KFAC_DEV void latch_status(int* status, int code) {
         cudaError_t _e = cudaGetLastError();                  \
         if (_e != cudaSuccess) return KFAC_CUDA_ERROR;        \
     } while (0)
+
+// Device timers: bracket a launch with events when timing is enabled.
+void timer_begin(kfac_pinn_handle* h, int cls, cudaStream_t s);
+void timer_end(kfac_pinn_handle* h, int cls, cudaStream_t s, double work);
+void timers_free(kfac_pinn_handle* h);
 
 static inline unsigned ceil_div_u(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 

@@ -312,6 +312,8 @@ __global__ void k_update(double* theta, const double* dir, double* delta_prev, l
 
 }  // namespace
 
+kfac_status_t linalg_precondition_impl(kfac_pinn_handle* h, cudaStream_t s, const double* grad, double* dir);
+
 size_t linalg_workspace_elems(const kfac_pinn_handle* h) {
     size_t tot = 0;
     for (int l = 1; l <= h->cfg.L; l++) {
@@ -341,12 +343,28 @@ kfac_status_t linalg_invert(kfac_pinn_handle* h, cudaStream_t s) {
             p.vec = ws; ws += 3 * (size_t)n;
         }
     }
+    double work = 0.0;
+    for (int i = 0; i < batch.count; i++) work += 10.0 * (double)batch.p[i].n * batch.p[i].n * batch.p[i].n;
+    timer_begin(h, KFAC_KC_EIG, s);
     k_gen_eig<<<batch.count, LA_THREADS, 0, s>>>(batch, h->status);
+    timer_end(h, KFAC_KC_EIG, s, work);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }
 
 kfac_status_t linalg_precondition(kfac_pinn_handle* h, cudaStream_t s, const double* grad, double* dir) {
+    double work = 0.0;
+    for (int l = 1; l <= h->cfg.L; l++) {
+        double na = h->dims[l - 1] + 1, nb = h->dims[l];
+        work += 4.0 * (nb * nb * na + nb * na * na);
+    }
+    timer_begin(h, KFAC_KC_PRECOND, s);
+    kfac_status_t r = linalg_precondition_impl(h, s, grad, dir);
+    timer_end(h, KFAC_KC_PRECOND, s, work);
+    return r;
+}
+
+kfac_status_t linalg_precondition_impl(kfac_pinn_handle* h, cudaStream_t s, const double* grad, double* dir) {
     for (int l = 1; l <= h->cfg.L; l++) {
         const int na = h->dims[l - 1] + 1, nb = h->dims[l];
         const double* G = grad + h->woff[l - 1];
