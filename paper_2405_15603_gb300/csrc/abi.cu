@@ -81,6 +81,9 @@ kfac_status_t alloc_pass(kfac_pinn_handle* h, PassBuffers& pb, int N, int S) {
     const int L = h->cfg.L;
     kfac_status_t st;
     int maxw = 0;
+    if (h->cfg.precision == KFAC_MIXED_BF16) {   // the mixed path keeps its own BF16 activations
+        return dalloc(&pb.r, (size_t)N);
+    }
     for (int l = 1; l <= L; l++) {
         size_t e = (size_t)S * N * h->dims[l];
         if ((st = dalloc(&pb.Z[l - 1], e))) return st;

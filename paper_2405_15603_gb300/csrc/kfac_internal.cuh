@@ -64,6 +64,7 @@ struct kfac_pinn_handle {
     // host staging for kfac_pinn_step_host
     double* stage;                        // device copy of the host batch
     size_t stage_elems;
+    void* mx;                             // mixed-precision state (tc_path.cu)
 
     // per-class device timers (kfac_pinn_timing_*)
     int timing;

@@ -1,13 +1,917 @@
-// Mixed-precision (tcgen05 BF16) path.
-#include "tc_path.cuh"
+// Mixed-precision path: tcgen05 BF16 tensor cores with FP32 accumulation for
+// the Taylor pass, its adjoint, the weight gradient and the factor Grams;
+// FP64 for the residuals, loss, factor accumulation (EMA) and everything
+// downstream (inverse, preconditioning, update).
+//
+// Layout (per pass, per hidden layer l): activations are BF16 matrices of
+// S*N_pad rows (Taylor column blocks of N_pad points, N_pad a multiple of
+// 128) by hp_l = round_up(h_l, 64) features.  The value and Laplacian rows
+// additionally keep the low BF16 half (x = hi + lo, split-BF16), and every
+// product that produces a value or Laplacian row sums three BF16 MMAs
+// (hi*hi + hi*lo + lo*hi), so the two channels the residuals depend on carry
+// about 16 significant bits into the FP32 accumulator.  Tangent rows are
+// plain BF16.
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
 
-kfac_status_t tc_alloc(kfac_pinn_handle*) { return KFAC_OK; }
-void tc_free(kfac_pinn_handle*) {}
-kfac_status_t tc_factors(kfac_pinn_handle*, cudaStream_t, const double*, const double*, int,
-                         const double*, const double*, int, const double*, double*) {
-    return KFAC_BAD_ARG;
+#include "tc_path.cuh"
+#include "tc_kernels.cuh"
+
+using tck::Args;
+
+typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                      const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                      CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                      CUtensorMapFloatOOBfill);
+
+bool tc_make_tmap_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t stride_bytes,
+                     uint32_t box_inner, uint32_t box_outer) {
+    static PFN_encodeTiled_t fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return false;
+        fn = (PFN_encodeTiled_t)p;
+    }
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {stride_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
-kfac_status_t tc_forward_laplacian(kfac_pinn_handle*, cudaStream_t, const double*, const double*, int,
-                                   double*, double*, double*) {
-    return KFAC_BAD_ARG;
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+constexpr int EW = 256;
+constexpr int MAX_CHUNKS = 16;
+constexpr int MAX_GRAM_CHUNKS = 32;
+
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+struct MxLayer {
+    int h, hp;
+    bf16 *T_hi, *T_lo, *Zb, *Gr;
+    float *A0, *AD, *SSQ, *YD;
+    CUtensorMap kT_hi, kT_lo, kZb;        // K-major operand maps (box 64 x 128)
+    CUtensorMap gT, gZb, gGr;             // MN-major Gram maps (box 64 x 64)
+};
+
+struct MxPass {
+    int N_pad, S, rows;
+    MxLayer lay[KFAC_MAX_LAYERS];         // hidden layers 1..L-1 (index l-1)
+    float* zl;                            // last-layer outputs, S*N_pad
+    bf16 *red_a, *red_g;                  // KFAC-reduce column sums (N_pad x hp_max)
+    CUtensorMap gRa[KFAC_MAX_LAYERS], gRg[KFAC_MAX_LAYERS];
+};
+
+struct MxWeights {
+    bf16 *W_hi[KFAC_MAX_LAYERS], *W_lo[KFAC_MAX_LAYERS], *Wt[KFAC_MAX_LAYERS];
+    float* bias[KFAC_MAX_LAYERS];
+    CUtensorMap kW_hi[KFAC_MAX_LAYERS], kW_lo[KFAC_MAX_LAYERS], kWt[KFAC_MAX_LAYERS];
+    float* wL;        // last layer weights (h_{L-1}) and bias at [hp]
+};
+
+struct MxState {
+    MxPass in, bd;
+    MxWeights w;
+    float* part;        // tangent-chunk partials (MAX_CHUNKS x N_pad x hp_max)
+    float* gpart;       // Gram partials (2 regions)
+    size_t gpart_region;
+    double* cs;         // column sums (4 x (hp_max + 8))
+    int hp_max;
+};
+
+MxState* MX(kfac_pinn_handle* h) { return (MxState*)h->mx; }
+
+template <class T>
+kfac_status_t dal(T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return KFAC_OOM; }
+    if (e != cudaSuccess) return KFAC_CUDA_ERROR;
+    return KFAC_OK;
+}
+
+// ============================================================================
+// Element-wise kernels
+// ============================================================================
+
+// theta (FP64, column-stacked W~_l) -> BF16 hi/lo row-major W (hout_p x hin_p),
+// BF16 transposed Wt (hin_p x hout_p), FP32 bias; zero padding.
+__global__ void k_convert_weights(const double* __restrict__ W, int hout, int hin, int hout_p, int hin_p,
+                                  bf16* Whi, bf16* Wlo, bf16* Wt, float* bias) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)hout_p * hin_p) return;
+    int i = (int)(idx / hin_p), k = (int)(idx % hin_p);
+    double v = (i < hout && k < hin) ? W[i + (long long)hout * k] : 0.0;
+    bf16 hi = __double2bfloat16(v);
+    bf16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+    Whi[idx] = hi;
+    Wlo[idx] = lo;
+    Wt[(long long)k * hout_p + i] = hi;
+    if (k == 0) bias[i] = (i < hout) ? (float)W[i + (long long)hout * hin] : 0.f;
+}
+
+__global__ void k_convert_last(const double* __restrict__ W, int hin, int hin_p, float* wL) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > hin_p) return;
+    if (k < hin_p) wL[k] = (k < hin) ? (float)W[k] : 0.f;
+    else wL[k] = (float)W[hin];     // bias at index hin_p
+}
+
+// First layer (Sec. 3.1): inputs (x, e_1..e_d, 0); tanh rule of Eq. 6.
+__global__ void k_layer1(const double* __restrict__ W, const double* __restrict__ X, int N, int N_pad, int d,
+                         int h, int hp, int S, int lap_first, bf16* T_hi, bf16* T_lo, float* A0, float* AD,
+                         float* SSQ) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)N_pad * hp) return;
+    int n = (int)(idx / hp), j = (int)(idx % hp);
+    bool live = (n < N) && (j < h);
+    double a0 = 0.0, ssq = 0.0;
+    if (live) {
+        a0 = W[j + (long long)h * d];
+        for (int k = 0; k < d; k++) a0 = fma(W[j + (long long)h * k], X[(long long)n * d + k], a0);
+    }
+    double y0 = live ? tanh(a0) : 0.0;
+    double s1 = 1.0 - y0 * y0, s2 = -2.0 * y0 * s1;
+    const long long blk = (long long)N_pad * hp;
+    bf16 hi = __double2bfloat16(y0);
+    T_hi[idx] = hi;
+    T_lo[idx] = __double2bfloat16(y0 - (double)__bfloat162float(hi));
+    if (S > 1) {
+        for (int i = 0; i < d; i++) {
+            double w = live ? W[j + (long long)h * i] : 0.0;
+            bf16 th = __double2bfloat16(s1 * w);
+            T_hi[(1 + i) * blk + idx] = th;
+            if (i == 0 && lap_first == 2)   // heat: time tangent keeps its low half (block 2)
+                T_lo[2 * blk + idx] = __double2bfloat16(s1 * w - (double)__bfloat162float(th));
+            if (1 + i >= lap_first) ssq = fma(w, w, ssq);
+        }
+        double yD = live ? s2 * ssq : 0.0;
+        bf16 dh = __double2bfloat16(yD);
+        T_hi[(S - 1) * blk + idx] = dh;
+        T_lo[blk + idx] = __double2bfloat16(yD - (double)__bfloat162float(dh));
+    }
+    A0[idx] = (float)a0;
+    AD[idx] = 0.f;
+    SSQ[idx] = (float)ssq;
+}
+
+// Laplacian row of a hidden layer once all tangent chunks are done:
+// y_D = s1 a_D + s2 sum_{i in C} a_i^2  (Eq. 6).
+__global__ void k_lap_finish(const float* __restrict__ part, int n_chunks, int N, int N_pad, int h, int hp, int S,
+                             const float* __restrict__ A0, const float* __restrict__ AD, float* SSQ, bf16* T_hi,
+                             bf16* T_lo) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long blk = (long long)N_pad * hp;
+    if (idx >= blk) return;
+    int n = (int)(idx / hp), j = (int)(idx % hp);
+    float ssq = 0.f;
+    for (int z = 0; z < n_chunks; z++) ssq += part[z * blk + idx];
+    bool live = (n < N) && (j < h);
+    float y0 = tanhf(A0[idx]);
+    float s1 = 1.f - y0 * y0, s2 = -2.f * y0 * s1;
+    float yD = live ? fmaf(s1, AD[idx], s2 * ssq) : 0.f;
+    SSQ[idx] = live ? ssq : 0.f;
+    bf16 hi = __float2bfloat16_rn(yD);
+    T_hi[(S - 1) * blk + idx] = hi;
+    T_lo[blk + idx] = __float2bfloat16_rn(yD - __bfloat162float(hi));
+}
+
+// Last linear layer (h_L = 1): z[row] = sum_j T[row][j] w[j] (+ bias on value
+// rows) for the selected Taylor blocks: all of them (nsel == 0) or the nsel
+// blocks listed in sel.  One warp per row; value and Laplacian rows add their
+// low halves.
+struct BlockSel {
+    int nsel;
+    int b[3];
+    int split_time;
+};
+__global__ void k_last_fwd(const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo, const float* __restrict__ wL,
+                           int N_pad, int S, int hp, BlockSel sel, float* zl) {
+    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    int lane = threadIdx.x % 32;
+    long long nrows = (long long)(sel.nsel ? sel.nsel : S) * N_pad;
+    if (wid >= nrows) return;
+    int bi = (int)(wid / N_pad), n = (int)(wid % N_pad);
+    int s = sel.nsel ? sel.b[bi] : bi;
+    wid = (long long)s * N_pad + n;
+    const bf16* row = T_hi + wid * hp;
+    const bf16* lrow = nullptr;
+    if (s == 0) lrow = T_lo + (long long)n * hp;
+    else if (s == S - 1) lrow = T_lo + ((long long)N_pad + n) * hp;
+    else if (s == 1 && sel.split_time) lrow = T_lo + (2LL * N_pad + n) * hp;
+    float acc = 0.f;
+    for (int j = lane * 2; j < hp; j += 64) {
+        float2 t = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(row + j));
+        if (lrow) {
+            float2 u = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(lrow + j));
+            t.x += u.x;
+            t.y += u.y;
+        }
+        acc = fmaf(t.x, wL[j], acc);
+        acc = fmaf(t.y, wL[j + 1], acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) zl[wid] = acc + (s == 0 ? wL[hp] : 0.f);
+}
+
+__global__ void k_residual_mx(const float* __restrict__ zl, const double* __restrict__ target, double* r, int N,
+                              int N_pad, int S, int interior, int heat, double kappa) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double v;
+    if (!interior) v = (double)zl[n] - target[n];
+    else if (heat) v = (double)zl[N_pad + n] - kappa * (double)zl[(long long)(S - 1) * N_pad + n] - target[n];
+    else v = -(double)zl[(long long)(S - 1) * N_pad + n] - target[n];
+    r[n] = v;
+}
+
+__global__ void k_extract_mx(const float* __restrict__ zl, int N, int N_pad, int S, int d, double* u, double* grad,
+                             double* lap) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    if (u) u[n] = zl[n];
+    if (grad)
+        for (int i = 0; i < d; i++) grad[(long long)n * d + i] = zl[(long long)(1 + i) * N_pad + n];
+    if (lap) lap[n] = zl[(long long)(S - 1) * N_pad + n];
+}
+
+// Adjoint through the last linear layer and the tanh of layer L-1: the
+// incoming T^bar_s = c_s w (h_L = 1, seed c = dr/dZ^{(L)}), then the tanh
+// adjoint (abar_i = s1 ybar_i - 4 y0 y_i ybar_D, ...).  Writes g = Zbar and
+// r_n g for every Taylor row.
+__global__ void k_last_bwd(const float* __restrict__ wL, const bf16* __restrict__ T_hi, const float* __restrict__ A0,
+                           const float* __restrict__ AD, const float* __restrict__ SSQ, const double* __restrict__ r,
+                           int N, int N_pad, int h, int hp, int S, int lap_first, int heat, float kappa,
+                           bf16* Zb, bf16* Gr) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long blk = (long long)N_pad * hp;
+    if (idx >= blk) return;
+    int n = (int)(idx / hp), j = (int)(idx % hp);
+    bool live = (n < N) && (j < h);
+    float w = live ? wL[j] : 0.f;
+    float rn = (n < N) ? (float)r[n] : 0.f;
+    float y0 = tanhf(A0[idx]);
+    float s1 = 1.f - y0 * y0;
+    if (S == 1) {
+        float ab = s1 * w;
+        Zb[idx] = __float2bfloat16_rn(ab);
+        Gr[idx] = __float2bfloat16_rn(rn * ab);
+        return;
+    }
+    float cD = heat ? -kappa : -1.f;
+    float cT = heat ? 1.f : 0.f;      // seed on tangent column 1 (time) for heat
+    float yD = cD * w;
+    float cross = 0.f;
+    for (int s = 1; s < S - 1; s++) {
+        float yi = __bfloat162float(T_hi[s * blk + idx]);
+        float ybar = (s == 1) ? cT * w : 0.f;
+        float ab = s1 * ybar;
+        if (s >= lap_first) ab -= 4.f * y0 * yi * yD;
+        cross = fmaf(yi, ybar, cross);
+        ab = live ? ab : 0.f;
+        Zb[s * blk + idx] = __float2bfloat16_rn(ab);
+        Gr[s * blk + idx] = __float2bfloat16_rn(rn * ab);
+    }
+    float a0b = -2.f * y0 * cross - 2.f * s1 * (y0 * AD[idx] + (1.f - 3.f * y0 * y0) * SSQ[idx]) * yD;
+    float aDb = s1 * yD;
+    a0b = live ? a0b : 0.f;
+    aDb = live ? aDb : 0.f;
+    Zb[idx] = __float2bfloat16_rn(a0b);
+    Gr[idx] = __float2bfloat16_rn(rn * a0b);
+    Zb[(S - 1) * blk + idx] = __float2bfloat16_rn(aDb);
+    Gr[(S - 1) * blk + idx] = __float2bfloat16_rn(rn * aDb);
+}
+
+// FP64 column sums of rows [row0, row0+nrows) of a BF16 matrix (+ optional lo block).
+__global__ void k_colsum(const bf16* __restrict__ X, const bf16* __restrict__ Xlo, int hp, long long row0, int nrows,
+                         int ncols, double* out) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= ncols) return;
+    double acc = 0.0;
+    for (int n = 0; n < nrows; n++) {
+        double v = (double)__bfloat162float(X[(row0 + n) * hp + q]);
+        if (Xlo) v += (double)__bfloat162float(Xlo[(long long)n * hp + q]);
+        acc += v;
+    }
+    out[q] = acc;
+}
+
+// KFAC-reduce per-point sums over the S Taylor columns: out = scale * sum_s X_s.
+__global__ void k_sum_over_s(const bf16* __restrict__ X, int N_pad, int S, int hp, float scale, bf16* out) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long blk = (long long)N_pad * hp;
+    if (idx >= blk) return;
+    float acc = 0.f;
+    for (int s = 0; s < S; s++) acc += __bfloat162float(X[s * blk + idx]);
+    out[idx] = __float2bfloat16_rn(scale * acc);
+}
+
+// Factor from Gram partials: M[p][q] = sc * sum_z part[z][min][max] (p,q < P),
+// bias row/column sc_b * cs[q], corner `corner`; EMA into the FP64 factor.
+__global__ void k_factor_reduce(const float* __restrict__ part, int nz, int P, int sym, const double* cs, double sc,
+                                double sc_b, double corner, int with_bias, double* fac, double beta, int* status) {
+    int n = P + with_bias;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * n) return;
+    int p = (int)(idx / n), q = (int)(idx % n);
+    double v;
+    if (p < P && q < P) {
+        int a = p, b = q;
+        if (sym && a > b) { a = q; b = p; }
+        double acc = 0.0;
+        for (int z = 0; z < nz; z++) acc += (double)part[((long long)z * P + a) * P + b];
+        v = sc * acc;
+    } else if (p < P) {
+        v = sc_b * cs[p];
+    } else if (q < P) {
+        v = sc_b * cs[q];
+    } else {
+        v = corner;
+    }
+    double o = beta * fac[idx] + (1.0 - beta) * v;
+    if (!isfinite(o)) latch_status(status, KFAC_NONFINITE);
+    fac[idx] = o;
+}
+
+// Weight gradient of a layer from interior and boundary Gram partials:
+// grad[i + P*q] = si * sum part_i[i][q] + sb * sum part_b[i][q] (q < Q), bias
+// column q = Q from the column sums.
+__global__ void k_grad_reduce(const float* __restrict__ pi, int zi, const float* __restrict__ pb, int zb, int P, int Q,
+                              const double* csi, const double* csb, double si, double sb, double* grad) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)P * (Q + 1)) return;
+    int i = (int)(idx / (Q + 1)), q = (int)(idx % (Q + 1));
+    double v;
+    if (q < Q) {
+        double a = 0.0, b = 0.0;
+        for (int z = 0; z < zi; z++) a += (double)pi[((long long)z * P + i) * Q + q];
+        for (int z = 0; z < zb; z++) b += (double)pb[((long long)z * P + i) * Q + q];
+        v = si * a + sb * b;
+    } else {
+        v = si * csi[i] + sb * csb[i];
+    }
+    grad[i + (long long)P * q] = v;
+}
+
+// First-layer input factor in closed form (Sec. 3.1: T^(0) has columns
+// (x, e_1..e_d, 0) and bias row (1, 0, .., 0)).
+__global__ void k_factor_A1(const double* __restrict__ X, int N, int d, int S, int reduce, int boundary, double* fac,
+                            double beta, int* status) {
+    int n1 = d + 1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n1 * n1) return;
+    int p = idx / n1, q = idx % n1;
+    double acc = 0.0;
+    double sh = (reduce && !boundary) ? 1.0 : 0.0;   // reduce: abar = (x + 1, 1) / S
+    for (int n = 0; n < N; n++) {
+        double xp = (p < d) ? X[(long long)n * d + p] + sh : 1.0;
+        double xq = (q < d) ? X[(long long)n * d + q] + sh : 1.0;
+        acc += xp * xq;
+    }
+    double v;
+    if (boundary) v = acc / N;
+    else if (reduce) v = acc / ((double)N * S * S);
+    else v = (acc + ((p == q && p < d) ? (double)N : 0.0)) / ((double)N * S);
+    double o = beta * fac[idx] + (1.0 - beta) * v;
+    if (!isfinite(o)) latch_status(status, KFAC_NONFINITE);
+    fac[idx] = o;
+}
+
+// Weight gradient of the first layer:
+//   (1/N) sum_n [ (r g)_{n,0} (x_n, 1)^T + sum_i (r g)_{n,i} (e_i, 0)^T ] + boundary term.
+__global__ void k_grad_layer1(const bf16* __restrict__ Gr, const bf16* __restrict__ Grb, const double* __restrict__ X,
+                              const double* __restrict__ Xb, int N, int N_pad, int Nb, int d, int h, int hp, int S,
+                              double* grad) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)h * (d + 1)) return;
+    int k = (int)(idx / h), j = (int)(idx % h);
+    const long long blk = (long long)N_pad * hp;
+    double a = 0.0, b = 0.0;
+    for (int n = 0; n < N; n++) {
+        double g0 = (double)__bfloat162float(Gr[(long long)n * hp + j]);
+        if (k < d) a += g0 * X[(long long)n * d + k] + (double)__bfloat162float(Gr[(1 + k) * blk + (long long)n * hp + j]);
+        else a += g0;
+    }
+    for (int n = 0; n < Nb; n++) {
+        double g0 = (double)__bfloat162float(Grb[(long long)n * hp + j]);
+        b += (k < d) ? g0 * Xb[(long long)n * d + k] : g0;
+    }
+    grad[j + (long long)h * k] = a / N + b / Nb;
+}
+
+// Last layer: gradient (1/N) sum_{n,s} r_n c_s T^_{n,s} + boundary, and the
+// 1x1 output factors B_L.
+__global__ void k_last_layer_terms(const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo,
+                                   const bf16* __restrict__ Tb_hi, const bf16* __restrict__ Tb_lo,
+                                   const double* __restrict__ r, const double* __restrict__ rb, int N, int N_pad,
+                                   int Nb, int Nb_pad, int h, int hp, int S, int heat, double kappa, int reduce,
+                                   double* grad, double* B_int, double* B_bdy, double beta, int* status) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q > h) return;
+    const double cD = heat ? -kappa : -1.0, cT = heat ? 1.0 : 0.0;
+    const long long blk = (long long)N_pad * hp;
+    double a = 0.0, b = 0.0;
+    if (q < h) {
+        for (int n = 0; n < N; n++) {
+            double tD = (double)__bfloat162float(T_hi[(S - 1) * blk + (long long)n * hp + q]) +
+                        (double)__bfloat162float(T_lo[blk + (long long)n * hp + q]);
+            double v = cD * tD;
+            if (heat)
+                v += cT * ((double)__bfloat162float(T_hi[blk + (long long)n * hp + q]) +
+                           (double)__bfloat162float(T_lo[2 * blk + (long long)n * hp + q]));
+            a += r[n] * v;
+        }
+        for (int n = 0; n < Nb; n++) {
+            double t0 = (double)__bfloat162float(Tb_hi[(long long)n * hp + q]) +
+                        (double)__bfloat162float(Tb_lo[(long long)n * hp + q]);
+            b += rb[n] * t0;
+        }
+    } else {
+        for (int n = 0; n < Nb; n++) b += rb[n];   // bias: c_0 = 0 in the interior
+    }
+    grad[q] = a / N + b / Nb;
+    if (q == 0) {
+        double e = reduce ? (cD + cT) * (cD + cT) : cD * cD + cT * cT;
+        double o1 = beta * B_int[0] + (1.0 - beta) * e;
+        double o2 = beta * B_bdy[0] + (1.0 - beta) * 1.0;
+        if (!isfinite(o1) || !isfinite(o2)) latch_status(status, KFAC_NONFINITE);
+        B_int[0] = o1;
+        B_bdy[0] = o2;
+    }
+}
+
+// ============================================================================
+// Host helpers
+// ============================================================================
+template <int MODE>
+kfac_status_t launch_engine(kfac_pinn_handle* h, cudaStream_t s, const Args& a, dim3 grid, int kclass, double work) {
+    using C = tck::Cfg<MODE>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaFuncSetAttribute(tck::tc_engine<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+            cudaSuccess)
+            return KFAC_CUDA_ERROR;
+        attr_set = true;
+    }
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return KFAC_OK;
+    timer_begin(h, kclass, s);
+    tck::tc_engine<MODE><<<grid, tck::NUM_THREADS, C::SMEM, s>>>(a);
+    timer_end(h, kclass, s, work);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+Args base_args(kfac_pinn_handle* h, const MxPass& P, int N) {
+    Args a;
+    memset(&a, 0, sizeof(a));
+    a.N_pad = P.N_pad;
+    a.N = N;
+    a.S = P.S;
+    a.lap_first = (h->cfg.op == KFAC_OP_HEAT) ? 2 : 1;
+    a.split_time = (h->cfg.op == KFAC_OP_HEAT && P.S > 2) ? 1 : 0;
+    a.status = h->status;
+    return a;
+}
+
+void choose_chunks(int S_tiles, int blocks, int sm, int& chunk_len, int& n_chunks) {
+    int want = (4 * sm + blocks - 1) / blocks;
+    if (want < 1) want = 1;
+    if (want > MAX_CHUNKS) want = MAX_CHUNKS;
+    if (want > S_tiles) want = S_tiles;
+    chunk_len = (S_tiles + want - 1) / want;
+    n_chunks = (S_tiles + chunk_len - 1) / chunk_len;
+}
+
+kfac_status_t alloc_pass(kfac_pinn_handle* h, MxPass& P, int Nmax, int S) {
+    const int L = h->cfg.L;
+    P.N_pad = round_up(Nmax, 128);
+    P.S = S;
+    P.rows = S * P.N_pad;
+    kfac_status_t st;
+    int hp_max = 64;
+    for (int l = 1; l <= L - 1; l++) {
+        MxLayer& ly = P.lay[l - 1];
+        ly.h = h->dims[l];
+        ly.hp = round_up(ly.h, 64);
+        if (ly.hp > hp_max) hp_max = ly.hp;
+        size_t big = (size_t)P.rows * ly.hp, small = (size_t)P.N_pad * ly.hp;
+        if ((st = dal(&ly.T_hi, big))) return st;
+        if ((st = dal(&ly.T_lo, 3 * small))) return st;
+        if ((st = dal(&ly.Zb, big))) return st;
+        if ((st = dal(&ly.Gr, big))) return st;
+        if ((st = dal(&ly.A0, small))) return st;
+        if ((st = dal(&ly.AD, small))) return st;
+        if ((st = dal(&ly.SSQ, small))) return st;
+        if ((st = dal(&ly.YD, small))) return st;
+        cudaMemset(ly.T_hi, 0, big * sizeof(bf16));
+        cudaMemset(ly.T_lo, 0, 3 * small * sizeof(bf16));
+        cudaMemset(ly.Zb, 0, big * sizeof(bf16));
+        cudaMemset(ly.Gr, 0, big * sizeof(bf16));
+        bool ok = tc_make_tmap_2d(&ly.kT_hi, ly.T_hi, ly.hp, P.rows, ly.hp * 2, 64, 128) &&
+                  tc_make_tmap_2d(&ly.kT_lo, ly.T_lo, ly.hp, 3 * P.N_pad, ly.hp * 2, 64, 128) &&
+                  tc_make_tmap_2d(&ly.kZb, ly.Zb, ly.hp, P.rows, ly.hp * 2, 64, 128) &&
+                  tc_make_tmap_2d(&ly.gT, ly.T_hi, ly.hp, P.rows, ly.hp * 2, 64, 64) &&
+                  tc_make_tmap_2d(&ly.gZb, ly.Zb, ly.hp, P.rows, ly.hp * 2, 64, 64) &&
+                  tc_make_tmap_2d(&ly.gGr, ly.Gr, ly.hp, P.rows, ly.hp * 2, 64, 64);
+        if (!ok) return KFAC_CUDA_ERROR;
+    }
+    if ((st = dal(&P.zl, (size_t)P.rows))) return st;
+    if (S > 1 && h->cfg.variant == KFAC_REDUCE) {
+        if ((st = dal(&P.red_a, (size_t)P.N_pad * hp_max))) return st;
+        if ((st = dal(&P.red_g, (size_t)P.N_pad * hp_max))) return st;
+        for (int l = 1; l <= L - 1; l++) {
+            int hp = P.lay[l - 1].hp;
+            if (!tc_make_tmap_2d(&P.gRa[l - 1], P.red_a, hp, P.N_pad, hp * 2, 64, 64) ||
+                !tc_make_tmap_2d(&P.gRg[l - 1], P.red_g, hp, P.N_pad, hp * 2, 64, 64))
+                return KFAC_CUDA_ERROR;
+        }
+    }
+    return KFAC_OK;
+}
+
+void free_pass(MxPass& P) {
+    for (int l = 0; l < KFAC_MAX_LAYERS; l++) {
+        MxLayer& ly = P.lay[l];
+        cudaFree(ly.T_hi); cudaFree(ly.T_lo); cudaFree(ly.Zb); cudaFree(ly.Gr);
+        cudaFree(ly.A0); cudaFree(ly.AD); cudaFree(ly.SSQ); cudaFree(ly.YD);
+    }
+    cudaFree(P.zl);
+    cudaFree(P.red_a);
+    cudaFree(P.red_g);
+}
+
+// Gram over rows: part[z][p][q] = sum_{rows in chunk z} X[row][p] Y[row][q].
+kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, const CUtensorMap& Y, int P, int Q,
+                   int rows, int sym, float* part, int& nz) {
+    using C = tck::Cfg<tck::GRAM>;
+    int p_tiles = (P + 127) / 128, q_tiles = (Q + C::BN - 1) / C::BN;
+    int tiles = 0;
+    for (int pb = 0; pb < p_tiles; pb++) tiles += q_tiles - (sym ? (pb * 128) / C::BN : 0);
+    int want = (2 * h->sm_count + tiles - 1) / tiles;
+    int max_chunks = (int)(MX(h)->gpart_region / ((size_t)P * Q));
+    if (want > MAX_GRAM_CHUNKS) want = MAX_GRAM_CHUNKS;
+    if (want > max_chunks) want = max_chunks;
+    if (want < 1) return KFAC_BAD_ARG;
+    int chunk = round_up((rows + want - 1) / want, 64);
+    nz = (rows + chunk - 1) / chunk;
+    Args a;
+    memset(&a, 0, sizeof(a));
+    a.a0 = X;
+    a.b0 = Y;
+    a.P = P;
+    a.Q = Q;
+    a.rows = rows;
+    a.row_chunk = chunk;
+    a.sym = sym;
+    a.q_tiles = q_tiles;
+    a.part = part;
+    a.status = h->status;
+    double work = 2.0 * (double)tiles * 128 * C::BN * rows;
+    return launch_engine<tck::GRAM>(h, s, a, dim3(tiles, nz, 1), KFAC_KC_GRAM, work);
+}
+
+// ============================================================================
+// Forward / backward of one pass
+// ============================================================================
+kfac_status_t convert_weights(kfac_pinn_handle* h, cudaStream_t s, const double* theta) {
+    MxWeights& w = MX(h)->w;
+    const int L = h->cfg.L;
+    for (int l = 2; l <= L - 1; l++) {
+        int hout = h->dims[l], hin = h->dims[l - 1];
+        int hout_p = round_up(hout, 64), hin_p = round_up(hin, 64);
+        k_convert_weights<<<ceil_div_u((long long)hout_p * hin_p, EW), EW, 0, s>>>(
+            theta + h->woff[l - 1], hout, hin, hout_p, hin_p, w.W_hi[l - 1], w.W_lo[l - 1], w.Wt[l - 1],
+            w.bias[l - 1]);
+        KFAC_LAUNCH_CHECK(h);
+    }
+    int hin = h->dims[L - 1], hin_p = round_up(hin, 64);
+    k_convert_last<<<ceil_div_u(hin_p + 1, EW), EW, 0, s>>>(theta + h->woff[L - 1], hin, hin_p, w.wL);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X, int N,
+                           MxPass& P, BlockSel sel) {
+    MxState* m = MX(h);
+    const int L = h->cfg.L, d = h->dims[0], S = P.S;
+    const int lap_first = (h->cfg.op == KFAC_OP_HEAT) ? 2 : 1;
+    {
+        MxLayer& l1 = P.lay[0];
+        long long cnt = (long long)P.N_pad * l1.hp;
+        timer_begin(h, KFAC_KC_ELEMENTWISE, s);
+        k_layer1<<<ceil_div_u(cnt, EW), EW, 0, s>>>(theta + h->woff[0], X, N, P.N_pad, d, l1.h, l1.hp, S, lap_first,
+                                                     l1.T_hi, l1.T_lo, l1.A0, l1.AD, l1.SSQ);
+        timer_end(h, KFAC_KC_ELEMENTWISE, s, 2.0 * (double)S * cnt + 16.0 * cnt);
+        KFAC_LAUNCH_CHECK(h);
+    }
+    for (int l = 2; l <= L - 1; l++) {
+        MxLayer& in = P.lay[l - 2];
+        MxLayer& out = P.lay[l - 1];
+        Args a = base_args(h, P, N);
+        a.a0 = in.kT_hi;
+        a.a1 = in.kT_lo;
+        a.b0 = m->w.kW_hi[l - 1];
+        a.b1 = m->w.kW_lo[l - 1];
+        a.k_steps = in.hp / 64;
+        a.n_out = out.h;
+        a.hp_out = out.hp;
+        a.out_hi = out.T_hi;
+        a.out_lo = out.T_lo;
+        a.bias = m->w.bias[l - 1];
+        a.A0 = out.A0;
+        a.AD = out.AD;
+        a.part = m->part;
+        const int jb = (out.hp + 127) / 128, pb = P.N_pad / 128;
+        double fl = 2.0 * P.N_pad * (double)out.hp * in.hp;
+        kfac_status_t st = launch_engine<tck::FWD_VALUE>(h, s, a, dim3(jb, pb, 1), KFAC_KC_LAYER_GEMM, 3 * fl);
+        if (st) return st;
+        if (S > 1) {
+            choose_chunks(S - 1, jb * pb, h->sm_count, a.chunk_len, a.n_chunks);
+            st = launch_engine<tck::FWD_TANLAP>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_LAYER_GEMM,
+                                                fl * (S + 1));
+            if (st) return st;
+            long long cnt = (long long)P.N_pad * out.hp;
+            timer_begin(h, KFAC_KC_ELEMENTWISE, s);
+            k_lap_finish<<<ceil_div_u(cnt, EW), EW, 0, s>>>(m->part, a.n_chunks, N, P.N_pad, out.h, out.hp, S,
+                                                             out.A0, out.AD, out.SSQ, out.T_hi, out.T_lo);
+            timer_end(h, KFAC_KC_ELEMENTWISE, s, (4.0 * a.n_chunks + 16.0) * cnt);
+            KFAC_LAUNCH_CHECK(h);
+        }
+    }
+    MxLayer& last = P.lay[L - 2];
+    long long threads = (long long)(sel.nsel ? sel.nsel : S) * P.N_pad * 32;
+    timer_begin(h, KFAC_KC_ELEMENTWISE, s);
+    k_last_fwd<<<ceil_div_u(threads, EW), EW, 0, s>>>(last.T_hi, last.T_lo, m->w.wL, P.N_pad, S, last.hp, sel,
+                                                       P.zl);
+    timer_end(h, KFAC_KC_ELEMENTWISE, s, 0.0);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+kfac_status_t backward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* r, int N, MxPass& P) {
+    MxState* m = MX(h);
+    const int L = h->cfg.L, S = P.S;
+    const int lap_first = (h->cfg.op == KFAC_OP_HEAT) ? 2 : 1;
+    {
+        MxLayer& ly = P.lay[L - 2];
+        long long cnt = (long long)P.N_pad * ly.hp;
+        timer_begin(h, KFAC_KC_ELEMENTWISE, s);
+        k_last_bwd<<<ceil_div_u(cnt, EW), EW, 0, s>>>(m->w.wL, ly.T_hi, ly.A0, ly.AD, ly.SSQ, r, N, P.N_pad, ly.h,
+                                                       ly.hp, S, lap_first, h->cfg.op == KFAC_OP_HEAT,
+                                                       (float)h->cfg.kappa, ly.Zb, ly.Gr);
+        timer_end(h, KFAC_KC_ELEMENTWISE, s, 6.0 * S * (double)cnt);
+        KFAC_LAUNCH_CHECK(h);
+    }
+    for (int l = L - 1; l >= 2; l--) {
+        MxLayer& up = P.lay[l - 1];    // g^{(l)}
+        MxLayer& dn = P.lay[l - 2];    // layer l-1 (output of the backward step)
+        Args a = base_args(h, P, N);
+        a.a0 = up.kZb;
+        a.b0 = m->w.kWt[l - 1];
+        a.k_steps = up.hp / 64;
+        a.n_out = dn.h;
+        a.hp_out = dn.hp;
+        a.out_hi = dn.Zb;
+        a.out_gr = dn.Gr;
+        a.A0 = dn.A0;
+        a.AD = dn.AD;
+        a.SSQ = dn.SSQ;
+        a.YD = dn.YD;
+        a.part = m->part;
+        a.ytan = dn.T_hi;
+        a.r = r;
+        const int jb = (dn.hp + 127) / 128, pb = P.N_pad / 128;
+        double fl = 2.0 * P.N_pad * (double)up.hp * dn.hp;
+        kfac_status_t st;
+        if (S > 1) {
+            st = launch_engine<tck::BWD_LAP>(h, s, a, dim3(jb, pb, 1), KFAC_KC_ADJOINT_GEMM, fl);
+            if (st) return st;
+            choose_chunks(S - 2, jb * pb, h->sm_count, a.chunk_len, a.n_chunks);
+            st = launch_engine<tck::BWD_TAN>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_ADJOINT_GEMM, fl * (S - 2));
+            if (st) return st;
+        }
+        st = launch_engine<tck::BWD_VALUE>(h, s, a, dim3(jb, pb, 1), KFAC_KC_ADJOINT_GEMM, fl);
+        if (st) return st;
+    }
+    return KFAC_OK;
+}
+
+kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double* X, int N, const double* Xb,
+                               int Nb) {
+    MxState* m = MX(h);
+    MxPass& I = m->in;
+    MxPass& B = m->bd;
+    const int L = h->cfg.L, d = h->dims[0], S = I.S;
+    const double beta = h->cfg.beta;
+    const bool reduce = (h->cfg.variant == KFAC_REDUCE);
+    float* part_i = m->gpart;
+    float* part_b = m->gpart + m->gpart_region;
+    double* cs_i = m->cs;
+    double* cs_b = m->cs + (m->hp_max + 8);
+    kfac_status_t st;
+    int zi = 0, zb = 0;
+
+    // ---- layer 1: closed-form A, gradient from the adjoints ---------------
+    {
+        int n1 = d + 1;
+        k_factor_A1<<<ceil_div_u(n1 * n1, EW), EW, 0, s>>>(X, N, d, S, reduce, 0, h->fac[KFAC_A_INT][0], beta,
+                                                            h->status);
+        KFAC_LAUNCH_CHECK(h);
+        k_factor_A1<<<ceil_div_u(n1 * n1, EW), EW, 0, s>>>(Xb, Nb, d, 1, 0, 1, h->fac[KFAC_A_BDY][0], beta,
+                                                            h->status);
+        KFAC_LAUNCH_CHECK(h);
+        MxLayer& l1 = I.lay[0];
+        k_grad_layer1<<<ceil_div_u((long long)l1.h * (d + 1), EW), EW, 0, s>>>(
+            l1.Gr, B.lay[0].Gr, X, Xb, N, I.N_pad, Nb, d, l1.h, l1.hp, S, h->grad + h->woff[0]);
+        KFAC_LAUNCH_CHECK(h);
+    }
+    // ---- hidden-layer output factors B_l, l = 1..L-1 -----------------------
+    for (int l = 1; l <= L - 1; l++) {
+        MxLayer& li = I.lay[l - 1];
+        MxLayer& lb = B.lay[l - 1];
+        if (reduce) {
+            long long cnt = (long long)I.N_pad * li.hp;
+            k_sum_over_s<<<ceil_div_u(cnt, EW), EW, 0, s>>>(li.Zb, I.N_pad, S, li.hp, 1.f, I.red_g);
+            KFAC_LAUNCH_CHECK(h);
+            if ((st = gram(h, s, I.gRg[l - 1], I.gRg[l - 1], li.h, li.h, I.N_pad, 1, part_i, zi))) return st;
+        } else {
+            if ((st = gram(h, s, li.gZb, li.gZb, li.h, li.h, I.rows, 1, part_i, zi))) return st;
+        }
+        long long nn = (long long)li.h * li.h;
+        k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_i, zi, li.h, 1, nullptr, 1.0 / N, 0.0, 0.0, 0,
+                                                         h->fac[KFAC_B_INT][l - 1], beta, h->status);
+        KFAC_LAUNCH_CHECK(h);
+        if ((st = gram(h, s, lb.gZb, lb.gZb, lb.h, lb.h, B.rows, 1, part_b, zb))) return st;
+        k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_b, zb, lb.h, 1, nullptr, 1.0 / Nb, 0.0, 0.0, 0,
+                                                         h->fac[KFAC_B_BDY][l - 1], beta, h->status);
+        KFAC_LAUNCH_CHECK(h);
+    }
+    // ---- input factors A_l and gradients of layers 2..L ---------------------
+    for (int l = 2; l <= L; l++) {
+        MxLayer& ti = I.lay[l - 2];   // T^{(l-1)}
+        MxLayer& tb = B.lay[l - 2];
+        const int hin = ti.h;
+        const long long nn = (long long)(hin + 1) * (hin + 1);
+        // interior A_l
+        if (reduce) {
+            long long cnt = (long long)I.N_pad * ti.hp;
+            k_sum_over_s<<<ceil_div_u(cnt, EW), EW, 0, s>>>(ti.T_hi, I.N_pad, S, ti.hp, 1.f / S, I.red_a);
+            KFAC_LAUNCH_CHECK(h);
+            if ((st = gram(h, s, I.gRa[l - 2], I.gRa[l - 2], hin, hin, I.N_pad, 1, part_i, zi))) return st;
+            k_colsum<<<ceil_div_u(hin, EW), EW, 0, s>>>(I.red_a, nullptr, ti.hp, 0, N, hin, cs_i);
+            KFAC_LAUNCH_CHECK(h);
+            k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_i, zi, hin, 1, cs_i, 1.0 / N, 1.0 / ((double)N * S),
+                                                             1.0 / ((double)S * S), 1, h->fac[KFAC_A_INT][l - 1], beta,
+                                                             h->status);
+        } else {
+            if ((st = gram(h, s, ti.gT, ti.gT, hin, hin, I.rows, 1, part_i, zi))) return st;
+            k_colsum<<<ceil_div_u(hin, EW), EW, 0, s>>>(ti.T_hi, ti.T_lo, ti.hp, 0, N, hin, cs_i);
+            KFAC_LAUNCH_CHECK(h);
+            double sc = 1.0 / ((double)N * S);
+            k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_i, zi, hin, 1, cs_i, sc, sc, 1.0 / S, 1,
+                                                             h->fac[KFAC_A_INT][l - 1], beta, h->status);
+        }
+        KFAC_LAUNCH_CHECK(h);
+        // boundary A_l
+        if ((st = gram(h, s, tb.gT, tb.gT, hin, hin, B.rows, 1, part_b, zb))) return st;
+        k_colsum<<<ceil_div_u(hin, EW), EW, 0, s>>>(tb.T_hi, tb.T_lo, tb.hp, 0, Nb, hin, cs_b);
+        KFAC_LAUNCH_CHECK(h);
+        k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_b, zb, hin, 1, cs_b, 1.0 / Nb, 1.0 / Nb, 1.0, 1,
+                                                         h->fac[KFAC_A_BDY][l - 1], beta, h->status);
+        KFAC_LAUNCH_CHECK(h);
+        // gradient of layer l
+        if (l < L) {
+            MxLayer& gi = I.lay[l - 1];
+            MxLayer& gb = B.lay[l - 1];
+            const int hout = gi.h;
+            if ((st = gram(h, s, gi.gGr, ti.gT, hout, hin, I.rows, 0, part_i, zi))) return st;
+            if ((st = gram(h, s, gb.gGr, tb.gT, hout, hin, B.rows, 0, part_b, zb))) return st;
+            k_colsum<<<ceil_div_u(hout, EW), EW, 0, s>>>(gi.Gr, nullptr, gi.hp, 0, N, hout, cs_i);
+            KFAC_LAUNCH_CHECK(h);
+            k_colsum<<<ceil_div_u(hout, EW), EW, 0, s>>>(gb.Gr, nullptr, gb.hp, 0, Nb, hout, cs_b);
+            KFAC_LAUNCH_CHECK(h);
+            k_grad_reduce<<<ceil_div_u((long long)hout * (hin + 1), EW), EW, 0, s>>>(
+                part_i, zi, part_b, zb, hout, hin, cs_i, cs_b, 1.0 / N, 1.0 / Nb, h->grad + h->woff[l - 1]);
+            KFAC_LAUNCH_CHECK(h);
+        } else {
+            k_last_layer_terms<<<ceil_div_u(hin + 1, EW), EW, 0, s>>>(
+                ti.T_hi, ti.T_lo, tb.T_hi, tb.T_lo, h->in.r, h->bd.r, N, I.N_pad, Nb, B.N_pad, hin, ti.hp, S,
+                h->cfg.op == KFAC_OP_HEAT, h->cfg.kappa, reduce, h->grad + h->woff[L - 1], h->fac[KFAC_B_INT][L - 1],
+                h->fac[KFAC_B_BDY][L - 1], beta, h->status);
+            KFAC_LAUNCH_CHECK(h);
+        }
+    }
+    return KFAC_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// Library-internal entry points
+// ============================================================================
+kfac_status_t tc_alloc(kfac_pinn_handle* h) {
+    if (h->cfg.L < 2) return KFAC_BAD_ARG;   // the mixed path needs a hidden layer
+    MxState* m = (MxState*)calloc(1, sizeof(MxState));
+    if (!m) return KFAC_OOM;
+    h->mx = m;
+    kfac_status_t st;
+    if ((st = alloc_pass(h, m->in, h->cfg.max_n_int, h->S))) return st;
+    if ((st = alloc_pass(h, m->bd, h->cfg.max_n_bdy, 1))) return st;
+    const int L = h->cfg.L;
+    int hp_max = 64;
+    for (int l = 0; l <= L; l++) hp_max = hp_max > round_up(h->dims[l], 64) ? hp_max : round_up(h->dims[l], 64);
+    m->hp_max = hp_max;
+    for (int l = 2; l <= L - 1; l++) {
+        int hout_p = round_up(h->dims[l], 64), hin_p = round_up(h->dims[l - 1], 64);
+        size_t e = (size_t)hout_p * hin_p;
+        if ((st = dal(&m->w.W_hi[l - 1], e))) return st;
+        if ((st = dal(&m->w.W_lo[l - 1], e))) return st;
+        if ((st = dal(&m->w.Wt[l - 1], e))) return st;
+        if ((st = dal(&m->w.bias[l - 1], (size_t)hout_p))) return st;
+        bool ok = tc_make_tmap_2d(&m->w.kW_hi[l - 1], m->w.W_hi[l - 1], hin_p, hout_p, hin_p * 2, 64, 128) &&
+                  tc_make_tmap_2d(&m->w.kW_lo[l - 1], m->w.W_lo[l - 1], hin_p, hout_p, hin_p * 2, 64, 128) &&
+                  tc_make_tmap_2d(&m->w.kWt[l - 1], m->w.Wt[l - 1], hout_p, hin_p, hout_p * 2, 64, 128);
+        if (!ok) return KFAC_CUDA_ERROR;
+    }
+    if ((st = dal(&m->w.wL, (size_t)round_up(h->dims[L - 1], 64) + 1))) return st;
+    if ((st = dal(&m->part, (size_t)MAX_CHUNKS * m->in.N_pad * hp_max))) return st;
+    size_t maxPQ = (size_t)hp_max * hp_max;
+    m->gpart_region = (size_t)MAX_GRAM_CHUNKS * maxPQ;
+    if ((st = dal(&m->gpart, 2 * m->gpart_region))) return st;
+    if ((st = dal(&m->cs, 2 * ((size_t)hp_max + 8)))) return st;
+    return KFAC_OK;
+}
+
+void tc_free(kfac_pinn_handle* h) {
+    MxState* m = MX(h);
+    if (!m) return;
+    free_pass(m->in);
+    free_pass(m->bd);
+    for (int l = 0; l < KFAC_MAX_LAYERS; l++) {
+        cudaFree(m->w.W_hi[l]); cudaFree(m->w.W_lo[l]); cudaFree(m->w.Wt[l]); cudaFree(m->w.bias[l]);
+    }
+    cudaFree(m->w.wL);
+    cudaFree(m->part);
+    cudaFree(m->gpart);
+    cudaFree(m->cs);
+    free(m);
+    h->mx = nullptr;
+}
+
+kfac_status_t tc_factors(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int, int N_int,
+                         const double* f, const double* X_bdy, int N_bdy, const double* g, double* loss) {
+    MxState* m = MX(h);
+    kfac_status_t st;
+    const int S = m->in.S;
+    const int heat = h->cfg.op == KFAC_OP_HEAT;
+    if ((st = convert_weights(h, s, theta))) return st;
+    // interior: the residual needs the Laplacian row (and the time row for heat)
+    BlockSel si;
+    si.nsel = heat ? 2 : 1;
+    si.b[0] = S - 1;
+    si.b[1] = 1;
+    si.b[2] = 0;
+    si.split_time = heat;
+    if ((st = forward_pass(h, s, theta, X_int, N_int, m->in, si))) return st;
+    k_residual_mx<<<ceil_div_u(N_int, EW), EW, 0, s>>>(m->in.zl, f, h->in.r, N_int, m->in.N_pad, S, 1, heat,
+                                                        h->cfg.kappa);
+    KFAC_LAUNCH_CHECK(h);
+    BlockSel sb;
+    sb.nsel = 1;
+    sb.b[0] = 0;
+    sb.b[1] = sb.b[2] = 0;
+    sb.split_time = 0;
+    if ((st = forward_pass(h, s, theta, X_bdy, N_bdy, m->bd, sb))) return st;
+    k_residual_mx<<<ceil_div_u(N_bdy, EW), EW, 0, s>>>(m->bd.zl, g, h->bd.r, N_bdy, m->bd.N_pad, 1, 0, heat,
+                                                        h->cfg.kappa);
+    KFAC_LAUNCH_CHECK(h);
+    if ((st = fp64_loss(h, s, N_int, N_bdy, loss))) return st;
+    if ((st = backward_pass(h, s, h->in.r, N_int, m->in))) return st;
+    if ((st = backward_pass(h, s, h->bd.r, N_bdy, m->bd))) return st;
+    return factors_and_grad(h, s, X_int, N_int, X_bdy, N_bdy);
+}
+
+kfac_status_t tc_forward_laplacian(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X, int N,
+                                   double* u, double* grad, double* lap) {
+    MxState* m = MX(h);
+    kfac_status_t st;
+    if ((st = convert_weights(h, s, theta))) return st;
+    BlockSel all;
+    all.nsel = 0;
+    all.b[0] = all.b[1] = all.b[2] = 0;
+    all.split_time = (h->cfg.op == KFAC_OP_HEAT) ? 1 : 0;
+    if ((st = forward_pass(h, s, theta, X, N, m->in, all))) return st;
+    k_extract_mx<<<ceil_div_u(N, EW), EW, 0, s>>>(m->in.zl, N, m->in.N_pad, m->in.S, h->dims[0], u, grad, lap);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
 }
