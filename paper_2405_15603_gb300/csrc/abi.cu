@@ -55,6 +55,7 @@ void free_handle(kfac_pinn_handle* h) {
     free_pass(h->in);
     free_pass(h->bd);
     tc_free(h);
+    eig_free(h);
     cudaFree(h->grad);
     cudaFree(h->dir);
     cudaFree(h->delta_prev);
@@ -333,6 +334,7 @@ kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out) {
     h->stage_elems = (size_t)cfg->max_n_int * (cfg->d + 1) + (size_t)cfg->max_n_bdy * (cfg->d + 1) + 8;
     TRY(dalloc(&h->stage, h->stage_elems));
     if (cfg->precision == KFAC_MIXED_BF16) TRY(tc_alloc(h));
+    TRY(eig_alloc(h));
     if (cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) { free_handle(h); return KFAC_CUDA_ERROR; }
     TRY(reset_state(h, 0));
     if (cudaDeviceSynchronize() != cudaSuccess) { free_handle(h); return KFAC_CUDA_ERROR; }

@@ -1,0 +1,1188 @@
+// Batched FP64 simultaneous diagonalisation of the damped factor pairs
+// (Sec. 3.4, "eigen-decomposing all Kronecker factors"):
+//     V^T P V = I,  V^T Q V = diag(w),   P = A~_Omega, Q = A~_bdy   (and B)
+// for every layer at once, each stage spread over the whole GPU:
+//   1. blocked Cholesky P = L L^T               (diag / panel / trailing kernels)
+//   2. M = L^{-1} Q L^{-T}                      (two column-parallel TRSMs)
+//   3. Householder tridiagonalisation of M      (one cooperative kernel; each
+//      problem owns a group of CTAs that sync through bounded global barriers)
+//   4. divide and conquer on the tridiagonal T  (Cuppen's rank-one tearing,
+//      deflation, secular equation solved by bisection, eigenvectors via the
+//      Gu-Eisenstat recomputed z, block GEMMs per merge level)
+//   5. back-transformation by the Householder reflectors (column-parallel)
+//   6. V = L^{-T} U                              (TRSM)
+// Errors (a P that is not positive definite, a barrier that gave up) are
+// latched in the handle's status word; the problem's V and w are then zero.
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#include <vector>
+#include <algorithm>
+
+#include "kfac_internal.cuh"
+
+namespace {
+
+constexpr int NB = 64;        // Cholesky / TRSM block
+constexpr int CB = 32;        // TRSM column block
+constexpr int BT_COLS = 16;   // back-transform column block
+constexpr int MAXP = 2 * KFAC_MAX_LAYERS;
+constexpr double DEPS = 2.220446049250313e-16;
+
+struct Prob {
+    int n;
+    const double* P;
+    const double* Q;
+    double* V;
+    double* w;
+    double *L, *M, *Qa, *Qb, *R, *R2;      // n x n row-major
+    double *d, *e, *tau, *D, *pbuf;        // n
+    double *Ds, *zs, *dK, *zK, *tauR, *zh, *rc, *rs, *val; // n (per-merge scratch at offset a)
+    int *perm, *defl, *Kidx, *org, *rj, *ri, *col;          // n
+    int *mk, *mnrot, *mflip;               // per merge (indexed by block start a)
+    double* mrh;
+    int final_buf;                         // 0: Qa, 1: Qb holds the D&C result
+};
+
+struct Merge {
+    int prob, a, s1, s2;
+    int r0;      // prefix sum of the merge sizes within the level
+};
+
+// merge owning global row index t of a level (binary search on r0)
+__device__ int find_merge(const Merge* mg, int n_merges, int t) {
+    int lo = 0, hi = n_merges - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (mg[mid].r0 <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct Gd {   // one block GEMM of a merge: C = A B, A (M x K), B (K x N), all row stride ld
+    const double* A;
+    const double* B;
+    double* C;
+    int ld, M, N, K, tile0;
+};
+
+struct Copy {
+    const double* src;
+    double* dst;
+    int ld, m;
+};
+
+struct Level {
+    Merge* merges;     // device
+    int n_merges;
+    int max_m;
+    Gd* gemms;         // device
+    int n_gemms, n_tiles;
+    Copy* copies;      // device
+    int n_copies, max_copy;
+    int roots;         // sum of m over merges
+};
+
+struct EigState {
+    int np;
+    Prob host[MAXP];
+    Prob* dev;                  // device copy of host[]
+    double* ws;                 // all double workspaces
+    int* iws;                   // all int workspaces
+    int* fail;                  // per problem
+    unsigned* bar;              // per problem: count, generation
+    int* abort_flag;
+    int* cta_prob;              // cooperative tridiagonalisation: problem of each CTA
+    int* cta_rank;
+    int* group;                 // group size per problem
+    int n_cta;
+    std::vector<Level> levels;
+    int nmax;
+};
+
+EigState* ES(kfac_pinn_handle* h) { return (EigState*)h->eig; }
+
+// --------------------------------------------------------------------------
+// Small helpers
+// --------------------------------------------------------------------------
+__device__ double block_reduce_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x / 32); i++) t += sh[i];
+        sh[32] = t;
+    }
+    __syncthreads();
+    double r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ double block_reduce_max(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x / 32); i++) t = fmax(t, sh[i]);
+        sh[32] = t;
+    }
+    __syncthreads();
+    double r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// --------------------------------------------------------------------------
+// 0. damped copies
+// --------------------------------------------------------------------------
+__global__ void k_damp(Prob* pr, double eps, int* fail) {
+    const Prob p = pr[blockIdx.y];
+    const int n = p.n;
+    if (threadIdx.x == 0 && blockIdx.x == 0) fail[blockIdx.y] = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)n * n;
+         i += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(i / n), c = (int)(i % n);
+        double e = (r == c) ? eps : 0.0;
+        p.L[i] = p.P[i] + e;
+        p.M[i] = p.Q[i] + e;
+    }
+}
+
+// --------------------------------------------------------------------------
+// 1. blocked Cholesky (lower), block k0
+// --------------------------------------------------------------------------
+__global__ void k_chol_diag(Prob* pr, int k0, int* fail, int* status) {
+    __shared__ double A[NB][NB + 1];
+    __shared__ int bad;
+    const Prob p = pr[blockIdx.x];
+    const int n = p.n;
+    if (k0 >= n || fail[blockIdx.x]) return;
+    const int nb = min(NB, n - k0);
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        int r = t / nb, c = t % nb;
+        A[r][c] = p.L[(long long)(k0 + r) * n + k0 + c];
+    }
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < nb; j++) {
+        if (threadIdx.x == 0) {
+            double a = A[j][j];
+            if (!(a > 0.0) || !isfinite(a)) bad = 1;
+            A[j][j] = sqrt(fmax(a, 0.0));
+        }
+        __syncthreads();
+        if (bad) break;
+        const double djj = A[j][j];
+        for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) A[i][j] /= djj;
+        __syncthreads();
+        const int m = nb - j - 1;
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+            int i = j + 1 + t / m, c = j + 1 + t % m;
+            if (c <= i) A[i][c] -= A[i][j] * A[c][j];
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (threadIdx.x == 0) {
+            fail[blockIdx.x] = 1;
+            latch_status(status, KFAC_NOT_PD);
+        }
+        return;
+    }
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        int r = t / nb, c = t % nb;
+        if (c <= r) p.L[(long long)(k0 + r) * n + k0 + c] = A[r][c];
+    }
+}
+
+// rows below the diagonal block: X = A L_kk^{-T}.  The 64 x 64 row block is
+// solved column by column in shared memory (right-looking): after column j
+// is final, its contribution is removed from the later columns.
+__global__ void __launch_bounds__(256) k_chol_panel(Prob* pr, int k0, int* fail) {
+    __shared__ double Lk[NB][NB + 1];
+    __shared__ double Xs[NB][NB + 1];
+    const Prob p = pr[blockIdx.y];
+    const int n = p.n;
+    if (k0 >= n || fail[blockIdx.y]) return;
+    const int nb = min(NB, n - k0);
+    const int r0 = k0 + nb + blockIdx.x * NB;
+    if (r0 >= n) return;
+    const int rows = min(NB, n - r0);
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+        int r = t / NB, c = t % NB;
+        Lk[r][c] = (r < nb && c <= r) ? p.L[(long long)(k0 + r) * n + k0 + c] : 0.0;
+        Xs[r][c] = (r < rows && c < nb) ? p.L[(long long)(r0 + r) * n + k0 + c] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < nb; j++) {
+        const double ljj = Lk[j][j];
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) Xs[r][j] /= ljj;
+        __syncthreads();
+        for (int t = threadIdx.x; t < rows * NB; t += blockDim.x) {
+            int r = t / NB, c = t % NB;
+            if (c > j && c < nb) Xs[r][c] -= Xs[r][j] * Lk[c][j];
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < rows * nb; t += blockDim.x) {
+        int r = t / nb, c = t % nb;
+        p.L[(long long)(r0 + r) * n + k0 + c] = Xs[r][c];
+    }
+}
+
+// trailing update of the lower triangle: A_ij -= L_i L_j^T over the panel
+__global__ void __launch_bounds__(256) k_chol_update(Prob* pr, int k0, int* fail) {
+    __shared__ double As[16][NB + 1];
+    __shared__ double Bs[16][NB + 1];
+    const Prob p = pr[blockIdx.y];
+    const int n = p.n;
+    if (k0 >= n || fail[blockIdx.y]) return;
+    const int nb = min(NB, n - k0);
+    const int t0 = k0 + nb;
+    if (t0 >= n) return;
+    const int nt = (n - t0 + NB - 1) / NB;
+    int t = blockIdx.x;
+    if (t >= nt * (nt + 1) / 2) return;
+    int bi = 0;
+    while ((bi + 1) * (bi + 2) / 2 <= t) bi++;
+    int bj = t - bi * (bi + 1) / 2;
+    const int i0 = t0 + bi * NB, j0 = t0 + bj * NB;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4] = {};
+    for (int kc = 0; kc < nb; kc += 16) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < NB * 16; q += blockDim.x) {
+            int r = q / 16, c = q % 16;
+            As[c][r] = (i0 + r < n && kc + c < nb) ? p.L[(long long)(i0 + r) * n + k0 + kc + c] : 0.0;
+            Bs[c][r] = (j0 + r < n && kc + c < nb) ? p.L[(long long)(j0 + r) * n + k0 + kc + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            int r = i0 + ty + 16 * i, c = j0 + tx + 16 * j;
+            if (r < n && c < n && c <= r) p.L[(long long)r * n + c] -= acc[i][j];
+        }
+}
+
+// --------------------------------------------------------------------------
+// 2/6. column-parallel triangular solves with L
+//   mode 0: X = L^{-1} B,   B = M (row-major),   X -> Qa
+//   mode 1: X = L^{-1} B^T, B = Qa,              X -> M
+//   mode 2: X = L^{-T} B,   B = final D&C buffer, X -> V
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_trsm(Prob* pr, int mode, int* fail) {
+    extern __shared__ double sm[];
+    double* Lb = sm;                       // NB x (NB+1)
+    double* Xk = Lb + NB * (NB + 1);       // NB x (CB+1)
+    double* acc = Xk + NB * (CB + 1);      // NB x (CB+1)
+    const Prob p = pr[blockIdx.y];
+    const int n = p.n;
+    const int c0 = blockIdx.x * CB;
+    if (c0 >= n) return;
+    const bool failed = fail[blockIdx.y] != 0;
+    const double* B;
+    double* X;
+    if (mode == 0) { B = p.M; X = p.Qa; }
+    else if (mode == 1) { B = p.Qa; X = p.M; }
+    else { B = p.final_buf ? p.Qb : p.Qa; X = p.V; }
+    const int ncb = min(CB, n - c0);
+    const int nblk = (n + NB - 1) / NB;
+    if (failed) {
+        if (mode == 2)
+            for (int t = threadIdx.x; t < n * ncb; t += blockDim.x) X[(long long)(t / ncb) * n + c0 + t % ncb] = 0.0;
+        return;
+    }
+    const bool upper = (mode == 2);
+    for (int s = 0; s < nblk; s++) {
+        const int ib = upper ? nblk - 1 - s : s;
+        const int r0 = ib * NB, rows = min(NB, n - r0);
+        for (int t = threadIdx.x; t < NB * CB; t += blockDim.x) {
+            int r = t / CB, c = t % CB;
+            double v = 0.0;
+            if (r < rows && c < ncb)
+                v = (mode == 1) ? B[(long long)(c0 + c) * n + r0 + r] : B[(long long)(r0 + r) * n + c0 + c];
+            acc[r * (CB + 1) + c] = v;
+        }
+        // subtract the solved blocks
+        for (int kk = 0; kk < s; kk++) {
+            const int kb = upper ? nblk - 1 - kk : kk;
+            const int k0 = kb * NB, kr = min(NB, n - k0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+                int r = t / NB, m = t % NB;
+                double v = 0.0;
+                if (r < rows && m < kr)
+                    v = upper ? p.L[(long long)(k0 + m) * n + r0 + r] : p.L[(long long)(r0 + r) * n + k0 + m];
+                Lb[r * (NB + 1) + m] = v;
+            }
+            for (int t = threadIdx.x; t < NB * CB; t += blockDim.x) {
+                int m = t / CB, c = t % CB;
+                Xk[m * (CB + 1) + c] = (m < kr && c < ncb) ? X[(long long)(k0 + m) * n + c0 + c] : 0.0;
+            }
+            __syncthreads();
+            // acc[r][c] -= sum_m Lb[r][m] Xk[m][c]; 256 threads -> 8 outputs each
+            const int c = threadIdx.x % CB, rg = threadIdx.x / CB;   // rg in 0..7
+#pragma unroll
+            for (int i = 0; i < NB / 8; i++) {
+                const int r = rg + 8 * i;
+                double v = 0.0;
+                for (int m = 0; m < NB; m++) v = fma(Lb[r * (NB + 1) + m], Xk[m * (CB + 1) + c], v);
+                acc[r * (CB + 1) + c] -= v;
+            }
+        }
+        // diagonal block
+        __syncthreads();
+        for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+            int r = t / NB, m = t % NB;
+            Lb[r * (NB + 1) + m] = (r < rows && m < rows) ? p.L[(long long)(r0 + r) * n + r0 + m] : 0.0;
+        }
+        __syncthreads();
+        // right-looking substitution; L_ii lower (rows x rows), upper uses L_ii^T
+        for (int q = 0; q < rows; q++) {
+            const int r = upper ? rows - 1 - q : q;
+            if (threadIdx.x < CB) {
+                acc[r * (CB + 1) + threadIdx.x] /= Lb[r * (NB + 1) + r];
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < NB * CB; t += blockDim.x) {
+                int rr = t / CB, c = t % CB;
+                bool below = upper ? (rr < r) : (rr > r && rr < rows);
+                if (below) {
+                    double l = upper ? Lb[r * (NB + 1) + rr] : Lb[rr * (NB + 1) + r];
+                    acc[rr * (CB + 1) + c] -= l * acc[r * (CB + 1) + c];
+                }
+            }
+            __syncthreads();
+        }
+        for (int t = threadIdx.x; t < NB * CB; t += blockDim.x) {
+            int r = t / CB, c = t % CB;
+            if (r < rows && c < ncb) X[(long long)(r0 + r) * n + c0 + c] = acc[r * (CB + 1) + c];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_symmetrize(Prob* pr, int* fail) {
+    const Prob p = pr[blockIdx.y];
+    const int n = p.n;
+    if (fail[blockIdx.y]) return;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)n * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(t / n), c = (int)(t % n);
+        if (r < c) {
+            double a = 0.5 * (p.M[(long long)r * n + c] + p.M[(long long)c * n + r]);
+            p.M[(long long)r * n + c] = a;
+            p.M[(long long)c * n + r] = a;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// 3. Householder tridiagonalisation, cooperative
+// --------------------------------------------------------------------------
+__device__ bool group_barrier(unsigned* bar, int g, int* abort_flag) {
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned* vgen = bar + 1;
+        unsigned gen = *vgen;
+        __threadfence();
+        unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == (unsigned)(g - 1)) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            uint64_t t0;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            for (unsigned it = 0;; it++) {
+                if (*vgen != gen) break;
+                if (*(volatile int*)abort_flag) { ok = 0; break; }
+                if ((it & 63u) == 0) {
+                    uint64_t t1;
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+                    if (t1 - t0 > 2000000000ull) { ok = 0; atomicExch(abort_flag, 1); break; }
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, const int* cta_rank,
+                                                 const int* group, unsigned* bars, int* abort_flag, int* status,
+                                                 int* fail) {
+    __shared__ double v[1024];
+    __shared__ double w[1024];
+    __shared__ double sh[40];
+    const int pi = cta_prob[blockIdx.x];
+    const int rank = cta_rank[blockIdx.x];
+    const int g = group[pi];
+    const Prob p = pr[pi];
+    const int n = p.n;
+    unsigned* bar = bars + 2 * pi;
+    double* M = p.M;
+    if (fail[pi]) return;   // uniform over the group
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
+    bool alive = true;
+    for (int k = 0; k + 2 < n && alive; k++) {
+        const int b = k + 1, m = n - b;
+        // Householder vector from column k (computed redundantly by every CTA)
+        double part = 0.0;
+        for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) {
+            double x = __ldcg(M + (long long)(b + i) * n + k);
+            part = fma(x, x, part);
+        }
+        const double sigma = block_reduce_sum(part, sh);
+        const double x0 = __ldcg(M + (long long)b * n + k);
+        double tk = 0.0, beta = x0, scale = 0.0;
+        if (sigma > 0.0) {
+            double mu = sqrt(x0 * x0 + sigma);
+            beta = (x0 <= 0.0) ? mu : -mu;
+            tk = (beta - x0) / beta;
+            scale = 1.0 / (x0 - beta);
+        }
+        for (int i = threadIdx.x; i < m; i += blockDim.x)
+            v[i] = (i == 0) ? 1.0 : __ldcg(M + (long long)(b + i) * n + k) * scale;
+        __syncthreads();
+        if (tk == 0.0) {
+            if (rank == 0 && threadIdx.x == 0) { p.tau[k] = 0.0; p.e[k] = beta; }
+            continue;     // every CTA of the group skips the same step
+        }
+        // p_i = tau sum_j M[b+i][b+j] v_j for owned rows (one warp per row)
+        for (int i = rank + warp * g; i < m; i += g * nwarps) {
+            const double* row = M + (long long)(b + i) * n + b;
+            double acc = 0.0;
+            for (int j = lane; j < m; j += 32) acc = fma(row[j], v[j], acc);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (lane == 0) p.pbuf[i] = tk * acc;
+        }
+        if (!group_barrier(bar, g, abort_flag)) { alive = false; break; }
+        double kp = 0.0;
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            double pj = __ldcg(p.pbuf + j);
+            w[j] = pj;
+            kp = fma(pj, v[j], kp);
+        }
+        const double K = 0.5 * tk * block_reduce_sum(kp, sh);
+        for (int j = threadIdx.x; j < m; j += blockDim.x) w[j] -= K * v[j];
+        __syncthreads();
+        // rank-2 update of the owned rows; keep v in column k
+        for (int i = rank + warp * g; i < m; i += g * nwarps) {
+            double* row = M + (long long)(b + i) * n + b;
+            const double vi = v[i], wi = w[i];
+            for (int j = lane; j < m; j += 32) row[j] -= vi * w[j] + wi * v[j];
+            if (lane == 0 && i >= 1) M[(long long)(b + i) * n + k] = vi;
+        }
+        if (rank == 0 && threadIdx.x == 0) { p.tau[k] = tk; p.e[k] = beta; }
+        if (!group_barrier(bar, g, abort_flag)) { alive = false; break; }
+    }
+    if (!alive) {
+        if (threadIdx.x == 0) latch_status(status, KFAC_TIMEOUT);
+        return;
+    }
+    if (rank == 0) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) p.d[i] = __ldcg(M + (long long)i * n + i);
+        if (threadIdx.x == 0 && n >= 2) p.e[n - 2] = __ldcg(M + (long long)(n - 1) * n + (n - 2));
+    }
+}
+
+// --------------------------------------------------------------------------
+// 4. divide and conquer on (d, e)
+// --------------------------------------------------------------------------
+// Rank-one tearing of every coupling and Q = I.
+__global__ void k_dc_init(Prob* pr, int* fail) {
+    const Prob p = pr[blockIdx.y];
+    const int n = p.n;
+    if (fail[blockIdx.y]) return;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)n * n;
+         t += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(t / n), c = (int)(t % n);
+        p.Qa[t] = (r == c) ? 1.0 : 0.0;
+        if (c == 0) {
+            double v = p.d[r];
+            if (r > 0) v -= p.e[r - 1];
+            if (r < n - 1) v -= p.e[r];
+            p.D[r] = v;
+        }
+    }
+}
+
+// Per merge: z, sign flip, merge-sort of the two sorted halves, normalisation,
+// deflation (small z components; nearly equal poles via plane rotations).
+__global__ void __launch_bounds__(256) k_dc_prepare(Prob* pr, const Merge* merges, int level_parity, int* fail) {
+    __shared__ double sh[40];
+    const Merge mg = merges[blockIdx.x];
+    const Prob p = pr[mg.prob];
+    if (fail[mg.prob]) return;
+    const int n = p.n, a = mg.a, s1 = mg.s1, s2 = mg.s2, m = s1 + s2;
+    const double* Q = level_parity ? p.Qb : p.Qa;
+    const double rho = p.e[a + s1 - 1];
+    const bool flip = rho < 0.0;
+    double* Ds = p.Ds + a;
+    double* zs = p.zs + a;
+    int* perm = p.perm + a;
+    double dmax = 0.0, zz = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const bool h1 = i < s1;
+        const double Di = flip ? -p.D[a + i] : p.D[a + i];
+        const double zi = h1 ? Q[(long long)(a + s1 - 1) * n + a + i] : Q[(long long)(a + s1) * n + a + i];
+        // own position (halves are ascending in D, descending after the flip)
+        const int loc = h1 ? i : i - s1;
+        const int sz = h1 ? s1 : s2, osz = h1 ? s2 : s1, obase = h1 ? s1 : 0;
+        const int own = flip ? sz - 1 - loc : loc;
+        // rank in the other half: # elements with key < Di (ties: half 1 first)
+        int lo = 0, hi = osz;
+        while (lo < hi) {
+            int mid = (lo + hi) / 2;
+            int oidx = obase + (flip ? osz - 1 - mid : mid);
+            double ok = flip ? -p.D[a + oidx] : p.D[a + oidx];
+            bool less = h1 ? (ok < Di) : (ok <= Di);
+            if (less) lo = mid + 1; else hi = mid;
+        }
+        const int pos = own + lo;
+        perm[pos] = i;
+        Ds[pos] = Di;
+        zs[pos] = zi;
+        dmax = fmax(dmax, fabs(Di));
+        zz = fma(zi, zi, zz);
+    }
+    const double zn2 = block_reduce_sum(zz, sh);
+    dmax = block_reduce_max(dmax, sh);
+    const double zn = sqrt(zn2);
+    const double rh = fabs(rho) * zn2;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) zs[i] /= zn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double tol = 8.0 * DEPS * fmax(dmax, rh);
+        int* defl = p.defl + a;
+        int nrot = 0, last = -1;
+        for (int i = 0; i < m; i++) {
+            defl[i] = 0;
+            if (rh * fabs(zs[i]) <= tol) { defl[i] = 1; continue; }
+            if (last >= 0) {
+                const int j = last;
+                const double rr = hypot(zs[j], zs[i]);
+                const double c = zs[i] / rr, s = -zs[j] / rr;
+                const double t = c * s * (Ds[i] - Ds[j]);
+                if (fabs(t) <= tol) {
+                    const double dj = Ds[j], di = Ds[i];
+                    Ds[j] = c * c * dj + s * s * di;
+                    Ds[i] = s * s * dj + c * c * di;
+                    zs[i] = rr;
+                    zs[j] = 0.0;
+                    defl[j] = 1;
+                    p.rj[a + nrot] = j;
+                    p.ri[a + nrot] = i;
+                    p.rc[a + nrot] = c;
+                    p.rs[a + nrot] = s;
+                    nrot++;
+                }
+            }
+            last = i;
+        }
+        int k = 0;
+        for (int i = 0; i < m; i++)
+            if (!defl[i]) {
+                p.Kidx[a + k] = i;
+                p.dK[a + k] = Ds[i];
+                p.zK[a + k] = zs[i];
+                k++;
+            }
+        p.mk[a] = k;
+        p.mnrot[a] = nrot;
+        p.mflip[a] = flip ? 1 : 0;
+        p.mrh[a] = rh;
+    }
+}
+
+// Secular equation 1 + rh sum_t zK_t^2 / (dK_t - lambda) = 0, one warp per
+// root; lambda_j = dK[org] + tau with tau found by bisection on the half
+// interval next to the nearer pole (differences stay exact).
+__global__ void k_dc_roots(Prob* pr, const Merge* merges, int n_merges, int* fail) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    // locate (merge, j): merges are ordered, sizes known
+    const int last = n_merges - 1;
+    if (gw >= merges[last].r0 + merges[last].s1 + merges[last].s2) return;
+    const int mi = find_merge(merges, n_merges, gw);
+    const Merge mg = merges[mi];
+    const int j = gw - mg.r0;
+    const Prob p = pr[mg.prob];
+    if (fail[mg.prob]) return;
+    const int a = mg.a;
+    const int k = p.mk[a];
+    if (j >= k) return;
+    const double rh = p.mrh[a];
+    const double* dK = p.dK + a;
+    const double* zK = p.zK + a;
+    auto f = [&](int o, double t) {
+        double s = 0.0;
+        const double dO = dK[o];
+        for (int q = lane; q < k; q += 32) {
+            double del = (dK[q] - dO) - t;
+            s += zK[q] * zK[q] / del;
+        }
+        for (int o2 = 16; o2 > 0; o2 >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o2);
+        return 1.0 + rh * s;
+    };
+    int o;
+    double lo, hi;
+    if (j < k - 1) {
+        const double gap = dK[j + 1] - dK[j];
+        if (f(j, 0.5 * gap) > 0.0) { o = j; lo = 0.0; hi = 0.5 * gap; }
+        else { o = j + 1; lo = -0.5 * gap; hi = 0.0; }
+    } else {
+        double zz = 0.0;
+        for (int q = lane; q < k; q += 32) zz += zK[q] * zK[q];
+        for (int o2 = 16; o2 > 0; o2 >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, o2);
+        o = j; lo = 0.0; hi = rh * zz * (1.0 + 8.0 * DEPS) + 4.0 * DEPS * fabs(dK[j]);
+    }
+    for (int it = 0; it < 200; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        if (f(o, mid) > 0.0) hi = mid; else lo = mid;
+    }
+    if (lane == 0) {
+        p.org[a + j] = o;
+        p.tauR[a + j] = 0.5 * (lo + hi);
+    }
+}
+
+// Gu-Eisenstat: zhat_i^2 = prod_j (lambda_j - d_i) / (rh prod_{j != i} (d_j - d_i)).
+__global__ void k_dc_zhat(Prob* pr, const Merge* merges, int n_merges, int* fail) {
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int last = n_merges - 1;
+    if (gt >= merges[last].r0 + merges[last].s1 + merges[last].s2) return;
+    const int mi = find_merge(merges, n_merges, gt);
+    const Merge mg = merges[mi];
+    const int i = gt - mg.r0;
+    const Prob p = pr[mg.prob];
+    if (fail[mg.prob]) return;
+    const int a = mg.a;
+    const int k = p.mk[a];
+    if (i >= k) return;
+    const double rh = p.mrh[a];
+    const double* dK = p.dK + a;
+    const double* tauR = p.tauR + a;
+    const int* org = p.org + a;
+    const double di = dK[i];
+    double prod = -((di - dK[org[i]]) - tauR[i]) / rh;   // (lambda_i - d_i) / rh
+    for (int q = 0; q < k; q++) {
+        if (q == i) continue;
+        const double lam_minus_di = -((di - dK[org[q]]) - tauR[q]);
+        prod *= lam_minus_di / (dK[q] - di);
+    }
+    const double z = sqrt(fmax(prod, 0.0));
+    p.zh[a + i] = (p.zK[a + i] < 0.0) ? -z : z;
+}
+
+// Eigenvalue order of the merged block: roots and deflated poles ranked by
+// value; writes the new eigenvalues and the output column of each pair.
+__global__ void __launch_bounds__(256) k_dc_order(Prob* pr, const Merge* merges, int* fail) {
+    const Merge mg = merges[blockIdx.x];
+    const Prob p = pr[mg.prob];
+    if (fail[mg.prob]) return;
+    const int a = mg.a, m = mg.s1 + mg.s2;
+    const int k = p.mk[a];
+    const bool flip = p.mflip[a] != 0;
+    // candidate list: entries 0..k-1 roots, k..m-1 deflated poles (in sorted-basis order)
+    double* val = p.val + a;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        double v;
+        if (t < k) v = p.dK[a + p.org[a + t]] + p.tauR[a + t];
+        else {
+            // the (t-k)-th deflated position
+            int cnt = -1, pos = 0;
+            for (pos = 0; pos < m; pos++)
+                if (p.defl[a + pos] && ++cnt == t - k) break;
+            v = p.Ds[a + pos];
+            val[t] = v;
+            p.Kidx[a + t] = pos;                     // deflated positions follow the roots
+            continue;
+        }
+        val[t] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const double v = val[t];
+        int r = 0;
+        for (int q = 0; q < m; q++) {
+            double u = val[q];
+            if (u < v || (u == v && q < t)) r++;
+        }
+        const int c = flip ? m - 1 - r : r;
+        p.col[a + t] = c;
+        p.D[a + c] = flip ? -v : v;
+    }
+}
+
+// Reduced eigenvectors u_j = zhat / (d - lambda_j), normalised, written into
+// the sorted-basis matrix R (rows = sorted positions, columns = output order);
+// deflated pairs are unit columns.  Grid: (column blocks of 32, merges).
+__global__ void __launch_bounds__(256) k_dc_fillU(Prob* pr, const Merge* merges, int* fail) {
+    const Merge mg = merges[blockIdx.y];
+    const Prob p = pr[mg.prob];
+    if (fail[mg.prob]) return;
+    const int n = p.n, a = mg.a, m = mg.s1 + mg.s2;
+    const int k = p.mk[a];
+    const int t0 = blockIdx.x * 32;
+    if (t0 >= m) return;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    double* R = p.R;
+    for (int tt = warp; tt < 32; tt += blockDim.x / 32) {
+        const int t = t0 + tt;
+        if (t >= m) break;
+        const int c = p.col[a + t];
+        if (t >= k) {   // deflated: unit vector at its sorted position
+            const int pos = p.Kidx[a + t];
+            for (int r = lane; r < m; r += 32) R[(long long)(a + r) * n + a + c] = (r == pos) ? 1.0 : 0.0;
+            continue;
+        }
+        const int o = p.org[a + t];
+        const double dO = p.dK[a + o], tt_ = p.tauR[a + t];
+        double ss = 0.0;
+        for (int q = lane; q < k; q += 32) {
+            double u = p.zh[a + q] / ((p.dK[a + q] - dO) - tt_);
+            ss = fma(u, u, ss);
+        }
+        for (int o2 = 16; o2 > 0; o2 >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o2);
+        const double inv = 1.0 / sqrt(ss);
+        for (int r = lane; r < m; r += 32) R[(long long)(a + r) * n + a + c] = 0.0;
+        __syncwarp();
+        for (int q = lane; q < k; q += 32) {
+            double u = p.zh[a + q] / ((p.dK[a + q] - dO) - tt_);
+            R[(long long)(a + p.Kidx[a + q]) * n + a + c] = u * inv;
+        }
+    }
+}
+
+// Undo the deflation rotations (reverse order, on rows of R) and scatter rows
+// to the block's original index order: R2[perm[pos]][c] = R[pos][c].
+__global__ void __launch_bounds__(256) k_dc_rotate_scatter(Prob* pr, const Merge* merges, int* fail) {
+    const Merge mg = merges[blockIdx.x];
+    const Prob p = pr[mg.prob];
+    if (fail[mg.prob]) return;
+    const int n = p.n, a = mg.a, m = mg.s1 + mg.s2;
+    const int nrot = p.mnrot[a];
+    double* R = p.R;
+    for (int t = nrot - 1; t >= 0; t--) {
+        const int j = p.rj[a + t], i = p.ri[a + t];
+        const double c = p.rc[a + t], s = p.rs[a + t];
+        for (int col = threadIdx.x; col < m; col += blockDim.x) {
+            double uj = R[(long long)(a + j) * n + a + col], ui = R[(long long)(a + i) * n + a + col];
+            R[(long long)(a + j) * n + a + col] = c * uj - s * ui;
+            R[(long long)(a + i) * n + a + col] = s * uj + c * ui;
+        }
+        __syncthreads();
+    }
+    for (long long t = threadIdx.x; t < (long long)m * m; t += blockDim.x) {
+        const int pos = (int)(t / m), col = (int)(t % m);
+        p.R2[(long long)(a + p.perm[a + pos]) * n + a + col] = R[(long long)(a + pos) * n + a + col];
+    }
+}
+
+// Batched block GEMMs of one level: C = A B (FP64, 64 x 64 tiles).
+__global__ void __launch_bounds__(256) k_dc_gemm(const Gd* gd, int n_gd, const int* fail_dummy) {
+    __shared__ double As[16][65];
+    __shared__ double Bs[16][65];
+    const int t = blockIdx.x;
+    int gi = 0, hi = n_gd - 1;
+    while (gi < hi) {
+        int mid = (gi + hi + 1) / 2;
+        if (gd[mid].tile0 <= t) gi = mid; else hi = mid - 1;
+    }
+    const Gd g = gd[gi];
+    const int lt = t - g.tile0;
+    const int ntn = (g.N + 63) / 64;
+    const int i0 = (lt / ntn) * 64, j0 = (lt % ntn) * 64;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < g.K; k0 += 16) {
+        for (int q = threadIdx.x; q < 64 * 16; q += blockDim.x) {
+            int r = q / 16, kk = q % 16;
+            As[kk][r] = (i0 + r < g.M && k0 + kk < g.K) ? g.A[(long long)(i0 + r) * g.ld + k0 + kk] : 0.0;
+            int kk2 = q / 64, c = q % 64;
+            Bs[kk2][c] = (k0 + kk2 < g.K && j0 + c < g.N) ? g.B[(long long)(k0 + kk2) * g.ld + j0 + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; kk++) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            int r = i0 + ty + 16 * i, c = j0 + tx + 16 * j;
+            if (r < g.M && c < g.N) g.C[(long long)r * g.ld + c] = acc[i][j];
+        }
+}
+
+__global__ void k_dc_copy(const Copy* cp, int n_cp) {
+    const Copy c = cp[blockIdx.y];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < c.m * c.m; t += gridDim.x * blockDim.x) {
+        int r = t / c.m, q = t % c.m;
+        c.dst[(long long)r * c.ld + q] = c.src[(long long)r * c.ld + q];
+    }
+}
+
+// --------------------------------------------------------------------------
+// 5. back-transformation: U <- H_0 H_1 .. H_{n-3} U, columns in parallel
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_backtransform(Prob* pr, int* fail) {
+    __shared__ double v[1024];
+    __shared__ double part[16][BT_COLS + 1];
+    const Prob p = pr[blockIdx.y];
+    const int n = p.n;
+    if (fail[blockIdx.y]) return;
+    const int c0 = blockIdx.x * BT_COLS;
+    if (c0 >= n) return;
+    double* U = p.final_buf ? p.Qb : p.Qa;
+    const int cl = threadIdx.x % BT_COLS, rg = threadIdx.x / BT_COLS;   // 16 row groups
+    const int c = c0 + cl;
+    for (int k = n - 3; k >= 0; k--) {
+        const double tk = p.tau[k];
+        if (tk == 0.0) continue;
+        const int b = k + 1, m = n - b;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = (i == 0) ? 1.0 : p.M[(long long)(b + i) * n + k];
+        __syncthreads();
+        double dot = 0.0;
+        if (c < n)
+            for (int i = rg; i < m; i += 16) dot = fma(v[i], U[(long long)(b + i) * n + c], dot);
+        part[rg][cl] = dot;
+        __syncthreads();
+        double tot = 0.0;
+        for (int q = 0; q < 16; q++) tot += part[q][cl];
+        tot *= tk;
+        if (c < n)
+            for (int i = rg; i < m; i += 16) U[(long long)(b + i) * n + c] -= tot * v[i];
+        __syncthreads();
+    }
+}
+
+__global__ void k_write_w(Prob* pr, int* fail, int* status) {
+    const Prob p = pr[blockIdx.x];
+    for (int i = threadIdx.x; i < p.n; i += blockDim.x) {
+        double v = fail[blockIdx.x] ? 0.0 : p.D[i];
+        if (!isfinite(v)) latch_status(status, KFAC_NONFINITE);
+        p.w[i] = v;
+    }
+}
+
+// --------------------------------------------------------------------------
+// host side
+// --------------------------------------------------------------------------
+template <class T>
+kfac_status_t dal(T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return KFAC_OOM; }
+    return e == cudaSuccess ? KFAC_OK : KFAC_CUDA_ERROR;
+}
+
+int ceil_log2(int n) {
+    int l = 0;
+    while ((1 << l) < n) l++;
+    return l;
+}
+
+}  // namespace
+
+kfac_status_t eig_alloc(kfac_pinn_handle* h) {
+    EigState* es = new EigState();
+    h->eig = es;
+    es->np = 0;
+    es->nmax = 0;
+    size_t dtot = 0, itot = 0;
+    std::vector<int> ns;
+    for (int l = 1; l <= h->cfg.L; l++) {
+        ns.push_back(h->dims[l - 1] + 1);
+        ns.push_back(h->dims[l]);
+    }
+    for (int n : ns) {
+        dtot += 6 * (size_t)n * n + 20 * (size_t)n;
+        itot += 12 * (size_t)n;
+        es->nmax = std::max(es->nmax, n);
+    }
+    kfac_status_t st;
+    if ((st = dal(&es->ws, dtot))) return st;
+    if ((st = dal(&es->iws, itot))) return st;
+    double* dp = es->ws;
+    int* ip = es->iws;
+    for (int l = 1; l <= h->cfg.L; l++) {
+        for (int which = 0; which < 2; which++) {
+            Prob& p = es->host[es->np++];
+            memset(&p, 0, sizeof(p));
+            const int n = which == 0 ? h->dims[l - 1] + 1 : h->dims[l];
+            p.n = n;
+            p.P = h->fac[which == 0 ? KFAC_A_INT : KFAC_B_INT][l - 1];
+            p.Q = h->fac[which == 0 ? KFAC_A_BDY : KFAC_B_BDY][l - 1];
+            p.V = which == 0 ? h->VA[l - 1] : h->VB[l - 1];
+            p.w = which == 0 ? h->wa[l - 1] : h->wb[l - 1];
+            size_t nn = (size_t)n * n;
+            p.L = dp; dp += nn;
+            p.M = dp; dp += nn;
+            p.Qa = dp; dp += nn;
+            p.Qb = dp; dp += nn;
+            p.R = dp; dp += nn;
+            p.R2 = dp; dp += nn;
+            double** dv[] = {&p.d, &p.e, &p.tau, &p.D, &p.pbuf, &p.Ds, &p.zs, &p.dK, &p.zK, &p.tauR, &p.zh,
+                             &p.rc, &p.rs, &p.val, &p.mrh};
+            for (double** q : dv) { *q = dp; dp += n; }
+            dp += 5 * (size_t)n;
+            int** iv[] = {&p.perm, &p.defl, &p.Kidx, &p.org, &p.rj, &p.ri, &p.col, &p.mk, &p.mnrot, &p.mflip};
+            for (int** q : iv) { *q = ip; ip += n; }
+            ip += 2 * (size_t)n;
+            // the number of merge levels fixes which buffer holds the result
+            p.final_buf = ceil_log2(n) & 1;
+        }
+    }
+    if ((st = dal(&es->dev, (size_t)es->np))) return st;
+    if (cudaMemcpy(es->dev, es->host, sizeof(Prob) * es->np, cudaMemcpyHostToDevice) != cudaSuccess)
+        return KFAC_CUDA_ERROR;
+    if ((st = dal(&es->fail, (size_t)es->np))) return st;
+    if ((st = dal(&es->bar, 2 * (size_t)es->np))) return st;
+    if ((st = dal(&es->abort_flag, 1))) return st;
+    cudaMemset(es->fail, 0, sizeof(int) * es->np);
+
+    // cooperative tridiagonalisation: CTAs per problem ~ n^3, one CTA per SM
+    {
+        int budget = h->sm_count;
+        std::vector<double> wgt(es->np);
+        double tot = 0.0;
+        int need = 0;
+        for (int i = 0; i < es->np; i++) {
+            double n = es->host[i].n;
+            wgt[i] = n > 2 ? n * n * n : 0.0;
+            tot += wgt[i];
+        }
+        std::vector<int> g(es->np, 1);
+        for (int i = 0; i < es->np; i++) need += 1;
+        int spare = std::max(0, budget - need);
+        for (int i = 0; i < es->np; i++) {
+            if (tot > 0) g[i] += (int)floor(spare * wgt[i] / tot);
+            int cap = std::max(1, es->host[i].n / 8);
+            g[i] = std::min(g[i], cap);
+        }
+        std::vector<int> cp, cr;
+        for (int i = 0; i < es->np; i++)
+            for (int r = 0; r < g[i]; r++) { cp.push_back(i); cr.push_back(r); }
+        es->n_cta = (int)cp.size();
+        if ((st = dal(&es->cta_prob, cp.size()))) return st;
+        if ((st = dal(&es->cta_rank, cr.size()))) return st;
+        if ((st = dal(&es->group, (size_t)es->np))) return st;
+        cudaMemcpy(es->cta_prob, cp.data(), sizeof(int) * cp.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(es->cta_rank, cr.data(), sizeof(int) * cr.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(es->group, g.data(), sizeof(int) * g.size(), cudaMemcpyHostToDevice);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag, 512, 0);
+        if (per_sm * h->sm_count < es->n_cta) return KFAC_BAD_ARG;
+    }
+
+    // divide-and-conquer schedules, one per merge level
+    for (int s = 1; s < es->nmax; s *= 2) {
+        std::vector<Merge> mg;
+        std::vector<Gd> gd;
+        std::vector<Copy> cp;
+        const int parity = (int)es->levels.size() & 1;     // input buffer of this level
+        int tiles = 0, roots = 0, max_m = 0, max_copy = 0;
+        for (int i = 0; i < es->np; i++) {
+            const Prob& p = es->host[i];
+            const int n = p.n;
+            if (s >= n) continue;          // this problem is done
+            double* Qin = parity ? p.Qb : p.Qa;
+            double* Qout = parity ? p.Qa : p.Qb;
+            for (int a = 0; a < n; a += 2 * s) {
+                const int s1 = std::min(s, n - a), s2 = std::min(s, n - a - s1);
+                if (s2 <= 0) {
+                    Copy c;
+                    c.src = Qin + (size_t)a * n + a;
+                    c.dst = Qout + (size_t)a * n + a;
+                    c.ld = n;
+                    c.m = s1;
+                    cp.push_back(c);
+                    max_copy = std::max(max_copy, s1);
+                    continue;
+                }
+                Merge m;
+                m.prob = i; m.a = a; m.s1 = s1; m.s2 = s2; m.r0 = roots;
+                mg.push_back(m);
+                roots += s1 + s2;
+                max_m = std::max(max_m, s1 + s2);
+                // Qout[a..a+s1, a..a+m] = Qin[a..a+s1, a..a+s1] R2[a..a+s1, a..a+m]
+                Gd g1;
+                g1.A = Qin + (size_t)a * n + a;
+                g1.B = p.R2 + (size_t)a * n + a;
+                g1.C = Qout + (size_t)a * n + a;
+                g1.ld = n; g1.M = s1; g1.N = s1 + s2; g1.K = s1; g1.tile0 = tiles;
+                tiles += ((s1 + 63) / 64) * ((s1 + s2 + 63) / 64);
+                gd.push_back(g1);
+                Gd g2;
+                g2.A = Qin + (size_t)(a + s1) * n + a + s1;
+                g2.B = p.R2 + (size_t)(a + s1) * n + a;
+                g2.C = Qout + (size_t)(a + s1) * n + a;
+                g2.ld = n; g2.M = s2; g2.N = s1 + s2; g2.K = s2; g2.tile0 = tiles;
+                tiles += ((s2 + 63) / 64) * ((s1 + s2 + 63) / 64);
+                gd.push_back(g2);
+            }
+        }
+        Level lv;
+        memset(&lv, 0, sizeof(lv));
+        lv.n_merges = (int)mg.size();
+        lv.n_gemms = (int)gd.size();
+        lv.n_tiles = tiles;
+        lv.n_copies = (int)cp.size();
+        lv.max_copy = max_copy;
+        lv.roots = roots;
+        lv.max_m = max_m;
+        if ((st = dal(&lv.merges, mg.size()))) return st;
+        if ((st = dal(&lv.gemms, gd.size()))) return st;
+        if ((st = dal(&lv.copies, cp.size()))) return st;
+        if (!mg.empty()) cudaMemcpy(lv.merges, mg.data(), sizeof(Merge) * mg.size(), cudaMemcpyHostToDevice);
+        if (!gd.empty()) cudaMemcpy(lv.gemms, gd.data(), sizeof(Gd) * gd.size(), cudaMemcpyHostToDevice);
+        if (!cp.empty()) cudaMemcpy(lv.copies, cp.data(), sizeof(Copy) * cp.size(), cudaMemcpyHostToDevice);
+        es->levels.push_back(lv);
+    }
+    cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB + 1)));
+    return cudaGetLastError() == cudaSuccess ? KFAC_OK : KFAC_CUDA_ERROR;
+}
+
+void eig_free(kfac_pinn_handle* h) {
+    EigState* es = ES(h);
+    if (!es) return;
+    cudaFree(es->ws);
+    cudaFree(es->iws);
+    cudaFree(es->dev);
+    cudaFree(es->fail);
+    cudaFree(es->bar);
+    cudaFree(es->abort_flag);
+    cudaFree(es->cta_prob);
+    cudaFree(es->cta_rank);
+    cudaFree(es->group);
+    for (auto& lv : es->levels) {
+        cudaFree(lv.merges);
+        cudaFree(lv.gemms);
+        cudaFree(lv.copies);
+    }
+    delete es;
+    h->eig = nullptr;
+}
+
+kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
+    EigState* es = ES(h);
+    const int np = es->np;
+    Prob* pr = es->dev;
+    const double eps = h->cfg.damping_sqrt ? sqrt(h->cfg.lambda) : h->cfg.lambda;
+    const int nmax = es->nmax;
+    const int nblk = (nmax + NB - 1) / NB;
+
+    k_damp<<<dim3(64, np), 256, 0, s>>>(pr, eps, es->fail);
+    KFAC_LAUNCH_CHECK(h);
+    // 1. Cholesky
+    for (int kb = 0; kb < nblk; kb++) {
+        const int k0 = kb * NB;
+        k_chol_diag<<<np, 256, 0, s>>>(pr, k0, es->fail, h->status);
+        KFAC_LAUNCH_CHECK(h);
+        const int rows = nmax - k0 - NB;
+        if (rows <= 0) continue;
+        const int rb = (rows + NB - 1) / NB;
+        k_chol_panel<<<dim3(rb, np), 256, 0, s>>>(pr, k0, es->fail);
+        KFAC_LAUNCH_CHECK(h);
+        k_chol_update<<<dim3(rb * (rb + 1) / 2, np), 256, 0, s>>>(pr, k0, es->fail);
+        KFAC_LAUNCH_CHECK(h);
+    }
+    // 2. whitening
+    const int smem_trsm = (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB + 1));
+    const int cbk = (nmax + CB - 1) / CB;
+    k_trsm<<<dim3(cbk, np), 256, smem_trsm, s>>>(pr, 0, es->fail);
+    KFAC_LAUNCH_CHECK(h);
+    k_trsm<<<dim3(cbk, np), 256, smem_trsm, s>>>(pr, 1, es->fail);
+    KFAC_LAUNCH_CHECK(h);
+    k_symmetrize<<<dim3(64, np), 256, 0, s>>>(pr, es->fail);
+    KFAC_LAUNCH_CHECK(h);
+    // 3. tridiagonalisation (cooperative: the groups wait on each other)
+    KFAC_CUDA_TRY(cudaMemsetAsync(es->bar, 0, sizeof(unsigned) * 2 * np, s));
+    KFAC_CUDA_TRY(cudaMemsetAsync(es->abort_flag, 0, sizeof(int), s));
+    {
+        void* args[] = {&pr, &es->cta_prob, &es->cta_rank, &es->group, &es->bar, &es->abort_flag, &h->status,
+                        &es->fail};
+        KFAC_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(es->n_cta), dim3(512), args, 0, s));
+        h->launches++;
+    }
+    // 4. divide and conquer
+    k_dc_init<<<dim3(64, np), 256, 0, s>>>(pr, es->fail);
+    KFAC_LAUNCH_CHECK(h);
+    for (size_t li = 0; li < es->levels.size(); li++) {
+        const Level& lv = es->levels[li];
+        const int parity = (int)li & 1;
+        if (lv.n_merges > 0) {
+            k_dc_prepare<<<lv.n_merges, 256, 0, s>>>(pr, lv.merges, parity, es->fail);
+            KFAC_LAUNCH_CHECK(h);
+            k_dc_roots<<<ceil_div_u((long long)lv.roots * 32, 256), 256, 0, s>>>(pr, lv.merges, lv.n_merges,
+                                                                                es->fail);
+            KFAC_LAUNCH_CHECK(h);
+            k_dc_zhat<<<ceil_div_u(lv.roots, 128), 128, 0, s>>>(pr, lv.merges, lv.n_merges, es->fail);
+            KFAC_LAUNCH_CHECK(h);
+            k_dc_order<<<lv.n_merges, 256, 0, s>>>(pr, lv.merges, es->fail);
+            KFAC_LAUNCH_CHECK(h);
+            k_dc_fillU<<<dim3((lv.max_m + 31) / 32, lv.n_merges), 256, 0, s>>>(pr, lv.merges, es->fail);
+            KFAC_LAUNCH_CHECK(h);
+            k_dc_rotate_scatter<<<lv.n_merges, 256, 0, s>>>(pr, lv.merges, es->fail);
+            KFAC_LAUNCH_CHECK(h);
+            k_dc_gemm<<<lv.n_tiles, 256, 0, s>>>(lv.gemms, lv.n_gemms, es->fail);
+            KFAC_LAUNCH_CHECK(h);
+        }
+        if (lv.n_copies > 0) {
+            k_dc_copy<<<dim3(ceil_div_u((long long)lv.max_copy * lv.max_copy, 256), lv.n_copies), 256, 0, s>>>(
+                lv.copies, lv.n_copies);
+            KFAC_LAUNCH_CHECK(h);
+        }
+    }
+    // 5. back-transformation, 6. V = L^{-T} U
+    k_backtransform<<<dim3((nmax + BT_COLS - 1) / BT_COLS, np), 256, 0, s>>>(pr, es->fail);
+    KFAC_LAUNCH_CHECK(h);
+    k_trsm<<<dim3(cbk, np), 256, smem_trsm, s>>>(pr, 2, es->fail);
+    KFAC_LAUNCH_CHECK(h);
+    k_write_w<<<np, 256, 0, s>>>(pr, es->fail, h->status);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}

@@ -65,6 +65,7 @@ struct kfac_pinn_handle {
     double* stage;                        // device copy of the host batch
     size_t stage_elems;
     void* mx;                             // mixed-precision state (tc_path.cu)
+    void* eig;                            // batched eigensolver state (eig.cu)
 
     // per-class device timers (kfac_pinn_timing_*)
     int timing;
@@ -129,6 +130,10 @@ kfac_status_t fp64_extract_outputs(kfac_pinn_handle* h, cudaStream_t s, PassBuff
 // Linear algebra (linalg.cu)
 // ---------------------------------------------------------------------------
 size_t linalg_workspace_elems(const kfac_pinn_handle* h);
+// Batched FP64 generalized eigensolver (eig.cu)
+kfac_status_t eig_alloc(kfac_pinn_handle* h);
+void eig_free(kfac_pinn_handle* h);
+kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s);
 kfac_status_t linalg_invert(kfac_pinn_handle* h, cudaStream_t s);
 kfac_status_t linalg_precondition(kfac_pinn_handle* h, cudaStream_t s, const double* grad,
                                   double* dir);

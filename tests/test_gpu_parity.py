@@ -153,6 +153,34 @@ def test_precondition_given_factors_and_gradient():
     assert rel(out, ref) < 1e-10
 
 
+@pytest.mark.parametrize("dims,rank", [((50, (300, 129, 1)), None), ((100, (768, 512, 1)), 40)])
+def test_eigensolver_large_and_low_rank_factors(dims, rank):
+    # Sizes that exercise the blocked Cholesky (several 64-blocks), the
+    # cooperative tridiagonalisation and every divide-and-conquer level;
+    # low-rank boundary factors give clustered whitened spectra.
+    d, widths = dims
+    opt = _opt(d, widths, lam=1e-3, max_n_int=4, max_n_bdy=4)
+    rng = np.random.default_rng(1)
+    mats = {}
+    full = [d] + list(widths)
+    for l in range(1, len(full)):
+        for which in ("A_int", "B_int", "A_bdy", "B_bdy"):
+            n = full[l - 1] + 1 if which[0] == "A" else full[l]
+            k = n + 3 if (rank is None or which.endswith("int")) else min(rank, n)
+            M = rng.standard_normal((n, k))
+            mats[(l, which)] = M @ M.T / k
+            opt.set_factor(l, which, mats[(l, which)])
+    G = rng.standard_normal(opt.D)
+    opt.invert()
+    out = opt.precondition(torch.tensor(G, device=DEV)).cpu().numpy()
+    assert opt.sync_status() == "KFAC_OK"
+    Gs = ko.unpack_theta(G, d, widths)
+    ref = ko.pack_theta([ko.kron_sum_inverse_apply(mats[(l, "A_int")], mats[(l, "B_int")],
+                                                   mats[(l, "A_bdy")], mats[(l, "B_bdy")], Gs[l - 1], 1e-3)
+                         for l in range(1, len(full))])
+    assert rel(out, ref) < 1e-9, rel(out, ref)
+
+
 @pytest.mark.parametrize("variant", ["expand", "reduce"])
 def test_kfac_steps_fp64(variant):
     # Three steps with EMA, momentum and identity initialisation.
