@@ -35,7 +35,8 @@ struct Prob {
     const double* Q;
     double* V;
     double* w;
-    double *L, *M, *Qa, *Qb, *R, *R2;      // n x n row-major
+    double *L, *M, *Qa, *Qb, *R, *R2, *H;  // n x n row-major (H: Householder vectors, one per row)
+    double* Ld;                            // inverses of the 64 x 64 diagonal blocks of L (n x 64)
     double *d, *e, *tau, *D, *pbuf;        // n
     double *Ds, *zs, *dK, *zK, *tauR, *zh, *rc, *rs, *val; // n (per-merge scratch at offset a)
     int *perm, *defl, *Kidx, *org, *rj, *ri, *col;          // n
@@ -352,35 +353,66 @@ __global__ void __launch_bounds__(256) k_trsm(Prob* pr, int mode, int* fail) {
                 acc[r * (CB + 1) + c] -= v;
             }
         }
-        // diagonal block
+        // diagonal block: X_i = L_ii^{-1} acc (lower) or L_ii^{-T} acc (upper),
+        // with the block inverse precomputed by k_diag_inv
         __syncthreads();
         for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
             int r = t / NB, m = t % NB;
-            Lb[r * (NB + 1) + m] = (r < rows && m < rows) ? p.L[(long long)(r0 + r) * n + r0 + m] : 0.0;
+            Lb[r * (NB + 1) + m] = (r < rows && m < rows) ? p.Ld[(long long)(r0 + r) * NB + m] : 0.0;
         }
         __syncthreads();
-        // right-looking substitution; L_ii lower (rows x rows), upper uses L_ii^T
-        for (int q = 0; q < rows; q++) {
-            const int r = upper ? rows - 1 - q : q;
-            if (threadIdx.x < CB) {
-                acc[r * (CB + 1) + threadIdx.x] /= Lb[r * (NB + 1) + r];
-            }
-            __syncthreads();
-            for (int t = threadIdx.x; t < NB * CB; t += blockDim.x) {
-                int rr = t / CB, c = t % CB;
-                bool below = upper ? (rr < r) : (rr > r && rr < rows);
-                if (below) {
-                    double l = upper ? Lb[r * (NB + 1) + rr] : Lb[rr * (NB + 1) + r];
-                    acc[rr * (CB + 1) + c] -= l * acc[r * (CB + 1) + c];
+        {
+            const int c = threadIdx.x % CB, rg = threadIdx.x / CB;
+#pragma unroll
+            for (int i = 0; i < NB / 8; i++) {
+                const int r = rg + 8 * i;
+                double v = 0.0;
+                for (int m = 0; m < NB; m++) {
+                    const double l = upper ? Lb[m * (NB + 1) + r] : Lb[r * (NB + 1) + m];
+                    v = fma(l, acc[m * (CB + 1) + c], v);
                 }
+                Xk[r * (CB + 1) + c] = v;
             }
-            __syncthreads();
         }
+        __syncthreads();
         for (int t = threadIdx.x; t < NB * CB; t += blockDim.x) {
             int r = t / CB, c = t % CB;
-            if (r < rows && c < ncb) X[(long long)(r0 + r) * n + c0 + c] = acc[r * (CB + 1) + c];
+            if (r < rows && c < ncb) X[(long long)(r0 + r) * n + c0 + c] = Xk[r * (CB + 1) + c];
         }
         __syncthreads();
+    }
+}
+
+// Inverse of every 64 x 64 diagonal block of L (lower triangular), one CTA
+// per block: column c of the inverse by forward substitution on e_c.
+__global__ void __launch_bounds__(256) k_diag_inv(Prob* pr, int* fail) {
+    extern __shared__ double dsm[];                       // 2 x NB x (NB+1), dynamic
+    double (*Ls)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(dsm);
+    double (*Xs)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(dsm + NB * (NB + 1));
+    const Prob p = pr[blockIdx.y];
+    const int n = p.n;
+    const int r0 = blockIdx.x * NB;
+    if (r0 >= n || fail[blockIdx.y]) return;
+    const int rows = min(NB, n - r0);
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+        int r = t / NB, c = t % NB;
+        Ls[r][c] = (r < rows && c <= r) ? p.L[(long long)(r0 + r) * n + r0 + c] : 0.0;
+        Xs[r][c] = (r == c && r < rows) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < rows; j++) {          // right-looking on all 64 columns at once
+        const double ljj = Ls[j][j];
+        for (int c = threadIdx.x; c < NB; c += blockDim.x) Xs[j][c] /= ljj;
+        __syncthreads();
+        for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+            int r = t / NB, c = t % NB;
+            if (r > j && r < rows) Xs[r][c] -= Ls[r][j] * Xs[j][c];
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+        int r = t / NB, c = t % NB;
+        if (r < rows) p.Ld[(long long)(r0 + r) * NB + c] = (c < rows) ? Xs[r][c] : 0.0;
     }
 }
 
@@ -453,14 +485,17 @@ __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, 
     bool alive = true;
     for (int k = 0; k + 2 < n && alive; k++) {
         const int b = k + 1, m = n - b;
-        // Householder vector from column k (computed redundantly by every CTA)
+        // Householder vector from row k (= column k, the matrix is kept in full
+        // symmetric storage), computed redundantly by every CTA of the group
+        const double* rowk = M + (long long)k * n + b;
         double part = 0.0;
-        for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) {
-            double x = __ldcg(M + (long long)(b + i) * n + k);
-            part = fma(x, x, part);
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            double x = __ldcg(rowk + i);
+            w[i] = x;
+            if (i >= 1) part = fma(x, x, part);
         }
         const double sigma = block_reduce_sum(part, sh);
-        const double x0 = __ldcg(M + (long long)b * n + k);
+        const double x0 = w[0];
         double tk = 0.0, beta = x0, scale = 0.0;
         if (sigma > 0.0) {
             double mu = sqrt(x0 * x0 + sigma);
@@ -468,8 +503,11 @@ __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, 
             tk = (beta - x0) / beta;
             scale = 1.0 / (x0 - beta);
         }
-        for (int i = threadIdx.x; i < m; i += blockDim.x)
-            v[i] = (i == 0) ? 1.0 : __ldcg(M + (long long)(b + i) * n + k) * scale;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const double vi = (i == 0) ? 1.0 : w[i] * scale;
+            v[i] = vi;
+            if (rank == 0) p.H[(long long)k * n + b + i] = vi;   // reflector k for the back-transformation
+        }
         __syncthreads();
         if (tk == 0.0) {
             if (rank == 0 && threadIdx.x == 0) { p.tau[k] = 0.0; p.e[k] = beta; }
@@ -493,12 +531,11 @@ __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, 
         const double K = 0.5 * tk * block_reduce_sum(kp, sh);
         for (int j = threadIdx.x; j < m; j += blockDim.x) w[j] -= K * v[j];
         __syncthreads();
-        // rank-2 update of the owned rows; keep v in column k
+        // rank-2 update of the owned rows
         for (int i = rank + warp * g; i < m; i += g * nwarps) {
             double* row = M + (long long)(b + i) * n + b;
             const double vi = v[i], wi = w[i];
             for (int j = lane; j < m; j += 32) row[j] -= vi * w[j] + wi * v[j];
-            if (lane == 0 && i >= 1) M[(long long)(b + i) * n + k] = vi;
         }
         if (rank == 0 && threadIdx.x == 0) { p.tau[k] = tk; p.e[k] = beta; }
         if (!group_barrier(bar, g, abort_flag)) { alive = false; break; }
@@ -623,8 +660,8 @@ __global__ void __launch_bounds__(256) k_dc_prepare(Prob* pr, const Merge* merge
 }
 
 // Secular equation 1 + rh sum_t zK_t^2 / (dK_t - lambda) = 0, one warp per
-// root; lambda_j = dK[org] + tau with tau found by bisection on the half
-// interval next to the nearer pole (differences stay exact).
+// root; lambda_j = dK[org] + tau with tau measured from the nearer pole, so
+// that the differences d_i - lambda_j stay accurate.
 __global__ void k_dc_roots(Prob* pr, const Merge* merges, int n_merges, int* fail) {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x % 32;
@@ -664,14 +701,69 @@ __global__ void k_dc_roots(Prob* pr, const Merge* merges, int n_merges, int* fai
         for (int o2 = 16; o2 > 0; o2 >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, o2);
         o = j; lo = 0.0; hi = rh * zz * (1.0 + 8.0 * DEPS) + 4.0 * DEPS * fabs(dK[j]);
     }
-    for (int it = 0; it < 200; it++) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid == lo || mid == hi) break;
-        if (f(o, mid) > 0.0) hi = mid; else lo = mid;
+    // Safeguarded rational iteration: psi (poles <= d_j) and phi (poles >=
+    // d_{j+1}) are each modelled by a constant plus one pole, matched in value
+    // and slope at the iterate; the model's root in (lo, hi) is the next
+    // iterate (bisection when it falls outside the bracket).
+    const double dO = dK[o];
+    const double dj = dK[j] - dO;
+    const bool has_up = (j < k - 1);
+    const double dj1 = has_up ? dK[j + 1] - dO : 0.0;
+    double t = 0.5 * (lo + hi);
+    for (int it = 0; it < 80; it++) {
+        double psi = 0.0, dpsi = 0.0, phi = 0.0, dphi = 0.0, ab = 0.0;
+        for (int q = lane; q < k; q += 32) {
+            const double del = (dK[q] - dO) - t;
+            const double z2 = zK[q] * zK[q];
+            const double tq = z2 / del;
+            const double dq = tq / del;
+            if (q <= j) { psi += tq; dpsi += dq; } else { phi += tq; dphi += dq; }
+            ab += fabs(tq);
+        }
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            psi += __shfl_xor_sync(0xffffffffu, psi, o2);
+            dpsi += __shfl_xor_sync(0xffffffffu, dpsi, o2);
+            phi += __shfl_xor_sync(0xffffffffu, phi, o2);
+            dphi += __shfl_xor_sync(0xffffffffu, dphi, o2);
+            ab += __shfl_xor_sync(0xffffffffu, ab, o2);
+        }
+        psi *= rh; dpsi *= rh; phi *= rh; dphi *= rh; ab *= rh;
+        const double fv = 1.0 + psi + phi;
+        if (fabs(fv) <= 8.0 * DEPS * (1.0 + ab)) break;
+        if (fv > 0.0) hi = t; else lo = t;
+        if (hi - lo <= 2.0 * DEPS * fmax(fabs(lo), fabs(hi))) break;
+        const double a1 = dj - t;
+        const double q1 = dpsi * a1 * a1;
+        const double p1 = psi - q1 / a1;
+        double tn;
+        if (!has_up) {
+            const double c = 1.0 + p1;
+            tn = (c != 0.0) ? dj + q1 / c : 0.5 * (lo + hi);
+        } else {
+            const double a2 = dj1 - t;
+            const double q2 = dphi * a2 * a2;
+            const double p2 = phi - q2 / a2;
+            const double c = 1.0 + p1 + p2;
+            // c (dj - x)(dj1 - x) + q1 (dj1 - x) + q2 (dj - x) = 0
+            const double B = -(c * (dj + dj1) + q1 + q2);
+            const double C = c * dj * dj1 + q1 * dj1 + q2 * dj;
+            tn = 0.5 * (lo + hi);
+            if (c == 0.0) {
+                if (B != 0.0) tn = -C / B;
+            } else {
+                const double sq = sqrt(fmax(B * B - 4.0 * c * C, 0.0));
+                const double r1 = (-B - copysign(sq, B)) / (2.0 * c);
+                const double r2 = (r1 != 0.0) ? C / (c * r1) : r1;
+                if (r1 > lo && r1 < hi) tn = r1;
+                else if (r2 > lo && r2 < hi) tn = r2;
+            }
+        }
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+        t = tn;
     }
     if (lane == 0) {
         p.org[a + j] = o;
-        p.tauR[a + j] = 0.5 * (lo + hi);
+        p.tauR[a + j] = t;
     }
 }
 
@@ -881,7 +973,7 @@ __global__ void __launch_bounds__(256) k_backtransform(Prob* pr, int* fail) {
         const double tk = p.tau[k];
         if (tk == 0.0) continue;
         const int b = k + 1, m = n - b;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = (i == 0) ? 1.0 : p.M[(long long)(b + i) * n + k];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = p.H[(long long)k * n + b + i];
         __syncthreads();
         double dot = 0.0;
         if (c < n)
@@ -938,7 +1030,7 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
         ns.push_back(h->dims[l]);
     }
     for (int n : ns) {
-        dtot += 6 * (size_t)n * n + 20 * (size_t)n;
+        dtot += 7 * (size_t)n * n + (size_t)n * NB + 20 * (size_t)n;
         itot += 12 * (size_t)n;
         es->nmax = std::max(es->nmax, n);
     }
@@ -964,6 +1056,8 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
             p.Qb = dp; dp += nn;
             p.R = dp; dp += nn;
             p.R2 = dp; dp += nn;
+            p.H = dp; dp += nn;
+            p.Ld = dp; dp += (size_t)n * NB;
             double** dv[] = {&p.d, &p.e, &p.tau, &p.D, &p.pbuf, &p.Ds, &p.zs, &p.dK, &p.zK, &p.tauR, &p.zh,
                              &p.rc, &p.rs, &p.val, &p.mrh};
             for (double** q : dv) { *q = dp; dp += n; }
@@ -1083,6 +1177,8 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
     }
     cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB + 1)));
+    cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(double) * 2 * NB * (NB + 1));
     return cudaGetLastError() == cudaSuccess ? KFAC_OK : KFAC_CUDA_ERROR;
 }
 
@@ -1131,6 +1227,8 @@ kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
         KFAC_LAUNCH_CHECK(h);
     }
     // 2. whitening
+    k_diag_inv<<<dim3(nblk, np), 256, 2 * NB * (NB + 1) * sizeof(double), s>>>(pr, es->fail);
+    KFAC_LAUNCH_CHECK(h);
     const int smem_trsm = (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB + 1));
     const int cbk = (nmax + CB - 1) / CB;
     k_trsm<<<dim3(cbk, np), 256, smem_trsm, s>>>(pr, 0, es->fail);

@@ -399,14 +399,29 @@ kfac_status_t fp64_extract_outputs(kfac_pinn_handle* h, cudaStream_t s, PassBuff
 kfac_status_t dgemm_strided(kfac_pinn_handle* h, cudaStream_t s, int P, int Q, int K,
                             const double* A, long long a_sp, long long a_sk,
                             const double* B, long long b_sk, long long b_sq,
-                            double* C, long long c_sp, long long c_sq, double alpha, double beta) {
+                            double* C, long long c_sp, long long c_sq, double alpha, double beta, bool fp32) {
     EpStore ep{C, c_sp, c_sq, alpha, beta, nullptr, 0, 0};
     cudaError_t e;
     bool akf = (a_sk == 1), bqf = (b_sq == 1);
-    if (akf && bqf) e = launch_dgemm(s, P, Q, K, 1, Strided<true>{A, a_sp, a_sk}, Strided<true>{B, b_sk, b_sq}, ep);
-    else if (akf) e = launch_dgemm(s, P, Q, K, 1, Strided<true>{A, a_sp, a_sk}, Strided<false>{B, b_sk, b_sq}, ep);
-    else if (bqf) e = launch_dgemm(s, P, Q, K, 1, Strided<false>{A, a_sp, a_sk}, Strided<true>{B, b_sk, b_sq}, ep);
-    else e = launch_dgemm(s, P, Q, K, 1, Strided<false>{A, a_sp, a_sk}, Strided<false>{B, b_sk, b_sq}, ep);
+    if (fp32) {
+        if (akf && bqf)
+            e = launch_dgemm<Strided<true>, Strided<true>, EpStore, float>(
+                s, P, Q, K, 1, Strided<true>{A, a_sp, a_sk}, Strided<true>{B, b_sk, b_sq}, ep);
+        else if (akf)
+            e = launch_dgemm<Strided<true>, Strided<false>, EpStore, float>(
+                s, P, Q, K, 1, Strided<true>{A, a_sp, a_sk}, Strided<false>{B, b_sk, b_sq}, ep);
+        else if (bqf)
+            e = launch_dgemm<Strided<false>, Strided<true>, EpStore, float>(
+                s, P, Q, K, 1, Strided<false>{A, a_sp, a_sk}, Strided<true>{B, b_sk, b_sq}, ep);
+        else
+            e = launch_dgemm<Strided<false>, Strided<false>, EpStore, float>(
+                s, P, Q, K, 1, Strided<false>{A, a_sp, a_sk}, Strided<false>{B, b_sk, b_sq}, ep);
+    } else {
+        if (akf && bqf) e = launch_dgemm(s, P, Q, K, 1, Strided<true>{A, a_sp, a_sk}, Strided<true>{B, b_sk, b_sq}, ep);
+        else if (akf) e = launch_dgemm(s, P, Q, K, 1, Strided<true>{A, a_sp, a_sk}, Strided<false>{B, b_sk, b_sq}, ep);
+        else if (bqf) e = launch_dgemm(s, P, Q, K, 1, Strided<false>{A, a_sp, a_sk}, Strided<true>{B, b_sk, b_sq}, ep);
+        else e = launch_dgemm(s, P, Q, K, 1, Strided<false>{A, a_sp, a_sk}, Strided<false>{B, b_sk, b_sq}, ep);
+    }
     h->launches++;
     return e == cudaSuccess ? KFAC_OK : KFAC_CUDA_ERROR;
 }

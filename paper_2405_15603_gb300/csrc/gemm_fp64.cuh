@@ -104,21 +104,23 @@ struct EpStore {
     }
 };
 
-template <class LA, class LB, class EP>
+// Acc is the arithmetic type of the tile (double, or float where the caller
+// accepts FP32 products); operands are read as double and converted.
+template <class Acc, class LA, class LB, class EP>
 __global__ void __launch_bounds__(GTHREADS)
 dgemm_tile_kernel(int P, int Q, int K, int kchunk, LA la, LB lb, EP ep) {
-    __shared__ double As[GK][GT + 1];
-    __shared__ double Bs[GK][GT + 1];
+    __shared__ Acc As[GK][GT + 1];
+    __shared__ Acc Bs[GK][GT + 1];
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
     const int p0 = blockIdx.y * GT, q0 = blockIdx.x * GT;
     const int kbeg = blockIdx.z * kchunk;
     const int kend = min(K, kbeg + kchunk);
-    double acc[4][4];
+    Acc acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+        for (int j = 0; j < 4; j++) acc[i][j] = Acc(0);
 
     for (int k0 = kbeg; k0 < kend; k0 += GK) {
 #pragma unroll
@@ -127,7 +129,7 @@ dgemm_tile_kernel(int P, int Q, int K, int kchunk, LA la, LB lb, EP ep) {
             int pp, kk;
             if (LA::kfast) { kk = e % GK; pp = e / GK; } else { pp = e % GT; kk = e / GT; }
             int p = p0 + pp, k = k0 + kk;
-            As[kk][pp] = (p < P && k < kend) ? la(p, k) : 0.0;
+            As[kk][pp] = (p < P && k < kend) ? Acc(la(p, k)) : Acc(0);
         }
 #pragma unroll
         for (int i = 0; i < (GT * GK) / GTHREADS; i++) {
@@ -135,12 +137,12 @@ dgemm_tile_kernel(int P, int Q, int K, int kchunk, LA la, LB lb, EP ep) {
             int qq, kk;
             if (LB::qfast) { qq = e % GT; kk = e / GT; } else { kk = e % GK; qq = e / GK; }
             int q = q0 + qq, k = k0 + kk;
-            Bs[kk][qq] = (q < Q && k < kend) ? lb(k, q) : 0.0;
+            Bs[kk][qq] = (q < Q && k < kend) ? Acc(lb(k, q)) : Acc(0);
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GK; kk++) {
-            double a[4], b[4];
+            Acc a[4], b[4];
 #pragma unroll
             for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -157,12 +159,12 @@ dgemm_tile_kernel(int P, int Q, int K, int kchunk, LA la, LB lb, EP ep) {
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             int p = p0 + ty + 16 * i, q = q0 + tx + 16 * j;
-            if (p < P && q < Q) ep(p, q, blockIdx.z, acc[i][j]);
+            if (p < P && q < Q) ep(p, q, blockIdx.z, (double)acc[i][j]);
         }
 }
 
 // Launch with an explicit number of k splits (>= 1).
-template <class LA, class LB, class EP>
+template <class LA, class LB, class EP, class Acc = double>
 inline cudaError_t launch_dgemm(cudaStream_t s, int P, int Q, int K, int splits, LA la, LB lb, EP ep) {
     if (P <= 0 || Q <= 0) return cudaSuccess;
     if (splits < 1) splits = 1;
@@ -172,7 +174,7 @@ inline cudaError_t launch_dgemm(cudaStream_t s, int P, int Q, int K, int splits,
     splits = (K + kchunk - 1) / kchunk;
     if (splits < 1) splits = 1;
     dim3 grid(ceil_div_u(Q, GT), ceil_div_u(P, GT), splits);
-    dgemm_tile_kernel<<<grid, GTHREADS, 0, s>>>(P, Q, K, kchunk, la, lb, ep);
+    dgemm_tile_kernel<Acc><<<grid, GTHREADS, 0, s>>>(P, Q, K, kchunk, la, lb, ep);
     return cudaGetLastError();
 }
 

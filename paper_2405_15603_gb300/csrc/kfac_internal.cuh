@@ -145,8 +145,9 @@ kfac_status_t linalg_update(kfac_pinn_handle* h, cudaStream_t s, double* theta);
 // C(p, q) = sum_k A(p, k) B(k, q) with strided operands:
 //   A(p, k) = A[p * a_sp + k * a_sk],  B(k, q) = B[k * b_sk + q * b_sq]
 // and C(p, q) written to C[p * c_sp + q * c_sq] as alpha * acc (+ beta * C if
-// beta != 0).  Strides are in elements.
+// beta != 0).  Strides are in elements.  fp32: products and sums in FP32.
 kfac_status_t dgemm_strided(kfac_pinn_handle* h, cudaStream_t s, int P, int Q, int K,
                             const double* A, long long a_sp, long long a_sk,
                             const double* B, long long b_sk, long long b_sq,
-                            double* C, long long c_sp, long long c_sq, double alpha, double beta);
+                            double* C, long long c_sp, long long c_sq, double alpha, double beta,
+                            bool fp32 = false);

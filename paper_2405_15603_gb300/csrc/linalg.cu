@@ -27,6 +27,9 @@ __global__ void k_update(double* theta, const double* dir, double* delta_prev, l
 }
 
 kfac_status_t precondition_impl(kfac_pinn_handle* h, cudaStream_t s, const double* grad, double* dir) {
+    // The mixed-precision path applies the (FP64) inverse with FP32 products:
+    // its gradient already carries BF16-level errors.
+    const bool f32 = (h->cfg.precision == KFAC_MIXED_BF16);
     for (int l = 1; l <= h->cfg.L; l++) {
         const int na = h->dims[l - 1] + 1, nb = h->dims[l];
         const double* G = grad + h->woff[l - 1];
@@ -36,18 +39,18 @@ kfac_status_t precondition_impl(kfac_pinn_handle* h, cudaStream_t s, const doubl
         const double* VB = h->VB[l - 1];
         kfac_status_t st;
         // X1 = V_B^T G      (nb x na, row-major)
-        st = dgemm_strided(h, s, nb, na, nb, VB, 1, nb, G, 1, nb, X1, na, 1, 1.0, 0.0);
+        st = dgemm_strided(h, s, nb, na, nb, VB, 1, nb, G, 1, nb, X1, na, 1, 1.0, 0.0, f32);
         if (st) return st;
         // Y = X1 V_A, then the element-wise division by 1 + b a^T
-        st = dgemm_strided(h, s, nb, na, na, X1, na, 1, VA, na, 1, Y, na, 1, 1.0, 0.0);
+        st = dgemm_strided(h, s, nb, na, na, X1, na, 1, VA, na, 1, Y, na, 1, 1.0, 0.0, f32);
         if (st) return st;
         k_div_kron<<<ceil_div_u((long long)nb * na, 256), 256, 0, s>>>(Y, nb, na, h->wb[l - 1], h->wa[l - 1]);
         KFAC_LAUNCH_CHECK(h);
         // X1 = V_B Y
-        st = dgemm_strided(h, s, nb, na, nb, VB, nb, 1, Y, na, 1, X1, na, 1, 1.0, 0.0);
+        st = dgemm_strided(h, s, nb, na, nb, VB, nb, 1, Y, na, 1, X1, na, 1, 1.0, 0.0, f32);
         if (st) return st;
         // Delta = -X1 V_A^T, stored column-stacked like theta
-        st = dgemm_strided(h, s, nb, na, na, X1, na, 1, VA, 1, na, dir + h->woff[l - 1], 1, nb, -1.0, 0.0);
+        st = dgemm_strided(h, s, nb, na, na, X1, na, 1, VA, 1, na, dir + h->woff[l - 1], 1, nb, -1.0, 0.0, f32);
         if (st) return st;
     }
     return KFAC_OK;

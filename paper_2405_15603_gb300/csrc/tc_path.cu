@@ -135,34 +135,35 @@ __global__ void k_layer1(const double* __restrict__ W, const double* __restrict_
     if (idx >= (long long)N_pad * hp) return;
     int n = (int)(idx / hp), j = (int)(idx % hp);
     bool live = (n < N) && (j < h);
-    double a0 = 0.0, ssq = 0.0;
+    // FP32 arithmetic: the outputs are split-BF16 (about 16 bits) at most
+    float a0 = 0.f, ssq = 0.f;
     if (live) {
-        a0 = W[j + (long long)h * d];
-        for (int k = 0; k < d; k++) a0 = fma(W[j + (long long)h * k], X[(long long)n * d + k], a0);
+        a0 = (float)W[j + (long long)h * d];
+        for (int k = 0; k < d; k++) a0 = fmaf((float)W[j + (long long)h * k], (float)X[(long long)n * d + k], a0);
     }
-    double y0 = live ? tanh(a0) : 0.0;
-    double s1 = 1.0 - y0 * y0, s2 = -2.0 * y0 * s1;
+    float y0 = live ? tanhf(a0) : 0.f;
+    float s1 = 1.f - y0 * y0, s2 = -2.f * y0 * s1;
     const long long blk = (long long)N_pad * hp;
-    bf16 hi = __double2bfloat16(y0);
+    bf16 hi = __float2bfloat16_rn(y0);
     T_hi[idx] = hi;
-    T_lo[idx] = __double2bfloat16(y0 - (double)__bfloat162float(hi));
+    T_lo[idx] = __float2bfloat16_rn(y0 - __bfloat162float(hi));
     if (S > 1) {
         for (int i = 0; i < d; i++) {
-            double w = live ? W[j + (long long)h * i] : 0.0;
-            bf16 th = __double2bfloat16(s1 * w);
+            float w = live ? (float)W[j + (long long)h * i] : 0.f;
+            bf16 th = __float2bfloat16_rn(s1 * w);
             T_hi[(1 + i) * blk + idx] = th;
             if (i == 0 && lap_first == 2)   // heat: time tangent keeps its low half (block 2)
-                T_lo[2 * blk + idx] = __double2bfloat16(s1 * w - (double)__bfloat162float(th));
-            if (1 + i >= lap_first) ssq = fma(w, w, ssq);
+                T_lo[2 * blk + idx] = __float2bfloat16_rn(s1 * w - __bfloat162float(th));
+            if (1 + i >= lap_first) ssq = fmaf(w, w, ssq);
         }
-        double yD = live ? s2 * ssq : 0.0;
-        bf16 dh = __double2bfloat16(yD);
+        float yD = live ? s2 * ssq : 0.f;
+        bf16 dh = __float2bfloat16_rn(yD);
         T_hi[(S - 1) * blk + idx] = dh;
-        T_lo[blk + idx] = __double2bfloat16(yD - (double)__bfloat162float(dh));
+        T_lo[blk + idx] = __float2bfloat16_rn(yD - __bfloat162float(dh));
     }
-    A0[idx] = (float)a0;
+    A0[idx] = a0;
     AD[idx] = 0.f;
-    SSQ[idx] = (float)ssq;
+    SSQ[idx] = ssq;
 }
 
 // Laplacian row of a hidden layer once all tangent chunks are done:
@@ -292,18 +293,34 @@ __global__ void k_last_bwd(const float* __restrict__ wL, const bf16* __restrict_
     Gr[(S - 1) * blk + idx] = __float2bfloat16_rn(rn * aDb);
 }
 
+// Column reductions run as 32 x 32 thread blocks: lane = column, warp = row
+// group (rows strided by 32), then a deterministic sum over the 32 groups.
+constexpr int RED_THREADS = 1024;
+__device__ double reduce_row_groups(double v, double (*sh)[33]) {
+    const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
+    sh[rg][cl] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (rg == 0)
+        for (int g = 0; g < 32; g++) s += sh[g][cl];
+    return s;   // valid in row group 0
+}
+
 // FP64 column sums of rows [row0, row0+nrows) of a BF16 matrix (+ optional lo block).
-__global__ void k_colsum(const bf16* __restrict__ X, const bf16* __restrict__ Xlo, int hp, long long row0, int nrows,
-                         int ncols, double* out) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= ncols) return;
+__global__ void __launch_bounds__(RED_THREADS) k_colsum(const bf16* __restrict__ X, const bf16* __restrict__ Xlo,
+                                                        int hp, long long row0, int nrows, int ncols, double* out) {
+    __shared__ double sh[32][33];
+    const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
+    const int q = blockIdx.x * 32 + cl;
     double acc = 0.0;
-    for (int n = 0; n < nrows; n++) {
-        double v = (double)__bfloat162float(X[(row0 + n) * hp + q]);
-        if (Xlo) v += (double)__bfloat162float(Xlo[(long long)n * hp + q]);
-        acc += v;
-    }
-    out[q] = acc;
+    if (q < ncols)
+        for (int n = rg; n < nrows; n += 32) {
+            double v = (double)__bfloat162float(X[(row0 + n) * hp + q]);
+            if (Xlo) v += (double)__bfloat162float(Xlo[(long long)n * hp + q]);
+            acc += v;
+        }
+    double s = reduce_row_groups(acc, sh);
+    if (rg == 0 && q < ncols) out[q] = s;
 }
 
 // KFAC-reduce per-point sums over the S Taylor columns: out = scale * sum_s X_s.
@@ -365,19 +382,24 @@ __global__ void k_grad_reduce(const float* __restrict__ pi, int zi, const float*
 
 // First-layer input factor in closed form (Sec. 3.1: T^(0) has columns
 // (x, e_1..e_d, 0) and bias row (1, 0, .., 0)).
-__global__ void k_factor_A1(const double* __restrict__ X, int N, int d, int S, int reduce, int boundary, double* fac,
-                            double beta, int* status) {
-    int n1 = d + 1;
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n1 * n1) return;
-    int p = idx / n1, q = idx % n1;
+__global__ void __launch_bounds__(RED_THREADS) k_factor_A1(const double* __restrict__ X, int N, int d, int S,
+                                                           int reduce, int boundary, double* fac, double beta,
+                                                           int* status) {
+    __shared__ double shm[32][33];
+    const int n1 = d + 1;
+    const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
+    const int p = blockIdx.y, q = blockIdx.x * 32 + cl;
     double acc = 0.0;
-    double sh = (reduce && !boundary) ? 1.0 : 0.0;   // reduce: abar = (x + 1, 1) / S
-    for (int n = 0; n < N; n++) {
-        double xp = (p < d) ? X[(long long)n * d + p] + sh : 1.0;
-        double xq = (q < d) ? X[(long long)n * d + q] + sh : 1.0;
-        acc += xp * xq;
-    }
+    const double sh = (reduce && !boundary) ? 1.0 : 0.0;   // reduce: abar = (x + 1, 1) / S
+    if (q < n1)
+        for (int n = rg; n < N; n += 32) {
+            double xp = (p < d) ? X[(long long)n * d + p] + sh : 1.0;
+            double xq = (q < d) ? X[(long long)n * d + q] + sh : 1.0;
+            acc += xp * xq;
+        }
+    acc = reduce_row_groups(acc, shm);
+    if (rg != 0 || q >= n1) return;
+    const int idx = p * n1 + q;
     double v;
     if (boundary) v = acc / N;
     else if (reduce) v = acc / ((double)N * S * S);
@@ -389,24 +411,29 @@ __global__ void k_factor_A1(const double* __restrict__ X, int N, int d, int S, i
 
 // Weight gradient of the first layer:
 //   (1/N) sum_n [ (r g)_{n,0} (x_n, 1)^T + sum_i (r g)_{n,i} (e_i, 0)^T ] + boundary term.
-__global__ void k_grad_layer1(const bf16* __restrict__ Gr, const bf16* __restrict__ Grb, const double* __restrict__ X,
-                              const double* __restrict__ Xb, int N, int N_pad, int Nb, int d, int h, int hp, int S,
-                              double* grad) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)h * (d + 1)) return;
-    int k = (int)(idx / h), j = (int)(idx % h);
+__global__ void __launch_bounds__(RED_THREADS) k_grad_layer1(const bf16* __restrict__ Gr, const bf16* __restrict__ Grb,
+                                                             const double* __restrict__ X,
+                                                             const double* __restrict__ Xb, int N, int N_pad, int Nb,
+                                                             int d, int h, int hp, int S, double* grad) {
+    __shared__ double shm[32][33];
+    const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
+    const int k = blockIdx.y, j = blockIdx.x * 32 + cl;
     const long long blk = (long long)N_pad * hp;
     double a = 0.0, b = 0.0;
-    for (int n = 0; n < N; n++) {
-        double g0 = (double)__bfloat162float(Gr[(long long)n * hp + j]);
-        if (k < d) a += g0 * X[(long long)n * d + k] + (double)__bfloat162float(Gr[(1 + k) * blk + (long long)n * hp + j]);
-        else a += g0;
+    if (j < h) {
+        for (int n = rg; n < N; n += 32) {
+            double g0 = (double)__bfloat162float(Gr[(long long)n * hp + j]);
+            if (k < d) a += g0 * X[(long long)n * d + k] + (double)__bfloat162float(Gr[(1 + k) * blk + (long long)n * hp + j]);
+            else a += g0;
+        }
+        for (int n = rg; n < Nb; n += 32) {
+            double g0 = (double)__bfloat162float(Grb[(long long)n * hp + j]);
+            b += (k < d) ? g0 * Xb[(long long)n * d + k] : g0;
+        }
     }
-    for (int n = 0; n < Nb; n++) {
-        double g0 = (double)__bfloat162float(Grb[(long long)n * hp + j]);
-        b += (k < d) ? g0 * Xb[(long long)n * d + k] : g0;
-    }
-    grad[j + (long long)h * k] = a / N + b / Nb;
+    const double v = a / N + b / Nb;
+    const double s = reduce_row_groups(v, shm);
+    if (rg == 0 && j < h) grad[j + (long long)h * k] = s;
 }
 
 // Last layer: gradient (1/N) sum_{n,s} r_n c_s T^_{n,s} + boundary, and the
@@ -416,13 +443,14 @@ __global__ void k_last_layer_terms(const bf16* __restrict__ T_hi, const bf16* __
                                    const double* __restrict__ r, const double* __restrict__ rb, int N, int N_pad,
                                    int Nb, int Nb_pad, int h, int hp, int S, int heat, double kappa, int reduce,
                                    double* grad, double* B_int, double* B_bdy, double beta, int* status) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q > h) return;
+    __shared__ double shm[32][33];
+    const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
+    const int q = blockIdx.x * 32 + cl;
     const double cD = heat ? -kappa : -1.0, cT = heat ? 1.0 : 0.0;
     const long long blk = (long long)N_pad * hp;
     double a = 0.0, b = 0.0;
     if (q < h) {
-        for (int n = 0; n < N; n++) {
+        for (int n = rg; n < N; n += 32) {
             double tD = (double)__bfloat162float(T_hi[(S - 1) * blk + (long long)n * hp + q]) +
                         (double)__bfloat162float(T_lo[blk + (long long)n * hp + q]);
             double v = cD * tD;
@@ -431,15 +459,17 @@ __global__ void k_last_layer_terms(const bf16* __restrict__ T_hi, const bf16* __
                            (double)__bfloat162float(T_lo[2 * blk + (long long)n * hp + q]));
             a += r[n] * v;
         }
-        for (int n = 0; n < Nb; n++) {
+        for (int n = rg; n < Nb; n += 32) {
             double t0 = (double)__bfloat162float(Tb_hi[(long long)n * hp + q]) +
                         (double)__bfloat162float(Tb_lo[(long long)n * hp + q]);
             b += rb[n] * t0;
         }
-    } else {
-        for (int n = 0; n < Nb; n++) b += rb[n];   // bias: c_0 = 0 in the interior
+    } else if (q == h) {
+        for (int n = rg; n < Nb; n += 32) b += rb[n];   // bias: c_0 = 0 in the interior
     }
-    grad[q] = a / N + b / Nb;
+    const double s = reduce_row_groups(a / N + b / Nb, shm);
+    if (rg != 0 || q > h) return;
+    grad[q] = s;
     if (q == 0) {
         double e = reduce ? (cD + cT) * (cD + cT) : cD * cD + cT * cT;
         double o1 = beta * B_int[0] + (1.0 - beta) * e;
@@ -724,14 +754,14 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
     // ---- layer 1: closed-form A, gradient from the adjoints ---------------
     {
         int n1 = d + 1;
-        k_factor_A1<<<ceil_div_u(n1 * n1, EW), EW, 0, s>>>(X, N, d, S, reduce, 0, h->fac[KFAC_A_INT][0], beta,
+        k_factor_A1<<<dim3(ceil_div_u(n1, 32), n1), RED_THREADS, 0, s>>>(X, N, d, S, reduce, 0, h->fac[KFAC_A_INT][0], beta,
                                                             h->status);
         KFAC_LAUNCH_CHECK(h);
-        k_factor_A1<<<ceil_div_u(n1 * n1, EW), EW, 0, s>>>(Xb, Nb, d, 1, 0, 1, h->fac[KFAC_A_BDY][0], beta,
+        k_factor_A1<<<dim3(ceil_div_u(n1, 32), n1), RED_THREADS, 0, s>>>(Xb, Nb, d, 1, 0, 1, h->fac[KFAC_A_BDY][0], beta,
                                                             h->status);
         KFAC_LAUNCH_CHECK(h);
         MxLayer& l1 = I.lay[0];
-        k_grad_layer1<<<ceil_div_u((long long)l1.h * (d + 1), EW), EW, 0, s>>>(
+        k_grad_layer1<<<dim3(ceil_div_u(l1.h, 32), d + 1), RED_THREADS, 0, s>>>(
             l1.Gr, B.lay[0].Gr, X, Xb, N, I.N_pad, Nb, d, l1.h, l1.hp, S, h->grad + h->woff[0]);
         KFAC_LAUNCH_CHECK(h);
     }
@@ -768,14 +798,14 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
             k_sum_over_s<<<ceil_div_u(cnt, EW), EW, 0, s>>>(ti.T_hi, I.N_pad, S, ti.hp, 1.f / S, I.red_a);
             KFAC_LAUNCH_CHECK(h);
             if ((st = gram(h, s, I.gRa[l - 2], I.gRa[l - 2], hin, hin, I.N_pad, 1, part_i, zi))) return st;
-            k_colsum<<<ceil_div_u(hin, EW), EW, 0, s>>>(I.red_a, nullptr, ti.hp, 0, N, hin, cs_i);
+            k_colsum<<<ceil_div_u(hin, 32), RED_THREADS, 0, s>>>(I.red_a, nullptr, ti.hp, 0, N, hin, cs_i);
             KFAC_LAUNCH_CHECK(h);
             k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_i, zi, hin, 1, cs_i, 1.0 / N, 1.0 / ((double)N * S),
                                                              1.0 / ((double)S * S), 1, h->fac[KFAC_A_INT][l - 1], beta,
                                                              h->status);
         } else {
             if ((st = gram(h, s, ti.gT, ti.gT, hin, hin, I.rows, 1, part_i, zi))) return st;
-            k_colsum<<<ceil_div_u(hin, EW), EW, 0, s>>>(ti.T_hi, ti.T_lo, ti.hp, 0, N, hin, cs_i);
+            k_colsum<<<ceil_div_u(hin, 32), RED_THREADS, 0, s>>>(ti.T_hi, ti.T_lo, ti.hp, 0, N, hin, cs_i);
             KFAC_LAUNCH_CHECK(h);
             double sc = 1.0 / ((double)N * S);
             k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_i, zi, hin, 1, cs_i, sc, sc, 1.0 / S, 1,
@@ -784,7 +814,7 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
         KFAC_LAUNCH_CHECK(h);
         // boundary A_l
         if ((st = gram(h, s, tb.gT, tb.gT, hin, hin, B.rows, 1, part_b, zb))) return st;
-        k_colsum<<<ceil_div_u(hin, EW), EW, 0, s>>>(tb.T_hi, tb.T_lo, tb.hp, 0, Nb, hin, cs_b);
+        k_colsum<<<ceil_div_u(hin, 32), RED_THREADS, 0, s>>>(tb.T_hi, tb.T_lo, tb.hp, 0, Nb, hin, cs_b);
         KFAC_LAUNCH_CHECK(h);
         k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_b, zb, hin, 1, cs_b, 1.0 / Nb, 1.0 / Nb, 1.0, 1,
                                                          h->fac[KFAC_A_BDY][l - 1], beta, h->status);
@@ -796,15 +826,15 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
             const int hout = gi.h;
             if ((st = gram(h, s, gi.gGr, ti.gT, hout, hin, I.rows, 0, part_i, zi))) return st;
             if ((st = gram(h, s, gb.gGr, tb.gT, hout, hin, B.rows, 0, part_b, zb))) return st;
-            k_colsum<<<ceil_div_u(hout, EW), EW, 0, s>>>(gi.Gr, nullptr, gi.hp, 0, N, hout, cs_i);
+            k_colsum<<<ceil_div_u(hout, 32), RED_THREADS, 0, s>>>(gi.Gr, nullptr, gi.hp, 0, N, hout, cs_i);
             KFAC_LAUNCH_CHECK(h);
-            k_colsum<<<ceil_div_u(hout, EW), EW, 0, s>>>(gb.Gr, nullptr, gb.hp, 0, Nb, hout, cs_b);
+            k_colsum<<<ceil_div_u(hout, 32), RED_THREADS, 0, s>>>(gb.Gr, nullptr, gb.hp, 0, Nb, hout, cs_b);
             KFAC_LAUNCH_CHECK(h);
             k_grad_reduce<<<ceil_div_u((long long)hout * (hin + 1), EW), EW, 0, s>>>(
                 part_i, zi, part_b, zb, hout, hin, cs_i, cs_b, 1.0 / N, 1.0 / Nb, h->grad + h->woff[l - 1]);
             KFAC_LAUNCH_CHECK(h);
         } else {
-            k_last_layer_terms<<<ceil_div_u(hin + 1, EW), EW, 0, s>>>(
+            k_last_layer_terms<<<ceil_div_u(hin + 1, 32), RED_THREADS, 0, s>>>(
                 ti.T_hi, ti.T_lo, tb.T_hi, tb.T_lo, h->in.r, h->bd.r, N, I.N_pad, Nb, B.N_pad, hin, ti.hp, S,
                 h->cfg.op == KFAC_OP_HEAT, h->cfg.kappa, reduce, h->grad + h->woff[L - 1], h->fac[KFAC_B_INT][L - 1],
                 h->fac[KFAC_B_BDY][L - 1], beta, h->status);
