@@ -221,6 +221,31 @@ kfac_status_t kfac_pinn_timing_enable(kfac_handle_t h, int enable);
 kfac_status_t kfac_pinn_timing_read(kfac_handle_t h, int kernel_class, double* total_ms,
                                     int64_t* launches, double* work);
 
+/* Allocation-free forward Laplacian.  The paper has no counterpart: this is
+ * a service for callers that cannot allocate device memory while they run
+ * (code inside another runtime's memory pool or fixed device-memory budget,
+ * or a process that must not grow after start-up).  It computes the same u,
+ * grad and lap as kfac_pinn_forward_laplacian on an FP64 handle built from
+ * cfg (cfg->precision is ignored; FP64 throughout), without a handle and
+ * without allocating anything: the per-layer Taylor matrices live in one
+ * static 32 MiB scratch array in device memory that every GPU loading this
+ * library holds until the process exits.
+ *   - Inputs and outputs are caller-owned device pointers as in
+ *     kfac_pinn_forward_laplacian; N >= 1.
+ *   - Capacity: sum over layers l of (2 if l < L else 1) * (d+2) * N * h_l
+ *     doubles must not exceed 4,194,304 (32 MiB); larger requests return
+ *     KFAC_BAD_ARG and queue nothing.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - Every call shares the scratch array: calls that overlap on the GPU
+ *     (other streams or host threads) race and must be serialised by the
+ *     caller.  Nothing needs clearing between calls: every scratch element a
+ *     call reads is first written by the same call. */
+kfac_status_t kfac_pinn_forward_laplacian_noalloc(const kfac_config_t* cfg, void* stream, const double* theta,
+                                                  const double* X, int N,
+                                                  double* u, double* grad, double* lap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,7 @@ EXPORTS = [
     "kfac_pinn_precondition", "kfac_pinn_update", "kfac_pinn_step", "kfac_pinn_step_host",
     "kfac_pinn_get_factor", "kfac_pinn_set_factor", "kfac_pinn_get_gradient",
     "kfac_pinn_get_direction", "kfac_pinn_sync_status", "kfac_pinn_launch_count",
-    "kfac_pinn_timing_enable", "kfac_pinn_timing_read",
+    "kfac_pinn_timing_enable", "kfac_pinn_timing_read", "kfac_pinn_forward_laplacian_noalloc",
 ]
 
 KERNEL_CLASSES = {0: "layer_gemm", 1: "adjoint_gemm", 2: "gram", 3: "elementwise", 4: "eig", 5: "precond"}
@@ -76,6 +76,7 @@ def load() -> C.CDLL:
         "kfac_pinn_sync_status": (st, [H, C.POINTER(C.c_int)]),
         "kfac_pinn_launch_count": (C.c_int64, [H]),
         "kfac_pinn_timing_enable": (st, [H, I]),
+        "kfac_pinn_forward_laplacian_noalloc": (st, [C.POINTER(KfacConfig), P, P, P, I, P, P, P]),
         "kfac_pinn_timing_read": (st, [H, I, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                        C.POINTER(C.c_double)]),
     }

@@ -1,0 +1,98 @@
+// Allocation-free forward Laplacian (FP64).
+//
+// Some callers cannot allocate device memory while they run: code executing
+// inside a memory pool or a fixed device-memory budget that another runtime
+// owns, or a process that must not grow its footprint after start-up.  For
+// them kfac_pinn_forward_laplacian_noalloc computes the same u, grad u and
+// Laplacian as kfac_pinn_forward_laplacian on an FP64 handle, without a
+// handle and without any allocation: the per-layer Taylor matrices live in
+// one fixed scratch array in device memory, compiled into this library.
+//
+// The scratch array is file-scope (`static __device__`), so every GPU that
+// loads the library holds it for the life of the process, and every call
+// shares it: calls that overlap on the GPU (different streams, or different
+// host threads) race on it and must be serialised by the caller.  Each call
+// writes every scratch element it reads before reading it, so nothing has to
+// be cleared between calls.
+#include <string.h>
+
+#include "kfac_internal.cuh"
+
+namespace {
+
+// 32 MiB of FP64 scratch: room for the Z and T matrices of all layers,
+// sum over layers of 2 * (d + 2) * N * h_l doubles.
+constexpr size_t NOALLOC_SCRATCH_DOUBLES = (size_t)4 << 20;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
+
+constexpr int MAX_DEVICES = 64;
+double* g_scratch_addr[MAX_DEVICES] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side symbol is only a stand-in, not a device address).
+kfac_status_t scratch_address(double** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return KFAC_CUDA_ERROR;
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return KFAC_CUDA_ERROR;
+        g_scratch_addr[dev] = (double*)p;
+    }
+    *out = g_scratch_addr[dev];
+    return KFAC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kfac_status_t kfac_pinn_forward_laplacian_noalloc(const kfac_config_t* cfg, void* stream, const double* theta,
+                                                  const double* X, int N, double* u, double* grad, double* lap) {
+    if (!cfg || !theta || !X || !u || N < 1) return KFAC_BAD_ARG;
+    if (cfg->d < 1 || cfg->L < 1 || cfg->L > KFAC_MAX_LAYERS) return KFAC_BAD_ARG;
+    if (cfg->op != KFAC_OP_LAPLACE && cfg->op != KFAC_OP_HEAT) return KFAC_BAD_ARG;
+    if (cfg->op == KFAC_OP_HEAT && cfg->d < 2) return KFAC_BAD_ARG;
+    for (int l = 0; l < cfg->L; l++)
+        if (cfg->widths[l] < 1) return KFAC_BAD_ARG;
+    if (cfg->widths[cfg->L - 1] != 1) return KFAC_BAD_ARG;
+
+    // A handle on the host stack describes the network for the FP64 kernels;
+    // its buffers point into the static scratch array.
+    kfac_pinn_handle h;
+    memset(&h, 0, sizeof(h));
+    h.cfg = *cfg;
+    h.cfg.precision = KFAC_FP64;
+    h.dims[0] = cfg->d;
+    for (int l = 0; l < cfg->L; l++) h.dims[l + 1] = cfg->widths[l];
+    h.woff[0] = 0;
+    for (int l = 1; l <= cfg->L; l++) h.woff[l] = h.woff[l - 1] + (int64_t)h.dims[l] * (h.dims[l - 1] + 1);
+    h.D = h.woff[cfg->L];
+    h.S = cfg->d + 2;
+
+    size_t need = 0;
+    for (int l = 1; l <= cfg->L; l++) need += (size_t)(l < cfg->L ? 2 : 1) * h.S * (size_t)N * h.dims[l];
+    if (need > NOALLOC_SCRATCH_DOUBLES) return KFAC_BAD_ARG;   // beyond the fixed scratch capacity
+
+    double* base = nullptr;
+    kfac_status_t st = scratch_address(&base);
+    if (st != KFAC_OK) return st;
+    PassBuffers pb;
+    memset(&pb, 0, sizeof(pb));
+    pb.N = N;
+    pb.S = h.S;
+    double* cur = base;
+    for (int l = 1; l <= cfg->L; l++) {
+        const size_t e = (size_t)h.S * N * h.dims[l];
+        pb.Z[l - 1] = cur;
+        cur += e;
+        if (l < cfg->L) {
+            pb.T[l - 1] = cur;
+            cur += e;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = fp64_forward(&h, s, theta, X, N, pb, h.S))) return st;
+    return fp64_extract_outputs(&h, s, pb, N, h.S, u, grad, lap);
+}
+
+}  // extern "C"
