@@ -16,6 +16,7 @@ the value is the total steps/s of all ranks over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -352,7 +353,14 @@ def main():
     ap.add_argument("--precision", default="mixed_bf16", choices=["fp64", "mixed_bf16"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--points", default=None,
+                    help="N_INT,N_BDY override (smaller cases for profiler captures; not the headline)")
     args = ap.parse_args()
+    if args.points:
+        global WORKLOAD, WORKLOAD_NAME
+        ni, nb = (int(v) for v in args.points.split(","))
+        WORKLOAD = dataclasses.replace(WORKLOAD, n_int=ni, n_bdy=nb)
+        WORKLOAD_NAME = f"poisson100d_100-768-768-512-512-1_{ni}int_{nb}bdy_resampled"
     if args.steps is None:
         args.steps = 5 if args.precision == "fp64" else 30
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
