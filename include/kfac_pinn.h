@@ -90,6 +90,10 @@ typedef struct {
     double momentum;               /* momentum mu on the previous update               */
     int max_n_int;                 /* capacity: interior points per call (>= 1)        */
     int max_n_bdy;                 /* capacity: boundary points per call (>= 1)        */
+    int line_search;               /* 0: theta += lr * dhat; 1: kfac_pinn_step picks
+                                      alpha = argmin over {2^0, 2^-1, .., 2^-30} of the
+                                      loss L(theta + alpha * dhat) on the step's batch
+                                      (Sec. 3.4), lr is then unused                    */
 } kfac_config_t;
 
 typedef struct kfac_pinn_handle* kfac_handle_t;
@@ -156,9 +160,13 @@ kfac_status_t kfac_pinn_precondition(kfac_handle_t h, void* stream, const double
 kfac_status_t kfac_pinn_update(kfac_handle_t h, void* stream, double* theta);
 
 /* One whole KFAC step: kfac_pinn_factors, kfac_pinn_invert,
- * kfac_pinn_precondition and kfac_pinn_update, in that order.  theta is
- * updated in place; loss (3 device doubles, may be NULL) is the loss at the
- * incoming theta. */
+ * kfac_pinn_precondition and the update, in that order.  theta is updated in
+ * place; loss (3 device doubles, may be NULL) is the loss at the incoming
+ * theta.  With cfg.line_search the update is theta += alpha* dhat with
+ * dhat = momentum * delta_prev + Delta and alpha* the grid point of least
+ * loss on this batch (ties: the larger alpha; non-finite losses never win),
+ * chosen on the device without a host synchronisation (31 loss evaluations,
+ * each a forward Laplacian pass). */
 kfac_status_t kfac_pinn_step(kfac_handle_t h, void* stream, double* theta,
                              const double* X_int, int N_int, const double* f,
                              const double* X_bdy, int N_bdy, const double* g,
@@ -188,6 +196,12 @@ kfac_status_t kfac_pinn_get_gradient(kfac_handle_t h, void* stream, double* dst)
 
 /* Copy the last preconditioned direction Delta (D doubles). */
 kfac_status_t kfac_pinn_get_direction(kfac_handle_t h, void* stream, double* dst);
+
+/* Line search of the last kfac_pinn_step (Sec. 3.4): copy the trial losses
+ * to dst, 31 x 3 device doubles, row k = (L, L_Omega, L_boundary) at
+ * theta + 2^-k dhat on that step's batch.  KFAC_NOT_READY when the handle was
+ * created without line_search or has not stepped yet. */
+kfac_status_t kfac_pinn_get_line_search_losses(kfac_handle_t h, void* stream, double* dst);
 
 /* Synchronise the handle's device, then read and clear the device status
  * word (first error latched since the last read). */

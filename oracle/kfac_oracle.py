@@ -25,8 +25,10 @@ design notes as well):
   * The loss is Eq. 1 with 1/(2N) on both terms, also for the heat equation.
   * The boundary curvature is A_∂ ⊗ B_∂ (Sec. 3.4 prints A_Ω ⊗ B_Ω there; the
     pseudo-code of App. B uses the boundary factors).
-  * The update is θ_{t+1} = θ_t + δ_t with δ_t = lr · δ̂_t (Sec. 3.4); the
-    pseudo-code of App. B multiplies by the step size twice.
+  * The update is θ_{t+1} = θ_t + δ_t with δ_t = α · δ̂_t (Sec. 3.4); the
+    pseudo-code of App. B multiplies by the step size twice.  α is either a
+    fixed learning rate or the grid line search of Sec. 3.4, whose ties (not
+    specified) keep the larger α.
   * KFAC-reduce, which the paper cites but does not restate, is read as
     A = (1/N) Σ_n ā_n ā_nᵀ with ā_n the mean of the S input columns and
     B = (1/N) Σ_n ḡ_n ḡ_nᵀ with ḡ_n the sum of the S output gradients.
@@ -361,6 +363,7 @@ class KfacConfig:
     init_identity: bool = False
     lr: float = 0.1
     momentum: float = 0.0
+    line_search: bool = False
 
 
 @dataclass
@@ -388,7 +391,7 @@ class StepResult:
     grads: List[np.ndarray]
     factors: Tuple[List[np.ndarray], List[np.ndarray], List[np.ndarray], List[np.ndarray]]
     direction: List[np.ndarray]          # Δ_t (preconditioned, before momentum/lr)
-    update: List[np.ndarray]             # δ_t = lr (μ δ_{t-1} + Δ_t)
+    update: List[np.ndarray]             # δ_t = α (μ δ_{t-1} + Δ_t), α = lr or line search
     theta_new: np.ndarray
     extras: dict = field(default_factory=dict)
 
@@ -413,6 +416,32 @@ def curvature_and_gradient(cfg: KfacConfig, Ws, X_int, f, X_bdy, g):
                 factors=(Ai, Bi, Ab, Bb), grads=grads, loss=loss(r_i, r_b))
 
 
+def batch_loss(cfg: KfacConfig, theta: np.ndarray, X_int, f, X_bdy, g) -> Tuple[float, float, float]:
+    """Eq. 1 at theta on one batch: forward passes and residuals only."""
+    Ws = unpack_theta(theta, cfg.d, cfg.widths)
+    r_i = interior_residual(taylor_forward(Ws, X_int, cfg.op, True), f, cfg.op, cfg.kappa)
+    r_b = boundary_residual(taylor_forward(Ws, X_bdy, cfg.op, False), g)
+    return loss(r_i, r_b)
+
+
+LINE_SEARCH_GRID = tuple(2.0 ** -k for k in range(31))   # {2^0, 2^-1, .., 2^-30} (Sec. 3.4)
+
+
+def line_search(cfg: KfacConfig, theta: np.ndarray, dhat: np.ndarray, X_int, f, X_bdy, g):
+    """α* = argmin_α L(θ + α δ̂) over the logarithmic grid (Sec. 3.4; App. B step 5).
+
+    Returns (α*, losses) with losses[k] = L(θ + 2^-k δ̂) as (L, L_Ω, L_∂).  Equal
+    losses keep the larger α; non-finite losses never win; α* = 0 when no
+    trial is finite."""
+    losses = [batch_loss(cfg, theta + a * dhat, X_int, f, X_bdy, g) for a in LINE_SEARCH_GRID]
+    best = None
+    for k, (tot, _, _) in enumerate(losses):
+        if np.isfinite(tot) and (best is None or tot < losses[best][0]):
+            best = k
+    alpha = 0.0 if best is None else LINE_SEARCH_GRID[best]
+    return alpha, np.array(losses)
+
+
 def kfac_step(cfg: KfacConfig, state: KfacState, theta: np.ndarray,
               X_int, f, X_bdy, g) -> StepResult:
     Ws = unpack_theta(theta, cfg.d, cfg.widths)
@@ -424,19 +453,25 @@ def kfac_step(cfg: KfacConfig, state: KfacState, theta: np.ndarray,
         state.B_int[l] = beta * state.B_int[l] + (1 - beta) * Bi[l]
         state.A_bdy[l] = beta * state.A_bdy[l] + (1 - beta) * Ab[l]
         state.B_bdy[l] = beta * state.B_bdy[l] + (1 - beta) * Bb[l]
-    direction, update = [], []
+    direction, dhat = [], []
     for l in range(len(Ws)):
         D = kron_sum_inverse_apply(state.A_int[l], state.B_int[l], state.A_bdy[l],
                                    state.B_bdy[l], cg["grads"][l], cfg.lam, cfg.damping_sqrt)
         direction.append(D)
-        dhat = D if (state.delta_prev is None) else cfg.momentum * state.delta_prev[l] + D
-        update.append(cfg.lr * dhat)
+        dhat.append(D if (state.delta_prev is None) else cfg.momentum * state.delta_prev[l] + D)
+    extras = dict(cg)
+    if cfg.line_search:
+        alpha, extras["line_search_losses"] = line_search(cfg, theta, pack_theta(dhat), X_int, f, X_bdy, g)
+        extras["alpha"] = alpha
+    else:
+        alpha = cfg.lr
+    update = [alpha * v for v in dhat]
     state.delta_prev = update
     state.t += 1
     theta_new = theta + pack_theta(update)
     return StepResult(cg["loss"], cg["grads"], (list(state.A_int), list(state.B_int),
                       list(state.A_bdy), list(state.B_bdy)), direction, update, theta_new,
-                      extras=cg)
+                      extras=extras)
 
 
 # ---------------------------------------------------------------------------

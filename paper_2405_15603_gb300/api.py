@@ -44,7 +44,7 @@ def make_config(d: int, widths: Sequence[int], op: str = "laplace", kappa: float
                 precision: str = "fp64", variant: str = "expand", beta: float = 0.0,
                 lam: float = 1e-3, damping_sqrt: bool = False, init_identity: bool = False,
                 lr: float = 0.1, momentum: float = 0.0, max_n_int: int = 1024,
-                max_n_bdy: int = 1024) -> KfacConfig:
+                max_n_bdy: int = 1024, line_search: bool = False) -> KfacConfig:
     cfg = KfacConfig()
     cfg.d = d
     cfg.L = len(widths)
@@ -62,6 +62,7 @@ def make_config(d: int, widths: Sequence[int], op: str = "laplace", kappa: float
     cfg.momentum = momentum
     cfg.max_n_int = max_n_int
     cfg.max_n_bdy = max_n_bdy
+    cfg.line_search = int(line_search)
     return cfg
 
 
@@ -178,6 +179,13 @@ class KfacPinn:
     def direction(self) -> torch.Tensor:
         out = torch.empty(self.D, dtype=torch.float64, device=self.device)
         _check("kfac_pinn_get_direction", self.lib.kfac_pinn_get_direction(self.h, _stream(), _ptr(out)))
+        return out
+
+    def line_search_losses(self) -> torch.Tensor:
+        """Trial losses of the last step's line search: (31, 3), row k at alpha = 2^-k."""
+        out = torch.empty(31, 3, dtype=torch.float64, device=self.device)
+        _check("kfac_pinn_get_line_search_losses", self.lib.kfac_pinn_get_line_search_losses(
+            self.h, _stream(), _ptr(out)))
         return out
 
     def sync_status(self) -> str:

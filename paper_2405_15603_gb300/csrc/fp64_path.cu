@@ -154,7 +154,7 @@ __global__ void k_loss(const double* __restrict__ r, int N, const double* __rest
         loss[0] = li + lb;
         loss[1] = li;
         loss[2] = lb;
-        if (!isfinite(li + lb)) latch_status(status, KFAC_NONFINITE);
+        if (status && !isfinite(li + lb)) latch_status(status, KFAC_NONFINITE);
     }
 }
 
@@ -297,6 +297,25 @@ kfac_status_t fp64_loss(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N_bd
     if (loss_out && loss_out != h->loss)
         KFAC_CUDA_TRY(cudaMemcpyAsync(loss_out, h->loss, 3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return KFAC_OK;
+}
+
+// Loss of the residuals in h->in.r / h->bd.r written to dst (3 doubles); a
+// non-finite value is recorded, not latched (line-search trials may diverge).
+kfac_status_t fp64_loss_to(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N_bdy, double* dst) {
+    k_loss<<<1, 1024, 0, s>>>(h->in.r, N_int, h->bd.r, N_bdy, dst, nullptr);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+kfac_status_t fp64_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int,
+                             int N_int, const double* f, const double* X_bdy, int N_bdy, const double* g,
+                             double* dst) {
+    kfac_status_t st;
+    if ((st = fp64_forward(h, s, theta, X_int, N_int, h->in, h->S))) return st;
+    if ((st = fp64_residual_and_seed(h, s, h->in, N_int, h->S, f, true))) return st;
+    if ((st = fp64_forward(h, s, theta, X_bdy, N_bdy, h->bd, 1))) return st;
+    if ((st = fp64_residual_and_seed(h, s, h->bd, N_bdy, 1, g, false))) return st;
+    return fp64_loss_to(h, s, N_int, N_bdy, dst);
 }
 
 namespace {

@@ -48,6 +48,9 @@ struct kfac_pinn_handle {
     double* grad;         // D
     double* dir;          // D
     double* delta_prev;   // D
+    double* dhat;         // D: momentum direction of the line search
+    double* trial;        // D: trial parameters of the line search
+    double* ls_loss;      // 3 x 31 trial losses
     double* fac[4][KFAC_MAX_LAYERS];      // EMA factors A_int, B_int, A_bdy, B_bdy (n x n)
     double* VA[KFAC_MAX_LAYERS];          // generalized eigenvectors (na x na, row-major)
     double* wa[KFAC_MAX_LAYERS];          // generalized eigenvalues (na)
@@ -123,6 +126,14 @@ kfac_status_t fp64_backward(kfac_pinn_handle* h, cudaStream_t s, const double* t
 kfac_status_t fp64_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, const double* X_int,
                                     int N_int, const double* X_bdy, int N_bdy);
 kfac_status_t fp64_loss(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N_bdy, double* loss_out);
+kfac_status_t fp64_loss_to(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N_bdy, double* dst);
+kfac_status_t fp64_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int,
+                             int N_int, const double* f, const double* X_bdy, int N_bdy, const double* g,
+                             double* dst);
+// Line-search update (linalg.cu): theta += alpha* dhat, alpha* from the grid 2^-k
+kfac_status_t linalg_line_search_update(kfac_pinn_handle* h, cudaStream_t s, double* theta, const double* X_int,
+                                        int N_int, const double* f, const double* X_bdy, int N_bdy,
+                                        const double* g);
 kfac_status_t fp64_extract_outputs(kfac_pinn_handle* h, cudaStream_t s, PassBuffers& pb, int N,
                                    int S, double* u, double* grad, double* lap);
 

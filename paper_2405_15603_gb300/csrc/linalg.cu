@@ -6,6 +6,7 @@
 //         = vec( V_B [ (V_B^T G V_A) / (1 + b a^T) ] V_A^T ),
 // which is exact because vec(B X A) = (A^T (x) B) vec X (Sec. 2).
 #include "kfac_internal.cuh"
+#include "tc_path.cuh"
 
 namespace {
 
@@ -24,6 +25,56 @@ __global__ void k_update(double* theta, const double* dir, double* delta_prev, l
     double dlt = lr * (mom * delta_prev[i] + dir[i]);
     delta_prev[i] = dlt;
     theta[i] += dlt;
+}
+
+// Line search over the grid alpha_k = 2^-k, k = 0..LS_GRID-1 (Sec. 3.4).
+constexpr int LS_GRID = 31;
+
+// dhat = mu delta_prev + Delta (delta_prev is zero before the first step).
+__global__ void k_dhat(const double* dir, const double* delta_prev, double* dhat, long long D, double mom) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D) return;
+    dhat[i] = mom * delta_prev[i] + dir[i];
+}
+
+__global__ void k_trial(const double* theta, const double* dhat, double* trial, long long D, double alpha) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D) return;
+    trial[i] = theta[i] + alpha * dhat[i];
+}
+
+// alpha* = argmin over the finite trial losses; equal losses keep the larger
+// alpha.  With no finite trial the step is skipped and NONFINITE latched.
+__device__ int ls_argmin(const double* ls_loss) {
+    int best = -1;
+    double bl = 0.0;
+    for (int k = 0; k < LS_GRID; k++) {
+        double v = ls_loss[3 * k];
+        if (!isfinite(v)) continue;
+        if (best < 0 || v < bl) {
+            best = k;
+            bl = v;
+        }
+    }
+    return best;
+}
+
+// delta = alpha* dhat; theta += delta.
+__global__ void k_ls_apply(double* theta, const double* dhat, double* delta_prev, long long D,
+                           const double* ls_loss, int* status) {
+    __shared__ int best;
+    if (threadIdx.x == 0) {
+        best = ls_argmin(ls_loss);
+        if (best < 0 && blockIdx.x == 0) latch_status(status, KFAC_NONFINITE);
+    }
+    __syncthreads();
+    const double alpha = best < 0 ? 0.0 : ldexp(1.0, -best);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < D;
+         i += (long long)gridDim.x * blockDim.x) {
+        double dlt = alpha * dhat[i];
+        delta_prev[i] = dlt;
+        theta[i] += dlt;
+    }
 }
 
 kfac_status_t precondition_impl(kfac_pinn_handle* h, cudaStream_t s, const double* grad, double* dir) {
@@ -88,6 +139,27 @@ kfac_status_t linalg_precondition(kfac_pinn_handle* h, cudaStream_t s, const dou
 kfac_status_t linalg_update(kfac_pinn_handle* h, cudaStream_t s, double* theta) {
     k_update<<<ceil_div_u(h->D, 256), 256, 0, s>>>(theta, h->dir, h->delta_prev, h->D, h->cfg.lr,
                                                    h->cfg.momentum);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+kfac_status_t linalg_line_search_update(kfac_pinn_handle* h, cudaStream_t s, double* theta, const double* X_int,
+                                        int N_int, const double* f, const double* X_bdy, int N_bdy,
+                                        const double* g) {
+    const unsigned blocks = ceil_div_u(h->D, 256);
+    k_dhat<<<blocks, 256, 0, s>>>(h->dir, h->delta_prev, h->dhat, h->D, h->cfg.momentum);
+    KFAC_LAUNCH_CHECK(h);
+    const bool mixed = (h->cfg.precision == KFAC_MIXED_BF16);
+    for (int k = 0; k < LS_GRID; k++) {
+        k_trial<<<blocks, 256, 0, s>>>(theta, h->dhat, h->trial, h->D, ldexp(1.0, -k));
+        KFAC_LAUNCH_CHECK(h);
+        double* dst = h->ls_loss + 3 * k;
+        kfac_status_t st = mixed ? tc_eval_loss(h, s, h->trial, X_int, N_int, f, X_bdy, N_bdy, g, dst)
+                                 : fp64_eval_loss(h, s, h->trial, X_int, N_int, f, X_bdy, N_bdy, g, dst);
+        if (st) return st;
+    }
+    unsigned ab = blocks < (unsigned)(4 * h->sm_count) ? blocks : (unsigned)(4 * h->sm_count);
+    k_ls_apply<<<ab, 256, 0, s>>>(theta, h->dhat, h->delta_prev, h->D, h->ls_loss, h->status);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }

@@ -898,8 +898,11 @@ void tc_free(kfac_pinn_handle* h) {
     h->mx = nullptr;
 }
 
-kfac_status_t tc_factors(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int, int N_int,
-                         const double* f, const double* X_bdy, int N_bdy, const double* g, double* loss) {
+namespace {
+
+// Forward passes of both terms and their residuals into h->in.r / h->bd.r.
+kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int,
+                                    int N_int, const double* f, const double* X_bdy, int N_bdy, const double* g) {
     MxState* m = MX(h);
     kfac_status_t st;
     const int S = m->in.S;
@@ -925,10 +928,27 @@ kfac_status_t tc_factors(kfac_pinn_handle* h, cudaStream_t s, const double* thet
     k_residual_mx<<<ceil_div_u(N_bdy, EW), EW, 0, s>>>(m->bd.zl, g, h->bd.r, N_bdy, m->bd.N_pad, 1, 0, heat,
                                                         h->cfg.kappa);
     KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+}  // namespace
+
+kfac_status_t tc_factors(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int, int N_int,
+                         const double* f, const double* X_bdy, int N_bdy, const double* g, double* loss) {
+    MxState* m = MX(h);
+    kfac_status_t st;
+    if ((st = forward_and_residuals(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g))) return st;
     if ((st = fp64_loss(h, s, N_int, N_bdy, loss))) return st;
     if ((st = backward_pass(h, s, h->in.r, N_int, m->in))) return st;
     if ((st = backward_pass(h, s, h->bd.r, N_bdy, m->bd))) return st;
     return factors_and_grad(h, s, X_int, N_int, X_bdy, N_bdy);
+}
+
+kfac_status_t tc_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int, int N_int,
+                           const double* f, const double* X_bdy, int N_bdy, const double* g, double* dst) {
+    kfac_status_t st;
+    if ((st = forward_and_residuals(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g))) return st;
+    return fp64_loss_to(h, s, N_int, N_bdy, dst);
 }
 
 kfac_status_t tc_forward_laplacian(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X, int N,

@@ -9,3 +9,7 @@ kfac_status_t tc_factors(kfac_pinn_handle* h, cudaStream_t s, const double* thet
                          const double* X_bdy, int N_bdy, const double* g, double* loss);
 kfac_status_t tc_forward_laplacian(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
                                    const double* X, int N, double* u, double* grad, double* lap);
+// Loss (3 doubles: total, interior, boundary) of theta on the batch, written to dst.
+kfac_status_t tc_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                           const double* X_int, int N_int, const double* f,
+                           const double* X_bdy, int N_bdy, const double* g, double* dst);

@@ -460,3 +460,74 @@ def test_kfac_direction_is_descent_poisson2d():
     assert ko.pack_theta(res.grads) @ ko.pack_theta(res.direction) < 0
     nxt = ko.curvature_and_gradient(cfg, ko.unpack_theta(res.theta_new, prob.d, wl.widths), Xi, f, Xb, g)
     assert nxt["loss"][0] < res.loss[0]
+
+
+# --------------------------------------------------------------------------
+# Log-grid line search (Sec. 3.4; App. B step 5)
+# --------------------------------------------------------------------------
+def _linear_loss_closed_form(w, b, Xi, f, Xb, g):
+    # u = wᵀx + b has Δu = 0, so the Poisson residuals are r_Ω = -f and
+    # r_∂ = wᵀx + b - g; Eq. 1 with 1/(2N) on each term.
+    li = (f ** 2).sum() / (2 * f.size)
+    lb = ((Xb @ w + b - g) ** 2).sum() / (2 * g.size)
+    return li + lb
+
+
+def test_line_search_grid_argmin_closed_form():
+    # A single linear layer: L(θ + αδ̂) is a quadratic in α known in closed
+    # form.  With δ̂ = 0.37 × (the exact minimiser − θ) the minimum over α is at
+    # 1/0.37 > 1, so the grid's answer is α = 1; with 3.1 × it sits at
+    # 1/3.1 and the grid picks whichever of 2^-1, 2^-2 is closer in loss.
+    d = 3
+    prob = si.poisson_cos_problem(d)
+    Xi, f, Xb, g = si.make_batch(prob, 20, 15, seed=11)
+    cfg = ko.KfacConfig(d=d, widths=(1,), line_search=True)
+    th = np.array([0.3, -0.2, 0.5, 0.1])                 # (w_1, w_2, w_3, b)
+    Aug = np.hstack([Xb, np.ones((Xb.shape[0], 1))])
+    opt = np.linalg.lstsq(Aug, g, rcond=None)[0]
+    for scale in (0.37, 3.1):
+        dhat = scale * (opt - th)
+        alpha, losses = ko.line_search(cfg, th, dhat, Xi, f, Xb, g)
+        ref = [_linear_loss_closed_form((th + a * dhat)[:3], (th + a * dhat)[3], Xi, f, Xb, g)
+               for a in ko.LINE_SEARCH_GRID]
+        np.testing.assert_allclose(losses[:, 0], ref, rtol=1e-12)
+        assert alpha == ko.LINE_SEARCH_GRID[int(np.argmin(ref))]
+    assert len(ko.LINE_SEARCH_GRID) == 31
+    assert ko.LINE_SEARCH_GRID[0] == 1.0 and ko.LINE_SEARCH_GRID[-1] == 2.0 ** -30
+
+
+def test_line_search_ties_and_nonfinite():
+    d = 2
+    prob = si.PROBLEMS["poisson2d_sin"]
+    Xi, f, Xb, g = si.make_batch(prob, 10, 8, seed=12)
+    cfg = ko.KfacConfig(d=d, widths=(1,), line_search=True)
+    th = np.array([0.1, 0.2, 0.3])
+    # δ̂ = 0: every trial has the same loss, the larger α is kept.
+    alpha, losses = ko.line_search(cfg, th, np.zeros(3), Xi, f, Xb, g)
+    assert alpha == 1.0 and np.all(losses[:, 0] == losses[0, 0])
+    # A huge δ̂ overflows the large-α trials; they never win.
+    with np.errstate(over="ignore", invalid="ignore"):
+        alpha, losses = ko.line_search(cfg, th, np.full(3, 1e160), Xi, f, Xb, g)
+    assert not np.isfinite(losses[0, 0])
+    assert np.isfinite(losses[-1, 0]) and alpha == 2.0 ** -30
+
+
+def test_kfac_step_with_line_search_descends():
+    # δ̂ is a descent direction (the damped curvature is positive definite),
+    # so the grid minimum is below L(θ) and θ_{t+1} = θ_t + α* δ̂ attains it.
+    wl = si.WORKLOADS["poisson2d_small"]
+    prob = wl.prob
+    th = si.xavier_theta(prob.d, wl.widths, 0)
+    Xi, f, Xb, g = si.make_batch(prob, 100, 40, seed=1)
+    cfg = ko.KfacConfig(d=prob.d, widths=wl.widths, lam=1e-3, momentum=0.5, line_search=True)
+    st = ko.init_state(cfg)
+    for step in range(2):
+        res = ko.kfac_step(cfg, st, th, Xi, f, Xb, g)
+        losses = res.extras["line_search_losses"]
+        k = int(np.argmin(losses[:, 0]))
+        assert res.extras["alpha"] == 2.0 ** -k
+        after = ko.curvature_and_gradient(cfg, ko.unpack_theta(res.theta_new, prob.d, wl.widths),
+                                          Xi, f, Xb, g)["loss"]
+        np.testing.assert_allclose(after, losses[k], rtol=1e-12)
+        assert after[0] < res.loss[0]
+        th = res.theta_new
