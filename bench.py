@@ -3,8 +3,9 @@
 One step = one whole KFAC step (forward Laplacian on 2048 interior points,
 plain forward on 512 boundary points, residuals and loss, adjoint, gradient,
 Kronecker factors with EMA, FP64 Kronecker-sum inverse, preconditioning,
-update), with the collocation points resampled every step from a seeded
-stream (App. A.5 workload shape; synthetic data).
+momentum and the 31-point logarithmic line search, update), with the
+collocation points resampled every step from a seeded stream (App. A.5
+workload shape; synthetic data).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P]
     python bench.py --impl reference ...    # the FP64 CPU oracle, timed on host cores
@@ -36,8 +37,9 @@ from synth import inputs as si  # noqa: E402
 METRIC = "KFAC steps/s on d=100 MLP vs plain FP64 GPU path at equal L2 error; Gram % peak"
 WORKLOAD = si.WORKLOADS["poisson100d"]
 WORKLOAD_NAME = "poisson100d_100-768-768-512-512-1_2048int_512bdy_resampled"
-# KFAC hyper-parameters of the timed run (identical for every precision).
-HYPER = dict(lam=1e-3, beta=0.95, lr=0.05, momentum=0.0, init_identity=True)
+# KFAC hyper-parameters of the timed run (identical for every precision): the
+# paper's KFAC update, momentum plus the logarithmic grid line search (Sec. 3.4).
+HYPER = dict(lam=1e-3, beta=0.99, momentum=0.7, init_identity=True, line_search=True)
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -213,32 +215,38 @@ def run_gpu(args, rank, world, local_rank):
         opt64 = new_opt("fp64")
         th64 = torch.tensor(theta0, device=dev)
         ms64, _, _, _ = timed_steps(opt64, th64, dev_batches, 1, args.fp64_steps)
+        st64 = opt64.sync_status()
         fp64 = {"value": args.fp64_steps / (ms64 / 1000.0), "unit": "steps/s",
-                "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
+                "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps, "warmup": 1,
+                "status": st64}
         opt64.close()
 
     # ---- roofline of the dominant kernel class -----------------------------
     peaks, peak_kind = load_peaks()
-    dom = max(tim.items(), key=lambda kv: kv[1]["ms"])
-    name, rec = dom
-    per_launch_ms = rec["ms"] / max(rec["launches"], 1)
-    per_launch_work = rec["work"] / max(rec["launches"], 1)
-    if name in ("layer_gemm", "adjoint_gemm", "gram", "precond", "eig"):
-        unit = "TFLOP/s"
-        achieved = per_launch_work / (per_launch_ms / 1e3) / 1e12
-        if args.precision == "fp64" or name in ("eig", "precond"):
-            bound, peak, peak_src = "alu", 1.25, "nominal FP64 rate of the GB300 (1.25 TFLOP/s)"
+
+    def class_roofline(name, rec):
+        per_launch_ms = rec["ms"] / max(rec["launches"], 1)
+        per_launch_work = rec["work"] / max(rec["launches"], 1)
+        if name in ("layer_gemm", "adjoint_gemm", "gram", "precond", "eig"):
+            unit = "TFLOP/s"
+            achieved = per_launch_work / max(per_launch_ms / 1e3, 1e-12) / 1e12
+            if args.precision == "fp64" or name in ("eig", "precond"):
+                bound, peak, peak_src = "alu", 1.25, "nominal FP64 rate of the GB300 (1.25 TFLOP/s)"
+            else:
+                bound, peak = "tensor", peaks["bf16_tflops_sustained"]
+                peak_src = f"{peak_kind} bf16 sustained"
         else:
-            bound, peak = "tensor", peaks["bf16_tflops_sustained"]
-            peak_src = f"{peak_kind} bf16 sustained"
-    else:
-        unit, bound = "GB/s", "hbm"
-        achieved = per_launch_work / (per_launch_ms / 1e3) / 1e9
-        peak, peak_src = peaks["hbm_gbs"], f"{peak_kind} hbm copy"
-    roofline = {"bound": bound, "achieved": round(achieved, 4), "peak": peak, "unit": unit,
+            unit, bound = "GB/s", "hbm"
+            achieved = per_launch_work / max(per_launch_ms / 1e3, 1e-12) / 1e9
+            peak, peak_src = peaks["hbm_gbs"], f"{peak_kind} hbm copy"
+        return {"bound": bound, "achieved": round(achieved, 4), "peak": peak, "unit": unit,
                 "frac": round(achieved / peak, 4), "traffic": None, "kernel_class": name,
                 "per_launch_ms": round(per_launch_ms, 5), "launches": rec["launches"],
                 "peak_source": peak_src}
+
+    name, rec = max(tim.items(), key=lambda kv: kv[1]["ms"])
+    roofline = class_roofline(name, rec)
+    class_rooflines = {k: class_roofline(k, v) for k, v in tim.items() if v["launches"] > 0}
     classes = {k: {"ms_per_step": round(v["ms"] / K, 4), "launches_per_step": v["launches"] / K}
                for k, v in tim.items()}
 
@@ -253,6 +261,7 @@ def run_gpu(args, rank, world, local_rank):
                    "variant": "expand", **HYPER, "parallelism": f"replicas{world}",
                    "l2": "flushed between steps (256 MiB write outside the step events)"},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
+        "class_rooflines": class_rooflines,
         "kernel_classes": classes, "clocks": clocks, "status": status,
         "wall_s_timed": round(wall, 3),
     }
@@ -275,17 +284,22 @@ def oracle_step_time(n_int, n_bdy, seed=0, step=0):
     widths = WORKLOAD.widths
     th = si.xavier_theta(prob.d, widths, seed)
     Xi, f, Xb, g = si.make_batch(prob, n_int, n_bdy, seed=seed, step=step)
-    cfg = ko.KfacConfig(d=prob.d, widths=widths, lam=HYPER["lam"], lr=HYPER["lr"])
+    cfg = ko.KfacConfig(d=prob.d, widths=widths, lam=HYPER["lam"], beta=HYPER["beta"],
+                        momentum=HYPER["momentum"], init_identity=HYPER["init_identity"],
+                        line_search=HYPER["line_search"])
     Ws = ko.unpack_theta(th, prob.d, widths)
     t0 = time.perf_counter()
     cg = ko.curvature_and_gradient(cfg, Ws, Xi, f, Xb, g)
     t1 = time.perf_counter()
     Ai, Bi, Ab, Bb = cg["factors"]
-    for l in range(len(widths)):
-        ko.kron_sum_inverse_apply(Ai[l], Bi[l], Ab[l], Bb[l], cg["grads"][l], cfg.lam)
+    dirs = [ko.kron_sum_inverse_apply(Ai[l], Bi[l], Ab[l], Bb[l], cg["grads"][l], cfg.lam)
+            for l in range(len(widths))]
     t2 = time.perf_counter()
+    if cfg.line_search:
+        ko.line_search(cfg, th, ko.pack_theta(dirs), Xi, f, Xb, g)
+    t3 = time.perf_counter()
     scale = WORKLOAD.n_int / n_int
-    return (t1 - t0) * scale + (t2 - t1), (t1 - t0), (t2 - t1)
+    return ((t1 - t0) + (t3 - t2)) * scale + (t2 - t1), (t1 - t0) + (t3 - t2), (t2 - t1)
 
 
 def cpu_cores():
@@ -296,7 +310,8 @@ def cpu_cores():
 
 
 SAMPLE = (16, 4)
-SAMPLE_DESC = ("oracle (numpy FP64) per-point stages on 16 interior + 4 boundary points of the "
+SAMPLE_DESC = ("oracle (numpy FP64) per-point stages (forward, adjoint, gradient, factors and "
+               "the 31 line-search loss evaluations) on 16 interior + 4 boundary points of the "
                "workload, scaled linearly to 2048 + 512 points, plus the full-size FP64 "
                "Kronecker-sum inverse of all 5 layers")
 
@@ -351,7 +366,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed_bf16", choices=["fp64", "mixed_bf16"])
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", default=None,
                     help="N_INT,N_BDY override (smaller cases for profiler captures; not the headline)")

@@ -125,6 +125,19 @@ kfac_status_t kfac_pinn_forward_laplacian(kfac_handle_t h, void* stream, const d
                                           const double* X, int N,
                                           double* u, double* grad, double* lap);
 
+/* Reverse mode through the forward Laplacian (the backward pass of Sec. 3.2,
+ * seeded by the caller instead of by a residual): for a scalar phi of the
+ * outputs with upstream gradients du = dphi/du (N), dgrad = dphi/d(grad u)
+ * (N x d row-major) and dlap = dphi/d(lap u) (N), each may be NULL (zero),
+ * writes dtheta = dphi/dtheta (D doubles, overwritten; same packing as theta)
+ * and, if dX is not NULL, dX = dphi/dX (N x d).  The Taylor activations of
+ * the forward pass are recomputed in chunks of max_n_int points, so memory
+ * does not grow with N.  FP64 handles only (KFAC_BAD_ARG otherwise). */
+kfac_status_t kfac_pinn_forward_laplacian_backward(kfac_handle_t h, void* stream, const double* theta,
+                                                   const double* X, int N, const double* du,
+                                                   const double* dgrad, const double* dlap,
+                                                   double* dtheta, double* dX);
+
 /* Curvature and gradient of one batch (App. B, Algorithm 1, steps 1, 2 and
  * 4): forward Laplacian on the interior points and plain forward pass on the
  * boundary points, residuals and loss (Eq. 1), one backward pass each for

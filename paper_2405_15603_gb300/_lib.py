@@ -16,7 +16,7 @@ EXPORTS = [
     "kfac_pinn_get_factor", "kfac_pinn_set_factor", "kfac_pinn_get_gradient",
     "kfac_pinn_get_direction", "kfac_pinn_sync_status", "kfac_pinn_launch_count",
     "kfac_pinn_timing_enable", "kfac_pinn_timing_read", "kfac_pinn_forward_laplacian_noalloc",
-    "kfac_pinn_get_line_search_losses",
+    "kfac_pinn_get_line_search_losses", "kfac_pinn_forward_laplacian_backward",
 ]
 
 KERNEL_CLASSES = {0: "layer_gemm", 1: "adjoint_gemm", 2: "gram", 3: "elementwise", 4: "eig", 5: "precond"}
@@ -64,6 +64,7 @@ def load() -> C.CDLL:
         "kfac_pinn_destroy": (st, [H]),
         "kfac_pinn_reset": (st, [H, P]),
         "kfac_pinn_forward_laplacian": (st, [H, P, P, P, I, P, P, P]),
+        "kfac_pinn_forward_laplacian_backward": (st, [H, P, P, P, I, P, P, P, P, P]),
         "kfac_pinn_factors": (st, [H, P, P, P, I, P, P, I, P, P]),
         "kfac_pinn_invert": (st, [H, P]),
         "kfac_pinn_precondition": (st, [H, P, P, P]),

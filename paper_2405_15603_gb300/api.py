@@ -112,6 +112,19 @@ class KfacPinn:
             self.h, _stream(), _ptr(theta), _ptr(X), N, _ptr(u), _ptr(g), _ptr(lap)))
         return u, g, lap
 
+    def forward_laplacian_backward(self, theta: torch.Tensor, X, du=None, dgrad=None, dlap=None,
+                                   need_dX: bool = False):
+        """dphi/dtheta (and dphi/dX) for upstream gradients of (u, grad u, lap u)."""
+        X = _dev(X, self.device)
+        N = X.shape[0]
+        ups = [None if t is None else _dev(t, self.device) for t in (du, dgrad, dlap)]
+        dtheta = torch.empty(self.D, dtype=torch.float64, device=self.device)
+        dX = torch.empty(N, self.d, dtype=torch.float64, device=self.device) if need_dX else None
+        _check("kfac_pinn_forward_laplacian_backward", self.lib.kfac_pinn_forward_laplacian_backward(
+            self.h, _stream(), _ptr(theta.detach().contiguous()), _ptr(X), N, _ptr(ups[0]), _ptr(ups[1]),
+            _ptr(ups[2]), _ptr(dtheta), _ptr(dX)))
+        return dtheta, dX
+
     def factors(self, theta, X_int, f, X_bdy, g) -> torch.Tensor:
         X_int, f, X_bdy, g = (_dev(a, self.device) for a in (X_int, f, X_bdy, g))
         _check("kfac_pinn_factors", self.lib.kfac_pinn_factors(
@@ -208,3 +221,26 @@ class KfacPinn:
                 self.h, cls, C.byref(ms), C.byref(n), C.byref(w)))
             out[name] = {"ms": ms.value, "launches": n.value, "work": w.value}
         return out
+
+
+class ForwardLaplacian(torch.autograd.Function):
+    """(u, grad u, lap u) of the MLP with packed parameters theta at the points X
+    (Sec. 3.1), differentiable in theta and X through the library's reverse pass.
+
+        u, g, lap = ForwardLaplacian.apply(theta, X, opt)     # opt: an FP64 KfacPinn
+    """
+
+    @staticmethod
+    def forward(ctx, theta, X, opt):
+        th = theta.detach().contiguous()
+        u, g, lap = opt.forward_laplacian(th, X.detach())
+        ctx.save_for_backward(th, X.detach())
+        ctx.opt = opt
+        return u, g, lap
+
+    @staticmethod
+    @torch.autograd.function.once_differentiable
+    def backward(ctx, du, dg, dl):
+        theta, X = ctx.saved_tensors
+        dtheta, dX = ctx.opt.forward_laplacian_backward(theta, X, du, dg, dl, need_dX=ctx.needs_input_grad[1])
+        return (dtheta if ctx.needs_input_grad[0] else None), dX, None

@@ -387,6 +387,29 @@ kfac_status_t kfac_pinn_forward_laplacian(kfac_handle_t h, void* stream, const d
     return KFAC_OK;
 }
 
+kfac_status_t kfac_pinn_forward_laplacian_backward(kfac_handle_t h, void* stream, const double* theta,
+                                                   const double* X, int N, const double* du,
+                                                   const double* dgrad, const double* dlap, double* dtheta,
+                                                   double* dX) {
+    if (!h || !theta || !X || !dtheta || N < 0) return KFAC_BAD_ARG;
+    if (h->cfg.precision != KFAC_FP64) return KFAC_BAD_ARG;
+    cudaStream_t s = S_(stream);
+    const int d = h->dims[0];
+    if (N == 0) {
+        KFAC_CUDA_TRY(cudaMemsetAsync(dtheta, 0, h->D * sizeof(double), s));
+        return KFAC_OK;
+    }
+    for (int off = 0; off < N; off += h->cfg.max_n_int) {
+        int n = N - off < h->cfg.max_n_int ? N - off : h->cfg.max_n_int;
+        kfac_status_t st = fp64_forward_laplacian_backward(
+            h, s, theta, X + (long long)off * d, n, du ? du + off : nullptr,
+            dgrad ? dgrad + (long long)off * d : nullptr, dlap ? dlap + off : nullptr, dtheta,
+            dX ? dX + (long long)off * d : nullptr, off > 0);
+        if (st) return st;
+    }
+    return KFAC_OK;
+}
+
 kfac_status_t kfac_pinn_factors(kfac_handle_t h, void* stream, const double* theta,
                                 const double* X_int, int N_int, const double* f,
                                 const double* X_bdy, int N_bdy, const double* g, double* loss) {

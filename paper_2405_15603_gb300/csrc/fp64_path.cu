@@ -395,6 +395,54 @@ kfac_status_t fp64_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, const d
 }
 
 namespace {
+// Output seed of the reverse pass through the Taylor forward: for a scalar
+// phi(u, grad u, lap u), Zbar^{(L)}_{n,s} = dphi/dZ^{(L)}_{n,s} with the
+// Taylor rows ordered (value, d tangents, Laplacian).  NULL inputs are zero.
+__global__ void k_seed_upstream(double* __restrict__ ZbL, int N, int S, const double* __restrict__ du,
+                                const double* __restrict__ dgrad, const double* __restrict__ dlap) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * S) return;
+    int s = (int)(idx / N), n = (int)(idx % N);
+    double c = 0.0;
+    if (s == 0) c = du ? du[n] : 0.0;
+    else if (s == S - 1) c = dlap ? dlap[n] : 0.0;
+    else c = dgrad ? dgrad[(long long)n * (S - 2) + (s - 1)] : 0.0;
+    ZbL[idx] = c;
+}
+}  // namespace
+
+kfac_status_t fp64_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                                              const double* X, int N, const double* du, const double* dgrad,
+                                              const double* dlap, double* dtheta, double* dX, bool accumulate) {
+    const int L = h->cfg.L, d = h->dims[0], S = h->S;
+    kfac_status_t st;
+    if ((st = fp64_forward(h, s, theta, X, N, h->in, S))) return st;
+    k_seed_upstream<<<ceil_div_u((long long)N * S, EW_THREADS), EW_THREADS, 0, s>>>(h->in.Zb[L - 1], N, S, du,
+                                                                                    dgrad, dlap);
+    KFAC_LAUNCH_CHECK(h);
+    if ((st = fp64_backward(h, s, theta, h->in, N, S))) return st;
+    // dphi/dW~_l = sum over rows (n, s) of g^{(l)}_{n,s} T^^{(l-1)T}_{n,s} (Sec. 3.2)
+    for (int l = 1; l <= L; l++) {
+        const int hout = h->dims[l], nin = h->dims[l - 1] + 1;
+        Transposed<WeightedRows> A{WeightedRows{h->in.Zb[l - 1], hout, N, nullptr}};
+        double* gW = dtheta + h->woff[l - 1];
+        if (l == 1) st = reduce_gemm(h, s, hout, nin, S * N, A, InputRows{X, d, N}, 1.0, gW, 1, hout,
+                                     accumulate, 0, 0.0);
+        else st = reduce_gemm(h, s, hout, nin, S * N, A, ActRows{h->in.T[l - 2], nin - 1, N}, 1.0, gW, 1, hout,
+                              accumulate, 0, 0.0);
+        if (st) return st;
+    }
+    // dphi/dx_n = W_1^T g^{(1)}_{n,0}: x enters the value column of layer 1 only
+    // (the tangent inputs e_i and the zero Laplacian input are constants).
+    if (dX) {
+        const int h1 = h->dims[1];
+        st = dgemm_strided(h, s, N, d, h1, h->in.Zb[0], h1, 1, theta, 1, h1, dX, d, 1, 1.0, 0.0);
+        if (st) return st;
+    }
+    return KFAC_OK;
+}
+
+namespace {
 __global__ void k_extract(const double* __restrict__ ZL, int N, int S, int d, double* u,
                           double* grad, double* lap) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;

@@ -134,6 +134,9 @@ kfac_status_t fp64_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* 
 kfac_status_t linalg_line_search_update(kfac_pinn_handle* h, cudaStream_t s, double* theta, const double* X_int,
                                         int N_int, const double* f, const double* X_bdy, int N_bdy,
                                         const double* g);
+kfac_status_t fp64_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                                              const double* X, int N, const double* du, const double* dgrad,
+                                              const double* dlap, double* dtheta, double* dX, bool accumulate);
 kfac_status_t fp64_extract_outputs(kfac_pinn_handle* h, cudaStream_t s, PassBuffers& pb, int N,
                                    int S, double* u, double* grad, double* lap);
 
