@@ -107,6 +107,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max(x: float, device) -> float:
+    """Maximum of x over the ranks of the default process group (x itself at N = 1)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(rank: int) -> int:
+    """Each replica draws its own point stream and initial weights."""
+    return 1000 * rank
+
+
+def replica_value(world: int, steps: int, ms_max: float) -> float:
+    """Whole-job steps/s: every rank runs `steps` steps; the slowest rank's time counts."""
+    return world * steps / (ms_max / 1000.0)
+
+
 def make_batches(n, seed_base):
     prob = WORKLOAD.prob
     return [si.make_batch(prob, WORKLOAD.n_int, WORKLOAD.n_bdy, seed=seed_base, step=k) for k in range(n)]
@@ -125,7 +146,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     prob = WORKLOAD.prob
     widths = WORKLOAD.widths
-    seed = 1000 * rank
+    seed = replica_seed(rank)
 
     def new_opt(precision):
         return KfacPinn(prob.d, widths, device=str(dev), precision=precision,
@@ -178,11 +199,8 @@ def run_gpu(args, rank, world, local_rank):
     clocks = sampler.stop()
     status = opt.sync_status()
     print(f"[bench] main arm: {ms / K:.3f} ms/step, status {status}, classes {tim}", file=sys.stderr, flush=True)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * K / (ms_max / 1000.0)
+    ms_max = reduce_max(ms, dev)
+    value = replica_value(world, K, ms_max)
 
     # ---- end to end through the C-ABI with host buffers -------------------
     import ctypes
@@ -201,12 +219,8 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     h2d = sum(a.size * 8 for a in host_batches[0])
-    e2e = {"value": world * K / e2e_s if world == 1 else None, "unit": "steps/s",
+    e2e = {"value": replica_value(world, K, 1000.0 * reduce_max(e2e_s, dev)), "unit": "steps/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 24}
-    if world > 1:
-        e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(e_t, op=torch.distributed.ReduceOp.MAX)
-        e2e["value"] = world * K / float(e_t.item())
     opt_e.close()
 
     # ---- plain FP64 GPU path beside it (same workload, fewer steps) -------
