@@ -29,6 +29,9 @@ design notes as well):
     pseudo-code of App. B multiplies by the step size twice.  α is either a
     fixed learning rate or the grid line search of Sec. 3.4, whose ties (not
     specified) keep the larger α.
+  * KFAC* (Sec. 3.4): the printed 2x2 system's lower-right entry δᵀGΔ is read
+    as δᵀGδ (the quadratic model's curvature along δ); on the first step, with
+    no previous update, only α is fitted and μ = 0.
   * KFAC-reduce, which the paper cites but does not restate, is read as
     A = (1/N) Σ_n ā_n ā_nᵀ with ā_n the mean of the S input columns and
     B = (1/N) Σ_n ḡ_n ḡ_nᵀ with ḡ_n the sum of the S output gradients.
@@ -364,6 +367,7 @@ class KfacConfig:
     lr: float = 0.1
     momentum: float = 0.0
     line_search: bool = False
+    kfac_star: bool = False     # automatic learning rate and momentum (KFAC*, Sec. 3.4)
 
 
 @dataclass
@@ -442,6 +446,41 @@ def line_search(cfg: KfacConfig, theta: np.ndarray, dhat: np.ndarray, X_int, f, 
     return alpha, np.array(losses)
 
 
+def residual_jvp(cg: dict, V: Sequence[np.ndarray]) -> Tuple[np.ndarray, np.ndarray]:
+    """J_θ r · v for the interior and boundary residuals: (J_n v) = Σ_l ⟨J_{W̃_l} r_n, V_l⟩
+    with the per-point weight Jacobians of Sec. 3.2 (V_l shaped like W̃_l)."""
+    ji = sum(np.einsum("nij,ij->n", weight_jacobian(cg["zb_i"][l], cg["fp_i"].T_in[l]), V[l])
+             for l in range(len(V)))
+    jb = sum(np.einsum("nij,ij->n", weight_jacobian(cg["zb_b"][l], cg["fp_b"].T_in[l]), V[l])
+             for l in range(len(V)))
+    return ji, jb
+
+
+def gramian_bilinear(ja: Tuple[np.ndarray, np.ndarray], jb: Tuple[np.ndarray, np.ndarray]) -> float:
+    """aᵀ G b with G of Eq. 2, from the residual JVPs J a and J b."""
+    return float(ja[0] @ jb[0] / ja[0].size + ja[1] @ jb[1] / ja[1].size)
+
+
+def kfac_star_coefficients(cfg: KfacConfig, cg: dict, Delta: np.ndarray, delta: Optional[np.ndarray],
+                           grad: np.ndarray) -> Tuple[float, float]:
+    """(α*, μ*) minimising the quadratic model m(αΔ + μδ) with the exact damped
+    Gramian G + λI (Sec. 3.4, after Martens & Grosse 2015, Sec. 7).  On the
+    first step (δ = 0) the model is minimised over α alone and μ* = 0."""
+    lam = cfg.lam
+    unpack = lambda v: unpack_theta(v, cfg.d, cfg.widths)
+    jD = residual_jvp(cg, unpack(Delta))
+    a11 = gramian_bilinear(jD, jD) + lam * float(Delta @ Delta)
+    b1 = float(Delta @ grad)
+    if delta is None or not np.any(delta):
+        return -b1 / a11, 0.0
+    jd = residual_jvp(cg, unpack(delta))
+    a12 = gramian_bilinear(jD, jd) + lam * float(Delta @ delta)
+    a22 = gramian_bilinear(jd, jd) + lam * float(delta @ delta)
+    b2 = float(delta @ grad)
+    alpha, mu = -np.linalg.solve(np.array([[a11, a12], [a12, a22]]), np.array([b1, b2]))
+    return float(alpha), float(mu)
+
+
 def kfac_step(cfg: KfacConfig, state: KfacState, theta: np.ndarray,
               X_int, f, X_bdy, g) -> StepResult:
     Ws = unpack_theta(theta, cfg.d, cfg.widths)
@@ -460,6 +499,19 @@ def kfac_step(cfg: KfacConfig, state: KfacState, theta: np.ndarray,
         direction.append(D)
         dhat.append(D if (state.delta_prev is None) else cfg.momentum * state.delta_prev[l] + D)
     extras = dict(cg)
+    if cfg.kfac_star:
+        # KFAC*: δ_t = α* Δ_t + μ* δ_{t-1} (Sec. 3.4)
+        prev = None if state.delta_prev is None else pack_theta(state.delta_prev)
+        alpha, mu = kfac_star_coefficients(cfg, cg, pack_theta(direction), prev, pack_theta(cg["grads"]))
+        extras["alpha"], extras["mu"] = alpha, mu
+        update = [alpha * direction[l] + (0.0 if prev is None else mu * state.delta_prev[l])
+                  for l in range(len(Ws))]
+        state.delta_prev = update
+        state.t += 1
+        theta_new = theta + pack_theta(update)
+        return StepResult(cg["loss"], cg["grads"], (list(state.A_int), list(state.B_int),
+                          list(state.A_bdy), list(state.B_bdy)), direction, update, theta_new,
+                          extras=extras)
     if cfg.line_search:
         alpha, extras["line_search_losses"] = line_search(cfg, theta, pack_theta(dhat), X_int, f, X_bdy, g)
         extras["alpha"] = alpha

@@ -531,3 +531,57 @@ def test_kfac_step_with_line_search_descends():
         np.testing.assert_allclose(after, losses[k], rtol=1e-12)
         assert after[0] < res.loss[0]
         th = res.theta_new
+
+
+# --------------------------------------------------------------------------
+# KFAC*: automatic learning rate and momentum (Sec. 3.4)
+# --------------------------------------------------------------------------
+def test_gramian_products_vs_full_ggn():
+    d, widths = 2, (4, 3, 1)
+    th = _theta(d, widths, seed=50)
+    prob = si.PROBLEMS["poisson2d_sin"]
+    Xi, f, Xb, g = si.make_batch(prob, 6, 5, seed=13)
+    cfg = ko.KfacConfig(d=d, widths=widths)
+    Ws = ko.unpack_theta(th, d, widths)
+    G = ko.full_ggn(cfg, Ws, Xi, f, Xb, g)
+    cg = ko.curvature_and_gradient(cfg, Ws, Xi, f, Xb, g)
+    rng = np.random.default_rng(1)
+    a, b = rng.standard_normal(th.size), rng.standard_normal(th.size)
+    ja = ko.residual_jvp(cg, ko.unpack_theta(a, d, widths))
+    jb = ko.residual_jvp(cg, ko.unpack_theta(b, d, widths))
+    np.testing.assert_allclose(ko.gramian_bilinear(ja, jb), a @ G @ b, rtol=1e-11)
+    # the residual JVP is the directional derivative of the residuals
+    h = 1e-6
+    rp = ko.curvature_and_gradient(cfg, ko.unpack_theta(th + h * a, d, widths), Xi, f, Xb, g)
+    rm = ko.curvature_and_gradient(cfg, ko.unpack_theta(th - h * a, d, widths), Xi, f, Xb, g)
+    np.testing.assert_allclose(ja[0], (rp["r_i"] - rm["r_i"]) / (2 * h), rtol=1e-6, atol=1e-8)
+    np.testing.assert_allclose(ja[1], (rp["r_b"] - rm["r_b"]) / (2 * h), rtol=1e-6, atol=1e-8)
+
+
+def test_kfac_star_minimises_quadratic_model():
+    d, widths = 2, (5, 4, 1)
+    th = _theta(d, widths, seed=51)
+    prob = si.PROBLEMS["poisson2d_sin"]
+    Xi, f, Xb, g = si.make_batch(prob, 8, 6, seed=14)
+    cfg = ko.KfacConfig(d=d, widths=widths, lam=1e-2, kfac_star=True)
+    st = ko.init_state(cfg)
+    res1 = ko.kfac_step(cfg, st, th, Xi, f, Xb, g)
+    assert res1.extras["mu"] == 0.0                     # first step: α only
+    res2 = ko.kfac_step(cfg, st, res1.theta_new, Xi, f, Xb, g)
+    Ws = ko.unpack_theta(res1.theta_new, d, widths)
+    G = ko.full_ggn(cfg, Ws, Xi, f, Xb, g) + cfg.lam * np.eye(th.size)
+    gr = ko.pack_theta(res2.grads)
+    Dl, dl = ko.pack_theta(res2.direction), ko.pack_theta(res1.update)
+
+    def model(a, m):
+        v = a * Dl + m * dl
+        return v @ gr + 0.5 * v @ G @ v
+
+    a, m = res2.extras["alpha"], res2.extras["mu"]
+    np.testing.assert_allclose(ko.pack_theta(res2.update), a * Dl + m * dl, rtol=1e-14)
+    best = model(a, m)
+    for da, dm in ((1e-3, 0), (-1e-3, 0), (0, 1e-3), (0, -1e-3)):
+        assert model(a + da * abs(a), m + dm * max(abs(m), 1.0)) > best
+    # stationarity of the model in (α, μ) with the dense Gramian
+    np.testing.assert_allclose([Dl @ (gr + G @ (a * Dl + m * dl)), dl @ (gr + G @ (a * Dl + m * dl))],
+                               [0.0, 0.0], atol=1e-9 * abs(Dl @ gr))
