@@ -39,7 +39,7 @@ WORKLOAD = si.WORKLOADS["poisson100d"]
 WORKLOAD_NAME = "poisson100d_100-768-768-512-512-1_2048int_512bdy_resampled"
 # KFAC hyper-parameters of the timed run (identical for every precision): the
 # paper's KFAC update, momentum plus the logarithmic grid line search (Sec. 3.4).
-HYPER = dict(lam=1e-3, beta=0.99, momentum=0.7, init_identity=True, line_search=True)
+HYPER = dict(lam=1e-3, beta=0.99, momentum=0.7, init_identity=True, update="line_search")
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -300,7 +300,7 @@ def oracle_step_time(n_int, n_bdy, seed=0, step=0):
     Xi, f, Xb, g = si.make_batch(prob, n_int, n_bdy, seed=seed, step=step)
     cfg = ko.KfacConfig(d=prob.d, widths=widths, lam=HYPER["lam"], beta=HYPER["beta"],
                         momentum=HYPER["momentum"], init_identity=HYPER["init_identity"],
-                        line_search=HYPER["line_search"])
+                        line_search=HYPER["update"] == "line_search")
     Ws = ko.unpack_theta(th, prob.d, widths)
     t0 = time.perf_counter()
     cg = ko.curvature_and_gradient(cfg, Ws, Xi, f, Xb, g)

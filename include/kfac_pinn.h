@@ -69,6 +69,18 @@ typedef enum { KFAC_EXPAND = 0, KFAC_REDUCE = 1 } kfac_variant_t;
  *          over coordinates 1..d-1 and coordinate 0 is time (App. A.6). */
 typedef enum { KFAC_OP_LAPLACE = 0, KFAC_OP_HEAT = 1 } kfac_operator_t;
 
+/* Update rule of kfac_pinn_step (Sec. 3.4), with Delta the preconditioned
+ * direction and delta_prev the previous update:
+ * FIXED:       delta = lr (momentum delta_prev + Delta)
+ * LINE_SEARCH: delta = alpha* dhat, dhat = momentum delta_prev + Delta and
+ *              alpha* = argmin over {2^0, 2^-1, .., 2^-30} of L(theta + alpha dhat)
+ *              on the step's batch (KFAC of the paper; lr unused)
+ * AUTO:        delta = alpha* Delta + mu* delta_prev with (alpha*, mu*) the
+ *              minimiser of the quadratic model with the exact damped Gramian
+ *              G + lambda I (KFAC* of the paper; lr and momentum unused; FP64
+ *              precision only). */
+typedef enum { KFAC_UPDATE_FIXED = 0, KFAC_UPDATE_LINE_SEARCH = 1, KFAC_UPDATE_AUTO = 2 } kfac_update_t;
+
 /* Factor selector of kfac_pinn_get_factor / kfac_pinn_set_factor. */
 typedef enum { KFAC_A_INT = 0, KFAC_B_INT = 1, KFAC_A_BDY = 2, KFAC_B_BDY = 3 } kfac_factor_t;
 
@@ -90,10 +102,7 @@ typedef struct {
     double momentum;               /* momentum mu on the previous update               */
     int max_n_int;                 /* capacity: interior points per call (>= 1)        */
     int max_n_bdy;                 /* capacity: boundary points per call (>= 1)        */
-    int line_search;               /* 0: theta += lr * dhat; 1: kfac_pinn_step picks
-                                      alpha = argmin over {2^0, 2^-1, .., 2^-30} of the
-                                      loss L(theta + alpha * dhat) on the step's batch
-                                      (Sec. 3.4), lr is then unused                    */
+    int update;                    /* kfac_update_t of kfac_pinn_step                  */
 } kfac_config_t;
 
 typedef struct kfac_pinn_handle* kfac_handle_t;
@@ -173,13 +182,15 @@ kfac_status_t kfac_pinn_precondition(kfac_handle_t h, void* stream, const double
 kfac_status_t kfac_pinn_update(kfac_handle_t h, void* stream, double* theta);
 
 /* One whole KFAC step: kfac_pinn_factors, kfac_pinn_invert,
- * kfac_pinn_precondition and the update, in that order.  theta is updated in
- * place; loss (3 device doubles, may be NULL) is the loss at the incoming
- * theta.  With cfg.line_search the update is theta += alpha* dhat with
- * dhat = momentum * delta_prev + Delta and alpha* the grid point of least
- * loss on this batch (ties: the larger alpha; non-finite losses never win),
- * chosen on the device without a host synchronisation (31 loss evaluations,
- * each a forward Laplacian pass). */
+ * kfac_pinn_precondition and the update rule cfg.update, in that order.  theta
+ * is updated in place; loss (3 device doubles, may be NULL) is the loss at the
+ * incoming theta.  LINE_SEARCH evaluates the 31 trial losses on the device
+ * (each a forward Laplacian pass) and picks alpha* there (ties: the larger
+ * alpha; non-finite losses never win; none finite: no update and
+ * KFAC_NONFINITE latched).  AUTO forms the two residual Jacobian-vector
+ * products J Delta and J delta_prev on the device (the Taylor pass in forward
+ * mode) and solves the 2x2 system there (first step: alpha only, mu* = 0).
+ * Neither synchronises the host. */
 kfac_status_t kfac_pinn_step(kfac_handle_t h, void* stream, double* theta,
                              const double* X_int, int N_int, const double* f,
                              const double* X_bdy, int N_bdy, const double* g,
@@ -213,8 +224,13 @@ kfac_status_t kfac_pinn_get_direction(kfac_handle_t h, void* stream, double* dst
 /* Line search of the last kfac_pinn_step (Sec. 3.4): copy the trial losses
  * to dst, 31 x 3 device doubles, row k = (L, L_Omega, L_boundary) at
  * theta + 2^-k dhat on that step's batch.  KFAC_NOT_READY when the handle was
- * created without line_search or has not stepped yet. */
+ * created with another update rule or has not stepped yet. */
 kfac_status_t kfac_pinn_get_line_search_losses(kfac_handle_t h, void* stream, double* dst);
+
+/* Coefficients of the last kfac_pinn_step's update delta = c0 Delta + c1 delta_prev:
+ * dst = (c0, c1), 2 device doubles.  FIXED: (lr, lr momentum); LINE_SEARCH:
+ * (alpha*, alpha* momentum); AUTO: (alpha*, mu*).  KFAC_NOT_READY before the first step. */
+kfac_status_t kfac_pinn_get_update_coefficients(kfac_handle_t h, void* stream, double* dst);
 
 /* Synchronise the handle's device, then read and clear the device status
  * word (first error latched since the last read). */

@@ -17,6 +17,7 @@ EXPORTS = [
     "kfac_pinn_get_direction", "kfac_pinn_sync_status", "kfac_pinn_launch_count",
     "kfac_pinn_timing_enable", "kfac_pinn_timing_read", "kfac_pinn_forward_laplacian_noalloc",
     "kfac_pinn_get_line_search_losses", "kfac_pinn_forward_laplacian_backward",
+    "kfac_pinn_get_update_coefficients",
 ]
 
 KERNEL_CLASSES = {0: "layer_gemm", 1: "adjoint_gemm", 2: "gram", 3: "elementwise", 4: "eig", 5: "precond"}
@@ -28,7 +29,7 @@ class KfacConfig(C.Structure):
         ("op", C.c_int), ("kappa", C.c_double), ("precision", C.c_int), ("variant", C.c_int),
         ("beta", C.c_double), ("lambda_", C.c_double), ("damping_sqrt", C.c_int),
         ("factor_init_identity", C.c_int), ("lr", C.c_double), ("momentum", C.c_double),
-        ("max_n_int", C.c_int), ("max_n_bdy", C.c_int), ("line_search", C.c_int),
+        ("max_n_int", C.c_int), ("max_n_bdy", C.c_int), ("update", C.c_int),
     ]
 
 
@@ -76,6 +77,7 @@ def load() -> C.CDLL:
         "kfac_pinn_get_gradient": (st, [H, P, P]),
         "kfac_pinn_get_direction": (st, [H, P, P]),
         "kfac_pinn_get_line_search_losses": (st, [H, P, P]),
+        "kfac_pinn_get_update_coefficients": (st, [H, P, P]),
         "kfac_pinn_sync_status": (st, [H, C.POINTER(C.c_int)]),
         "kfac_pinn_launch_count": (C.c_int64, [H]),
         "kfac_pinn_timing_enable": (st, [H, I]),

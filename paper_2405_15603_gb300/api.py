@@ -18,6 +18,7 @@ OPS = {"laplace": 0, "heat": 1}
 PRECISIONS = {"fp64": 0, "mixed_bf16": 1}
 VARIANTS = {"expand": 0, "reduce": 1}
 FACTORS = {"A_int": 0, "B_int": 1, "A_bdy": 2, "B_bdy": 3}
+UPDATES = {"fixed": 0, "line_search": 1, "kfac_star": 2}
 
 
 def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
@@ -44,7 +45,8 @@ def make_config(d: int, widths: Sequence[int], op: str = "laplace", kappa: float
                 precision: str = "fp64", variant: str = "expand", beta: float = 0.0,
                 lam: float = 1e-3, damping_sqrt: bool = False, init_identity: bool = False,
                 lr: float = 0.1, momentum: float = 0.0, max_n_int: int = 1024,
-                max_n_bdy: int = 1024, line_search: bool = False) -> KfacConfig:
+                max_n_bdy: int = 1024, line_search: bool = False, update: str = "fixed") -> KfacConfig:
+    """line_search=True is shorthand for update="line_search"."""
     cfg = KfacConfig()
     cfg.d = d
     cfg.L = len(widths)
@@ -62,7 +64,7 @@ def make_config(d: int, widths: Sequence[int], op: str = "laplace", kappa: float
     cfg.momentum = momentum
     cfg.max_n_int = max_n_int
     cfg.max_n_bdy = max_n_bdy
-    cfg.line_search = int(line_search)
+    cfg.update = UPDATES["line_search" if line_search else update]
     return cfg
 
 
@@ -198,6 +200,13 @@ class KfacPinn:
         """Trial losses of the last step's line search: (31, 3), row k at alpha = 2^-k."""
         out = torch.empty(31, 3, dtype=torch.float64, device=self.device)
         _check("kfac_pinn_get_line_search_losses", self.lib.kfac_pinn_get_line_search_losses(
+            self.h, _stream(), _ptr(out)))
+        return out
+
+    def update_coefficients(self) -> torch.Tensor:
+        """(c0, c1) of the last step's update delta = c0 Delta + c1 delta_prev."""
+        out = torch.empty(2, dtype=torch.float64, device=self.device)
+        _check("kfac_pinn_get_update_coefficients", self.lib.kfac_pinn_get_update_coefficients(
             self.h, _stream(), _ptr(out)))
         return out
 

@@ -23,7 +23,8 @@ bool valid_config(const kfac_config_t* c) {
     if (!(c->lambda > 0.0) || !isfinite(c->lambda)) return false;
     if (!isfinite(c->lr) || !isfinite(c->momentum) || !isfinite(c->kappa)) return false;
     if (c->max_n_int < 1 || c->max_n_bdy < 1) return false;
-    if (c->line_search != 0 && c->line_search != 1) return false;
+    if (c->update < KFAC_UPDATE_FIXED || c->update > KFAC_UPDATE_AUTO) return false;
+    if (c->update == KFAC_UPDATE_AUTO && c->precision != KFAC_FP64) return false;
     long long rows = (long long)(c->d + 2) * c->max_n_int;
     if (rows > (1LL << 30)) return false;
     return true;
@@ -63,6 +64,9 @@ void free_handle(kfac_pinn_handle* h) {
     cudaFree(h->dhat);
     cudaFree(h->trial);
     cudaFree(h->ls_loss);
+    cudaFree(h->ks_jv);
+    cudaFree(h->ks_part);
+    cudaFree(h->coef);
     for (int w = 0; w < 4; w++)
         for (int l = 0; l < KFAC_MAX_LAYERS; l++) cudaFree(h->fac[w][l]);
     for (int l = 0; l < KFAC_MAX_LAYERS; l++) {
@@ -314,11 +318,16 @@ kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out) {
     TRY(dalloc(&h->grad, (size_t)h->D));
     TRY(dalloc(&h->dir, (size_t)h->D));
     TRY(dalloc(&h->delta_prev, (size_t)h->D));
-    if (cfg->line_search) {
+    if (cfg->update == KFAC_UPDATE_LINE_SEARCH) {
         TRY(dalloc(&h->dhat, (size_t)h->D));
         TRY(dalloc(&h->trial, (size_t)h->D));
         TRY(dalloc(&h->ls_loss, 3 * 31));
     }
+    if (cfg->update == KFAC_UPDATE_AUTO) {
+        TRY(dalloc(&h->ks_jv, 2 * ((size_t)cfg->max_n_int + cfg->max_n_bdy)));
+        TRY(dalloc(&h->ks_part, linalg_auto_part_elems()));
+    }
+    TRY(dalloc(&h->coef, 8));
     size_t tmp = 0;
     for (int l = 1; l <= cfg->L; l++) {
         size_t na = h->dims[l - 1] + 1, nb = h->dims[l];
@@ -456,15 +465,26 @@ kfac_status_t kfac_pinn_step(kfac_handle_t h, void* stream, double* theta,
     if ((st = run_factors(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g, loss))) return st;
     if ((st = kfac_pinn_invert(h, stream))) return st;
     if ((st = kfac_pinn_precondition(h, stream, nullptr, nullptr))) return st;
-    if (!h->cfg.line_search) return kfac_pinn_update(h, stream, theta);
-    if ((st = linalg_line_search_update(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g))) return st;
+    if (h->cfg.update == KFAC_UPDATE_FIXED) return kfac_pinn_update(h, stream, theta);
+    if (h->cfg.update == KFAC_UPDATE_LINE_SEARCH)
+        st = linalg_line_search_update(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g);
+    else
+        st = linalg_auto_update(h, s, theta, X_int, N_int, X_bdy, N_bdy);
+    if (st) return st;
     h->t++;
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_get_update_coefficients(kfac_handle_t h, void* stream, double* dst) {
+    if (!h || !dst) return KFAC_BAD_ARG;
+    if (h->t == 0) return KFAC_NOT_READY;
+    KFAC_CUDA_TRY(cudaMemcpyAsync(dst, h->coef, 2 * sizeof(double), cudaMemcpyDeviceToDevice, S_(stream)));
     return KFAC_OK;
 }
 
 kfac_status_t kfac_pinn_get_line_search_losses(kfac_handle_t h, void* stream, double* dst) {
     if (!h || !dst) return KFAC_BAD_ARG;
-    if (!h->cfg.line_search || h->t == 0) return KFAC_NOT_READY;
+    if (h->cfg.update != KFAC_UPDATE_LINE_SEARCH || h->t == 0) return KFAC_NOT_READY;
     KFAC_CUDA_TRY(cudaMemcpyAsync(dst, h->ls_loss, 3 * 31 * sizeof(double), cudaMemcpyDeviceToDevice, S_(stream)));
     return KFAC_OK;
 }

@@ -107,6 +107,50 @@ __global__ void k_act_bwd(const double* __restrict__ Z, double* __restrict__ G,
     G[(S - 1) * blk + idx] = s1 * yd;
 }
 
+// Forward-mode derivative of k_act_fwd, in place on D (incoming da -> outgoing dy):
+//   dy_0 = s1 da_0
+//   dy_i = s2 da_0 a_i + s1 da_i
+//   dy_D = s2 da_0 a_D + s1 da_D + s3 da_0 sum_C a_i^2 + 2 s2 sum_C a_i da_i
+__global__ void k_act_jvp(const double* __restrict__ Z, double* __restrict__ Dz, int N, int S, int h,
+                          int lap_first) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long blk = (long long)N * h;
+    if (idx >= blk) return;
+    double y = tanh(Z[idx]);
+    double s1 = 1.0 - y * y;
+    double da0 = Dz[idx];
+    Dz[idx] = s1 * da0;
+    if (S == 1) return;
+    double s2 = -2.0 * y * s1;
+    double s3 = -2.0 * s1 * (1.0 - 3.0 * y * y);
+    double sumsq = 0.0, cross = 0.0;
+    for (int s = 1; s < S - 1; s++) {
+        double a = Z[s * blk + idx];
+        double da = Dz[s * blk + idx];
+        Dz[s * blk + idx] = fma(s2 * da0, a, s1 * da);
+        if (s >= lap_first) {
+            sumsq = fma(a, a, sumsq);
+            cross = fma(a, da, cross);
+        }
+    }
+    double aD = Z[(S - 1) * blk + idx];
+    double daD = Dz[(S - 1) * blk + idx];
+    Dz[(S - 1) * blk + idx] = s2 * da0 * aD + s1 * daD + s3 * da0 * sumsq + 2.0 * s2 * cross;
+}
+
+// Directional derivative of the residuals: the residual rule applied to dZ^{(L)}
+// (the data f, g do not depend on theta).
+__global__ void k_residual_jvp(const double* __restrict__ dZL, double* __restrict__ jv, int N, int S,
+                               int interior, int heat, double kappa) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double v;
+    if (!interior) v = dZL[n];
+    else if (heat) v = dZL[N + n] - kappa * dZL[(long long)(S - 1) * N + n];
+    else v = -dZL[(long long)(S - 1) * N + n];
+    jv[n] = v;
+}
+
 // Residuals (Eq. 1): interior r = -Lap u - f, or du/dt - kappa Lap_x u - f
 // for the heat operator; boundary r = u - g.  Z_L has one feature per row.
 __global__ void k_residual(const double* __restrict__ ZL, const double* __restrict__ target,
@@ -439,6 +483,62 @@ kfac_status_t fp64_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t 
         st = dgemm_strided(h, s, N, d, h1, h->in.Zb[0], h1, 1, theta, 1, h1, dX, d, 1, 1.0, 0.0);
         if (st) return st;
     }
+    return KFAC_OK;
+}
+
+// J_theta r . v for one pass whose forward activations (Z, T) at theta are in
+// pb: the Taylor pass differentiated in the direction v (Sec. 3.1-3.2),
+//   dZ^{(1)} = dW~_1 T^^{(0)},  dZ^{(l)} = dW~_l T^^{(l-1)} + W_l dT^{(l-1)},
+// with dT from the linearised tanh rule.  Overwrites pb.Zb; jv: N doubles.
+kfac_status_t fp64_jvp(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* v,
+                       const double* X, int N, PassBuffers& pb, int S, bool interior, double* jv) {
+    const int L = h->cfg.L, d = h->dims[0];
+    const int lap_first = (h->cfg.op == KFAC_OP_HEAT) ? 2 : 1;
+    {
+        const int h1 = h->dims[1];
+        long long cnt = (long long)N * h1;
+        k_layer1_fwd<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(v + h->woff[0], X, pb.Zb[0], nullptr, N, d,
+                                                                         h1, S, lap_first, 0);
+        KFAC_LAUNCH_CHECK(h);
+        if (L > 1) {
+            k_act_jvp<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[0], pb.Zb[0], N, S, h1, lap_first);
+            KFAC_LAUNCH_CHECK(h);
+        }
+    }
+    for (int l = 2; l <= L; l++) {
+        const int hin = h->dims[l - 1], hout = h->dims[l];
+        const double* W = theta + h->woff[l - 1];
+        const double* V = v + h->woff[l - 1];
+        // dZ = T dW^T (+ db on the value rows)
+        {
+            Strided<true> A{pb.T[l - 2], hin, 1};
+            Strided<true> B{V, hout, 1};
+            EpStore ep{pb.Zb[l - 1], hout, 1, 1.0, 0.0, V + (long long)hout * hin, 1, N};
+            timer_begin(h, KFAC_KC_LAYER_GEMM, s);
+            if (cudaSuccess != launch_dgemm(s, S * N, hout, hin, 1, A, B, ep)) return KFAC_CUDA_ERROR;
+            timer_end(h, KFAC_KC_LAYER_GEMM, s, 2.0 * S * N * (double)hout * hin);
+            h->launches++;
+        }
+        // dZ += dT W^T
+        {
+            Strided<true> A{pb.Zb[l - 2], hin, 1};
+            Strided<true> B{W, hout, 1};
+            EpStore ep{pb.Zb[l - 1], hout, 1, 1.0, 1.0, nullptr, 0, 0};
+            timer_begin(h, KFAC_KC_LAYER_GEMM, s);
+            if (cudaSuccess != launch_dgemm(s, S * N, hout, hin, 1, A, B, ep)) return KFAC_CUDA_ERROR;
+            timer_end(h, KFAC_KC_LAYER_GEMM, s, 2.0 * S * N * (double)hout * hin);
+            h->launches++;
+        }
+        if (l < L) {
+            long long cnt = (long long)N * hout;
+            k_act_jvp<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[l - 1], pb.Zb[l - 1], N, S, hout,
+                                                                         lap_first);
+            KFAC_LAUNCH_CHECK(h);
+        }
+    }
+    k_residual_jvp<<<ceil_div_u(N, EW_THREADS), EW_THREADS, 0, s>>>(pb.Zb[L - 1], jv, N, S, interior,
+                                                                    h->cfg.op == KFAC_OP_HEAT, h->cfg.kappa);
+    KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }
 

@@ -51,6 +51,9 @@ struct kfac_pinn_handle {
     double* dhat;         // D: momentum direction of the line search
     double* trial;        // D: trial parameters of the line search
     double* ls_loss;      // 3 x 31 trial losses
+    double* ks_jv;        // residual JVPs of the automatic update (2 (max_n_int + max_n_bdy))
+    double* ks_part;      // block partial sums of the automatic update
+    double* coef;         // (c0, c1) of the last update delta = c0 Delta + c1 delta_prev, + diagnostics
     double* fac[4][KFAC_MAX_LAYERS];      // EMA factors A_int, B_int, A_bdy, B_bdy (n x n)
     double* VA[KFAC_MAX_LAYERS];          // generalized eigenvectors (na x na, row-major)
     double* wa[KFAC_MAX_LAYERS];          // generalized eigenvalues (na)
@@ -130,6 +133,11 @@ kfac_status_t fp64_loss_to(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N
 kfac_status_t fp64_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int,
                              int N_int, const double* f, const double* X_bdy, int N_bdy, const double* g,
                              double* dst);
+kfac_status_t fp64_jvp(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* v,
+                       const double* X, int N, PassBuffers& pb, int S, bool interior, double* jv);
+// Automatic learning rate and momentum (linalg.cu), FP64 handles
+kfac_status_t linalg_auto_update(kfac_pinn_handle* h, cudaStream_t s, double* theta, const double* X_int,
+                                 int N_int, const double* X_bdy, int N_bdy);
 // Line-search update (linalg.cu): theta += alpha* dhat, alpha* from the grid 2^-k
 kfac_status_t linalg_line_search_update(kfac_pinn_handle* h, cudaStream_t s, double* theta, const double* X_int,
                                         int N_int, const double* f, const double* X_bdy, int N_bdy,
@@ -144,6 +152,7 @@ kfac_status_t fp64_extract_outputs(kfac_pinn_handle* h, cudaStream_t s, PassBuff
 // Linear algebra (linalg.cu)
 // ---------------------------------------------------------------------------
 size_t linalg_workspace_elems(const kfac_pinn_handle* h);
+size_t linalg_auto_part_elems();
 // Batched FP64 generalized eigensolver (eig.cu)
 kfac_status_t eig_alloc(kfac_pinn_handle* h);
 void eig_free(kfac_pinn_handle* h);

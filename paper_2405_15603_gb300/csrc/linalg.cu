@@ -19,8 +19,12 @@ __global__ void k_div_kron(double* Y, int nb, int na, const double* wb, const do
 
 // delta = lr (mu delta_prev + Delta); theta += delta (Sec. 3.4, fixed learning rate).
 __global__ void k_update(double* theta, const double* dir, double* delta_prev, long long D, double lr,
-                         double mom) {
+                         double mom, double* coef) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        coef[0] = lr;
+        coef[1] = lr * mom;
+    }
     if (i >= D) return;
     double dlt = lr * (mom * delta_prev[i] + dir[i]);
     delta_prev[i] = dlt;
@@ -61,7 +65,7 @@ __device__ int ls_argmin(const double* ls_loss) {
 
 // delta = alpha* dhat; theta += delta.
 __global__ void k_ls_apply(double* theta, const double* dhat, double* delta_prev, long long D,
-                           const double* ls_loss, int* status) {
+                           const double* ls_loss, int* status, double mom, double* coef) {
     __shared__ int best;
     if (threadIdx.x == 0) {
         best = ls_argmin(ls_loss);
@@ -69,12 +73,122 @@ __global__ void k_ls_apply(double* theta, const double* dhat, double* delta_prev
     }
     __syncthreads();
     const double alpha = best < 0 ? 0.0 : ldexp(1.0, -best);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        coef[0] = alpha;
+        coef[1] = alpha * mom;
+    }
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < D;
          i += (long long)gridDim.x * blockDim.x) {
         double dlt = alpha * dhat[i];
         delta_prev[i] = dlt;
         theta[i] += dlt;
     }
+}
+
+// KFAC*: (alpha*, mu*) = argmin of the quadratic model
+//   m(alpha Delta + mu delta) = L + (alpha Delta + mu delta)^T g
+//                              + 1/2 (alpha Delta + mu delta)^T (G + lambda I) (alpha Delta + mu delta)
+// (Sec. 3.4), with v^T G w = (1/N) sum_n (J_n v)(J_n w) + (1/N_b) sum_b (J_b v)(J_b w)
+// (Eq. 2) from the residual JVPs.  Eleven sums, reduced in a fixed order.
+constexpr int KS_BLOCKS = 256;
+constexpr int KS_Q = 11;
+
+__device__ double ks_block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x / 32); w++) t += sh[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(256) k_ks_dots(const double* __restrict__ Dl, const double* __restrict__ dl,
+                                                 const double* __restrict__ g, long long D,
+                                                 const double* __restrict__ jDi, const double* __restrict__ jdi,
+                                                 int Ni, const double* __restrict__ jDb,
+                                                 const double* __restrict__ jdb, int Nb, int have_prev,
+                                                 double* part) {
+    __shared__ double sh[8];
+    double acc[KS_Q];
+#pragma unroll
+    for (int q = 0; q < KS_Q; q++) acc[q] = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long i = i0; i < D; i += stride) {
+        const double a = Dl[i], b = have_prev ? dl[i] : 0.0, gi = g[i];
+        acc[0] = fma(a, a, acc[0]);
+        acc[1] = fma(a, b, acc[1]);
+        acc[2] = fma(b, b, acc[2]);
+        acc[3] = fma(a, gi, acc[3]);
+        acc[4] = fma(b, gi, acc[4]);
+    }
+    for (long long i = i0; i < Ni; i += stride) {
+        const double a = jDi[i], b = have_prev ? jdi[i] : 0.0;
+        acc[5] = fma(a, a, acc[5]);
+        acc[6] = fma(a, b, acc[6]);
+        acc[7] = fma(b, b, acc[7]);
+    }
+    for (long long i = i0; i < Nb; i += stride) {
+        const double a = jDb[i], b = have_prev ? jdb[i] : 0.0;
+        acc[8] = fma(a, a, acc[8]);
+        acc[9] = fma(a, b, acc[9]);
+        acc[10] = fma(b, b, acc[10]);
+    }
+#pragma unroll
+    for (int q = 0; q < KS_Q; q++) {
+        double t = ks_block_sum(acc[q], sh);
+        if (threadIdx.x == 0) part[(long long)blockIdx.x * KS_Q + q] = t;
+    }
+}
+
+__global__ void k_ks_solve(const double* __restrict__ part, int nblocks, int Ni, int Nb, double lam, int have_prev,
+                           double* coef, int* status) {
+    __shared__ double tot[KS_Q];
+    if (threadIdx.x < KS_Q) {
+        double t = 0.0;
+        for (int b = 0; b < nblocks; b++) t += part[(long long)b * KS_Q + threadIdx.x];
+        tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double a11 = tot[5] / Ni + tot[8] / Nb + lam * tot[0];
+    const double b1 = tot[3];
+    double alpha, mu = 0.0, a12 = 0.0, a22 = 0.0, b2 = 0.0;
+    if (have_prev && tot[2] > 0.0) {
+        a12 = tot[6] / Ni + tot[9] / Nb + lam * tot[1];
+        a22 = tot[7] / Ni + tot[10] / Nb + lam * tot[2];
+        b2 = tot[4];
+        const double det = a11 * a22 - a12 * a12;
+        alpha = -(a22 * b1 - a12 * b2) / det;
+        mu = -(a11 * b2 - a12 * b1) / det;
+    } else {
+        alpha = -b1 / a11;
+    }
+    if (!(a11 > 0.0) || !isfinite(alpha) || !isfinite(mu)) {
+        latch_status(status, KFAC_NONFINITE);
+        alpha = 0.0;
+        mu = 0.0;
+    }
+    coef[0] = alpha;
+    coef[1] = mu;
+    coef[2] = a11;
+    coef[3] = a12;
+    coef[4] = a22;
+    coef[5] = b1;
+    coef[6] = b2;
+}
+
+// delta = alpha* Delta + mu* delta_prev; theta += delta.
+__global__ void k_ks_apply(double* theta, const double* __restrict__ Dl, double* delta_prev, long long D,
+                           const double* __restrict__ coef) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= D) return;
+    const double dlt = coef[0] * Dl[i] + coef[1] * delta_prev[i];
+    delta_prev[i] = dlt;
+    theta[i] += dlt;
 }
 
 kfac_status_t precondition_impl(kfac_pinn_handle* h, cudaStream_t s, const double* grad, double* dir) {
@@ -138,7 +252,7 @@ kfac_status_t linalg_precondition(kfac_pinn_handle* h, cudaStream_t s, const dou
 
 kfac_status_t linalg_update(kfac_pinn_handle* h, cudaStream_t s, double* theta) {
     k_update<<<ceil_div_u(h->D, 256), 256, 0, s>>>(theta, h->dir, h->delta_prev, h->D, h->cfg.lr,
-                                                   h->cfg.momentum);
+                                                   h->cfg.momentum, h->coef);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }
@@ -159,7 +273,35 @@ kfac_status_t linalg_line_search_update(kfac_pinn_handle* h, cudaStream_t s, dou
         if (st) return st;
     }
     unsigned ab = blocks < (unsigned)(4 * h->sm_count) ? blocks : (unsigned)(4 * h->sm_count);
-    k_ls_apply<<<ab, 256, 0, s>>>(theta, h->dhat, h->delta_prev, h->D, h->ls_loss, h->status);
+    k_ls_apply<<<ab, 256, 0, s>>>(theta, h->dhat, h->delta_prev, h->D, h->ls_loss, h->status, h->cfg.momentum,
+                                  h->coef);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+size_t linalg_auto_part_elems() { return (size_t)KS_BLOCKS * KS_Q; }
+
+kfac_status_t linalg_auto_update(kfac_pinn_handle* h, cudaStream_t s, double* theta, const double* X_int,
+                                 int N_int, const double* X_bdy, int N_bdy) {
+    if (h->cfg.precision != KFAC_FP64) return KFAC_BAD_ARG;
+    double* jDi = h->ks_jv;
+    double* jDb = jDi + h->cfg.max_n_int;
+    double* jdi = jDb + h->cfg.max_n_bdy;
+    double* jdb = jdi + h->cfg.max_n_int;
+    const int have_prev = h->t > 0;
+    kfac_status_t st;
+    if ((st = fp64_jvp(h, s, theta, h->dir, X_int, N_int, h->in, h->S, true, jDi))) return st;
+    if ((st = fp64_jvp(h, s, theta, h->dir, X_bdy, N_bdy, h->bd, 1, false, jDb))) return st;
+    if (have_prev) {
+        if ((st = fp64_jvp(h, s, theta, h->delta_prev, X_int, N_int, h->in, h->S, true, jdi))) return st;
+        if ((st = fp64_jvp(h, s, theta, h->delta_prev, X_bdy, N_bdy, h->bd, 1, false, jdb))) return st;
+    }
+    k_ks_dots<<<KS_BLOCKS, 256, 0, s>>>(h->dir, h->delta_prev, h->grad, h->D, jDi, jdi, N_int, jDb, jdb, N_bdy,
+                                        have_prev, h->ks_part);
+    KFAC_LAUNCH_CHECK(h);
+    k_ks_solve<<<1, 32, 0, s>>>(h->ks_part, KS_BLOCKS, N_int, N_bdy, h->cfg.lambda, have_prev, h->coef, h->status);
+    KFAC_LAUNCH_CHECK(h);
+    k_ks_apply<<<ceil_div_u(h->D, 256), 256, 0, s>>>(theta, h->dir, h->delta_prev, h->D, h->coef);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }

@@ -1,0 +1,81 @@
+"""GPU parity of KFAC* (Sec. 3.4): δ_t = α* Δ_t + μ* δ_{t-1} with (α*, μ*)
+minimising the quadratic model with the exact damped Gramian, formed on the
+device from two residual Jacobian-vector products (the Taylor pass in
+forward mode).  FP64 path against the oracle, whose Gramian products come
+from per-point weight Jacobians instead."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import kfac_oracle as ko
+from synth import inputs as si
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+CASES = [
+    ("poisson2d_2-32-32-1", si.PROBLEMS["poisson2d_sin"], (32, 32, 1), 300, 80, "expand"),
+    ("poisson5d_5-64-64-48-48-1_reduce", si.PROBLEMS["poisson5d_cos"], (64, 64, 48, 48, 1), 200, 50, "reduce"),
+    ("heat4d_5-128-128-64-1", si.PROBLEMS["heat4d_sin"], (128, 128, 64, 1), 120, 60, "expand"),
+    ("ragged_7-40-72-1", si.poisson_cos_problem(7), (40, 72, 1), 67, 13, "expand"),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_kfac_star_steps_fp64(case):
+    from paper_2405_15603_gb300.api import KfacPinn
+    _, prob, widths, N, Nb, variant = case
+    kw = dict(beta=0.9, lam=1e-3, init_identity=True, variant=variant)
+    cfg = ko.KfacConfig(d=prob.d, widths=widths, op=prob.op, kappa=prob.kappa, kfac_star=True, **kw)
+    st = ko.init_state(cfg)
+    opt = KfacPinn(prob.d, widths, device=DEV, op=prob.op, kappa=prob.kappa, max_n_int=N, max_n_bdy=Nb,
+                   update="kfac_star", **kw)
+    th = si.xavier_theta(prob.d, widths, 0)
+    for step in range(3):
+        Xi, f, Xb, g = si.make_batch(prob, N, Nb, seed=6, step=step)
+        res = ko.kfac_step(cfg, st, th, Xi, f, Xb, g)
+        theta = torch.tensor(th, device=DEV)
+        loss = opt.step(theta, Xi, f, Xb, g)
+        coef = opt.update_coefficients().cpu().numpy()
+        torch.cuda.synchronize()
+        assert rel(loss.cpu().numpy(), np.array(res.loss)) < 1e-10
+        np.testing.assert_allclose(coef[0], res.extras["alpha"], rtol=1e-9)
+        if step == 0:
+            assert coef[1] == 0.0
+        else:
+            np.testing.assert_allclose(coef[1], res.extras["mu"], rtol=1e-8, atol=1e-12)
+        assert rel(theta.cpu().numpy() - th, res.theta_new - th) < 1e-8
+        th = res.theta_new
+    assert opt.sync_status() == "KFAC_OK"
+
+
+def test_kfac_star_requires_fp64():
+    from paper_2405_15603_gb300.api import KfacPinn, KfacError
+    with pytest.raises(KfacError):
+        KfacPinn(2, (16, 1), device=DEV, precision="mixed_bf16", update="kfac_star", max_n_int=8, max_n_bdy=8)
+
+
+def test_update_coefficients_of_fixed_and_line_search_rules():
+    from paper_2405_15603_gb300.api import KfacPinn, KfacError
+    prob = si.PROBLEMS["poisson2d_sin"]
+    widths = (16, 16, 1)
+    Xi, f, Xb, g = si.make_batch(prob, 60, 20, seed=7)
+    th = si.xavier_theta(prob.d, widths, 3)
+    fixed = KfacPinn(prob.d, widths, device=DEV, max_n_int=60, max_n_bdy=20, lr=0.25, momentum=0.5)
+    with pytest.raises(KfacError):
+        fixed.update_coefficients()
+    fixed.step(torch.tensor(th, device=DEV), Xi, f, Xb, g)
+    assert fixed.update_coefficients().cpu().numpy().tolist() == [0.25, 0.125]
+    ls = KfacPinn(prob.d, widths, device=DEV, max_n_int=60, max_n_bdy=20, momentum=0.5, update="line_search")
+    ls.step(torch.tensor(th, device=DEV), Xi, f, Xb, g)
+    c = ls.update_coefficients().cpu().numpy()
+    k = int(np.argmin(ls.line_search_losses().cpu().numpy()[:, 0]))
+    assert c.tolist() == [2.0 ** -k, 0.5 * 2.0 ** -k]
