@@ -373,6 +373,93 @@ def run_reference(args, rank, world):
     }
 
 
+# ---------------------------------------------------------------------------
+# Forward Laplacian vs autodiff Laplacian (App. C.4): time and peak memory
+# ---------------------------------------------------------------------------
+E10_WIDTHS = (768, 768, 512, 512, 1)
+E10_N = 1024
+
+
+def run_e10(reps=5):
+    """Time and device memory of one forward Laplacian over N = 1024 points of
+    the d -> 768 -> 768 -> 512 -> 512 -> 1 tanh MLP for d in {1, 10, 100}:
+    this library (FP64 and mixed precision) beside torch's functorch Hessian
+    trace (vmap of hessian, FP64) on the same GPU, the comparison of App. C.4."""
+    import torch
+    from paper_2405_15603_gb300 import build as _build
+    _build.build()
+    from paper_2405_15603_gb300.api import KfacPinn
+    dev = torch.device("cuda:0")
+    rows = []
+    for d in (1, 10, 100):
+        prob = si.poisson_norm_problem(d)
+        X = torch.tensor(si.sample_interior(E10_N, d, np.random.default_rng(d)), device=dev)
+        th = torch.tensor(si.xavier_theta(d, E10_WIDTHS, d), device=dev)
+        row = {"d": d, "N": E10_N}
+        for prec in ("fp64", "mixed_bf16"):
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
+            opt = KfacPinn(d, E10_WIDTHS, device=str(dev), precision=prec, max_n_int=E10_N, max_n_bdy=1)
+            torch.cuda.synchronize()
+            held = free0 - torch.cuda.mem_get_info()[0]
+            opt.forward_laplacian(th, X)
+            times = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                u, g, lap = opt.forward_laplacian(th, X)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+            row[f"ours_{prec}_s"] = min(times)
+            row[f"ours_{prec}_handle_gib"] = held / 2 ** 30
+            opt.close()
+            del u, g, lap
+        # functorch autodiff Laplacian: trace of the per-point Hessian
+        Ws = []
+        dims = [d] + list(E10_WIDTHS)
+        off = 0
+        for l in range(1, len(dims)):
+            r, c = dims[l], dims[l - 1] + 1
+            Ws.append(th[off:off + r * c].reshape(c, r).T)
+            off += r * c
+
+        def net(x):
+            z = x
+            for l, W in enumerate(Ws):
+                z = W[:, :-1] @ z + W[:, -1]
+                if l < len(Ws) - 1:
+                    z = torch.tanh(z)
+            return z[0]
+
+        lap_fn = torch.vmap(lambda x: torch.func.hessian(net)(x).diagonal().sum())
+        lap_fn(X)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            torch.cuda.reset_peak_memory_stats()
+            base = torch.cuda.memory_allocated()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ref = lap_fn(X)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            peak = torch.cuda.max_memory_allocated() - base
+        row["autodiff_fp64_s"] = min(times)
+        row["autodiff_fp64_peak_gib"] = peak / 2 ** 30
+        opt = KfacPinn(d, E10_WIDTHS, device=str(dev), precision="fp64", max_n_int=E10_N, max_n_bdy=1)
+        _, _, lap = opt.forward_laplacian(th, X)
+        row["max_rel_diff_vs_autodiff"] = float((lap - ref).abs().max() / ref.abs().max())
+        opt.close()
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    return {"metric": "forward Laplacian time [s] and device memory [GiB], N=1024, d->768->768->512->512->1",
+            "unit": "s", "higher_is_better": False, "rows": rows,
+            "paper_context": "App. C.4 (RTX 6000, FP64): forward 0.033/0.10/0.84 s vs autodiff 0.051/0.20/1.7 s "
+                             "for d = 1/10/100"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,6 +469,8 @@ def main():
     ap.add_argument("--precision", default="mixed_bf16", choices=["fp64", "mixed_bf16"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e10", action="store_true",
+                    help="forward vs autodiff Laplacian time and memory (App. C.4) instead of the step bench")
     ap.add_argument("--points", default=None,
                     help="N_INT,N_BDY override (smaller cases for profiler captures; not the headline)")
     args = ap.parse_args()
@@ -390,8 +479,11 @@ def main():
         ni, nb = (int(v) for v in args.points.split(","))
         WORKLOAD = dataclasses.replace(WORKLOAD, n_int=ni, n_bdy=nb)
         WORKLOAD_NAME = f"poisson100d_100-768-768-512-512-1_{ni}int_{nb}bdy_resampled"
+    if args.e10:
+        print(json.dumps(run_e10()), flush=True)
+        return
     if args.steps is None:
-        args.steps = 5 if args.precision == "fp64" else 30
+        args.steps = 2 if args.precision == "fp64" else 30
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -37,7 +37,7 @@ struct Prob {
     double* w;
     double *L, *M, *Qa, *Qb, *R, *R2, *H;  // n x n row-major (H: Householder vectors, one per row)
     double* Ld;                            // inverses of the 64 x 64 diagonal blocks of L (n x 64)
-    double *d, *e, *tau, *D, *pbuf;        // n
+    double *d, *e, *tau, *D, *pbuf, *pbuf2;  // n
     double *Ds, *zs, *dK, *zK, *tauR, *zh, *rc, *rs, *val; // n (per-merge scratch at offset a)
     int *perm, *defl, *Kidx, *org, *rj, *ri, *col;          // n
     int *mk, *mnrot, *mflip;               // per merge (indexed by block start a)
@@ -467,6 +467,37 @@ __device__ bool group_barrier(unsigned* bar, int g, int* abort_flag) {
     return ok != 0;
 }
 
+// Waits (bounded, thread 0) until the pivot row `k` has been published.
+__device__ bool wait_row(const unsigned* ready, unsigned k, int* abort_flag) {
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const volatile unsigned* vr = ready;
+        uint64_t t0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        for (unsigned it = 0; *vr < k; it++) {
+            if (*(volatile int*)abort_flag) { ok = 0; break; }
+            if ((it & 63u) == 0) {
+                uint64_t t1;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+                if (t1 - t0 > 2000000000ull) { ok = 0; atomicExch(abort_flag, 1); break; }
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Householder tridiagonalisation of M (full symmetric storage), one problem
+// per CTA group.  Row r belongs to CTA (r mod g) for the whole reduction, and
+// within it to warp ((r div g) mod nwarps), so the matrix-vector product and
+// the rank-2 update of a row are done by the same threads.  Per column k:
+// read the published pivot row k, form the reflector (redundantly in every
+// CTA), p = tau M v on owned rows, one group barrier to exchange p, then the
+// rank-2 update of owned rows; the owner of row k+1 updates it first and
+// publishes it through a counter, which replaces a second barrier.
 __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, const int* cta_rank,
                                                  const int* group, unsigned* bars, int* abort_flag, int* status,
                                                  int* fail) {
@@ -478,15 +509,17 @@ __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, 
     const int g = group[pi];
     const Prob p = pr[pi];
     const int n = p.n;
-    unsigned* bar = bars + 2 * pi;
+    unsigned* bar = bars + 3 * pi;
+    unsigned* ready = bar + 2;
     double* M = p.M;
     if (fail[pi]) return;   // uniform over the group
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
     bool alive = true;
     for (int k = 0; k + 2 < n && alive; k++) {
         const int b = k + 1, m = n - b;
-        // Householder vector from row k (= column k, the matrix is kept in full
-        // symmetric storage), computed redundantly by every CTA of the group
+        double* pb = (k & 1) ? p.pbuf2 : p.pbuf;
+        if (k > 0 && !wait_row(ready, (unsigned)k, abort_flag)) { alive = false; break; }
+        // reflector from the published row k (= column k)
         const double* rowk = M + (long long)k * n + b;
         double part = 0.0;
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -511,35 +544,56 @@ __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, 
         __syncthreads();
         if (tk == 0.0) {
             if (rank == 0 && threadIdx.x == 0) { p.tau[k] = 0.0; p.e[k] = beta; }
+            if (rank == b % g && threadIdx.x == 0) {    // row b is unchanged: publish it as is
+                __threadfence();
+                atomicExch(ready, (unsigned)b);
+            }
             continue;     // every CTA of the group skips the same step
         }
-        // p_i = tau sum_j M[b+i][b+j] v_j for owned rows (one warp per row)
-        for (int i = rank + warp * g; i < m; i += g * nwarps) {
-            const double* row = M + (long long)(b + i) * n + b;
+        // p_r = tau sum_j M[r][b+j] v_j for owned rows r >= b
+        for (int t = warp;; t += nwarps) {
+            const int r = rank + g * t;
+            if (r >= n) break;
+            if (r < b) continue;
+            const double* row = M + (long long)r * n + b;
             double acc = 0.0;
             for (int j = lane; j < m; j += 32) acc = fma(row[j], v[j], acc);
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-            if (lane == 0) p.pbuf[i] = tk * acc;
+            if (lane == 0) pb[r - b] = tk * acc;
         }
         if (!group_barrier(bar, g, abort_flag)) { alive = false; break; }
         double kp = 0.0;
         for (int j = threadIdx.x; j < m; j += blockDim.x) {
-            double pj = __ldcg(p.pbuf + j);
+            double pj = __ldcg(pb + j);
             w[j] = pj;
             kp = fma(pj, v[j], kp);
         }
         const double K = 0.5 * tk * block_reduce_sum(kp, sh);
         for (int j = threadIdx.x; j < m; j += blockDim.x) w[j] -= K * v[j];
         __syncthreads();
-        // rank-2 update of the owned rows
-        for (int i = rank + warp * g; i < m; i += g * nwarps) {
-            double* row = M + (long long)(b + i) * n + b;
-            const double vi = v[i], wi = w[i];
+        // the next pivot row first (all threads of its owner), then publish it
+        if (rank == b % g) {
+            double* row = M + (long long)b * n + b;
+            const double v0 = v[0], w0 = w[0];
+            for (int j = threadIdx.x; j < m; j += blockDim.x) row[j] -= v0 * w[j] + w0 * v[j];
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicExch(ready, (unsigned)b);
+        }
+        // rank-2 update of the other owned rows
+        for (int t = warp;; t += nwarps) {
+            const int r = rank + g * t;
+            if (r >= n) break;
+            if (r <= b) continue;
+            double* row = M + (long long)r * n + b;
+            const double vi = v[r - b], wi = w[r - b];
             for (int j = lane; j < m; j += 32) row[j] -= vi * w[j] + wi * v[j];
         }
         if (rank == 0 && threadIdx.x == 0) { p.tau[k] = tk; p.e[k] = beta; }
-        if (!group_barrier(bar, g, abort_flag)) { alive = false; break; }
+        __syncthreads();
     }
+    // every update must be in place before the diagonal is read
+    if (alive && !group_barrier(bar, g, abort_flag)) alive = false;
     if (!alive) {
         if (threadIdx.x == 0) latch_status(status, KFAC_TIMEOUT);
         return;
@@ -958,35 +1012,50 @@ __global__ void k_dc_copy(const Copy* cp, int n_cp) {
 // --------------------------------------------------------------------------
 // 5. back-transformation: U <- H_0 H_1 .. H_{n-3} U, columns in parallel
 // --------------------------------------------------------------------------
+// Shared memory of k_backtransform for matrices up to n: the CTA's column
+// slice of U (n x BT_COLS), the current reflector (n) and the dot partials.
+inline size_t bt_smem_bytes(int n) {
+    return sizeof(double) * ((size_t)n * BT_COLS + (size_t)n + 16 * (BT_COLS + 1));
+}
+
+// U <- H_0 H_1 .. H_{n-3} U.  Each CTA holds BT_COLS columns of U in shared
+// memory for the whole sequence of reflectors, so the FP64 FMAs (the bound on
+// this part) read operands from shared memory; the reflectors are read once
+// per CTA from L2.
 __global__ void __launch_bounds__(256) k_backtransform(Prob* pr, int* fail) {
-    __shared__ double v[1024];
-    __shared__ double part[16][BT_COLS + 1];
+    extern __shared__ double bt_sm[];
     const Prob p = pr[blockIdx.y];
     const int n = p.n;
     if (fail[blockIdx.y]) return;
     const int c0 = blockIdx.x * BT_COLS;
     if (c0 >= n) return;
+    double* Us = bt_sm;                          // n x BT_COLS
+    double* v = Us + (size_t)n * BT_COLS;        // n
+    double (*part)[BT_COLS + 1] = reinterpret_cast<double (*)[BT_COLS + 1]>(v + n);
     double* U = p.final_buf ? p.Qb : p.Qa;
     const int cl = threadIdx.x % BT_COLS, rg = threadIdx.x / BT_COLS;   // 16 row groups
     const int c = c0 + cl;
+    for (int i = rg; i < n; i += 16) Us[i * BT_COLS + cl] = (c < n) ? U[(long long)i * n + c] : 0.0;
     for (int k = n - 3; k >= 0; k--) {
         const double tk = p.tau[k];
         if (tk == 0.0) continue;
         const int b = k + 1, m = n - b;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = p.H[(long long)k * n + b + i];
+        __syncthreads();                         // previous reflector fully applied
+        for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = __ldcg(p.H + (long long)k * n + b + i);
         __syncthreads();
         double dot = 0.0;
-        if (c < n)
-            for (int i = rg; i < m; i += 16) dot = fma(v[i], U[(long long)(b + i) * n + c], dot);
+        for (int i = rg; i < m; i += 16) dot = fma(v[i], Us[(b + i) * BT_COLS + cl], dot);
         part[rg][cl] = dot;
         __syncthreads();
         double tot = 0.0;
+#pragma unroll
         for (int q = 0; q < 16; q++) tot += part[q][cl];
         tot *= tk;
-        if (c < n)
-            for (int i = rg; i < m; i += 16) U[(long long)(b + i) * n + c] -= tot * v[i];
-        __syncthreads();
+        for (int i = rg; i < m; i += 16) Us[(b + i) * BT_COLS + cl] -= tot * v[i];
     }
+    __syncthreads();
+    if (c < n)
+        for (int i = rg; i < n; i += 16) U[(long long)i * n + c] = Us[i * BT_COLS + cl];
 }
 
 __global__ void k_write_w(Prob* pr, int* fail, int* status) {
@@ -1061,6 +1130,7 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
             double** dv[] = {&p.d, &p.e, &p.tau, &p.D, &p.pbuf, &p.Ds, &p.zs, &p.dK, &p.zK, &p.tauR, &p.zh,
                              &p.rc, &p.rs, &p.val, &p.mrh};
             for (double** q : dv) { *q = dp; dp += n; }
+            p.pbuf2 = dp;
             dp += 5 * (size_t)n;
             int** iv[] = {&p.perm, &p.defl, &p.Kidx, &p.org, &p.rj, &p.ri, &p.col, &p.mk, &p.mnrot, &p.mflip};
             for (int** q : iv) { *q = ip; ip += n; }
@@ -1073,7 +1143,7 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
     if (cudaMemcpy(es->dev, es->host, sizeof(Prob) * es->np, cudaMemcpyHostToDevice) != cudaSuccess)
         return KFAC_CUDA_ERROR;
     if ((st = dal(&es->fail, (size_t)es->np))) return st;
-    if ((st = dal(&es->bar, 2 * (size_t)es->np))) return st;
+    if ((st = dal(&es->bar, 3 * (size_t)es->np))) return st;
     if ((st = dal(&es->abort_flag, 1))) return st;
     cudaMemset(es->fail, 0, sizeof(int) * es->np);
 
@@ -1179,6 +1249,8 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
                          (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB + 1)));
     cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(double) * 2 * NB * (NB + 1));
+    if (bt_smem_bytes(es->nmax) > 220 * 1024) return KFAC_BAD_ARG;
+    cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem_bytes(es->nmax));
     return cudaGetLastError() == cudaSuccess ? KFAC_OK : KFAC_CUDA_ERROR;
 }
 
@@ -1238,7 +1310,7 @@ kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
     k_symmetrize<<<dim3(64, np), 256, 0, s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
     // 3. tridiagonalisation (cooperative: the groups wait on each other)
-    KFAC_CUDA_TRY(cudaMemsetAsync(es->bar, 0, sizeof(unsigned) * 2 * np, s));
+    KFAC_CUDA_TRY(cudaMemsetAsync(es->bar, 0, sizeof(unsigned) * 3 * np, s));
     KFAC_CUDA_TRY(cudaMemsetAsync(es->abort_flag, 0, sizeof(int), s));
     {
         void* args[] = {&pr, &es->cta_prob, &es->cta_rank, &es->group, &es->bar, &es->abort_flag, &h->status,
@@ -1276,7 +1348,7 @@ kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
         }
     }
     // 5. back-transformation, 6. V = L^{-T} U
-    k_backtransform<<<dim3((nmax + BT_COLS - 1) / BT_COLS, np), 256, 0, s>>>(pr, es->fail);
+    k_backtransform<<<dim3((nmax + BT_COLS - 1) / BT_COLS, np), 256, bt_smem_bytes(nmax), s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
     k_trsm<<<dim3(cbk, np), 256, smem_trsm, s>>>(pr, 2, es->fail);
     KFAC_LAUNCH_CHECK(h);

@@ -67,6 +67,7 @@ struct MxPass {
     int N_pad, S, rows;
     MxLayer lay[KFAC_MAX_LAYERS];         // hidden layers 1..L-1 (index l-1)
     float* zl;                            // last-layer outputs, S*N_pad
+    float* Xf;                            // FP32 copy of the points (N_pad x d, zero padded)
     bf16 *red_a, *red_g;                  // KFAC-reduce column sums (N_pad x hp_max)
     CUtensorMap gRa[KFAC_MAX_LAYERS], gRg[KFAC_MAX_LAYERS];
 };
@@ -76,6 +77,7 @@ struct MxWeights {
     float* bias[KFAC_MAX_LAYERS];
     CUtensorMap kW_hi[KFAC_MAX_LAYERS], kW_lo[KFAC_MAX_LAYERS], kWt[KFAC_MAX_LAYERS];
     float* wL;        // last layer weights (h_{L-1}) and bias at [hp]
+    float* W1f;       // first layer in FP32, input-major: W1f[k * hp_1 + j] = W~_1[j][k], k = 0..d (d: bias)
 };
 
 struct MxState {
@@ -111,9 +113,10 @@ __global__ void k_convert_weights(const double* __restrict__ W, int hout, int hi
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)hout_p * hin_p) return;
     int i = (int)(idx / hin_p), k = (int)(idx % hin_p);
-    double v = (i < hout && k < hin) ? W[i + (long long)hout * k] : 0.0;
-    bf16 hi = __double2bfloat16(v);
-    bf16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+    // one FP64 operation per element (the conversion); the split is done in FP32
+    float v = (i < hout && k < hin) ? (float)W[i + (long long)hout * k] : 0.f;
+    bf16 hi = __float2bfloat16_rn(v);
+    bf16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
     Whi[idx] = hi;
     Wlo[idx] = lo;
     Wt[(long long)k * hout_p + i] = hi;
@@ -127,43 +130,102 @@ __global__ void k_convert_last(const double* __restrict__ W, int hin, int hin_p,
     else wL[k] = (float)W[hin];     // bias at index hin_p
 }
 
-// First layer (Sec. 3.1): inputs (x, e_1..e_d, 0); tanh rule of Eq. 6.
-__global__ void k_layer1(const double* __restrict__ W, const double* __restrict__ X, int N, int N_pad, int d,
+// First-layer weights in FP32, input-major with the features contiguous.
+__global__ void k_convert_first(const double* __restrict__ W, int h, int hp, int d, float* W1f) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)(d + 1) * hp) return;
+    int k = (int)(idx / hp), j = (int)(idx % hp);
+    W1f[idx] = (j < h) ? (float)W[j + (long long)h * k] : 0.f;
+}
+
+// Points in FP32 (rows >= N zero).
+__global__ void k_points_f32(const double* __restrict__ X, int N, int N_pad, int d, float* Xf) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)N_pad * d) return;
+    Xf[idx] = (idx < (long long)N * d) ? (float)X[idx] : 0.f;
+}
+
+KFAC_DEV void store4_bf16(bf16* dst, const float* v) {
+    __align__(8) __nv_bfloat162 t[2] = {__floats2bfloat162_rn(v[0], v[1]), __floats2bfloat162_rn(v[2], v[3])};
+    *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(t);
+}
+
+// First layer (Sec. 3.1): inputs (x, e_1..e_d, 0), so the tangent columns of
+// Z^{(1)} are the columns of W_1 and its Laplacian column is 0; tanh rule of
+// Eq. 6.  FP32 arithmetic (the outputs are split-BF16, about 16 bits, at most);
+// one thread per point and 4 consecutive features.
+__global__ void k_layer1(const float* __restrict__ W1f, const float* __restrict__ Xf, int N, int N_pad, int d,
                          int h, int hp, int S, int lap_first, bf16* T_hi, bf16* T_lo, float* A0, float* AD,
                          float* SSQ) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)N_pad * hp) return;
-    int n = (int)(idx / hp), j = (int)(idx % hp);
-    bool live = (n < N) && (j < h);
-    // FP32 arithmetic: the outputs are split-BF16 (about 16 bits) at most
-    float a0 = 0.f, ssq = 0.f;
-    if (live) {
-        a0 = (float)W[j + (long long)h * d];
-        for (int k = 0; k < d; k++) a0 = fmaf((float)W[j + (long long)h * k], (float)X[(long long)n * d + k], a0);
-    }
-    float y0 = live ? tanhf(a0) : 0.f;
-    float s1 = 1.f - y0 * y0, s2 = -2.f * y0 * s1;
+    const int hq = hp / 4;
+    if (idx >= (long long)N_pad * hq) return;
+    const int n = (int)(idx / hq), j = 4 * (int)(idx % hq);
+    const long long o = (long long)n * hp + j;
     const long long blk = (long long)N_pad * hp;
-    bf16 hi = __float2bfloat16_rn(y0);
-    T_hi[idx] = hi;
-    T_lo[idx] = __float2bfloat16_rn(y0 - __bfloat162float(hi));
+    float a0[4], y0[4], s1[4], hi[4], lo[4];
+    bool live[4];
+    {
+        float4 b = *reinterpret_cast<const float4*>(W1f + (long long)d * hp + j);
+        a0[0] = b.x; a0[1] = b.y; a0[2] = b.z; a0[3] = b.w;
+    }
+    for (int k = 0; k < d; k++) {
+        const float x = Xf[(long long)n * d + k];
+        float4 w = *reinterpret_cast<const float4*>(W1f + (long long)k * hp + j);
+        a0[0] = fmaf(w.x, x, a0[0]); a0[1] = fmaf(w.y, x, a0[1]);
+        a0[2] = fmaf(w.z, x, a0[2]); a0[3] = fmaf(w.w, x, a0[3]);
+    }
+    const bool row_live = n < N;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        live[q] = row_live && (j + q < h);
+        a0[q] = live[q] ? a0[q] : 0.f;
+        y0[q] = live[q] ? tanhf(a0[q]) : 0.f;
+        s1[q] = live[q] ? 1.f - y0[q] * y0[q] : 0.f;
+        __nv_bfloat16 hb = __float2bfloat16_rn(y0[q]);
+        hi[q] = __bfloat162float(hb);
+        lo[q] = y0[q] - hi[q];
+    }
+    store4_bf16(T_hi + o, hi);
+    store4_bf16(T_lo + o, lo);
+    float ssq[4] = {0.f, 0.f, 0.f, 0.f};
+    if (S == 1) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) live[q] = false;   // no tangents: SSQ = 0
+    }
     if (S > 1) {
         for (int i = 0; i < d; i++) {
-            float w = live ? (float)W[j + (long long)h * i] : 0.f;
-            bf16 th = __float2bfloat16_rn(s1 * w);
-            T_hi[(1 + i) * blk + idx] = th;
-            if (i == 0 && lap_first == 2)   // heat: time tangent keeps its low half (block 2)
-                T_lo[2 * blk + idx] = __float2bfloat16_rn(s1 * w - __bfloat162float(th));
-            if (1 + i >= lap_first) ssq = fmaf(w, w, ssq);
+            float4 w4 = *reinterpret_cast<const float4*>(W1f + (long long)i * hp + j);
+            const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+            float t[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) t[q] = s1[q] * w[q];
+            store4_bf16(T_hi + (1 + i) * blk + o, t);
+            if (i == 0 && lap_first == 2) {     // heat: the time tangent keeps its low half (block 2)
+                float tl[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) tl[q] = t[q] - __bfloat162float(__float2bfloat16_rn(t[q]));
+                store4_bf16(T_lo + 2 * blk + o, tl);
+            }
+            if (1 + i >= lap_first)
+#pragma unroll
+                for (int q = 0; q < 4; q++) ssq[q] = fmaf(w[q], w[q], ssq[q]);
         }
-        float yD = live ? s2 * ssq : 0.f;
-        bf16 dh = __float2bfloat16_rn(yD);
-        T_hi[(S - 1) * blk + idx] = dh;
-        T_lo[blk + idx] = __float2bfloat16_rn(yD - __bfloat162float(dh));
+        float dh[4], dl[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (!live[q]) ssq[q] = 0.f;
+            const float yD = -2.f * y0[q] * s1[q] * ssq[q];
+            __nv_bfloat16 hb = __float2bfloat16_rn(yD);
+            dh[q] = __bfloat162float(hb);
+            dl[q] = yD - dh[q];
+        }
+        store4_bf16(T_hi + (S - 1) * blk + o, dh);
+        store4_bf16(T_lo + blk + o, dl);
     }
-    A0[idx] = a0;
-    AD[idx] = 0.f;
-    SSQ[idx] = ssq;
+    *reinterpret_cast<float4*>(A0 + o) = make_float4(a0[0], a0[1], a0[2], a0[3]);
+    *reinterpret_cast<float4*>(AD + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(SSQ + o) = make_float4(ssq[0], ssq[1], ssq[2], ssq[3]);
 }
 
 // Laplacian row of a hidden layer once all tangent chunks are done:
@@ -312,14 +374,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_colsum(const bf16* __restrict__
     __shared__ double sh[32][33];
     const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
     const int q = blockIdx.x * 32 + cl;
-    double acc = 0.0;
+    // FP32 partial sums per row group (FP64 arithmetic is scarce on this part),
+    // combined in FP64
+    float acc = 0.f;
     if (q < ncols)
         for (int n = rg; n < nrows; n += 32) {
-            double v = (double)__bfloat162float(X[(row0 + n) * hp + q]);
-            if (Xlo) v += (double)__bfloat162float(Xlo[(long long)n * hp + q]);
+            float v = __bfloat162float(X[(row0 + n) * hp + q]);
+            if (Xlo) v += __bfloat162float(Xlo[(long long)n * hp + q]);
             acc += v;
         }
-    double s = reduce_row_groups(acc, sh);
+    double s = reduce_row_groups((double)acc, sh);
     if (rg == 0 && q < ncols) out[q] = s;
 }
 
@@ -382,28 +446,28 @@ __global__ void k_grad_reduce(const float* __restrict__ pi, int zi, const float*
 
 // First-layer input factor in closed form (Sec. 3.1: T^(0) has columns
 // (x, e_1..e_d, 0) and bias row (1, 0, .., 0)).
-__global__ void __launch_bounds__(RED_THREADS) k_factor_A1(const double* __restrict__ X, int N, int d, int S,
+__global__ void __launch_bounds__(RED_THREADS) k_factor_A1(const float* __restrict__ X, int N, int d, int S,
                                                            int reduce, int boundary, double* fac, double beta,
                                                            int* status) {
     __shared__ double shm[32][33];
     const int n1 = d + 1;
     const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
     const int p = blockIdx.y, q = blockIdx.x * 32 + cl;
-    double acc = 0.0;
-    const double sh = (reduce && !boundary) ? 1.0 : 0.0;   // reduce: abar = (x + 1, 1) / S
+    float acc = 0.f;     // FP32 partial sums per row group, combined in FP64
+    const float sh = (reduce && !boundary) ? 1.f : 0.f;   // reduce: abar = (x + 1, 1) / S
     if (q < n1)
         for (int n = rg; n < N; n += 32) {
-            double xp = (p < d) ? X[(long long)n * d + p] + sh : 1.0;
-            double xq = (q < d) ? X[(long long)n * d + q] + sh : 1.0;
-            acc += xp * xq;
+            float xp = (p < d) ? X[(long long)n * d + p] + sh : 1.f;
+            float xq = (q < d) ? X[(long long)n * d + q] + sh : 1.f;
+            acc = fmaf(xp, xq, acc);
         }
-    acc = reduce_row_groups(acc, shm);
+    double tot = reduce_row_groups((double)acc, shm);
     if (rg != 0 || q >= n1) return;
     const int idx = p * n1 + q;
     double v;
-    if (boundary) v = acc / N;
-    else if (reduce) v = acc / ((double)N * S * S);
-    else v = (acc + ((p == q && p < d) ? (double)N : 0.0)) / ((double)N * S);
+    if (boundary) v = tot / N;
+    else if (reduce) v = tot / ((double)N * S * S);
+    else v = (tot + ((p == q && p < d) ? (double)N : 0.0)) / ((double)N * S);
     double o = beta * fac[idx] + (1.0 - beta) * v;
     if (!isfinite(o)) latch_status(status, KFAC_NONFINITE);
     fac[idx] = o;
@@ -412,26 +476,26 @@ __global__ void __launch_bounds__(RED_THREADS) k_factor_A1(const double* __restr
 // Weight gradient of the first layer:
 //   (1/N) sum_n [ (r g)_{n,0} (x_n, 1)^T + sum_i (r g)_{n,i} (e_i, 0)^T ] + boundary term.
 __global__ void __launch_bounds__(RED_THREADS) k_grad_layer1(const bf16* __restrict__ Gr, const bf16* __restrict__ Grb,
-                                                             const double* __restrict__ X,
-                                                             const double* __restrict__ Xb, int N, int N_pad, int Nb,
+                                                             const float* __restrict__ X,
+                                                             const float* __restrict__ Xb, int N, int N_pad, int Nb,
                                                              int d, int h, int hp, int S, double* grad) {
     __shared__ double shm[32][33];
     const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
     const int k = blockIdx.y, j = blockIdx.x * 32 + cl;
     const long long blk = (long long)N_pad * hp;
-    double a = 0.0, b = 0.0;
+    float a = 0.f, b = 0.f;     // FP32 partial sums per row group, combined in FP64
     if (j < h) {
         for (int n = rg; n < N; n += 32) {
-            double g0 = (double)__bfloat162float(Gr[(long long)n * hp + j]);
-            if (k < d) a += g0 * X[(long long)n * d + k] + (double)__bfloat162float(Gr[(1 + k) * blk + (long long)n * hp + j]);
+            float g0 = __bfloat162float(Gr[(long long)n * hp + j]);
+            if (k < d) a += fmaf(g0, X[(long long)n * d + k], __bfloat162float(Gr[(1 + k) * blk + (long long)n * hp + j]));
             else a += g0;
         }
         for (int n = rg; n < Nb; n += 32) {
-            double g0 = (double)__bfloat162float(Grb[(long long)n * hp + j]);
+            float g0 = __bfloat162float(Grb[(long long)n * hp + j]);
             b += (k < d) ? g0 * Xb[(long long)n * d + k] : g0;
         }
     }
-    const double v = a / N + b / Nb;
+    const double v = (double)a / N + (double)b / Nb;
     const double s = reduce_row_groups(v, shm);
     if (rg == 0 && j < h) grad[j + (long long)h * k] = s;
 }
@@ -556,6 +620,7 @@ kfac_status_t alloc_pass(kfac_pinn_handle* h, MxPass& P, int Nmax, int S) {
         if (!ok) return KFAC_CUDA_ERROR;
     }
     if ((st = dal(&P.zl, (size_t)P.rows))) return st;
+    if ((st = dal(&P.Xf, (size_t)P.N_pad * h->dims[0]))) return st;
     if (S > 1 && h->cfg.variant == KFAC_REDUCE) {
         if ((st = dal(&P.red_a, (size_t)P.N_pad * hp_max))) return st;
         if ((st = dal(&P.red_g, (size_t)P.N_pad * hp_max))) return st;
@@ -576,6 +641,7 @@ void free_pass(MxPass& P) {
         cudaFree(ly.A0); cudaFree(ly.AD); cudaFree(ly.SSQ); cudaFree(ly.YD);
     }
     cudaFree(P.zl);
+    cudaFree(P.Xf);
     cudaFree(P.red_a);
     cudaFree(P.red_g);
 }
@@ -624,6 +690,12 @@ kfac_status_t convert_weights(kfac_pinn_handle* h, cudaStream_t s, const double*
             w.bias[l - 1]);
         KFAC_LAUNCH_CHECK(h);
     }
+    {
+        const int h1 = h->dims[1], hp1 = round_up(h1, 64), d = h->dims[0];
+        k_convert_first<<<ceil_div_u((long long)(d + 1) * hp1, EW), EW, 0, s>>>(theta + h->woff[0], h1, hp1, d,
+                                                                                 w.W1f);
+        KFAC_LAUNCH_CHECK(h);
+    }
     int hin = h->dims[L - 1], hin_p = round_up(hin, 64);
     k_convert_last<<<ceil_div_u(hin_p + 1, EW), EW, 0, s>>>(theta + h->woff[L - 1], hin, hin_p, w.wL);
     KFAC_LAUNCH_CHECK(h);
@@ -639,8 +711,10 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
         MxLayer& l1 = P.lay[0];
         long long cnt = (long long)P.N_pad * l1.hp;
         timer_begin(h, KFAC_KC_ELEMENTWISE, s);
-        k_layer1<<<ceil_div_u(cnt, EW), EW, 0, s>>>(theta + h->woff[0], X, N, P.N_pad, d, l1.h, l1.hp, S, lap_first,
-                                                     l1.T_hi, l1.T_lo, l1.A0, l1.AD, l1.SSQ);
+        k_points_f32<<<ceil_div_u((long long)P.N_pad * d, EW), EW, 0, s>>>(X, N, P.N_pad, d, P.Xf);
+        KFAC_LAUNCH_CHECK(h);
+        k_layer1<<<ceil_div_u(cnt / 4, EW), EW, 0, s>>>(m->w.W1f, P.Xf, N, P.N_pad, d, l1.h, l1.hp, S, lap_first,
+                                                         l1.T_hi, l1.T_lo, l1.A0, l1.AD, l1.SSQ);
         timer_end(h, KFAC_KC_ELEMENTWISE, s, 2.0 * (double)S * cnt + 16.0 * cnt);
         KFAC_LAUNCH_CHECK(h);
     }
@@ -754,15 +828,15 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
     // ---- layer 1: closed-form A, gradient from the adjoints ---------------
     {
         int n1 = d + 1;
-        k_factor_A1<<<dim3(ceil_div_u(n1, 32), n1), RED_THREADS, 0, s>>>(X, N, d, S, reduce, 0, h->fac[KFAC_A_INT][0], beta,
-                                                            h->status);
+        k_factor_A1<<<dim3(ceil_div_u(n1, 32), n1), RED_THREADS, 0, s>>>(I.Xf, N, d, S, reduce, 0, h->fac[KFAC_A_INT][0],
+                                                                          beta, h->status);
         KFAC_LAUNCH_CHECK(h);
-        k_factor_A1<<<dim3(ceil_div_u(n1, 32), n1), RED_THREADS, 0, s>>>(Xb, Nb, d, 1, 0, 1, h->fac[KFAC_A_BDY][0], beta,
-                                                            h->status);
+        k_factor_A1<<<dim3(ceil_div_u(n1, 32), n1), RED_THREADS, 0, s>>>(B.Xf, Nb, d, 1, 0, 1, h->fac[KFAC_A_BDY][0],
+                                                                          beta, h->status);
         KFAC_LAUNCH_CHECK(h);
         MxLayer& l1 = I.lay[0];
         k_grad_layer1<<<dim3(ceil_div_u(l1.h, 32), d + 1), RED_THREADS, 0, s>>>(
-            l1.Gr, B.lay[0].Gr, X, Xb, N, I.N_pad, Nb, d, l1.h, l1.hp, S, h->grad + h->woff[0]);
+            l1.Gr, B.lay[0].Gr, I.Xf, B.Xf, N, I.N_pad, Nb, d, l1.h, l1.hp, S, h->grad + h->woff[0]);
         KFAC_LAUNCH_CHECK(h);
     }
     // ---- hidden-layer output factors B_l, l = 1..L-1 -----------------------
@@ -874,6 +948,7 @@ kfac_status_t tc_alloc(kfac_pinn_handle* h) {
         if (!ok) return KFAC_CUDA_ERROR;
     }
     if ((st = dal(&m->w.wL, (size_t)round_up(h->dims[L - 1], 64) + 1))) return st;
+    if ((st = dal(&m->w.W1f, (size_t)(h->dims[0] + 1) * round_up(h->dims[1], 64)))) return st;
     if ((st = dal(&m->part, (size_t)MAX_CHUNKS * m->in.N_pad * hp_max))) return st;
     size_t maxPQ = (size_t)hp_max * hp_max;
     m->gpart_region = (size_t)MAX_GRAM_CHUNKS * maxPQ;
@@ -891,6 +966,7 @@ void tc_free(kfac_pinn_handle* h) {
         cudaFree(m->w.W_hi[l]); cudaFree(m->w.W_lo[l]); cudaFree(m->w.Wt[l]); cudaFree(m->w.bias[l]);
     }
     cudaFree(m->w.wL);
+    cudaFree(m->w.W1f);
     cudaFree(m->part);
     cudaFree(m->gpart);
     cudaFree(m->cs);
