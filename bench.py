@@ -460,6 +460,81 @@ def run_e10(reps=5):
                              "for d = 1/10/100"}
 
 
+# ---------------------------------------------------------------------------
+# Many independent PINNs served together (batched stepping, CUDA graph)
+# ---------------------------------------------------------------------------
+def run_many(steps=10, warmup=3, n_streams=16, count=64):
+    """Aggregate KFAC steps/s of `count` uneven Poisson PINNs stepped as one
+    batch (mixed precision, worker streams, CUDA graph replay), beside the same
+    problems stepped one after another: mixed precision on one stream, and the
+    plain FP64 path (one step each, timed after one warm-up step)."""
+    import torch
+    from paper_2405_15603_gb300 import build as _build
+    _build.build()
+    from paper_2405_15603_gb300.api import KfacBatch, KfacPinn
+    dev = torch.device("cuda:0")
+    members = si.many_pinns(count, seed=0)
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    kw = dict(lam=1e-3, beta=0.95, lr=0.05, momentum=0.0, init_identity=True, update="fixed",
+              eig_sm_budget=max(8, sm // 8))
+    opts = [KfacPinn(m.d, m.widths, device=str(dev), precision="mixed_bf16", max_n_int=m.n_int,
+                     max_n_bdy=m.n_bdy, **kw) for m in members]
+    thetas = [torch.tensor(si.xavier_theta(m.d, m.widths, i), device=dev) for i, m in enumerate(members)]
+    bufs = [[torch.tensor(a, device=dev) for a in si.make_batch(m.prob, m.n_int, m.n_bdy, seed=i)]
+            for i, m in enumerate(members)]
+    cols = [[b[j] for b in bufs] for j in range(4)]
+    losses = [torch.zeros(3, dtype=torch.float64, device=dev) for _ in members]
+    batch = KfacBatch(opts, n_streams=n_streams)
+    for _ in range(warmup):                  # eager, capture, replay
+        batch.step(thetas, *cols, losses)
+    torch.cuda.synchronize()
+    l0 = sum(o.launch_count() for o in opts)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        batch.step(thetas, *cols, losses)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / steps
+    launches = (sum(o.launch_count() for o in opts) - l0) // steps
+    status = sorted({o.sync_status() for o in opts})
+    batch.close()
+    # the same problems one after another, mixed precision, one stream
+    e0.record()
+    for i, o in enumerate(opts):
+        o.step(thetas[i], *bufs[i])
+    e1.record()
+    torch.cuda.synchronize()
+    ms_seq_mixed = e0.elapsed_time(e1)
+    for o in opts:
+        o.close()
+    # plain FP64 path, one problem at a time
+    ms_fp64 = 0.0
+    for i, m in enumerate(members):
+        o = KfacPinn(m.d, m.widths, device=str(dev), precision="fp64", max_n_int=m.n_int, max_n_bdy=m.n_bdy, **kw)
+        th = torch.tensor(si.xavier_theta(m.d, m.widths, i), device=dev)
+        o.step(th, *bufs[i])
+        torch.cuda.synchronize()
+        e0.record()
+        o.step(th, *bufs[i])
+        e1.record()
+        torch.cuda.synchronize()
+        ms_fp64 += e0.elapsed_time(e1)
+        o.close()
+    value = count / (ms_batch / 1e3)
+    return {"metric": f"aggregate KFAC steps/s, {count} uneven Poisson PINNs stepped as one batch",
+            "value": round(value, 3), "unit": "steps/s", "higher_is_better": True, "n_gpus": 1,
+            "steps": steps, "warmup": warmup, "ms_per_batch_step": round(ms_batch, 4), "dtype": "bf16",
+            "data": "synthetic (seeded problem sizes and collocation points)",
+            "config": {"workload": f"many_pinns_{count}_seed0", "d": "uniform {2,5,10,20,50}",
+                       "widths": "uniform {32..512}, 2-3 hidden layers", "n_int": "uniform [500, 4000]",
+                       "n_bdy": "n_int/4", "n_streams": n_streams, **kw, "graph": True},
+            "gpu_launches_per_batch_step": int(launches), "status": status,
+            "mixed_sequential": {"value": round(count / (ms_seq_mixed / 1e3), 3), "unit": "steps/s"},
+            "fp64_sequential": {"value": round(count / (ms_fp64 / 1e3), 3), "unit": "steps/s"},
+            "speedup_vs_fp64_sequential": round(ms_fp64 / ms_batch, 2)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -471,6 +546,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e10", action="store_true",
                     help="forward vs autodiff Laplacian time and memory (App. C.4) instead of the step bench")
+    ap.add_argument("--many", action="store_true",
+                    help="64 uneven PINNs stepped as one batch (CUDA graph) instead of the step bench")
     ap.add_argument("--points", default=None,
                     help="N_INT,N_BDY override (smaller cases for profiler captures; not the headline)")
     args = ap.parse_args()
@@ -481,6 +558,9 @@ def main():
         WORKLOAD_NAME = f"poisson100d_100-768-768-512-512-1_{ni}int_{nb}bdy_resampled"
     if args.e10:
         print(json.dumps(run_e10()), flush=True)
+        return
+    if args.many:
+        print(json.dumps(run_many()), flush=True)
         return
     if args.steps is None:
         args.steps = 2 if args.precision == "fp64" else 30

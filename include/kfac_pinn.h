@@ -66,8 +66,14 @@ typedef enum { KFAC_EXPAND = 0, KFAC_REDUCE = 1 } kfac_variant_t;
 /* Residual operator of the interior term.
  * LAPLACE: r = -Laplacian(u) - f   (Eq. 1 with L = -Laplacian)
  * HEAT:    r = du/dt - kappa * Laplacian_x(u) - f, where the Laplacian runs
- *          over coordinates 1..d-1 and coordinate 0 is time (App. A.6). */
-typedef enum { KFAC_OP_LAPLACE = 0, KFAC_OP_HEAT = 1 } kfac_operator_t;
+ *          over coordinates 1..d-1 and coordinate 0 is time (App. A.6).
+ * GENERAL: r = sum_ij c_ij d^2 u / dx_i dx_j - f with the symmetric d x d
+ *          coefficient matrix cfg.op_coef (Sec. 3.1; App. C.3).  The Taylor
+ *          pass propagates the derivatives along the eigenvectors q_m of C
+ *          and the second-order column sum_m lambda_m d^2u/dq_m^2, which is
+ *          the same operator; the gradient output is rotated back to the
+ *          coordinate axes.  KFAC-expand only. */
+typedef enum { KFAC_OP_LAPLACE = 0, KFAC_OP_HEAT = 1, KFAC_OP_GENERAL = 2 } kfac_operator_t;
 
 /* Update rule of kfac_pinn_step (Sec. 3.4), with Delta the preconditioned
  * direction and delta_prev the previous update:
@@ -103,6 +109,13 @@ typedef struct {
     int max_n_int;                 /* capacity: interior points per call (>= 1)        */
     int max_n_bdy;                 /* capacity: boundary points per call (>= 1)        */
     int update;                    /* kfac_update_t of kfac_pinn_step                  */
+    int eig_sm_budget;             /* SMs the cooperative tridiagonalisation of the
+                                      inverse may occupy (0: all).  Handles stepped
+                                      concurrently (kfac_pinn_batch_step) should split
+                                      the GPU between them.                          */
+    const double* op_coef;         /* GENERAL: host pointer to the d x d coefficient
+                                      matrix C (row-major, symmetric), read by
+                                      kfac_pinn_create only; otherwise ignored        */
 } kfac_config_t;
 
 typedef struct kfac_pinn_handle* kfac_handle_t;
@@ -264,6 +277,32 @@ kfac_status_t kfac_pinn_timing_enable(kfac_handle_t h, int enable);
 kfac_status_t kfac_pinn_timing_read(kfac_handle_t h, int kernel_class, double* total_ms,
                                     int64_t* launches, double* work);
 
+/* Batched stepping of many independent problems (handles), each with its own
+ * network, point counts and buffers.  The paper steps one problem at a time;
+ * this serves many small PINNs together: the handles' steps are queued on
+ * n_streams worker streams forked from and joined back into the caller's
+ * stream, and from the second call on the whole batch is captured once into
+ * a CUDA graph and replayed.
+ *   - kfac_pinn_batch_create copies the handle array (the handles stay owned
+ *     by the caller and must outlive the batch); all must be on the current
+ *     device.  n_streams in 1..64.
+ *   - kfac_pinn_batch_step: per-handle arrays (host arrays of device
+ *     pointers and counts, count entries each) as in kfac_pinn_step; loss may
+ *     be NULL or hold NULL entries.  Call 1 runs eagerly; call 2 captures and
+ *     launches the graph; later calls replay it when every pointer and count
+ *     equals those captured (write new batches into the same buffers), and
+ *     re-capture otherwise.  use_graph = 0 always runs eagerly.
+ *   - Same results as calling kfac_pinn_step on each handle in turn.  A handle
+ *     with timing enabled is stepped eagerly (its timers need the host). */
+typedef struct kfac_pinn_batch* kfac_batch_t;
+
+kfac_status_t kfac_pinn_batch_create(const kfac_handle_t* handles, int count, int n_streams, kfac_batch_t* out);
+kfac_status_t kfac_pinn_batch_destroy(kfac_batch_t b);
+kfac_status_t kfac_pinn_batch_step(kfac_batch_t b, void* stream, double* const* theta,
+                                   const double* const* X_int, const int* N_int, const double* const* f,
+                                   const double* const* X_bdy, const int* N_bdy, const double* const* g,
+                                   double* const* loss, int use_graph);
+
 /* Allocation-free forward Laplacian.  The paper has no counterpart: this is
  * a service for callers that cannot allocate device memory while they run
  * (code inside another runtime's memory pool or fixed device-memory budget,
@@ -275,7 +314,7 @@ kfac_status_t kfac_pinn_timing_read(kfac_handle_t h, int kernel_class, double* t
  * library holds until the process exits.
  *   - Inputs and outputs are caller-owned device pointers as in
  *     kfac_pinn_forward_laplacian; N >= 1.
- *   - Capacity: sum over layers l of (2 if l < L else 1) * (d+2) * N * h_l
+ *   - Capacity: d + sum over layers l of (2 if l < L else 1) * (d+2) * N * h_l
  *     doubles must not exceed 4,194,304 (32 MiB); larger requests return
  *     KFAC_BAD_ARG and queue nothing.
  *   - The first call on a device looks up the scratch array's device address

@@ -80,6 +80,20 @@ def laplacian_set(d: int, op: str) -> np.ndarray:
     return np.arange(d)
 
 
+def operator_matrix(d: int, op: str, coef: Optional[np.ndarray] = None) -> np.ndarray:
+    """Coefficients c_ij of the second-order column Σ_ij c_ij ∂²_ij z (App. C.3):
+    the identity for the Laplacian, the spatial identity for the heat operator's
+    partial Laplacian, the given symmetric matrix for a general operator."""
+    if op == "general":
+        C = np.asarray(coef, dtype=np.float64)
+        assert C.shape == (d, d) and np.allclose(C, C.T, rtol=0, atol=1e-12 * np.abs(C).max())
+        return C
+    C = np.zeros((d, d))
+    idx = laplacian_set(d, op)
+    C[idx, idx] = 1.0
+    return C
+
+
 # ---------------------------------------------------------------------------
 # Forward Laplacian (Sec. 3.1 Eq. 5-6; App. C.2 Eq. 19-20)
 # ---------------------------------------------------------------------------
@@ -115,12 +129,12 @@ def input_taylor_matrix(X: np.ndarray, with_derivatives: bool) -> np.ndarray:
     return T
 
 
-def tanh_taylor(Z: np.ndarray, lap_set: Optional[np.ndarray]) -> np.ndarray:
-    """Element-wise tanh through the Taylor columns (Eq. 6).
+def tanh_taylor(Z: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """Element-wise tanh through the Taylor columns (Eq. 6; App. C.3).
 
     value  y_0 = σ(a_0)
     ∂_i    y_i = σ'(a_0) a_i
-    Δ      y_Δ = σ'(a_0) a_Δ + σ''(a_0) Σ_{i in lap_set} a_i²
+    second y_C = σ'(a_0) a_C + σ''(a_0) Σ_ij c_ij a_i a_j     (Laplacian: c = I)
     with σ = tanh, σ' = 1 - σ², σ'' = -2 σ σ'.
     """
     a0 = Z[:, :, 0]
@@ -131,9 +145,10 @@ def tanh_taylor(Z: np.ndarray, lap_set: Optional[np.ndarray]) -> np.ndarray:
     Y[:, :, 0] = y0
     S = Z.shape[2]
     if S > 1:
-        Y[:, :, 1:S - 1] = s1[:, :, None] * Z[:, :, 1:S - 1]
-        sumsq = (Z[:, :, 1 + lap_set] ** 2).sum(axis=2)
-        Y[:, :, S - 1] = s1 * Z[:, :, S - 1] + s2 * sumsq
+        a_tan = Z[:, :, 1:S - 1]
+        Y[:, :, 1:S - 1] = s1[:, :, None] * a_tan
+        quad = np.einsum("nhi,ij,nhj->nh", a_tan, C, a_tan)
+        Y[:, :, S - 1] = s1 * Z[:, :, S - 1] + s2 * quad
     return Y
 
 
@@ -147,7 +162,7 @@ def append_bias_row(T: np.ndarray) -> np.ndarray:
 
 
 def taylor_forward(Ws: Sequence[np.ndarray], X: np.ndarray, op: str = "laplace",
-                   with_derivatives: bool = True) -> TaylorPass:
+                   with_derivatives: bool = True, coef: Optional[np.ndarray] = None) -> TaylorPass:
     """Forward Laplacian with intermediates (App. B step 1; App. C.2).
 
     Z^{(l)} = W̃_l T̂^{(l-1)}; for l < L the tanh rule gives T^{(l)} and its
@@ -155,7 +170,7 @@ def taylor_forward(Ws: Sequence[np.ndarray], X: np.ndarray, op: str = "laplace",
     forward pass of the boundary term (S = 1)."""
     d = X.shape[1]
     T = input_taylor_matrix(X, with_derivatives)
-    lap_set = laplacian_set(d, op)
+    C = operator_matrix(d, op, coef)
     T_in, Zs = [], []
     L = len(Ws)
     for l, W in enumerate(Ws):
@@ -163,13 +178,15 @@ def taylor_forward(Ws: Sequence[np.ndarray], X: np.ndarray, op: str = "laplace",
         Z = np.matmul(W[None, :, :], T)
         Zs.append(Z)
         if l < L - 1:
-            T = append_bias_row(tanh_taylor(Z, lap_set))
+            T = append_bias_row(tanh_taylor(Z, C))
     return TaylorPass(T_in=T_in, Z=Zs, S=T.shape[2])
 
 
-def forward_laplacian(Ws: Sequence[np.ndarray], X: np.ndarray, op: str = "laplace"):
-    """u, ∇u and the (partial, for heat) Laplacian per point."""
-    fp = taylor_forward(Ws, X, op)
+def forward_laplacian(Ws: Sequence[np.ndarray], X: np.ndarray, op: str = "laplace",
+                      coef: Optional[np.ndarray] = None):
+    """u, ∇u and the second-order column per point: the Laplacian (partial for
+    heat) or Σ_ij c_ij ∂²_ij u for a general operator (App. C.3)."""
+    fp = taylor_forward(Ws, X, op, True, coef)
     out = fp.Z[-1][:, 0, :]
     return out[:, 0].copy(), out[:, 1:-1].copy(), out[:, -1].copy()
 
@@ -181,6 +198,8 @@ def forward_laplacian(Ws: Sequence[np.ndarray], X: np.ndarray, op: str = "laplac
 
 def interior_residual(fp: TaylorPass, f: np.ndarray, op: str, kappa: float) -> np.ndarray:
     out = fp.Z[-1][:, 0, :]
+    if op == "general":
+        return out[:, -1] - f                          # Σ c_ij ∂²_ij u - f
     if op == "heat":
         return out[:, 1] - kappa * out[:, -1] - f      # ∂_t u - κ Δ_x u - f
     return -out[:, -1] - f                             # -Δu - f
@@ -195,6 +214,8 @@ def residual_seed(S: int, op: str, kappa: float, interior: bool) -> np.ndarray:
     c = np.zeros(S)
     if not interior:
         c[0] = 1.0
+    elif op == "general":
+        c[S - 1] = 1.0
     elif op == "heat":
         c[1] = 1.0
         c[S - 1] = -kappa
@@ -214,12 +235,12 @@ def loss(r_int: np.ndarray, r_bdy: np.ndarray) -> Tuple[float, float, float]:
 # ---------------------------------------------------------------------------
 
 
-def tanh_taylor_adjoint(Z: np.ndarray, Ybar: np.ndarray, lap_set: np.ndarray) -> np.ndarray:
-    """Vector-Jacobian product of `tanh_taylor` (derived from Eq. 6).
+def tanh_taylor_adjoint(Z: np.ndarray, Ybar: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """Vector-Jacobian product of `tanh_taylor` (derived from Eq. 6; App. C.3).
 
-    ā_Δ = σ' ȳ_Δ
-    ā_i = σ' ȳ_i + 2 σ'' a_i ȳ_Δ           (i in lap_set; else no second term)
-    ā_0 = σ' ȳ_0 + σ'' Σ_i a_i ȳ_i + (σ'' a_Δ + σ''' Σ_{i in lap_set} a_i²) ȳ_Δ
+    ā_C = σ' ȳ_C
+    ā_i = σ' ȳ_i + 2 σ'' (C a)_i ȳ_C          (C symmetric)
+    ā_0 = σ' ȳ_0 + σ'' Σ_i a_i ȳ_i + (σ'' a_C + σ''' Σ_ij c_ij a_i a_j) ȳ_C
     with σ''' = -2 σ' (1 - 3 σ²).
     """
     a0 = Z[:, :, 0]
@@ -235,17 +256,17 @@ def tanh_taylor_adjoint(Z: np.ndarray, Ybar: np.ndarray, lap_set: np.ndarray) ->
     yd = Ybar[:, :, S - 1]
     a_tan = Z[:, :, 1:S - 1]
     Abar[:, :, S - 1] = s1 * yd
-    Abar[:, :, 1:S - 1] = s1[:, :, None] * Ybar[:, :, 1:S - 1]
-    Abar[:, :, 1 + lap_set] += 2.0 * (s2 * yd)[:, :, None] * Z[:, :, 1 + lap_set]
-    sumsq = (Z[:, :, 1 + lap_set] ** 2).sum(axis=2)
+    Ca = np.einsum("ij,nhj->nhi", C, a_tan)
+    Abar[:, :, 1:S - 1] = s1[:, :, None] * Ybar[:, :, 1:S - 1] + 2.0 * (s2 * yd)[:, :, None] * Ca
+    quad = (a_tan * Ca).sum(axis=2)
     Abar[:, :, 0] = (s1 * Ybar[:, :, 0]
                      + s2 * (a_tan * Ybar[:, :, 1:S - 1]).sum(axis=2)
-                     + (s2 * Z[:, :, S - 1] + s3 * sumsq) * yd)
+                     + (s2 * Z[:, :, S - 1] + s3 * quad) * yd)
     return Abar
 
 
 def taylor_adjoint(Ws: Sequence[np.ndarray], fp: TaylorPass, seed: np.ndarray,
-                   op: str = "laplace") -> List[np.ndarray]:
+                   op: str = "laplace", coef: Optional[np.ndarray] = None) -> List[np.ndarray]:
     """Backpropagate the seed c through the Taylor pass (App. B, the backward
     that yields g^{(l)}).  Returns Zbar[l] = g^{(l+1)}, shape (N, h_{l+1}, S).
 
@@ -254,7 +275,7 @@ def taylor_adjoint(Ws: Sequence[np.ndarray], fp: TaylorPass, seed: np.ndarray,
     L = len(Ws)
     N = fp.Z[-1].shape[0]
     d = fp.T_in[0].shape[1] - 1
-    lap_set = laplacian_set(d, op)
+    C = operator_matrix(d, op, coef)
     Zbar: List[Optional[np.ndarray]] = [None] * L
     cur = np.broadcast_to(seed[None, None, :], (N, 1, seed.size)).copy()
     for l in range(L - 1, -1, -1):
@@ -263,7 +284,7 @@ def taylor_adjoint(Ws: Sequence[np.ndarray], fp: TaylorPass, seed: np.ndarray,
             break
         W = Ws[l][:, :-1]                       # drop the bias column
         Tbar = np.matmul(W.T[None, :, :], cur)  # (N, h_{l}, S)
-        cur = tanh_taylor_adjoint(fp.Z[l - 1], Tbar, lap_set)
+        cur = tanh_taylor_adjoint(fp.Z[l - 1], Tbar, C)
     return Zbar  # type: ignore[return-value]
 
 
@@ -368,6 +389,7 @@ class KfacConfig:
     momentum: float = 0.0
     line_search: bool = False
     kfac_star: bool = False     # automatic learning rate and momentum (KFAC*, Sec. 3.4)
+    op_coef: Optional[np.ndarray] = None   # op == "general": symmetric d x d c_ij (App. C.3)
 
 
 @dataclass
@@ -402,12 +424,12 @@ class StepResult:
 
 def curvature_and_gradient(cfg: KfacConfig, Ws, X_int, f, X_bdy, g):
     """App. B steps 1, 2 and 4 (without the preconditioner)."""
-    fp_i = taylor_forward(Ws, X_int, cfg.op, True)
+    fp_i = taylor_forward(Ws, X_int, cfg.op, True, cfg.op_coef)
     r_i = interior_residual(fp_i, f, cfg.op, cfg.kappa)
-    zb_i = taylor_adjoint(Ws, fp_i, residual_seed(fp_i.S, cfg.op, cfg.kappa, True), cfg.op)
-    fp_b = taylor_forward(Ws, X_bdy, cfg.op, False)
+    zb_i = taylor_adjoint(Ws, fp_i, residual_seed(fp_i.S, cfg.op, cfg.kappa, True), cfg.op, cfg.op_coef)
+    fp_b = taylor_forward(Ws, X_bdy, cfg.op, False, cfg.op_coef)
     r_b = boundary_residual(fp_b, g)
-    zb_b = taylor_adjoint(Ws, fp_b, residual_seed(1, cfg.op, cfg.kappa, False), cfg.op)
+    zb_b = taylor_adjoint(Ws, fp_b, residual_seed(1, cfg.op, cfg.kappa, False), cfg.op, cfg.op_coef)
     fac = factors_expand if cfg.variant == "expand" else factors_reduce
     Ai, Bi, Ab, Bb = [], [], [], []
     for l in range(len(Ws)):
@@ -423,8 +445,8 @@ def curvature_and_gradient(cfg: KfacConfig, Ws, X_int, f, X_bdy, g):
 def batch_loss(cfg: KfacConfig, theta: np.ndarray, X_int, f, X_bdy, g) -> Tuple[float, float, float]:
     """Eq. 1 at theta on one batch: forward passes and residuals only."""
     Ws = unpack_theta(theta, cfg.d, cfg.widths)
-    r_i = interior_residual(taylor_forward(Ws, X_int, cfg.op, True), f, cfg.op, cfg.kappa)
-    r_b = boundary_residual(taylor_forward(Ws, X_bdy, cfg.op, False), g)
+    r_i = interior_residual(taylor_forward(Ws, X_int, cfg.op, True, cfg.op_coef), f, cfg.op, cfg.kappa)
+    r_b = boundary_residual(taylor_forward(Ws, X_bdy, cfg.op, False, cfg.op_coef), g)
     return loss(r_i, r_b)
 
 

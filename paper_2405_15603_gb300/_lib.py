@@ -17,7 +17,8 @@ EXPORTS = [
     "kfac_pinn_get_direction", "kfac_pinn_sync_status", "kfac_pinn_launch_count",
     "kfac_pinn_timing_enable", "kfac_pinn_timing_read", "kfac_pinn_forward_laplacian_noalloc",
     "kfac_pinn_get_line_search_losses", "kfac_pinn_forward_laplacian_backward",
-    "kfac_pinn_get_update_coefficients",
+    "kfac_pinn_get_update_coefficients", "kfac_pinn_batch_create", "kfac_pinn_batch_destroy",
+    "kfac_pinn_batch_step",
 ]
 
 KERNEL_CLASSES = {0: "layer_gemm", 1: "adjoint_gemm", 2: "gram", 3: "elementwise", 4: "eig", 5: "precond"}
@@ -29,7 +30,8 @@ class KfacConfig(C.Structure):
         ("op", C.c_int), ("kappa", C.c_double), ("precision", C.c_int), ("variant", C.c_int),
         ("beta", C.c_double), ("lambda_", C.c_double), ("damping_sqrt", C.c_int),
         ("factor_init_identity", C.c_int), ("lr", C.c_double), ("momentum", C.c_double),
-        ("max_n_int", C.c_int), ("max_n_bdy", C.c_int), ("update", C.c_int),
+        ("max_n_int", C.c_int), ("max_n_bdy", C.c_int), ("update", C.c_int), ("eig_sm_budget", C.c_int),
+        ("op_coef", C.c_void_p),
     ]
 
 
@@ -78,6 +80,9 @@ def load() -> C.CDLL:
         "kfac_pinn_get_direction": (st, [H, P, P]),
         "kfac_pinn_get_line_search_losses": (st, [H, P, P]),
         "kfac_pinn_get_update_coefficients": (st, [H, P, P]),
+        "kfac_pinn_batch_create": (st, [P, I, I, C.POINTER(C.c_void_p)]),
+        "kfac_pinn_batch_destroy": (st, [P]),
+        "kfac_pinn_batch_step": (st, [P, P, P, P, P, P, P, P, P, P, I]),
         "kfac_pinn_sync_status": (st, [H, C.POINTER(C.c_int)]),
         "kfac_pinn_launch_count": (C.c_int64, [H]),
         "kfac_pinn_timing_enable": (st, [H, I]),

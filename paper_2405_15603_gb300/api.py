@@ -14,7 +14,7 @@ import torch
 from . import _lib
 from ._lib import KfacConfig, KfacError
 
-OPS = {"laplace": 0, "heat": 1}
+OPS = {"laplace": 0, "heat": 1, "general": 2}
 PRECISIONS = {"fp64": 0, "mixed_bf16": 1}
 VARIANTS = {"expand": 0, "reduce": 1}
 FACTORS = {"A_int": 0, "B_int": 1, "A_bdy": 2, "B_bdy": 3}
@@ -45,8 +45,10 @@ def make_config(d: int, widths: Sequence[int], op: str = "laplace", kappa: float
                 precision: str = "fp64", variant: str = "expand", beta: float = 0.0,
                 lam: float = 1e-3, damping_sqrt: bool = False, init_identity: bool = False,
                 lr: float = 0.1, momentum: float = 0.0, max_n_int: int = 1024,
-                max_n_bdy: int = 1024, line_search: bool = False, update: str = "fixed") -> KfacConfig:
-    """line_search=True is shorthand for update="line_search"."""
+                max_n_bdy: int = 1024, line_search: bool = False, update: str = "fixed",
+                eig_sm_budget: int = 0, op_coef=None) -> KfacConfig:
+    """line_search=True is shorthand for update="line_search".  op="general" takes
+    the symmetric d x d coefficient matrix op_coef (kept alive on the config)."""
     cfg = KfacConfig()
     cfg.d = d
     cfg.L = len(widths)
@@ -65,6 +67,11 @@ def make_config(d: int, widths: Sequence[int], op: str = "laplace", kappa: float
     cfg.max_n_int = max_n_int
     cfg.max_n_bdy = max_n_bdy
     cfg.update = UPDATES["line_search" if line_search else update]
+    cfg.eig_sm_budget = eig_sm_budget
+    if op_coef is not None:
+        arr = np.ascontiguousarray(op_coef, dtype=np.float64)
+        cfg._op_coef_keepalive = arr
+        cfg.op_coef = arr.ctypes.data
     return cfg
 
 
@@ -253,3 +260,42 @@ class ForwardLaplacian(torch.autograd.Function):
         theta, X = ctx.saved_tensors
         dtheta, dX = ctx.opt.forward_laplacian_backward(theta, X, du, dg, dl, need_dX=ctx.needs_input_grad[1])
         return (dtheta if ctx.needs_input_grad[0] else None), dX, None
+
+
+class KfacBatch:
+    """Many KfacPinn problems stepped together (worker streams, CUDA graph replay)."""
+
+    def __init__(self, problems: Sequence[KfacPinn], n_streams: int = 8):
+        self.lib = _lib.load()
+        self.problems = list(problems)
+        hs = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
+        self.b = C.c_void_p()
+        _check("kfac_pinn_batch_create", self.lib.kfac_pinn_batch_create(hs, len(self.problems), n_streams,
+                                                                         C.byref(self.b)))
+
+    def close(self):
+        if self.b:
+            self.lib.kfac_pinn_batch_destroy(self.b)
+            self.b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, thetas, X_int, f, X_bdy, g, losses=None, use_graph: bool = True):
+        """One step of every problem; all arguments are lists of device tensors
+        (FP64, contiguous) that stay at the same addresses between calls for the
+        graph to be replayed."""
+        n = len(self.problems)
+        P = C.c_void_p * n
+        Ia = C.c_int * n
+
+        def ptrs(ts):
+            return P(*[None if t is None else t.data_ptr() for t in ts])
+
+        _check("kfac_pinn_batch_step", self.lib.kfac_pinn_batch_step(
+            self.b, _stream(), ptrs(thetas), ptrs(X_int), Ia(*[x.shape[0] for x in X_int]), ptrs(f),
+            ptrs(X_bdy), Ia(*[x.shape[0] for x in X_bdy]), ptrs(g), None if losses is None else ptrs(losses),
+            int(use_graph)))

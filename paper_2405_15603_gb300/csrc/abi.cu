@@ -3,6 +3,8 @@
 #include <string.h>
 #include <math.h>
 
+#include <vector>
+
 #include "kfac_internal.cuh"
 #include "tc_path.cuh"
 
@@ -15,7 +17,18 @@ bool valid_config(const kfac_config_t* c) {
         if (c->widths[l] < 1 || c->widths[l] > 1023) return false;
     if (c->widths[c->L - 1] != 1) return false;
     if (c->d + 1 > 1024) return false;
-    if (c->op != KFAC_OP_LAPLACE && c->op != KFAC_OP_HEAT) return false;
+    if (c->op != KFAC_OP_LAPLACE && c->op != KFAC_OP_HEAT && c->op != KFAC_OP_GENERAL) return false;
+    if (c->op == KFAC_OP_GENERAL) {
+        if (!c->op_coef || c->variant != KFAC_EXPAND) return false;
+        double mx = 0.0;
+        for (int i = 0; i < c->d * c->d; i++) {
+            if (!isfinite(c->op_coef[i])) return false;
+            mx = fmax(mx, fabs(c->op_coef[i]));
+        }
+        for (int i = 0; i < c->d; i++)
+            for (int j = 0; j < i; j++)
+                if (fabs(c->op_coef[i * c->d + j] - c->op_coef[j * c->d + i]) > 1e-12 * mx) return false;
+    }
     if (c->op == KFAC_OP_HEAT && c->d < 2) return false;
     if (c->precision != KFAC_FP64 && c->precision != KFAC_MIXED_BF16) return false;
     if (c->variant != KFAC_EXPAND && c->variant != KFAC_REDUCE) return false;
@@ -24,6 +37,7 @@ bool valid_config(const kfac_config_t* c) {
     if (!isfinite(c->lr) || !isfinite(c->momentum) || !isfinite(c->kappa)) return false;
     if (c->max_n_int < 1 || c->max_n_bdy < 1) return false;
     if (c->update < KFAC_UPDATE_FIXED || c->update > KFAC_UPDATE_AUTO) return false;
+    if (c->eig_sm_budget < 0) return false;
     if (c->update == KFAC_UPDATE_AUTO && c->precision != KFAC_FP64) return false;
     long long rows = (long long)(c->d + 2) * c->max_n_int;
     if (rows > (1LL << 30)) return false;
@@ -37,6 +51,83 @@ kfac_status_t dalloc(T** p, size_t elems) {
     cudaError_t e = cudaMalloc((void**)p, elems * sizeof(T));
     if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); *p = nullptr; return KFAC_OOM; }
     if (e != cudaSuccess) { *p = nullptr; return KFAC_CUDA_ERROR; }
+    return KFAC_OK;
+}
+
+// Symmetric eigendecomposition C = Q diag(lam) Q^T on the host (cyclic
+// Jacobi rotations; C is small and read once per handle).  Q row-major,
+// Q[i * d + m] = component i of eigenvector m.
+void host_sym_eig(const double* C, int d, std::vector<double>& Q, std::vector<double>& lam) {
+    std::vector<double> A(C, C + (size_t)d * d);
+    Q.assign((size_t)d * d, 0.0);
+    for (int i = 0; i < d; i++) Q[(size_t)i * d + i] = 1.0;
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < d; i++)
+            for (int j = 0; j < d; j++) {
+                double a = A[(size_t)i * d + j] * A[(size_t)i * d + j];
+                tot += a;
+                if (i != j) off += a;
+            }
+        if (off <= 1e-30 * tot || off == 0.0) break;
+        for (int p = 0; p < d; p++)
+            for (int q = p + 1; q < d; q++) {
+                const double apq = A[(size_t)p * d + q];
+                if (apq == 0.0) continue;
+                const double app = A[(size_t)p * d + p], aqq = A[(size_t)q * d + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < d; k++) {     // columns p, q
+                    const double akp = A[(size_t)k * d + p], akq = A[(size_t)k * d + q];
+                    A[(size_t)k * d + p] = c * akp - sn * akq;
+                    A[(size_t)k * d + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < d; k++) {     // rows p, q
+                    const double apk = A[(size_t)p * d + k], aqk = A[(size_t)q * d + k];
+                    A[(size_t)p * d + k] = c * apk - sn * aqk;
+                    A[(size_t)q * d + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < d; k++) {
+                    const double qkp = Q[(size_t)k * d + p], qkq = Q[(size_t)k * d + q];
+                    Q[(size_t)k * d + p] = c * qkp - sn * qkq;
+                    Q[(size_t)k * d + q] = sn * qkp + c * qkq;
+                }
+            }
+    }
+    lam.resize(d);
+    for (int i = 0; i < d; i++) lam[i] = A[(size_t)i * d + i];
+}
+
+// Operator description on the device: residual coefficients, tangent
+// directions and channel weights of the second-order column.
+kfac_status_t setup_operator(kfac_pinn_handle* h) {
+    const int d = h->dims[0];
+    std::vector<double> w(d, 1.0);
+    h->cT = 0.0;
+    h->cD = -1.0;
+    if (h->cfg.op == KFAC_OP_HEAT) {
+        h->cT = 1.0;
+        h->cD = -h->cfg.kappa;
+        w[0] = 0.0;                     // time is outside the spatial Laplacian
+    }
+    kfac_status_t st;
+    if (h->cfg.op == KFAC_OP_GENERAL) {
+        std::vector<double> Q, lam;
+        host_sym_eig(h->cfg.op_coef, d, Q, lam);
+        w = lam;
+        h->cD = 1.0;
+        if ((st = dalloc(&h->opQ, (size_t)d * d))) return st;
+        if ((st = dalloc(&h->w1q, (size_t)h->dims[1] * d))) return st;
+        if ((st = dalloc(&h->w1q2, (size_t)h->dims[1] * d))) return st;
+        KFAC_CUDA_TRY(cudaMemcpy(h->opQ, Q.data(), sizeof(double) * d * d, cudaMemcpyHostToDevice));
+    }
+    h->cfg.op_coef = nullptr;           // read only here
+    std::vector<float> wf(w.begin(), w.end());
+    if ((st = dalloc(&h->chw64, (size_t)d))) return st;
+    if ((st = dalloc(&h->chw32, (size_t)d))) return st;
+    KFAC_CUDA_TRY(cudaMemcpy(h->chw64, w.data(), sizeof(double) * d, cudaMemcpyHostToDevice));
+    KFAC_CUDA_TRY(cudaMemcpy(h->chw32, wf.data(), sizeof(float) * d, cudaMemcpyHostToDevice));
     return KFAC_OK;
 }
 
@@ -67,6 +158,11 @@ void free_handle(kfac_pinn_handle* h) {
     cudaFree(h->ks_jv);
     cudaFree(h->ks_part);
     cudaFree(h->coef);
+    cudaFree(h->opQ);
+    cudaFree(h->chw64);
+    cudaFree(h->chw32);
+    cudaFree(h->w1q);
+    cudaFree(h->w1q2);
     for (int w = 0; w < 4; w++)
         for (int l = 0; l < KFAC_MAX_LAYERS; l++) cudaFree(h->fac[w][l]);
     for (int l = 0; l < KFAC_MAX_LAYERS; l++) {
@@ -313,6 +409,7 @@ kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out) {
 
     kfac_status_t st = KFAC_OK;
 #define TRY(x) do { st = (x); if (st != KFAC_OK) { free_handle(h); return st; } } while (0)
+    TRY(setup_operator(h));
     TRY(alloc_pass(h, h->in, cfg->max_n_int, h->S));
     TRY(alloc_pass(h, h->bd, cfg->max_n_bdy, 1));
     TRY(dalloc(&h->grad, (size_t)h->D));

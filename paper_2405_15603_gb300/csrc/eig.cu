@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, 
         if (rank == b % g) {
             double* row = M + (long long)b * n + b;
             const double v0 = v[0], w0 = w[0];
-            for (int j = threadIdx.x; j < m; j += blockDim.x) row[j] -= v0 * w[j] + w0 * v[j];
+            for (int j = threadIdx.x; j < m; j += blockDim.x) row[j] = fma(-v0, w[j], fma(-w0, v[j], row[j]));
             __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) atomicExch(ready, (unsigned)b);
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, 
             if (r <= b) continue;
             double* row = M + (long long)r * n + b;
             const double vi = v[r - b], wi = w[r - b];
-            for (int j = lane; j < m; j += 32) row[j] -= vi * w[j] + wi * v[j];
+            for (int j = lane; j < m; j += 32) row[j] = fma(-vi, w[j], fma(-wi, v[j], row[j]));
         }
         if (rank == 0 && threadIdx.x == 0) { p.tau[k] = tk; p.e[k] = beta; }
         __syncthreads();
@@ -1147,9 +1147,13 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
     if ((st = dal(&es->abort_flag, 1))) return st;
     cudaMemset(es->fail, 0, sizeof(int) * es->np);
 
-    // cooperative tridiagonalisation: CTAs per problem ~ n^3, one CTA per SM
+    // cooperative tridiagonalisation: CTAs per problem ~ n^3, two CTAs per SM
+    // (one CTA's synchronisation stalls overlap the other's FP64 work)
     {
-        int budget = h->sm_count;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag, 512, 0);
+        const int sms = h->cfg.eig_sm_budget > 0 ? std::min(h->cfg.eig_sm_budget, h->sm_count) : h->sm_count;
+        int budget = sms * std::max(1, std::min(per_sm, 2));
         std::vector<double> wgt(es->np);
         double tot = 0.0;
         int need = 0;
@@ -1176,8 +1180,6 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
         cudaMemcpy(es->cta_prob, cp.data(), sizeof(int) * cp.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(es->cta_rank, cr.data(), sizeof(int) * cr.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(es->group, g.data(), sizeof(int) * g.size(), cudaMemcpyHostToDevice);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tridiag, 512, 0);
         if (per_sm * h->sm_count < es->n_cta) return KFAC_BAD_ARG;
     }
 

@@ -14,13 +14,15 @@ namespace {
 constexpr int EW_THREADS = 256;
 
 // --------------------------------------------------------------------------
-// First layer (Sec. 3.1): the inputs are (x, e_1..e_d, 0), so the tangent
-// columns of Z^{(1)} are the columns of W_1 and its Laplacian column is 0.
-// Writes Z^{(1)} and, when a tanh follows, T^{(1)} by the rule of Eq. 6.
+// First layer (Sec. 3.1): the inputs are (x, v_1..v_d, 0), so the tangent
+// columns of Z^{(1)} are W_1 v_i (Wt, h x d column-major: the columns of W_1
+// for the coordinate directions v_i = e_i) and its Laplacian column is 0.
+// Writes Z^{(1)} and, when a tanh follows, T^{(1)} by the rule of Eq. 6 with
+// the tangent channels weighted by chw (App. C.3).
 // --------------------------------------------------------------------------
-__global__ void k_layer1_fwd(const double* __restrict__ W, const double* __restrict__ X,
-                             double* __restrict__ Z, double* __restrict__ T,
-                             int N, int d, int h, int S, int lap_first, int has_act) {
+__global__ void k_layer1_fwd(const double* __restrict__ W, const double* __restrict__ Wt,
+                             const double* __restrict__ X, double* __restrict__ Z, double* __restrict__ T,
+                             int N, int d, int h, int S, const double* __restrict__ chw, int has_act) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)N * h) return;
     int n = (int)(idx / h), j = (int)(idx % h);
@@ -30,7 +32,7 @@ __global__ void k_layer1_fwd(const double* __restrict__ W, const double* __restr
     const long long o = (long long)n * h + j;
     Z[o] = a0;
     if (S > 1) {
-        for (int i = 0; i < d; i++) Z[(1 + i) * blk + o] = W[j + (long long)h * i];
+        for (int i = 0; i < d; i++) Z[(1 + i) * blk + o] = Wt[j + (long long)h * i];
         Z[(S - 1) * blk + o] = 0.0;
     }
     if (!has_act) return;
@@ -41,19 +43,21 @@ __global__ void k_layer1_fwd(const double* __restrict__ W, const double* __restr
     if (S > 1) {
         double sumsq = 0.0;
         for (int i = 0; i < d; i++) {
-            double w = W[j + (long long)h * i];
+            double w = Wt[j + (long long)h * i];
             T[(1 + i) * blk + o] = s1 * w;
-            if (1 + i >= lap_first) sumsq = fma(w, w, sumsq);
+            sumsq = fma(chw[i] * w, w, sumsq);
         }
         T[(S - 1) * blk + o] = s2 * sumsq;
     }
 }
 
-// Tanh through the Taylor columns (Eq. 6):
-//   y_0 = tanh(a_0), y_i = s1 a_i, y_D = s1 a_D + s2 sum_{i in C} a_i^2
-// with s1 = 1 - y_0^2 and s2 = -2 y_0 s1; C = tangent columns >= lap_first.
+// Tanh through the Taylor columns (Eq. 6; App. C.3 for weighted channels):
+//   y_0 = tanh(a_0), y_i = s1 a_i, y_D = s1 a_D + s2 sum_i w_i a_i^2
+// with s1 = 1 - y_0^2 and s2 = -2 y_0 s1; w = chw (1 for a Laplacian
+// channel, 0 for a channel outside the operator, the operator's eigenvalues
+// for a general one).
 __global__ void k_act_fwd(const double* __restrict__ Z, double* __restrict__ T,
-                          int N, int S, int h, int lap_first) {
+                          int N, int S, int h, const double* __restrict__ chw) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long blk = (long long)N * h;
     if (idx >= blk) return;
@@ -67,18 +71,18 @@ __global__ void k_act_fwd(const double* __restrict__ Z, double* __restrict__ T,
     for (int s = 1; s < S - 1; s++) {
         double a = Z[s * blk + idx];
         T[s * blk + idx] = s1 * a;
-        if (s >= lap_first) sumsq = fma(a, a, sumsq);
+        sumsq = fma(chw[s - 1] * a, a, sumsq);
     }
     T[(S - 1) * blk + idx] = fma(s1, Z[(S - 1) * blk + idx], s2 * sumsq);
 }
 
 // Adjoint of k_act_fwd, in place on G (incoming ybar -> outgoing abar):
 //   abar_D = s1 ybar_D
-//   abar_i = s1 ybar_i + 2 s2 a_i ybar_D            (i in C)
-//   abar_0 = s1 ybar_0 + s2 sum_i a_i ybar_i + (s2 a_D + s3 sum_C a_i^2) ybar_D
+//   abar_i = s1 ybar_i + 2 s2 w_i a_i ybar_D
+//   abar_0 = s1 ybar_0 + s2 sum_i a_i ybar_i + (s2 a_D + s3 sum_i w_i a_i^2) ybar_D
 // with s3 = -2 s1 (1 - 3 y^2).
 __global__ void k_act_bwd(const double* __restrict__ Z, double* __restrict__ G,
-                          int N, int S, int h, int lap_first) {
+                          int N, int S, int h, const double* __restrict__ chw) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long blk = (long long)N * h;
     if (idx >= blk) return;
@@ -96,10 +100,9 @@ __global__ void k_act_bwd(const double* __restrict__ Z, double* __restrict__ G,
         double yb = G[s * blk + idx];
         cross = fma(a, yb, cross);
         double ab = s1 * yb;
-        if (s >= lap_first) {
-            sumsq = fma(a, a, sumsq);
-            ab = fma(2.0 * s2 * a, yd, ab);
-        }
+        const double wa = chw[s - 1] * a;
+        sumsq = fma(wa, a, sumsq);
+        ab = fma(2.0 * s2 * wa, yd, ab);
         G[s * blk + idx] = ab;
     }
     double aD = Z[(S - 1) * blk + idx];
@@ -110,9 +113,9 @@ __global__ void k_act_bwd(const double* __restrict__ Z, double* __restrict__ G,
 // Forward-mode derivative of k_act_fwd, in place on D (incoming da -> outgoing dy):
 //   dy_0 = s1 da_0
 //   dy_i = s2 da_0 a_i + s1 da_i
-//   dy_D = s2 da_0 a_D + s1 da_D + s3 da_0 sum_C a_i^2 + 2 s2 sum_C a_i da_i
+//   dy_D = s2 da_0 a_D + s1 da_D + s3 da_0 sum_i w_i a_i^2 + 2 s2 sum_i w_i a_i da_i
 __global__ void k_act_jvp(const double* __restrict__ Z, double* __restrict__ Dz, int N, int S, int h,
-                          int lap_first) {
+                          const double* __restrict__ chw) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long blk = (long long)N * h;
     if (idx >= blk) return;
@@ -128,10 +131,9 @@ __global__ void k_act_jvp(const double* __restrict__ Z, double* __restrict__ Dz,
         double a = Z[s * blk + idx];
         double da = Dz[s * blk + idx];
         Dz[s * blk + idx] = fma(s2 * da0, a, s1 * da);
-        if (s >= lap_first) {
-            sumsq = fma(a, a, sumsq);
-            cross = fma(a, da, cross);
-        }
+        const double wa = chw[s - 1] * a;
+        sumsq = fma(wa, a, sumsq);
+        cross = fma(wa, da, cross);
     }
     double aD = Z[(S - 1) * blk + idx];
     double daD = Dz[(S - 1) * blk + idx];
@@ -141,39 +143,44 @@ __global__ void k_act_jvp(const double* __restrict__ Z, double* __restrict__ Dz,
 // Directional derivative of the residuals: the residual rule applied to dZ^{(L)}
 // (the data f, g do not depend on theta).
 __global__ void k_residual_jvp(const double* __restrict__ dZL, double* __restrict__ jv, int N, int S,
-                               int interior, int heat, double kappa) {
+                               int interior, double cT, double cD) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     double v;
-    if (!interior) v = dZL[n];
-    else if (heat) v = dZL[N + n] - kappa * dZL[(long long)(S - 1) * N + n];
-    else v = -dZL[(long long)(S - 1) * N + n];
+    if (!interior) {
+        v = dZL[n];
+    } else {
+        v = cD * dZL[(long long)(S - 1) * N + n];
+        if (cT != 0.0) v += cT * dZL[N + n];
+    }
     jv[n] = v;
 }
 
-// Residuals (Eq. 1): interior r = -Lap u - f, or du/dt - kappa Lap_x u - f
-// for the heat operator; boundary r = u - g.  Z_L has one feature per row.
+// Residuals (Eq. 1): interior r = cT z_t + cD z_D - f (cT: coefficient of the
+// time tangent, heat only; cD of the Laplacian column), boundary r = u - g.
 __global__ void k_residual(const double* __restrict__ ZL, const double* __restrict__ target,
-                           double* __restrict__ r, int N, int S, int interior, int heat,
-                           double kappa) {
+                           double* __restrict__ r, int N, int S, int interior, double cT, double cD) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     double v;
-    if (!interior) v = ZL[n] - target[n];
-    else if (heat) v = ZL[N + n] - kappa * ZL[(long long)(S - 1) * N + n] - target[n];
-    else v = -ZL[(long long)(S - 1) * N + n] - target[n];
+    if (!interior) {
+        v = ZL[n] - target[n];
+    } else {
+        v = cD * ZL[(long long)(S - 1) * N + n];
+        if (cT != 0.0) v += cT * ZL[N + n];
+        v -= target[n];
+    }
     r[n] = v;
 }
 
 // Seed of the backward pass, c = dr/dZ^{(L)} (one row per point).
-__global__ void k_seed(double* __restrict__ ZbL, int N, int S, int interior, int heat, double kappa) {
+__global__ void k_seed(double* __restrict__ ZbL, int N, int S, int interior, double cT, double cD) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)N * S) return;
     int s = (int)(idx / N);
     double c = 0.0;
     if (!interior) c = 1.0;
-    else if (heat) c = (s == 1) ? 1.0 : (s == S - 1 ? -kappa : 0.0);
-    else c = (s == S - 1) ? -1.0 : 0.0;
+    else c = (s == S - 1) ? cD : (s == 1 ? cT : 0.0);
     ZbL[idx] = c;
 }
 
@@ -263,15 +270,25 @@ kfac_status_t reduce_gemm(kfac_pinn_handle* h, cudaStream_t s, int P, int Q, int
 // --------------------------------------------------------------------------
 // Public (library-internal) entry points of the FP64 path
 // --------------------------------------------------------------------------
+// Tangent inputs of layer 1 for directions v_m = Q e_m: W_1 Q (h_1 x d,
+// column-major, written to dst), or W_1 itself for the coordinate directions.
+static const double* tangent_inputs(kfac_pinn_handle* h, cudaStream_t s, const double* W1, double* dst) {
+    if (!h->opQ) return W1;
+    const int h1 = h->dims[1], d = h->dims[0];
+    if (dgemm_strided(h, s, h1, d, d, W1, 1, h1, h->opQ, d, 1, dst, 1, h1, 1.0, 0.0) != KFAC_OK) return nullptr;
+    return dst;
+}
+
 kfac_status_t fp64_forward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
                            const double* X, int N, PassBuffers& pb, int S) {
     const int L = h->cfg.L, d = h->dims[0];
-    const int lap_first = (h->cfg.op == KFAC_OP_HEAT) ? 2 : 1;
     {
         int h1 = h->dims[1];
         long long cnt = (long long)N * h1;
+        const double* Wt = tangent_inputs(h, s, theta + h->woff[0], h->w1q);
+        if (!Wt) return KFAC_CUDA_ERROR;
         k_layer1_fwd<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(
-            theta + h->woff[0], X, pb.Z[0], pb.T[0], N, d, h1, S, lap_first, L > 1);
+            theta + h->woff[0], Wt, X, pb.Z[0], pb.T[0], N, d, h1, S, h->chw64, L > 1);
         KFAC_LAUNCH_CHECK(h);
     }
     for (int l = 2; l <= L; l++) {
@@ -288,7 +305,7 @@ kfac_status_t fp64_forward(kfac_pinn_handle* h, cudaStream_t s, const double* th
             long long cnt = (long long)N * hout;
             timer_begin(h, KFAC_KC_ELEMENTWISE, s);
             k_act_fwd<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[l - 1], pb.T[l - 1], N,
-                                                                         S, hout, lap_first);
+                                                                         S, hout, h->chw64);
             timer_end(h, KFAC_KC_ELEMENTWISE, s, 16.0 * S * (double)cnt);
             KFAC_LAUNCH_CHECK(h);
         }
@@ -299,13 +316,11 @@ kfac_status_t fp64_forward(kfac_pinn_handle* h, cudaStream_t s, const double* th
 kfac_status_t fp64_residual_and_seed(kfac_pinn_handle* h, cudaStream_t s, PassBuffers& pb, int N,
                                      int S, const double* target, bool interior) {
     const int L = h->cfg.L;
-    const int heat = h->cfg.op == KFAC_OP_HEAT;
     k_residual<<<ceil_div_u(N, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[L - 1], target, pb.r, N, S,
-                                                                interior, heat, h->cfg.kappa);
+                                                                interior, h->cT, h->cD);
     KFAC_LAUNCH_CHECK(h);
     k_seed<<<ceil_div_u((long long)N * S, EW_THREADS), EW_THREADS, 0, s>>>(pb.Zb[L - 1], N, S,
-                                                                            interior, heat,
-                                                                            h->cfg.kappa);
+                                                                            interior, h->cT, h->cD);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }
@@ -313,7 +328,6 @@ kfac_status_t fp64_residual_and_seed(kfac_pinn_handle* h, cudaStream_t s, PassBu
 kfac_status_t fp64_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
                             PassBuffers& pb, int N, int S) {
     const int L = h->cfg.L;
-    const int lap_first = (h->cfg.op == KFAC_OP_HEAT) ? 2 : 1;
     for (int l = L; l >= 2; l--) {
         int hin = h->dims[l - 1], hout = h->dims[l];
         const double* W = theta + h->woff[l - 1];
@@ -328,7 +342,7 @@ kfac_status_t fp64_backward(kfac_pinn_handle* h, cudaStream_t s, const double* t
         long long cnt = (long long)N * hin;
         timer_begin(h, KFAC_KC_ELEMENTWISE, s);
         k_act_bwd<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[l - 2], pb.Zb[l - 2], N, S,
-                                                                     hin, lap_first);
+                                                                     hin, h->chw64);
         timer_end(h, KFAC_KC_ELEMENTWISE, s, 24.0 * S * (double)cnt);
         KFAC_LAUNCH_CHECK(h);
     }
@@ -426,7 +440,7 @@ kfac_status_t fp64_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, const d
     for (int l = 1; l <= L; l++) {
         kfac_status_t st;
         if (l == 1) {
-            st = layer_grad_and_factors(h, s, 1, InputRows{X_int, d, N_int}, InputRows{X_bdy, d, N_bdy},
+            st = layer_grad_and_factors(h, s, 1, InputRows{X_int, d, N_int, h->opQ}, InputRows{X_bdy, d, N_bdy, h->opQ},
                                         N_int, N_bdy);
         } else {
             int hin = h->dims[l - 1];
@@ -442,15 +456,21 @@ namespace {
 // Output seed of the reverse pass through the Taylor forward: for a scalar
 // phi(u, grad u, lap u), Zbar^{(L)}_{n,s} = dphi/dZ^{(L)}_{n,s} with the
 // Taylor rows ordered (value, d tangents, Laplacian).  NULL inputs are zero.
-__global__ void k_seed_upstream(double* __restrict__ ZbL, int N, int S, const double* __restrict__ du,
-                                const double* __restrict__ dgrad, const double* __restrict__ dlap) {
+// With tangent directions v_m = Q e_m the gradient is Q times the tangent
+// outputs, so its upstream gradient maps to Q^T dgrad on the tangent rows.
+__global__ void k_seed_upstream(double* __restrict__ ZbL, int N, int S, const double* __restrict__ Q,
+                                const double* __restrict__ du, const double* __restrict__ dgrad,
+                                const double* __restrict__ dlap) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)N * S) return;
     int s = (int)(idx / N), n = (int)(idx % N);
+    const int d = S - 2;
     double c = 0.0;
     if (s == 0) c = du ? du[n] : 0.0;
     else if (s == S - 1) c = dlap ? dlap[n] : 0.0;
-    else c = dgrad ? dgrad[(long long)n * (S - 2) + (s - 1)] : 0.0;
+    else if (dgrad && !Q) c = dgrad[(long long)n * d + (s - 1)];
+    else if (dgrad)
+        for (int i = 0; i < d; i++) c = fma(Q[(long long)i * d + (s - 1)], dgrad[(long long)n * d + i], c);
     ZbL[idx] = c;
 }
 }  // namespace
@@ -461,8 +481,8 @@ kfac_status_t fp64_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t 
     const int L = h->cfg.L, d = h->dims[0], S = h->S;
     kfac_status_t st;
     if ((st = fp64_forward(h, s, theta, X, N, h->in, S))) return st;
-    k_seed_upstream<<<ceil_div_u((long long)N * S, EW_THREADS), EW_THREADS, 0, s>>>(h->in.Zb[L - 1], N, S, du,
-                                                                                    dgrad, dlap);
+    k_seed_upstream<<<ceil_div_u((long long)N * S, EW_THREADS), EW_THREADS, 0, s>>>(h->in.Zb[L - 1], N, S, h->opQ,
+                                                                                    du, dgrad, dlap);
     KFAC_LAUNCH_CHECK(h);
     if ((st = fp64_backward(h, s, theta, h->in, N, S))) return st;
     // dphi/dW~_l = sum over rows (n, s) of g^{(l)}_{n,s} T^^{(l-1)T}_{n,s} (Sec. 3.2)
@@ -470,7 +490,7 @@ kfac_status_t fp64_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t 
         const int hout = h->dims[l], nin = h->dims[l - 1] + 1;
         Transposed<WeightedRows> A{WeightedRows{h->in.Zb[l - 1], hout, N, nullptr}};
         double* gW = dtheta + h->woff[l - 1];
-        if (l == 1) st = reduce_gemm(h, s, hout, nin, S * N, A, InputRows{X, d, N}, 1.0, gW, 1, hout,
+        if (l == 1) st = reduce_gemm(h, s, hout, nin, S * N, A, InputRows{X, d, N, h->opQ}, 1.0, gW, 1, hout,
                                      accumulate, 0, 0.0);
         else st = reduce_gemm(h, s, hout, nin, S * N, A, ActRows{h->in.T[l - 2], nin - 1, N}, 1.0, gW, 1, hout,
                               accumulate, 0, 0.0);
@@ -493,15 +513,16 @@ kfac_status_t fp64_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t 
 kfac_status_t fp64_jvp(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* v,
                        const double* X, int N, PassBuffers& pb, int S, bool interior, double* jv) {
     const int L = h->cfg.L, d = h->dims[0];
-    const int lap_first = (h->cfg.op == KFAC_OP_HEAT) ? 2 : 1;
     {
         const int h1 = h->dims[1];
         long long cnt = (long long)N * h1;
-        k_layer1_fwd<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(v + h->woff[0], X, pb.Zb[0], nullptr, N, d,
-                                                                         h1, S, lap_first, 0);
+        const double* Vt = tangent_inputs(h, s, v + h->woff[0], h->w1q2);
+        if (!Vt) return KFAC_CUDA_ERROR;
+        k_layer1_fwd<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(v + h->woff[0], Vt, X, pb.Zb[0], nullptr, N,
+                                                                         d, h1, S, h->chw64, 0);
         KFAC_LAUNCH_CHECK(h);
         if (L > 1) {
-            k_act_jvp<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[0], pb.Zb[0], N, S, h1, lap_first);
+            k_act_jvp<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[0], pb.Zb[0], N, S, h1, h->chw64);
             KFAC_LAUNCH_CHECK(h);
         }
     }
@@ -532,24 +553,35 @@ kfac_status_t fp64_jvp(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
         if (l < L) {
             long long cnt = (long long)N * hout;
             k_act_jvp<<<ceil_div_u(cnt, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[l - 1], pb.Zb[l - 1], N, S, hout,
-                                                                         lap_first);
+                                                                         h->chw64);
             KFAC_LAUNCH_CHECK(h);
         }
     }
-    k_residual_jvp<<<ceil_div_u(N, EW_THREADS), EW_THREADS, 0, s>>>(pb.Zb[L - 1], jv, N, S, interior,
-                                                                    h->cfg.op == KFAC_OP_HEAT, h->cfg.kappa);
+    k_residual_jvp<<<ceil_div_u(N, EW_THREADS), EW_THREADS, 0, s>>>(pb.Zb[L - 1], jv, N, S, interior, h->cT,
+                                                                    h->cD);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }
 
 namespace {
-__global__ void k_extract(const double* __restrict__ ZL, int N, int S, int d, double* u,
-                          double* grad, double* lap) {
+// u, grad u and the operator column; with tangent directions v_m = Q e_m the
+// gradient is grad u = sum_m Q[:, m] (directional derivative along v_m).
+__global__ void k_extract(const double* __restrict__ ZL, int N, int S, int d, const double* __restrict__ Q,
+                          double* u, double* grad, double* lap) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     if (u) u[n] = ZL[n];
-    if (grad)
-        for (int i = 0; i < d; i++) grad[(long long)n * d + i] = ZL[(long long)(1 + i) * N + n];
+    if (grad) {
+        if (!Q) {
+            for (int i = 0; i < d; i++) grad[(long long)n * d + i] = ZL[(long long)(1 + i) * N + n];
+        } else {
+            for (int i = 0; i < d; i++) {
+                double acc = 0.0;
+                for (int m = 0; m < d; m++) acc = fma(Q[(long long)i * d + m], ZL[(long long)(1 + m) * N + n], acc);
+                grad[(long long)n * d + i] = acc;
+            }
+        }
+    }
     if (lap) lap[n] = ZL[(long long)(S - 1) * N + n];
 }
 }  // namespace
@@ -557,7 +589,7 @@ __global__ void k_extract(const double* __restrict__ ZL, int N, int S, int d, do
 kfac_status_t fp64_extract_outputs(kfac_pinn_handle* h, cudaStream_t s, PassBuffers& pb, int N,
                                    int S, double* u, double* grad, double* lap) {
     k_extract<<<ceil_div_u(N, EW_THREADS), EW_THREADS, 0, s>>>(pb.Z[h->cfg.L - 1], N, S, h->dims[0],
-                                                               u, grad, lap);
+                                                               h->opQ, u, grad, lap);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }

@@ -43,16 +43,21 @@ struct ActRows {
 };
 
 // The input matrix T^{(0)} of the first layer, never stored: per point the
-// columns (x, e_1..e_d, 0) with bias row (1, 0, .., 0) (Sec. 3.1), in the
+// columns (x, v_1..v_d, 0) with bias row (1, 0, .., 0) (Sec. 3.1; v_m = e_m,
+// or the coefficient matrix's eigenvectors for a general operator), in the
 // column-block-major row order of the activations.
 struct InputRows {
     const double* X;
     int d, N;
+    const double* Q;    // tangent directions v_m = Q e_m (d x d row-major), nullptr: e_m
     static constexpr bool qfast = true;
     KFAC_DEV double operator()(int row, int q) const {
         int s = row / N, n = row - s * N;
         if (s == 0) return q < d ? X[(long long)n * d + q] : 1.0;
-        if (s <= d) return q == s - 1 ? 1.0 : 0.0;
+        if (s <= d) {
+            if (q >= d) return 0.0;
+            return Q ? Q[(long long)q * d + (s - 1)] : (q == s - 1 ? 1.0 : 0.0);
+        }
         return 0.0;
     }
 };

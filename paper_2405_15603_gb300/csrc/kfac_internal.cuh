@@ -54,6 +54,15 @@ struct kfac_pinn_handle {
     double* ks_jv;        // residual JVPs of the automatic update (2 (max_n_int + max_n_bdy))
     double* ks_part;      // block partial sums of the automatic update
     double* coef;         // (c0, c1) of the last update delta = c0 Delta + c1 delta_prev, + diagnostics
+    // operator: interior residual r = cT z_t + cD z_D - f; tangent channel m of the
+    // Taylor pass has direction v_m = opQ e_m (opQ == nullptr: e_m) and weight chw[m]
+    // in the second-order column (App. C.3)
+    double cT, cD;
+    double* opQ;          // d x d row-major (general operator only)
+    double* chw64;        // d
+    float* chw32;         // d
+    double* w1q;          // h_1 x d: W_1 Q (general operator only)
+    double* w1q2;         // h_1 x d: V_1 Q for forward-mode products
     double* fac[4][KFAC_MAX_LAYERS];      // EMA factors A_int, B_int, A_bdy, B_bdy (n x n)
     double* VA[KFAC_MAX_LAYERS];          // generalized eigenvectors (na x na, row-major)
     double* wa[KFAC_MAX_LAYERS];          // generalized eigenvalues (na)

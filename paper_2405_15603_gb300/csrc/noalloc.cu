@@ -42,6 +42,13 @@ kfac_status_t scratch_address(double** out) {
     return KFAC_OK;
 }
 
+// Channel weights of the second-order column: 1 for a Laplacian coordinate,
+// 0 for time under the heat operator.
+__global__ void k_noalloc_weights(double* w, int d, int heat) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < d) w[i] = (heat && i == 0) ? 0.0 : 1.0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -69,7 +76,7 @@ kfac_status_t kfac_pinn_forward_laplacian_noalloc(const kfac_config_t* cfg, void
     h.D = h.woff[cfg->L];
     h.S = cfg->d + 2;
 
-    size_t need = 0;
+    size_t need = (size_t)cfg->d;    // channel weights
     for (int l = 1; l <= cfg->L; l++) need += (size_t)(l < cfg->L ? 2 : 1) * h.S * (size_t)N * h.dims[l];
     if (need > NOALLOC_SCRATCH_DOUBLES) return KFAC_BAD_ARG;   // beyond the fixed scratch capacity
 
@@ -81,6 +88,8 @@ kfac_status_t kfac_pinn_forward_laplacian_noalloc(const kfac_config_t* cfg, void
     pb.N = N;
     pb.S = h.S;
     double* cur = base;
+    h.chw64 = cur;
+    cur += cfg->d;
     for (int l = 1; l <= cfg->L; l++) {
         const size_t e = (size_t)h.S * N * h.dims[l];
         pb.Z[l - 1] = cur;
@@ -91,6 +100,8 @@ kfac_status_t kfac_pinn_forward_laplacian_noalloc(const kfac_config_t* cfg, void
         }
     }
     cudaStream_t s = (cudaStream_t)stream;
+    k_noalloc_weights<<<(cfg->d + 255) / 256, 256, 0, s>>>(h.chw64, cfg->d, cfg->op == KFAC_OP_HEAT);
+    if (cudaGetLastError() != cudaSuccess) return KFAC_CUDA_ERROR;
     if ((st = fp64_forward(&h, s, theta, X, N, pb, h.S))) return st;
     return fp64_extract_outputs(&h, s, pb, N, h.S, u, grad, lap);
 }

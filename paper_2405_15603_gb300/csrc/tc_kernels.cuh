@@ -36,7 +36,7 @@ struct Args {
     int k_steps;                    // contraction length / 64 (FWD/BWD modes)
     int n_out;                      // real output features
     int hp_out;                     // row stride of the outputs (elements)
-    int lap_first;                  // first tangent column in the Laplacian (1 or 2)
+    const float* chw;               // weights of the tangent columns in the second-order column (d)
     int split_time;                 // heat: the time tangent row (s = 1) is split-BF16 too
     int chunk_len, n_chunks;        // tangent-column chunking over blockIdx.z
     // GRAM
@@ -346,10 +346,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                         store16_f32(a.AD + (long long)n * hp + j, v);
                     } else {
                         float y[16];
+                        const float wc = a.chw[s - 1];
 #pragma unroll
                         for (int i = 0; i < 16; i++) {
                             y[i] = st1[c + i] * v[i];
-                            if (s >= a.lap_first) st2[c + i] = fmaf(v[i], v[i], st2[c + i]);
+                            st2[c + i] = fmaf(wc * v[i], v[i], st2[c + i]);
                         }
                         if (a.split_time && s == 1) {
                             float hi[16], lo[16];
@@ -381,11 +382,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                     } else if (MODE == BWD_TAN) {
                         float yi[16];
                         load16_bf16(a.ytan + ((long long)s * a.N_pad + n) * hp + j, yi);
-                        const bool inC = (s >= a.lap_first);
+                        const float wc = a.chw[s - 1];
 #pragma unroll
                         for (int i = 0; i < 16; i++) {
                             float t = st1[c + i] * v[i];
-                            if (inC) t -= __bfloat162float(stq[c + i]) * yi[i];
+                            t -= wc * __bfloat162float(stq[c + i]) * yi[i];
                             ab[i] = t;
                             st2[c + i] = fmaf(yi[i], v[i], st2[c + i]);
                         }

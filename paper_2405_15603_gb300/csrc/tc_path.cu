@@ -16,6 +16,8 @@
 #include <math.h>
 
 #include "tc_path.cuh"
+
+#include <vector>
 #include "tc_kernels.cuh"
 
 using tck::Args;
@@ -78,6 +80,7 @@ struct MxWeights {
     CUtensorMap kW_hi[KFAC_MAX_LAYERS], kW_lo[KFAC_MAX_LAYERS], kWt[KFAC_MAX_LAYERS];
     float* wL;        // last layer weights (h_{L-1}) and bias at [hp]
     float* W1f;       // first layer in FP32, input-major: W1f[k * hp_1 + j] = W~_1[j][k], k = 0..d (d: bias)
+    float* W1Qf;      // general operator: tangent inputs W_1 q_m, W1Qf[m * hp_1 + j]
 };
 
 struct MxState {
@@ -88,6 +91,8 @@ struct MxState {
     size_t gpart_region;
     double* cs;         // column sums (4 x (hp_max + 8))
     int hp_max;
+    float* Qf;          // general operator: tangent directions (d x d, FP32)
+    double* gtan;       // general operator: first-layer tangent gradient sums (h_1 x d)
 };
 
 MxState* MX(kfac_pinn_handle* h) { return (MxState*)h->mx; }
@@ -150,13 +155,14 @@ KFAC_DEV void store4_bf16(bf16* dst, const float* v) {
     *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(t);
 }
 
-// First layer (Sec. 3.1): inputs (x, e_1..e_d, 0), so the tangent columns of
-// Z^{(1)} are the columns of W_1 and its Laplacian column is 0; tanh rule of
-// Eq. 6.  FP32 arithmetic (the outputs are split-BF16, about 16 bits, at most);
-// one thread per point and 4 consecutive features.
-__global__ void k_layer1(const float* __restrict__ W1f, const float* __restrict__ Xf, int N, int N_pad, int d,
-                         int h, int hp, int S, int lap_first, bf16* T_hi, bf16* T_lo, float* A0, float* AD,
-                         float* SSQ) {
+// First layer (Sec. 3.1): inputs (x, v_1..v_d, 0), so the tangent columns of
+// Z^{(1)} are W_1 v_m (Wt, input-major like W1f: the rows of W1f for v_m = e_m)
+// and its Laplacian column is 0; tanh rule of Eq. 6 with channel weights chw
+// (App. C.3).  FP32 arithmetic (the outputs are split-BF16, about 16 bits, at
+// most); one thread per point and 4 consecutive features.
+__global__ void k_layer1(const float* __restrict__ W1f, const float* __restrict__ Wt, const float* __restrict__ Xf,
+                         int N, int N_pad, int d, int h, int hp, int S, const float* __restrict__ chw,
+                         int split_time, bf16* T_hi, bf16* T_lo, float* A0, float* AD, float* SSQ) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int hq = hp / 4;
     if (idx >= (long long)N_pad * hq) return;
@@ -195,21 +201,21 @@ __global__ void k_layer1(const float* __restrict__ W1f, const float* __restrict_
     }
     if (S > 1) {
         for (int i = 0; i < d; i++) {
-            float4 w4 = *reinterpret_cast<const float4*>(W1f + (long long)i * hp + j);
+            float4 w4 = *reinterpret_cast<const float4*>(Wt + (long long)i * hp + j);
             const float w[4] = {w4.x, w4.y, w4.z, w4.w};
             float t[4];
 #pragma unroll
             for (int q = 0; q < 4; q++) t[q] = s1[q] * w[q];
             store4_bf16(T_hi + (1 + i) * blk + o, t);
-            if (i == 0 && lap_first == 2) {     // heat: the time tangent keeps its low half (block 2)
+            if (i == 0 && split_time) {     // heat: the time tangent keeps its low half (block 2)
                 float tl[4];
 #pragma unroll
                 for (int q = 0; q < 4; q++) tl[q] = t[q] - __bfloat162float(__float2bfloat16_rn(t[q]));
                 store4_bf16(T_lo + 2 * blk + o, tl);
             }
-            if (1 + i >= lap_first)
+            const float wc = chw[i];
 #pragma unroll
-                for (int q = 0; q < 4; q++) ssq[q] = fmaf(w[q], w[q], ssq[q]);
+            for (int q = 0; q < 4; q++) ssq[q] = fmaf(wc * w[q], w[q], ssq[q]);
         }
         float dh[4], dl[4];
 #pragma unroll
@@ -287,24 +293,41 @@ __global__ void k_last_fwd(const bf16* __restrict__ T_hi, const bf16* __restrict
     if (lane == 0) zl[wid] = acc + (s == 0 ? wL[hp] : 0.f);
 }
 
+// Residuals (Eq. 1): interior r = cT z_t + cD z_D - f, boundary r = u - g.
 __global__ void k_residual_mx(const float* __restrict__ zl, const double* __restrict__ target, double* r, int N,
-                              int N_pad, int S, int interior, int heat, double kappa) {
+                              int N_pad, int S, int interior, double cT, double cD) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     double v;
-    if (!interior) v = (double)zl[n] - target[n];
-    else if (heat) v = (double)zl[N_pad + n] - kappa * (double)zl[(long long)(S - 1) * N_pad + n] - target[n];
-    else v = -(double)zl[(long long)(S - 1) * N_pad + n] - target[n];
+    if (!interior) {
+        v = (double)zl[n] - target[n];
+    } else {
+        v = cD * (double)zl[(long long)(S - 1) * N_pad + n];
+        if (cT != 0.0) v += cT * (double)zl[N_pad + n];
+        v -= target[n];
+    }
     r[n] = v;
 }
 
-__global__ void k_extract_mx(const float* __restrict__ zl, int N, int N_pad, int S, int d, double* u, double* grad,
-                             double* lap) {
+// u, grad u (rotated back to the coordinate axes when the tangent directions
+// are the columns of Q) and the second-order column.
+__global__ void k_extract_mx(const float* __restrict__ zl, int N, int N_pad, int S, int d, const float* __restrict__ Qf,
+                             double* u, double* grad, double* lap) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     if (u) u[n] = zl[n];
-    if (grad)
-        for (int i = 0; i < d; i++) grad[(long long)n * d + i] = zl[(long long)(1 + i) * N_pad + n];
+    if (grad) {
+        for (int i = 0; i < d; i++) {
+            float g;
+            if (!Qf) {
+                g = zl[(long long)(1 + i) * N_pad + n];
+            } else {
+                g = 0.f;
+                for (int m = 0; m < d; m++) g = fmaf(Qf[(long long)i * d + m], zl[(long long)(1 + m) * N_pad + n], g);
+            }
+            grad[(long long)n * d + i] = g;
+        }
+    }
     if (lap) lap[n] = zl[(long long)(S - 1) * N_pad + n];
 }
 
@@ -314,8 +337,8 @@ __global__ void k_extract_mx(const float* __restrict__ zl, int N, int N_pad, int
 // r_n g for every Taylor row.
 __global__ void k_last_bwd(const float* __restrict__ wL, const bf16* __restrict__ T_hi, const float* __restrict__ A0,
                            const float* __restrict__ AD, const float* __restrict__ SSQ, const double* __restrict__ r,
-                           int N, int N_pad, int h, int hp, int S, int lap_first, int heat, float kappa,
-                           bf16* Zb, bf16* Gr) {
+                           int N, int N_pad, int h, int hp, int S, const float* __restrict__ chw, float cT,
+                           float cD, bf16* Zb, bf16* Gr) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long blk = (long long)N_pad * hp;
     if (idx >= blk) return;
@@ -331,15 +354,14 @@ __global__ void k_last_bwd(const float* __restrict__ wL, const bf16* __restrict_
         Gr[idx] = __float2bfloat16_rn(rn * ab);
         return;
     }
-    float cD = heat ? -kappa : -1.f;
-    float cT = heat ? 1.f : 0.f;      // seed on tangent column 1 (time) for heat
+    // seed c = dr/dZ^{(L)}: cD on the second-order column, cT on tangent column 1 (time, heat)
     float yD = cD * w;
     float cross = 0.f;
     for (int s = 1; s < S - 1; s++) {
         float yi = __bfloat162float(T_hi[s * blk + idx]);
         float ybar = (s == 1) ? cT * w : 0.f;
         float ab = s1 * ybar;
-        if (s >= lap_first) ab -= 4.f * y0 * yi * yD;
+        ab -= 4.f * chw[s - 1] * y0 * yi * yD;
         cross = fmaf(yi, ybar, cross);
         ab = live ? ab : 0.f;
         Zb[s * blk + idx] = __float2bfloat16_rn(ab);
@@ -478,26 +500,61 @@ __global__ void __launch_bounds__(RED_THREADS) k_factor_A1(const float* __restri
 __global__ void __launch_bounds__(RED_THREADS) k_grad_layer1(const bf16* __restrict__ Gr, const bf16* __restrict__ Grb,
                                                              const float* __restrict__ X,
                                                              const float* __restrict__ Xb, int N, int N_pad, int Nb,
-                                                             int d, int h, int hp, int S, double* grad) {
+                                                             int d, int h, int hp, int S, double* grad, double* gtan) {
+    // dL/dW~_1[j][k] = (1/N) sum_n (r g_{n,0,j} x_{n,k} + sum_m r g_{n,m,j} (v_m)_k) + boundary term;
+    // with gtan the tangent sums t_{j,m} = (1/N) sum_n r g_{n,m,j} are written there
+    // (the caller rotates them by the tangent directions), else v_m = e_m.
     __shared__ double shm[32][33];
     const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
     const int k = blockIdx.y, j = blockIdx.x * 32 + cl;
     const long long blk = (long long)N_pad * hp;
-    float a = 0.f, b = 0.f;     // FP32 partial sums per row group, combined in FP64
+    float a = 0.f, t = 0.f, b = 0.f;     // FP32 partial sums per row group, combined in FP64
     if (j < h) {
         for (int n = rg; n < N; n += 32) {
             float g0 = __bfloat162float(Gr[(long long)n * hp + j]);
-            if (k < d) a += fmaf(g0, X[(long long)n * d + k], __bfloat162float(Gr[(1 + k) * blk + (long long)n * hp + j]));
-            else a += g0;
+            if (k < d) {
+                a = fmaf(g0, X[(long long)n * d + k], a);
+                t += __bfloat162float(Gr[(1 + k) * blk + (long long)n * hp + j]);
+            } else {
+                a += g0;
+            }
         }
         for (int n = rg; n < Nb; n += 32) {
             float g0 = __bfloat162float(Grb[(long long)n * hp + j]);
             b += (k < d) ? g0 * Xb[(long long)n * d + k] : g0;
         }
     }
-    const double v = (double)a / N + (double)b / Nb;
+    const double tv = (double)t / N;
+    const double v = (double)a / N + (double)b / Nb + (gtan ? 0.0 : tv);
     const double s = reduce_row_groups(v, shm);
     if (rg == 0 && j < h) grad[j + (long long)h * k] = s;
+    if (gtan && k < d) {
+        __syncthreads();
+        const double st = reduce_row_groups(tv, shm);
+        if (rg == 0 && j < h) gtan[j + (long long)h * k] = st;
+    }
+}
+
+// grad[j][k] += sum_m t_{j,m} (v_m)_k for the first layer's input columns k < d.
+__global__ void k_rotate_grad1(const double* __restrict__ gtan, const float* __restrict__ Qf, int h, int d,
+                               double* grad) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)h * d) return;
+    const int j = (int)(idx % h), k = (int)(idx / h);
+    double acc = 0.0;
+    for (int m = 0; m < d; m++) acc += gtan[j + (long long)h * m] * (double)Qf[(long long)k * d + m];
+    grad[j + (long long)h * k] += acc;
+}
+
+// Tangent inputs of the first layer for the directions v_m = Q e_m: W1Qf[m][j] = sum_k W1f[k][j] Q[k][m].
+__global__ void k_rotate_first(const float* __restrict__ W1f, const float* __restrict__ Qf, int d, int hp,
+                               float* W1Qf) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)d * hp) return;
+    const int m = (int)(idx / hp), j = (int)(idx % hp);
+    float acc = 0.f;
+    for (int k = 0; k < d; k++) acc = fmaf(W1f[(long long)k * hp + j], Qf[(long long)k * d + m], acc);
+    W1Qf[idx] = acc;
 }
 
 // Last layer: gradient (1/N) sum_{n,s} r_n c_s T^_{n,s} + boundary, and the
@@ -505,12 +562,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_grad_layer1(const bf16* __restr
 __global__ void k_last_layer_terms(const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo,
                                    const bf16* __restrict__ Tb_hi, const bf16* __restrict__ Tb_lo,
                                    const double* __restrict__ r, const double* __restrict__ rb, int N, int N_pad,
-                                   int Nb, int Nb_pad, int h, int hp, int S, int heat, double kappa, int reduce,
+                                   int Nb, int Nb_pad, int h, int hp, int S, double cT, double cD, int reduce,
                                    double* grad, double* B_int, double* B_bdy, double beta, int* status) {
     __shared__ double shm[32][33];
     const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
     const int q = blockIdx.x * 32 + cl;
-    const double cD = heat ? -kappa : -1.0, cT = heat ? 1.0 : 0.0;
     const long long blk = (long long)N_pad * hp;
     double a = 0.0, b = 0.0;
     if (q < h) {
@@ -518,7 +574,7 @@ __global__ void k_last_layer_terms(const bf16* __restrict__ T_hi, const bf16* __
             double tD = (double)__bfloat162float(T_hi[(S - 1) * blk + (long long)n * hp + q]) +
                         (double)__bfloat162float(T_lo[blk + (long long)n * hp + q]);
             double v = cD * tD;
-            if (heat)
+            if (cT != 0.0)     // heat: the time tangent carries its low half (block 2)
                 v += cT * ((double)__bfloat162float(T_hi[blk + (long long)n * hp + q]) +
                            (double)__bfloat162float(T_lo[2 * blk + (long long)n * hp + q]));
             a += r[n] * v;
@@ -571,7 +627,7 @@ Args base_args(kfac_pinn_handle* h, const MxPass& P, int N) {
     a.N_pad = P.N_pad;
     a.N = N;
     a.S = P.S;
-    a.lap_first = (h->cfg.op == KFAC_OP_HEAT) ? 2 : 1;
+    a.chw = h->chw32;
     a.split_time = (h->cfg.op == KFAC_OP_HEAT && P.S > 2) ? 1 : 0;
     a.status = h->status;
     return a;
@@ -695,6 +751,10 @@ kfac_status_t convert_weights(kfac_pinn_handle* h, cudaStream_t s, const double*
         k_convert_first<<<ceil_div_u((long long)(d + 1) * hp1, EW), EW, 0, s>>>(theta + h->woff[0], h1, hp1, d,
                                                                                  w.W1f);
         KFAC_LAUNCH_CHECK(h);
+        if (w.W1Qf) {
+            k_rotate_first<<<ceil_div_u((long long)d * hp1, EW), EW, 0, s>>>(w.W1f, MX(h)->Qf, d, hp1, w.W1Qf);
+            KFAC_LAUNCH_CHECK(h);
+        }
     }
     int hin = h->dims[L - 1], hin_p = round_up(hin, 64);
     k_convert_last<<<ceil_div_u(hin_p + 1, EW), EW, 0, s>>>(theta + h->woff[L - 1], hin, hin_p, w.wL);
@@ -706,15 +766,16 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
                            MxPass& P, BlockSel sel) {
     MxState* m = MX(h);
     const int L = h->cfg.L, d = h->dims[0], S = P.S;
-    const int lap_first = (h->cfg.op == KFAC_OP_HEAT) ? 2 : 1;
     {
         MxLayer& l1 = P.lay[0];
         long long cnt = (long long)P.N_pad * l1.hp;
         timer_begin(h, KFAC_KC_ELEMENTWISE, s);
         k_points_f32<<<ceil_div_u((long long)P.N_pad * d, EW), EW, 0, s>>>(X, N, P.N_pad, d, P.Xf);
         KFAC_LAUNCH_CHECK(h);
-        k_layer1<<<ceil_div_u(cnt / 4, EW), EW, 0, s>>>(m->w.W1f, P.Xf, N, P.N_pad, d, l1.h, l1.hp, S, lap_first,
-                                                         l1.T_hi, l1.T_lo, l1.A0, l1.AD, l1.SSQ);
+        k_layer1<<<ceil_div_u(cnt / 4, EW), EW, 0, s>>>(m->w.W1f, m->w.W1Qf ? m->w.W1Qf : m->w.W1f, P.Xf, N,
+                                                         P.N_pad, d, l1.h, l1.hp, S, h->chw32,
+                                                         (h->cfg.op == KFAC_OP_HEAT && S > 2) ? 1 : 0, l1.T_hi,
+                                                         l1.T_lo, l1.A0, l1.AD, l1.SSQ);
         timer_end(h, KFAC_KC_ELEMENTWISE, s, 2.0 * (double)S * cnt + 16.0 * cnt);
         KFAC_LAUNCH_CHECK(h);
     }
@@ -765,14 +826,13 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
 kfac_status_t backward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* r, int N, MxPass& P) {
     MxState* m = MX(h);
     const int L = h->cfg.L, S = P.S;
-    const int lap_first = (h->cfg.op == KFAC_OP_HEAT) ? 2 : 1;
     {
         MxLayer& ly = P.lay[L - 2];
         long long cnt = (long long)P.N_pad * ly.hp;
         timer_begin(h, KFAC_KC_ELEMENTWISE, s);
         k_last_bwd<<<ceil_div_u(cnt, EW), EW, 0, s>>>(m->w.wL, ly.T_hi, ly.A0, ly.AD, ly.SSQ, r, N, P.N_pad, ly.h,
-                                                       ly.hp, S, lap_first, h->cfg.op == KFAC_OP_HEAT,
-                                                       (float)h->cfg.kappa, ly.Zb, ly.Gr);
+                                                       ly.hp, S, h->chw32, (float)h->cT, (float)h->cD, ly.Zb,
+                                                       ly.Gr);
         timer_end(h, KFAC_KC_ELEMENTWISE, s, 6.0 * S * (double)cnt);
         KFAC_LAUNCH_CHECK(h);
     }
@@ -836,8 +896,13 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
         KFAC_LAUNCH_CHECK(h);
         MxLayer& l1 = I.lay[0];
         k_grad_layer1<<<dim3(ceil_div_u(l1.h, 32), d + 1), RED_THREADS, 0, s>>>(
-            l1.Gr, B.lay[0].Gr, I.Xf, B.Xf, N, I.N_pad, Nb, d, l1.h, l1.hp, S, h->grad + h->woff[0]);
+            l1.Gr, B.lay[0].Gr, I.Xf, B.Xf, N, I.N_pad, Nb, d, l1.h, l1.hp, S, h->grad + h->woff[0], m->gtan);
         KFAC_LAUNCH_CHECK(h);
+        if (m->gtan) {
+            k_rotate_grad1<<<ceil_div_u((long long)l1.h * d, EW), EW, 0, s>>>(m->gtan, m->Qf, l1.h, d,
+                                                                              h->grad + h->woff[0]);
+            KFAC_LAUNCH_CHECK(h);
+        }
     }
     // ---- hidden-layer output factors B_l, l = 1..L-1 -----------------------
     for (int l = 1; l <= L - 1; l++) {
@@ -910,7 +975,7 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
         } else {
             k_last_layer_terms<<<ceil_div_u(hin + 1, 32), RED_THREADS, 0, s>>>(
                 ti.T_hi, ti.T_lo, tb.T_hi, tb.T_lo, h->in.r, h->bd.r, N, I.N_pad, Nb, B.N_pad, hin, ti.hp, S,
-                h->cfg.op == KFAC_OP_HEAT, h->cfg.kappa, reduce, h->grad + h->woff[L - 1], h->fac[KFAC_B_INT][L - 1],
+                h->cT, h->cD, reduce, h->grad + h->woff[L - 1], h->fac[KFAC_B_INT][L - 1],
                 h->fac[KFAC_B_BDY][L - 1], beta, h->status);
             KFAC_LAUNCH_CHECK(h);
         }
@@ -949,6 +1014,19 @@ kfac_status_t tc_alloc(kfac_pinn_handle* h) {
     }
     if ((st = dal(&m->w.wL, (size_t)round_up(h->dims[L - 1], 64) + 1))) return st;
     if ((st = dal(&m->w.W1f, (size_t)(h->dims[0] + 1) * round_up(h->dims[1], 64)))) return st;
+    if (h->opQ) {
+        const int d = h->dims[0];
+        if ((st = dal(&m->w.W1Qf, (size_t)d * round_up(h->dims[1], 64)))) return st;
+        if ((st = dal(&m->Qf, (size_t)d * d))) return st;
+        if ((st = dal(&m->gtan, (size_t)h->dims[1] * d))) return st;
+        std::vector<double> q((size_t)d * d);
+        std::vector<float> qf((size_t)d * d);
+        if (cudaMemcpy(q.data(), h->opQ, sizeof(double) * d * d, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return KFAC_CUDA_ERROR;
+        for (size_t i = 0; i < q.size(); i++) qf[i] = (float)q[i];
+        if (cudaMemcpy(m->Qf, qf.data(), sizeof(float) * d * d, cudaMemcpyHostToDevice) != cudaSuccess)
+            return KFAC_CUDA_ERROR;
+    }
     if ((st = dal(&m->part, (size_t)MAX_CHUNKS * m->in.N_pad * hp_max))) return st;
     size_t maxPQ = (size_t)hp_max * hp_max;
     m->gpart_region = (size_t)MAX_GRAM_CHUNKS * maxPQ;
@@ -967,6 +1045,9 @@ void tc_free(kfac_pinn_handle* h) {
     }
     cudaFree(m->w.wL);
     cudaFree(m->w.W1f);
+    cudaFree(m->w.W1Qf);
+    cudaFree(m->Qf);
+    cudaFree(m->gtan);
     cudaFree(m->part);
     cudaFree(m->gpart);
     cudaFree(m->cs);
@@ -992,8 +1073,8 @@ kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const d
     si.b[2] = 0;
     si.split_time = heat;
     if ((st = forward_pass(h, s, theta, X_int, N_int, m->in, si))) return st;
-    k_residual_mx<<<ceil_div_u(N_int, EW), EW, 0, s>>>(m->in.zl, f, h->in.r, N_int, m->in.N_pad, S, 1, heat,
-                                                        h->cfg.kappa);
+    k_residual_mx<<<ceil_div_u(N_int, EW), EW, 0, s>>>(m->in.zl, f, h->in.r, N_int, m->in.N_pad, S, 1, h->cT,
+                                                        h->cD);
     KFAC_LAUNCH_CHECK(h);
     BlockSel sb;
     sb.nsel = 1;
@@ -1001,8 +1082,8 @@ kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const d
     sb.b[1] = sb.b[2] = 0;
     sb.split_time = 0;
     if ((st = forward_pass(h, s, theta, X_bdy, N_bdy, m->bd, sb))) return st;
-    k_residual_mx<<<ceil_div_u(N_bdy, EW), EW, 0, s>>>(m->bd.zl, g, h->bd.r, N_bdy, m->bd.N_pad, 1, 0, heat,
-                                                        h->cfg.kappa);
+    k_residual_mx<<<ceil_div_u(N_bdy, EW), EW, 0, s>>>(m->bd.zl, g, h->bd.r, N_bdy, m->bd.N_pad, 1, 0, h->cT,
+                                                        h->cD);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }
@@ -1037,7 +1118,8 @@ kfac_status_t tc_forward_laplacian(kfac_pinn_handle* h, cudaStream_t s, const do
     all.b[0] = all.b[1] = all.b[2] = 0;
     all.split_time = (h->cfg.op == KFAC_OP_HEAT) ? 1 : 0;
     if ((st = forward_pass(h, s, theta, X, N, m->in, all))) return st;
-    k_extract_mx<<<ceil_div_u(N, EW), EW, 0, s>>>(m->in.zl, N, m->in.N_pad, m->in.S, h->dims[0], u, grad, lap);
+    k_extract_mx<<<ceil_div_u(N, EW), EW, 0, s>>>(m->in.zl, N, m->in.N_pad, m->in.S, h->dims[0], m->Qf, u, grad,
+                                                   lap);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }

@@ -192,6 +192,34 @@ WORKLOADS: Dict[str, Workload] = {
 }
 
 
+@dataclass(frozen=True)
+class BatchMember:
+    """One problem of the many-PINN serving workload."""
+    d: int
+    widths: Tuple[int, ...]
+    n_int: int
+    n_bdy: int
+
+    @property
+    def prob(self) -> Problem:
+        return poisson_cos_problem(self.d)
+
+
+def many_pinns(count: int = 64, seed: int = 0) -> Tuple[BatchMember, ...]:
+    """Independent Poisson PINNs of uneven size: d uniform in {2, 5, 10, 20, 50},
+    2 or 3 hidden tanh layers (3 or 4 linear layers) with widths uniform in
+    {32, 64, 128, 256, 512}, N_Ω uniform in [500, 4000] and N_∂ = N_Ω / 4."""
+    rng = np.random.Generator(np.random.PCG64([seed, 64]))
+    out = []
+    for _ in range(count):
+        d = int(rng.choice([2, 5, 10, 20, 50]))
+        depth = int(rng.integers(3, 5))
+        widths = tuple(int(rng.choice([32, 64, 128, 256, 512])) for _ in range(depth - 1)) + (1,)
+        n_int = int(rng.integers(500, 4001))
+        out.append(BatchMember(d, widths, n_int, max(1, n_int // 4)))
+    return tuple(out)
+
+
 def make_batch(prob: Problem, n_int: int, n_bdy: int, seed: int, step: int = 0):
     """Interior points, f, boundary points, g for one step of a seeded stream."""
     rng = np.random.Generator(np.random.PCG64([seed, step]))

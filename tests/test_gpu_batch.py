@@ -1,0 +1,74 @@
+"""Batched stepping of many independent problems (worker streams, CUDA graph
+capture and replay) gives the same parameters as stepping each problem on its
+own, for every update rule and both precisions."""
+import numpy as np
+import pytest
+import torch
+
+from synth import inputs as si
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _members():
+    return [si.BatchMember(2, (32, 32, 1), 300, 60), si.BatchMember(5, (64, 48, 1), 517, 130),
+            si.BatchMember(10, (128, 64, 32, 1), 211, 53), si.BatchMember(20, (32, 256, 1), 400, 100),
+            si.BatchMember(7, (40, 72, 1), 67, 13)]
+
+
+def _make(members, precision, update):
+    from paper_2405_15603_gb300.api import KfacPinn
+    kw = dict(lam=1e-3, beta=0.9, lr=0.05, momentum=0.5, init_identity=True, update=update, eig_sm_budget=30)
+    return [KfacPinn(m.d, m.widths, device=DEV, precision=precision, max_n_int=m.n_int, max_n_bdy=m.n_bdy, **kw)
+            for m in members]
+
+
+@pytest.mark.parametrize("precision,update", [("fp64", "fixed"), ("mixed_bf16", "line_search"),
+                                              ("fp64", "kfac_star")])
+def test_batch_matches_individual_steps(precision, update):
+    from paper_2405_15603_gb300.api import KfacBatch
+    members = _members()
+    solo = _make(members, precision, update)
+    batched = _make(members, precision, update)
+    th0 = [torch.tensor(si.xavier_theta(m.d, m.widths, i), device=DEV) for i, m in enumerate(members)]
+    th_solo = [t.clone() for t in th0]
+    th_b = [t.clone() for t in th0]
+    # fixed input buffers (the graph replays read from the same addresses)
+    bufs = [[torch.empty(m.n_int, m.d, dtype=torch.float64, device=DEV),
+             torch.empty(m.n_int, dtype=torch.float64, device=DEV),
+             torch.empty(m.n_bdy, m.d, dtype=torch.float64, device=DEV),
+             torch.empty(m.n_bdy, dtype=torch.float64, device=DEV)] for m in members]
+    losses = [torch.zeros(3, dtype=torch.float64, device=DEV) for _ in members]
+    batch = KfacBatch(batched, n_streams=3)
+    for step in range(4):                     # eager, capture, replay, replay
+        for i, m in enumerate(members):
+            arrs = si.make_batch(m.prob, m.n_int, m.n_bdy, seed=i, step=step)
+            for b, a in zip(bufs[i], arrs):
+                b.copy_(torch.from_numpy(a))
+            solo[i].step(th_solo[i], *bufs[i])
+        batch.step(th_b, [b[0] for b in bufs], [b[1] for b in bufs], [b[2] for b in bufs],
+                   [b[3] for b in bufs], losses)
+        torch.cuda.synchronize()
+        for i in range(len(members)):
+            assert torch.equal(th_b[i], th_solo[i]), (step, i)
+    for opt in solo + batched:
+        assert opt.sync_status() == "KFAC_OK"
+    batch.close()
+
+
+def test_batch_rejects_bad_arguments():
+    from paper_2405_15603_gb300.api import KfacBatch, KfacError
+    members = _members()[:2]
+    opts = _make(members, "fp64", "fixed")
+    with pytest.raises(KfacError):
+        KfacBatch(opts, n_streams=0)
+    batch = KfacBatch(opts, n_streams=2)
+    too_many = [torch.zeros(m.n_int + 1, m.d, dtype=torch.float64, device=DEV) for m in members]
+    small = [torch.zeros(m.n_int, dtype=torch.float64, device=DEV) for m in members]
+    xb = [torch.zeros(m.n_bdy, m.d, dtype=torch.float64, device=DEV) for m in members]
+    gb = [torch.zeros(m.n_bdy, dtype=torch.float64, device=DEV) for m in members]
+    th = [torch.zeros(o.D, dtype=torch.float64, device=DEV) for o in opts]
+    with pytest.raises(KfacError):
+        batch.step(th, too_many, small, xb, gb)
+    batch.close()

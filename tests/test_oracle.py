@@ -213,7 +213,7 @@ def test_adjoint_vs_finite_differences_of_intermediate():
     X = np.random.default_rng(8).uniform(size=(1, d))
     fp = ko.taylor_forward(Ws, X)
     zb = ko.taylor_adjoint(Ws, fp, ko.residual_seed(fp.S, "laplace", 0.0, True))
-    lap_set = ko.laplacian_set(d, "laplace")
+    lap_set = ko.operator_matrix(d, "laplace")
 
     def r_from(l, Z):
         T = ko.append_bias_row(ko.tanh_taylor(Z, lap_set))
@@ -585,3 +585,46 @@ def test_kfac_star_minimises_quadratic_model():
     # stationarity of the model in (α, μ) with the dense Gramian
     np.testing.assert_allclose([Dl @ (gr + G @ (a * Dl + m * dl)), dl @ (gr + G @ (a * Dl + m * dl))],
                                [0.0, 0.0], atol=1e-9 * abs(Dl @ gr))
+
+
+# --------------------------------------------------------------------------
+# General second-order operator Σ c_ij ∂²_ij (App. C.3)
+# --------------------------------------------------------------------------
+def _sym(d, seed):
+    rng = np.random.default_rng(seed)
+    M = rng.standard_normal((d, d))
+    return 0.5 * (M + M.T)       # indefinite in general
+
+
+def test_general_operator_forward_vs_autograd():
+    d, widths = 4, (7, 5, 1)
+    th = _theta(d, widths, seed=60)
+    X = np.random.default_rng(61).random((6, d))
+    C = _sym(d, 62)
+    Ws = ko.unpack_theta(th, d, widths)
+    u, g, cu = ko.forward_laplacian(Ws, X, "general", C)
+    np.testing.assert_allclose(cu, tr.operator_value(th, d, widths, X, C), rtol=1e-11, atol=1e-12)
+    # c = I reproduces the Laplacian column, c = diag(0, 1, ..) the heat operator's
+    _, _, lap = ko.forward_laplacian(Ws, X, "laplace")
+    np.testing.assert_allclose(ko.forward_laplacian(Ws, X, "general", np.eye(d))[2], lap, rtol=1e-13)
+    _, _, plap = ko.forward_laplacian(Ws, X, "heat")
+    np.testing.assert_allclose(ko.forward_laplacian(Ws, X, "general", np.diag([0.0] + [1.0] * (d - 1)))[2],
+                               plap, rtol=1e-13)
+
+
+def test_general_operator_jacobian_and_gradient_vs_autograd():
+    d, widths = 3, (6, 4, 1)
+    th = _theta(d, widths, seed=63)
+    rng = np.random.default_rng(64)
+    Xi, f = rng.random((5, d)), rng.standard_normal(5)
+    Xb, g = rng.random((4, d)), rng.standard_normal(4)
+    C = _sym(d, 65)
+    cfg = ko.KfacConfig(d=d, widths=widths, op="general", op_coef=C)
+    cg = ko.curvature_and_gradient(cfg, ko.unpack_theta(th, d, widths), Xi, f, Xb, g)
+    J = tr.residual_jacobians(th, d, widths, Xi, f, op="general", coef=C)
+    Jo = np.stack([np.concatenate([ko.weight_jacobian(cg["zb_i"][l][n:n + 1], cg["fp_i"].T_in[l][n:n + 1])[0]
+                                   .reshape(-1, order="F") for l in range(len(widths))]) for n in range(5)])
+    np.testing.assert_allclose(Jo, J, rtol=1e-10, atol=1e-12)
+    Jb = tr.residual_jacobians(th, d, widths, Xb, g, interior=False)
+    grad = J.T @ cg["r_i"] / 5 + Jb.T @ cg["r_b"] / 4
+    np.testing.assert_allclose(ko.pack_theta(cg["grads"]), grad, rtol=1e-10, atol=1e-12)

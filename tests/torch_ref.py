@@ -53,7 +53,7 @@ def value_grad_lap(theta: np.ndarray, d: int, widths, X: np.ndarray, lap_coords=
     return np.array(us), np.stack(gs), np.array(ls)
 
 
-def residual_fn(d, widths, op, kappa):
+def residual_fn(d, widths, op, kappa, coef=None):
     """Returns r(theta_t, x, target, interior) as a torch scalar function."""
     def r(theta_t, x, target, interior):
         net = mlp_from_flat(theta_t, d, widths)
@@ -62,6 +62,13 @@ def residual_fn(d, widths, op, kappa):
         xg = x.clone().requires_grad_(True)
         u = net(xg)
         (g,) = torch.autograd.grad(u, xg, create_graph=True)
+        if op == "general":                       # sum_ij c_ij d2u/dx_i dx_j - f
+            C = torch.as_tensor(coef, dtype=torch.float64)
+            tot = 0.0
+            for i in range(d):
+                (gi,) = torch.autograd.grad(g[i], xg, create_graph=True)
+                tot = tot + (C[i] * gi).sum()
+            return tot - target
         lap = 0.0
         coords = range(1, d) if op == "heat" else range(d)
         for i in coords:
@@ -73,9 +80,9 @@ def residual_fn(d, widths, op, kappa):
     return r
 
 
-def residual_jacobians(theta, d, widths, X, targets, op="laplace", kappa=0.0, interior=True):
+def residual_jacobians(theta, d, widths, X, targets, op="laplace", kappa=0.0, interior=True, coef=None):
     """Rows J_θ r_n (N x D) by autograd."""
-    rf = residual_fn(d, widths, op, kappa)
+    rf = residual_fn(d, widths, op, kappa, coef)
     rows = []
     for x, t in zip(X, targets):
         th = torch.as_tensor(theta, dtype=torch.float64).clone().requires_grad_(True)
@@ -90,3 +97,15 @@ def residuals(theta, d, widths, X, targets, op="laplace", kappa=0.0, interior=Tr
     th = torch.as_tensor(theta, dtype=torch.float64)
     return np.array([float(rf(th, torch.as_tensor(x, dtype=torch.float64), float(t), interior))
                      for x, t in zip(X, targets)])
+
+
+def operator_value(theta: np.ndarray, d: int, widths, X: np.ndarray, coef: np.ndarray):
+    """sum_ij c_ij d2u/dx_i dx_j per point from the autograd Hessian."""
+    th = torch.as_tensor(theta, dtype=torch.float64)
+    net = mlp_from_flat(th, d, widths)
+    C = torch.as_tensor(coef, dtype=torch.float64)
+    out = []
+    for x in X:
+        H = torch.autograd.functional.hessian(net, torch.as_tensor(x, dtype=torch.float64))
+        out.append(float((C * H).sum()))
+    return np.array(out)
