@@ -26,6 +26,7 @@ namespace {
 constexpr int NB = 64;        // Cholesky / TRSM block
 constexpr int CB = 32;        // TRSM column block
 constexpr int BT_COLS = 16;   // back-transform column block
+constexpr int KFAC_MAX_WIDTH_PLUS_ONE = 1024;   // widths <= 1023 and d + 1 <= 1024 (create checks)
 constexpr int MAXP = 2 * KFAC_MAX_LAYERS;
 constexpr double DEPS = 2.220446049250313e-16;
 
@@ -1251,8 +1252,13 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
                          (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB + 1)));
     cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(double) * 2 * NB * (NB + 1));
-    if (bt_smem_bytes(es->nmax) > 220 * 1024) return KFAC_BAD_ARG;
-    cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem_bytes(es->nmax));
+    // The attribute belongs to the kernel, not to this handle: set it for the
+    // largest factor any handle can have (h_l + 1 <= 1024), so that handles of
+    // different sizes can be created in any order.
+    static_assert(KFAC_MAX_WIDTH_PLUS_ONE == 1024, "factor size bound");
+    if (bt_smem_bytes(es->nmax) > bt_smem_bytes(KFAC_MAX_WIDTH_PLUS_ONE)) return KFAC_BAD_ARG;
+    cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bt_smem_bytes(KFAC_MAX_WIDTH_PLUS_ONE));
     return cudaGetLastError() == cudaSuccess ? KFAC_OK : KFAC_CUDA_ERROR;
 }
 
