@@ -126,6 +126,11 @@ int64_t kfac_pinn_param_count(const kfac_config_t* cfg);
 /* Human-readable name of a status code (static string). */
 const char* kfac_pinn_status_string(kfac_status_t st);
 
+/* The cudaError_t behind the last KFAC_CUDA_ERROR returned on the calling host
+ * thread (0 if none), and its description (static string). */
+int kfac_pinn_last_cuda_error(void);
+const char* kfac_pinn_last_cuda_error_string(void);
+
 /* Create a handle on the current CUDA device: validates cfg, allocates every
  * internal buffer for max_n_int / max_n_bdy points, and sets the EMA factors
  * to their initial value (0 or I), momentum to 0 and the step counter to 0.

@@ -18,7 +18,7 @@ EXPORTS = [
     "kfac_pinn_timing_enable", "kfac_pinn_timing_read", "kfac_pinn_forward_laplacian_noalloc",
     "kfac_pinn_get_line_search_losses", "kfac_pinn_forward_laplacian_backward",
     "kfac_pinn_get_update_coefficients", "kfac_pinn_batch_create", "kfac_pinn_batch_destroy",
-    "kfac_pinn_batch_step",
+    "kfac_pinn_batch_step", "kfac_pinn_last_cuda_error", "kfac_pinn_last_cuda_error_string",
 ]
 
 KERNEL_CLASSES = {0: "layer_gemm", 1: "adjoint_gemm", 2: "gram", 3: "elementwise", 4: "eig", 5: "precond"}
@@ -37,7 +37,10 @@ class KfacConfig(C.Structure):
 
 class KfacError(RuntimeError):
     def __init__(self, fn: str, code: int):
-        super().__init__(f"{fn} returned {STATUS.get(code, code)}")
+        msg = f"{fn} returned {STATUS.get(code, code)}"
+        if code == 6 and _LIB is not None:      # KFAC_CUDA_ERROR: name the CUDA error behind it
+            msg += f" ({_LIB.kfac_pinn_last_cuda_error_string().decode()})"
+        super().__init__(msg)
         self.code = code
         self.status = STATUS.get(code, str(code))
 
@@ -80,6 +83,8 @@ def load() -> C.CDLL:
         "kfac_pinn_get_direction": (st, [H, P, P]),
         "kfac_pinn_get_line_search_losses": (st, [H, P, P]),
         "kfac_pinn_get_update_coefficients": (st, [H, P, P]),
+        "kfac_pinn_last_cuda_error": (I, []),
+        "kfac_pinn_last_cuda_error_string": (C.c_char_p, []),
         "kfac_pinn_batch_create": (st, [P, I, I, C.POINTER(C.c_void_p)]),
         "kfac_pinn_batch_destroy": (st, [P]),
         "kfac_pinn_batch_step": (st, [P, P, P, P, P, P, P, P, P, P, I]),

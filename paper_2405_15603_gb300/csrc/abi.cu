@@ -326,7 +326,19 @@ void timers_free(kfac_pinn_handle* h) {
     }
 }
 
+namespace {
+thread_local int g_last_cuda_error = 0;
+}
+
+void kfac_record_cuda_error(cudaError_t e) { g_last_cuda_error = (int)e; }
+
 extern "C" {
+
+int kfac_pinn_last_cuda_error(void) { return g_last_cuda_error; }
+
+const char* kfac_pinn_last_cuda_error_string(void) {
+    return cudaGetErrorString((cudaError_t)g_last_cuda_error);
+}
 
 kfac_status_t kfac_pinn_timing_enable(kfac_handle_t h, int enable) {
     if (!h) return KFAC_BAD_ARG;

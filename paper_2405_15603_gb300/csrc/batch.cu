@@ -15,6 +15,8 @@ struct kfac_pinn_batch {
     std::vector<const void*> key_ptr;     // pointers and counts the graph was captured with
     std::vector<int> key_n;
     std::vector<long long> graph_launches;   // kernels each handle has in the graph
+    cudaStream_t cap;                        // capture / replay stream (the caller's may be the legacy one)
+    cudaEvent_t ev_in, ev_out;
 };
 
 namespace {
@@ -22,6 +24,9 @@ namespace {
 void batch_free(kfac_pinn_batch* b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
@@ -66,7 +71,15 @@ kfac_status_t kfac_pinn_batch_create(const kfac_handle_t* handles, int count, in
     b->calls = 0;
     b->exec = nullptr;
     b->fork = nullptr;
-    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) { batch_free(b); return KFAC_CUDA_ERROR; }
+    b->cap = nullptr;
+    b->ev_in = b->ev_out = nullptr;
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        batch_free(b);
+        return KFAC_CUDA_ERROR;
+    }
     for (int w = 0; w < n_streams; w++) {
         cudaStream_t st;
         cudaEvent_t ev;
@@ -82,6 +95,7 @@ kfac_status_t kfac_pinn_batch_create(const kfac_handle_t* handles, int count, in
 kfac_status_t kfac_pinn_batch_destroy(kfac_batch_t b) {
     if (!b) return KFAC_BAD_ARG;
     for (cudaStream_t s : b->streams) cudaStreamSynchronize(s);
+    if (b->cap) cudaStreamSynchronize(b->cap);
     batch_free(b);
     return KFAC_OK;
 }
@@ -109,26 +123,37 @@ kfac_status_t kfac_pinn_batch_step(kfac_batch_t b, void* stream, double* const* 
         kn.push_back(N_int[i]);
         kn.push_back(N_bdy[i]);
     }
+    // Graphs are captured and replayed on the batch's own stream, ordered after
+    // the work already queued on the caller's stream and before what follows it.
+    KFAC_CUDA_TRY(cudaEventRecord(b->ev_in, s));
+    KFAC_CUDA_TRY(cudaStreamWaitEvent(b->cap, b->ev_in, 0));
     if (!b->exec || kp != b->key_ptr || kn != b->key_n) {
         if (b->exec) {
             cudaGraphExecDestroy(b->exec);
             b->exec = nullptr;
         }
-        // the host-side step counters advance during capture exactly as in an eager step
         std::vector<long long> before;
         for (kfac_handle_t h : b->handles) before.push_back(h->launches);
-        KFAC_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        kfac_status_t st = enqueue(b, s, theta, X_int, N_int, f, X_bdy, N_bdy, g, loss);
+        // the host-side step counters advance during capture exactly as in an eager step
+        KFAC_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        kfac_status_t st = enqueue(b, b->cap, theta, X_int, N_int, f, X_bdy, N_bdy, g, loss);
         cudaGraph_t graph = nullptr;
-        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        cudaError_t ce = cudaStreamEndCapture(b->cap, &graph);
         if (st) {
             if (graph) cudaGraphDestroy(graph);
             return st;
         }
-        if (ce != cudaSuccess) return KFAC_CUDA_ERROR;
+        if (ce != cudaSuccess) {
+            kfac_record_cuda_error(ce);
+            return KFAC_CUDA_ERROR;
+        }
         ce = cudaGraphInstantiate(&b->exec, graph, 0);
         cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) { b->exec = nullptr; return KFAC_CUDA_ERROR; }
+        if (ce != cudaSuccess) {
+            kfac_record_cuda_error(ce);
+            b->exec = nullptr;
+            return KFAC_CUDA_ERROR;
+        }
         b->key_ptr = kp;
         b->key_n = kn;
         b->graph_launches.clear();
@@ -140,7 +165,9 @@ kfac_status_t kfac_pinn_batch_step(kfac_batch_t b, void* stream, double* const* 
             b->handles[i]->launches += b->graph_launches[i];
         }
     }
-    KFAC_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+    KFAC_CUDA_TRY(cudaGraphLaunch(b->exec, b->cap));
+    KFAC_CUDA_TRY(cudaEventRecord(b->ev_out, b->cap));
+    KFAC_CUDA_TRY(cudaStreamWaitEvent(s, b->ev_out, 0));
     return KFAC_OK;
 }
 

@@ -1321,9 +1321,20 @@ kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
     KFAC_CUDA_TRY(cudaMemsetAsync(es->bar, 0, sizeof(unsigned) * 3 * np, s));
     KFAC_CUDA_TRY(cudaMemsetAsync(es->abort_flag, 0, sizeof(int), s));
     {
-        void* args[] = {&pr, &es->cta_prob, &es->cta_rank, &es->group, &es->bar, &es->abort_flag, &h->status,
-                        &es->fail};
-        KFAC_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_tridiag, dim3(es->n_cta), dim3(512), args, 0, s));
+        // cooperative launch (every CTA co-resident), in the form stream capture accepts
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeCooperative;
+        attr.val.cooperative = 1;
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(es->n_cta);
+        lc.blockDim = dim3(512);
+        lc.dynamicSmemBytes = 0;
+        lc.stream = s;
+        lc.attrs = &attr;
+        lc.numAttrs = 1;
+        KFAC_CUDA_TRY(cudaLaunchKernelEx(&lc, k_tridiag, (Prob*)pr, (const int*)es->cta_prob,
+                                         (const int*)es->cta_rank, (const int*)es->group, (unsigned*)es->bar,
+                                         (int*)es->abort_flag, (int*)h->status, (int*)es->fail));
         h->launches++;
     }
     // 4. divide and conquer

@@ -106,17 +106,27 @@ KFAC_DEV void latch_status(int* status, int code) {
     atomicCAS(status, 0, code);
 }
 
+// The CUDA error behind the last KFAC_CUDA_ERROR on this host thread
+// (kfac_pinn_last_cuda_error).
+void kfac_record_cuda_error(cudaError_t e);
+
 #define KFAC_CUDA_TRY(expr)                                   \
     do {                                                      \
         cudaError_t _e = (expr);                              \
-        if (_e != cudaSuccess) return KFAC_CUDA_ERROR;        \
+        if (_e != cudaSuccess) {                              \
+            kfac_record_cuda_error(_e);                       \
+            return KFAC_CUDA_ERROR;                           \
+        }                                                     \
     } while (0)
 
 #define KFAC_LAUNCH_CHECK(h)                                  \
     do {                                                      \
         (h)->launches++;                                      \
         cudaError_t _e = cudaGetLastError();                  \
-        if (_e != cudaSuccess) return KFAC_CUDA_ERROR;        \
+        if (_e != cudaSuccess) {                              \
+            kfac_record_cuda_error(_e);                       \
+            return KFAC_CUDA_ERROR;                           \
+        }                                                     \
     } while (0)
 
 // Device timers: bracket a launch with events when timing is enabled.
