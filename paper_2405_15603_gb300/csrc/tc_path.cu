@@ -633,13 +633,31 @@ Args base_args(kfac_pinn_handle* h, const MxPass& P, int N) {
     return a;
 }
 
+// Fraction of the SM-time of ceil(ctas / sm) full waves that `ctas` equal CTAs
+// (one per SM at a time) keep busy.
+double wave_efficiency(long long ctas, int sm) {
+    const long long waves = (ctas + sm - 1) / sm;
+    return (double)ctas / (double)(waves * sm);
+}
+
+// Split the S_tiles tangent tiles of each of `blocks` output tiles into chunks
+// (one CTA each) so that the waves are full and the chunks even; ties keep
+// fewer, longer chunks (fewer partial sums to combine).
 void choose_chunks(int S_tiles, int blocks, int sm, int& chunk_len, int& n_chunks) {
-    int want = (4 * sm + blocks - 1) / blocks;
-    if (want < 1) want = 1;
-    if (want > MAX_CHUNKS) want = MAX_CHUNKS;
-    if (want > S_tiles) want = S_tiles;
-    chunk_len = (S_tiles + want - 1) / want;
-    n_chunks = (S_tiles + chunk_len - 1) / chunk_len;
+    double best = -1.0;
+    n_chunks = 1;
+    chunk_len = S_tiles;
+    const int top = S_tiles < MAX_CHUNKS ? S_tiles : MAX_CHUNKS;
+    for (int n = 1; n <= top; n++) {
+        const int len = (S_tiles + n - 1) / n;
+        const int cnt = (S_tiles + len - 1) / len;
+        const double e = wave_efficiency((long long)blocks * cnt, sm) * (double)S_tiles / ((double)cnt * len);
+        if (e > best + 1e-9) {
+            best = e;
+            n_chunks = cnt;
+            chunk_len = len;
+        }
+    }
 }
 
 kfac_status_t alloc_pass(kfac_pinn_handle* h, MxPass& P, int Nmax, int S) {
@@ -709,12 +727,21 @@ kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, co
     int p_tiles = (P + 127) / 128, q_tiles = (Q + C::BN - 1) / C::BN;
     int tiles = 0;
     for (int pb = 0; pb < p_tiles; pb++) tiles += q_tiles - (sym ? (pb * 128) / C::BN : 0);
-    int want = (2 * h->sm_count + tiles - 1) / tiles;
+    // split-K over the rows: full waves of one CTA per SM and even chunks
     int max_chunks = (int)(MX(h)->gpart_region / ((size_t)P * Q));
-    if (want > MAX_GRAM_CHUNKS) want = MAX_GRAM_CHUNKS;
-    if (want > max_chunks) want = max_chunks;
-    if (want < 1) return KFAC_BAD_ARG;
-    int chunk = round_up((rows + want - 1) / want, 64);
+    if (max_chunks > MAX_GRAM_CHUNKS) max_chunks = MAX_GRAM_CHUNKS;
+    if (max_chunks < 1) return KFAC_BAD_ARG;
+    int chunk = round_up(rows, 64);
+    double best = -1.0;
+    for (int want = 1; want <= max_chunks; want++) {
+        const int c = round_up((rows + want - 1) / want, 64);
+        const int cnt = (rows + c - 1) / c;
+        const double e = wave_efficiency((long long)tiles * cnt, h->sm_count) * (double)rows / ((double)cnt * c);
+        if (e > best + 1e-9) {
+            best = e;
+            chunk = c;
+        }
+    }
     nz = (rows + chunk - 1) / chunk;
     Args a;
     memset(&a, 0, sizeof(a));
