@@ -128,6 +128,31 @@ def replica_value(world: int, steps: int, ms_max: float) -> float:
     return world * steps / (ms_max / 1000.0)
 
 
+def measure_alu_peaks(dev):
+    """FP64 and FP32 (CUDA-core) GEMM rates of this GPU, measured with cuBLAS:
+    the denominators of the FP64 and FP32 rooflines, and the comparator that
+    shows what the plain FP64 path's arithmetic can reach."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    for key, dt, n in (("fp64_tflops", torch.float64, 4096), ("fp32_tflops", torch.float32, 8192)):
+        a = torch.randn(n, n, dtype=dt, device=dev)
+        b = torch.randn(n, n, dtype=dt, device=dev)
+        c = a @ b
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            c = a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        out[key] = round(2.0 * n ** 3 * 3 / (e0.elapsed_time(e1) / 1e3) / 1e12, 3)
+        del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    return out
+
+
 def make_batches(n, seed_base):
     prob = WORKLOAD.prob
     return [si.make_batch(prob, WORKLOAD.n_int, WORKLOAD.n_bdy, seed=seed_base, step=k) for k in range(n)]
@@ -228,15 +253,19 @@ def run_gpu(args, rank, world, local_rank):
     if args.precision != "fp64" and args.fp64_steps > 0 and rank == 0:
         opt64 = new_opt("fp64")
         th64 = torch.tensor(theta0, device=dev)
-        ms64, _, _, _ = timed_steps(opt64, th64, dev_batches, 1, args.fp64_steps)
+        ms64, _, _, tim64 = timed_steps(opt64, th64, dev_batches, 1, args.fp64_steps, timing=True)
         st64 = opt64.sync_status()
+        lg = tim64["layer_gemm"]
+        fp64_gemm_tflops = lg["work"] / max(lg["ms"] / 1e3, 1e-12) / 1e12
         fp64 = {"value": args.fp64_steps / (ms64 / 1000.0), "unit": "steps/s",
                 "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps, "warmup": 1,
-                "status": st64}
+                "status": st64, "layer_gemm_tflops": round(fp64_gemm_tflops, 3),
+                "classes_ms_per_step": {k: round(v["ms"] / args.fp64_steps, 2) for k, v in tim64.items()}}
         opt64.close()
 
     # ---- roofline of the dominant kernel class -----------------------------
     peaks, peak_kind = load_peaks()
+    alu = measure_alu_peaks(dev)
 
     def class_roofline(name, rec):
         per_launch_ms = rec["ms"] / max(rec["launches"], 1)
@@ -245,10 +274,11 @@ def run_gpu(args, rank, world, local_rank):
             unit = "TFLOP/s"
             achieved = per_launch_work / max(per_launch_ms / 1e3, 1e-12) / 1e12
             if name == "precond" and args.precision != "fp64":
-                # FP32 products on the CUDA cores: 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz
-                bound, peak, peak_src = "alu", 80.5, "FP32 CUDA-core rate from unit counts and clock (80.5 TFLOP/s)"
+                bound, peak = "alu", alu["fp32_tflops"]
+                peak_src = "measured FP32 CUDA-core GEMM (cuBLAS SGEMM 8192^3, TF32 off) in this run"
             elif args.precision == "fp64" or name in ("eig", "precond"):
-                bound, peak, peak_src = "alu", 1.25, "nominal FP64 rate of the GB300 (1.25 TFLOP/s)"
+                bound, peak = "alu", alu["fp64_tflops"]
+                peak_src = "measured FP64 GEMM (cuBLAS DGEMM 4096^3) in this run"
             else:
                 bound, peak = "tensor", peaks["bf16_tflops_sustained"]
                 peak_src = f"{peak_kind} bf16 sustained"
@@ -279,7 +309,7 @@ def run_gpu(args, rank, world, local_rank):
                    "l2": "flushed between steps (256 MiB write outside the step events)"},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline,
         "class_rooflines": class_rooflines,
-        "kernel_classes": classes, "clocks": clocks, "status": status,
+        "kernel_classes": classes, "clocks": clocks, "status": status, "alu_peaks_measured": alu,
         "wall_s_timed": round(wall, 3),
     }
     if fp64:
