@@ -568,6 +568,49 @@ def run_many(steps=10, warmup=3, n_streams=16, count=64):
             "speedup_vs_fp64_sequential": round(ms_fp64 / ms_batch, 2)}
 
 
+# ---------------------------------------------------------------------------
+# Equal-L2 check: mixed precision vs the plain FP64 path over the same steps
+# ---------------------------------------------------------------------------
+def run_equal_l2(steps=40, every=5):
+    """Both precisions run `steps` KFAC steps (the benchmark's hyper-parameters
+    and resampled points) from the same initialisation; the relative L2 error
+    against u* is measured with the FP64 forward Laplacian on 10,000 held-out
+    points every `every` steps."""
+    import torch
+    from paper_2405_15603_gb300 import build as _build
+    _build.build()
+    from paper_2405_15603_gb300.api import KfacPinn
+    dev = torch.device("cuda:0")
+    prob, widths = WORKLOAD.prob, WORKLOAD.widths
+    Xe = torch.tensor(si.eval_points(prob, 10000, 0), device=dev)
+    ue = torch.tensor(prob.u_star(Xe.cpu().numpy()), device=dev)
+    ev = KfacPinn(prob.d, widths, device=str(dev), precision="fp64", max_n_int=2048, max_n_bdy=8)
+
+    def l2(th):
+        u, _, _ = ev.forward_laplacian(th, Xe)
+        return float(torch.linalg.norm(u - ue) / torch.linalg.norm(ue))
+
+    out = {}
+    for prec in ("mixed_bf16", "fp64"):
+        opt = KfacPinn(prob.d, widths, device=str(dev), precision=prec, max_n_int=WORKLOAD.n_int,
+                       max_n_bdy=WORKLOAD.n_bdy, **HYPER)
+        th = torch.tensor(si.xavier_theta(prob.d, widths, 0), device=dev)
+        rec = [(0, l2(th))]
+        t0 = time.perf_counter()
+        for k in range(steps):
+            b = [torch.tensor(a, device=dev) for a in si.make_batch(prob, WORKLOAD.n_int, WORKLOAD.n_bdy, 0, k)]
+            opt.step(th, *b)
+            if (k + 1) % every == 0 or k + 1 == steps:
+                rec.append((k + 1, l2(th)))
+        torch.cuda.synchronize()
+        out[prec] = {"l2": rec, "wall_s": round(time.perf_counter() - t0, 1), "status": opt.sync_status()}
+        opt.close()
+    fm, ff = out["mixed_bf16"]["l2"][-1][1], out["fp64"]["l2"][-1][1]
+    return {"metric": "relative L2 error after the same KFAC steps, mixed precision vs plain FP64",
+            "steps": steps, "workload": WORKLOAD_NAME, "hyper": HYPER, "runs": out,
+            "final_l2": {"mixed_bf16": fm, "fp64": ff}, "relative_gap": abs(fm - ff) / ff}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -579,6 +622,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e10", action="store_true",
                     help="forward vs autodiff Laplacian time and memory (App. C.4) instead of the step bench")
+    ap.add_argument("--equal-l2", type=int, default=0, metavar="STEPS",
+                    help="L2 error after STEPS steps, mixed vs FP64 (about 17 s per FP64 step)")
     ap.add_argument("--many", action="store_true",
                     help="64 uneven PINNs stepped as one batch (CUDA graph) instead of the step bench")
     ap.add_argument("--points", default=None,
@@ -594,6 +639,9 @@ def main():
         return
     if args.many:
         print(json.dumps(run_many()), flush=True)
+        return
+    if args.equal_l2:
+        print(json.dumps(run_equal_l2(args.equal_l2)), flush=True)
         return
     if args.steps is None:
         args.steps = 2 if args.precision == "fp64" else 30
