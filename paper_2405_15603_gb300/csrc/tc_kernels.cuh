@@ -56,22 +56,16 @@ struct Args {
     int* status;
 };
 
-// GRAM tiles are 256 x 256: two M = 128 accumulators that share each B stage,
-// which halves the B bytes per FLOP and so covers more load latency with the
-// same shared memory; the other modes use one 128 x 128 accumulator, double
-// buffered (their epilogues keep per-(point, feature) state in registers).
 template <int MODE>
 struct Cfg {
     static constexpr bool MN = (MODE == GRAM);
     static constexpr int BN = MN ? 256 : 128;
-    static constexpr int MH = MN ? 2 : 1;              // M halves of a tile
-    static constexpr int PM = MH * BM;                 // tile rows
-    static constexpr int STAGES = MN ? 3 : 6;
-    static constexpr int A_BYTES = PM * BK * 2;
+    static constexpr int STAGES = MN ? 4 : 6;
+    static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
-    static constexpr int TMEM_COLS = MN ? MH * BN : 2 * BN;
+    static constexpr int TMEM_COLS = MN ? 256 : 2 * BN;
     static constexpr int NBUF = MN ? 1 : 2;
     static constexpr uint32_t IDESC = tc::idesc_bf16(BM, BN, MN ? 1 : 0, MN ? 1 : 0);
 };
@@ -159,14 +153,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
         // blockIdx.x enumerates the (p, q) output tiles, symmetric ones only
         // when they touch the upper triangle; blockIdx.y is the row chunk.
         int t = blockIdx.x, pb = 0, qb = 0, cnt = 0;
-        int p_tiles = (a.P + C::PM - 1) / C::PM;
+        int p_tiles = (a.P + BM - 1) / BM;
         for (pb = 0; pb < p_tiles; pb++) {
-            int q_first = a.sym ? (pb * C::PM) / C::BN : 0;
+            int q_first = a.sym ? (pb * BM) / C::BN : 0;
             int n = a.q_tiles - q_first;
             if (t < cnt + n) { qb = q_first + (t - cnt); break; }
             cnt += n;
         }
-        p0 = pb * C::PM;
+        p0 = pb * BM;
         j0 = qb * C::BN;
         k_begin = blockIdx.y * a.row_chunk;
         int k_end = min(a.rows, k_begin + a.row_chunk);
@@ -212,9 +206,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                         tc::mbar_arrive_expect_tx(&full_bar[stage], C::STAGE_BYTES);
                         if (MODE == GRAM) {
                             const int row = k_begin + k * BK;
-#pragma unroll
-                            for (int b = 0; b < C::PM / 64; b++)
-                                tc::tma_load_2d(sa + 8192 * b, &a.a0, &full_bar[stage], p0 + 64 * b, row);
+                            tc::tma_load_2d(sa, &a.a0, &full_bar[stage], p0, row);
+                            tc::tma_load_2d(sa + 8192, &a.a0, &full_bar[stage], p0 + 64, row);
 #pragma unroll
                             for (int b = 0; b < C::BN / 64; b++)
                                 tc::tma_load_2d(sb + 8192 * b, &a.b0, &full_bar[stage], j0 + 64 * b, row);
@@ -253,20 +246,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                         const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; kk++) {
+                            uint64_t ad, bd;
                             if (C::MN) {
-                                // M half m: A rows p0 + 128 m .. (boxes 2m, 2m+1), accumulator at column m * BN
-                                const uint64_t bd = tc::smem_desc(sb + kk * 2048, 8192, 1024, tc::LAYOUT_SW128);
-#pragma unroll
-                                for (int m = 0; m < C::MH; m++) {
-                                    const uint64_t ad = tc::smem_desc(sa + m * 16384 + kk * 2048, 8192, 1024,
-                                                                      tc::LAYOUT_SW128);
-                                    tc::mma_bf16(dcol + (uint32_t)(m * C::BN), ad, bd, C::IDESC, first ? 0u : 1u);
-                                }
+                                ad = tc::smem_desc(sa + kk * 2048, 8192, 1024, tc::LAYOUT_SW128);
+                                bd = tc::smem_desc(sb + kk * 2048, 8192, 1024, tc::LAYOUT_SW128);
                             } else {
-                                const uint64_t ad = tc::smem_desc(sa + kk * 32, 16, 1024, tc::LAYOUT_SW128);
-                                const uint64_t bd = tc::smem_desc(sb + kk * 32, 16, 1024, tc::LAYOUT_SW128);
-                                tc::mma_bf16(dcol, ad, bd, C::IDESC, first ? 0u : 1u);
+                                ad = tc::smem_desc(sa + kk * 32, 16, 1024, tc::LAYOUT_SW128);
+                                bd = tc::smem_desc(sb + kk * 32, 16, 1024, tc::LAYOUT_SW128);
                             }
+                            tc::mma_bf16(dcol, ad, bd, C::IDESC, first ? 0u : 1u);
                             first = false;
                         }
                         tc::mma_commit(&empty_bar[stage]);
@@ -319,27 +307,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
             bool ok = tc::mbar_wait(&acc_full[buf], use & 1);
             if (!ok) { abort_flag = 1; break; }
             tc::tc_fence_after();
-            if (MODE == GRAM) {
-                // warp half m drains accumulator m (tile rows p0 + 128 m + r), all BN columns
-                const uint32_t gcol = tbase + lane_off + (uint32_t)(half * C::BN);
-                const int p = p0 + half * BM + r;
-                for (int c = 0; c < C::BN; c += 16) {
-                    float v[16];
-                    tc::tmem_ld16(gcol + c, v);
-                    tc::tmem_wait_ld();
-                    const int j = j0 + c;
-                    if (p < a.P && j < a.Q) {
-                        float* dst = a.part + ((long long)blockIdx.y * a.P + p) * a.Q + j;
-                        // float4 stores need 16-byte alignment: Q % 4 == 0
-                        if (j + 16 <= a.Q && (a.Q & 3) == 0) store16_f32(dst, v);
-                        else for (int i = 0; i < 16 && j + i < a.Q; i++) dst[i] = v[i];
-                    }
-                }
-                tc::tc_fence_before();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
-                continue;
-            }
             const uint32_t tcol = tbase + lane_off + (uint32_t)(buf * C::BN + c0);
 #pragma unroll
             for (int c = 0; c < CW; c += 16) {
@@ -347,6 +314,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                 tc::tmem_ld16(tcol + c, v);
                 tc::tmem_wait_ld();
                 const int j = j0 + c0 + c;
+                if (MODE == GRAM) {
+                    const int p = p0 + r;
+                    if (p < a.P) {
+                        float* dst = a.part + ((long long)blockIdx.y * a.P + p) * a.Q + j;
+                        // float4 stores need 16-byte alignment: Q % 4 == 0
+                        if (j + 16 <= a.Q && (a.Q & 3) == 0) store16_f32(dst, v);
+                        else for (int i = 0; i < 16 && j + i < a.Q; i++) dst[i] = v[i];
+                    }
+                    continue;
+                }
                 if (j >= a.hp_out) continue;
                 const bool live = (n < a.N);
                 if (MODE == FWD_VALUE) {

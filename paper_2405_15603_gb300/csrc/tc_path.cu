@@ -724,9 +724,9 @@ void free_pass(MxPass& P) {
 kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, const CUtensorMap& Y, int P, int Q,
                    int rows, int sym, float* part, int& nz) {
     using C = tck::Cfg<tck::GRAM>;
-    int p_tiles = (P + C::PM - 1) / C::PM, q_tiles = (Q + C::BN - 1) / C::BN;
+    int p_tiles = (P + 127) / 128, q_tiles = (Q + C::BN - 1) / C::BN;
     int tiles = 0;
-    for (int pb = 0; pb < p_tiles; pb++) tiles += q_tiles - (sym ? (pb * C::PM) / C::BN : 0);
+    for (int pb = 0; pb < p_tiles; pb++) tiles += q_tiles - (sym ? (pb * 128) / C::BN : 0);
     // split-K over the rows: full waves of one CTA per SM and even chunks
     int max_chunks = (int)(MX(h)->gpart_region / ((size_t)P * Q));
     if (max_chunks > MAX_GRAM_CHUNKS) max_chunks = MAX_GRAM_CHUNKS;
@@ -755,7 +755,7 @@ kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, co
     a.q_tiles = q_tiles;
     a.part = part;
     a.status = h->status;
-    double work = 2.0 * (double)tiles * C::PM * C::BN * rows;
+    double work = 2.0 * (double)tiles * 128 * C::BN * rows;
     return launch_engine<tck::GRAM>(h, s, a, dim3(tiles, nz, 1), KFAC_KC_GRAM, work);
 }
 
