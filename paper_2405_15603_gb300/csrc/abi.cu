@@ -485,7 +485,9 @@ kfac_status_t kfac_pinn_reset(kfac_handle_t h, void* stream) {
 kfac_status_t kfac_pinn_forward_laplacian(kfac_handle_t h, void* stream, const double* theta,
                                           const double* X, int N, double* u, double* grad,
                                           double* lap) {
-    if (!h || !theta || !X || !u || N < 0) return KFAC_BAD_ARG;
+    if (!h || !theta || N < 0) return KFAC_BAD_ARG;
+    if (N == 0) return KFAC_OK;                  // nothing to evaluate
+    if (!X || !u) return KFAC_BAD_ARG;
     cudaStream_t s = S_(stream);
     const int S = h->S, d = h->dims[0];
     for (int off = 0; off < N; off += h->cfg.max_n_int) {

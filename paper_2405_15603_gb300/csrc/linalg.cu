@@ -77,6 +77,7 @@ __global__ void k_ls_apply(double* theta, const double* dhat, double* delta_prev
         coef[0] = alpha;
         coef[1] = alpha * mom;
     }
+    if (best < 0) return;       // no finite trial: theta and delta_prev stay as they are
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < D;
          i += (long long)gridDim.x * blockDim.x) {
         double dlt = alpha * dhat[i];
@@ -167,11 +168,14 @@ __global__ void k_ks_solve(const double* __restrict__ part, int nblocks, int Ni,
     } else {
         alpha = -b1 / a11;
     }
+    double skip = 0.0;
     if (!(a11 > 0.0) || !isfinite(alpha) || !isfinite(mu)) {
         latch_status(status, KFAC_NONFINITE);
         alpha = 0.0;
         mu = 0.0;
+        skip = 1.0;
     }
+    coef[7] = skip;
     coef[0] = alpha;
     coef[1] = mu;
     coef[2] = a11;
@@ -185,7 +189,7 @@ __global__ void k_ks_solve(const double* __restrict__ part, int nblocks, int Ni,
 __global__ void k_ks_apply(double* theta, const double* __restrict__ Dl, double* delta_prev, long long D,
                            const double* __restrict__ coef) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= D) return;
+    if (i >= D || coef[7] != 0.0) return;       // a non-finite model leaves theta unchanged
     const double dlt = coef[0] * Dl[i] + coef[1] * delta_prev[i];
     delta_prev[i] = dlt;
     theta[i] += dlt;
