@@ -539,7 +539,8 @@ def kfac_step(cfg: KfacConfig, state: KfacState, theta: np.ndarray,
         extras["alpha"] = alpha
     else:
         alpha = cfg.lr
-    update = [alpha * v for v in dhat]
+    # with no finite trial the line search makes no step (α* = 0, reading of Sec. 3.4)
+    update = [alpha * v if alpha != 0.0 else np.zeros_like(v) for v in dhat]
     state.delta_prev = update
     state.t += 1
     theta_new = theta + pack_theta(update)
