@@ -165,6 +165,15 @@ kfac_status_t kfac_pinn_forward_laplacian_backward(kfac_handle_t h, void* stream
                                                    const double* dgrad, const double* dlap,
                                                    double* dtheta, double* dX);
 
+/* Store instead of recompute: when enabled, the Taylor activations of the last
+ * kfac_pinn_forward_laplacian (FP64, N <= max_n_int, one chunk) stay in the
+ * handle and a kfac_pinn_forward_laplacian_backward with the same theta and X
+ * pointers and N reuses them instead of recomputing the forward pass; any
+ * factors or step call discards them.  The caller must not change theta or X
+ * in between.  Larger N is always recomputed chunk by chunk, so memory does
+ * not grow with N.  Default: disabled. */
+kfac_status_t kfac_pinn_set_store_forward(kfac_handle_t h, int enable);
+
 /* Curvature and gradient of one batch (App. B, Algorithm 1, steps 1, 2 and
  * 4): forward Laplacian on the interior points and plain forward pass on the
  * boundary points, residuals and loss (Eq. 1), one backward pass each for

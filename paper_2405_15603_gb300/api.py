@@ -134,6 +134,10 @@ class KfacPinn:
             _ptr(ups[2]), _ptr(dtheta), _ptr(dX)))
         return dtheta, dX
 
+    def set_store_forward(self, enable: bool = True):
+        """Reverse mode reuses the last forward pass's activations (same theta, X) instead of recomputing."""
+        _check("kfac_pinn_set_store_forward", self.lib.kfac_pinn_set_store_forward(self.h, int(enable)))
+
     def factors(self, theta, X_int, f, X_bdy, g) -> torch.Tensor:
         X_int, f, X_bdy, g = (_dev(a, self.device) for a in (X_int, f, X_bdy, g))
         _check("kfac_pinn_factors", self.lib.kfac_pinn_factors(

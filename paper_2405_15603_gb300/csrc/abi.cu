@@ -268,6 +268,7 @@ kfac_status_t check_batch(kfac_pinn_handle* h, const void* X_int, int N_int, con
 kfac_status_t run_factors(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
                           const double* X_int, int N_int, const double* f,
                           const double* X_bdy, int N_bdy, const double* g, double* loss) {
+    h->fwd_valid = 0;       // the pass buffers are about to be overwritten
     if (h->cfg.precision == KFAC_MIXED_BF16)
         return tc_factors(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g, loss);
     kfac_status_t st;
@@ -504,6 +505,10 @@ kfac_status_t kfac_pinn_forward_laplacian(kfac_handle_t h, void* stream, const d
         }
         if (st) return st;
     }
+    h->fwd_valid = h->store_forward && h->cfg.precision == KFAC_FP64 && N <= h->cfg.max_n_int;
+    h->fwd_theta = theta;
+    h->fwd_X = X;
+    h->fwd_N = N;
     return KFAC_OK;
 }
 
@@ -519,14 +524,28 @@ kfac_status_t kfac_pinn_forward_laplacian_backward(kfac_handle_t h, void* stream
         KFAC_CUDA_TRY(cudaMemsetAsync(dtheta, 0, h->D * sizeof(double), s));
         return KFAC_OK;
     }
+    const bool reuse = h->store_forward && h->fwd_valid && h->fwd_theta == theta && h->fwd_X == X &&
+                       h->fwd_N == N && N <= h->cfg.max_n_int;
     for (int off = 0; off < N; off += h->cfg.max_n_int) {
         int n = N - off < h->cfg.max_n_int ? N - off : h->cfg.max_n_int;
         kfac_status_t st = fp64_forward_laplacian_backward(
             h, s, theta, X + (long long)off * d, n, du ? du + off : nullptr,
             dgrad ? dgrad + (long long)off * d : nullptr, dlap ? dlap + off : nullptr, dtheta,
-            dX ? dX + (long long)off * d : nullptr, off > 0);
+            dX ? dX + (long long)off * d : nullptr, off > 0, reuse);
         if (st) return st;
     }
+    // the pass buffers now hold this chunk's forward activations either way
+    h->fwd_valid = h->store_forward && N <= h->cfg.max_n_int;
+    h->fwd_theta = theta;
+    h->fwd_X = X;
+    h->fwd_N = N;
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_set_store_forward(kfac_handle_t h, int enable) {
+    if (!h) return KFAC_BAD_ARG;
+    h->store_forward = enable ? 1 : 0;
+    h->fwd_valid = 0;
     return KFAC_OK;
 }
 

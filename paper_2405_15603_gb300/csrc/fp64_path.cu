@@ -477,10 +477,13 @@ __global__ void k_seed_upstream(double* __restrict__ ZbL, int N, int S, const do
 
 kfac_status_t fp64_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
                                               const double* X, int N, const double* du, const double* dgrad,
-                                              const double* dlap, double* dtheta, double* dX, bool accumulate) {
+                                              const double* dlap, double* dtheta, double* dX, bool accumulate,
+                                              bool reuse_forward) {
     const int L = h->cfg.L, d = h->dims[0], S = h->S;
     kfac_status_t st;
-    if ((st = fp64_forward(h, s, theta, X, N, h->in, S))) return st;
+    // the Taylor activations are recomputed unless the caller holds them from the
+    // forward pass on the same inputs (stored mode)
+    if (!reuse_forward && (st = fp64_forward(h, s, theta, X, N, h->in, S))) return st;
     k_seed_upstream<<<ceil_div_u((long long)N * S, EW_THREADS), EW_THREADS, 0, s>>>(h->in.Zb[L - 1], N, S, h->opQ,
                                                                                     du, dgrad, dlap);
     KFAC_LAUNCH_CHECK(h);

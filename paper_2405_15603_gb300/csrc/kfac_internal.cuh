@@ -95,6 +95,13 @@ struct kfac_pinn_handle {
     int t;                 // completed steps
     int have_inverse;
     int have_direction;
+    // reverse mode with stored activations: the interior pass buffers hold the
+    // forward Laplacian of (fwd_theta, fwd_X, fwd_N) while fwd_valid is set
+    int store_forward;
+    int fwd_valid;
+    const double* fwd_theta;
+    const double* fwd_X;
+    int fwd_N;
     long long launches;    // kernels launched (host counter)
 };
 
@@ -163,7 +170,8 @@ kfac_status_t linalg_line_search_update(kfac_pinn_handle* h, cudaStream_t s, dou
                                         const double* g);
 kfac_status_t fp64_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
                                               const double* X, int N, const double* du, const double* dgrad,
-                                              const double* dlap, double* dtheta, double* dX, bool accumulate);
+                                              const double* dlap, double* dtheta, double* dX, bool accumulate,
+                                              bool reuse_forward);
 kfac_status_t fp64_extract_outputs(kfac_pinn_handle* h, cudaStream_t s, PassBuffers& pb, int N,
                                    int S, double* u, double* grad, double* lap);
 

@@ -134,3 +134,39 @@ def test_backward_rejects_mixed_handle():
     with pytest.raises(KfacError):
         opt.forward_laplacian_backward(torch.zeros(opt.D, dtype=torch.float64, device=DEV),
                                        np.zeros((4, 3)), np.ones(4))
+
+
+def test_store_forward_matches_recompute():
+    # Reverse mode reusing the stored activations of the forward pass gives the
+    # same gradient as recomputing them, with fewer kernels; a step in between
+    # discards the stored pass.
+    from paper_2405_15603_gb300.api import ForwardLaplacian
+    d, widths = 4, (32, 24, 1)
+    rng = np.random.default_rng(12)
+    N = 120
+    X = torch.tensor(rng.random((N, d)), device=DEV)
+    th = torch.tensor(_theta(d, widths, 13), device=DEV)
+    a = torch.tensor(rng.standard_normal(N), device=DEV)
+    out = {}
+    for store in (False, True):
+        opt = _opt(d, widths, max_n_int=N, max_n_bdy=4)
+        opt.set_store_forward(store)
+        theta = th.clone().requires_grad_(True)
+        u, g, lap = ForwardLaplacian.apply(theta, X, opt)
+        phi = (a * lap).sum() + u.sum() + g.sum()
+        n0 = opt.launch_count()
+        (gr,) = torch.autograd.grad(phi, theta)
+        torch.cuda.synchronize()
+        out[store] = (gr.cpu().numpy(), opt.launch_count() - n0)
+    assert np.array_equal(out[True][0], out[False][0])
+    assert out[True][1] < out[False][1]
+    # a step in between discards the stored activations: still the right gradient
+    opt = _opt(d, widths, max_n_int=N, max_n_bdy=4)
+    opt.set_store_forward(True)
+    theta = th.clone().requires_grad_(True)
+    u, g, lap = ForwardLaplacian.apply(theta, X, opt)
+    prob = si.poisson_cos_problem(d)
+    Xi, f, Xb, gb = si.make_batch(prob, N, 4, seed=1)
+    opt.step(th.clone(), Xi, f, Xb, gb)
+    (gr,) = torch.autograd.grad((a * lap).sum() + u.sum() + g.sum(), theta)
+    assert np.array_equal(gr.cpu().numpy(), out[False][0])
