@@ -159,7 +159,9 @@ kfac_status_t kfac_pinn_forward_laplacian(kfac_handle_t h, void* stream, const d
  * writes dtheta = dphi/dtheta (D doubles, overwritten; same packing as theta)
  * and, if dX is not NULL, dX = dphi/dX (N x d).  The Taylor activations of
  * the forward pass are recomputed in chunks of max_n_int points, so memory
- * does not grow with N.  FP64 handles only (KFAC_BAD_ARG otherwise). */
+ * does not grow with N.  Both precisions: a mixed-precision handle runs the
+ * pass and its adjoint on the tensor cores (BF16 with split-BF16 value and
+ * second-order rows, FP32 accumulation) and sums the gradient in FP64. */
 kfac_status_t kfac_pinn_forward_laplacian_backward(kfac_handle_t h, void* stream, const double* theta,
                                                    const double* X, int N, const double* du,
                                                    const double* dgrad, const double* dlap,

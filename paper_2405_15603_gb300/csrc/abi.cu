@@ -517,11 +517,22 @@ kfac_status_t kfac_pinn_forward_laplacian_backward(kfac_handle_t h, void* stream
                                                    const double* dgrad, const double* dlap, double* dtheta,
                                                    double* dX) {
     if (!h || !theta || !X || !dtheta || N < 0) return KFAC_BAD_ARG;
-    if (h->cfg.precision != KFAC_FP64) return KFAC_BAD_ARG;
     cudaStream_t s = S_(stream);
     const int d = h->dims[0];
     if (N == 0) {
         KFAC_CUDA_TRY(cudaMemsetAsync(dtheta, 0, h->D * sizeof(double), s));
+        return KFAC_OK;
+    }
+    if (h->cfg.precision == KFAC_MIXED_BF16) {
+        h->fwd_valid = 0;
+        for (int off = 0; off < N; off += h->cfg.max_n_int) {
+            int n = N - off < h->cfg.max_n_int ? N - off : h->cfg.max_n_int;
+            kfac_status_t st = tc_forward_laplacian_backward(
+                h, s, theta, X + (long long)off * d, n, du ? du + off : nullptr,
+                dgrad ? dgrad + (long long)off * d : nullptr, dlap ? dlap + off : nullptr, dtheta,
+                dX ? dX + (long long)off * d : nullptr, off > 0);
+            if (st) return st;
+        }
         return KFAC_OK;
     }
     const bool reuse = h->store_forward && h->fwd_valid && h->fwd_theta == theta && h->fwd_X == X &&

@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                     }
                 } else {
                     // backward modes: v = ybar (T^bar) of this row block
-                    const float rn = live ? (float)a.r[n] : 0.f;
+                    const float rn = live ? (a.r ? (float)a.r[n] : 1.f) : 0.f;   // r == nullptr: Gr = g
                     float ab[16], gr[16];
                     if (MODE == BWD_LAP) {
                         float a0v[16];

@@ -93,6 +93,7 @@ struct MxState {
     int hp_max;
     float* Qf;          // general operator: tangent directions (d x d, FP32)
     double* gtan;       // general operator: first-layer tangent gradient sums (h_1 x d)
+    float* seed;        // reverse mode: per-point seeds c_{n,s} of the interior pass (S x N_pad)
 };
 
 MxState* MX(kfac_pinn_handle* h) { return (MxState*)h->mx; }
@@ -338,28 +339,32 @@ __global__ void k_extract_mx(const float* __restrict__ zl, int N, int N_pad, int
 __global__ void k_last_bwd(const float* __restrict__ wL, const bf16* __restrict__ T_hi, const float* __restrict__ A0,
                            const float* __restrict__ AD, const float* __restrict__ SSQ, const double* __restrict__ r,
                            int N, int N_pad, int h, int hp, int S, const float* __restrict__ chw, float cT,
-                           float cD, bf16* Zb, bf16* Gr) {
+                           float cD, const float* __restrict__ seed, bf16* Zb, bf16* Gr) {
+    // seed == nullptr: the residual's constant seed c (cT, cD; 1 on the value of a
+    // boundary pass); else c_{n,s} = seed[s * N_pad + n] (reverse mode of the forward
+    // Laplacian).  r == nullptr: Gr = Zb.
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long blk = (long long)N_pad * hp;
     if (idx >= blk) return;
     int n = (int)(idx / hp), j = (int)(idx % hp);
     bool live = (n < N) && (j < h);
     float w = live ? wL[j] : 0.f;
-    float rn = (n < N) ? (float)r[n] : 0.f;
+    float rn = (n < N) ? (r ? (float)r[n] : 1.f) : 0.f;
     float y0 = tanhf(A0[idx]);
     float s1 = 1.f - y0 * y0;
+    const float c0 = seed ? seed[n] : (S == 1 ? 1.f : 0.f);
     if (S == 1) {
-        float ab = s1 * w;
+        float ab = s1 * c0 * w;
         Zb[idx] = __float2bfloat16_rn(ab);
         Gr[idx] = __float2bfloat16_rn(rn * ab);
         return;
     }
     // seed c = dr/dZ^{(L)}: cD on the second-order column, cT on tangent column 1 (time, heat)
-    float yD = cD * w;
+    float yD = (seed ? seed[(long long)(S - 1) * N_pad + n] : cD) * w;
     float cross = 0.f;
     for (int s = 1; s < S - 1; s++) {
         float yi = __bfloat162float(T_hi[s * blk + idx]);
-        float ybar = (s == 1) ? cT * w : 0.f;
+        float ybar = (seed ? seed[(long long)s * N_pad + n] : (s == 1 ? cT : 0.f)) * w;
         float ab = s1 * ybar;
         ab -= 4.f * chw[s - 1] * y0 * yi * yD;
         cross = fmaf(yi, ybar, cross);
@@ -367,7 +372,7 @@ __global__ void k_last_bwd(const float* __restrict__ wL, const bf16* __restrict_
         Zb[s * blk + idx] = __float2bfloat16_rn(ab);
         Gr[s * blk + idx] = __float2bfloat16_rn(rn * ab);
     }
-    float a0b = -2.f * y0 * cross - 2.f * s1 * (y0 * AD[idx] + (1.f - 3.f * y0 * y0) * SSQ[idx]) * yD;
+    float a0b = s1 * c0 * w - 2.f * y0 * cross - 2.f * s1 * (y0 * AD[idx] + (1.f - 3.f * y0 * y0) * SSQ[idx]) * yD;
     float aDb = s1 * yD;
     a0b = live ? a0b : 0.f;
     aDb = live ? aDb : 0.f;
@@ -500,9 +505,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_factor_A1(const float* __restri
 __global__ void __launch_bounds__(RED_THREADS) k_grad_layer1(const bf16* __restrict__ Gr, const bf16* __restrict__ Grb,
                                                              const float* __restrict__ X,
                                                              const float* __restrict__ Xb, int N, int N_pad, int Nb,
-                                                             int d, int h, int hp, int S, double* grad, double* gtan) {
-    // dL/dW~_1[j][k] = (1/N) sum_n (r g_{n,0,j} x_{n,k} + sum_m r g_{n,m,j} (v_m)_k) + boundary term;
-    // with gtan the tangent sums t_{j,m} = (1/N) sum_n r g_{n,m,j} are written there
+                                                             int d, int h, int hp, int S, double si, double sb,
+                                                             double* grad, double* gtan) {
+    // dL/dW~_1[j][k] = si sum_n (r g_{n,0,j} x_{n,k} + sum_m r g_{n,m,j} (v_m)_k) + boundary term (sb);
+    // with gtan the tangent sums t_{j,m} = si sum_n r g_{n,m,j} are written there
     // (the caller rotates them by the tangent directions), else v_m = e_m.
     __shared__ double shm[32][33];
     const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
@@ -524,8 +530,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_grad_layer1(const bf16* __restr
             b += (k < d) ? g0 * Xb[(long long)n * d + k] : g0;
         }
     }
-    const double tv = (double)t / N;
-    const double v = (double)a / N + (double)b / Nb + (gtan ? 0.0 : tv);
+    const double tv = si * (double)t;
+    const double v = si * (double)a + sb * (double)b + (gtan ? 0.0 : tv);
     const double s = reduce_row_groups(v, shm);
     if (rg == 0 && j < h) grad[j + (long long)h * k] = s;
     if (gtan && k < d) {
@@ -556,6 +562,84 @@ __global__ void k_rotate_first(const float* __restrict__ W1f, const float* __res
     for (int k = 0; k < d; k++) acc = fmaf(W1f[(long long)k * hp + j], Qf[(long long)k * d + m], acc);
     W1Qf[idx] = acc;
 }
+
+// Reverse mode of the forward Laplacian: the seed c_{n,s} = dphi/dZ^{(L)}_{n,s} per
+// point, in FP32: the value row takes du, the tangent rows dgrad (rotated into
+// the tangent directions, Q^T dgrad, for a general operator), the last row dlap.
+__global__ void k_seed_mx(float* seed, int N, int N_pad, int S, const float* __restrict__ Qf,
+                          const double* __restrict__ du, const double* __restrict__ dgrad,
+                          const double* __restrict__ dlap) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)S * N_pad) return;
+    const int s = (int)(idx / N_pad), n = (int)(idx % N_pad), d = S - 2;
+    float c = 0.f;
+    if (n < N) {
+        if (s == 0) {
+            c = du ? (float)du[n] : 0.f;
+        } else if (s == S - 1) {
+            c = dlap ? (float)dlap[n] : 0.f;
+        } else if (dgrad) {
+            if (!Qf) {
+                c = (float)dgrad[(long long)n * d + (s - 1)];
+            } else {
+                for (int i = 0; i < d; i++) c = fmaf(Qf[(long long)i * d + (s - 1)], (float)dgrad[(long long)n * d + i], c);
+            }
+        }
+    }
+    seed[idx] = c;
+}
+
+// dphi/dW~_L[q] = sum_n sum_s c_{n,s} T^_{n,s}[q]: the hidden rows with their low
+// halves where they have one (value, second-order, heat time), and the bias
+// entry q = h_{L-1} from the value rows.  FP32 partial sums per row group.
+__global__ void __launch_bounds__(RED_THREADS) k_last_grad_seeded(const bf16* __restrict__ T_hi,
+                                                                  const bf16* __restrict__ T_lo,
+                                                                  const float* __restrict__ seed, int N, int N_pad,
+                                                                  int hin, int hp, int S, int split_time,
+                                                                  double* grad) {
+    __shared__ double shm[32][33];
+    const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
+    const int q = blockIdx.x * 32 + cl;
+    const long long blk = (long long)N_pad * hp;
+    float acc = 0.f;
+    if (q < hin) {
+        for (int s = 0; s < S; s++) {
+            const bf16* lo = nullptr;
+            if (s == 0) lo = T_lo;
+            else if (s == S - 1) lo = T_lo + blk;
+            else if (s == 1 && split_time) lo = T_lo + 2 * blk;
+            for (int n = rg; n < N; n += 32) {
+                float t = __bfloat162float(T_hi[s * blk + (long long)n * hp + q]);
+                if (lo) t += __bfloat162float(lo[(long long)n * hp + q]);
+                acc = fmaf(seed[(long long)s * N_pad + n], t, acc);
+            }
+        }
+    } else if (q == hin) {
+        for (int n = rg; n < N; n += 32) acc += seed[n];
+    }
+    const double tot = reduce_row_groups((double)acc, shm);
+    if (rg == 0 && q <= hin) grad[q] = tot;
+}
+
+// dphi/dx_n = W_1^T g^{(1)}_{n,0}: x enters the value column of layer 1 only.
+__global__ void k_dX_mx(const bf16* __restrict__ Zb1, int N, int hp, int h1, int d, const float* __restrict__ W1f,
+                        double* dX) {
+    extern __shared__ float zrow[];
+    const int n = blockIdx.x;
+    for (int j = threadIdx.x; j < h1; j += blockDim.x) zrow[j] = __bfloat162float(Zb1[(long long)n * hp + j]);
+    __syncthreads();
+    for (int k = threadIdx.x; k < d; k += blockDim.x) {
+        float acc = 0.f;
+        for (int j = 0; j < h1; j++) acc = fmaf(zrow[j], W1f[(long long)k * hp + j], acc);
+        dX[(long long)n * d + k] = acc;
+    }
+}
+
+__global__ void k_copy_or_add(double* dst, const double* src, long long n, int add) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = add ? dst[i] + src[i] : src[i];
+}
+
 
 // Last layer: gradient (1/N) sum_{n,s} r_n c_s T^_{n,s} + boundary, and the
 // 1x1 output factors B_L.
@@ -850,7 +934,8 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
     return KFAC_OK;
 }
 
-kfac_status_t backward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* r, int N, MxPass& P) {
+kfac_status_t backward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* r, int N, MxPass& P,
+                            const float* seed = nullptr) {
     MxState* m = MX(h);
     const int L = h->cfg.L, S = P.S;
     {
@@ -858,7 +943,7 @@ kfac_status_t backward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* r
         long long cnt = (long long)P.N_pad * ly.hp;
         timer_begin(h, KFAC_KC_ELEMENTWISE, s);
         k_last_bwd<<<ceil_div_u(cnt, EW), EW, 0, s>>>(m->w.wL, ly.T_hi, ly.A0, ly.AD, ly.SSQ, r, N, P.N_pad, ly.h,
-                                                       ly.hp, S, h->chw32, (float)h->cT, (float)h->cD, ly.Zb,
+                                                       ly.hp, S, h->chw32, (float)h->cT, (float)h->cD, seed, ly.Zb,
                                                        ly.Gr);
         timer_end(h, KFAC_KC_ELEMENTWISE, s, 6.0 * S * (double)cnt);
         KFAC_LAUNCH_CHECK(h);
@@ -923,7 +1008,8 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
         KFAC_LAUNCH_CHECK(h);
         MxLayer& l1 = I.lay[0];
         k_grad_layer1<<<dim3(ceil_div_u(l1.h, 32), d + 1), RED_THREADS, 0, s>>>(
-            l1.Gr, B.lay[0].Gr, I.Xf, B.Xf, N, I.N_pad, Nb, d, l1.h, l1.hp, S, h->grad + h->woff[0], m->gtan);
+            l1.Gr, B.lay[0].Gr, I.Xf, B.Xf, N, I.N_pad, Nb, d, l1.h, l1.hp, S, 1.0 / N, 1.0 / Nb,
+            h->grad + h->woff[0], m->gtan);
         KFAC_LAUNCH_CHECK(h);
         if (m->gtan) {
             k_rotate_grad1<<<ceil_div_u((long long)l1.h * d, EW), EW, 0, s>>>(m->gtan, m->Qf, l1.h, d,
@@ -1059,6 +1145,7 @@ kfac_status_t tc_alloc(kfac_pinn_handle* h) {
     m->gpart_region = (size_t)MAX_GRAM_CHUNKS * maxPQ;
     if ((st = dal(&m->gpart, 2 * m->gpart_region))) return st;
     if ((st = dal(&m->cs, 2 * ((size_t)hp_max + 8)))) return st;
+    if ((st = dal(&m->seed, (size_t)h->S * m->in.N_pad))) return st;
     return KFAC_OK;
 }
 
@@ -1075,6 +1162,7 @@ void tc_free(kfac_pinn_handle* h) {
     cudaFree(m->w.W1Qf);
     cudaFree(m->Qf);
     cudaFree(m->gtan);
+    cudaFree(m->seed);
     cudaFree(m->part);
     cudaFree(m->gpart);
     cudaFree(m->cs);
@@ -1148,5 +1236,64 @@ kfac_status_t tc_forward_laplacian(kfac_pinn_handle* h, cudaStream_t s, const do
     k_extract_mx<<<ceil_div_u(N, EW), EW, 0, s>>>(m->in.zl, N, m->in.N_pad, m->in.S, h->dims[0], m->Qf, u, grad,
                                                    lap);
     KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+kfac_status_t tc_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X,
+                                            int N, const double* du, const double* dgrad, const double* dlap,
+                                            double* dtheta, double* dX, bool accumulate) {
+    MxState* m = MX(h);
+    MxPass& I = m->in;
+    const int L = h->cfg.L, d = h->dims[0], S = I.S;
+    const int heat = h->cfg.op == KFAC_OP_HEAT;
+    kfac_status_t st;
+    if ((st = convert_weights(h, s, theta))) return st;
+    BlockSel all;
+    all.nsel = 0;
+    all.b[0] = all.b[1] = all.b[2] = 0;
+    all.split_time = heat;
+    if ((st = forward_pass(h, s, theta, X, N, I, all))) return st;
+    k_seed_mx<<<ceil_div_u((long long)S * I.N_pad, EW), EW, 0, s>>>(m->seed, N, I.N_pad, S, m->Qf, du, dgrad, dlap);
+    KFAC_LAUNCH_CHECK(h);
+    if ((st = backward_pass(h, s, nullptr, N, I, m->seed))) return st;
+    // gradient of every layer into the handle's gradient buffer, then into dtheta
+    double* G = h->grad;
+    float* part = m->gpart;
+    double* cs = m->cs;
+    int z = 0;
+    {
+        MxLayer& l1 = I.lay[0];
+        k_grad_layer1<<<dim3(ceil_div_u(l1.h, 32), d + 1), RED_THREADS, 0, s>>>(
+            l1.Gr, l1.Gr, I.Xf, I.Xf, N, I.N_pad, 0, d, l1.h, l1.hp, S, 1.0, 0.0, G + h->woff[0], m->gtan);
+        KFAC_LAUNCH_CHECK(h);
+        if (m->gtan) {
+            k_rotate_grad1<<<ceil_div_u((long long)l1.h * d, EW), EW, 0, s>>>(m->gtan, m->Qf, l1.h, d, G + h->woff[0]);
+            KFAC_LAUNCH_CHECK(h);
+        }
+    }
+    for (int l = 2; l <= L - 1; l++) {
+        MxLayer& ti = I.lay[l - 2];
+        MxLayer& gi = I.lay[l - 1];
+        if ((st = gram(h, s, gi.gGr, ti.gT, gi.h, ti.h, I.rows, 0, part, z))) return st;
+        k_colsum<<<ceil_div_u(gi.h, 32), RED_THREADS, 0, s>>>(gi.Gr, nullptr, gi.hp, 0, N, gi.h, cs);
+        KFAC_LAUNCH_CHECK(h);
+        k_grad_reduce<<<ceil_div_u((long long)gi.h * (ti.h + 1), EW), EW, 0, s>>>(part, z, part, 0, gi.h, ti.h, cs, cs,
+                                                                                  1.0, 0.0, G + h->woff[l - 1]);
+        KFAC_LAUNCH_CHECK(h);
+    }
+    {
+        MxLayer& ti = I.lay[L - 2];
+        k_last_grad_seeded<<<ceil_div_u(ti.h + 1, 32), RED_THREADS, 0, s>>>(ti.T_hi, ti.T_lo, m->seed, N, I.N_pad, ti.h,
+                                                                            ti.hp, S, heat && S > 2,
+                                                                            G + h->woff[L - 1]);
+        KFAC_LAUNCH_CHECK(h);
+    }
+    k_copy_or_add<<<ceil_div_u(h->D, EW), EW, 0, s>>>(dtheta, G, h->D, accumulate ? 1 : 0);
+    KFAC_LAUNCH_CHECK(h);
+    if (dX) {
+        const MxLayer& l1 = I.lay[0];
+        k_dX_mx<<<N, 128, sizeof(float) * l1.hp, s>>>(l1.Zb, N, l1.hp, l1.h, d, m->w.W1f, dX);
+        KFAC_LAUNCH_CHECK(h);
+    }
     return KFAC_OK;
 }

@@ -13,3 +13,8 @@ kfac_status_t tc_forward_laplacian(kfac_pinn_handle* h, cudaStream_t s, const do
 kfac_status_t tc_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
                            const double* X_int, int N_int, const double* f,
                            const double* X_bdy, int N_bdy, const double* g, double* dst);
+// Reverse mode of the forward Laplacian on one chunk (N <= max_n_int): dtheta
+// (overwritten, or accumulated into), and dX when not NULL.
+kfac_status_t tc_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                                            const double* X, int N, const double* du, const double* dgrad,
+                                            const double* dlap, double* dtheta, double* dX, bool accumulate);
