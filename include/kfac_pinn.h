@@ -83,8 +83,10 @@ typedef enum { KFAC_OP_LAPLACE = 0, KFAC_OP_HEAT = 1, KFAC_OP_GENERAL = 2 } kfac
  *              on the step's batch (KFAC of the paper; lr unused)
  * AUTO:        delta = alpha* Delta + mu* delta_prev with (alpha*, mu*) the
  *              minimiser of the quadratic model with the exact damped Gramian
- *              G + lambda I (KFAC* of the paper; lr and momentum unused; FP64
- *              precision only). */
+ *              G + lambda I (KFAC* of the paper; lr and momentum unused).  The
+ *              Gramian products come from forward-mode passes through the
+ *              Taylor pass: FP64, or on the tensor cores (BF16 operands, FP32
+ *              accumulation) for a mixed-precision handle. */
 typedef enum { KFAC_UPDATE_FIXED = 0, KFAC_UPDATE_LINE_SEARCH = 1, KFAC_UPDATE_AUTO = 2 } kfac_update_t;
 
 /* Factor selector of kfac_pinn_get_factor / kfac_pinn_set_factor. */

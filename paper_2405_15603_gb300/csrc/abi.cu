@@ -38,7 +38,6 @@ bool valid_config(const kfac_config_t* c) {
     if (c->max_n_int < 1 || c->max_n_bdy < 1) return false;
     if (c->update < KFAC_UPDATE_FIXED || c->update > KFAC_UPDATE_AUTO) return false;
     if (c->eig_sm_budget < 0) return false;
-    if (c->update == KFAC_UPDATE_AUTO && c->precision != KFAC_FP64) return false;
     long long rows = (long long)(c->d + 2) * c->max_n_int;
     if (rows > (1LL << 30)) return false;
     return true;

@@ -287,18 +287,24 @@ size_t linalg_auto_part_elems() { return (size_t)KS_BLOCKS * KS_Q; }
 
 kfac_status_t linalg_auto_update(kfac_pinn_handle* h, cudaStream_t s, double* theta, const double* X_int,
                                  int N_int, const double* X_bdy, int N_bdy) {
-    if (h->cfg.precision != KFAC_FP64) return KFAC_BAD_ARG;
+    const bool mixed = (h->cfg.precision == KFAC_MIXED_BF16);
     double* jDi = h->ks_jv;
     double* jDb = jDi + h->cfg.max_n_int;
     double* jdi = jDb + h->cfg.max_n_bdy;
     double* jdb = jdi + h->cfg.max_n_int;
     const int have_prev = h->t > 0;
     kfac_status_t st;
-    if ((st = fp64_jvp(h, s, theta, h->dir, X_int, N_int, h->in, h->S, true, jDi))) return st;
-    if ((st = fp64_jvp(h, s, theta, h->dir, X_bdy, N_bdy, h->bd, 1, false, jDb))) return st;
-    if (have_prev) {
-        if ((st = fp64_jvp(h, s, theta, h->delta_prev, X_int, N_int, h->in, h->S, true, jdi))) return st;
-        if ((st = fp64_jvp(h, s, theta, h->delta_prev, X_bdy, N_bdy, h->bd, 1, false, jdb))) return st;
+    if (mixed) {
+        // forward-mode products on the tensor cores, from the step's stored forward pass
+        if ((st = tc_residual_jvp(h, s, h->dir, N_int, N_bdy, jDi, jDb))) return st;
+        if (have_prev && (st = tc_residual_jvp(h, s, h->delta_prev, N_int, N_bdy, jdi, jdb))) return st;
+    } else {
+        if ((st = fp64_jvp(h, s, theta, h->dir, X_int, N_int, h->in, h->S, true, jDi))) return st;
+        if ((st = fp64_jvp(h, s, theta, h->dir, X_bdy, N_bdy, h->bd, 1, false, jDb))) return st;
+        if (have_prev) {
+            if ((st = fp64_jvp(h, s, theta, h->delta_prev, X_int, N_int, h->in, h->S, true, jdi))) return st;
+            if ((st = fp64_jvp(h, s, theta, h->delta_prev, X_bdy, N_bdy, h->bd, 1, false, jdb))) return st;
+        }
     }
     k_ks_dots<<<KS_BLOCKS, 256, 0, s>>>(h->dir, h->delta_prev, h->grad, h->D, jDi, jdi, N_int, jDb, jdb, N_bdy,
                                         have_prev, h->ks_part);

@@ -18,6 +18,10 @@
 //   BWD_TAN     adjoint of tangent rows: abar_i = s1 ybar_i - 4 y_0 y_i ybar_D
 //   BWD_VALUE   adjoint of value rows (uses the tangent cross sums)
 //   GRAM        C = X^T Y over a chunk of rows (factor Grams, weight gradient)
+//   JVP_VALUE   forward-mode derivative of the value rows in direction dW:
+//               da_0 = T_0 dW~^T + dT_0 W^T, dy_0 = s1 da_0
+//   JVP_TAN     tangent rows dy_i = -2 y_0 y_i da_0 + s1 da_i (partial sums of
+//               w_i y_i da_i over the CTA's columns) and the second-order row's da_D
 #pragma once
 #include "tc_common.cuh"
 
@@ -28,7 +32,8 @@ constexpr int BK = 64;
 constexpr int NUM_THREADS = 320;
 constexpr int EPI_WARPS = 8;
 
-enum Mode { FWD_VALUE = 0, FWD_TANLAP = 1, BWD_LAP = 2, BWD_TAN = 3, BWD_VALUE = 4, GRAM = 5 };
+enum Mode { FWD_VALUE = 0, FWD_TANLAP = 1, BWD_LAP = 2, BWD_TAN = 3, BWD_VALUE = 4, GRAM = 5, JVP_VALUE = 6,
+            JVP_TAN = 7 };
 
 struct Args {
     CUtensorMap a0, a1, b0, b1;     // operand maps; a1/b1 carry the low BF16 halves
@@ -51,7 +56,8 @@ struct Args {
     float* SSQ;                     // sum of squared tangents
     float* YD;                      // ybar_Delta (BWD)
     float* part;                    // chunk partials / Gram partials
-    const __nv_bfloat16* ytan;      // BWD_TAN: T^{(l-1)} (y_i)
+    const __nv_bfloat16* ytan;      // BWD_TAN: T^{(l-1)} (y_i); JVP_TAN: T^{(l)}
+    float* DAD;                     // JVP_TAN: da_D of the second-order row (YD holds da_0 in the JVP modes)
     const double* r;                // residuals (BWD: for r_n g)
     int* status;
 };
@@ -63,7 +69,8 @@ struct Cfg {
     // the forward modes take two 64-wide K blocks per stage (half the barrier round
     // trips for the same bytes in flight: measured 16 % faster); each block is one
     // 128-byte-swizzled TMA box.  The adjoint modes keep one block and six stages.
-    static constexpr int KSUB = (MODE == FWD_VALUE || MODE == FWD_TANLAP) ? 2 : 1;
+    static constexpr int KSUB =
+        (MODE == FWD_VALUE || MODE == FWD_TANLAP || MODE == JVP_VALUE || MODE == JVP_TAN) ? 2 : 1;
     static constexpr int STAGES = MN ? 4 : (KSUB == 2 ? 3 : 6);
     static constexpr int A_BYTES = KSUB * BM * BK * 2;
     static constexpr int B_BYTES = KSUB * BN * BK * 2;
@@ -79,6 +86,7 @@ template <int MODE>
 KFAC_DEV int n_terms(int s, int S, int split_time) {
     if (MODE == FWD_VALUE) return 3;
     if (MODE == FWD_TANLAP) return (s == S - 1 || (split_time && s == 1)) ? 3 : 1;
+    if (MODE == JVP_VALUE || MODE == JVP_TAN) return 2;    // T dW~^T + dT W^T
     return 1;
 }
 
@@ -87,9 +95,9 @@ KFAC_DEV int lo_block(int s, int S) { return s == 0 ? 0 : (s == S - 1 ? 1 : 2); 
 
 template <int MODE>
 KFAC_DEV void tile_range(const Args& a, int& s_begin, int& s_end) {
-    if (MODE == FWD_VALUE || MODE == BWD_VALUE || MODE == GRAM) { s_begin = 0; s_end = 1; return; }
+    if (MODE == FWD_VALUE || MODE == BWD_VALUE || MODE == GRAM || MODE == JVP_VALUE) { s_begin = 0; s_end = 1; return; }
     if (MODE == BWD_LAP) { s_begin = a.S - 1; s_end = a.S; return; }
-    int last = (MODE == FWD_TANLAP) ? a.S : a.S - 1;   // FWD covers the Laplacian tile too
+    int last = (MODE == FWD_TANLAP || MODE == JVP_TAN) ? a.S : a.S - 1;   // FWD covers the Laplacian tile too
     s_begin = 1 + blockIdx.z * a.chunk_len;
     s_end = min(last, s_begin + a.chunk_len);
 }
@@ -186,7 +194,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
     }
     if (warp == 0 && lane == 0) {
         tc::prefetch_tmap(&a.a0); tc::prefetch_tmap(&a.b0);
-        if (MODE == FWD_VALUE || MODE == FWD_TANLAP) { tc::prefetch_tmap(&a.a1); tc::prefetch_tmap(&a.b1); }
+        if (MODE == FWD_VALUE || MODE == FWD_TANLAP || MODE == JVP_VALUE || MODE == JVP_TAN) {
+            tc::prefetch_tmap(&a.a1);
+            tc::prefetch_tmap(&a.b1);
+        }
     }
     if (warp == 1) { tc::tmem_alloc(&tmem_base, C::TMEM_COLS); tc::tmem_relinquish(); }
     tc::tc_fence_before();
@@ -216,10 +227,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                             for (int b = 0; b < C::BN / 64; b++)
                                 tc::tma_load_2d(sb + 8192 * b, &a.b0, &full_bar[stage], j0 + 64 * b, row);
                         } else {
-                            // term 0: hi x hi, term 1: hi x W_lo, term 2: lo x W_hi
-                            const CUtensorMap* am = (term == 2) ? &a.a1 : &a.a0;
+                            // term 0: hi x hi, term 1: hi x W_lo, term 2: lo x W_hi;
+                            // JVP modes: term 0: T x dW, term 1: dT x W
+                            const bool jvp = (MODE == JVP_VALUE || MODE == JVP_TAN);
+                            const CUtensorMap* am = (jvp ? term == 1 : term == 2) ? &a.a1 : &a.a0;
                             const CUtensorMap* bm = (term == 1) ? &a.b1 : &a.b0;
-                            int arow = (term == 2) ? (lo_block(s, a.S) * a.N_pad + p0) : (s * a.N_pad + p0);
+                            int arow = (!jvp && term == 2) ? (lo_block(s, a.S) * a.N_pad + p0) : (s * a.N_pad + p0);
 #pragma unroll
                             for (int u = 0; u < C::KSUB; u++) {   // blocks past K read zeros
                                 const int kx = (k * C::KSUB + u) * BK;
@@ -285,10 +298,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
         const long long hp = a.hp_out;
 
         // per-thread state kept across the CTA's tiles
-        float st1[(MODE == FWD_TANLAP || MODE == BWD_TAN) ? CW : 1];
-        float st2[(MODE == FWD_TANLAP || MODE == BWD_TAN) ? CW : 1];
-        __nv_bfloat16 stq[(MODE == BWD_TAN) ? CW : 1];
-        if (MODE == FWD_TANLAP || MODE == BWD_TAN) {
+        constexpr bool STATE = (MODE == FWD_TANLAP || MODE == BWD_TAN || MODE == JVP_TAN);
+        float st1[STATE ? CW : 1];
+        float st2[STATE ? CW : 1];
+        __nv_bfloat16 stq[(MODE == BWD_TAN || MODE == JVP_TAN) ? CW : 1];
+        if (STATE) {
 #pragma unroll
             for (int c = 0; c < CW; c += 16) {
                 if (j0 + c0 + c >= a.hp_out) {
@@ -299,13 +313,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                 float a0v[16];
                 load16_f32(a.A0 + (long long)n * hp + j0 + c0 + c, a0v);
                 float ydv[16];
-                if (MODE == BWD_TAN) load16_f32(a.YD + (long long)n * hp + j0 + c0 + c, ydv);
+                if (MODE == BWD_TAN || MODE == JVP_TAN) load16_f32(a.YD + (long long)n * hp + j0 + c0 + c, ydv);
 #pragma unroll
                 for (int i = 0; i < 16; i++) {
                     float y0 = tanhf(a0v[i]);
                     st1[c + i] = 1.f - y0 * y0;
                     st2[c + i] = 0.f;
                     if (MODE == BWD_TAN) stq[c + i] = __float2bfloat16_rn(4.f * y0 * ydv[i]);
+                    if (MODE == JVP_TAN) stq[c + i] = __float2bfloat16_rn(-2.f * y0 * ydv[i]);   // -2 y_0 da_0
                 }
             }
         }
@@ -350,6 +365,33 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                     store16_f32(a.A0 + (long long)n * hp + j, a0v);
                     store16_bf16(a.out_hi + (long long)n * hp + j, hi);
                     store16_bf16(a.out_lo + (long long)n * hp + j, lo);
+                } else if (MODE == JVP_VALUE) {
+                    float da[16], dy[16], a0v[16];
+                    load16_f32(a.A0 + (long long)n * hp + j, a0v);
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        bool valid = live && (j + i < a.n_out);
+                        da[i] = valid ? v[i] + a.bias[j + i] : 0.f;
+                        float y0 = tanhf(a0v[i]);
+                        dy[i] = (1.f - y0 * y0) * da[i];
+                    }
+                    store16_f32(a.YD + (long long)n * hp + j, da);
+                    store16_bf16(a.out_hi + (long long)n * hp + j, dy);
+                } else if (MODE == JVP_TAN) {
+                    if (s == a.S - 1) {
+                        store16_f32(a.DAD + (long long)n * hp + j, v);
+                    } else {
+                        float yi[16], dy[16];
+                        load16_bf16(a.ytan + ((long long)s * a.N_pad + n) * hp + j, yi);
+                        const float wc = a.chw[s - 1];
+#pragma unroll
+                        for (int i = 0; i < 16; i++) {
+                            dy[i] = fmaf(__bfloat162float(stq[c + i]), yi[i], st1[c + i] * v[i]);
+                            st2[c + i] = fmaf(wc * yi[i], v[i], st2[c + i]);
+                            if (!live || j + i >= a.n_out) dy[i] = 0.f;
+                        }
+                        store16_bf16(a.out_hi + ((long long)s * a.N_pad + n) * hp + j, dy);
+                    }
                 } else if (MODE == FWD_TANLAP) {
                     if (s == a.S - 1) {
                         store16_f32(a.AD + (long long)n * hp + j, v);
@@ -443,7 +485,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
         }
-        if ((MODE == FWD_TANLAP || MODE == BWD_TAN) && !abort_flag) {
+        if (STATE && !abort_flag) {
 #pragma unroll
             for (int c = 0; c < CW; c += 16) {
                 const int j = j0 + c0 + c;

@@ -94,6 +94,9 @@ struct MxState {
     float* Qf;          // general operator: tangent directions (d x d, FP32)
     double* gtan;       // general operator: first-layer tangent gradient sums (h_1 x d)
     float* seed;        // reverse mode: per-point seeds c_{n,s} of the interior pass (S x N_pad)
+    MxWeights dw;       // KFAC*: the direction converted like the weights
+    bool have_dw;
+    float* jdad[KFAC_MAX_LAYERS];   // KFAC*: da_D of the second-order row per hidden layer (N_pad x hp)
 };
 
 MxState* MX(kfac_pinn_handle* h) { return (MxState*)h->mx; }
@@ -563,6 +566,103 @@ __global__ void k_rotate_first(const float* __restrict__ W1f, const float* __res
     W1Qf[idx] = acc;
 }
 
+// ---------------------------------------------------------------------------
+// Forward-mode derivative of the Taylor pass in a parameter direction dW (the
+// residual JVPs of KFAC*); the linearised tanh rule of Eq. 6 in the y-form:
+//   dy_0 = s1 da_0,  dy_i = -2 y_0 y_i da_0 + s1 da_i,
+//   dy_D = s2 da_0 a_D + s1 da_D + s3 da_0 sum_i w_i a_i^2 - 4 y_0 sum_i w_i y_i da_i
+// ---------------------------------------------------------------------------
+__global__ void k_jvp_layer1(const float* __restrict__ dW1f, const float* __restrict__ Wt,
+                             const float* __restrict__ dWt, const float* __restrict__ Xf,
+                             const float* __restrict__ A0, const float* __restrict__ SSQ,
+                             const float* __restrict__ chw, int N, int N_pad, int d, int h, int hp, int S, bf16* dT,
+                             float* DA0) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)N_pad * hp) return;
+    const int n = (int)(idx / hp), j = (int)(idx % hp);
+    const long long blk = (long long)N_pad * hp;
+    const bool live = (n < N) && (j < h);
+    float da0 = dW1f[(long long)d * hp + j];
+    for (int k = 0; k < d; k++) da0 = fmaf(dW1f[(long long)k * hp + j], Xf[(long long)n * d + k], da0);
+    da0 = live ? da0 : 0.f;
+    const float y0 = live ? tanhf(A0[idx]) : 0.f;
+    const float s1 = 1.f - y0 * y0;
+    DA0[idx] = da0;
+    dT[idx] = __float2bfloat16_rn(s1 * da0);
+    if (S == 1) return;
+    float P = 0.f;
+    for (int i = 0; i < d; i++) {
+        const float yi = s1 * Wt[(long long)i * hp + j];
+        const float dai = dWt[(long long)i * hp + j];
+        const float dyi = live ? fmaf(-2.f * y0 * yi, da0, s1 * dai) : 0.f;
+        dT[(1 + i) * blk + idx] = __float2bfloat16_rn(dyi);
+        P = fmaf(chw[i] * yi, dai, P);
+    }
+    const float s3 = -2.f * s1 * (1.f - 3.f * y0 * y0);
+    const float dyD = live ? s3 * da0 * SSQ[idx] - 4.f * y0 * P : 0.f;   // a_D = da_D = 0 at layer 1
+    dT[(S - 1) * blk + idx] = __float2bfloat16_rn(dyD);
+}
+
+__global__ void k_jvp_lap_finish(const float* __restrict__ part, int n_chunks, int N, int N_pad, int h, int hp,
+                                 int S, const float* __restrict__ A0, const float* __restrict__ AD,
+                                 const float* __restrict__ SSQ, const float* __restrict__ DA0,
+                                 const float* __restrict__ DAD, bf16* dT) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long blk = (long long)N_pad * hp;
+    if (idx >= blk) return;
+    const int n = (int)(idx / hp), j = (int)(idx % hp);
+    float P = 0.f;
+    for (int z = 0; z < n_chunks; z++) P += part[z * blk + idx];
+    const float y0 = tanhf(A0[idx]);
+    const float s1 = 1.f - y0 * y0, s2 = -2.f * y0 * s1, s3 = -2.f * s1 * (1.f - 3.f * y0 * y0);
+    const float da0 = DA0[idx];
+    float dyD = s2 * da0 * AD[idx] + s1 * DAD[idx] + s3 * da0 * SSQ[idx] - 4.f * y0 * P;
+    if (n >= N || j >= h) dyD = 0.f;
+    dT[(S - 1) * blk + idx] = __float2bfloat16_rn(dyD);
+}
+
+// dZ^{(L)} rows of the selected Taylor blocks: T dw_L (+ db_L on value rows) + dT w_L.
+__global__ void k_last_jvp(const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo, const bf16* __restrict__ dT,
+                           const float* __restrict__ wL, const float* __restrict__ dwL, int N_pad, int S, int hp,
+                           BlockSel sel, float* jz) {
+    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    const long long nrows = (long long)(sel.nsel ? sel.nsel : S) * N_pad;
+    if (wid >= nrows) return;
+    const int bi = (int)(wid / N_pad), n = (int)(wid % N_pad);
+    const int s = sel.nsel ? sel.b[bi] : bi;
+    wid = (long long)s * N_pad + n;
+    const bf16* row = T_hi + wid * hp;
+    const bf16* drow = dT + wid * hp;
+    const bf16* lrow = nullptr;
+    if (s == 0) lrow = T_lo + (long long)n * hp;
+    else if (s == S - 1) lrow = T_lo + ((long long)N_pad + n) * hp;
+    else if (s == 1 && sel.split_time) lrow = T_lo + (2LL * N_pad + n) * hp;
+    float acc = 0.f;
+    for (int j = lane; j < hp; j += 32) {
+        float t = __bfloat162float(row[j]);
+        if (lrow) t += __bfloat162float(lrow[j]);
+        acc = fmaf(t, dwL[j], acc);
+        acc = fmaf(__bfloat162float(drow[j]), wL[j], acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) jz[wid] = acc + (s == 0 ? dwL[hp] : 0.f);
+}
+
+__global__ void k_residual_jvp_mx(const float* __restrict__ jz, double* jv, int N, int N_pad, int S, int interior,
+                                  double cT, double cD) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double v;
+    if (!interior) {
+        v = (double)jz[n];
+    } else {
+        v = cD * (double)jz[(long long)(S - 1) * N_pad + n];
+        if (cT != 0.0) v += cT * (double)jz[N_pad + n];
+    }
+    jv[n] = v;
+}
+
 // Reverse mode of the forward Laplacian: the seed c_{n,s} = dphi/dZ^{(L)}_{n,s} per
 // point, in FP32: the value row takes du, the tangent rows dgrad (rotated into
 // the tangent directions, Q^T dgrad, for a general operator), the last row dlap.
@@ -846,8 +946,7 @@ kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, co
 // ============================================================================
 // Forward / backward of one pass
 // ============================================================================
-kfac_status_t convert_weights(kfac_pinn_handle* h, cudaStream_t s, const double* theta) {
-    MxWeights& w = MX(h)->w;
+kfac_status_t convert_weights_into(kfac_pinn_handle* h, cudaStream_t s, const double* theta, MxWeights& w) {
     const int L = h->cfg.L;
     for (int l = 2; l <= L - 1; l++) {
         int hout = h->dims[l], hin = h->dims[l - 1];
@@ -871,6 +970,10 @@ kfac_status_t convert_weights(kfac_pinn_handle* h, cudaStream_t s, const double*
     k_convert_last<<<ceil_div_u(hin_p + 1, EW), EW, 0, s>>>(theta + h->woff[L - 1], hin, hin_p, w.wL);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
+}
+
+kfac_status_t convert_weights(kfac_pinn_handle* h, cudaStream_t s, const double* theta) {
+    return convert_weights_into(h, s, theta, MX(h)->w);
 }
 
 kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X, int N,
@@ -1101,6 +1204,41 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
 // ============================================================================
 // Library-internal entry points
 // ============================================================================
+namespace {
+
+// Device copies of one parameter vector in the layouts the kernels read.
+kfac_status_t alloc_weights(kfac_pinn_handle* h, MxWeights& w) {
+    const int L = h->cfg.L;
+    kfac_status_t st;
+    for (int l = 2; l <= L - 1; l++) {
+        int hout_p = round_up(h->dims[l], 64), hin_p = round_up(h->dims[l - 1], 64);
+        size_t e = (size_t)hout_p * hin_p;
+        if ((st = dal(&w.W_hi[l - 1], e))) return st;
+        if ((st = dal(&w.W_lo[l - 1], e))) return st;
+        if ((st = dal(&w.Wt[l - 1], e))) return st;
+        if ((st = dal(&w.bias[l - 1], (size_t)hout_p))) return st;
+        bool ok = tc_make_tmap_2d(&w.kW_hi[l - 1], w.W_hi[l - 1], hin_p, hout_p, hin_p * 2, 64, 128) &&
+                  tc_make_tmap_2d(&w.kW_lo[l - 1], w.W_lo[l - 1], hin_p, hout_p, hin_p * 2, 64, 128) &&
+                  tc_make_tmap_2d(&w.kWt[l - 1], w.Wt[l - 1], hout_p, hin_p, hout_p * 2, 64, 128);
+        if (!ok) return KFAC_CUDA_ERROR;
+    }
+    if ((st = dal(&w.wL, (size_t)round_up(h->dims[L - 1], 64) + 1))) return st;
+    if ((st = dal(&w.W1f, (size_t)(h->dims[0] + 1) * round_up(h->dims[1], 64)))) return st;
+    if (h->opQ && (st = dal(&w.W1Qf, (size_t)h->dims[0] * round_up(h->dims[1], 64)))) return st;
+    return KFAC_OK;
+}
+
+void free_weights(MxWeights& w) {
+    for (int l = 0; l < KFAC_MAX_LAYERS; l++) {
+        cudaFree(w.W_hi[l]); cudaFree(w.W_lo[l]); cudaFree(w.Wt[l]); cudaFree(w.bias[l]);
+    }
+    cudaFree(w.wL);
+    cudaFree(w.W1f);
+    cudaFree(w.W1Qf);
+}
+
+}  // namespace
+
 kfac_status_t tc_alloc(kfac_pinn_handle* h) {
     if (h->cfg.L < 2) return KFAC_BAD_ARG;   // the mixed path needs a hidden layer
     MxState* m = (MxState*)calloc(1, sizeof(MxState));
@@ -1113,23 +1251,15 @@ kfac_status_t tc_alloc(kfac_pinn_handle* h) {
     int hp_max = 64;
     for (int l = 0; l <= L; l++) hp_max = hp_max > round_up(h->dims[l], 64) ? hp_max : round_up(h->dims[l], 64);
     m->hp_max = hp_max;
-    for (int l = 2; l <= L - 1; l++) {
-        int hout_p = round_up(h->dims[l], 64), hin_p = round_up(h->dims[l - 1], 64);
-        size_t e = (size_t)hout_p * hin_p;
-        if ((st = dal(&m->w.W_hi[l - 1], e))) return st;
-        if ((st = dal(&m->w.W_lo[l - 1], e))) return st;
-        if ((st = dal(&m->w.Wt[l - 1], e))) return st;
-        if ((st = dal(&m->w.bias[l - 1], (size_t)hout_p))) return st;
-        bool ok = tc_make_tmap_2d(&m->w.kW_hi[l - 1], m->w.W_hi[l - 1], hin_p, hout_p, hin_p * 2, 64, 128) &&
-                  tc_make_tmap_2d(&m->w.kW_lo[l - 1], m->w.W_lo[l - 1], hin_p, hout_p, hin_p * 2, 64, 128) &&
-                  tc_make_tmap_2d(&m->w.kWt[l - 1], m->w.Wt[l - 1], hout_p, hin_p, hout_p * 2, 64, 128);
-        if (!ok) return KFAC_CUDA_ERROR;
+    if ((st = alloc_weights(h, m->w))) return st;
+    if (h->cfg.update == KFAC_UPDATE_AUTO) {
+        if ((st = alloc_weights(h, m->dw))) return st;
+        m->have_dw = true;
+        for (int l = 1; l <= L - 1; l++)
+            if ((st = dal(&m->jdad[l - 1], (size_t)m->in.N_pad * round_up(h->dims[l], 64)))) return st;
     }
-    if ((st = dal(&m->w.wL, (size_t)round_up(h->dims[L - 1], 64) + 1))) return st;
-    if ((st = dal(&m->w.W1f, (size_t)(h->dims[0] + 1) * round_up(h->dims[1], 64)))) return st;
     if (h->opQ) {
         const int d = h->dims[0];
-        if ((st = dal(&m->w.W1Qf, (size_t)d * round_up(h->dims[1], 64)))) return st;
         if ((st = dal(&m->Qf, (size_t)d * d))) return st;
         if ((st = dal(&m->gtan, (size_t)h->dims[1] * d))) return st;
         std::vector<double> q((size_t)d * d);
@@ -1154,12 +1284,9 @@ void tc_free(kfac_pinn_handle* h) {
     if (!m) return;
     free_pass(m->in);
     free_pass(m->bd);
-    for (int l = 0; l < KFAC_MAX_LAYERS; l++) {
-        cudaFree(m->w.W_hi[l]); cudaFree(m->w.W_lo[l]); cudaFree(m->w.Wt[l]); cudaFree(m->w.bias[l]);
-    }
-    cudaFree(m->w.wL);
-    cudaFree(m->w.W1f);
-    cudaFree(m->w.W1Qf);
+    free_weights(m->w);
+    if (m->have_dw) free_weights(m->dw);
+    for (int l = 0; l < KFAC_MAX_LAYERS; l++) cudaFree(m->jdad[l]);
     cudaFree(m->Qf);
     cudaFree(m->gtan);
     cudaFree(m->seed);
@@ -1296,4 +1423,87 @@ kfac_status_t tc_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s,
         KFAC_LAUNCH_CHECK(h);
     }
     return KFAC_OK;
+}
+
+namespace {
+
+// J_theta r . v for one pass whose forward activations at theta are held in P,
+// with the direction v already converted into m->dw.
+kfac_status_t jvp_pass(kfac_pinn_handle* h, cudaStream_t s, MxPass& P, int N, bool interior, double* jv) {
+    MxState* m = MX(h);
+    const int L = h->cfg.L, d = h->dims[0], S = P.S;
+    const int heat = h->cfg.op == KFAC_OP_HEAT;
+    kfac_status_t st;
+    {
+        MxLayer& l1 = P.lay[0];
+        const float* Wt = m->w.W1Qf ? m->w.W1Qf : m->w.W1f;
+        const float* dWt = m->dw.W1Qf ? m->dw.W1Qf : m->dw.W1f;
+        k_jvp_layer1<<<ceil_div_u((long long)P.N_pad * l1.hp, EW), EW, 0, s>>>(
+            m->dw.W1f, Wt, dWt, P.Xf, l1.A0, l1.SSQ, h->chw32, N, P.N_pad, d, l1.h, l1.hp, S, l1.Zb, l1.YD);
+        KFAC_LAUNCH_CHECK(h);
+    }
+    for (int l = 2; l <= L - 1; l++) {
+        MxLayer& in = P.lay[l - 2];
+        MxLayer& out = P.lay[l - 1];
+        Args a = base_args(h, P, N);
+        a.a0 = in.kT_hi;
+        a.b0 = m->dw.kW_hi[l - 1];
+        a.a1 = in.kZb;
+        a.b1 = m->w.kW_hi[l - 1];
+        a.k_steps = in.hp / 64;
+        a.n_out = out.h;
+        a.hp_out = out.hp;
+        a.out_hi = out.Zb;
+        a.bias = m->dw.bias[l - 1];
+        a.A0 = out.A0;
+        a.YD = out.YD;
+        const int jb = (out.hp + 127) / 128, pb = P.N_pad / 128;
+        const double fl = 2.0 * 2.0 * P.N_pad * (double)out.hp * in.hp;
+        if ((st = launch_engine<tck::JVP_VALUE>(h, s, a, dim3(jb, pb, 1), KFAC_KC_LAYER_GEMM, fl))) return st;
+        if (S > 1) {
+            a.ytan = out.T_hi;
+            a.DAD = m->jdad[l - 1];
+            a.part = m->part;
+            choose_chunks(S - 1, jb * pb, h->sm_count, a.chunk_len, a.n_chunks);
+            if ((st = launch_engine<tck::JVP_TAN>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_LAYER_GEMM,
+                                                  fl * (S - 1))))
+                return st;
+            const long long cnt = (long long)P.N_pad * out.hp;
+            k_jvp_lap_finish<<<ceil_div_u(cnt, EW), EW, 0, s>>>(m->part, a.n_chunks, N, P.N_pad, out.h, out.hp, S,
+                                                                 out.A0, out.AD, out.SSQ, out.YD, m->jdad[l - 1],
+                                                                 out.Zb);
+            KFAC_LAUNCH_CHECK(h);
+        }
+    }
+    MxLayer& last = P.lay[L - 2];
+    BlockSel sel;
+    sel.b[0] = sel.b[1] = sel.b[2] = 0;
+    sel.split_time = 0;
+    if (interior) {
+        sel.nsel = heat ? 2 : 1;
+        sel.b[0] = S - 1;
+        sel.b[1] = 1;
+        sel.split_time = heat;
+    } else {
+        sel.nsel = 1;
+    }
+    k_last_jvp<<<ceil_div_u((long long)sel.nsel * P.N_pad * 32, EW), EW, 0, s>>>(last.T_hi, last.T_lo, last.Zb,
+                                                                                 m->w.wL, m->dw.wL, P.N_pad, S,
+                                                                                 last.hp, sel, P.zl);
+    KFAC_LAUNCH_CHECK(h);
+    k_residual_jvp_mx<<<ceil_div_u(N, EW), EW, 0, s>>>(P.zl, jv, N, P.N_pad, S, interior ? 1 : 0, h->cT, h->cD);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+}  // namespace
+
+kfac_status_t tc_residual_jvp(kfac_pinn_handle* h, cudaStream_t s, const double* v, int N_int, int N_bdy,
+                              double* jv_int, double* jv_bdy) {
+    MxState* m = MX(h);
+    if (!m->have_dw) return KFAC_BAD_ARG;
+    kfac_status_t st;
+    if ((st = convert_weights_into(h, s, v, m->dw))) return st;
+    if ((st = jvp_pass(h, s, m->in, N_int, true, jv_int))) return st;
+    return jvp_pass(h, s, m->bd, N_bdy, false, jv_bdy);
 }

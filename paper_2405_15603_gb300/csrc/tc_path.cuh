@@ -18,3 +18,7 @@ kfac_status_t tc_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* th
 kfac_status_t tc_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
                                             const double* X, int N, const double* du, const double* dgrad,
                                             const double* dlap, double* dtheta, double* dX, bool accumulate);
+// J_theta r . v for the interior and boundary residuals of the last kfac_pinn_step's
+// batch (forward activations at theta still held by the handle), KFAC*.
+kfac_status_t tc_residual_jvp(kfac_pinn_handle* h, cudaStream_t s, const double* v, int N_int, int N_bdy,
+                              double* jv_int, double* jv_bdy);

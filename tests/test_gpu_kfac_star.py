@@ -57,10 +57,55 @@ def test_kfac_star_steps_fp64(case):
     assert opt.sync_status() == "KFAC_OK"
 
 
-def test_kfac_star_requires_fp64():
-    from paper_2405_15603_gb300.api import KfacPinn, KfacError
-    with pytest.raises(KfacError):
-        KfacPinn(2, (16, 1), device=DEV, precision="mixed_bf16", update="kfac_star", max_n_int=8, max_n_bdy=8)
+MIXED_CASES = [
+    ("poisson5d_5-64-64-48-48-1", si.PROBLEMS["poisson5d_cos"], (64, 64, 48, 48, 1), 256, 64),
+    ("heat4d_5-128-128-64-1", si.PROBLEMS["heat4d_sin"], (128, 128, 64, 1), 200, 100),
+]
+
+
+@pytest.mark.parametrize("case", MIXED_CASES, ids=[c[0] for c in MIXED_CASES])
+def test_kfac_star_mixed_precision(case):
+    # The mixed path's (alpha*, mu*) against the oracle's quadratic model built
+    # along the GPU's own direction and previous update (so only the tensor-core
+    # JVPs are under test), at the BF16 tolerance of the JVPs.
+    from paper_2405_15603_gb300.api import KfacPinn
+    _, prob, widths, N, Nb = case
+    lam = 1e-3
+    opt = KfacPinn(prob.d, widths, device=DEV, op=prob.op, kappa=prob.kappa, precision="mixed_bf16",
+                   max_n_int=N, max_n_bdy=Nb, lam=lam, beta=0.9, init_identity=True, update="kfac_star")
+    cfg = ko.KfacConfig(d=prob.d, widths=widths, op=prob.op, kappa=prob.kappa, lam=lam)
+    th = si.xavier_theta(prob.d, widths, 3)
+    theta = torch.tensor(th, device=DEV)
+    prev = None
+    for step in range(2):
+        Xi, f, Xb, g = si.make_batch(prob, N, Nb, seed=8, step=step)
+        th_before = theta.cpu().numpy().copy()
+        opt.step(theta, Xi, f, Xb, g)
+        Dl = opt.direction().cpu().numpy()
+        gr = opt.gradient().cpu().numpy()
+        coef = opt.update_coefficients().cpu().numpy()
+        th_after = theta.cpu().numpy()
+        assert opt.sync_status() == "KFAC_OK"
+        cg = ko.curvature_and_gradient(cfg, ko.unpack_theta(th_before, prob.d, widths), Xi, f, Xb, g)
+        unpack = lambda v: ko.unpack_theta(v, prob.d, widths)
+        jD = ko.residual_jvp(cg, unpack(Dl))
+        a11 = ko.gramian_bilinear(jD, jD) + lam * Dl @ Dl
+        b1 = Dl @ gr
+        if prev is None:
+            alpha_ref, mu_ref = -b1 / a11, 0.0
+        else:
+            jd = ko.residual_jvp(cg, unpack(prev))
+            a12 = ko.gramian_bilinear(jD, jd) + lam * Dl @ prev
+            a22 = ko.gramian_bilinear(jd, jd) + lam * prev @ prev
+            alpha_ref, mu_ref = -np.linalg.solve([[a11, a12], [a12, a22]], [b1, prev @ gr])
+        assert abs(coef[0] - alpha_ref) <= 3e-2 * abs(alpha_ref), (coef[0], alpha_ref)
+        if prev is None:
+            assert coef[1] == 0.0
+        else:
+            assert abs(coef[1] - mu_ref) <= 3e-2 * max(abs(mu_ref), 0.05), (coef[1], mu_ref)
+        np.testing.assert_allclose(th_after - th_before, coef[0] * Dl + (0 if prev is None else coef[1] * prev),
+                                   rtol=1e-9, atol=1e-15)
+        prev = th_after - th_before
 
 
 def test_update_coefficients_of_fixed_and_line_search_rules():
