@@ -4,8 +4,10 @@
 // for every layer at once, each stage spread over the whole GPU:
 //   1. blocked Cholesky P = L L^T               (diag / panel / trailing kernels)
 //   2. M = L^{-1} Q L^{-T}                      (two column-parallel TRSMs)
-//   3. Householder tridiagonalisation of M      (one cooperative kernel; each
-//      problem owns a group of CTAs that sync through bounded global barriers)
+//   3. Householder tridiagonalisation of M      (one thread-block cluster per
+//      problem with the triangle in distributed shared memory; for factors
+//      too large for it, one cooperative kernel where each problem owns a
+//      group of CTAs that sync through bounded global barriers)
 //   4. divide and conquer on the tridiagonal T  (Cuppen's rank-one tearing,
 //      deflation, secular equation solved by bisection, eigenvectors via the
 //      Gu-Eisenstat recomputed z, block GEMMs per merge level)
@@ -18,6 +20,7 @@
 #include <math.h>
 #include <vector>
 #include <algorithm>
+#include <cooperative_groups.h>
 
 #include "kfac_internal.cuh"
 
@@ -100,6 +103,11 @@ struct EigState {
     int n_cta;
     std::vector<Level> levels;
     int nmax;
+    // cluster tridiagonalisation (used when every problem's triangle fits)
+    int trc_cl;                 // CTAs per cluster; 0: the cooperative kernel instead
+    int trc_lds, trc_rmax;
+    size_t trc_smem;
+    int* clu_prob;              // problem of each cluster, largest first
 };
 
 EigState* ES(kfac_pinn_handle* h) { return (EigState*)h->eig; }
@@ -603,6 +611,256 @@ __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, 
         for (int i = threadIdx.x; i < n; i += blockDim.x) p.d[i] = __ldcg(M + (long long)i * n + i);
         if (threadIdx.x == 0 && n >= 2) p.e[n - 2] = __ldcg(M + (long long)(n - 1) * n + (n - 2));
     }
+}
+
+// The same reduction with the lower triangle of M held in the distributed
+// shared memory of one thread-block cluster per problem (up to 16 CTAs).  CTA
+// c of the cluster owns rows r = c + CL*t, t = 0, 1, ..., each stored as its
+// columns 0..r, packed one row after another.  Per column k (b = k + 1):
+//   - gather the pivot column x = M[b.., k] from its owners and form the
+//     reflector (the same arithmetic in every CTA, so every CTA takes the
+//     same decisions);
+//   - M v over the owned rows, from M x and the column M e_0: column sums for
+//     the transposed part and the diagonal, warp dots for the strictly lower
+//     part (every stored element is used twice, so the symmetric matrix costs
+//     half the FP64 operations of a full one);
+//   - each CTA sums its slice of M v over the cluster's partials (fixed
+//     order), and every CTA assembles w = tau M v - K v from the slices;
+//   - rank-2 update of the owned rows, column b first: the next pivot column
+//     is sent, the cluster barrier arrived at, and the rest of the update runs
+//     while the barrier completes.
+// Every exchange is a store into the consumer's shared memory before a
+// barrier (no remote loads wait on the critical path).
+// Three cluster barriers per column and no global-memory synchronisation;
+// the cluster's barriers are hardware barriers that every CTA reaches in the
+// same order (all control flow is uniform over the cluster).
+constexpr int TRC_THREADS = 512;
+constexpr int TRC_CL = 16;    // CTAs per cluster (a non-portable cluster size)
+constexpr int TRC_RED = TRC_THREADS + 8;   // reduction scratch: one slot per thread + scalars
+constexpr int TRC_TK = TRC_THREADS, TRC_SCALE = TRC_THREADS + 1, TRC_KP = TRC_THREADS + 2, TRC_K = TRC_THREADS + 3;
+
+// Warp 0's sum of the per-thread partials sh[0..TRC_THREADS) (written and
+// synchronised by the caller); every lane of warp 0 gets the same total.  The
+// FP64 pipe is the scarce unit on this part, so the other warps issue no FP64
+// adds for a reduction, and the dependency chain is kept short (four
+// independent chains, then a butterfly).
+__device__ __forceinline__ double trc_warp0_sum(const double* sh) {
+    const int l = threadIdx.x % 32;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+    for (int u = 0; u < TRC_THREADS / 32; u += 4) {
+        a0 += sh[l + 32 * u];
+        a1 += sh[l + 32 * (u + 1)];
+        a2 += sh[l + 32 * (u + 2)];
+        a3 += sh[l + 32 * (u + 3)];
+    }
+    double t = (a0 + a1) + (a2 + a3);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+}
+
+__host__ __device__ inline long long trc_off(int t, int c, int cl) {
+    return (long long)t * (c + 1) + (long long)cl * t * (t - 1) / 2;
+}
+
+__global__ void __launch_bounds__(TRC_THREADS, 1) k_tridiag_cluster(Prob* pr, const int* clu_prob, int lds, int nmax,
+                                                                    int rmax, int* fail) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double trc_sm[];
+    constexpr int CL = TRC_CL;
+    const int c = (int)cl.block_rank();
+    const int pi = clu_prob[blockIdx.x / CL];
+    if (fail[pi]) return;   // uniform over the cluster, before any barrier
+    const Prob p = pr[pi];
+    const int n = p.n;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int warp = tid / 32, lane = tid % 32, nwarps = T / 32;
+    double* As = trc_sm;              // owned rows, packed
+    double* xb = As + lds;            // pivot column by global row (pushed by its owners)
+    double* v = xb + nmax;            // reflector, by i = j - b
+    double* w = v + nmax;             // tau M v - K v, by i
+    double* pp = w + nmax;            // this CTA's partial of M x, by i
+    double* pf = pp + nmax;           // tau M v, by i (pushed by the slice owners)
+    double* ppin = pf + nmax;         // the cluster's partials of this CTA's slice, [source][entry]
+    double* kpin = ppin + CL * rmax;  // the slices' (tau M v)^T v (pushed)
+    double* rd = kpin + CL;           // strictly-lower row dots, by local row
+    double* red = rd + rmax;          // reductions and the per-column scalars
+    const int R = c < n ? (n - c + CL - 1) / CL : 0;
+
+    for (int t = warp; t < R; t += nwarps) {
+        const int r = c + CL * t;
+        const long long o = trc_off(t, c, CL);
+        for (int j = lane; j <= r; j += 32) As[o + j] = p.M[(long long)r * n + j];
+    }
+    __syncthreads();
+    for (int t = tid; t < R; t += T) {     // the first pivot column, to every CTA
+        const int r = c + CL * t;
+        if (r < 1) continue;
+        const double val = As[trc_off(t, c, CL)];
+#pragma unroll
+        for (int d = 0; d < CL; d++) cl.map_shared_rank(xb, d)[r] = val;
+    }
+    cl.sync();
+
+    for (int k = 0; k + 2 < n; k++) {
+        const int b = k + 1, m = n - b;
+        // x = M[b.., k] is in xb[b..n)
+        double part = 0.0;
+        for (int r = b + 1 + tid; r < n; r += T) part = fma(xb[r], xb[r], part);
+        red[tid] = part;
+        __syncthreads();
+        // Warp 0 forms the reflector's scalars while every warp computes M x
+        // over the owned rows: v = s x + (1 - s x_0) e_0 (s = 1/(x_0 - beta)),
+        // so M v = s (M x) + (1 - s x_0) M e_0 is assembled afterwards and the
+        // latency of the square root and division hides behind the FP64 work.
+        if (warp == 0) {
+            const double sigma = trc_warp0_sum(red);
+            if (lane == 0) {
+                const double x0 = xb[b];
+                double tk = 0.0, beta = x0, scale = 0.0;
+                if (sigma > 0.0) {
+                    const double mu = sqrt(x0 * x0 + sigma);
+                    beta = (x0 <= 0.0) ? mu : -mu;
+                    tk = (beta - x0) / beta;
+                    scale = 1.0 / (x0 - beta);
+                }
+                red[TRC_TK] = tk;
+                red[TRC_SCALE] = scale;
+                if (c == 0) { p.tau[k] = tk; p.e[k] = beta; }
+            }
+        }
+        // transposed part and diagonal of M x, one thread per column j.  The
+        // work of a column falls with j; 32-column chunks go to the warps in a
+        // snake order over the four SM sub-partitions (warp w runs on
+        // sub-partition w mod 4), so every sub-partition's FP64 pipe gets the
+        // same share.
+        const int sp = warp & 3, slot = warp >> 2;
+        const int snake = (slot & 1) ? 3 - sp : sp;
+        for (int q = 4 * slot + snake; 32 * q < m; q += 16) {
+            const int j = b + 32 * q + lane;
+            if (j >= n) break;
+            double acc = 0.0;
+            int t0 = j < c ? 0 : (j - c) / CL + 1;
+            if (j >= c && (j - c) % CL == 0) acc = As[trc_off(t0 - 1, c, CL) + j] * xb[j];
+            long long o = trc_off(t0, c, CL);
+            for (int t = t0; t < R; t++) {
+                const int r = c + CL * t;
+                acc = fma(As[o + j], xb[r], acc);
+                o += r + 1;
+            }
+            pp[j - b] = acc;
+        }
+        // strictly lower part of the owned rows r > b: four rows per warp,
+        // eight lanes per row, one three-step butterfly for all four; the
+        // groups (whose work grows with the row) in the same snake order
+        {
+            const int g = lane >> 3, gl = lane & 7;
+            for (int t4 = 4 * (4 * slot + snake); t4 < R; t4 += 4 * nwarps) {
+                const int t = t4 + g;
+                const int r = c + CL * t;
+                double acc = 0.0;
+                if (t < R && r > b) {
+                    const double* row = As + trc_off(t, c, CL);
+                    for (int j = b + gl; j < r; j += 8) acc = fma(row[j], xb[j], acc);
+                }
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+                if (gl == 0 && t < R) rd[t] = acc;
+            }
+        }
+        __syncthreads();
+        const double tk = red[TRC_TK], scale = red[TRC_SCALE];
+        const bool act = tk != 0.0;      // uniform: every CTA computed the same tk
+        const double coef = fma(-scale, xb[b], 1.0);
+        const int S = (m + CL - 1) / CL;  // slice length of the cluster reduction
+        // this CTA's partial of M v, pushed to the owner of each entry's slice
+        for (int i = tid; i < m; i += T) {
+            const int r = b + i;
+            double a = pp[i], e0 = 0.0;
+            if (r % CL == c) {
+                const int t = r / CL;
+                if (r > b) a += rd[t];
+                e0 = As[trc_off(t, c, CL) + b];
+            }
+            const int dst = i / S;
+            cl.map_shared_rank(ppin, dst)[c * rmax + (i - dst * S)] = fma(scale, a, coef * e0);
+            const double vi = (i == 0) ? 1.0 : xb[r] * scale;
+            v[i] = vi;
+            if (c == 0) p.H[(long long)k * n + b + i] = vi;   // reflector k for the back-transformation
+        }
+        cl.sync();
+        // this CTA's slice of tau M v, summed over the partials in a fixed
+        // order and pushed to every CTA with the slice's share of (tau M v)^T v
+        if (act && warp == 0) {
+            const int lo = c * S, hi = min(m, lo + S);
+            double kpart = 0.0;
+            for (int i = lo + lane; i < hi; i += 32) {
+                double y[CL];
+#pragma unroll
+                for (int u = 0; u < CL; u++) y[u] = ppin[u * rmax + (i - lo)];
+#pragma unroll
+                for (int h2 = CL / 2; h2 > 0; h2 >>= 1)
+#pragma unroll
+                    for (int u = 0; u < h2; u++) y[u] += y[u + h2];
+                const double pv = tk * y[0];
+#pragma unroll
+                for (int d = 0; d < CL; d++) cl.map_shared_rank(pf, d)[i] = pv;
+                kpart = fma(pv, v[i], kpart);
+            }
+            for (int o = 16; o > 0; o >>= 1) kpart += __shfl_xor_sync(0xffffffffu, kpart, o);
+            if (lane < CL) cl.map_shared_rank(kpin, lane)[c] = kpart;
+        }
+        cl.sync();
+        if (act) {
+            if (warp == 0) {   // K = tau (tau M v)^T v / 2 (the same tree in every CTA)
+                double ks = lane < CL ? kpin[lane] : 0.0;
+                for (int o = 16; o > 0; o >>= 1) ks += __shfl_xor_sync(0xffffffffu, ks, o);
+                if (lane == 0) red[TRC_K] = 0.5 * tk * ks;
+            }
+            __syncthreads();
+            const double K = red[TRC_K];
+            for (int i = tid; i < m; i += T) w[i] = fma(-K, v[i], pf[i]);
+            __syncthreads();
+        }
+        // column b of the owned rows first, pushed to every CTA as the next pivot column
+        for (int t = tid; t < R; t += T) {
+            const int r = c + CL * t;
+            if (r < b) continue;
+            double* a = As + trc_off(t, c, CL) + b;
+            double val = *a;
+            if (act) {
+                val = fma(-v[r - b], w[0], fma(-w[r - b], v[0], val));
+                *a = val;
+            }
+            if (r > b) {
+#pragma unroll
+                for (int d = 0; d < CL; d++) cl.map_shared_rank(xb, d)[r] = val;
+            }
+        }
+        __cluster_barrier_arrive();
+        if (act) {
+            // the rest of the update, one warp per row; the rows (whose work
+            // grows with t) go to the warps in the snake order, so every SM
+            // sub-partition gets the same share of the FP64 work
+            for (int t = 4 * slot + snake; t < R; t += nwarps) {
+                const int r = c + CL * t;
+                if (r <= b) continue;
+                double* row = As + trc_off(t, c, CL);
+                const double vr = v[r - b], wr = w[r - b];
+                for (int j = b + 1 + lane; j <= r; j += 32) row[j] = fma(-vr, w[j - b], fma(-wr, v[j - b], row[j]));
+            }
+        }
+        __syncthreads();
+        __cluster_barrier_wait();
+    }
+    for (int t = tid; t < R; t += T) {
+        const int r = c + CL * t;
+        p.d[r] = As[trc_off(t, c, CL) + r];
+    }
+    if (tid == 0 && n >= 2 && (n - 1) % CL == c)
+        p.e[n - 2] = As[trc_off((n - 1 - c) / CL, c, CL) + n - 2];
 }
 
 // --------------------------------------------------------------------------
@@ -1184,6 +1442,55 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
         if (per_sm * h->sm_count < es->n_cta) return KFAC_BAD_ARG;
     }
 
+    // cluster tridiagonalisation: one 16-CTA cluster per problem when the
+    // largest problem's lower triangle fits in the cluster's shared memory
+    es->trc_cl = 0;
+    es->clu_prob = nullptr;
+    {
+        const int CL = TRC_CL;
+        int lds = 0;
+        for (int i = 0; i < es->np; i++) {
+            const int n = es->host[i].n;
+            for (int c = 0; c < CL && c < n; c++) {
+                const int R = (n - c + CL - 1) / CL;
+                lds = std::max(lds, (int)trc_off(R, c, CL));
+            }
+        }
+        const int rmax = (es->nmax + CL - 1) / CL;
+        const size_t smem = sizeof(double) * ((size_t)lds + 5 * (size_t)es->nmax + (size_t)(CL + 1) * rmax + CL + TRC_RED);
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+        if (smem <= (size_t)optin) {
+            cudaFuncSetAttribute(k_tridiag_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaFuncSetAttribute(k_tridiag_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            cudaLaunchAttribute attr;
+            attr.id = cudaLaunchAttributeClusterDimension;
+            attr.val.clusterDim.x = CL;
+            attr.val.clusterDim.y = 1;
+            attr.val.clusterDim.z = 1;
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3(CL * es->np);
+            lc.blockDim = dim3(TRC_THREADS);
+            lc.dynamicSmemBytes = smem;
+            lc.attrs = &attr;
+            lc.numAttrs = 1;
+            int clusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&clusters, k_tridiag_cluster, &lc) == cudaSuccess && clusters >= 1) {
+                std::vector<int> order(es->np);
+                for (int i = 0; i < es->np; i++) order[i] = i;
+                std::stable_sort(order.begin(), order.end(),
+                                 [&](int x, int y) { return es->host[x].n > es->host[y].n; });
+                if ((st = dal(&es->clu_prob, order.size()))) return st;
+                cudaMemcpy(es->clu_prob, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice);
+                es->trc_cl = CL;
+                es->trc_lds = lds;
+                es->trc_rmax = rmax;
+                es->trc_smem = smem;
+            }
+            cudaGetLastError();   // a refused configuration only selects the cooperative kernel
+        }
+    }
+
     // divide-and-conquer schedules, one per merge level
     for (int s = 1; s < es->nmax; s *= 2) {
         std::vector<Merge> mg;
@@ -1274,6 +1581,7 @@ void eig_free(kfac_pinn_handle* h) {
     cudaFree(es->cta_prob);
     cudaFree(es->cta_rank);
     cudaFree(es->group);
+    cudaFree(es->clu_prob);
     for (auto& lv : es->levels) {
         cudaFree(lv.merges);
         cudaFree(lv.gemms);
@@ -1317,10 +1625,26 @@ kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
     KFAC_LAUNCH_CHECK(h);
     k_symmetrize<<<dim3(64, np), 256, 0, s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
-    // 3. tridiagonalisation (cooperative: the groups wait on each other)
-    KFAC_CUDA_TRY(cudaMemsetAsync(es->bar, 0, sizeof(unsigned) * 3 * np, s));
-    KFAC_CUDA_TRY(cudaMemsetAsync(es->abort_flag, 0, sizeof(int), s));
-    {
+    // 3. tridiagonalisation: one cluster per problem, or cooperative groups of CTAs
+    if (es->trc_cl > 0) {
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = es->trc_cl;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(es->trc_cl * np);
+        lc.blockDim = dim3(TRC_THREADS);
+        lc.dynamicSmemBytes = es->trc_smem;
+        lc.stream = s;
+        lc.attrs = &attr;
+        lc.numAttrs = 1;
+        KFAC_CUDA_TRY(cudaLaunchKernelEx(&lc, k_tridiag_cluster, (Prob*)pr, (const int*)es->clu_prob, es->trc_lds,
+                                         es->nmax, es->trc_rmax, (int*)es->fail));
+        h->launches++;
+    } else {
+        KFAC_CUDA_TRY(cudaMemsetAsync(es->bar, 0, sizeof(unsigned) * 3 * np, s));
+        KFAC_CUDA_TRY(cudaMemsetAsync(es->abort_flag, 0, sizeof(int), s));
         // cooperative launch (every CTA co-resident), in the form stream capture accepts
         cudaLaunchAttribute attr;
         attr.id = cudaLaunchAttributeCooperative;
