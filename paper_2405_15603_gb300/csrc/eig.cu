@@ -2,7 +2,9 @@
 // (Sec. 3.4, "eigen-decomposing all Kronecker factors"):
 //     V^T P V = I,  V^T Q V = diag(w),   P = A~_Omega, Q = A~_bdy   (and B)
 // for every layer at once, each stage spread over the whole GPU:
-//   1. blocked Cholesky P = L L^T               (diag / panel / trailing kernels)
+//   1. Cholesky P = L L^T                       (one cluster per problem, as in 3;
+//                                                 blocked diag / panel / trailing
+//                                                 kernels for the largest factors)
 //   2. M = L^{-1} Q L^{-T}                      (two column-parallel TRSMs)
 //   3. Householder tridiagonalisation of M      (one thread-block cluster per
 //      problem with the triangle in distributed shared memory; for factors
@@ -27,7 +29,7 @@
 namespace {
 
 constexpr int NB = 64;        // Cholesky / TRSM block
-constexpr int CB = 32;        // TRSM column block
+constexpr int CB_MAX = 32;    // widest TRSM column strip
 constexpr int BT_COLS = 16;   // back-transform column block
 constexpr int KFAC_MAX_WIDTH_PLUS_ONE = 1024;   // widths <= 1023 and d + 1 <= 1024 (create checks)
 constexpr int MAXP = 2 * KFAC_MAX_LAYERS;
@@ -101,6 +103,8 @@ struct EigState {
     int* cta_rank;
     int* group;                 // group size per problem
     int n_cta;
+    void* trsm_jobs;            // TrsmJob list, largest work first
+    int n_trsm_jobs;
     std::vector<Level> levels;
     int nmax;
     // cluster tridiagonalisation (used when every problem's triangle fits)
@@ -302,16 +306,14 @@ __global__ void __launch_bounds__(256) k_chol_update(Prob* pr, int k0, int* fail
 //   mode 1: X = L^{-1} B^T, B = Qa,              X -> M
 //   mode 2: X = L^{-T} B,   B = final D&C buffer, X -> V
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_trsm(Prob* pr, int mode, int* fail) {
-    extern __shared__ double sm[];
+// One column strip [c0, c0 + CB) of a triangular solve with NB x NB blocks.
+template <int CB>
+__device__ void trsm_strip(const Prob& p, int c0, int mode, bool failed, double* sm) {
+    constexpr int TRSM_RG = 256 / CB;      // row groups of the 256 threads
     double* Lb = sm;                       // NB x (NB+1)
     double* Xk = Lb + NB * (NB + 1);       // NB x (CB+1)
     double* acc = Xk + NB * (CB + 1);      // NB x (CB+1)
-    const Prob p = pr[blockIdx.y];
     const int n = p.n;
-    const int c0 = blockIdx.x * CB;
-    if (c0 >= n) return;
-    const bool failed = fail[blockIdx.y] != 0;
     const double* B;
     double* X;
     if (mode == 0) { B = p.M; X = p.Qa; }
@@ -352,15 +354,19 @@ __global__ void __launch_bounds__(256) k_trsm(Prob* pr, int mode, int* fail) {
                 Xk[m * (CB + 1) + c] = (m < kr && c < ncb) ? X[(long long)(k0 + m) * n + c0 + c] : 0.0;
             }
             __syncthreads();
-            // acc[r][c] -= sum_m Lb[r][m] Xk[m][c]; 256 threads -> 8 outputs each
-            const int c = threadIdx.x % CB, rg = threadIdx.x / CB;   // rg in 0..7
+            // acc[r][c] -= sum_m Lb[r][m] Xk[m][c]; NB / TRSM_RG outputs per thread
+            const int c = threadIdx.x % CB, rg = threadIdx.x / CB;
+            double v[NB / TRSM_RG];
 #pragma unroll
-            for (int i = 0; i < NB / 8; i++) {
-                const int r = rg + 8 * i;
-                double v = 0.0;
-                for (int m = 0; m < NB; m++) v = fma(Lb[r * (NB + 1) + m], Xk[m * (CB + 1) + c], v);
-                acc[r * (CB + 1) + c] -= v;
+            for (int i = 0; i < NB / TRSM_RG; i++) v[i] = 0.0;
+#pragma unroll 4
+            for (int m = 0; m < NB; m++) {
+                const double x = Xk[m * (CB + 1) + c];
+#pragma unroll
+                for (int i = 0; i < NB / TRSM_RG; i++) v[i] = fma(Lb[(rg + TRSM_RG * i) * (NB + 1) + m], x, v[i]);
             }
+#pragma unroll
+            for (int i = 0; i < NB / TRSM_RG; i++) acc[(rg + TRSM_RG * i) * (CB + 1) + c] -= v[i];
         }
         // diagonal block: X_i = L_ii^{-1} acc (lower) or L_ii^{-T} acc (upper),
         // with the block inverse precomputed by k_diag_inv
@@ -372,16 +378,20 @@ __global__ void __launch_bounds__(256) k_trsm(Prob* pr, int mode, int* fail) {
         __syncthreads();
         {
             const int c = threadIdx.x % CB, rg = threadIdx.x / CB;
+            double v[NB / TRSM_RG];
 #pragma unroll
-            for (int i = 0; i < NB / 8; i++) {
-                const int r = rg + 8 * i;
-                double v = 0.0;
-                for (int m = 0; m < NB; m++) {
-                    const double l = upper ? Lb[m * (NB + 1) + r] : Lb[r * (NB + 1) + m];
-                    v = fma(l, acc[m * (CB + 1) + c], v);
+            for (int i = 0; i < NB / TRSM_RG; i++) v[i] = 0.0;
+#pragma unroll 4
+            for (int m = 0; m < NB; m++) {
+                const double x = acc[m * (CB + 1) + c];
+#pragma unroll
+                for (int i = 0; i < NB / TRSM_RG; i++) {
+                    const int r = rg + TRSM_RG * i;
+                    v[i] = fma(upper ? Lb[m * (NB + 1) + r] : Lb[r * (NB + 1) + m], x, v[i]);
                 }
-                Xk[r * (CB + 1) + c] = v;
             }
+#pragma unroll
+            for (int i = 0; i < NB / TRSM_RG; i++) Xk[(rg + TRSM_RG * i) * (CB + 1) + c] = v[i];
         }
         __syncthreads();
         for (int t = threadIdx.x; t < NB * CB; t += blockDim.x) {
@@ -390,6 +400,23 @@ __global__ void __launch_bounds__(256) k_trsm(Prob* pr, int mode, int* fail) {
         }
         __syncthreads();
     }
+}
+
+// One CTA per job (problem, first column, strip width); the widths make the
+// jobs' FP64 work about equal (16 columns of the largest factors, 32 of the
+// others) and the list is sorted by work, largest first.
+struct TrsmJob {
+    int prob, c0, cb;
+};
+
+__global__ void __launch_bounds__(256, 2) k_trsm(Prob* pr, const TrsmJob* jobs, int mode, int* fail) {
+    extern __shared__ double sm[];
+    const TrsmJob jb = jobs[blockIdx.x];
+    const Prob p = pr[jb.prob];
+    if (jb.c0 >= p.n) return;
+    const bool failed = fail[jb.prob] != 0;
+    if (jb.cb == 16) trsm_strip<16>(p, jb.c0, mode, failed, sm);
+    else trsm_strip<32>(p, jb.c0, mode, failed, sm);
 }
 
 // Inverse of every 64 x 64 diagonal block of L (lower triangular), one CTA
@@ -661,6 +688,106 @@ __device__ __forceinline__ double trc_warp0_sum(const double* sh) {
 
 __host__ __device__ inline long long trc_off(int t, int c, int cl) {
     return (long long)t * (c + 1) + (long long)cl * t * (t - 1) / 2;
+}
+
+// Cholesky P = L L^T of the damped factor (in place in p.L, lower triangle)
+// in one thread-block cluster per problem, with the same row ownership and
+// packed storage as the tridiagonalisation.  Right-looking, one column per
+// step: every CTA holds the pivot column (sent by its owners before the
+// barrier), forms L_kk and the scaled column, updates column k+1 of its rows
+// first and sends it, arrives at the cluster barrier, then runs the rest of
+// the rank-1 update while the barrier completes.  One cluster barrier per
+// column.  A pivot that is not positive and finite stops every CTA of the
+// cluster at the same column (they all see the same pushed value) and marks
+// the problem failed.
+__global__ void __launch_bounds__(TRC_THREADS, 1) k_chol_cluster(Prob* pr, const int* clu_prob, int lds, int nmax,
+                                                                 int* fail, int* status) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double trc_sm[];
+    constexpr int CL = TRC_CL;
+    const int c = (int)cl.block_rank();
+    const int pi = clu_prob[blockIdx.x / CL];
+    const Prob p = pr[pi];
+    const int n = p.n;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int warp = tid / 32, lane = tid % 32, nwarps = T / 32;
+    const int sp = warp & 3, slot = warp >> 2;
+    const int snake = (slot & 1) ? 3 - sp : sp;   // rows to warps evenly over the SM sub-partitions
+    double* As = trc_sm;              // owned rows, packed
+    double* colb = As + lds;          // pivot columns by global row, two buffers (pushed by the owners)
+    double* lb = colb + 2 * nmax;     // scaled column L[k+1.., k], by i = r - k - 1
+    double* red = lb + nmax;          // per-column scalars
+    const int R = c < n ? (n - c + CL - 1) / CL : 0;
+
+    for (int t = warp; t < R; t += nwarps) {
+        const int r = c + CL * t;
+        const long long o = trc_off(t, c, CL);
+        for (int j = lane; j <= r; j += 32) As[o + j] = p.L[(long long)r * n + j];
+    }
+    __syncthreads();
+    for (int t = tid; t < R; t += T) {     // column 0, to every CTA
+        const int r = c + CL * t;
+        const double val = As[trc_off(t, c, CL)];
+#pragma unroll
+        for (int d = 0; d < CL; d++) cl.map_shared_rank(colb, d)[r] = val;
+    }
+    cl.sync();
+
+    bool ok = true;
+    for (int k = 0; k < n; k++) {
+        const double* col = colb + (k & 1) * nmax;
+        double* nxt = colb + ((k + 1) & 1) * nmax;
+        const int m = n - k - 1;
+        if (tid == 0) {
+            const double a = col[k];
+            const bool good = a > 0.0 && isfinite(a);
+            const double lkk = sqrt(good ? a : 1.0);
+            red[0] = lkk;
+            red[1] = 1.0 / lkk;
+            red[2] = good ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        if (red[2] == 0.0) { ok = false; break; }      // uniform over the cluster
+        const double lkk = red[0], rinv = red[1];
+        for (int i = tid; i < m; i += T) lb[i] = col[k + 1 + i] * rinv;
+        __syncthreads();
+        // column k of the owned rows, then column k + 1 updated and sent
+        for (int t = tid; t < R; t += T) {
+            const int r = c + CL * t;
+            if (r < k) continue;
+            double* row = As + trc_off(t, c, CL);
+            if (r == k) { row[k] = lkk; continue; }
+            const double lr = lb[r - k - 1];
+            row[k] = lr;
+            const double a = fma(-lr, lb[0], row[k + 1]);
+            row[k + 1] = a;
+#pragma unroll
+            for (int d = 0; d < CL; d++) cl.map_shared_rank(nxt, d)[r] = a;
+        }
+        __cluster_barrier_arrive();
+        for (int t = 4 * slot + snake; t < R; t += nwarps) {
+            const int r = c + CL * t;
+            if (r <= k + 1) continue;
+            double* row = As + trc_off(t, c, CL);
+            const double lr = lb[r - k - 1];
+            for (int j = k + 2 + lane; j <= r; j += 32) row[j] = fma(-lr, lb[j - k - 1], row[j]);
+        }
+        __syncthreads();
+        __cluster_barrier_wait();
+    }
+    if (!ok) {
+        if (c == 0 && tid == 0) {
+            fail[pi] = 1;
+            latch_status(status, KFAC_NOT_PD);
+        }
+        return;
+    }
+    for (int t = warp; t < R; t += nwarps) {
+        const int r = c + CL * t;
+        const long long o = trc_off(t, c, CL);
+        for (int j = lane; j <= r; j += 32) p.L[(long long)r * n + j] = As[o + j];
+    }
 }
 
 __global__ void __launch_bounds__(TRC_THREADS, 1) k_tridiag_cluster(Prob* pr, const int* clu_prob, int lds, int nmax,
@@ -1442,6 +1569,24 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
         if (per_sm * h->sm_count < es->n_cta) return KFAC_BAD_ARG;
     }
 
+    // triangular-solve jobs of about equal work, largest first
+    {
+        std::vector<TrsmJob> jobs;
+        for (int i = 0; i < es->np; i++) {
+            const int n = es->host[i].n;
+            const int cb = n >= 640 ? 16 : 32;
+            for (int c0 = 0; c0 < n; c0 += cb) jobs.push_back(TrsmJob{i, c0, cb});
+        }
+        std::stable_sort(jobs.begin(), jobs.end(), [&](const TrsmJob& x, const TrsmJob& y) {
+            const double wx = (double)es->host[x.prob].n * es->host[x.prob].n * x.cb;
+            const double wy = (double)es->host[y.prob].n * es->host[y.prob].n * y.cb;
+            return wx > wy;
+        });
+        es->n_trsm_jobs = (int)jobs.size();
+        if (cudaMalloc(&es->trsm_jobs, sizeof(TrsmJob) * jobs.size()) != cudaSuccess) return KFAC_OOM;
+        cudaMemcpy(es->trsm_jobs, jobs.data(), sizeof(TrsmJob) * jobs.size(), cudaMemcpyHostToDevice);
+    }
+
     // cluster tridiagonalisation: one 16-CTA cluster per problem when the
     // largest problem's lower triangle fits in the cluster's shared memory
     es->trc_cl = 0;
@@ -1463,6 +1608,8 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
         if (smem <= (size_t)optin) {
             cudaFuncSetAttribute(k_tridiag_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             cudaFuncSetAttribute(k_tridiag_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
             cudaLaunchAttribute attr;
             attr.id = cudaLaunchAttributeClusterDimension;
             attr.val.clusterDim.x = CL;
@@ -1556,7 +1703,7 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
         es->levels.push_back(lv);
     }
     cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB + 1)));
+                         (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB_MAX + 1)));
     cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(double) * 2 * NB * (NB + 1));
     // The attribute belongs to the kernel, not to this handle: set it for the
@@ -1582,6 +1729,7 @@ void eig_free(kfac_pinn_handle* h) {
     cudaFree(es->cta_rank);
     cudaFree(es->group);
     cudaFree(es->clu_prob);
+    cudaFree(es->trsm_jobs);
     for (auto& lv : es->levels) {
         cudaFree(lv.merges);
         cudaFree(lv.gemms);
@@ -1601,8 +1749,25 @@ kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
 
     k_damp<<<dim3(64, np), 256, 0, s>>>(pr, eps, es->fail);
     KFAC_LAUNCH_CHECK(h);
-    // 1. Cholesky
-    for (int kb = 0; kb < nblk; kb++) {
+    // 1. Cholesky: one cluster per problem, or the blocked kernels
+    if (es->trc_cl > 0) {
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = es->trc_cl;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(es->trc_cl * np);
+        lc.blockDim = dim3(TRC_THREADS);
+        lc.dynamicSmemBytes = sizeof(double) * ((size_t)es->trc_lds + 3 * (size_t)nmax + 8);
+        lc.stream = s;
+        lc.attrs = &attr;
+        lc.numAttrs = 1;
+        KFAC_CUDA_TRY(cudaLaunchKernelEx(&lc, k_chol_cluster, (Prob*)pr, (const int*)es->clu_prob, es->trc_lds, nmax,
+                                         (int*)es->fail, (int*)h->status));
+        h->launches++;
+    }
+    for (int kb = 0; es->trc_cl == 0 && kb < nblk; kb++) {
         const int k0 = kb * NB;
         k_chol_diag<<<np, 256, 0, s>>>(pr, k0, es->fail, h->status);
         KFAC_LAUNCH_CHECK(h);
@@ -1617,11 +1782,10 @@ kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
     // 2. whitening
     k_diag_inv<<<dim3(nblk, np), 256, 2 * NB * (NB + 1) * sizeof(double), s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
-    const int smem_trsm = (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB + 1));
-    const int cbk = (nmax + CB - 1) / CB;
-    k_trsm<<<dim3(cbk, np), 256, smem_trsm, s>>>(pr, 0, es->fail);
+    const int smem_trsm = (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB_MAX + 1));
+    k_trsm<<<es->n_trsm_jobs, 256, smem_trsm, s>>>(pr, (const TrsmJob*)es->trsm_jobs, 0, es->fail);
     KFAC_LAUNCH_CHECK(h);
-    k_trsm<<<dim3(cbk, np), 256, smem_trsm, s>>>(pr, 1, es->fail);
+    k_trsm<<<es->n_trsm_jobs, 256, smem_trsm, s>>>(pr, (const TrsmJob*)es->trsm_jobs, 1, es->fail);
     KFAC_LAUNCH_CHECK(h);
     k_symmetrize<<<dim3(64, np), 256, 0, s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
@@ -1693,7 +1857,7 @@ kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
     // 5. back-transformation, 6. V = L^{-T} U
     k_backtransform<<<dim3((nmax + BT_COLS - 1) / BT_COLS, np), 256, bt_smem_bytes(nmax), s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
-    k_trsm<<<dim3(cbk, np), 256, smem_trsm, s>>>(pr, 2, es->fail);
+    k_trsm<<<es->n_trsm_jobs, 256, smem_trsm, s>>>(pr, (const TrsmJob*)es->trsm_jobs, 2, es->fail);
     KFAC_LAUNCH_CHECK(h);
     k_write_w<<<np, 256, 0, s>>>(pr, es->fail, h->status);
     KFAC_LAUNCH_CHECK(h);
