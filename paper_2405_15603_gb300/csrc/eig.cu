@@ -30,7 +30,7 @@ namespace {
 
 constexpr int NB = 64;        // Cholesky / TRSM block
 constexpr int CB_MAX = 32;    // widest TRSM column strip
-constexpr int BT_COLS = 16;   // back-transform column block
+constexpr int STRIP_NARROW_FROM = 640;   // factors this large get 16-column strips (TRSM, back-transform)
 constexpr int KFAC_MAX_WIDTH_PLUS_ONE = 1024;   // widths <= 1023 and d + 1 <= 1024 (create checks)
 constexpr int MAXP = 2 * KFAC_MAX_LAYERS;
 constexpr double DEPS = 2.220446049250313e-16;
@@ -103,8 +103,9 @@ struct EigState {
     int* cta_rank;
     int* group;                 // group size per problem
     int n_cta;
-    void* trsm_jobs;            // TrsmJob list, largest work first
+    void* trsm_jobs;            // TrsmJob list, largest work first (also the back-transform's)
     int n_trsm_jobs;
+    size_t bt_smem;             // back-transform shared memory for the widest job
     std::vector<Level> levels;
     int nmax;
     // cluster tridiagonalisation (used when every problem's triangle fits)
@@ -1153,10 +1154,12 @@ __global__ void k_dc_roots(Prob* pr, const Merge* merges, int n_merges, int* fai
     for (int it = 0; it < 80; it++) {
         double psi = 0.0, dpsi = 0.0, phi = 0.0, dphi = 0.0, ab = 0.0;
         for (int q = lane; q < k; q += 32) {
-            const double del = (dK[q] - dO) - t;
+            // one reciprocal instead of two divisions (FP64 division is a long
+            // instruction sequence on this part)
+            const double rdel = 1.0 / ((dK[q] - dO) - t);
             const double z2 = zK[q] * zK[q];
-            const double tq = z2 / del;
-            const double dq = tq / del;
+            const double tq = z2 * rdel;
+            const double dq = tq * rdel;
             if (q <= j) { psi += tq; dpsi += dq; } else { phi += tq; dphi += dq; }
             ab += fabs(tq);
         }
@@ -1398,50 +1401,87 @@ __global__ void k_dc_copy(const Copy* cp, int n_cp) {
 // --------------------------------------------------------------------------
 // 5. back-transformation: U <- H_0 H_1 .. H_{n-3} U, columns in parallel
 // --------------------------------------------------------------------------
-// Shared memory of k_backtransform for matrices up to n: the CTA's column
-// slice of U (n x BT_COLS), the current reflector (n) and the dot partials.
-inline size_t bt_smem_bytes(int n) {
-    return sizeof(double) * ((size_t)n * BT_COLS + (size_t)n + 16 * (BT_COLS + 1));
+// Shared memory of k_backtransform for a strip of W columns of an n x n U:
+// the strip (n x W), two reflector buffers (2n), the dot partials (8 x W) and
+// the reflector coefficients (W).
+inline size_t bt_smem_bytes(int n, int W) {
+    return sizeof(double) * ((size_t)n * W + 2 * (size_t)n + 9 * (size_t)W);
+}
+// the most any job can ask for: 16 columns of the largest factor, or 32
+// columns of a factor just below the width threshold
+inline size_t bt_smem_max() {
+    return std::max(bt_smem_bytes(KFAC_MAX_WIDTH_PLUS_ONE, 16), bt_smem_bytes(STRIP_NARROW_FROM - 1, 32));
 }
 
-// U <- H_0 H_1 .. H_{n-3} U.  Each CTA holds BT_COLS columns of U in shared
-// memory for the whole sequence of reflectors, so the FP64 FMAs (the bound on
-// this part) read operands from shared memory; the reflectors are read once
-// per CTA from L2.
-__global__ void __launch_bounds__(256) k_backtransform(Prob* pr, int* fail) {
-    extern __shared__ double bt_sm[];
-    const Prob p = pr[blockIdx.y];
+// U <- H_0 H_1 .. H_{n-3} U on a strip of W columns held in shared memory.
+// Per reflector: the column dots over 256 / W row groups, folded to one
+// partial per warp, summed by warp 0 only (FP64 adds are the scarce
+// resource), then the rank-1 update.  The next reflector is loaded into
+// registers while the current one is applied (two buffers).
+template <int W>
+__device__ void bt_strip(const Prob& p, int c0, double* sm) {
+    constexpr int RG = 256 / W;                  // row groups
     const int n = p.n;
-    if (fail[blockIdx.y]) return;
-    const int c0 = blockIdx.x * BT_COLS;
-    if (c0 >= n) return;
-    double* Us = bt_sm;                          // n x BT_COLS
-    double* v = Us + (size_t)n * BT_COLS;        // n
-    double (*part)[BT_COLS + 1] = reinterpret_cast<double (*)[BT_COLS + 1]>(v + n);
+    double* Us = sm;                             // n x W
+    double* vb = Us + (size_t)n * W;             // two reflectors of n
+    double* part = vb + 2 * (size_t)n;           // 8 x W
+    double* tot = part + 8 * W;                  // W
     double* U = p.final_buf ? p.Qb : p.Qa;
-    const int cl = threadIdx.x % BT_COLS, rg = threadIdx.x / BT_COLS;   // 16 row groups
+    const int cl = threadIdx.x % W, rg = threadIdx.x / W;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int c = c0 + cl;
-    for (int i = rg; i < n; i += 16) Us[i * BT_COLS + cl] = (c < n) ? U[(long long)i * n + c] : 0.0;
-    for (int k = n - 3; k >= 0; k--) {
-        const double tk = p.tau[k];
-        if (tk == 0.0) continue;
-        const int b = k + 1, m = n - b;
-        __syncthreads();                         // previous reflector fully applied
-        for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = __ldcg(p.H + (long long)k * n + b + i);
-        __syncthreads();
-        double dot = 0.0;
-        for (int i = rg; i < m; i += 16) dot = fma(v[i], Us[(b + i) * BT_COLS + cl], dot);
-        part[rg][cl] = dot;
-        __syncthreads();
-        double tot = 0.0;
+    for (int i = rg; i < n; i += RG) Us[i * W + cl] = (c < n) ? U[(long long)i * n + c] : 0.0;
+    // reflector k occupies H[k][k+1 .. n); at most 4 values per thread (n <= 1024)
+    auto fetch = [&](int k, double* r4) {
 #pragma unroll
-        for (int q = 0; q < 16; q++) tot += part[q][cl];
-        tot *= tk;
-        for (int i = rg; i < m; i += 16) Us[(b + i) * BT_COLS + cl] -= tot * v[i];
+        for (int u = 0; u < 4; u++) {
+            const int i = threadIdx.x + 256 * u;
+            r4[u] = (k >= 0 && i < n - k - 1) ? __ldcg(p.H + (long long)k * n + k + 1 + i) : 0.0;
+        }
+    };
+    double nx[4];
+    fetch(n - 3, nx);
+    for (int k = n - 3; k >= 0; k--) {
+        const int b = k + 1, m = n - b;
+        double* v = vb + (k & 1) * n;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int i = threadIdx.x + 256 * u;
+            if (i < m) v[i] = nx[u];
+        }
+        fetch(k - 1, nx);
+        const double tk = p.tau[k];
+        __syncthreads();
+        if (tk == 0.0) continue;                  // uniform
+        double dot = 0.0;
+        for (int i = rg; i < m; i += RG) dot = fma(v[i], Us[(b + i) * W + cl], dot);
+        if (W == 16) dot += __shfl_xor_sync(0xffffffffu, dot, 16);
+        if (lane < W) part[warp * W + lane] = dot;
+        __syncthreads();
+        if (warp == 0 && lane < W) {
+            double t = 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; q++) t += part[q * W + lane];
+            tot[lane] = t * tk;
+        }
+        __syncthreads();
+        const double tt = tot[cl];
+        for (int i = rg; i < m; i += RG) Us[(b + i) * W + cl] -= tt * v[i];
     }
     __syncthreads();
     if (c < n)
-        for (int i = rg; i < n; i += 16) U[(long long)i * n + c] = Us[i * BT_COLS + cl];
+        for (int i = rg; i < n; i += RG) U[(long long)i * n + c] = Us[i * W + cl];
+}
+
+// One CTA per back-transformation job (problem, first column, strip width):
+// the widths make the jobs' work about equal, the list is sorted largest first.
+__global__ void __launch_bounds__(256) k_backtransform(Prob* pr, const TrsmJob* jobs, int* fail) {
+    extern __shared__ double bt_sm[];
+    const TrsmJob jb = jobs[blockIdx.x];
+    const Prob p = pr[jb.prob];
+    if (fail[jb.prob] || jb.c0 >= p.n) return;
+    if (jb.cb == 16) bt_strip<16>(p, jb.c0, bt_sm);
+    else bt_strip<32>(p, jb.c0, bt_sm);
 }
 
 __global__ void k_write_w(Prob* pr, int* fail, int* status) {
@@ -1574,7 +1614,7 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
         std::vector<TrsmJob> jobs;
         for (int i = 0; i < es->np; i++) {
             const int n = es->host[i].n;
-            const int cb = n >= 640 ? 16 : 32;
+            const int cb = n >= STRIP_NARROW_FROM ? 16 : 32;
             for (int c0 = 0; c0 < n; c0 += cb) jobs.push_back(TrsmJob{i, c0, cb});
         }
         std::stable_sort(jobs.begin(), jobs.end(), [&](const TrsmJob& x, const TrsmJob& y) {
@@ -1583,6 +1623,8 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
             return wx > wy;
         });
         es->n_trsm_jobs = (int)jobs.size();
+        es->bt_smem = 0;
+        for (const TrsmJob& j : jobs) es->bt_smem = std::max(es->bt_smem, bt_smem_bytes(es->host[j.prob].n, j.cb));
         if (cudaMalloc(&es->trsm_jobs, sizeof(TrsmJob) * jobs.size()) != cudaSuccess) return KFAC_OOM;
         cudaMemcpy(es->trsm_jobs, jobs.data(), sizeof(TrsmJob) * jobs.size(), cudaMemcpyHostToDevice);
     }
@@ -1710,9 +1752,8 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
     // largest factor any handle can have (h_l + 1 <= 1024), so that handles of
     // different sizes can be created in any order.
     static_assert(KFAC_MAX_WIDTH_PLUS_ONE == 1024, "factor size bound");
-    if (bt_smem_bytes(es->nmax) > bt_smem_bytes(KFAC_MAX_WIDTH_PLUS_ONE)) return KFAC_BAD_ARG;
-    cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)bt_smem_bytes(KFAC_MAX_WIDTH_PLUS_ONE));
+    if (es->bt_smem > bt_smem_max()) return KFAC_BAD_ARG;
+    cudaFuncSetAttribute(k_backtransform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem_max());
     return cudaGetLastError() == cudaSuccess ? KFAC_OK : KFAC_CUDA_ERROR;
 }
 
@@ -1855,7 +1896,7 @@ kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
         }
     }
     // 5. back-transformation, 6. V = L^{-T} U
-    k_backtransform<<<dim3((nmax + BT_COLS - 1) / BT_COLS, np), 256, bt_smem_bytes(nmax), s>>>(pr, es->fail);
+    k_backtransform<<<es->n_trsm_jobs, 256, es->bt_smem, s>>>(pr, (const TrsmJob*)es->trsm_jobs, es->fail);
     KFAC_LAUNCH_CHECK(h);
     k_trsm<<<es->n_trsm_jobs, 256, smem_trsm, s>>>(pr, (const TrsmJob*)es->trsm_jobs, 2, es->fail);
     KFAC_LAUNCH_CHECK(h);
