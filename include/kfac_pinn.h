@@ -178,6 +178,18 @@ kfac_status_t kfac_pinn_forward_laplacian_backward(kfac_handle_t h, void* stream
  * not grow with N.  Default: disabled. */
 kfac_status_t kfac_pinn_set_store_forward(kfac_handle_t h, int enable);
 
+/* Graph mode for kfac_pinn_step and kfac_pinn_step_host (no counterpart in the
+ * paper: a runtime option).  When enabled, a step copies its batch into the
+ * handle's staging buffers (device to device; step_host copies there from the
+ * host anyway) and runs as a CUDA graph: the first step after enabling runs
+ * eagerly, the second is captured, later steps with the same theta and loss
+ * pointers and point counts replay it (a change re-captures).  The results
+ * are bit-identical to eager steps.  The graph runs on a stream of its own,
+ * ordered after the work queued on `stream` and before what follows it.
+ * Device timers (kfac_pinn_timing_enable) make steps eager.  Default:
+ * disabled.  Errors: KFAC_BAD_ARG for a NULL handle. */
+kfac_status_t kfac_pinn_set_graph(kfac_handle_t h, int enable);
+
 /* Curvature and gradient of one batch (App. B, Algorithm 1, steps 1, 2 and
  * 4): forward Laplacian on the interior points and plain forward pass on the
  * boundary points, residuals and loss (Eq. 1), one backward pass each for

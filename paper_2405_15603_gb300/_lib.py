@@ -20,6 +20,7 @@ EXPORTS = [
     "kfac_pinn_get_update_coefficients", "kfac_pinn_batch_create", "kfac_pinn_batch_destroy",
     "kfac_pinn_batch_step", "kfac_pinn_last_cuda_error", "kfac_pinn_last_cuda_error_string",
     "kfac_pinn_set_store_forward",
+    "kfac_pinn_set_graph",
 ]
 
 KERNEL_CLASSES = {0: "layer_gemm", 1: "adjoint_gemm", 2: "gram", 3: "elementwise", 4: "eig", 5: "precond"}
@@ -86,6 +87,7 @@ def load() -> C.CDLL:
         "kfac_pinn_get_update_coefficients": (st, [H, P, P]),
         "kfac_pinn_last_cuda_error": (I, []),
         "kfac_pinn_set_store_forward": (st, [H, I]),
+        "kfac_pinn_set_graph": (st, [H, I]),
         "kfac_pinn_last_cuda_error_string": (C.c_char_p, []),
         "kfac_pinn_batch_create": (st, [P, I, I, C.POINTER(C.c_void_p)]),
         "kfac_pinn_batch_destroy": (st, [P]),

@@ -138,6 +138,12 @@ class KfacPinn:
         """Reverse mode reuses the last forward pass's activations (same theta, X) instead of recomputing."""
         _check("kfac_pinn_set_store_forward", self.lib.kfac_pinn_set_store_forward(self.h, int(enable)))
 
+    def set_graph(self, enable: bool = True):
+        """Run step / step_host as a captured CUDA graph (kfac_pinn_set_graph):
+        the batch is staged into the handle's buffers, the second step is
+        captured and later ones replay it; results are bit-identical."""
+        _check("kfac_pinn_set_graph", self.lib.kfac_pinn_set_graph(self.h, int(enable)))
+
     def factors(self, theta, X_int, f, X_bdy, g) -> torch.Tensor:
         X_int, f, X_bdy, g = (_dev(a, self.device) for a in (X_int, f, X_bdy, g))
         _check("kfac_pinn_factors", self.lib.kfac_pinn_factors(

@@ -473,6 +473,7 @@ kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out) {
 kfac_status_t kfac_pinn_destroy(kfac_handle_t h) {
     if (!h) return KFAC_BAD_ARG;
     cudaDeviceSynchronize();
+    handle_graph_free(h);
     free_handle(h);
     return KFAC_OK;
 }
@@ -559,6 +560,13 @@ kfac_status_t kfac_pinn_set_store_forward(kfac_handle_t h, int enable) {
     return KFAC_OK;
 }
 
+kfac_status_t kfac_pinn_set_graph(kfac_handle_t h, int enable) {
+    if (!h) return KFAC_BAD_ARG;
+    h->graph_mode = enable ? 1 : 0;
+    if (!enable) handle_graph_free(h);
+    return KFAC_OK;
+}
+
 kfac_status_t kfac_pinn_factors(kfac_handle_t h, void* stream, const double* theta,
                                 const double* X_int, int N_int, const double* f,
                                 const double* X_bdy, int N_bdy, const double* g, double* loss) {
@@ -602,6 +610,21 @@ kfac_status_t kfac_pinn_step(kfac_handle_t h, void* stream, double* theta,
     if (st) return st;
     if (!theta) return KFAC_BAD_ARG;
     cudaStream_t s = S_(stream);
+    if (h->graph_mode && !h->in_graph) {
+        // stage the batch where the graph expects it (unless it is there already)
+        const int d = h->dims[0];
+        double* xi = h->stage;
+        double* fi = xi + (size_t)N_int * d;
+        double* xb = fi + N_int;
+        double* gb = xb + (size_t)N_bdy * d;
+        if (X_int != xi) {
+            KFAC_CUDA_TRY(cudaMemcpyAsync(xi, X_int, (size_t)N_int * d * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            KFAC_CUDA_TRY(cudaMemcpyAsync(fi, f, (size_t)N_int * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            KFAC_CUDA_TRY(cudaMemcpyAsync(xb, X_bdy, (size_t)N_bdy * d * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            KFAC_CUDA_TRY(cudaMemcpyAsync(gb, g, (size_t)N_bdy * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+        return handle_graph_step(h, s, theta, xi, N_int, fi, xb, N_bdy, gb, loss);
+    }
     if ((st = run_factors(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g, loss))) return st;
     if ((st = kfac_pinn_invert(h, stream))) return st;
     if ((st = kfac_pinn_precondition(h, stream, nullptr, nullptr))) return st;

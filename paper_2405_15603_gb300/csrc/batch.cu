@@ -172,3 +172,27 @@ kfac_status_t kfac_pinn_batch_step(kfac_batch_t b, void* stream, double* const* 
 }
 
 }  // extern "C"
+
+// Graph mode of a single handle: the handle owns a batch of itself, created at
+// the first graph step.  The nested kfac_pinn_step calls of the batch run
+// eagerly (in_graph), so the step is captured once and then replayed.
+kfac_status_t handle_graph_step(kfac_pinn_handle* h, cudaStream_t s, double* theta, const double* X_int, int N_int,
+                                const double* f, const double* X_bdy, int N_bdy, const double* g, double* loss) {
+    if (!h->gbatch) {
+        kfac_batch_t b = nullptr;
+        kfac_handle_t hh = h;
+        kfac_status_t st = kfac_pinn_batch_create(&hh, 1, 1, &b);
+        if (st) return st;
+        h->gbatch = b;
+    }
+    h->in_graph = 1;
+    kfac_status_t st = kfac_pinn_batch_step(h->gbatch, s, &theta, &X_int, &N_int, &f, &X_bdy, &N_bdy, &g,
+                                            &loss, 1);
+    h->in_graph = 0;
+    return st;
+}
+
+void handle_graph_free(kfac_pinn_handle* h) {
+    if (h->gbatch) kfac_pinn_batch_destroy(h->gbatch);
+    h->gbatch = nullptr;
+}

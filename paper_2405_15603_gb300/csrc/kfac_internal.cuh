@@ -98,6 +98,11 @@ struct kfac_pinn_handle {
     // reverse mode with stored activations: the interior pass buffers hold the
     // forward Laplacian of (fwd_theta, fwd_X, fwd_N) while fwd_valid is set
     int store_forward;
+    // graph mode (kfac_pinn_set_graph): a batch of this handle alone; in_graph
+    // marks the eager step run inside it (capture or first call)
+    int graph_mode;
+    int in_graph;
+    struct kfac_pinn_batch* gbatch;
     int fwd_valid;
     const double* fwd_theta;
     const double* fwd_X;
@@ -135,6 +140,11 @@ void kfac_record_cuda_error(cudaError_t e);
             return KFAC_CUDA_ERROR;                           \
         }                                                     \
     } while (0)
+
+// Graph mode (batch.cu): one step of h through its own single-handle batch.
+kfac_status_t handle_graph_step(kfac_pinn_handle* h, cudaStream_t s, double* theta, const double* X_int, int N_int,
+                                const double* f, const double* X_bdy, int N_bdy, const double* g, double* loss);
+void handle_graph_free(kfac_pinn_handle* h);
 
 // Device timers: bracket a launch with events when timing is enabled.
 void timer_begin(kfac_pinn_handle* h, int cls, cudaStream_t s);

@@ -72,3 +72,34 @@ def test_batch_rejects_bad_arguments():
     with pytest.raises(KfacError):
         batch.step(th, too_many, small, xb, gb)
     batch.close()
+
+
+@pytest.mark.parametrize("precision,update", [("mixed_bf16", "line_search"), ("fp64", "kfac_star"),
+                                              ("fp64", "fixed")])
+def test_single_handle_graph_mode_is_bit_identical(precision, update):
+    # kfac_pinn_set_graph: eager first step, captured second, replays after;
+    # batches in fresh device tensors every step (staged by the library) and
+    # through step_host, against plain eager steps
+    from paper_2405_15603_gb300.api import KfacPinn
+    prob = si.PROBLEMS["poisson5d_cos"]
+    widths = (48, 40, 1)
+    kw = dict(device=DEV, precision=precision, update=update, max_n_int=150, max_n_bdy=50, lam=1e-3,
+              lr=0.1, momentum=0.3, beta=0.9, init_identity=True)
+    eager, graph = KfacPinn(prob.d, widths, **kw), KfacPinn(prob.d, widths, **kw)
+    graph.set_graph(True)
+    th0 = si.xavier_theta(prob.d, widths, 4)
+    te, tg = torch.tensor(th0, device=DEV), torch.tensor(th0, device=DEV)
+    for step in range(5):
+        Xi, f, Xb, g = si.make_batch(prob, 150 - 10 * (step == 4), 50, seed=2, step=step)
+        le = eager.step(te, Xi, f, Xb, g).clone()
+        n0 = graph.launch_count()
+        if step == 3:
+            lh = graph.step_host(tg, Xi, f, Xb, g)
+            lg = torch.tensor(lh, device=DEV)
+        else:
+            lg = graph.step(tg, *(torch.tensor(a, device=DEV) for a in (Xi, f, Xb, g))).clone()
+        torch.cuda.synchronize()
+        assert graph.launch_count() > n0
+        assert torch.equal(te, tg), step
+        assert torch.equal(le, lg), step
+    assert eager.sync_status() == "KFAC_OK" and graph.sync_status() == "KFAC_OK"
