@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, 
 constexpr int TRC_THREADS = 512;
 constexpr int TRC_CL = 16;    // CTAs per cluster (a non-portable cluster size)
 constexpr int TRC_RED = TRC_THREADS + 8;   // reduction scratch: one slot per thread + scalars
-constexpr int TRC_TK = TRC_THREADS, TRC_SCALE = TRC_THREADS + 1, TRC_KP = TRC_THREADS + 2, TRC_K = TRC_THREADS + 3;
+constexpr int TRC_TK = TRC_THREADS, TRC_SCALE = TRC_THREADS + 1, TRC_K = TRC_THREADS + 3;
 
 // Warp 0's sum of the per-thread partials sh[0..TRC_THREADS) (written and
 // synchronised by the caller); every lane of warp 0 gets the same total.  The
@@ -1055,7 +1055,8 @@ __global__ void __launch_bounds__(256) k_dc_prepare(Prob* pr, const Merge* merge
     dmax = block_reduce_max(dmax, sh);
     const double zn = sqrt(zn2);
     const double rh = fabs(rho) * zn2;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) zs[i] /= zn;
+    const double rzn = 1.0 / zn;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) zs[i] *= rzn;
     __syncthreads();
     if (threadIdx.x == 0) {
         const double tol = 8.0 * DEPS * fmax(dmax, rh);
@@ -1066,10 +1067,14 @@ __global__ void __launch_bounds__(256) k_dc_prepare(Prob* pr, const Merge* merge
             if (rh * fabs(zs[i]) <= tol) { defl[i] = 1; continue; }
             if (last >= 0) {
                 const int j = last;
-                const double rr = hypot(zs[j], zs[i]);
-                const double c = zs[i] / rr, s = -zs[j] / rr;
-                const double t = c * s * (Ds[i] - Ds[j]);
-                if (fabs(t) <= tol) {
+                // |c s (D_i - D_j)| <= tol with c = z_i / r, s = -z_j / r,
+                // r^2 = z_i^2 + z_j^2, tested without a division (this loop is
+                // serial, and FP64 division is a long sequence on this part);
+                // c and s are formed only when the rotation is applied
+                const double r2 = fma(zs[j], zs[j], zs[i] * zs[i]);
+                if (fabs(zs[i] * zs[j] * (Ds[i] - Ds[j])) <= tol * r2) {
+                    const double rr = hypot(zs[j], zs[i]);
+                    const double c = zs[i] / rr, s = -zs[j] / rr;
                     const double dj = Ds[j], di = Ds[i];
                     Ds[j] = c * c * dj + s * s * di;
                     Ds[i] = s * s * dj + c * c * di;
@@ -1229,11 +1234,22 @@ __global__ void k_dc_zhat(Prob* pr, const Merge* merges, int n_merges, int* fail
     const int* org = p.org + a;
     const double di = dK[i];
     double prod = -((di - dK[org[i]]) - tauR[i]) / rh;   // (lambda_i - d_i) / rh
+    // the factors are O(1) ratios of nearby quantities (interlacing); four
+    // numerators and denominators stay far inside the FP64 range, so one
+    // division serves four factors
+    double num = 1.0, den = 1.0;
+    int cnt = 0;
     for (int q = 0; q < k; q++) {
         if (q == i) continue;
-        const double lam_minus_di = -((di - dK[org[q]]) - tauR[q]);
-        prod *= lam_minus_di / (dK[q] - di);
+        num *= -((di - dK[org[q]]) - tauR[q]);
+        den *= dK[q] - di;
+        if (++cnt == 4) {
+            prod *= num / den;
+            num = den = 1.0;
+            cnt = 0;
+        }
     }
+    prod *= num / den;
     const double z = sqrt(fmax(prod, 0.0));
     p.zh[a + i] = (p.zK[a + i] < 0.0) ? -z : z;
 }
@@ -1265,12 +1281,22 @@ __global__ void __launch_bounds__(256) k_dc_order(Prob* pr, const Merge* merges,
         val[t] = v;
     }
     __syncthreads();
+    // ranks by order-preserving 64-bit integer keys of the values (integer
+    // compares run on the ALUs, not the scarce FP64 pipe); -0 and +0 tie
+    long long* key = reinterpret_cast<long long*>(p.pbuf2 + a);   // scratch of m doubles, free during the merges
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const double v = val[t] == 0.0 ? 0.0 : val[t];
+        const long long b = __double_as_longlong(v);
+        key[t] = b >= 0 ? b : (long long)(0x8000000000000000ull ^ ~(unsigned long long)b);
+    }
+    __syncthreads();
     for (int t = threadIdx.x; t < m; t += blockDim.x) {
         const double v = val[t];
+        const long long kv = key[t];
         int r = 0;
         for (int q = 0; q < m; q++) {
-            double u = val[q];
-            if (u < v || (u == v && q < t)) r++;
+            const long long u = key[q];
+            r += (u < kv || (u == kv && q < t)) ? 1 : 0;
         }
         const int c = flip ? m - 1 - r : r;
         p.col[a + t] = c;
@@ -1302,43 +1328,51 @@ __global__ void __launch_bounds__(256) k_dc_fillU(Prob* pr, const Merge* merges,
         }
         const int o = p.org[a + t];
         const double dO = p.dK[a + o], tt_ = p.tauR[a + t];
+        for (int r = lane; r < m; r += 32) R[(long long)(a + r) * n + a + c] = 0.0;
+        __syncwarp();
+        // unnormalised entries first (one division each), then the scaling
         double ss = 0.0;
         for (int q = lane; q < k; q += 32) {
-            double u = p.zh[a + q] / ((p.dK[a + q] - dO) - tt_);
+            const double u = p.zh[a + q] / ((p.dK[a + q] - dO) - tt_);
+            R[(long long)(a + p.Kidx[a + q]) * n + a + c] = u;
             ss = fma(u, u, ss);
         }
         for (int o2 = 16; o2 > 0; o2 >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o2);
         const double inv = 1.0 / sqrt(ss);
-        for (int r = lane; r < m; r += 32) R[(long long)(a + r) * n + a + c] = 0.0;
-        __syncwarp();
-        for (int q = lane; q < k; q += 32) {
-            double u = p.zh[a + q] / ((p.dK[a + q] - dO) - tt_);
-            R[(long long)(a + p.Kidx[a + q]) * n + a + c] = u * inv;
-        }
+        for (int q = lane; q < k; q += 32) R[(long long)(a + p.Kidx[a + q]) * n + a + c] *= inv;
     }
 }
 
 // Undo the deflation rotations (reverse order, on rows of R) and scatter rows
 // to the block's original index order: R2[perm[pos]][c] = R[pos][c].
+// Deflation rotations on the columns of R, then R2[perm[pos]] = R[pos]; the
+// columns are independent, so each CTA takes a chunk of 64 of them.
+constexpr int RS_COLS = 64;
 __global__ void __launch_bounds__(256) k_dc_rotate_scatter(Prob* pr, const Merge* merges, int* fail) {
-    const Merge mg = merges[blockIdx.x];
+    const Merge mg = merges[blockIdx.y];
     const Prob p = pr[mg.prob];
     if (fail[mg.prob]) return;
     const int n = p.n, a = mg.a, m = mg.s1 + mg.s2;
+    const int c0 = blockIdx.x * RS_COLS;
+    if (c0 >= m) return;
+    const int nc = min(RS_COLS, m - c0);
     const int nrot = p.mnrot[a];
     double* R = p.R;
-    for (int t = nrot - 1; t >= 0; t--) {
-        const int j = p.rj[a + t], i = p.ri[a + t];
-        const double c = p.rc[a + t], s = p.rs[a + t];
-        for (int col = threadIdx.x; col < m; col += blockDim.x) {
-            double uj = R[(long long)(a + j) * n + a + col], ui = R[(long long)(a + i) * n + a + col];
+    if (threadIdx.x < nc) {
+        const int col = c0 + threadIdx.x;
+        for (int t = nrot - 1; t >= 0; t--) {
+            const int j = p.rj[a + t], i = p.ri[a + t];
+            const double c = p.rc[a + t], s = p.rs[a + t];
+            const double uj = R[(long long)(a + j) * n + a + col], ui = R[(long long)(a + i) * n + a + col];
             R[(long long)(a + j) * n + a + col] = c * uj - s * ui;
             R[(long long)(a + i) * n + a + col] = s * uj + c * ui;
         }
-        __syncthreads();
     }
-    for (long long t = threadIdx.x; t < (long long)m * m; t += blockDim.x) {
-        const int pos = (int)(t / m), col = (int)(t % m);
+    __syncthreads();
+    for (int t = threadIdx.x; t < m * RS_COLS; t += blockDim.x) {
+        const int pos = t / RS_COLS, cc = t % RS_COLS;
+        if (cc >= nc) continue;
+        const int col = c0 + cc;
         p.R2[(long long)(a + p.perm[a + pos]) * n + a + col] = R[(long long)(a + pos) * n + a + col];
     }
 }
@@ -1884,7 +1918,8 @@ kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
             KFAC_LAUNCH_CHECK(h);
             k_dc_fillU<<<dim3((lv.max_m + 31) / 32, lv.n_merges), 256, 0, s>>>(pr, lv.merges, es->fail);
             KFAC_LAUNCH_CHECK(h);
-            k_dc_rotate_scatter<<<lv.n_merges, 256, 0, s>>>(pr, lv.merges, es->fail);
+            k_dc_rotate_scatter<<<dim3((lv.max_m + RS_COLS - 1) / RS_COLS, lv.n_merges), 256, 0, s>>>(
+                pr, lv.merges, es->fail);
             KFAC_LAUNCH_CHECK(h);
             k_dc_gemm<<<lv.n_tiles, 256, 0, s>>>(lv.gemms, lv.n_gemms, es->fail);
             KFAC_LAUNCH_CHECK(h);
