@@ -11,10 +11,12 @@
 //      too large for it, one cooperative kernel where each problem owns a
 //      group of CTAs that sync through bounded global barriers)
 //   4. divide and conquer on the tridiagonal T  (Cuppen's rank-one tearing,
-//      deflation, secular equation solved by bisection, eigenvectors via the
+//      deflation, secular equation by a safeguarded rational iteration, eigenvectors via the
 //      Gu-Eisenstat recomputed z, block GEMMs per merge level)
 //   5. back-transformation by the Householder reflectors (column-parallel)
 //   6. V = L^{-T} U                              (TRSM)
+// The factor pairs form two groups (the largest, the rest) whose kernel
+// sequences run on two streams at once.
 // Errors (a P that is not positive definite, a barrier that gave up) are
 // latched in the handle's status word; the problem's V and w are then zero.
 #include <stdlib.h>
@@ -115,7 +117,18 @@ struct EigState {
     int* clu_prob;              // problem of each cluster, largest first
 };
 
-EigState* ES(kfac_pinn_handle* h) { return (EigState*)h->eig; }
+// The factor pairs in up to two groups run on two streams: the largest
+// problems (whose latency-bound stages, such as the cluster
+// tridiagonalisation, hold only part of the GPU) and the rest, which fills the
+// idle SMs meanwhile.
+struct EigAll {
+    EigState* g[2];
+    int ng;
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+};
+
+EigAll* EA(kfac_pinn_handle* h) { return (EigAll*)h->eig; }
 
 // --------------------------------------------------------------------------
 // Small helpers
@@ -1547,17 +1560,16 @@ int ceil_log2(int n) {
 
 }  // namespace
 
-kfac_status_t eig_alloc(kfac_pinn_handle* h) {
-    EigState* es = new EigState();
-    h->eig = es;
+static int pair_n(const kfac_pinn_handle* h, int l, int which) { return which == 0 ? h->dims[l - 1] + 1 : h->dims[l]; }
+
+// One group of factor pairs (layer, 0: A / 1: B) solved by one sequence of
+// batched kernels.
+static kfac_status_t group_alloc(kfac_pinn_handle* h, EigState* es, const std::vector<std::pair<int, int>>& pairs) {
     es->np = 0;
     es->nmax = 0;
     size_t dtot = 0, itot = 0;
     std::vector<int> ns;
-    for (int l = 1; l <= h->cfg.L; l++) {
-        ns.push_back(h->dims[l - 1] + 1);
-        ns.push_back(h->dims[l]);
-    }
+    for (const auto& pw : pairs) ns.push_back(pair_n(h, pw.first, pw.second));
     for (int n : ns) {
         dtot += 7 * (size_t)n * n + (size_t)n * NB + 20 * (size_t)n;
         itot += 12 * (size_t)n;
@@ -1568,8 +1580,9 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
     if ((st = dal(&es->iws, itot))) return st;
     double* dp = es->ws;
     int* ip = es->iws;
-    for (int l = 1; l <= h->cfg.L; l++) {
-        for (int which = 0; which < 2; which++) {
+    for (const auto& pw : pairs) {
+        {
+            const int l = pw.first, which = pw.second;
             Prob& p = es->host[es->np++];
             memset(&p, 0, sizeof(p));
             const int n = which == 0 ? h->dims[l - 1] + 1 : h->dims[l];
@@ -1791,8 +1804,7 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
     return cudaGetLastError() == cudaSuccess ? KFAC_OK : KFAC_CUDA_ERROR;
 }
 
-void eig_free(kfac_pinn_handle* h) {
-    EigState* es = ES(h);
+static void group_free(EigState* es) {
     if (!es) return;
     cudaFree(es->ws);
     cudaFree(es->iws);
@@ -1811,11 +1823,9 @@ void eig_free(kfac_pinn_handle* h) {
         cudaFree(lv.copies);
     }
     delete es;
-    h->eig = nullptr;
 }
 
-kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
-    EigState* es = ES(h);
+static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s) {
     const int np = es->np;
     Prob* pr = es->dev;
     const double eps = h->cfg.damping_sqrt ? sqrt(h->cfg.lambda) : h->cfg.lambda;
@@ -1938,4 +1948,64 @@ kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
     k_write_w<<<np, 256, 0, s>>>(pr, es->fail, h->status);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
+}
+
+// Factor pairs of size at least 3/4 of the largest form the first group, the
+// rest the second (run on a stream of the handle's own, forked from and joined
+// back into the caller's stream; both are captured when the step is).
+kfac_status_t eig_alloc(kfac_pinn_handle* h) {
+    EigAll* ea = new EigAll();
+    memset(ea, 0, sizeof(*ea));
+    h->eig = ea;
+    int nmax = 0;
+    for (int l = 1; l <= h->cfg.L; l++)
+        for (int w = 0; w < 2; w++) nmax = std::max(nmax, pair_n(h, l, w));
+    std::vector<std::pair<int, int>> big, rest;
+    for (int l = 1; l <= h->cfg.L; l++)
+        for (int w = 0; w < 2; w++) (4 * pair_n(h, l, w) >= 3 * nmax ? big : rest).push_back({l, w});
+    kfac_status_t st;
+    ea->g[0] = new EigState();
+    ea->ng = 1;
+    if ((st = group_alloc(h, ea->g[0], big))) return st;
+    if (!rest.empty()) {
+        ea->g[1] = new EigState();
+        ea->ng = 2;
+        if ((st = group_alloc(h, ea->g[1], rest))) return st;
+        if (cudaStreamCreateWithFlags(&ea->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ea->fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ea->join, cudaEventDisableTiming) != cudaSuccess)
+            return KFAC_CUDA_ERROR;
+    }
+    return KFAC_OK;
+}
+
+void eig_free(kfac_pinn_handle* h) {
+    EigAll* ea = EA(h);
+    if (!ea) return;
+    if (ea->side) cudaStreamSynchronize(ea->side);
+    for (int i = 0; i < 2; i++) group_free(ea->g[i]);
+    if (ea->side) cudaStreamDestroy(ea->side);
+    if (ea->fork) cudaEventDestroy(ea->fork);
+    if (ea->join) cudaEventDestroy(ea->join);
+    delete ea;
+    h->eig = nullptr;
+}
+
+kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
+    EigAll* ea = EA(h);
+    if (ea->ng == 1) return group_run(h, ea->g[0], s);
+    if (ea->g[0]->trc_cl == 0 || ea->g[1]->trc_cl == 0) {
+        // a cooperative tridiagonalisation needs all its CTAs resident at
+        // once: nothing runs beside it
+        kfac_status_t st = group_run(h, ea->g[1], s);
+        return st ? st : group_run(h, ea->g[0], s);
+    }
+    KFAC_CUDA_TRY(cudaEventRecord(ea->fork, s));
+    KFAC_CUDA_TRY(cudaStreamWaitEvent(ea->side, ea->fork, 0));
+    kfac_status_t st = group_run(h, ea->g[1], ea->side);
+    // the join is recorded even after an error so that s never runs ahead of side
+    KFAC_CUDA_TRY(cudaEventRecord(ea->join, ea->side));
+    if (st == KFAC_OK) st = group_run(h, ea->g[0], s);
+    KFAC_CUDA_TRY(cudaStreamWaitEvent(s, ea->join, 0));
+    return st;
 }
