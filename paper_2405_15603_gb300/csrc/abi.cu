@@ -450,6 +450,9 @@ kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out) {
         TRY(dalloc(&h->wb[l - 1], nb));
         if (2 * na * nb > tmp) tmp = 2 * na * nb;
     }
+    // the mixed path's batched preconditioning holds every layer's two
+    // scratch matrices at once
+    if (cfg->precision == KFAC_MIXED_BF16) tmp = std::max(tmp, 2 * (size_t)h->D);
     h->tmp_elems = tmp;
     TRY(dalloc(&h->tmp, tmp));
     TRY(dalloc(&h->loss, 3));

@@ -195,10 +195,156 @@ __global__ void k_ks_apply(double* theta, const double* __restrict__ Dl, double*
     theta[i] += dlt;
 }
 
+// Batched FP32 GEMM of the mixed path's preconditioning: one launch runs the
+// same stage for every layer (C = alpha op(A) op(B), operands read as FP64
+// through strides and rounded to FP32, FP32 accumulation, FP64 result;
+// optionally divided by 1 + dr[p] dc[q]).  64 x 64 tiles, 16-deep k slices,
+// 256 threads with a 4 x 4 block of consecutive rows and columns each (vector
+// shared-memory loads); the tiles of all layers form one grid.
+struct PGemm {
+    const double* A;
+    long long a_sp, a_sk;
+    const double* B;
+    long long b_sk, b_sq;
+    double* C;
+    long long c_sp, c_sq;
+    const double* dr;
+    const double* dc;
+    int P, Q, K, tiles_q, tile0;
+    double alpha;
+};
+struct PBatch {
+    PGemm g[KFAC_MAX_LAYERS];
+    int n;
+};
+
+__global__ void __launch_bounds__(256) k_pgemm_f32(const __grid_constant__ PBatch b) {
+    __shared__ __align__(16) float As[16][68];
+    __shared__ __align__(16) float Bs[16][68];
+    int gi = 0;
+    while (gi + 1 < b.n && (int)blockIdx.x >= b.g[gi + 1].tile0) gi++;
+    const PGemm& g = b.g[gi];
+    const int t = (int)blockIdx.x - g.tile0;
+    const int p0 = (t / g.tiles_q) * 64, q0 = (t % g.tiles_q) * 64;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const bool akf = g.a_sk == 1, bqf = g.b_sq == 1;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < g.K; k0 += 16) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int e = tid + 256 * i;
+            const int kk = akf ? e % 16 : e / 64, pp = akf ? e / 16 : e % 64;
+            const int pr = p0 + pp, k = k0 + kk;
+            As[kk][pp] = (pr < g.P && k < g.K) ? (float)g.A[(long long)pr * g.a_sp + (long long)k * g.a_sk] : 0.f;
+            const int qq = bqf ? e % 64 : e / 16, kb = bqf ? e / 64 : e % 16;
+            const int q = q0 + qq, kq = k0 + kb;
+            Bs[kb][qq] = (q < g.Q && kq < g.K) ? (float)g.B[(long long)kq * g.b_sk + (long long)q * g.b_sq] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; kk++) {
+            const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+            const float4 b4 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+            const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int pr = p0 + ty * 4 + i;
+        if (pr >= g.P) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int q = q0 + tx * 4 + j;
+            if (q >= g.Q) continue;
+            float v = (float)g.alpha * acc[i][j];
+            if (g.dr) v /= 1.f + (float)(g.dr[pr] * g.dc[q]);
+            g.C[(long long)pr * g.c_sp + (long long)q * g.c_sq] = (double)v;
+        }
+    }
+}
+
+// One stage over all layers: the stage's GEMM of layer l has the shape
+// (P, Q, K) = (nb, na, K_l) and strides from `desc`.
+template <class F>
+kfac_status_t pgemm_stage(kfac_pinn_handle* h, cudaStream_t s, F desc) {
+    PBatch b;
+    memset(&b, 0, sizeof(b));
+    int tiles = 0;
+    for (int l = 1; l <= h->cfg.L; l++) {
+        PGemm g = desc(l);
+        g.tiles_q = (g.Q + 63) / 64;
+        g.tile0 = tiles;
+        tiles += ((g.P + 63) / 64) * g.tiles_q;
+        b.g[b.n++] = g;
+    }
+    k_pgemm_f32<<<tiles, 256, 0, s>>>(b);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
 kfac_status_t precondition_impl(kfac_pinn_handle* h, cudaStream_t s, const double* grad, double* dir) {
-    // The mixed-precision path applies the (FP64) inverse with FP32 products:
-    // its gradient already carries BF16-level errors.
-    const bool f32 = (h->cfg.precision == KFAC_MIXED_BF16);
+    if (h->cfg.precision == KFAC_MIXED_BF16) {
+        // the four products of every layer as four batched launches; the
+        // layers' scratch matrices X1 and Y are laid out one after another
+        auto X1 = [&](int l) { return h->tmp + 2 * (size_t)h->woff[l - 1]; };
+        auto Yb = [&](int l) { return h->tmp + 2 * (size_t)h->woff[l - 1] + (size_t)h->dims[l] * (h->dims[l - 1] + 1); };
+        kfac_status_t st;
+        // X1 = V_B^T G
+        st = pgemm_stage(h, s, [&](int l) {
+            const int na = h->dims[l - 1] + 1, nb = h->dims[l];
+            PGemm g = {};
+            g.A = h->VB[l - 1]; g.a_sp = 1; g.a_sk = nb;
+            g.B = grad + h->woff[l - 1]; g.b_sk = 1; g.b_sq = nb;
+            g.C = X1(l); g.c_sp = na; g.c_sq = 1;
+            g.P = nb; g.Q = na; g.K = nb; g.alpha = 1.0;
+            return g;
+        });
+        if (st) return st;
+        // Y = (X1 V_A) / (1 + b a^T)
+        st = pgemm_stage(h, s, [&](int l) {
+            const int na = h->dims[l - 1] + 1, nb = h->dims[l];
+            PGemm g = {};
+            g.A = X1(l); g.a_sp = na; g.a_sk = 1;
+            g.B = h->VA[l - 1]; g.b_sk = na; g.b_sq = 1;
+            g.C = Yb(l); g.c_sp = na; g.c_sq = 1;
+            g.dr = h->wb[l - 1]; g.dc = h->wa[l - 1];
+            g.P = nb; g.Q = na; g.K = na; g.alpha = 1.0;
+            return g;
+        });
+        if (st) return st;
+        // X1 = V_B Y
+        st = pgemm_stage(h, s, [&](int l) {
+            const int na = h->dims[l - 1] + 1, nb = h->dims[l];
+            PGemm g = {};
+            g.A = h->VB[l - 1]; g.a_sp = nb; g.a_sk = 1;
+            g.B = Yb(l); g.b_sk = na; g.b_sq = 1;
+            g.C = X1(l); g.c_sp = na; g.c_sq = 1;
+            g.P = nb; g.Q = na; g.K = nb; g.alpha = 1.0;
+            return g;
+        });
+        if (st) return st;
+        // Delta = -X1 V_A^T, stored column-stacked like theta
+        return pgemm_stage(h, s, [&](int l) {
+            const int na = h->dims[l - 1] + 1, nb = h->dims[l];
+            PGemm g = {};
+            g.A = X1(l); g.a_sp = na; g.a_sk = 1;
+            g.B = h->VA[l - 1]; g.b_sk = 1; g.b_sq = na;
+            g.C = dir + h->woff[l - 1]; g.c_sp = 1; g.c_sq = nb;
+            g.P = nb; g.Q = na; g.K = na; g.alpha = -1.0;
+            return g;
+        });
+    }
+    // FP64 handles: FP64 products, one GEMM at a time
+    const bool f32 = false;
     for (int l = 1; l <= h->cfg.L; l++) {
         const int na = h->dims[l - 1] + 1, nb = h->dims[l];
         const double* G = grad + h->woff[l - 1];
