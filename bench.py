@@ -631,7 +631,7 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed_bf16", choices=["fp64", "mixed_bf16"])
+    ap.add_argument("--precision", default="mixed_bf16", choices=["fp64", "mixed_bf16", "mixed_split"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e10", action="store_true",

@@ -55,10 +55,17 @@ typedef enum {
 
 typedef enum {
     KFAC_FP64 = 0,         /* every stage in FP64 SIMT arithmetic              */
-    KFAC_MIXED_BF16 = 1    /* tensor-core BF16 (split-BF16 on the value and
+    KFAC_MIXED_BF16 = 1,   /* tensor-core BF16 (split-BF16 on the value and
                               Laplacian columns) with FP32 accumulation for the
                               Taylor pass, adjoint, gradient and Grams; FP64
                               for loss, factors, Cholesky and eigensolver      */
+    KFAC_MIXED_SPLIT = 2   /* the same tensor-core path with split-BF16 (hi +
+                              lo, about 16 significant bits, three products
+                              per contraction) on every Taylor column, every
+                              adjoint and every Gram: per-result errors near
+                              1e-5 against FP64, at about three times the
+                              tensor work.  Expand variant, FIXED and
+                              LINE_SEARCH updates only (create rejects others) */
 } kfac_precision_t;
 
 typedef enum { KFAC_EXPAND = 0, KFAC_REDUCE = 1 } kfac_variant_t;

@@ -30,7 +30,8 @@ bool valid_config(const kfac_config_t* c) {
                 if (fabs(c->op_coef[i * c->d + j] - c->op_coef[j * c->d + i]) > 1e-12 * mx) return false;
     }
     if (c->op == KFAC_OP_HEAT && c->d < 2) return false;
-    if (c->precision != KFAC_FP64 && c->precision != KFAC_MIXED_BF16) return false;
+    if (c->precision != KFAC_FP64 && c->precision != KFAC_MIXED_BF16 && c->precision != KFAC_MIXED_SPLIT) return false;
+    if (c->precision == KFAC_MIXED_SPLIT && (c->variant != KFAC_EXPAND || c->update == KFAC_UPDATE_AUTO)) return false;
     if (c->variant != KFAC_EXPAND && c->variant != KFAC_REDUCE) return false;
     if (!(c->beta >= 0.0 && c->beta < 1.0)) return false;
     if (!(c->lambda > 0.0) || !isfinite(c->lambda)) return false;
@@ -185,7 +186,7 @@ kfac_status_t alloc_pass(kfac_pinn_handle* h, PassBuffers& pb, int N, int S) {
     const int L = h->cfg.L;
     kfac_status_t st;
     int maxw = 0;
-    if (h->cfg.precision == KFAC_MIXED_BF16) {   // the mixed path keeps its own BF16 activations
+    if (is_mixed(h)) {   // the mixed path keeps its own BF16 activations
         return dalloc(&pb.r, (size_t)N);
     }
     for (int l = 1; l <= L; l++) {
@@ -268,7 +269,7 @@ kfac_status_t run_factors(kfac_pinn_handle* h, cudaStream_t s, const double* the
                           const double* X_int, int N_int, const double* f,
                           const double* X_bdy, int N_bdy, const double* g, double* loss) {
     h->fwd_valid = 0;       // the pass buffers are about to be overwritten
-    if (h->cfg.precision == KFAC_MIXED_BF16)
+    if (is_mixed(h))
         return tc_factors(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g, loss);
     kfac_status_t st;
     const int S = h->S;
@@ -452,7 +453,7 @@ kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out) {
     }
     // the mixed path's batched preconditioning holds every layer's two
     // scratch matrices at once
-    if (cfg->precision == KFAC_MIXED_BF16) tmp = std::max(tmp, 2 * (size_t)h->D);
+    if (cfg->precision != KFAC_FP64) tmp = std::max(tmp, 2 * (size_t)h->D);
     h->tmp_elems = tmp;
     TRY(dalloc(&h->tmp, tmp));
     TRY(dalloc(&h->loss, 3));
@@ -463,7 +464,7 @@ kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out) {
     TRY(dalloc(&h->status, 1));
     h->stage_elems = (size_t)cfg->max_n_int * (cfg->d + 1) + (size_t)cfg->max_n_bdy * (cfg->d + 1) + 8;
     TRY(dalloc(&h->stage, h->stage_elems));
-    if (cfg->precision == KFAC_MIXED_BF16) TRY(tc_alloc(h));
+    if (cfg->precision != KFAC_FP64) TRY(tc_alloc(h));
     TRY(eig_alloc(h));
     if (cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) { free_handle(h); return KFAC_CUDA_ERROR; }
     TRY(reset_state(h, 0));
@@ -497,7 +498,7 @@ kfac_status_t kfac_pinn_forward_laplacian(kfac_handle_t h, void* stream, const d
     for (int off = 0; off < N; off += h->cfg.max_n_int) {
         int n = N - off < h->cfg.max_n_int ? N - off : h->cfg.max_n_int;
         kfac_status_t st;
-        if (h->cfg.precision == KFAC_MIXED_BF16) {
+        if (is_mixed(h)) {
             st = tc_forward_laplacian(h, s, theta, X + (long long)off * d, n, u + off,
                                       grad ? grad + (long long)off * d : nullptr, lap ? lap + off : nullptr);
         } else {
@@ -526,7 +527,7 @@ kfac_status_t kfac_pinn_forward_laplacian_backward(kfac_handle_t h, void* stream
         KFAC_CUDA_TRY(cudaMemsetAsync(dtheta, 0, h->D * sizeof(double), s));
         return KFAC_OK;
     }
-    if (h->cfg.precision == KFAC_MIXED_BF16) {
+    if (is_mixed(h)) {
         h->fwd_valid = 0;
         for (int off = 0; off < N; off += h->cfg.max_n_int) {
             int n = N - off < h->cfg.max_n_int ? N - off : h->cfg.max_n_int;

@@ -146,6 +146,10 @@ kfac_status_t handle_graph_step(kfac_pinn_handle* h, cudaStream_t s, double* the
                                 const double* f, const double* X_bdy, int N_bdy, const double* g, double* loss);
 void handle_graph_free(kfac_pinn_handle* h);
 
+// The tensor-core path (BF16, or split-BF16 everywhere) vs the FP64 path.
+static inline bool is_mixed(const kfac_pinn_handle* h) { return h->cfg.precision != KFAC_FP64; }
+static inline bool is_split_all(const kfac_pinn_handle* h) { return h->cfg.precision == KFAC_MIXED_SPLIT; }
+
 // Device timers: bracket a launch with events when timing is enabled.
 void timer_begin(kfac_pinn_handle* h, int cls, cudaStream_t s);
 void timer_end(kfac_pinn_handle* h, int cls, cudaStream_t s, double work);

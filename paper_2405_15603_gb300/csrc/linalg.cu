@@ -292,7 +292,7 @@ kfac_status_t pgemm_stage(kfac_pinn_handle* h, cudaStream_t s, F desc) {
 }
 
 kfac_status_t precondition_impl(kfac_pinn_handle* h, cudaStream_t s, const double* grad, double* dir) {
-    if (h->cfg.precision == KFAC_MIXED_BF16) {
+    if (is_mixed(h)) {
         // the four products of every layer as four batched launches; the
         // layers' scratch matrices X1 and Y are laid out one after another
         auto X1 = [&](int l) { return h->tmp + 2 * (size_t)h->woff[l - 1]; };
@@ -413,7 +413,7 @@ kfac_status_t linalg_line_search_update(kfac_pinn_handle* h, cudaStream_t s, dou
     const unsigned blocks = ceil_div_u(h->D, 256);
     k_dhat<<<blocks, 256, 0, s>>>(h->dir, h->delta_prev, h->dhat, h->D, h->cfg.momentum);
     KFAC_LAUNCH_CHECK(h);
-    const bool mixed = (h->cfg.precision == KFAC_MIXED_BF16);
+    const bool mixed = (is_mixed(h));
     for (int k = 0; k < LS_GRID; k++) {
         k_trial<<<blocks, 256, 0, s>>>(theta, h->dhat, h->trial, h->D, ldexp(1.0, -k));
         KFAC_LAUNCH_CHECK(h);
@@ -433,7 +433,7 @@ size_t linalg_auto_part_elems() { return (size_t)KS_BLOCKS * KS_Q; }
 
 kfac_status_t linalg_auto_update(kfac_pinn_handle* h, cudaStream_t s, double* theta, const double* X_int,
                                  int N_int, const double* X_bdy, int N_bdy) {
-    const bool mixed = (h->cfg.precision == KFAC_MIXED_BF16);
+    const bool mixed = (is_mixed(h));
     double* jDi = h->ks_jv;
     double* jDb = jDi + h->cfg.max_n_int;
     double* jdi = jDb + h->cfg.max_n_bdy;

@@ -60,6 +60,10 @@ struct Args {
     float* DAD;                     // JVP_TAN: da_D of the second-order row (YD holds da_0 in the JVP modes)
     const double* r;                // residuals (BWD: for r_n g)
     int* status;
+    // split-BF16 on every row (tc_engine<MODE, true>): low halves laid out like the high ones
+    int split_all;
+    __nv_bfloat16* out_gr_lo;       // BWD: low half of r_n * g
+    const __nv_bfloat16* ytan_lo;   // BWD_TAN: low half of y_i
 };
 
 template <int MODE>
@@ -83,10 +87,11 @@ struct Cfg {
 
 // Number of accumulation terms of tile s (split-BF16 on value/Laplacian rows).
 template <int MODE>
-KFAC_DEV int n_terms(int s, int S, int split_time) {
+KFAC_DEV int n_terms(int s, int S, int split_time, int split_all) {
     if (MODE == FWD_VALUE) return 3;
-    if (MODE == FWD_TANLAP) return (s == S - 1 || (split_time && s == 1)) ? 3 : 1;
     if (MODE == JVP_VALUE || MODE == JVP_TAN) return 2;    // T dW~^T + dT W^T
+    if (split_all) return 3;                              // hi x hi + hi x lo + lo x hi everywhere
+    if (MODE == FWD_TANLAP) return (s == S - 1 || (split_time && s == 1)) ? 3 : 1;
     return 1;
 }
 
@@ -147,7 +152,9 @@ KFAC_DEV void load16_f32(const float* src, float* v) {
 }
 
 // ---------------------------------------------------------------------------
-template <int MODE>
+// SPLIT (split-BF16 on every row, Args::split_all) is a template parameter so
+// that the plain instantiations keep their register budget.
+template <int MODE, bool SPLIT>
 __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constant__ Args a) {
     using C = Cfg<MODE>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -194,7 +201,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
     }
     if (warp == 0 && lane == 0) {
         tc::prefetch_tmap(&a.a0); tc::prefetch_tmap(&a.b0);
-        if (MODE == FWD_VALUE || MODE == FWD_TANLAP || MODE == JVP_VALUE || MODE == JVP_TAN) {
+        if (MODE == FWD_VALUE || MODE == FWD_TANLAP || MODE == JVP_VALUE || MODE == JVP_TAN || SPLIT) {
             tc::prefetch_tmap(&a.a1);
             tc::prefetch_tmap(&a.b1);
         }
@@ -212,7 +219,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
             uint32_t phase = 0;
             for (int ti = 0; ti < n_tiles && !abort_flag; ti++) {
                 const int s = s_begin + ti;
-                const int terms = n_terms<MODE>(s, a.S, a.split_time);
+                const int terms = SPLIT ? n_terms<MODE>(s, a.S, a.split_time, 1) : n_terms<MODE>(s, a.S, a.split_time, 0);
                 for (int term = 0; term < terms && !abort_flag; term++) {
                     for (int k = 0; k < k_steps; k++) {
                         if (!tc::mbar_wait(&empty_bar[stage], phase ^ 1)) { abort_flag = 1; break; }
@@ -220,19 +227,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                         unsigned char* sb = sa + C::A_BYTES;
                         tc::mbar_arrive_expect_tx(&full_bar[stage], C::STAGE_BYTES);
                         if (MODE == GRAM) {
+                            // terms: X_hi^T Y_hi, X_hi^T Y_lo, X_lo^T Y_hi
                             const int row = k_begin + k * BK;
-                            tc::tma_load_2d(sa, &a.a0, &full_bar[stage], p0, row);
-                            tc::tma_load_2d(sa + 8192, &a.a0, &full_bar[stage], p0 + 64, row);
+                            const CUtensorMap* am = (term == 2) ? &a.a1 : &a.a0;
+                            const CUtensorMap* bm = (term == 1) ? &a.b1 : &a.b0;
+                            tc::tma_load_2d(sa, am, &full_bar[stage], p0, row);
+                            tc::tma_load_2d(sa + 8192, am, &full_bar[stage], p0 + 64, row);
 #pragma unroll
                             for (int b = 0; b < C::BN / 64; b++)
-                                tc::tma_load_2d(sb + 8192 * b, &a.b0, &full_bar[stage], j0 + 64 * b, row);
+                                tc::tma_load_2d(sb + 8192 * b, bm, &full_bar[stage], j0 + 64 * b, row);
                         } else {
                             // term 0: hi x hi, term 1: hi x W_lo, term 2: lo x W_hi;
                             // JVP modes: term 0: T x dW, term 1: dT x W
                             const bool jvp = (MODE == JVP_VALUE || MODE == JVP_TAN);
                             const CUtensorMap* am = (jvp ? term == 1 : term == 2) ? &a.a1 : &a.a0;
                             const CUtensorMap* bm = (term == 1) ? &a.b1 : &a.b0;
-                            int arow = (!jvp && term == 2) ? (lo_block(s, a.S) * a.N_pad + p0) : (s * a.N_pad + p0);
+                            int arow;
+                            if constexpr (SPLIT) arow = s * a.N_pad + p0;   // low halves laid out like the high
+                            else arow = (!jvp && term == 2) ? (lo_block(s, a.S) * a.N_pad + p0) : (s * a.N_pad + p0);
 #pragma unroll
                             for (int u = 0; u < C::KSUB; u++) {   // blocks past K read zeros
                                 const int kx = (k * C::KSUB + u) * BK;
@@ -257,7 +269,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                 if (!tc::mbar_wait(&acc_empty[buf], (use & 1) ^ 1)) { abort_flag = 1; break; }
                 tc::tc_fence_after();
                 const uint32_t dcol = tbase + (uint32_t)(buf * C::BN);
-                const int terms = n_terms<MODE>(s, a.S, a.split_time);
+                const int terms = SPLIT ? n_terms<MODE>(s, a.S, a.split_time, 1) : n_terms<MODE>(s, a.S, a.split_time, 0);
                 bool first = true;
                 for (int term = 0; term < terms && !abort_flag; term++) {
                     for (int k = 0; k < k_steps; k++) {
@@ -403,7 +415,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                             y[i] = st1[c + i] * v[i];
                             st2[c + i] = fmaf(wc * v[i], v[i], st2[c + i]);
                         }
-                        if (a.split_time && s == 1) {
+                        if constexpr (SPLIT) {
+                            float hi[16], lo[16];
+#pragma unroll
+                            for (int i = 0; i < 16; i++) {
+                                __nv_bfloat16 hb;
+                                lo[i] = bf_round_lo(y[i], hb);
+                                hi[i] = __bfloat162float(hb);
+                            }
+                            store16_bf16(a.out_hi + ((long long)s * a.N_pad + n) * hp + j, hi);
+                            store16_bf16(a.out_lo + ((long long)s * a.N_pad + n) * hp + j, lo);
+                        } else if (a.split_time && s == 1) {
                             float hi[16], lo[16];
 #pragma unroll
                             for (int i = 0; i < 16; i++) {
@@ -434,12 +456,29 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                         float yi[16];
                         load16_bf16(a.ytan + ((long long)s * a.N_pad + n) * hp + j, yi);
                         const float wc = a.chw[s - 1];
+                        if (SPLIT) {
+                            // full-precision y_i and 4 y_0 ybar_D (reloaded: FP32 state for
+                            // it would not fit the registers beside st1 and st2)
+                            float yl[16], a0v[16], ydv[16];
+                            load16_bf16(a.ytan_lo + ((long long)s * a.N_pad + n) * hp + j, yl);
+                            load16_f32(a.A0 + (long long)n * hp + j, a0v);
+                            load16_f32(a.YD + (long long)n * hp + j, ydv);
 #pragma unroll
-                        for (int i = 0; i < 16; i++) {
-                            float t = st1[c + i] * v[i];
-                            t -= wc * __bfloat162float(stq[c + i]) * yi[i];
-                            ab[i] = t;
-                            st2[c + i] = fmaf(yi[i], v[i], st2[c + i]);
+                            for (int i = 0; i < 16; i++) {
+                                const float y = yi[i] + yl[i];
+                                float t = st1[c + i] * v[i];
+                                t -= wc * (4.f * tanhf(a0v[i]) * ydv[i]) * y;
+                                ab[i] = t;
+                                st2[c + i] = fmaf(y, v[i], st2[c + i]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; i++) {
+                                float t = st1[c + i] * v[i];
+                                t -= wc * __bfloat162float(stq[c + i]) * yi[i];
+                                ab[i] = t;
+                                st2[c + i] = fmaf(yi[i], v[i], st2[c + i]);
+                            }
                         }
                     } else {  // BWD_VALUE
                         float a0v[16];
@@ -477,8 +516,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                         if (!live || j + i >= a.n_out) ab[i] = 0.f;
                         gr[i] = rn * ab[i];
                     }
-                    store16_bf16(a.out_hi + ((long long)s * a.N_pad + n) * hp + j, ab);
-                    store16_bf16(a.out_gr + ((long long)s * a.N_pad + n) * hp + j, gr);
+                    if (SPLIT) {
+                        float ah[16], al[16], gh[16], gl[16];
+#pragma unroll
+                        for (int i = 0; i < 16; i++) {
+                            __nv_bfloat16 hb;
+                            al[i] = bf_round_lo(ab[i], hb);
+                            ah[i] = __bfloat162float(hb);
+                            gl[i] = bf_round_lo(gr[i], hb);
+                            gh[i] = __bfloat162float(hb);
+                        }
+                        store16_bf16(a.out_hi + ((long long)s * a.N_pad + n) * hp + j, ah);
+                        store16_bf16(a.out_lo + ((long long)s * a.N_pad + n) * hp + j, al);
+                        store16_bf16(a.out_gr + ((long long)s * a.N_pad + n) * hp + j, gh);
+                        store16_bf16(a.out_gr_lo + ((long long)s * a.N_pad + n) * hp + j, gl);
+                    } else {
+                        store16_bf16(a.out_hi + ((long long)s * a.N_pad + n) * hp + j, ab);
+                        store16_bf16(a.out_gr + ((long long)s * a.N_pad + n) * hp + j, gr);
+                    }
                 }
             }
             tc::tc_fence_before();

@@ -60,9 +60,10 @@ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 struct MxLayer {
     int h, hp;
     bf16 *T_hi, *T_lo, *Zb, *Gr;
+    bf16 *Zb_lo, *Gr_lo;                  // split-BF16 everywhere: low halves of the adjoints
     float *A0, *AD, *SSQ, *YD;
-    CUtensorMap kT_hi, kT_lo, kZb;        // K-major operand maps (box 64 x 128)
-    CUtensorMap gT, gZb, gGr;             // MN-major Gram maps (box 64 x 64)
+    CUtensorMap kT_hi, kT_lo, kZb, kZb_lo;       // K-major operand maps (box 64 x 128)
+    CUtensorMap gT, gZb, gGr, gT_lo, gZb_lo, gGr_lo;   // MN-major Gram maps (box 64 x 64)
 };
 
 struct MxPass {
@@ -76,6 +77,8 @@ struct MxPass {
 
 struct MxWeights {
     bf16 *W_hi[KFAC_MAX_LAYERS], *W_lo[KFAC_MAX_LAYERS], *Wt[KFAC_MAX_LAYERS];
+    bf16* Wt_lo[KFAC_MAX_LAYERS];         // split-BF16 everywhere: low half of Wt
+    CUtensorMap kWt_lo[KFAC_MAX_LAYERS];
     float* bias[KFAC_MAX_LAYERS];
     CUtensorMap kW_hi[KFAC_MAX_LAYERS], kW_lo[KFAC_MAX_LAYERS], kWt[KFAC_MAX_LAYERS];
     float* wL;        // last layer weights (h_{L-1}) and bias at [hp]
@@ -118,7 +121,7 @@ kfac_status_t dal(T** p, size_t n) {
 // theta (FP64, column-stacked W~_l) -> BF16 hi/lo row-major W (hout_p x hin_p),
 // BF16 transposed Wt (hin_p x hout_p), FP32 bias; zero padding.
 __global__ void k_convert_weights(const double* __restrict__ W, int hout, int hin, int hout_p, int hin_p,
-                                  bf16* Whi, bf16* Wlo, bf16* Wt, float* bias) {
+                                  bf16* Whi, bf16* Wlo, bf16* Wt, bf16* Wt_lo, float* bias) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)hout_p * hin_p) return;
     int i = (int)(idx / hin_p), k = (int)(idx % hin_p);
@@ -129,6 +132,7 @@ __global__ void k_convert_weights(const double* __restrict__ W, int hout, int hi
     Whi[idx] = hi;
     Wlo[idx] = lo;
     Wt[(long long)k * hout_p + i] = hi;
+    if (Wt_lo) Wt_lo[(long long)k * hout_p + i] = lo;
     if (k == 0) bias[i] = (i < hout) ? (float)W[i + (long long)hout * hin] : 0.f;
 }
 
@@ -166,7 +170,9 @@ KFAC_DEV void store4_bf16(bf16* dst, const float* v) {
 // most); one thread per point and 4 consecutive features.
 __global__ void k_layer1(const float* __restrict__ W1f, const float* __restrict__ Wt, const float* __restrict__ Xf,
                          int N, int N_pad, int d, int h, int hp, int S, const float* __restrict__ chw,
-                         int split_time, bf16* T_hi, bf16* T_lo, float* A0, float* AD, float* SSQ) {
+                         int split_time, int split_all, bf16* T_hi, bf16* T_lo, float* A0, float* AD, float* SSQ) {
+    // low halves: block 0 value, 1 Laplacian, 2 time (heat); every block s at
+    // its own row block when split_all
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int hq = hp / 4;
     if (idx >= (long long)N_pad * hq) return;
@@ -211,11 +217,11 @@ __global__ void k_layer1(const float* __restrict__ W1f, const float* __restrict_
 #pragma unroll
             for (int q = 0; q < 4; q++) t[q] = s1[q] * w[q];
             store4_bf16(T_hi + (1 + i) * blk + o, t);
-            if (i == 0 && split_time) {     // heat: the time tangent keeps its low half (block 2)
+            if (split_all || (i == 0 && split_time)) {     // heat: the time tangent keeps its low half
                 float tl[4];
 #pragma unroll
                 for (int q = 0; q < 4; q++) tl[q] = t[q] - __bfloat162float(__float2bfloat16_rn(t[q]));
-                store4_bf16(T_lo + 2 * blk + o, tl);
+                store4_bf16(T_lo + (split_all ? (1 + i) : 2) * blk + o, tl);
             }
             const float wc = chw[i];
 #pragma unroll
@@ -231,7 +237,7 @@ __global__ void k_layer1(const float* __restrict__ W1f, const float* __restrict_
             dl[q] = yD - dh[q];
         }
         store4_bf16(T_hi + (S - 1) * blk + o, dh);
-        store4_bf16(T_lo + blk + o, dl);
+        store4_bf16(T_lo + (split_all ? S - 1 : 1) * blk + o, dl);
     }
     *reinterpret_cast<float4*>(A0 + o) = make_float4(a0[0], a0[1], a0[2], a0[3]);
     *reinterpret_cast<float4*>(AD + o) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -242,7 +248,7 @@ __global__ void k_layer1(const float* __restrict__ W1f, const float* __restrict_
 // y_D = s1 a_D + s2 sum_{i in C} a_i^2  (Eq. 6).
 __global__ void k_lap_finish(const float* __restrict__ part, int n_chunks, int N, int N_pad, int h, int hp, int S,
                              const float* __restrict__ A0, const float* __restrict__ AD, float* SSQ, bf16* T_hi,
-                             bf16* T_lo) {
+                             bf16* T_lo, int split_all) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long blk = (long long)N_pad * hp;
     if (idx >= blk) return;
@@ -256,7 +262,7 @@ __global__ void k_lap_finish(const float* __restrict__ part, int n_chunks, int N
     SSQ[idx] = live ? ssq : 0.f;
     bf16 hi = __float2bfloat16_rn(yD);
     T_hi[(S - 1) * blk + idx] = hi;
-    T_lo[blk + idx] = __float2bfloat16_rn(yD - __bfloat162float(hi));
+    T_lo[(split_all ? S - 1 : 1) * blk + idx] = __float2bfloat16_rn(yD - __bfloat162float(hi));
 }
 
 // Last linear layer (h_L = 1): z[row] = sum_j T[row][j] w[j] (+ bias on value
@@ -267,6 +273,7 @@ struct BlockSel {
     int nsel;
     int b[3];
     int split_time;
+    int split_all;      // every block has its low half at its own row block
 };
 __global__ void k_last_fwd(const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo, const float* __restrict__ wL,
                            int N_pad, int S, int hp, BlockSel sel, float* zl) {
@@ -279,7 +286,8 @@ __global__ void k_last_fwd(const bf16* __restrict__ T_hi, const bf16* __restrict
     wid = (long long)s * N_pad + n;
     const bf16* row = T_hi + wid * hp;
     const bf16* lrow = nullptr;
-    if (s == 0) lrow = T_lo + (long long)n * hp;
+    if (sel.split_all) lrow = T_lo + ((long long)s * N_pad + n) * hp;
+    else if (s == 0) lrow = T_lo + (long long)n * hp;
     else if (s == S - 1) lrow = T_lo + ((long long)N_pad + n) * hp;
     else if (s == 1 && sel.split_time) lrow = T_lo + (2LL * N_pad + n) * hp;
     float acc = 0.f;
@@ -342,7 +350,9 @@ __global__ void k_extract_mx(const float* __restrict__ zl, int N, int N_pad, int
 __global__ void k_last_bwd(const float* __restrict__ wL, const bf16* __restrict__ T_hi, const float* __restrict__ A0,
                            const float* __restrict__ AD, const float* __restrict__ SSQ, const double* __restrict__ r,
                            int N, int N_pad, int h, int hp, int S, const float* __restrict__ chw, float cT,
-                           float cD, const float* __restrict__ seed, bf16* Zb, bf16* Gr) {
+                           float cD, const float* __restrict__ seed, bf16* Zb, bf16* Gr,
+                           const bf16* __restrict__ T_lo, bf16* Zb_lo, bf16* Gr_lo) {
+    // T_lo, Zb_lo, Gr_lo: split-BF16 everywhere (all three, or none)
     // seed == nullptr: the residual's constant seed c (cT, cD; 1 on the value of a
     // boundary pass); else c_{n,s} = seed[s * N_pad + n] (reverse mode of the forward
     // Laplacian).  r == nullptr: Gr = Zb.
@@ -356,10 +366,17 @@ __global__ void k_last_bwd(const float* __restrict__ wL, const bf16* __restrict_
     float y0 = tanhf(A0[idx]);
     float s1 = 1.f - y0 * y0;
     const float c0 = seed ? seed[n] : (S == 1 ? 1.f : 0.f);
+    auto put = [&](long long o, float ab) {
+        const bf16 zh = __float2bfloat16_rn(ab), gh = __float2bfloat16_rn(rn * ab);
+        Zb[o] = zh;
+        Gr[o] = gh;
+        if (Zb_lo) {
+            Zb_lo[o] = __float2bfloat16_rn(ab - __bfloat162float(zh));
+            Gr_lo[o] = __float2bfloat16_rn(rn * ab - __bfloat162float(gh));
+        }
+    };
     if (S == 1) {
-        float ab = s1 * c0 * w;
-        Zb[idx] = __float2bfloat16_rn(ab);
-        Gr[idx] = __float2bfloat16_rn(rn * ab);
+        put(idx, s1 * c0 * w);
         return;
     }
     // seed c = dr/dZ^{(L)}: cD on the second-order column, cT on tangent column 1 (time, heat)
@@ -367,22 +384,20 @@ __global__ void k_last_bwd(const float* __restrict__ wL, const bf16* __restrict_
     float cross = 0.f;
     for (int s = 1; s < S - 1; s++) {
         float yi = __bfloat162float(T_hi[s * blk + idx]);
+        if (T_lo) yi += __bfloat162float(T_lo[s * blk + idx]);
         float ybar = (seed ? seed[(long long)s * N_pad + n] : (s == 1 ? cT : 0.f)) * w;
         float ab = s1 * ybar;
         ab -= 4.f * chw[s - 1] * y0 * yi * yD;
         cross = fmaf(yi, ybar, cross);
         ab = live ? ab : 0.f;
-        Zb[s * blk + idx] = __float2bfloat16_rn(ab);
-        Gr[s * blk + idx] = __float2bfloat16_rn(rn * ab);
+        put(s * blk + idx, ab);
     }
     float a0b = s1 * c0 * w - 2.f * y0 * cross - 2.f * s1 * (y0 * AD[idx] + (1.f - 3.f * y0 * y0) * SSQ[idx]) * yD;
     float aDb = s1 * yD;
     a0b = live ? a0b : 0.f;
     aDb = live ? aDb : 0.f;
-    Zb[idx] = __float2bfloat16_rn(a0b);
-    Gr[idx] = __float2bfloat16_rn(rn * a0b);
-    Zb[(S - 1) * blk + idx] = __float2bfloat16_rn(aDb);
-    Gr[(S - 1) * blk + idx] = __float2bfloat16_rn(rn * aDb);
+    put(idx, a0b);
+    put((S - 1) * blk + idx, aDb);
 }
 
 // Column reductions run as 32 x 32 thread blocks: lane = column, warp = row
@@ -509,7 +524,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_grad_layer1(const bf16* __restr
                                                              const float* __restrict__ X,
                                                              const float* __restrict__ Xb, int N, int N_pad, int Nb,
                                                              int d, int h, int hp, int S, double si, double sb,
-                                                             double* grad, double* gtan) {
+                                                             double* grad, double* gtan, const bf16* __restrict__ Gr_lo,
+                                                             const bf16* __restrict__ Grb_lo) {
+    // Gr_lo / Grb_lo: low halves (split-BF16 everywhere), or nullptr
     // dL/dW~_1[j][k] = si sum_n (r g_{n,0,j} x_{n,k} + sum_m r g_{n,m,j} (v_m)_k) + boundary term (sb);
     // with gtan the tangent sums t_{j,m} = si sum_n r g_{n,m,j} are written there
     // (the caller rotates them by the tangent directions), else v_m = e_m.
@@ -521,15 +538,18 @@ __global__ void __launch_bounds__(RED_THREADS) k_grad_layer1(const bf16* __restr
     if (j < h) {
         for (int n = rg; n < N; n += 32) {
             float g0 = __bfloat162float(Gr[(long long)n * hp + j]);
+            if (Gr_lo) g0 += __bfloat162float(Gr_lo[(long long)n * hp + j]);
             if (k < d) {
                 a = fmaf(g0, X[(long long)n * d + k], a);
                 t += __bfloat162float(Gr[(1 + k) * blk + (long long)n * hp + j]);
+                if (Gr_lo) t += __bfloat162float(Gr_lo[(1 + k) * blk + (long long)n * hp + j]);
             } else {
                 a += g0;
             }
         }
         for (int n = rg; n < Nb; n += 32) {
             float g0 = __bfloat162float(Grb[(long long)n * hp + j]);
+            if (Grb_lo) g0 += __bfloat162float(Grb_lo[(long long)n * hp + j]);
             b += (k < d) ? g0 * Xb[(long long)n * d + k] : g0;
         }
     }
@@ -635,7 +655,8 @@ __global__ void k_last_jvp(const bf16* __restrict__ T_hi, const bf16* __restrict
     const bf16* row = T_hi + wid * hp;
     const bf16* drow = dT + wid * hp;
     const bf16* lrow = nullptr;
-    if (s == 0) lrow = T_lo + (long long)n * hp;
+    if (sel.split_all) lrow = T_lo + ((long long)s * N_pad + n) * hp;
+    else if (s == 0) lrow = T_lo + (long long)n * hp;
     else if (s == S - 1) lrow = T_lo + ((long long)N_pad + n) * hp;
     else if (s == 1 && sel.split_time) lrow = T_lo + (2LL * N_pad + n) * hp;
     float acc = 0.f;
@@ -747,7 +768,10 @@ __global__ void k_last_layer_terms(const bf16* __restrict__ T_hi, const bf16* __
                                    const bf16* __restrict__ Tb_hi, const bf16* __restrict__ Tb_lo,
                                    const double* __restrict__ r, const double* __restrict__ rb, int N, int N_pad,
                                    int Nb, int Nb_pad, int h, int hp, int S, double cT, double cD, int reduce,
-                                   double* grad, double* B_int, double* B_bdy, double beta, int* status) {
+                                   double* grad, double* B_int, double* B_bdy, double beta, int* status,
+                                   int split_all) {
+    // low halves of the Laplacian (block 1) and time (block 2) rows, or at the
+    // rows' own blocks when every row is split
     __shared__ double shm[32][33];
     const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
     const int q = blockIdx.x * 32 + cl;
@@ -756,11 +780,11 @@ __global__ void k_last_layer_terms(const bf16* __restrict__ T_hi, const bf16* __
     if (q < h) {
         for (int n = rg; n < N; n += 32) {
             double tD = (double)__bfloat162float(T_hi[(S - 1) * blk + (long long)n * hp + q]) +
-                        (double)__bfloat162float(T_lo[blk + (long long)n * hp + q]);
+                        (double)__bfloat162float(T_lo[(split_all ? S - 1 : 1) * blk + (long long)n * hp + q]);
             double v = cD * tD;
             if (cT != 0.0)     // heat: the time tangent carries its low half (block 2)
                 v += cT * ((double)__bfloat162float(T_hi[blk + (long long)n * hp + q]) +
-                           (double)__bfloat162float(T_lo[2 * blk + (long long)n * hp + q]));
+                           (double)__bfloat162float(T_lo[(split_all ? 1 : 2) * blk + (long long)n * hp + q]));
             a += r[n] * v;
         }
         for (int n = rg; n < Nb; n += 32) {
@@ -787,19 +811,33 @@ __global__ void k_last_layer_terms(const bf16* __restrict__ T_hi, const bf16* __
 // ============================================================================
 // Host helpers
 // ============================================================================
-template <int MODE>
-kfac_status_t launch_engine(kfac_pinn_handle* h, cudaStream_t s, const Args& a, dim3 grid, int kclass, double work) {
+template <int MODE, bool SPLIT>
+kfac_status_t launch_engine_as(kfac_pinn_handle* h, cudaStream_t s, const Args& a, dim3 grid) {
     using C = tck::Cfg<MODE>;
     static bool attr_set = false;
     if (!attr_set) {
-        if (cudaFuncSetAttribute(tck::tc_engine<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+        if (cudaFuncSetAttribute(tck::tc_engine<MODE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
             cudaSuccess)
             return KFAC_CUDA_ERROR;
         attr_set = true;
     }
+    tck::tc_engine<MODE, SPLIT><<<grid, tck::NUM_THREADS, C::SMEM, s>>>(a);
+    return KFAC_OK;
+}
+
+template <int MODE>
+kfac_status_t launch_engine(kfac_pinn_handle* h, cudaStream_t s, const Args& a, dim3 grid, int kclass, double work) {
     if (grid.x == 0 || grid.y == 0 || grid.z == 0) return KFAC_OK;
     timer_begin(h, kclass, s);
-    tck::tc_engine<MODE><<<grid, tck::NUM_THREADS, C::SMEM, s>>>(a);
+    kfac_status_t st;
+    // the forward-mode JVPs (KFAC*) have no split-everywhere form
+    if constexpr (MODE != tck::JVP_VALUE && MODE != tck::JVP_TAN) {
+        st = a.split_all ? launch_engine_as<MODE, true>(h, s, a, grid) : launch_engine_as<MODE, false>(h, s, a, grid);
+    } else {
+        if (a.split_all) return KFAC_BAD_ARG;
+        st = launch_engine_as<MODE, false>(h, s, a, grid);
+    }
+    if (st) return st;
     timer_end(h, kclass, s, work);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
@@ -813,6 +851,7 @@ Args base_args(kfac_pinn_handle* h, const MxPass& P, int N) {
     a.S = P.S;
     a.chw = h->chw32;
     a.split_time = (h->cfg.op == KFAC_OP_HEAT && P.S > 2) ? 1 : 0;
+    a.split_all = is_split_all(h) ? 1 : 0;
     a.status = h->status;
     return a;
 }
@@ -857,20 +896,35 @@ kfac_status_t alloc_pass(kfac_pinn_handle* h, MxPass& P, int Nmax, int S) {
         ly.hp = round_up(ly.h, 64);
         if (ly.hp > hp_max) hp_max = ly.hp;
         size_t big = (size_t)P.rows * ly.hp, small = (size_t)P.N_pad * ly.hp;
+        // low halves: the value, Laplacian and (heat) time blocks, or every
+        // block (laid out like the high halves) when every row is split
+        const bool sa = is_split_all(h);
+        const size_t lo_rows = sa ? (size_t)P.rows : 3 * (size_t)P.N_pad;
         if ((st = dal(&ly.T_hi, big))) return st;
-        if ((st = dal(&ly.T_lo, 3 * small))) return st;
+        if ((st = dal(&ly.T_lo, lo_rows * ly.hp))) return st;
         if ((st = dal(&ly.Zb, big))) return st;
         if ((st = dal(&ly.Gr, big))) return st;
+        if (sa) {
+            if ((st = dal(&ly.Zb_lo, big))) return st;
+            if ((st = dal(&ly.Gr_lo, big))) return st;
+            cudaMemset(ly.Zb_lo, 0, big * sizeof(bf16));
+            cudaMemset(ly.Gr_lo, 0, big * sizeof(bf16));
+            bool ok = tc_make_tmap_2d(&ly.kZb_lo, ly.Zb_lo, ly.hp, P.rows, ly.hp * 2, 64, 128) &&
+                      tc_make_tmap_2d(&ly.gT_lo, ly.T_lo, ly.hp, P.rows, ly.hp * 2, 64, 64) &&
+                      tc_make_tmap_2d(&ly.gZb_lo, ly.Zb_lo, ly.hp, P.rows, ly.hp * 2, 64, 64) &&
+                      tc_make_tmap_2d(&ly.gGr_lo, ly.Gr_lo, ly.hp, P.rows, ly.hp * 2, 64, 64);
+            if (!ok) return KFAC_CUDA_ERROR;
+        }
         if ((st = dal(&ly.A0, small))) return st;
         if ((st = dal(&ly.AD, small))) return st;
         if ((st = dal(&ly.SSQ, small))) return st;
         if ((st = dal(&ly.YD, small))) return st;
         cudaMemset(ly.T_hi, 0, big * sizeof(bf16));
-        cudaMemset(ly.T_lo, 0, 3 * small * sizeof(bf16));
+        cudaMemset(ly.T_lo, 0, lo_rows * ly.hp * sizeof(bf16));
         cudaMemset(ly.Zb, 0, big * sizeof(bf16));
         cudaMemset(ly.Gr, 0, big * sizeof(bf16));
         bool ok = tc_make_tmap_2d(&ly.kT_hi, ly.T_hi, ly.hp, P.rows, ly.hp * 2, 64, 128) &&
-                  tc_make_tmap_2d(&ly.kT_lo, ly.T_lo, ly.hp, 3 * P.N_pad, ly.hp * 2, 64, 128) &&
+                  tc_make_tmap_2d(&ly.kT_lo, ly.T_lo, ly.hp, lo_rows, ly.hp * 2, 64, 128) &&
                   tc_make_tmap_2d(&ly.kZb, ly.Zb, ly.hp, P.rows, ly.hp * 2, 64, 128) &&
                   tc_make_tmap_2d(&ly.gT, ly.T_hi, ly.hp, P.rows, ly.hp * 2, 64, 64) &&
                   tc_make_tmap_2d(&ly.gZb, ly.Zb, ly.hp, P.rows, ly.hp * 2, 64, 64) &&
@@ -896,6 +950,7 @@ void free_pass(MxPass& P) {
     for (int l = 0; l < KFAC_MAX_LAYERS; l++) {
         MxLayer& ly = P.lay[l];
         cudaFree(ly.T_hi); cudaFree(ly.T_lo); cudaFree(ly.Zb); cudaFree(ly.Gr);
+        cudaFree(ly.Zb_lo); cudaFree(ly.Gr_lo);
         cudaFree(ly.A0); cudaFree(ly.AD); cudaFree(ly.SSQ); cudaFree(ly.YD);
     }
     cudaFree(P.zl);
@@ -905,8 +960,11 @@ void free_pass(MxPass& P) {
 }
 
 // Gram over rows: part[z][p][q] = sum_{rows in chunk z} X[row][p] Y[row][q].
+// With X_lo and Y_lo (split-BF16 everywhere) the three products
+// X_hi^T Y_hi + X_hi^T Y_lo + X_lo^T Y_hi are accumulated.
 kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, const CUtensorMap& Y, int P, int Q,
-                   int rows, int sym, float* part, int& nz) {
+                   int rows, int sym, float* part, int& nz, const CUtensorMap* X_lo = nullptr,
+                   const CUtensorMap* Y_lo = nullptr) {
     using C = tck::Cfg<tck::GRAM>;
     int p_tiles = (P + 127) / 128, q_tiles = (Q + C::BN - 1) / C::BN;
     int tiles = 0;
@@ -939,7 +997,12 @@ kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, co
     a.q_tiles = q_tiles;
     a.part = part;
     a.status = h->status;
-    double work = 2.0 * (double)tiles * 128 * C::BN * rows;
+    if (X_lo && Y_lo) {
+        a.a1 = *X_lo;
+        a.b1 = *Y_lo;
+        a.split_all = 1;
+    }
+    double work = 2.0 * (double)tiles * 128 * C::BN * rows;   // algorithmic: one product per entry
     return launch_engine<tck::GRAM>(h, s, a, dim3(tiles, nz, 1), KFAC_KC_GRAM, work);
 }
 
@@ -953,7 +1016,7 @@ kfac_status_t convert_weights_into(kfac_pinn_handle* h, cudaStream_t s, const do
         int hout_p = round_up(hout, 64), hin_p = round_up(hin, 64);
         k_convert_weights<<<ceil_div_u((long long)hout_p * hin_p, EW), EW, 0, s>>>(
             theta + h->woff[l - 1], hout, hin, hout_p, hin_p, w.W_hi[l - 1], w.W_lo[l - 1], w.Wt[l - 1],
-            w.bias[l - 1]);
+            w.Wt_lo[l - 1], w.bias[l - 1]);
         KFAC_LAUNCH_CHECK(h);
     }
     {
@@ -988,8 +1051,9 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
         KFAC_LAUNCH_CHECK(h);
         k_layer1<<<ceil_div_u(cnt / 4, EW), EW, 0, s>>>(m->w.W1f, m->w.W1Qf ? m->w.W1Qf : m->w.W1f, P.Xf, N,
                                                          P.N_pad, d, l1.h, l1.hp, S, h->chw32,
-                                                         (h->cfg.op == KFAC_OP_HEAT && S > 2) ? 1 : 0, l1.T_hi,
-                                                         l1.T_lo, l1.A0, l1.AD, l1.SSQ);
+                                                         (h->cfg.op == KFAC_OP_HEAT && S > 2) ? 1 : 0,
+                                                         is_split_all(h) ? 1 : 0, l1.T_hi, l1.T_lo, l1.A0, l1.AD,
+                                                         l1.SSQ);
         timer_end(h, KFAC_KC_ELEMENTWISE, s, 2.0 * (double)S * cnt + 16.0 * cnt);
         KFAC_LAUNCH_CHECK(h);
     }
@@ -1022,7 +1086,8 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
             long long cnt = (long long)P.N_pad * out.hp;
             timer_begin(h, KFAC_KC_ELEMENTWISE, s);
             k_lap_finish<<<ceil_div_u(cnt, EW), EW, 0, s>>>(m->part, a.n_chunks, N, P.N_pad, out.h, out.hp, S,
-                                                             out.A0, out.AD, out.SSQ, out.T_hi, out.T_lo);
+                                                             out.A0, out.AD, out.SSQ, out.T_hi, out.T_lo,
+                                                             is_split_all(h) ? 1 : 0);
             timer_end(h, KFAC_KC_ELEMENTWISE, s, (4.0 * a.n_chunks + 16.0) * cnt);
             KFAC_LAUNCH_CHECK(h);
         }
@@ -1047,7 +1112,7 @@ kfac_status_t backward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* r
         timer_begin(h, KFAC_KC_ELEMENTWISE, s);
         k_last_bwd<<<ceil_div_u(cnt, EW), EW, 0, s>>>(m->w.wL, ly.T_hi, ly.A0, ly.AD, ly.SSQ, r, N, P.N_pad, ly.h,
                                                        ly.hp, S, h->chw32, (float)h->cT, (float)h->cD, seed, ly.Zb,
-                                                       ly.Gr);
+                                                       ly.Gr, ly.Zb_lo ? ly.T_lo : nullptr, ly.Zb_lo, ly.Gr_lo);
         timer_end(h, KFAC_KC_ELEMENTWISE, s, 6.0 * S * (double)cnt);
         KFAC_LAUNCH_CHECK(h);
     }
@@ -1057,6 +1122,13 @@ kfac_status_t backward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* r
         Args a = base_args(h, P, N);
         a.a0 = up.kZb;
         a.b0 = m->w.kWt[l - 1];
+        if (a.split_all) {       // three products: G_hi W_hi + G_hi W_lo + G_lo W_hi
+            a.a1 = up.kZb_lo;
+            a.b1 = m->w.kWt_lo[l - 1];
+            a.out_lo = dn.Zb_lo;
+            a.out_gr_lo = dn.Gr_lo;
+            a.ytan_lo = dn.T_lo;
+        }
         a.k_steps = up.hp / 64;
         a.n_out = dn.h;
         a.hp_out = dn.hp;
@@ -1099,6 +1171,7 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
     double* cs_b = m->cs + (m->hp_max + 8);
     kfac_status_t st;
     int zi = 0, zb = 0;
+    const bool sa = is_split_all(h);     // split-BF16 everywhere: three-product Grams
 
     // ---- layer 1: closed-form A, gradient from the adjoints ---------------
     {
@@ -1112,7 +1185,7 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
         MxLayer& l1 = I.lay[0];
         k_grad_layer1<<<dim3(ceil_div_u(l1.h, 32), d + 1), RED_THREADS, 0, s>>>(
             l1.Gr, B.lay[0].Gr, I.Xf, B.Xf, N, I.N_pad, Nb, d, l1.h, l1.hp, S, 1.0 / N, 1.0 / Nb,
-            h->grad + h->woff[0], m->gtan);
+            h->grad + h->woff[0], m->gtan, l1.Gr_lo, B.lay[0].Gr_lo);
         KFAC_LAUNCH_CHECK(h);
         if (m->gtan) {
             k_rotate_grad1<<<ceil_div_u((long long)l1.h * d, EW), EW, 0, s>>>(m->gtan, m->Qf, l1.h, d,
@@ -1130,13 +1203,17 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
             KFAC_LAUNCH_CHECK(h);
             if ((st = gram(h, s, I.gRg[l - 1], I.gRg[l - 1], li.h, li.h, I.N_pad, 1, part_i, zi))) return st;
         } else {
-            if ((st = gram(h, s, li.gZb, li.gZb, li.h, li.h, I.rows, 1, part_i, zi))) return st;
+            if ((st = gram(h, s, li.gZb, li.gZb, li.h, li.h, I.rows, 1, part_i, zi, sa ? &li.gZb_lo : nullptr,
+                           sa ? &li.gZb_lo : nullptr)))
+                return st;
         }
         long long nn = (long long)li.h * li.h;
         k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_i, zi, li.h, 1, nullptr, 1.0 / N, 0.0, 0.0, 0,
                                                          h->fac[KFAC_B_INT][l - 1], beta, h->status);
         KFAC_LAUNCH_CHECK(h);
-        if ((st = gram(h, s, lb.gZb, lb.gZb, lb.h, lb.h, B.rows, 1, part_b, zb))) return st;
+        if ((st = gram(h, s, lb.gZb, lb.gZb, lb.h, lb.h, B.rows, 1, part_b, zb, sa ? &lb.gZb_lo : nullptr,
+                       sa ? &lb.gZb_lo : nullptr)))
+            return st;
         k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_b, zb, lb.h, 1, nullptr, 1.0 / Nb, 0.0, 0.0, 0,
                                                          h->fac[KFAC_B_BDY][l - 1], beta, h->status);
         KFAC_LAUNCH_CHECK(h);
@@ -1159,7 +1236,9 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
                                                              1.0 / ((double)S * S), 1, h->fac[KFAC_A_INT][l - 1], beta,
                                                              h->status);
         } else {
-            if ((st = gram(h, s, ti.gT, ti.gT, hin, hin, I.rows, 1, part_i, zi))) return st;
+            if ((st = gram(h, s, ti.gT, ti.gT, hin, hin, I.rows, 1, part_i, zi, sa ? &ti.gT_lo : nullptr,
+                           sa ? &ti.gT_lo : nullptr)))
+                return st;
             k_colsum<<<ceil_div_u(hin, 32), RED_THREADS, 0, s>>>(ti.T_hi, ti.T_lo, ti.hp, 0, N, hin, cs_i);
             KFAC_LAUNCH_CHECK(h);
             double sc = 1.0 / ((double)N * S);
@@ -1168,7 +1247,9 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
         }
         KFAC_LAUNCH_CHECK(h);
         // boundary A_l
-        if ((st = gram(h, s, tb.gT, tb.gT, hin, hin, B.rows, 1, part_b, zb))) return st;
+        if ((st = gram(h, s, tb.gT, tb.gT, hin, hin, B.rows, 1, part_b, zb, sa ? &tb.gT_lo : nullptr,
+                       sa ? &tb.gT_lo : nullptr)))
+            return st;
         k_colsum<<<ceil_div_u(hin, 32), RED_THREADS, 0, s>>>(tb.T_hi, tb.T_lo, tb.hp, 0, Nb, hin, cs_b);
         KFAC_LAUNCH_CHECK(h);
         k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_b, zb, hin, 1, cs_b, 1.0 / Nb, 1.0 / Nb, 1.0, 1,
@@ -1179,11 +1260,15 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
             MxLayer& gi = I.lay[l - 1];
             MxLayer& gb = B.lay[l - 1];
             const int hout = gi.h;
-            if ((st = gram(h, s, gi.gGr, ti.gT, hout, hin, I.rows, 0, part_i, zi))) return st;
-            if ((st = gram(h, s, gb.gGr, tb.gT, hout, hin, B.rows, 0, part_b, zb))) return st;
-            k_colsum<<<ceil_div_u(hout, 32), RED_THREADS, 0, s>>>(gi.Gr, nullptr, gi.hp, 0, N, hout, cs_i);
+            if ((st = gram(h, s, gi.gGr, ti.gT, hout, hin, I.rows, 0, part_i, zi, sa ? &gi.gGr_lo : nullptr,
+                           sa ? &ti.gT_lo : nullptr)))
+                return st;
+            if ((st = gram(h, s, gb.gGr, tb.gT, hout, hin, B.rows, 0, part_b, zb, sa ? &gb.gGr_lo : nullptr,
+                           sa ? &tb.gT_lo : nullptr)))
+                return st;
+            k_colsum<<<ceil_div_u(hout, 32), RED_THREADS, 0, s>>>(gi.Gr, gi.Gr_lo, gi.hp, 0, N, hout, cs_i);
             KFAC_LAUNCH_CHECK(h);
-            k_colsum<<<ceil_div_u(hout, 32), RED_THREADS, 0, s>>>(gb.Gr, nullptr, gb.hp, 0, Nb, hout, cs_b);
+            k_colsum<<<ceil_div_u(hout, 32), RED_THREADS, 0, s>>>(gb.Gr, gb.Gr_lo, gb.hp, 0, Nb, hout, cs_b);
             KFAC_LAUNCH_CHECK(h);
             k_grad_reduce<<<ceil_div_u((long long)hout * (hin + 1), EW), EW, 0, s>>>(
                 part_i, zi, part_b, zb, hout, hin, cs_i, cs_b, 1.0 / N, 1.0 / Nb, h->grad + h->woff[l - 1]);
@@ -1192,7 +1277,7 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
             k_last_layer_terms<<<ceil_div_u(hin + 1, 32), RED_THREADS, 0, s>>>(
                 ti.T_hi, ti.T_lo, tb.T_hi, tb.T_lo, h->in.r, h->bd.r, N, I.N_pad, Nb, B.N_pad, hin, ti.hp, S,
                 h->cT, h->cD, reduce, h->grad + h->woff[L - 1], h->fac[KFAC_B_INT][L - 1],
-                h->fac[KFAC_B_BDY][L - 1], beta, h->status);
+                h->fac[KFAC_B_BDY][L - 1], beta, h->status, sa ? 1 : 0);
             KFAC_LAUNCH_CHECK(h);
         }
     }
@@ -1221,6 +1306,11 @@ kfac_status_t alloc_weights(kfac_pinn_handle* h, MxWeights& w) {
                   tc_make_tmap_2d(&w.kW_lo[l - 1], w.W_lo[l - 1], hin_p, hout_p, hin_p * 2, 64, 128) &&
                   tc_make_tmap_2d(&w.kWt[l - 1], w.Wt[l - 1], hout_p, hin_p, hout_p * 2, 64, 128);
         if (!ok) return KFAC_CUDA_ERROR;
+        if (is_split_all(h)) {
+            if ((st = dal(&w.Wt_lo[l - 1], e))) return st;
+            if (!tc_make_tmap_2d(&w.kWt_lo[l - 1], w.Wt_lo[l - 1], hout_p, hin_p, hout_p * 2, 64, 128))
+                return KFAC_CUDA_ERROR;
+        }
     }
     if ((st = dal(&w.wL, (size_t)round_up(h->dims[L - 1], 64) + 1))) return st;
     if ((st = dal(&w.W1f, (size_t)(h->dims[0] + 1) * round_up(h->dims[1], 64)))) return st;
@@ -1231,6 +1321,7 @@ kfac_status_t alloc_weights(kfac_pinn_handle* h, MxWeights& w) {
 void free_weights(MxWeights& w) {
     for (int l = 0; l < KFAC_MAX_LAYERS; l++) {
         cudaFree(w.W_hi[l]); cudaFree(w.W_lo[l]); cudaFree(w.Wt[l]); cudaFree(w.bias[l]);
+        cudaFree(w.Wt_lo[l]);
     }
     cudaFree(w.wL);
     cudaFree(w.W1f);
@@ -1314,6 +1405,7 @@ kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const d
     si.b[1] = 1;
     si.b[2] = 0;
     si.split_time = heat;
+    si.split_all = is_split_all(h) ? 1 : 0;
     if ((st = forward_pass(h, s, theta, X_int, N_int, m->in, si))) return st;
     k_residual_mx<<<ceil_div_u(N_int, EW), EW, 0, s>>>(m->in.zl, f, h->in.r, N_int, m->in.N_pad, S, 1, h->cT,
                                                         h->cD);
@@ -1323,6 +1415,7 @@ kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const d
     sb.b[0] = 0;
     sb.b[1] = sb.b[2] = 0;
     sb.split_time = 0;
+    sb.split_all = is_split_all(h) ? 1 : 0;
     if ((st = forward_pass(h, s, theta, X_bdy, N_bdy, m->bd, sb))) return st;
     k_residual_mx<<<ceil_div_u(N_bdy, EW), EW, 0, s>>>(m->bd.zl, g, h->bd.r, N_bdy, m->bd.N_pad, 1, 0, h->cT,
                                                         h->cD);
@@ -1359,6 +1452,7 @@ kfac_status_t tc_forward_laplacian(kfac_pinn_handle* h, cudaStream_t s, const do
     all.nsel = 0;
     all.b[0] = all.b[1] = all.b[2] = 0;
     all.split_time = (h->cfg.op == KFAC_OP_HEAT) ? 1 : 0;
+    all.split_all = is_split_all(h) ? 1 : 0;
     if ((st = forward_pass(h, s, theta, X, N, m->in, all))) return st;
     k_extract_mx<<<ceil_div_u(N, EW), EW, 0, s>>>(m->in.zl, N, m->in.N_pad, m->in.S, h->dims[0], m->Qf, u, grad,
                                                    lap);
@@ -1379,6 +1473,7 @@ kfac_status_t tc_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s,
     all.nsel = 0;
     all.b[0] = all.b[1] = all.b[2] = 0;
     all.split_time = heat;
+    all.split_all = is_split_all(h) ? 1 : 0;
     if ((st = forward_pass(h, s, theta, X, N, I, all))) return st;
     k_seed_mx<<<ceil_div_u((long long)S * I.N_pad, EW), EW, 0, s>>>(m->seed, N, I.N_pad, S, m->Qf, du, dgrad, dlap);
     KFAC_LAUNCH_CHECK(h);
@@ -1391,7 +1486,8 @@ kfac_status_t tc_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s,
     {
         MxLayer& l1 = I.lay[0];
         k_grad_layer1<<<dim3(ceil_div_u(l1.h, 32), d + 1), RED_THREADS, 0, s>>>(
-            l1.Gr, l1.Gr, I.Xf, I.Xf, N, I.N_pad, 0, d, l1.h, l1.hp, S, 1.0, 0.0, G + h->woff[0], m->gtan);
+            l1.Gr, l1.Gr, I.Xf, I.Xf, N, I.N_pad, 0, d, l1.h, l1.hp, S, 1.0, 0.0, G + h->woff[0], m->gtan,
+            l1.Gr_lo, l1.Gr_lo);
         KFAC_LAUNCH_CHECK(h);
         if (m->gtan) {
             k_rotate_grad1<<<ceil_div_u((long long)l1.h * d, EW), EW, 0, s>>>(m->gtan, m->Qf, l1.h, d, G + h->woff[0]);
@@ -1479,6 +1575,7 @@ kfac_status_t jvp_pass(kfac_pinn_handle* h, cudaStream_t s, MxPass& P, int N, bo
     BlockSel sel;
     sel.b[0] = sel.b[1] = sel.b[2] = 0;
     sel.split_time = 0;
+    sel.split_all = is_split_all(h) ? 1 : 0;
     if (interior) {
         sel.nsel = heat ? 2 : 1;
         sel.b[0] = S - 1;

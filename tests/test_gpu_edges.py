@@ -118,3 +118,18 @@ def test_no_hidden_layer_and_single_point():
         opt.step(theta, Xi, f, Xb, g)
         assert rel(theta.cpu().numpy() - th, res.theta_new - th) < 1e-10
         assert opt.sync_status() == "KFAC_OK"
+
+
+def test_split_mode_rejects_unsupported_combinations():
+    # split-BF16 everywhere supports the expand variant with the fixed and
+    # line-search updates only
+    from paper_2405_15603_gb300.api import KfacError
+    for kw in (dict(variant="reduce"), dict(update="kfac_star")):
+        with pytest.raises(KfacError):
+            _opt(3, (16, 1), precision="mixed_split", max_n_int=8, max_n_bdy=8, **kw)
+    opt = _opt(3, (16, 16, 1), precision="mixed_split", max_n_int=8, max_n_bdy=8, update="line_search")
+    prob = si.poisson_cos_problem(3)
+    Xi, f, Xb, g = si.make_batch(prob, 8, 8, seed=3)
+    th = torch.tensor(si.xavier_theta(3, (16, 16, 1), 0), device=DEV)
+    opt.step(th, Xi, f, Xb, g)
+    assert opt.sync_status() == "KFAC_OK"
