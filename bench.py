@@ -236,6 +236,18 @@ def run_gpu(args, rank, world, local_rank):
     print(f"[bench] main arm: {ms / K:.3f} ms/step (instrumented {ms_t / K:.3f}), status {status}, "
           f"classes {tim}", file=sys.stderr, flush=True)
 
+    # ---- the split-BF16-everywhere mode beside it (the mode that meets the
+    # 1e-4 factor / 1e-3 update tolerances against the FP64 oracle) ---------
+    split = None
+    if args.precision == "mixed_bf16":
+        opt_s = new_opt("mixed_split")
+        opt_s.set_graph(True)
+        theta_s = torch.tensor(theta0, device=dev)
+        ms_s, _, _, _ = timed_steps(opt_s, theta_s, dev_batches, W, K)
+        split = {"precision": "mixed_split", "value": replica_value(world, K, reduce_max(ms_s, dev)),
+                 "unit": "steps/s", "ms_per_step": round(ms_s / K, 4), "status": opt_s.sync_status()}
+        opt_s.close()
+
     # ---- end to end through the C-ABI with host buffers -------------------
     import ctypes
     pinned = []
@@ -326,6 +338,8 @@ def run_gpu(args, rank, world, local_rank):
         "kernel_classes": classes, "clocks": clocks, "status": status, "alu_peaks_measured": alu,
         "wall_s_timed": round(wall, 3),
     }
+    if split:
+        out["split_mode"] = split
     if fp64:
         out["fp64_path"] = fp64
         out["speedup_vs_fp64_path"] = round(value / world / fp64["value"], 2)
