@@ -308,10 +308,13 @@ def run_gpu(args, rank, world, local_rank):
             unit, bound = "GB/s", "hbm"
             achieved = per_launch_work / max(per_launch_ms / 1e3, 1e-12) / 1e9
             peak, peak_src = peaks["hbm_gbs"], f"{peak_kind} hbm copy"
-        return {"bound": bound, "achieved": round(achieved, 4), "peak": peak, "unit": unit,
-                "frac": round(achieved / peak, 4), "traffic": None, "kernel_class": name,
-                "per_launch_ms": round(per_launch_ms, 5), "launches": rec["launches"],
-                "peak_source": peak_src}
+        out = {"bound": bound, "achieved": round(achieved, 4), "peak": peak, "unit": unit,
+               "frac": round(achieved / peak, 4), "traffic": None, "kernel_class": name,
+               "per_launch_ms": round(per_launch_ms, 5), "launches": rec["launches"],
+               "peak_source": peak_src}
+        if bound == "tensor":   # the burst figure too (a kernel timed alone)
+            out["frac_of_burst"] = round(achieved / peaks["bf16_tflops"], 4)
+        return out
 
     name, rec = max(tim.items(), key=lambda kv: kv[1]["ms"])
     roofline = class_roofline(name, rec)
