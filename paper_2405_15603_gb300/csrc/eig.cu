@@ -1169,6 +1169,62 @@ __global__ void k_dc_roots(Prob* pr, const Merge* merges, int n_merges, int* fai
     const bool has_up = (j < k - 1);
     const double dj1 = has_up ? dK[j + 1] - dO : 0.0;
     double t = 0.5 * (lo + hi);
+    {
+        // Warm start in FP32 (a reciprocal is one instruction there, a long
+        // FP64 sequence on this part): the same two-pole iteration on an FP32
+        // copy of the bracket, to about 1e-6 relative.  Only its end point is
+        // used, clamped into the FP64 bracket; the FP64 iteration below, whose
+        // bracket moves on FP64 signs only, decides the root.
+        float l32 = (float)lo, h32 = (float)hi, t32 = (float)t;
+        const float dj32 = (float)dj, dj132 = (float)dj1, rh32 = (float)rh;
+        for (int it = 0; it < 16; it++) {
+            float psi = 0.f, dpsi = 0.f, phi = 0.f, dphi = 0.f;
+            for (int q = lane; q < k; q += 32) {
+                const float r = 1.0f / ((float)(dK[q] - dO) - t32);
+                const float z = (float)zK[q];
+                const float tq = z * z * r, dq = tq * r;
+                if (q <= j) { psi += tq; dpsi += dq; } else { phi += tq; dphi += dq; }
+            }
+            for (int o2 = 16; o2 > 0; o2 >>= 1) {
+                psi += __shfl_xor_sync(0xffffffffu, psi, o2);
+                dpsi += __shfl_xor_sync(0xffffffffu, dpsi, o2);
+                phi += __shfl_xor_sync(0xffffffffu, phi, o2);
+                dphi += __shfl_xor_sync(0xffffffffu, dphi, o2);
+            }
+            psi *= rh32; dpsi *= rh32; phi *= rh32; dphi *= rh32;
+            const float fv = 1.f + psi + phi;
+            if (fv > 0.f) h32 = t32; else l32 = t32;
+            const float a1 = dj32 - t32;
+            const float q1 = dpsi * a1 * a1;
+            const float p1 = psi - q1 / a1;
+            float tn = 0.5f * (l32 + h32);
+            if (!has_up) {
+                const float c = 1.f + p1;
+                if (c != 0.f) tn = dj32 + q1 / c;
+            } else {
+                const float a2 = dj132 - t32;
+                const float q2 = dphi * a2 * a2;
+                const float p2 = phi - q2 / a2;
+                const float c = 1.f + p1 + p2;
+                const float B = -(c * (dj32 + dj132) + q1 + q2);
+                const float C = c * dj32 * dj132 + q1 * dj132 + q2 * dj32;
+                if (c == 0.f) {
+                    if (B != 0.f) tn = -C / B;
+                } else {
+                    const float sq = sqrtf(fmaxf(B * B - 4.f * c * C, 0.f));
+                    const float r1 = (-B - copysignf(sq, B)) / (2.f * c);
+                    const float r2 = (r1 != 0.f) ? C / (c * r1) : r1;
+                    if (r1 > l32 && r1 < h32) tn = r1;
+                    else if (r2 > l32 && r2 < h32) tn = r2;
+                }
+            }
+            if (!(tn > l32 && tn < h32)) tn = 0.5f * (l32 + h32);
+            const bool done = fabsf(tn - t32) <= 1e-6f * fabsf(tn);
+            t32 = tn;
+            if (done) break;
+        }
+        if ((double)t32 > lo && (double)t32 < hi) t = (double)t32;
+    }
     for (int it = 0; it < 80; it++) {
         double psi = 0.0, dpsi = 0.0, phi = 0.0, dphi = 0.0, ab = 0.0;
         for (int q = lane; q < k; q += 32) {
