@@ -1285,30 +1285,33 @@ __global__ void k_dc_roots(Prob* pr, const Merge* merges, int n_merges, int* fai
 }
 
 // Gu-Eisenstat: zhat_i^2 = prod_j (lambda_j - d_i) / (rh prod_{j != i} (d_j - d_i)).
+// Gu-Eisenstat: |zhat_i|^2 = (lambda_i - d_i) / rh * prod_{q != i} (lambda_q - d_i) / (d_q - d_i).
+// One warp per root: each lane multiplies its share of the factors, then the
+// lanes' products are multiplied by a butterfly.
 __global__ void k_dc_zhat(Prob* pr, const Merge* merges, int n_merges, int* fail) {
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
     const int last = n_merges - 1;
-    if (gt >= merges[last].r0 + merges[last].s1 + merges[last].s2) return;
-    const int mi = find_merge(merges, n_merges, gt);
+    if (gw >= merges[last].r0 + merges[last].s1 + merges[last].s2) return;
+    const int mi = find_merge(merges, n_merges, gw);
     const Merge mg = merges[mi];
-    const int i = gt - mg.r0;
+    const int i = gw - mg.r0;
     const Prob p = pr[mg.prob];
     if (fail[mg.prob]) return;
     const int a = mg.a;
     const int k = p.mk[a];
-    if (i >= k) return;
+    if (i >= k) return;     // uniform over the warp
     const double rh = p.mrh[a];
     const double* dK = p.dK + a;
     const double* tauR = p.tauR + a;
     const int* org = p.org + a;
     const double di = dK[i];
-    double prod = -((di - dK[org[i]]) - tauR[i]) / rh;   // (lambda_i - d_i) / rh
-    // the factors are O(1) ratios of nearby quantities (interlacing); four
-    // numerators and denominators stay far inside the FP64 range, so one
-    // division serves four factors
-    double num = 1.0, den = 1.0;
+    // the ratio (lambda_q - d_i) / (d_q - d_i) is O(1) by interlacing, while
+    // numerators and denominators alone can be tiny: one division per four
+    // factors keeps every intermediate far inside the FP64 range
+    double prod = 1.0, num = 1.0, den = 1.0;
     int cnt = 0;
-    for (int q = 0; q < k; q++) {
+    for (int q = lane; q < k; q += 32) {
         if (q == i) continue;
         num *= -((di - dK[org[q]]) - tauR[q]);
         den *= dK[q] - di;
@@ -1319,6 +1322,9 @@ __global__ void k_dc_zhat(Prob* pr, const Merge* merges, int n_merges, int* fail
         }
     }
     prod *= num / den;
+    for (int o = 16; o > 0; o >>= 1) prod *= __shfl_xor_sync(0xffffffffu, prod, o);
+    if (lane != 0) return;
+    prod *= -((di - dK[org[i]]) - tauR[i]) / rh;    // (lambda_i - d_i) / rh
     const double z = sqrt(fmax(prod, 0.0));
     p.zh[a + i] = (p.zK[a + i] < 0.0) ? -z : z;
 }
@@ -1978,7 +1984,7 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
             k_dc_roots<<<ceil_div_u((long long)lv.roots * 32, 256), 256, 0, s>>>(pr, lv.merges, lv.n_merges,
                                                                                 es->fail);
             KFAC_LAUNCH_CHECK(h);
-            k_dc_zhat<<<ceil_div_u(lv.roots, 128), 128, 0, s>>>(pr, lv.merges, lv.n_merges, es->fail);
+            k_dc_zhat<<<ceil_div_u((long long)lv.roots * 32, 256), 256, 0, s>>>(pr, lv.merges, lv.n_merges, es->fail);
             KFAC_LAUNCH_CHECK(h);
             k_dc_order<<<lv.n_merges, 256, 0, s>>>(pr, lv.merges, es->fail);
             KFAC_LAUNCH_CHECK(h);
