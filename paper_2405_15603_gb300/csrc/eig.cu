@@ -1071,8 +1071,88 @@ __global__ void __launch_bounds__(256) k_dc_prepare(Prob* pr, const Merge* merge
     const double rzn = 1.0 / zn;
     for (int i = threadIdx.x; i < m; i += blockDim.x) zs[i] *= rzn;
     __syncthreads();
+    const double tol = 8.0 * DEPS * fmax(dmax, rh);
+    // Speculative parallel deflation: the magnitude test per entry, then the
+    // pair test of every surviving entry against the previous survivor on the
+    // unmodified values.  When no pair deflates, that is exactly what the
+    // serial scan below computes (its values only change at a pair deflation),
+    // so the survivors are compacted in parallel; otherwise the serial scan
+    // runs.  Each thread takes four consecutive entries (m <= 1024).
+    if (m <= 4 * (int)blockDim.x) {
+        __shared__ int wsh[32];
+        const int i0 = 4 * threadIdx.x;
+        bool small[4];
+        int mylast = -1, mycnt = 0;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int i = i0 + u;
+            small[u] = (i >= m) || (rh * fabs(zs[i]) <= tol);
+            if (!small[u]) { mylast = i; mycnt++; }
+        }
+        // exclusive max-scan of the last survivor over the threads
+        const int lane = threadIdx.x % 32, wid = threadIdx.x / 32, nw = blockDim.x / 32;
+        int incl = mylast;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl = max(incl, y);
+        }
+        if (lane == 31) wsh[wid] = incl;
+        __syncthreads();
+        int before = -1;
+        for (int w = 0; w < wid; w++) before = max(before, wsh[w]);
+        const int up = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane > 0) before = max(before, up);
+        __syncthreads();
+        bool pair = false;
+        int last = before;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int i = i0 + u;
+            if (small[u]) continue;
+            if (last >= 0) {
+                const int j = last;
+                const double r2 = fma(zs[j], zs[j], zs[i] * zs[i]);
+                if (fabs(zs[i] * zs[j] * (Ds[i] - Ds[j])) <= tol * r2) pair = true;
+            }
+            last = i;
+        }
+        if (!__syncthreads_or(pair ? 1 : 0)) {
+            // exclusive sum-scan of the survivor counts: the compaction
+            int incs = mycnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incs, o);
+                if (lane >= o) incs += y;
+            }
+            if (lane == 31) wsh[wid] = incs;
+            __syncthreads();
+            int base = 0, total = 0;
+            for (int w = 0; w < nw; w++) {
+                if (w < wid) base += wsh[w];
+                total += wsh[w];
+            }
+            int kpos = base + incs - mycnt;
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int i = i0 + u;
+                if (i >= m) break;
+                p.defl[a + i] = small[u] ? 1 : 0;
+                if (!small[u]) {
+                    p.Kidx[a + kpos] = i;
+                    p.dK[a + kpos] = Ds[i];
+                    p.zK[a + kpos] = zs[i];
+                    kpos++;
+                }
+            }
+            if (threadIdx.x == 0) {
+                p.mk[a] = total;
+                p.mnrot[a] = 0;
+                p.mflip[a] = flip ? 1 : 0;
+                p.mrh[a] = rh;
+            }
+            return;
+        }
+    }
     if (threadIdx.x == 0) {
-        const double tol = 8.0 * DEPS * fmax(dmax, rh);
         int* defl = p.defl + a;
         int nrot = 0, last = -1;
         for (int i = 0; i < m; i++) {
