@@ -118,8 +118,11 @@ typedef struct {
     int max_n_int;                 /* capacity: interior points per call (>= 1)        */
     int max_n_bdy;                 /* capacity: boundary points per call (>= 1)        */
     int update;                    /* kfac_update_t of kfac_pinn_step                  */
-    int eig_sm_budget;             /* SMs the cooperative tridiagonalisation of the
-                                      inverse may occupy (0: all).  Handles stepped
+    int eig_sm_budget;             /* SMs the cooperative tridiagonalisation may
+                                      occupy (0: all).  It is used only for factors too
+                                      large for one thread-block cluster's shared memory
+                                      (h_l + 1 above about 890); the others run one
+                                      cluster per factor pair.  Handles stepped
                                       concurrently (kfac_pinn_batch_step) should split
                                       the GPU between them.                          */
     const double* op_coef;         /* GENERAL: host pointer to the d x d coefficient
@@ -215,7 +218,9 @@ kfac_status_t kfac_pinn_factors(kfac_handle_t h, void* stream, const double* the
  * diagonalisation V^T A~_Omega V = I, V^T A~_bdy V = diag(a) through an FP64
  * Cholesky of A~_Omega and an FP64 symmetric eigendecomposition of the
  * whitened A~_bdy; likewise for B.  A factor that is not positive definite
- * latches KFAC_NOT_PD. */
+ * latches KFAC_NOT_PD.  Part of the work runs on a stream of the handle's own,
+ * forked from `stream` and joined back into it: the call stays ordered with
+ * the rest of `stream` (and is captured with it). */
 kfac_status_t kfac_pinn_invert(kfac_handle_t h, void* stream);
 
 /* direction = -(A~_Omega x B~_Omega + A~_bdy x B~_bdy)^{-1} grad per layer,
