@@ -100,6 +100,11 @@ struct MxState {
     MxWeights dw;       // KFAC*: the direction converted like the weights
     bool have_dw;
     float* jdad[KFAC_MAX_LAYERS];   // KFAC*: da_D of the second-order row per hidden layer (N_pad x hp)
+    // the boundary pass runs beside the interior pass (they share only the
+    // read-only weights): a stream of its own, forked from the caller's and
+    // joined back
+    cudaStream_t side;
+    cudaEvent_t fork, join;
 };
 
 MxState* MX(kfac_pinn_handle* h) { return (MxState*)h->mx; }
@@ -1367,6 +1372,10 @@ kfac_status_t tc_alloc(kfac_pinn_handle* h) {
     if ((st = dal(&m->gpart, 2 * m->gpart_region))) return st;
     if ((st = dal(&m->cs, 2 * ((size_t)hp_max + 8)))) return st;
     if ((st = dal(&m->seed, (size_t)h->S * m->in.N_pad))) return st;
+    if (cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->join, cudaEventDisableTiming) != cudaSuccess)
+        return KFAC_CUDA_ERROR;
     return KFAC_OK;
 }
 
@@ -1384,6 +1393,12 @@ void tc_free(kfac_pinn_handle* h) {
     cudaFree(m->part);
     cudaFree(m->gpart);
     cudaFree(m->cs);
+    if (m->side) {
+        cudaStreamSynchronize(m->side);
+        cudaStreamDestroy(m->side);
+    }
+    if (m->fork) cudaEventDestroy(m->fork);
+    if (m->join) cudaEventDestroy(m->join);
     free(m);
     h->mx = nullptr;
 }
@@ -1398,6 +1413,28 @@ kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const d
     const int S = m->in.S;
     const int heat = h->cfg.op == KFAC_OP_HEAT;
     if ((st = convert_weights(h, s, theta))) return st;
+    // boundary pass on the side stream: it fills the SMs the interior pass's
+    // value GEMMs leave idle (its grids are N_bdy / 128 point blocks wide)
+    BlockSel sb;
+    sb.nsel = 1;
+    sb.b[0] = 0;
+    sb.b[1] = sb.b[2] = 0;
+    sb.split_time = 0;
+    sb.split_all = is_split_all(h) ? 1 : 0;
+    KFAC_CUDA_TRY(cudaEventRecord(m->fork, s));
+    KFAC_CUDA_TRY(cudaStreamWaitEvent(m->side, m->fork, 0));
+    st = forward_pass(h, m->side, theta, X_bdy, N_bdy, m->bd, sb);
+    if (st == KFAC_OK) {
+        k_residual_mx<<<ceil_div_u(N_bdy, EW), EW, 0, m->side>>>(m->bd.zl, g, h->bd.r, N_bdy, m->bd.N_pad, 1, 0,
+                                                                 h->cT, h->cD);
+        KFAC_LAUNCH_CHECK(h);
+    }
+    // the join is recorded even after an error, so that s never runs ahead of the side stream
+    KFAC_CUDA_TRY(cudaEventRecord(m->join, m->side));
+    if (st) {
+        KFAC_CUDA_TRY(cudaStreamWaitEvent(s, m->join, 0));
+        return st;
+    }
     // interior: the residual needs the Laplacian row (and the time row for heat)
     BlockSel si;
     si.nsel = heat ? 2 : 1;
@@ -1406,21 +1443,14 @@ kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const d
     si.b[2] = 0;
     si.split_time = heat;
     si.split_all = is_split_all(h) ? 1 : 0;
-    if ((st = forward_pass(h, s, theta, X_int, N_int, m->in, si))) return st;
-    k_residual_mx<<<ceil_div_u(N_int, EW), EW, 0, s>>>(m->in.zl, f, h->in.r, N_int, m->in.N_pad, S, 1, h->cT,
-                                                        h->cD);
-    KFAC_LAUNCH_CHECK(h);
-    BlockSel sb;
-    sb.nsel = 1;
-    sb.b[0] = 0;
-    sb.b[1] = sb.b[2] = 0;
-    sb.split_time = 0;
-    sb.split_all = is_split_all(h) ? 1 : 0;
-    if ((st = forward_pass(h, s, theta, X_bdy, N_bdy, m->bd, sb))) return st;
-    k_residual_mx<<<ceil_div_u(N_bdy, EW), EW, 0, s>>>(m->bd.zl, g, h->bd.r, N_bdy, m->bd.N_pad, 1, 0, h->cT,
-                                                        h->cD);
-    KFAC_LAUNCH_CHECK(h);
-    return KFAC_OK;
+    st = forward_pass(h, s, theta, X_int, N_int, m->in, si);
+    if (st == KFAC_OK) {
+        k_residual_mx<<<ceil_div_u(N_int, EW), EW, 0, s>>>(m->in.zl, f, h->in.r, N_int, m->in.N_pad, S, 1, h->cT,
+                                                            h->cD);
+        KFAC_LAUNCH_CHECK(h);
+    }
+    KFAC_CUDA_TRY(cudaStreamWaitEvent(s, m->join, 0));
+    return st;
 }
 
 }  // namespace
