@@ -1461,8 +1461,15 @@ kfac_status_t tc_factors(kfac_pinn_handle* h, cudaStream_t s, const double* thet
     kfac_status_t st;
     if ((st = forward_and_residuals(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g))) return st;
     if ((st = fp64_loss(h, s, N_int, N_bdy, loss))) return st;
-    if ((st = backward_pass(h, s, h->in.r, N_int, m->in))) return st;
-    if ((st = backward_pass(h, s, h->bd.r, N_bdy, m->bd))) return st;
+    // the boundary adjoint beside the interior one (disjoint buffers)
+    KFAC_CUDA_TRY(cudaEventRecord(m->fork, s));
+    KFAC_CUDA_TRY(cudaStreamWaitEvent(m->side, m->fork, 0));
+    const kfac_status_t sb = backward_pass(h, m->side, h->bd.r, N_bdy, m->bd);
+    KFAC_CUDA_TRY(cudaEventRecord(m->join, m->side));
+    st = backward_pass(h, s, h->in.r, N_int, m->in);
+    KFAC_CUDA_TRY(cudaStreamWaitEvent(s, m->join, 0));
+    if (sb) return sb;
+    if (st) return st;
     return factors_and_grad(h, s, X_int, N_int, X_bdy, N_bdy);
 }
 
