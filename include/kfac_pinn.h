@@ -200,9 +200,9 @@ kfac_status_t kfac_pinn_set_store_forward(kfac_handle_t h, int enable);
  * disabled.  Errors: KFAC_BAD_ARG for a NULL handle. */
 kfac_status_t kfac_pinn_set_graph(kfac_handle_t h, int enable);
 
-/* Curvature and gradient of one batch (App. B, Algorithm 1, steps 1, 2 and
- * 4): forward Laplacian on the interior points and plain forward pass on the
- * boundary points, residuals and loss (Eq. 1), one backward pass each for
+/* Curvature and gradient of one batch (App. B, Algorithm 1): forward
+ * Laplacian on the interior points and plain forward pass on the boundary
+ * points, residuals and loss (Eq. 1), one backward pass each for
  * g^{(l)} (Sec. 3.2), the loss gradient, the Kronecker factors (Eq. 8 or
  * KFAC-reduce; Eq. 3) and their exponential moving average (Sec. 3.4).
  * loss: 3 device doubles (L, L_Omega, L_boundary), may be NULL.  The gradient
@@ -213,7 +213,7 @@ kfac_status_t kfac_pinn_factors(kfac_handle_t h, void* stream, const double* the
                                 const double* X_bdy, int N_bdy, const double* g,
                                 double* loss);
 
-/* Damped inverse of the Kronecker sum (Sec. 3.4; App. B step 3): for every
+/* Damped inverse of the Kronecker sum (Sec. 3.4; App. B): for every
  * layer, with A~ = A^ + lambda I (or sqrt(lambda) I), the simultaneous
  * diagonalisation V^T A~_Omega V = I, V^T A~_bdy V = diag(a) through an FP64
  * Cholesky of A~_Omega and an FP64 symmetric eigendecomposition of the

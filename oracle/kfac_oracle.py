@@ -163,7 +163,7 @@ def append_bias_row(T: np.ndarray) -> np.ndarray:
 
 def taylor_forward(Ws: Sequence[np.ndarray], X: np.ndarray, op: str = "laplace",
                    with_derivatives: bool = True, coef: Optional[np.ndarray] = None) -> TaylorPass:
-    """Forward Laplacian with intermediates (App. B step 1; App. C.2).
+    """Forward Laplacian with intermediates (App. B; App. C.2).
 
     Z^{(l)} = W̃_l T̂^{(l-1)}; for l < L the tanh rule gives T^{(l)} and its
     bias row is appended.  With with_derivatives=False this is the plain
@@ -289,7 +289,7 @@ def taylor_adjoint(Ws: Sequence[np.ndarray], fp: TaylorPass, seed: np.ndarray,
 
 
 # ---------------------------------------------------------------------------
-# Gradient of the loss (App. B step 4)
+# Gradient of the loss (App. B)
 # ---------------------------------------------------------------------------
 
 
@@ -358,7 +358,7 @@ def generalized_eig(P: np.ndarray, Q: np.ndarray) -> Tuple[np.ndarray, np.ndarra
 
 
 def kron_sum_inverse_apply(A_i, B_i, A_b, B_b, G, lam, damping_sqrt=False):
-    """Δ = -(Ã_Ω ⊗ B̃_Ω + Ã_∂ ⊗ B̃_∂)⁻¹ vec G, returned as a matrix (App. B step 3-4).
+    """Δ = -(Ã_Ω ⊗ B̃_Ω + Ã_∂ ⊗ B̃_∂)⁻¹ vec G, returned as a matrix (App. B).
 
     With V_A, a from (Ã_Ω, Ã_∂) and V_B, b from (B̃_Ω, B̃_∂):
     Δ = -V_B [(V_Bᵀ G V_A) ⊘ (1 + b aᵀ)] V_Aᵀ, using vec(BXA) = (Aᵀ ⊗ B) vec X."""
@@ -423,7 +423,7 @@ class StepResult:
 
 
 def curvature_and_gradient(cfg: KfacConfig, Ws, X_int, f, X_bdy, g):
-    """App. B steps 1, 2 and 4 (without the preconditioner)."""
+    """App. B (without the preconditioner)."""
     fp_i = taylor_forward(Ws, X_int, cfg.op, True, cfg.op_coef)
     r_i = interior_residual(fp_i, f, cfg.op, cfg.kappa)
     zb_i = taylor_adjoint(Ws, fp_i, residual_seed(fp_i.S, cfg.op, cfg.kappa, True), cfg.op, cfg.op_coef)
@@ -454,7 +454,7 @@ LINE_SEARCH_GRID = tuple(2.0 ** -k for k in range(31))   # {2^0, 2^-1, .., 2^-30
 
 
 def line_search(cfg: KfacConfig, theta: np.ndarray, dhat: np.ndarray, X_int, f, X_bdy, g):
-    """α* = argmin_α L(θ + α δ̂) over the logarithmic grid (Sec. 3.4; App. B step 5).
+    """α* = argmin_α L(θ + α δ̂) over the logarithmic grid (Sec. 3.4; App. B).
 
     Returns (α*, losses) with losses[k] = L(θ + 2^-k δ̂) as (L, L_Ω, L_∂).  Equal
     losses keep the larger α; non-finite losses never win; α* = 0 when no

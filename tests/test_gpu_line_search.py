@@ -1,5 +1,5 @@
 """GPU parity of the KFAC update with momentum and log-grid line search
-(Sec. 3.4; App. B step 5): δ̂ = μ δ_{t-1} + Δ_t, α* = argmin over
+(Sec. 3.4; App. B): δ̂ = μ δ_{t-1} + Δ_t, α* = argmin over
 {2^0, .., 2^-30} of L(θ + α δ̂) on the step's batch, θ += α* δ̂.
 
 FP64 path: trial losses to 1e-10, parameters to 1e-8 over several steps.

@@ -463,7 +463,7 @@ def test_kfac_direction_is_descent_poisson2d():
 
 
 # --------------------------------------------------------------------------
-# Log-grid line search (Sec. 3.4; App. B step 5)
+# Log-grid line search (Sec. 3.4; App. B)
 # --------------------------------------------------------------------------
 def _linear_loss_closed_form(w, b, Xi, f, Xb, g):
     # u = wᵀx + b has Δu = 0, so the Poisson residuals are r_Ω = -f and
