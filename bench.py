@@ -218,6 +218,8 @@ def run_gpu(args, rank, world, local_rank):
     # ---- main arm: steps replayed as a CUDA graph, no instrumentation ------
     opt = new_opt(args.precision)
     opt.set_graph(True)
+    if not args.no_autotune:
+        opt.set_autotune(True)          # measured on the first (eager) warm-up step
     theta = torch.tensor(theta0, device=dev)
     sampler = ClockSampler(local_rank)
     sampler.start()
@@ -226,10 +228,19 @@ def run_gpu(args, rank, world, local_rank):
     status = opt.sync_status()
     ms_max = reduce_max(ms, dev)
     value = replica_value(world, K, ms_max)
+    table = opt.tuning()
+    tuning = None
+    if table:
+        tuning = {"gram_shapes": len(table),
+                  "changed_from_model": sum(e["row_chunk"] != e["model_row_chunk"] for e in table),
+                  "tuned_us_sum": round(sum(e["us"] for e in table), 2),
+                  "model_us_sum": round(sum(e["model_us"] for e in table), 2),
+                  "how": "first warm-up step: model's row chunk and 3 runners-up, 1 warm + 3 timed launches each"}
     # ---- kernel classes: the same K steps again, eager, every launch
     # bracketed by CUDA events on its stream (the events cost ~3 % of a step,
     # which is why the headline above is timed without them)
     opt_t = new_opt(args.precision)
+    opt_t.set_tuning(table)
     theta_t = torch.tensor(theta0, device=dev)
     ms_t, _, _, tim = timed_steps(opt_t, theta_t, dev_batches, W, K, timing=True)
     opt_t.close()
@@ -242,6 +253,8 @@ def run_gpu(args, rank, world, local_rank):
     if args.precision == "mixed_bf16":
         opt_s = new_opt("mixed_split")
         opt_s.set_graph(True)
+        if not args.no_autotune:
+            opt_s.set_autotune(True)
         theta_s = torch.tensor(theta0, device=dev)
         ms_s, _, _, _ = timed_steps(opt_s, theta_s, dev_batches, W, K)
         split = {"precision": "mixed_split", "value": replica_value(world, K, reduce_max(ms_s, dev)),
@@ -256,6 +269,7 @@ def run_gpu(args, rank, world, local_rank):
     theta_e = torch.tensor(theta0, device=dev)
     opt_e = new_opt(args.precision)
     opt_e.set_graph(True)
+    opt_e.set_tuning(table)
     loss_host = np.zeros(3)
     for k in range(W):
         opt_e.step_host(theta_e, *pinned[k], loss_host=loss_host)
@@ -341,6 +355,8 @@ def run_gpu(args, rank, world, local_rank):
         "kernel_classes": classes, "clocks": clocks, "status": status, "alu_peaks_measured": alu,
         "wall_s_timed": round(wall, 3),
     }
+    if tuning:
+        out["gram_autotune"] = tuning
     if split:
         out["split_mode"] = split
     if fp64:
@@ -651,6 +667,8 @@ def main():
     ap.add_argument("--precision", default="mixed_bf16", choices=["fp64", "mixed_bf16", "mixed_split"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="Gram row chunks from the wave model instead of measured on the first warm-up step")
     ap.add_argument("--e10", action="store_true",
                     help="forward vs autodiff Laplacian time and memory (App. C.4) instead of the step bench")
     ap.add_argument("--equal-l2", type=int, default=0, metavar="STEPS",

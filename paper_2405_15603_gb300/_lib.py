@@ -20,8 +20,10 @@ EXPORTS = [
     "kfac_pinn_get_update_coefficients", "kfac_pinn_batch_create", "kfac_pinn_batch_destroy",
     "kfac_pinn_batch_step", "kfac_pinn_last_cuda_error", "kfac_pinn_last_cuda_error_string",
     "kfac_pinn_set_store_forward",
-    "kfac_pinn_set_graph",
+    "kfac_pinn_set_graph", "kfac_pinn_set_autotune", "kfac_pinn_get_tuning", "kfac_pinn_set_tuning",
 ]
+
+KFAC_TUNE_CAP = 128
 
 KERNEL_CLASSES = {0: "layer_gemm", 1: "adjoint_gemm", 2: "gram", 3: "elementwise", 4: "eig", 5: "precond"}
 
@@ -34,6 +36,13 @@ class KfacConfig(C.Structure):
         ("factor_init_identity", C.c_int), ("lr", C.c_double), ("momentum", C.c_double),
         ("max_n_int", C.c_int), ("max_n_bdy", C.c_int), ("update", C.c_int), ("eig_sm_budget", C.c_int),
         ("op_coef", C.c_void_p),
+    ]
+
+
+class KfacTuneEntry(C.Structure):
+    _fields_ = [
+        ("P", C.c_int), ("Q", C.c_int), ("rows", C.c_int), ("sym", C.c_int), ("split", C.c_int),
+        ("row_chunk", C.c_int), ("model_row_chunk", C.c_int), ("us", C.c_float), ("model_us", C.c_float),
     ]
 
 
@@ -88,6 +97,9 @@ def load() -> C.CDLL:
         "kfac_pinn_last_cuda_error": (I, []),
         "kfac_pinn_set_store_forward": (st, [H, I]),
         "kfac_pinn_set_graph": (st, [H, I]),
+        "kfac_pinn_set_autotune": (st, [H, I]),
+        "kfac_pinn_get_tuning": (st, [H, C.POINTER(KfacTuneEntry), I, C.POINTER(C.c_int)]),
+        "kfac_pinn_set_tuning": (st, [H, C.POINTER(KfacTuneEntry), I]),
         "kfac_pinn_last_cuda_error_string": (C.c_char_p, []),
         "kfac_pinn_batch_create": (st, [P, I, I, C.POINTER(C.c_void_p)]),
         "kfac_pinn_batch_destroy": (st, [P]),

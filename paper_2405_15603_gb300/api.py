@@ -144,6 +144,27 @@ class KfacPinn:
         captured and later ones replay it; results are bit-identical."""
         _check("kfac_pinn_set_graph", self.lib.kfac_pinn_set_graph(self.h, int(enable)))
 
+    def set_autotune(self, enable: bool = True):
+        """Time candidate row-chunk lengths of each new Gram shape on the next
+        eager step and keep the fastest (kfac_pinn_set_autotune)."""
+        _check("kfac_pinn_set_autotune", self.lib.kfac_pinn_set_autotune(self.h, int(enable)))
+
+    def tuning(self) -> list:
+        """The handle's tuning table, one dict per Gram shape."""
+        n = C.c_int()
+        _check("kfac_pinn_get_tuning", self.lib.kfac_pinn_get_tuning(self.h, None, 0, C.byref(n)))
+        arr = (_lib.KfacTuneEntry * max(n.value, 1))()
+        _check("kfac_pinn_get_tuning", self.lib.kfac_pinn_get_tuning(self.h, arr, n.value, C.byref(n)))
+        return [{k: getattr(e, k) for k, _ in _lib.KfacTuneEntry._fields_} for e in arr[:n.value]]
+
+    def set_tuning(self, table: Sequence[dict]):
+        """Replace the tuning table (e.g. by another handle's tuning())."""
+        arr = (_lib.KfacTuneEntry * max(len(table), 1))()
+        for e, t in zip(arr, table):
+            for k, _ in _lib.KfacTuneEntry._fields_:
+                setattr(e, k, t.get(k, 0))
+        _check("kfac_pinn_set_tuning", self.lib.kfac_pinn_set_tuning(self.h, arr, len(table)))
+
     def factors(self, theta, X_int, f, X_bdy, g) -> torch.Tensor:
         X_int, f, X_bdy, g = (_dev(a, self.device) for a in (X_int, f, X_bdy, g))
         _check("kfac_pinn_factors", self.lib.kfac_pinn_factors(

@@ -177,6 +177,8 @@ void free_handle(kfac_pinn_handle* h) {
     cudaFree(h->tmp);
     cudaFree(h->status);
     cudaFree(h->stage);
+    for (cudaEvent_t e : h->tune_ev)
+        if (e) cudaEventDestroy(e);
     free(h);
 }
 
@@ -568,6 +570,40 @@ kfac_status_t kfac_pinn_set_graph(kfac_handle_t h, int enable) {
     if (!h) return KFAC_BAD_ARG;
     h->graph_mode = enable ? 1 : 0;
     if (!enable) handle_graph_free(h);
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_set_autotune(kfac_handle_t h, int enable) {
+    if (!h) return KFAC_BAD_ARG;
+    h->autotune = enable ? 1 : 0;
+    if (enable) handle_graph_free(h);
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_get_tuning(kfac_handle_t h, kfac_tune_entry_t* out, int cap, int* count) {
+    if (!h || !count || cap < 0 || (cap > 0 && !out)) return KFAC_BAD_ARG;
+    const int n = h->n_tune < cap ? h->n_tune : cap;
+    if (n > 0) memcpy(out, h->tune, (size_t)n * sizeof(kfac_tune_entry_t));
+    *count = h->n_tune;
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_set_tuning(kfac_handle_t h, const kfac_tune_entry_t* in, int count) {
+    if (!h || count < 0 || count > KFAC_TUNE_CAP || (count > 0 && !in)) return KFAC_BAD_ARG;
+    for (int i = 0; i < count; i++) {
+        const kfac_tune_entry_t& e = in[i];
+        const long long top = ((long long)e.rows + 63) / 64 * 64;
+        if (e.P < 1 || e.Q < 1 || e.rows < 1 || (e.sym != 0 && e.sym != 1) || (e.split != 0 && e.split != 1) ||
+            e.row_chunk < 64 || e.row_chunk % 64 != 0 || e.row_chunk > top)
+            return KFAC_BAD_ARG;
+    }
+    for (int i = 0; i < count; i++) {
+        h->tune[i] = in[i];
+        h->tune[i].us = 0.f;
+        h->tune[i].model_us = 0.f;
+    }
+    h->n_tune = count;
+    handle_graph_free(h);
     return KFAC_OK;
 }
 

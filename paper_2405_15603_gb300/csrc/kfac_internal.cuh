@@ -103,6 +103,11 @@ struct kfac_pinn_handle {
     int graph_mode;
     int in_graph;
     struct kfac_pinn_batch* gbatch;
+    // Gram tile autotuner (kfac_pinn_set_autotune): measured row-chunk lengths
+    int autotune;
+    int n_tune;
+    kfac_tune_entry_t tune[KFAC_TUNE_CAP];
+    cudaEvent_t tune_ev[2];
     int fwd_valid;
     const double* fwd_theta;
     const double* fwd_X;

@@ -967,6 +967,15 @@ void free_pass(MxPass& P) {
 // Gram over rows: part[z][p][q] = sum_{rows in chunk z} X[row][p] Y[row][q].
 // With X_lo and Y_lo (split-BF16 everywhere) the three products
 // X_hi^T Y_hi + X_hi^T Y_lo + X_lo^T Y_hi are accumulated.
+//
+// The row-chunk length comes from the handle's tuning table when it holds
+// this shape, else from the wave model (full waves of one CTA per SM, even
+// chunks; ties keep fewer chunks).  With autotuning enabled and the stream
+// not capturing, an unseen shape is timed at the model's length and up to
+// three runners-up, and the fastest is recorded.
+constexpr int TUNE_CANDIDATES = 4;
+constexpr int TUNE_REPS = 3;
+
 kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, const CUtensorMap& Y, int P, int Q,
                    int rows, int sym, float* part, int& nz, const CUtensorMap* X_lo = nullptr,
                    const CUtensorMap* Y_lo = nullptr) {
@@ -974,22 +983,41 @@ kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, co
     int p_tiles = (P + 127) / 128, q_tiles = (Q + C::BN - 1) / C::BN;
     int tiles = 0;
     for (int pb = 0; pb < p_tiles; pb++) tiles += q_tiles - (sym ? (pb * 128) / C::BN : 0);
-    // split-K over the rows: full waves of one CTA per SM and even chunks
     int max_chunks = (int)(MX(h)->gpart_region / ((size_t)P * Q));
     if (max_chunks > MAX_GRAM_CHUNKS) max_chunks = MAX_GRAM_CHUNKS;
     if (max_chunks < 1) return KFAC_BAD_ARG;
-    int chunk = round_up(rows, 64);
-    double best = -1.0;
+    const int split = (X_lo && Y_lo) ? 1 : 0;
+    // candidate chunk lengths with their modelled efficiency; every candidate
+    // needs at most max_chunks chunks
+    int cand[MAX_GRAM_CHUNKS];
+    double eff[MAX_GRAM_CHUNKS];
+    int nc = 0, model = 0;
     for (int want = 1; want <= max_chunks; want++) {
         const int c = round_up((rows + want - 1) / want, 64);
         const int cnt = (rows + c - 1) / c;
         const double e = wave_efficiency((long long)tiles * cnt, h->sm_count) * (double)rows / ((double)cnt * c);
-        if (e > best + 1e-9) {
-            best = e;
-            chunk = c;
+        bool seen = false;
+        for (int i = 0; i < nc; i++) seen = seen || cand[i] == c;
+        if (seen) continue;
+        cand[nc] = c;
+        eff[nc] = e;
+        if (e > eff[model] + 1e-9) model = nc;
+        nc++;
+    }
+    int chunk = cand[model];
+    int tuned = -1;
+    for (int i = 0; i < h->n_tune; i++) {
+        const kfac_tune_entry_t& t = h->tune[i];
+        if (t.P == P && t.Q == Q && t.rows == rows && t.sym == sym && t.split == split) {
+            tuned = i;
+            break;
         }
     }
-    nz = (rows + chunk - 1) / chunk;
+    if (tuned >= 0) {
+        const int c = h->tune[tuned].row_chunk;
+        if (c >= 64 && c % 64 == 0 && c <= round_up(rows, 64) && (rows + c - 1) / c <= max_chunks) chunk = c;
+    }
+
     Args a;
     memset(&a, 0, sizeof(a));
     a.a0 = X;
@@ -997,17 +1025,71 @@ kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, co
     a.P = P;
     a.Q = Q;
     a.rows = rows;
-    a.row_chunk = chunk;
     a.sym = sym;
     a.q_tiles = q_tiles;
     a.part = part;
     a.status = h->status;
-    if (X_lo && Y_lo) {
+    if (split) {
         a.a1 = *X_lo;
         a.b1 = *Y_lo;
         a.split_all = 1;
     }
     double work = 2.0 * (double)tiles * 128 * C::BN * rows;   // algorithmic: one product per entry
+
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (tuned < 0 && h->autotune && h->n_tune < KFAC_TUNE_CAP && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+        cs == cudaStreamCaptureStatusNone) {
+        // the model's choice first, then the runners-up by modelled efficiency
+        int order[TUNE_CANDIDATES];
+        int no = 0;
+        order[no++] = model;
+        while (no < TUNE_CANDIDATES && no < nc) {
+            int best = -1;
+            for (int i = 0; i < nc; i++) {
+                bool used = false;
+                for (int j = 0; j < no; j++) used = used || order[j] == i;
+                if (!used && (best < 0 || eff[i] > eff[best] + 1e-9)) best = i;
+            }
+            order[no++] = best;
+        }
+        for (cudaEvent_t& e : h->tune_ev)
+            if (!e) KFAC_CUDA_TRY(cudaEventCreate(&e));
+        float t_best = 0.f, t_model = 0.f;
+        int c_best = cand[model];
+        for (int k = 0; k < no; k++) {
+            const int c = cand[order[k]];
+            a.row_chunk = c;
+            const dim3 grid(tiles, (rows + c - 1) / c, 1);
+            kfac_status_t st = launch_engine<tck::GRAM>(h, s, a, grid, KFAC_KC_GRAM, work);   // warm-up
+            if (st) return st;
+            KFAC_CUDA_TRY(cudaEventRecord(h->tune_ev[0], s));
+            for (int r = 0; r < TUNE_REPS; r++)
+                if ((st = launch_engine<tck::GRAM>(h, s, a, grid, KFAC_KC_GRAM, work))) return st;
+            KFAC_CUDA_TRY(cudaEventRecord(h->tune_ev[1], s));
+            KFAC_CUDA_TRY(cudaEventSynchronize(h->tune_ev[1]));
+            float ms = 0.f;
+            KFAC_CUDA_TRY(cudaEventElapsedTime(&ms, h->tune_ev[0], h->tune_ev[1]));
+            const float us = 1000.f * ms / TUNE_REPS;
+            if (k == 0) t_model = us;
+            if (k == 0 || us < t_best) {
+                t_best = us;
+                c_best = c;
+            }
+        }
+        kfac_tune_entry_t& t = h->tune[h->n_tune++];
+        t.P = P;
+        t.Q = Q;
+        t.rows = rows;
+        t.sym = sym;
+        t.split = split;
+        t.row_chunk = c_best;
+        t.model_row_chunk = cand[model];
+        t.us = t_best;
+        t.model_us = t_model;
+        chunk = c_best;
+    }
+    nz = (rows + chunk - 1) / chunk;
+    a.row_chunk = chunk;
     return launch_engine<tck::GRAM>(h, s, a, dim3(tiles, nz, 1), KFAC_KC_GRAM, work);
 }
 
