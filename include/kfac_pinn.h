@@ -217,7 +217,8 @@ kfac_status_t kfac_pinn_set_graph(kfac_handle_t h, int enable);
  * orders: results agree to FP32 rounding, not bit for bit.  Nothing is
  * measured while the stream is being captured into a graph.  Enabling frees
  * the handle's graph (kfac_pinn_set_graph), so the next step runs eagerly
- * and measures.  The FP64 precision has no tuned launches.  Default:
+ * and measures; a kfac_pinn_batch holding the handle keeps the lengths its
+ * graph was captured with until it re-captures.  The FP64 precision has no tuned launches.  Default:
  * disabled.  Errors: KFAC_BAD_ARG for a NULL handle. */
 #define KFAC_TUNE_CAP 128
 typedef struct {
