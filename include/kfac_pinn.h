@@ -200,38 +200,50 @@ kfac_status_t kfac_pinn_set_store_forward(kfac_handle_t h, int enable);
  * disabled.  Errors: KFAC_BAD_ARG for a NULL handle. */
 kfac_status_t kfac_pinn_set_graph(kfac_handle_t h, int enable);
 
-/* Tile autotuner of the Gram contractions of the tensor-core precisions (the
- * Kronecker factors of Eq. 8 and Eq. 3 and the weight gradient; no
- * counterpart in the paper: a runtime option).  A Gram over K = S * N_cap
- * rows (N_cap = max_n_int or max_n_bdy rounded up to 128) is split into row
- * chunks, one CTA per (output tile, chunk), whose FP32 partial sums are then
- * added in a fixed order.  By default the chunk length comes from a wave
- * model: full waves of one CTA per SM and chunks of equal length.  While
- * autotuning is enabled, the first eager call that meets a Gram shape not yet
- * in the handle's table times the model's chunk length and up to three
- * runners-up by the model (one warm-up and three timed launches each, CUDA
- * events on the launching stream, which the host then waits for), records
- * the fastest and computes the Gram with it; later launches of that shape
- * use the recorded length, so results are deterministic once the table is
- * filled.  Different chunk lengths add the partial sums in different
- * orders: results agree to FP32 rounding, not bit for bit.  Nothing is
- * measured while the stream is being captured into a graph.  Enabling frees
- * the handle's graph (kfac_pinn_set_graph), so the next step runs eagerly
- * and measures; a kfac_pinn_batch holding the handle keeps the lengths its
- * graph was captured with until it re-captures.  The FP64 precision has no tuned launches.  Default:
- * disabled.  Errors: KFAC_BAD_ARG for a NULL handle. */
+/* Autotuner of the split-K partitions of the tensor-core precisions (no
+ * counterpart in the paper: a runtime option).  Three kinds of launch are
+ * split into chunks, one CTA per (output tile, chunk), whose FP32 partial
+ * sums are then added in a fixed order:
+ *   KFAC_TUNE_GRAM     the Grams of the Kronecker factors (Eq. 8, Eq. 3) and
+ *                      the weight-gradient contractions: their K = S * N_cap
+ *                      rows (N_cap = max_n_int or max_n_bdy rounded up to
+ *                      128) are split into row chunks;
+ *   KFAC_TUNE_FWD_TAN  the layer GEMM of the tangent and Laplacian columns of
+ *                      the Taylor pass: its tiles (one per tangent column) are
+ *                      split into chunks, each adding its share of the
+ *                      Laplacian's sum of squares;
+ *   KFAC_TUNE_BWD_TAN  the adjoint GEMM of the tangent columns, likewise.
+ * By default the chunk length comes from a wave model: full waves of one CTA
+ * per SM and chunks of equal length.  While autotuning is enabled, the first
+ * eager call that meets a launch shape not yet in the handle's table times
+ * the model's chunk length and up to three runners-up by the model (one
+ * warm-up and three timed launches each, CUDA events on the launching
+ * stream, which the host then waits for), records the fastest and computes
+ * with it; later launches of that shape use the recorded length, so results
+ * are deterministic once the table is filled.  Different chunk lengths add
+ * the partial sums in different orders: results agree to FP32 rounding, not
+ * bit for bit.  Nothing is measured while the stream is being captured into
+ * a graph.  Enabling frees the handle's graph (kfac_pinn_set_graph), so the
+ * next step runs eagerly and measures; a kfac_pinn_batch holding the handle
+ * keeps the lengths its graph was captured with until it re-captures.  The
+ * FP64 precision and the forward-mode products of the AUTO update have no
+ * tuned launches.  Default: disabled.  Errors: KFAC_BAD_ARG for a NULL
+ * handle. */
 #define KFAC_TUNE_CAP 128
+typedef enum { KFAC_TUNE_GRAM = 0, KFAC_TUNE_FWD_TAN = 1, KFAC_TUNE_BWD_TAN = 2 } kfac_tune_kind_t;
 typedef struct {
-    int P, Q;              /* output size of the Gram (P x Q)                     */
-    int rows;              /* contraction length K (rows of S * N_cap)            */
-    int sym;               /* 1: symmetric, upper-triangle tiles only            */
-    int split;             /* 1: three split-BF16 products per entry             */
-    int row_chunk;         /* chunk length in rows: a multiple of 64 in
-                              64..rows rounded up to 64                          */
-    int model_row_chunk;   /* the wave model's chunk length                      */
-    float us;              /* measured time of row_chunk per launch (us), 0 when
-                              the entry was set by kfac_pinn_set_tuning           */
-    float model_us;        /* measured time of model_row_chunk per launch (us)   */
+    int kind;              /* kfac_tune_kind_t                                     */
+    int P, Q, K;           /* GRAM: P x Q output, K rows; *_TAN: P = N_cap points,
+                              Q output and K input features (padded to 64)        */
+    int tiles;             /* *_TAN: tangent tiles that are split; GRAM: 0         */
+    int sym;               /* GRAM: 1 = symmetric, upper-triangle tiles only      */
+    int split;             /* 1: three split-BF16 products per entry              */
+    int chunk;             /* GRAM: rows per chunk, a multiple of 64 in 64..K
+                              rounded up to 64; *_TAN: tiles per chunk, 1..tiles  */
+    int model_chunk;       /* the wave model's chunk length                       */
+    float us;              /* measured time of chunk per launch (us), 0 when the
+                              entry was set by kfac_pinn_set_tuning               */
+    float model_us;        /* measured time of model_chunk per launch (us)        */
 } kfac_tune_entry_t;
 
 kfac_status_t kfac_pinn_set_autotune(kfac_handle_t h, int enable);
@@ -244,13 +256,15 @@ kfac_status_t kfac_pinn_get_tuning(kfac_handle_t h, kfac_tune_entry_t* out, int 
 
 /* Replace the handle's tuning table by count entries from in (host memory),
  * e.g. a table read from another handle of the same configuration; count 0
- * clears it.  Only P, Q, rows, sym, split and row_chunk are used.  An entry
- * whose chunk count would not fit the handle's partial-sum workspace is
- * ignored at launch time (the wave model decides).  Frees the handle's
+ * clears it.  Every field but model_chunk, us and model_us is used.  An
+ * entry whose chunk count would not fit the handle's partial-sum workspace
+ * is ignored at launch time (the wave model decides).  Frees the handle's
  * graph.  Errors: KFAC_BAD_ARG for a NULL handle, count outside
- * 0..KFAC_TUNE_CAP, in NULL with count > 0, or an entry with P, Q or rows
- * below 1, sym or split not 0 or 1, or row_chunk not a multiple of 64 in
- * 64..rows rounded up to 64 (the table is then left unchanged). */
+ * 0..KFAC_TUNE_CAP, in NULL with count > 0, or an entry with an unknown
+ * kind, P, Q or K below 1, sym or split not 0 or 1, or a chunk outside the
+ * range its kind allows (GRAM: tiles 0 and chunk a multiple of 64 in 64..K
+ * rounded up to 64; *_TAN: sym 0, tiles >= 1 and chunk in 1..tiles); the
+ * table is then left unchanged. */
 kfac_status_t kfac_pinn_set_tuning(kfac_handle_t h, const kfac_tune_entry_t* in, int count);
 
 /* Curvature and gradient of one batch (App. B, Algorithm 1): forward

@@ -39,10 +39,14 @@ class KfacConfig(C.Structure):
     ]
 
 
+TUNE_KINDS = {0: "gram", 1: "fwd_tan", 2: "bwd_tan"}
+
+
 class KfacTuneEntry(C.Structure):
     _fields_ = [
-        ("P", C.c_int), ("Q", C.c_int), ("rows", C.c_int), ("sym", C.c_int), ("split", C.c_int),
-        ("row_chunk", C.c_int), ("model_row_chunk", C.c_int), ("us", C.c_float), ("model_us", C.c_float),
+        ("kind", C.c_int), ("P", C.c_int), ("Q", C.c_int), ("K", C.c_int), ("tiles", C.c_int),
+        ("sym", C.c_int), ("split", C.c_int), ("chunk", C.c_int), ("model_chunk", C.c_int),
+        ("us", C.c_float), ("model_us", C.c_float),
     ]
 
 

@@ -145,12 +145,14 @@ class KfacPinn:
         _check("kfac_pinn_set_graph", self.lib.kfac_pinn_set_graph(self.h, int(enable)))
 
     def set_autotune(self, enable: bool = True):
-        """Time candidate row-chunk lengths of each new Gram shape on the next
-        eager step and keep the fastest (kfac_pinn_set_autotune)."""
+        """Time candidate split-K chunk lengths of each new Gram and tangent
+        GEMM shape on the next eager step and keep the fastest
+        (kfac_pinn_set_autotune)."""
         _check("kfac_pinn_set_autotune", self.lib.kfac_pinn_set_autotune(self.h, int(enable)))
 
     def tuning(self) -> list:
-        """The handle's tuning table, one dict per Gram shape."""
+        """The handle's tuning table, one dict per launch shape (kind: 0 Gram,
+        1 forward tangent GEMM, 2 adjoint tangent GEMM)."""
         n = C.c_int()
         _check("kfac_pinn_get_tuning", self.lib.kfac_pinn_get_tuning(self.h, None, 0, C.byref(n)))
         arr = (_lib.KfacTuneEntry * max(n.value, 1))()

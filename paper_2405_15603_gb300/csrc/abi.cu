@@ -592,10 +592,16 @@ kfac_status_t kfac_pinn_set_tuning(kfac_handle_t h, const kfac_tune_entry_t* in,
     if (!h || count < 0 || count > KFAC_TUNE_CAP || (count > 0 && !in)) return KFAC_BAD_ARG;
     for (int i = 0; i < count; i++) {
         const kfac_tune_entry_t& e = in[i];
-        const long long top = ((long long)e.rows + 63) / 64 * 64;
-        if (e.P < 1 || e.Q < 1 || e.rows < 1 || (e.sym != 0 && e.sym != 1) || (e.split != 0 && e.split != 1) ||
-            e.row_chunk < 64 || e.row_chunk % 64 != 0 || e.row_chunk > top)
+        if (e.P < 1 || e.Q < 1 || e.K < 1 || (e.sym != 0 && e.sym != 1) || (e.split != 0 && e.split != 1))
             return KFAC_BAD_ARG;
+        if (e.kind == KFAC_TUNE_GRAM) {
+            const long long top = ((long long)e.K + 63) / 64 * 64;
+            if (e.tiles != 0 || e.chunk < 64 || e.chunk % 64 != 0 || e.chunk > top) return KFAC_BAD_ARG;
+        } else if (e.kind == KFAC_TUNE_FWD_TAN || e.kind == KFAC_TUNE_BWD_TAN) {
+            if (e.sym != 0 || e.tiles < 1 || e.chunk < 1 || e.chunk > e.tiles) return KFAC_BAD_ARG;
+        } else {
+            return KFAC_BAD_ARG;
+        }
     }
     for (int i = 0; i < count; i++) {
         h->tune[i] = in[i];

@@ -868,24 +868,141 @@ double wave_efficiency(long long ctas, int sm) {
     return (double)ctas / (double)(waves * sm);
 }
 
-// Split the S_tiles tangent tiles of each of `blocks` output tiles into chunks
-// (one CTA each) so that the waves are full and the chunks even; ties keep
-// fewer, longer chunks (fewer partial sums to combine).
-void choose_chunks(int S_tiles, int blocks, int sm, int& chunk_len, int& n_chunks) {
-    double best = -1.0;
-    n_chunks = 1;
-    chunk_len = S_tiles;
+// Candidate chunk lengths of one split-K launch with the wave model's
+// efficiency (the fraction of full waves kept busy times the fraction of
+// chunk slots holding work); `model` is the first of the highest efficiency,
+// so ties keep fewer, longer chunks (fewer partial sums to combine).
+struct Cands {
+    int n = 0, model = 0;
+    int len[64];
+    double eff[64];
+    void add(int c, double e) {
+        for (int i = 0; i < n; i++)
+            if (len[i] == c) return;
+        if (n == 64) return;
+        len[n] = c;
+        eff[n] = e;
+        if (e > eff[model] + 1e-9) model = n;
+        n++;
+    }
+};
+
+// Chunks of the S_tiles tangent tiles of each of `blocks` output tiles, one
+// CTA per (output tile, chunk), at most MAX_CHUNKS chunks.
+Cands tangent_candidates(int S_tiles, int blocks, int sm) {
+    Cands c;
     const int top = S_tiles < MAX_CHUNKS ? S_tiles : MAX_CHUNKS;
     for (int n = 1; n <= top; n++) {
         const int len = (S_tiles + n - 1) / n;
         const int cnt = (S_tiles + len - 1) / len;
-        const double e = wave_efficiency((long long)blocks * cnt, sm) * (double)S_tiles / ((double)cnt * len);
-        if (e > best + 1e-9) {
-            best = e;
-            n_chunks = cnt;
-            chunk_len = len;
+        c.add(len, wave_efficiency((long long)blocks * cnt, sm) * (double)S_tiles / ((double)cnt * len));
+    }
+    return c;
+}
+
+void choose_chunks(int S_tiles, int blocks, int sm, int& chunk_len, int& n_chunks) {
+    const Cands c = tangent_candidates(S_tiles, blocks, sm);
+    chunk_len = c.len[c.model];
+    n_chunks = (S_tiles + chunk_len - 1) / chunk_len;
+}
+
+// ------------------------------------------------------- split-K autotuner
+// The handle's table maps a launch shape to a chunk length (see
+// kfac_pinn_set_autotune).  With autotuning enabled and the stream not
+// capturing, an unseen shape is timed at the model's length and up to three
+// runners-up by the model (one warm-up and TUNE_REPS timed launches each);
+// the fastest is recorded.  Every candidate is a length the model could
+// pick, so it fits the partial-sum workspace.
+constexpr int TUNE_CANDIDATES = 4;
+constexpr int TUNE_REPS = 3;
+
+bool same_shape(const kfac_tune_entry_t& a, const kfac_tune_entry_t& b) {
+    return a.kind == b.kind && a.P == b.P && a.Q == b.Q && a.K == b.K && a.tiles == b.tiles && a.sym == b.sym &&
+           a.split == b.split;
+}
+
+int tune_find(const kfac_pinn_handle* h, const kfac_tune_entry_t& key) {
+    for (int i = 0; i < h->n_tune; i++)
+        if (same_shape(h->tune[i], key)) return i;
+    return -1;
+}
+
+bool tune_may_measure(const kfac_pinn_handle* h, cudaStream_t s) {
+    if (!h->autotune || h->n_tune >= KFAC_TUNE_CAP) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+}
+
+// Time launch(len) over the candidates, record the fastest in the table and
+// return it in `best`.  The caller launches once more with `best`.
+template <class F>
+kfac_status_t tune_measure(kfac_pinn_handle* h, cudaStream_t s, kfac_tune_entry_t key, const Cands& c, F&& launch,
+                           int& best) {
+    int order[TUNE_CANDIDATES];
+    int no = 0;
+    order[no++] = c.model;
+    while (no < TUNE_CANDIDATES && no < c.n) {
+        int pick = -1;
+        for (int i = 0; i < c.n; i++) {
+            bool used = false;
+            for (int j = 0; j < no; j++) used = used || order[j] == i;
+            if (!used && (pick < 0 || c.eff[i] > c.eff[pick] + 1e-9)) pick = i;
+        }
+        order[no++] = pick;
+    }
+    for (cudaEvent_t& e : h->tune_ev)
+        if (!e) KFAC_CUDA_TRY(cudaEventCreate(&e));
+    float t_best = 0.f, t_model = 0.f;
+    best = c.len[c.model];
+    for (int k = 0; k < no; k++) {
+        const int len = c.len[order[k]];
+        kfac_status_t st = launch(len);   // warm-up
+        if (st) return st;
+        KFAC_CUDA_TRY(cudaEventRecord(h->tune_ev[0], s));
+        for (int r = 0; r < TUNE_REPS; r++)
+            if ((st = launch(len))) return st;
+        KFAC_CUDA_TRY(cudaEventRecord(h->tune_ev[1], s));
+        KFAC_CUDA_TRY(cudaEventSynchronize(h->tune_ev[1]));
+        float ms = 0.f;
+        KFAC_CUDA_TRY(cudaEventElapsedTime(&ms, h->tune_ev[0], h->tune_ev[1]));
+        const float us = 1000.f * ms / TUNE_REPS;
+        if (k == 0) t_model = us;
+        if (k == 0 || us < t_best) {
+            t_best = us;
+            best = len;
         }
     }
+    key.chunk = best;
+    key.model_chunk = c.len[c.model];
+    key.us = t_best;
+    key.model_us = t_model;
+    h->tune[h->n_tune++] = key;
+    return KFAC_OK;
+}
+
+// Tangent-tile chunk length of a FWD_TAN / BWD_TAN launch: the table's, else
+// the model's, measured first when the tuner may.
+template <class F>
+kfac_status_t tangent_chunk(kfac_pinn_handle* h, cudaStream_t s, int kind, int N_pad, int hp_out, int hp_in,
+                            int S_tiles, int blocks, F&& launch, int& len) {
+    const Cands c = tangent_candidates(S_tiles, blocks, h->sm_count);
+    len = c.len[c.model];
+    kfac_tune_entry_t key;
+    memset(&key, 0, sizeof(key));
+    key.kind = kind;
+    key.P = N_pad;
+    key.Q = hp_out;
+    key.K = hp_in;
+    key.tiles = S_tiles;
+    key.split = is_split_all(h) ? 1 : 0;
+    const int ti = tune_find(h, key);
+    if (ti >= 0) {
+        const int t = h->tune[ti].chunk;
+        if (t >= 1 && t <= S_tiles && (S_tiles + t - 1) / t <= MAX_CHUNKS) len = t;
+        return KFAC_OK;
+    }
+    if (tune_may_measure(h, s)) return tune_measure(h, s, key, c, launch, len);
+    return KFAC_OK;
 }
 
 kfac_status_t alloc_pass(kfac_pinn_handle* h, MxPass& P, int Nmax, int S) {
@@ -966,16 +1083,9 @@ void free_pass(MxPass& P) {
 
 // Gram over rows: part[z][p][q] = sum_{rows in chunk z} X[row][p] Y[row][q].
 // With X_lo and Y_lo (split-BF16 everywhere) the three products
-// X_hi^T Y_hi + X_hi^T Y_lo + X_lo^T Y_hi are accumulated.
-//
-// The row-chunk length comes from the handle's tuning table when it holds
-// this shape, else from the wave model (full waves of one CTA per SM, even
-// chunks; ties keep fewer chunks).  With autotuning enabled and the stream
-// not capturing, an unseen shape is timed at the model's length and up to
-// three runners-up, and the fastest is recorded.
-constexpr int TUNE_CANDIDATES = 4;
-constexpr int TUNE_REPS = 3;
-
+// X_hi^T Y_hi + X_hi^T Y_lo + X_lo^T Y_hi are accumulated.  The row-chunk
+// length comes from the tuning table, else from the wave model (measured
+// first when the tuner may).
 kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, const CUtensorMap& Y, int P, int Q,
                    int rows, int sym, float* part, int& nz, const CUtensorMap* X_lo = nullptr,
                    const CUtensorMap* Y_lo = nullptr) {
@@ -987,35 +1097,12 @@ kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, co
     if (max_chunks > MAX_GRAM_CHUNKS) max_chunks = MAX_GRAM_CHUNKS;
     if (max_chunks < 1) return KFAC_BAD_ARG;
     const int split = (X_lo && Y_lo) ? 1 : 0;
-    // candidate chunk lengths with their modelled efficiency; every candidate
-    // needs at most max_chunks chunks
-    int cand[MAX_GRAM_CHUNKS];
-    double eff[MAX_GRAM_CHUNKS];
-    int nc = 0, model = 0;
+    // every candidate needs at most max_chunks chunks
+    Cands c;
     for (int want = 1; want <= max_chunks; want++) {
-        const int c = round_up((rows + want - 1) / want, 64);
-        const int cnt = (rows + c - 1) / c;
-        const double e = wave_efficiency((long long)tiles * cnt, h->sm_count) * (double)rows / ((double)cnt * c);
-        bool seen = false;
-        for (int i = 0; i < nc; i++) seen = seen || cand[i] == c;
-        if (seen) continue;
-        cand[nc] = c;
-        eff[nc] = e;
-        if (e > eff[model] + 1e-9) model = nc;
-        nc++;
-    }
-    int chunk = cand[model];
-    int tuned = -1;
-    for (int i = 0; i < h->n_tune; i++) {
-        const kfac_tune_entry_t& t = h->tune[i];
-        if (t.P == P && t.Q == Q && t.rows == rows && t.sym == sym && t.split == split) {
-            tuned = i;
-            break;
-        }
-    }
-    if (tuned >= 0) {
-        const int c = h->tune[tuned].row_chunk;
-        if (c >= 64 && c % 64 == 0 && c <= round_up(rows, 64) && (rows + c - 1) / c <= max_chunks) chunk = c;
+        const int cl = round_up((rows + want - 1) / want, 64);
+        const int cnt = (rows + cl - 1) / cl;
+        c.add(cl, wave_efficiency((long long)tiles * cnt, h->sm_count) * (double)rows / ((double)cnt * cl));
     }
 
     Args a;
@@ -1034,63 +1121,31 @@ kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, co
         a.b1 = *Y_lo;
         a.split_all = 1;
     }
-    double work = 2.0 * (double)tiles * 128 * C::BN * rows;   // algorithmic: one product per entry
+    const double work = 2.0 * (double)tiles * 128 * C::BN * rows;   // algorithmic: one product per entry
+    auto launch = [&](int cl) {
+        a.row_chunk = cl;
+        return launch_engine<tck::GRAM>(h, s, a, dim3(tiles, (rows + cl - 1) / cl, 1), KFAC_KC_GRAM, work);
+    };
 
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (tuned < 0 && h->autotune && h->n_tune < KFAC_TUNE_CAP && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
-        cs == cudaStreamCaptureStatusNone) {
-        // the model's choice first, then the runners-up by modelled efficiency
-        int order[TUNE_CANDIDATES];
-        int no = 0;
-        order[no++] = model;
-        while (no < TUNE_CANDIDATES && no < nc) {
-            int best = -1;
-            for (int i = 0; i < nc; i++) {
-                bool used = false;
-                for (int j = 0; j < no; j++) used = used || order[j] == i;
-                if (!used && (best < 0 || eff[i] > eff[best] + 1e-9)) best = i;
-            }
-            order[no++] = best;
-        }
-        for (cudaEvent_t& e : h->tune_ev)
-            if (!e) KFAC_CUDA_TRY(cudaEventCreate(&e));
-        float t_best = 0.f, t_model = 0.f;
-        int c_best = cand[model];
-        for (int k = 0; k < no; k++) {
-            const int c = cand[order[k]];
-            a.row_chunk = c;
-            const dim3 grid(tiles, (rows + c - 1) / c, 1);
-            kfac_status_t st = launch_engine<tck::GRAM>(h, s, a, grid, KFAC_KC_GRAM, work);   // warm-up
-            if (st) return st;
-            KFAC_CUDA_TRY(cudaEventRecord(h->tune_ev[0], s));
-            for (int r = 0; r < TUNE_REPS; r++)
-                if ((st = launch_engine<tck::GRAM>(h, s, a, grid, KFAC_KC_GRAM, work))) return st;
-            KFAC_CUDA_TRY(cudaEventRecord(h->tune_ev[1], s));
-            KFAC_CUDA_TRY(cudaEventSynchronize(h->tune_ev[1]));
-            float ms = 0.f;
-            KFAC_CUDA_TRY(cudaEventElapsedTime(&ms, h->tune_ev[0], h->tune_ev[1]));
-            const float us = 1000.f * ms / TUNE_REPS;
-            if (k == 0) t_model = us;
-            if (k == 0 || us < t_best) {
-                t_best = us;
-                c_best = c;
-            }
-        }
-        kfac_tune_entry_t& t = h->tune[h->n_tune++];
-        t.P = P;
-        t.Q = Q;
-        t.rows = rows;
-        t.sym = sym;
-        t.split = split;
-        t.row_chunk = c_best;
-        t.model_row_chunk = cand[model];
-        t.us = t_best;
-        t.model_us = t_model;
-        chunk = c_best;
+    int chunk = c.len[c.model];
+    kfac_tune_entry_t key;
+    memset(&key, 0, sizeof(key));
+    key.kind = KFAC_TUNE_GRAM;
+    key.P = P;
+    key.Q = Q;
+    key.K = rows;
+    key.sym = sym;
+    key.split = split;
+    const int ti = tune_find(h, key);
+    if (ti >= 0) {
+        const int t = h->tune[ti].chunk;
+        if (t >= 64 && t % 64 == 0 && t <= round_up(rows, 64) && (rows + t - 1) / t <= max_chunks) chunk = t;
+    } else if (tune_may_measure(h, s)) {
+        kfac_status_t st = tune_measure(h, s, key, c, launch, chunk);
+        if (st) return st;
     }
     nz = (rows + chunk - 1) / chunk;
-    a.row_chunk = chunk;
-    return launch_engine<tck::GRAM>(h, s, a, dim3(tiles, nz, 1), KFAC_KC_GRAM, work);
+    return launch(chunk);
 }
 
 // ============================================================================
@@ -1166,10 +1221,17 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
         kfac_status_t st = launch_engine<tck::FWD_VALUE>(h, s, a, dim3(jb, pb, 1), KFAC_KC_LAYER_GEMM, 3 * fl);
         if (st) return st;
         if (S > 1) {
-            choose_chunks(S - 1, jb * pb, h->sm_count, a.chunk_len, a.n_chunks);
-            st = launch_engine<tck::FWD_TANLAP>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_LAYER_GEMM,
-                                                fl * (S + 1));
-            if (st) return st;
+            const int tiles = S - 1;
+            auto launch = [&](int len) {
+                a.chunk_len = len;
+                a.n_chunks = (tiles + len - 1) / len;
+                return launch_engine<tck::FWD_TANLAP>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_LAYER_GEMM,
+                                                      fl * (S + 1));
+            };
+            int len = 0;
+            if ((st = tangent_chunk(h, s, KFAC_TUNE_FWD_TAN, P.N_pad, out.hp, in.hp, tiles, jb * pb, launch, len)))
+                return st;
+            if ((st = launch(len))) return st;
             long long cnt = (long long)P.N_pad * out.hp;
             timer_begin(h, KFAC_KC_ELEMENTWISE, s);
             k_lap_finish<<<ceil_div_u(cnt, EW), EW, 0, s>>>(m->part, a.n_chunks, N, P.N_pad, out.h, out.hp, S,
@@ -1234,9 +1296,17 @@ kfac_status_t backward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* r
         if (S > 1) {
             st = launch_engine<tck::BWD_LAP>(h, s, a, dim3(jb, pb, 1), KFAC_KC_ADJOINT_GEMM, fl);
             if (st) return st;
-            choose_chunks(S - 2, jb * pb, h->sm_count, a.chunk_len, a.n_chunks);
-            st = launch_engine<tck::BWD_TAN>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_ADJOINT_GEMM, fl * (S - 2));
-            if (st) return st;
+            const int tiles = S - 2;
+            auto launch = [&](int len) {
+                a.chunk_len = len;
+                a.n_chunks = (tiles + len - 1) / len;
+                return launch_engine<tck::BWD_TAN>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_ADJOINT_GEMM,
+                                                   fl * (S - 2));
+            };
+            int len = 0;
+            if ((st = tangent_chunk(h, s, KFAC_TUNE_BWD_TAN, P.N_pad, dn.hp, up.hp, tiles, jb * pb, launch, len)))
+                return st;
+            if ((st = launch(len))) return st;
         }
         st = launch_engine<tck::BWD_VALUE>(h, s, a, dim3(jb, pb, 1), KFAC_KC_ADJOINT_GEMM, fl);
         if (st) return st;

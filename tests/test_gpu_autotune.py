@@ -1,7 +1,8 @@
-"""Gram tile autotuner (kfac_pinn_set_autotune, kfac_pinn_get_tuning,
-kfac_pinn_set_tuning).
+"""Split-K autotuner (kfac_pinn_set_autotune, kfac_pinn_get_tuning,
+kfac_pinn_set_tuning) of the Grams (row chunks) and of the tangent GEMMs of
+the Taylor pass and its adjoint (tangent-tile chunks).
 
-A measured row-chunk length changes only how a Gram's K rows are split among
+A measured chunk length changes only how a launch's work is split among
 CTAs, i.e. the order in which FP32 partial sums are added.  So:
   * an autotuned step still matches the FP64 oracle within the bounds of its
     precision (mixed_bf16: 2e-2 on gradient and factors; mixed_split: 1e-4);
@@ -56,16 +57,29 @@ def test_autotuned_step_matches_oracle(precision, tol):
     torch.cuda.synchronize()
     assert opt.sync_status() == "KFAC_OK"
     table = opt.tuning()
-    assert table, "no Gram shape was measured"
+    assert {e["kind"] for e in table} == {0, 1, 2}, table
     for e in table:
-        top = -(-e["rows"] // 64) * 64
-        assert e["row_chunk"] % 64 == 0 and 64 <= e["row_chunk"] <= top, e
-        assert e["model_row_chunk"] % 64 == 0 and 64 <= e["model_row_chunk"] <= top, e
         assert 0 < e["us"] <= e["model_us"], e          # the model's length is one of the candidates
         assert e["split"] == (precision == "mixed_split"), e
-        assert e["sym"] in (0, 1)
+        if e["kind"] == 0:
+            top = -(-e["K"] // 64) * 64
+            assert e["tiles"] == 0 and e["sym"] in (0, 1), e
+            for c in (e["chunk"], e["model_chunk"]):
+                assert c % 64 == 0 and 64 <= c <= top, e
+        else:
+            # S - 1 tangent and Laplacian tiles forward, S - 2 tangent tiles in the adjoint
+            assert e["tiles"] == PROB.d + 2 - e["kind"] and e["sym"] == 0, e
+            assert e["P"] == -(-N // 128) * 128 and e["Q"] % 64 == 0 and e["K"] % 64 == 0, e
+            for c in (e["chunk"], e["model_chunk"]):
+                assert 1 <= c <= e["tiles"] and -(-e["tiles"] // c) <= 16, e
     # symmetric Grams of the factors and the weight-gradient contractions
-    assert {e["sym"] for e in table} == {0, 1}
+    assert {e["sym"] for e in table if e["kind"] == 0} == {0, 1}
+    # one entry per distinct padded (output, input) width pair of the hidden
+    # layers 2..L-1, forward and adjoint (layers of equal padded widths share it)
+    h = [-(-w // 64) * 64 for w in (PROB.d,) + WIDTHS]
+    pairs = {(h[l], h[l - 1]) for l in range(2, len(WIDTHS))}
+    assert {(e["Q"], e["K"]) for e in table if e["kind"] == 1} == pairs
+    assert {(e["K"], e["Q"]) for e in table if e["kind"] == 2} == pairs
 
     cfg = ko.KfacConfig(d=PROB.d, widths=WIDTHS, op=PROB.op, kappa=PROB.kappa, **KW)
     st = ko.init_state(cfg)
@@ -115,23 +129,27 @@ def test_copied_table_reproduces_the_measuring_step():
 def test_set_tuning_validation_and_workspace_fallback():
     from paper_2405_15603_gb300.api import KfacError
     opt = _opt("mixed_bf16")
-    ok = dict(P=64, Q=64, rows=7 * 3072, sym=1, split=0, row_chunk=1024)
-    for bad in (dict(row_chunk=100), dict(row_chunk=0), dict(row_chunk=7 * 3072 + 64), dict(sym=2),
-                dict(split=-1), dict(P=0), dict(rows=0)):
+    ok = dict(kind=0, P=64, Q=64, K=7 * 3072, tiles=0, sym=1, split=0, chunk=1024)
+    tan = dict(kind=1, P=3072, Q=64, K=64, tiles=6, sym=0, split=0, chunk=3)
+    for base, bad in ((ok, dict(chunk=100)), (ok, dict(chunk=0)), (ok, dict(chunk=7 * 3072 + 64)),
+                      (ok, dict(sym=2)), (ok, dict(split=-1)), (ok, dict(P=0)), (ok, dict(K=0)),
+                      (ok, dict(tiles=3)), (ok, dict(kind=3)), (tan, dict(chunk=0)), (tan, dict(chunk=7)),
+                      (tan, dict(tiles=0)), (tan, dict(sym=1)), (dict(tan, kind=2), dict(Q=0))):
         with pytest.raises(KfacError) as ei:
-            opt.set_tuning([{**ok, **bad}])
-        assert ei.value.status == "KFAC_BAD_ARG", bad
+            opt.set_tuning([{**base, **bad}])
+        assert ei.value.status == "KFAC_BAD_ARG", (base, bad)
     with pytest.raises(KfacError):
         opt.set_tuning([ok] * 129)                       # more than KFAC_TUNE_CAP entries
     assert opt.tuning() == []                            # a rejected table leaves it unchanged
-    opt.set_tuning([ok])
-    assert len(opt.tuning()) == 1 and opt.tuning()[0]["row_chunk"] == 1024
+    opt.set_tuning([ok, tan, dict(tan, kind=2)])
+    assert [e["chunk"] for e in opt.tuning()] == [1024, 3, 3]
     opt.set_tuning([])
     assert opt.tuning() == []
 
     # 64-row chunks of the interior Grams would need hundreds of partial sums
-    # (the workspace holds 32): ignored at launch; the boundary Grams keep the
-    # model's length
+    # (the workspace holds 32) and one-tile chunks of the 7-tile tangent
+    # GEMMs are within the 16 the workspace holds, so take the interior Grams
+    # only: ignored at launch; every other shape keeps the model's length
     th0 = si.xavier_theta(PROB.d, WIDTHS, 2)
     Xi, f, Xb, g = si.make_batch(PROB, N, NB, seed=2)
     ref = _opt("mixed_bf16")
@@ -141,9 +159,9 @@ def test_set_tuning_validation_and_workspace_fallback():
     probe.set_autotune(True)
     probe.step(torch.tensor(th0, device=DEV), Xi, f, Xb, g)
     torch.cuda.synchronize()
-    huge = [{**e, "row_chunk": 64 if -(-e["rows"] // 64) > 32 else e["model_row_chunk"]}
+    huge = [{**e, "chunk": 64 if e["kind"] == 0 and -(-e["K"] // 64) > 32 else e["model_chunk"]}
             for e in probe.tuning()]
-    assert sum(e["row_chunk"] == 64 for e in huge) >= 4
+    assert sum(e["chunk"] == 64 for e in huge) >= 4
     fb = _opt("mixed_bf16")
     fb.set_tuning(huge)
     tf = torch.tensor(th0, device=DEV)
