@@ -386,6 +386,16 @@ kfac_status_t kfac_pinn_timing_enable(kfac_handle_t h, int enable);
 kfac_status_t kfac_pinn_timing_read(kfac_handle_t h, int kernel_class, double* total_ms,
                                     int64_t* launches, double* work);
 
+/* kfac_pinn_timing_read plus exec_work: the work as the hardware executed it
+ * (tiles padded to the kernel's tile and feature multiples, and every
+ * split-BF16 product: three tensor-core products per contraction where both
+ * operands carry low halves), while `work` counts the method's contraction
+ * once over the real sizes (2 P Q K per GEMM; n (n + 1) K per symmetric Gram
+ * of K rows; element-wise kernels: bytes read + written).  exec_work may be
+ * NULL.  The class's timers are cleared. */
+kfac_status_t kfac_pinn_timing_read_ex(kfac_handle_t h, int kernel_class, double* total_ms,
+                                       int64_t* launches, double* work, double* exec_work);
+
 /* Batched stepping of many independent problems (handles), each with its own
  * network, point counts and buffers.  The paper steps one problem at a time;
  * this serves many small PINNs together: the handles' steps are queued on

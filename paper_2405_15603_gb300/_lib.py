@@ -15,7 +15,8 @@ EXPORTS = [
     "kfac_pinn_precondition", "kfac_pinn_update", "kfac_pinn_step", "kfac_pinn_step_host",
     "kfac_pinn_get_factor", "kfac_pinn_set_factor", "kfac_pinn_get_gradient",
     "kfac_pinn_get_direction", "kfac_pinn_sync_status", "kfac_pinn_launch_count",
-    "kfac_pinn_timing_enable", "kfac_pinn_timing_read", "kfac_pinn_forward_laplacian_noalloc",
+    "kfac_pinn_timing_enable", "kfac_pinn_timing_read", "kfac_pinn_timing_read_ex",
+    "kfac_pinn_forward_laplacian_noalloc",
     "kfac_pinn_get_line_search_losses", "kfac_pinn_forward_laplacian_backward",
     "kfac_pinn_get_update_coefficients", "kfac_pinn_batch_create", "kfac_pinn_batch_destroy",
     "kfac_pinn_batch_step", "kfac_pinn_last_cuda_error", "kfac_pinn_last_cuda_error_string",
@@ -114,6 +115,8 @@ def load() -> C.CDLL:
         "kfac_pinn_forward_laplacian_noalloc": (st, [C.POINTER(KfacConfig), P, P, P, I, P, P, P]),
         "kfac_pinn_timing_read": (st, [H, I, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                        C.POINTER(C.c_double)]),
+        "kfac_pinn_timing_read_ex": (st, [H, I, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

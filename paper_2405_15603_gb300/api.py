@@ -262,13 +262,16 @@ class KfacPinn:
         _check("kfac_pinn_timing_enable", self.lib.kfac_pinn_timing_enable(self.h, int(on)))
 
     def timing_read(self) -> dict:
-        """Per kernel class: (device ms, launches, algorithmic work) since the last read."""
+        """Per kernel class since the last read: device ms, launches, the method's
+        work ("work": real sizes, one product per contraction, symmetric Grams
+        counted once) and the work as executed ("exec": padded tiles and every
+        split-BF16 product)."""
         out = {}
         for cls, name in _lib.KERNEL_CLASSES.items():
-            ms, n, w = C.c_double(), C.c_int64(), C.c_double()
-            _check("kfac_pinn_timing_read", self.lib.kfac_pinn_timing_read(
-                self.h, cls, C.byref(ms), C.byref(n), C.byref(w)))
-            out[name] = {"ms": ms.value, "launches": n.value, "work": w.value}
+            ms, n, w, x = C.c_double(), C.c_int64(), C.c_double(), C.c_double()
+            _check("kfac_pinn_timing_read_ex", self.lib.kfac_pinn_timing_read_ex(
+                self.h, cls, C.byref(ms), C.byref(n), C.byref(w), C.byref(x)))
+            out[name] = {"ms": ms.value, "launches": n.value, "work": w.value, "exec": x.value}
         return out
 
 

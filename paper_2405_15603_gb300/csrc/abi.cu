@@ -308,13 +308,14 @@ void timer_begin(kfac_pinn_handle* h, int cls, cudaStream_t s) {
     cudaEventRecord(t.ev[2 * t.n], s);
 }
 
-void timer_end(kfac_pinn_handle* h, int cls, cudaStream_t s, double work) {
+void timer_end(kfac_pinn_handle* h, int cls, cudaStream_t s, double work, double exec) {
     if (!h->timing) return;
     auto& t = h->timers[cls];
     cudaEventRecord(t.ev[2 * t.n + 1], s);
     t.n++;
     t.launches++;
     t.work += work;
+    t.exec += exec < 0.0 ? work : exec;
 }
 
 void timers_free(kfac_pinn_handle* h) {
@@ -358,6 +359,7 @@ kfac_status_t kfac_pinn_timing_enable(kfac_handle_t h, int enable) {
             t.n = 0;
             t.launches = 0;
             t.work = 0.0;
+            t.exec = 0.0;
             t.ms = 0.0;
         }
     }
@@ -365,18 +367,25 @@ kfac_status_t kfac_pinn_timing_enable(kfac_handle_t h, int enable) {
     return KFAC_OK;
 }
 
-kfac_status_t kfac_pinn_timing_read(kfac_handle_t h, int kernel_class, double* total_ms,
-                                    int64_t* launches, double* work) {
+kfac_status_t kfac_pinn_timing_read_ex(kfac_handle_t h, int kernel_class, double* total_ms, int64_t* launches,
+                                       double* work, double* exec_work) {
     if (!h || kernel_class < 0 || kernel_class >= KFAC_KC_COUNT) return KFAC_BAD_ARG;
     auto& t = h->timers[kernel_class];
     if (t.ev) timer_fold(h, kernel_class);
     if (total_ms) *total_ms = t.ms;
     if (launches) *launches = t.launches;
     if (work) *work = t.work;
+    if (exec_work) *exec_work = t.exec;
     t.ms = 0.0;
     t.launches = 0;
     t.work = 0.0;
+    t.exec = 0.0;
     return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_timing_read(kfac_handle_t h, int kernel_class, double* total_ms,
+                                    int64_t* launches, double* work) {
+    return kfac_pinn_timing_read_ex(h, kernel_class, total_ms, launches, work, nullptr);
 }
 
 

@@ -88,7 +88,8 @@ struct kfac_pinn_handle {
         cudaEvent_t* ev;   // 2 * cap events
         int cap, n;
         long long launches;
-        double work;
+        double work;       // algorithmic work of the method (FLOPs or bytes)
+        double exec;       // work the hardware executed (padded tiles, split-BF16 products)
         double ms;         // folded-in time of earlier batches
     } timers[KFAC_KC_COUNT];
 
@@ -157,7 +158,9 @@ static inline bool is_split_all(const kfac_pinn_handle* h) { return h->cfg.preci
 
 // Device timers: bracket a launch with events when timing is enabled.
 void timer_begin(kfac_pinn_handle* h, int cls, cudaStream_t s);
-void timer_end(kfac_pinn_handle* h, int cls, cudaStream_t s, double work);
+// work: algorithmic work of the launch; exec: work as executed (padding and
+// split-BF16 products included), exec < 0 meaning the same as work.
+void timer_end(kfac_pinn_handle* h, int cls, cudaStream_t s, double work, double exec = -1.0);
 void timers_free(kfac_pinn_handle* h);
 
 static inline unsigned ceil_div_u(long long a, long long b) { return (unsigned)((a + b - 1) / b); }

@@ -66,18 +66,30 @@ struct Args {
     const __nv_bfloat16* ytan_lo;   // BWD_TAN: low half of y_i
 };
 
-template <int MODE>
+template <int MODE, bool SPLIT = false>
 struct Cfg {
     static constexpr bool MN = (MODE == GRAM);
     static constexpr int BN = MN ? 256 : 128;
-    // the forward modes take two 64-wide K blocks per stage (half the barrier round
-    // trips for the same bytes in flight: measured 16 % faster); each block is one
-    // 128-byte-swizzled TMA box.  The adjoint modes keep one block and six stages.
-    static constexpr int KSUB =
-        (MODE == FWD_VALUE || MODE == FWD_TANLAP || MODE == JVP_VALUE || MODE == JVP_TAN) ? 2 : 1;
-    static constexpr int STAGES = MN ? 4 : (KSUB == 2 ? 3 : 6);
-    static constexpr int A_BYTES = KSUB * BM * BK * 2;
-    static constexpr int B_BYTES = KSUB * BN * BK * 2;
+    // Two-slot stages: a stage holds two A and two B boxes (each one 64-wide K
+    // block, one 128-byte-swizzled TMA box).  A tile with a single product per
+    // K block fills the slots with two consecutive K blocks (half the barrier
+    // round trips for the same bytes in flight: measured 16 % faster for the
+    // forward modes); a tile with several products per K block (the split-BF16
+    // terms hi*hi + hi*lo + lo*hi, or the JVP terms T dW + dT W) fills them with
+    // the two A and the two B operands of ONE K block and issues every product
+    // from them, so each operand crosses L2 -> SM once per K block instead of
+    // once per product.  The forward and JVP modes always use two slots; the
+    // adjoint modes only when every row is split (one slot and six stages
+    // otherwise); the Gram keeps one slot.
+    static constexpr bool FUSED =
+        (MODE == FWD_VALUE || MODE == FWD_TANLAP || MODE == JVP_VALUE || MODE == JVP_TAN) ||
+        (SPLIT && (MODE == BWD_LAP || MODE == BWD_TAN || MODE == BWD_VALUE));
+    static constexpr int SLOTS = FUSED ? 2 : 1;
+    static constexpr int STAGES = MN ? 4 : (FUSED ? 3 : 6);
+    static constexpr int SLOT_A = BM * BK * 2;
+    static constexpr int SLOT_B = BN * BK * 2;
+    static constexpr int A_BYTES = SLOTS * SLOT_A;
+    static constexpr int B_BYTES = SLOTS * SLOT_B;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
     static constexpr int TMEM_COLS = MN ? 256 : 2 * BN;
@@ -156,7 +168,7 @@ KFAC_DEV void load16_f32(const float* src, float* v) {
 // that the plain instantiations keep their register budget.
 template <int MODE, bool SPLIT>
 __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constant__ Args a) {
-    using C = Cfg<MODE>;
+    using C = Cfg<MODE, SPLIT>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t full_bar[C::STAGES], empty_bar[C::STAGES];
@@ -188,7 +200,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
     } else {
         j0 = blockIdx.x * C::BN;
         p0 = blockIdx.y * BM;
-        k_steps = (a.k_steps + C::KSUB - 1) / C::KSUB;   // stages of KSUB 64-wide K blocks
+        k_steps = a.k_steps;                              // 64-wide K blocks (one-slot modes)
         tile_range<MODE>(a, s_begin, s_end);
     }
     const int n_tiles = max(0, s_end - s_begin);
@@ -220,39 +232,66 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
             for (int ti = 0; ti < n_tiles && !abort_flag; ti++) {
                 const int s = s_begin + ti;
                 const int terms = SPLIT ? n_terms<MODE>(s, a.S, a.split_time, 1) : n_terms<MODE>(s, a.S, a.split_time, 0);
-                for (int term = 0; term < terms && !abort_flag; term++) {
-                    for (int k = 0; k < k_steps; k++) {
+                if constexpr (C::FUSED) {
+                    // rows of the second A operand: the low half (laid out like the high
+                    // half when every row is split, else in its value / Laplacian / time
+                    // block) or, in the JVP modes, dT
+                    const bool jvp = (MODE == JVP_VALUE || MODE == JVP_TAN);
+                    const int arow = s * a.N_pad + p0;
+                    const int arow1 = (SPLIT || jvp) ? arow : (lo_block(s, a.S) * a.N_pad + p0);
+                    const bool fuse = terms > 1;
+                    const int nst = fuse ? a.k_steps : (a.k_steps + 1) / 2;
+                    for (int k = 0; k < nst; k++) {
                         if (!tc::mbar_wait(&empty_bar[stage], phase ^ 1)) { abort_flag = 1; break; }
                         unsigned char* sa = smem + stage * C::STAGE_BYTES;
                         unsigned char* sb = sa + C::A_BYTES;
                         tc::mbar_arrive_expect_tx(&full_bar[stage], C::STAGE_BYTES);
-                        if (MODE == GRAM) {
-                            // terms: X_hi^T Y_hi, X_hi^T Y_lo, X_lo^T Y_hi
-                            const int row = k_begin + k * BK;
-                            const CUtensorMap* am = (term == 2) ? &a.a1 : &a.a0;
-                            const CUtensorMap* bm = (term == 1) ? &a.b1 : &a.b0;
-                            tc::tma_load_2d(sa, am, &full_bar[stage], p0, row);
-                            tc::tma_load_2d(sa + 8192, am, &full_bar[stage], p0 + 64, row);
+                        if (fuse) {      // a0, a1, b0, b1 of K block k
+                            const int kx = k * BK;
+                            tc::tma_load_2d(sa, &a.a0, &full_bar[stage], kx, arow);
+                            tc::tma_load_2d(sa + C::SLOT_A, &a.a1, &full_bar[stage], kx, arow1);
+                            tc::tma_load_2d(sb, &a.b0, &full_bar[stage], kx, j0);
+                            tc::tma_load_2d(sb + C::SLOT_B, &a.b1, &full_bar[stage], kx, j0);
+                        } else {         // K blocks 2k and 2k+1 (blocks past K read zeros)
 #pragma unroll
-                            for (int b = 0; b < C::BN / 64; b++)
-                                tc::tma_load_2d(sb + 8192 * b, bm, &full_bar[stage], j0 + 64 * b, row);
-                        } else {
-                            // term 0: hi x hi, term 1: hi x W_lo, term 2: lo x W_hi;
-                            // JVP modes: term 0: T x dW, term 1: dT x W
-                            const bool jvp = (MODE == JVP_VALUE || MODE == JVP_TAN);
-                            const CUtensorMap* am = (jvp ? term == 1 : term == 2) ? &a.a1 : &a.a0;
-                            const CUtensorMap* bm = (term == 1) ? &a.b1 : &a.b0;
-                            int arow;
-                            if constexpr (SPLIT) arow = s * a.N_pad + p0;   // low halves laid out like the high
-                            else arow = (!jvp && term == 2) ? (lo_block(s, a.S) * a.N_pad + p0) : (s * a.N_pad + p0);
-#pragma unroll
-                            for (int u = 0; u < C::KSUB; u++) {   // blocks past K read zeros
-                                const int kx = (k * C::KSUB + u) * BK;
-                                tc::tma_load_2d(sa + u * (BM * BK * 2), am, &full_bar[stage], kx, arow);
-                                tc::tma_load_2d(sb + u * (C::BN * BK * 2), bm, &full_bar[stage], kx, j0);
+                            for (int u = 0; u < 2; u++) {
+                                const int kx = (2 * k + u) * BK;
+                                tc::tma_load_2d(sa + u * C::SLOT_A, &a.a0, &full_bar[stage], kx, arow);
+                                tc::tma_load_2d(sb + u * C::SLOT_B, &a.b0, &full_bar[stage], kx, j0);
                             }
                         }
                         if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                    }
+                } else {
+                    for (int term = 0; term < terms && !abort_flag; term++) {
+                        for (int k = 0; k < k_steps; k++) {
+                            if (!tc::mbar_wait(&empty_bar[stage], phase ^ 1)) { abort_flag = 1; break; }
+                            unsigned char* sa = smem + stage * C::STAGE_BYTES;
+                            unsigned char* sb = sa + C::A_BYTES;
+                            tc::mbar_arrive_expect_tx(&full_bar[stage], C::STAGE_BYTES);
+                            if (MODE == GRAM) {
+                                // terms: X_hi^T Y_hi, X_hi^T Y_lo, X_lo^T Y_hi
+                                const int row = k_begin + k * BK;
+                                const CUtensorMap* am = (term == 2) ? &a.a1 : &a.a0;
+                                const CUtensorMap* bm = (term == 1) ? &a.b1 : &a.b0;
+                                tc::tma_load_2d(sa, am, &full_bar[stage], p0, row);
+                                tc::tma_load_2d(sa + 8192, am, &full_bar[stage], p0 + 64, row);
+#pragma unroll
+                                for (int b = 0; b < C::BN / 64; b++)
+                                    tc::tma_load_2d(sb + 8192 * b, bm, &full_bar[stage], j0 + 64 * b, row);
+                            } else {
+                                // one slot: term 0 hi x hi, term 1 hi x W_lo, term 2 lo x W_hi
+                                const CUtensorMap* am = (term == 2) ? &a.a1 : &a.a0;
+                                const CUtensorMap* bm = (term == 1) ? &a.b1 : &a.b0;
+                                int arow;
+                                if constexpr (SPLIT) arow = s * a.N_pad + p0;   // low halves laid out like the high
+                                else arow = (term == 2) ? (lo_block(s, a.S) * a.N_pad + p0) : (s * a.N_pad + p0);
+                                const int kx = k * BK;
+                                tc::tma_load_2d(sa, am, &full_bar[stage], kx, arow);
+                                tc::tma_load_2d(sb, bm, &full_bar[stage], kx, j0);
+                            }
+                            if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                        }
                     }
                 }
             }
@@ -271,28 +310,57 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                 const uint32_t dcol = tbase + (uint32_t)(buf * C::BN);
                 const int terms = SPLIT ? n_terms<MODE>(s, a.S, a.split_time, 1) : n_terms<MODE>(s, a.S, a.split_time, 0);
                 bool first = true;
-                for (int term = 0; term < terms && !abort_flag; term++) {
-                    for (int k = 0; k < k_steps; k++) {
+                if constexpr (C::FUSED) {
+                    const bool jvp = (MODE == JVP_VALUE || MODE == JVP_TAN);
+                    const bool fuse = terms > 1;
+                    const int nst = fuse ? a.k_steps : (a.k_steps + 1) / 2;
+                    for (int k = 0; k < nst; k++) {
                         if (!tc::mbar_wait(&full_bar[stage], phase)) { abort_flag = 1; break; }
                         tc::tc_fence_after();
                         const uint32_t sa = tc::smem_u32(smem + stage * C::STAGE_BYTES);
                         const uint32_t sb = sa + C::A_BYTES;
+                        // (A slot, B slot) of each product: one K block per slot pair when
+                        // not fused; hi*hi, hi*lo, lo*hi (or T dW, dT W) of one K block when fused
+                        const int np = fuse ? (jvp ? 2 : 3) : 2;
 #pragma unroll
-                        for (int kk = 0; kk < C::KSUB * BK / 16; kk++) {
-                            uint64_t ad, bd;
-                            if (C::MN) {
-                                ad = tc::smem_desc(sa + kk * 2048, 8192, 1024, tc::LAYOUT_SW128);
-                                bd = tc::smem_desc(sb + kk * 2048, 8192, 1024, tc::LAYOUT_SW128);
-                            } else {
-                                const uint32_t u = (uint32_t)(kk / (BK / 16)), w = (uint32_t)(kk % (BK / 16));
-                                ad = tc::smem_desc(sa + u * (BM * BK * 2) + w * 32, 16, 1024, tc::LAYOUT_SW128);
-                                bd = tc::smem_desc(sb + u * (C::BN * BK * 2) + w * 32, 16, 1024, tc::LAYOUT_SW128);
+                        for (int pi = 0; pi < 3; pi++) {
+                            if (pi >= np) break;
+                            const uint32_t ua = fuse ? (jvp ? pi : (pi == 2 ? 1u : 0u)) : pi;
+                            const uint32_t ub = fuse ? (jvp ? pi : (pi == 1 ? 1u : 0u)) : pi;
+#pragma unroll
+                            for (int w = 0; w < BK / 16; w++) {
+                                const uint64_t ad = tc::smem_desc(sa + ua * C::SLOT_A + w * 32, 16, 1024, tc::LAYOUT_SW128);
+                                const uint64_t bd = tc::smem_desc(sb + ub * C::SLOT_B + w * 32, 16, 1024, tc::LAYOUT_SW128);
+                                tc::mma_bf16(dcol, ad, bd, C::IDESC, first ? 0u : 1u);
+                                first = false;
                             }
-                            tc::mma_bf16(dcol, ad, bd, C::IDESC, first ? 0u : 1u);
-                            first = false;
                         }
                         tc::mma_commit(&empty_bar[stage]);
                         if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                    }
+                } else {
+                    for (int term = 0; term < terms && !abort_flag; term++) {
+                        for (int k = 0; k < k_steps; k++) {
+                            if (!tc::mbar_wait(&full_bar[stage], phase)) { abort_flag = 1; break; }
+                            tc::tc_fence_after();
+                            const uint32_t sa = tc::smem_u32(smem + stage * C::STAGE_BYTES);
+                            const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+                            for (int kk = 0; kk < BK / 16; kk++) {
+                                uint64_t ad, bd;
+                                if (C::MN) {
+                                    ad = tc::smem_desc(sa + kk * 2048, 8192, 1024, tc::LAYOUT_SW128);
+                                    bd = tc::smem_desc(sb + kk * 2048, 8192, 1024, tc::LAYOUT_SW128);
+                                } else {
+                                    ad = tc::smem_desc(sa + kk * 32, 16, 1024, tc::LAYOUT_SW128);
+                                    bd = tc::smem_desc(sb + kk * 32, 16, 1024, tc::LAYOUT_SW128);
+                                }
+                                tc::mma_bf16(dcol, ad, bd, C::IDESC, first ? 0u : 1u);
+                                first = false;
+                            }
+                            tc::mma_commit(&empty_bar[stage]);
+                            if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
+                        }
                     }
                 }
                 tc::mma_commit(&acc_full[buf]);

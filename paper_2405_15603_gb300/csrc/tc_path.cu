@@ -72,7 +72,9 @@ struct MxPass {
     float* zl;                            // last-layer outputs, S*N_pad
     float* Xf;                            // FP32 copy of the points (N_pad x d, zero padded)
     bf16 *red_a, *red_g;                  // KFAC-reduce column sums (N_pad x hp_max)
+    bf16 *red_a_lo, *red_g_lo;            // their low halves (split-BF16 everywhere)
     CUtensorMap gRa[KFAC_MAX_LAYERS], gRg[KFAC_MAX_LAYERS];
+    CUtensorMap gRa_lo[KFAC_MAX_LAYERS], gRg_lo[KFAC_MAX_LAYERS];
 };
 
 struct MxWeights {
@@ -438,13 +440,22 @@ __global__ void __launch_bounds__(RED_THREADS) k_colsum(const bf16* __restrict__
 }
 
 // KFAC-reduce per-point sums over the S Taylor columns: out = scale * sum_s X_s.
-__global__ void k_sum_over_s(const bf16* __restrict__ X, int N_pad, int S, int hp, float scale, bf16* out) {
+// With X_lo (split-BF16 everywhere) the sum runs over hi + lo and is stored
+// split again (out_lo = the rounding remainder of out).
+__global__ void k_sum_over_s(const bf16* __restrict__ X, const bf16* __restrict__ X_lo, int N_pad, int S, int hp,
+                             float scale, bf16* out, bf16* out_lo) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long blk = (long long)N_pad * hp;
     if (idx >= blk) return;
     float acc = 0.f;
-    for (int s = 0; s < S; s++) acc += __bfloat162float(X[s * blk + idx]);
-    out[idx] = __float2bfloat16_rn(scale * acc);
+    for (int s = 0; s < S; s++) {
+        acc += __bfloat162float(X[s * blk + idx]);
+        if (X_lo) acc += __bfloat162float(X_lo[s * blk + idx]);
+    }
+    const float v = scale * acc;
+    const bf16 hi = __float2bfloat16_rn(v);
+    out[idx] = hi;
+    if (out_lo) out_lo[idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
 // Factor from Gram partials: M[p][q] = sc * sum_z part[z][min][max] (p,q < P),
@@ -818,7 +829,7 @@ __global__ void k_last_layer_terms(const bf16* __restrict__ T_hi, const bf16* __
 // ============================================================================
 template <int MODE, bool SPLIT>
 kfac_status_t launch_engine_as(kfac_pinn_handle* h, cudaStream_t s, const Args& a, dim3 grid) {
-    using C = tck::Cfg<MODE>;
+    using C = tck::Cfg<MODE, SPLIT>;
     static bool attr_set = false;
     if (!attr_set) {
         if (cudaFuncSetAttribute(tck::tc_engine<MODE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
@@ -830,8 +841,12 @@ kfac_status_t launch_engine_as(kfac_pinn_handle* h, cudaStream_t s, const Args& 
     return KFAC_OK;
 }
 
+// work: the method's FLOPs of the launch (real sizes, one product per
+// contraction); exec: the tensor-core FLOPs it issues (padded tiles, every
+// split-BF16 product).
 template <int MODE>
-kfac_status_t launch_engine(kfac_pinn_handle* h, cudaStream_t s, const Args& a, dim3 grid, int kclass, double work) {
+kfac_status_t launch_engine(kfac_pinn_handle* h, cudaStream_t s, const Args& a, dim3 grid, int kclass, double work,
+                            double exec) {
     if (grid.x == 0 || grid.y == 0 || grid.z == 0) return KFAC_OK;
     timer_begin(h, kclass, s);
     kfac_status_t st;
@@ -843,7 +858,7 @@ kfac_status_t launch_engine(kfac_pinn_handle* h, cudaStream_t s, const Args& a, 
         st = launch_engine_as<MODE, false>(h, s, a, grid);
     }
     if (st) return st;
-    timer_end(h, kclass, s, work);
+    timer_end(h, kclass, s, work, exec);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }
@@ -983,8 +998,8 @@ kfac_status_t tune_measure(kfac_pinn_handle* h, cudaStream_t s, kfac_tune_entry_
 // Tangent-tile chunk length of a FWD_TAN / BWD_TAN launch: the table's, else
 // the model's, measured first when the tuner may.
 template <class F>
-kfac_status_t tangent_chunk(kfac_pinn_handle* h, cudaStream_t s, int kind, int N_pad, int hp_out, int hp_in,
-                            int S_tiles, int blocks, F&& launch, int& len) {
+kfac_status_t tangent_chunk(kfac_pinn_handle* h, cudaStream_t s, int kind, int split, int N_pad, int hp_out,
+                            int hp_in, int S_tiles, int blocks, F&& launch, int& len) {
     const Cands c = tangent_candidates(S_tiles, blocks, h->sm_count);
     len = c.len[c.model];
     kfac_tune_entry_t key;
@@ -994,7 +1009,7 @@ kfac_status_t tangent_chunk(kfac_pinn_handle* h, cudaStream_t s, int kind, int N
     key.Q = hp_out;
     key.K = hp_in;
     key.tiles = S_tiles;
-    key.split = is_split_all(h) ? 1 : 0;
+    key.split = split;
     const int ti = tune_find(h, key);
     if (ti >= 0) {
         const int t = h->tune[ti].chunk;
@@ -1056,12 +1071,20 @@ kfac_status_t alloc_pass(kfac_pinn_handle* h, MxPass& P, int Nmax, int S) {
     if ((st = dal(&P.zl, (size_t)P.rows))) return st;
     if ((st = dal(&P.Xf, (size_t)P.N_pad * h->dims[0]))) return st;
     if (S > 1 && h->cfg.variant == KFAC_REDUCE) {
+        const bool sa = is_split_all(h);
         if ((st = dal(&P.red_a, (size_t)P.N_pad * hp_max))) return st;
         if ((st = dal(&P.red_g, (size_t)P.N_pad * hp_max))) return st;
+        if (sa) {
+            if ((st = dal(&P.red_a_lo, (size_t)P.N_pad * hp_max))) return st;
+            if ((st = dal(&P.red_g_lo, (size_t)P.N_pad * hp_max))) return st;
+        }
         for (int l = 1; l <= L - 1; l++) {
             int hp = P.lay[l - 1].hp;
             if (!tc_make_tmap_2d(&P.gRa[l - 1], P.red_a, hp, P.N_pad, hp * 2, 64, 64) ||
                 !tc_make_tmap_2d(&P.gRg[l - 1], P.red_g, hp, P.N_pad, hp * 2, 64, 64))
+                return KFAC_CUDA_ERROR;
+            if (sa && (!tc_make_tmap_2d(&P.gRa_lo[l - 1], P.red_a_lo, hp, P.N_pad, hp * 2, 64, 64) ||
+                       !tc_make_tmap_2d(&P.gRg_lo[l - 1], P.red_g_lo, hp, P.N_pad, hp * 2, 64, 64)))
                 return KFAC_CUDA_ERROR;
         }
     }
@@ -1079,6 +1102,8 @@ void free_pass(MxPass& P) {
     cudaFree(P.Xf);
     cudaFree(P.red_a);
     cudaFree(P.red_g);
+    cudaFree(P.red_a_lo);
+    cudaFree(P.red_g_lo);
 }
 
 // Gram over rows: part[z][p][q] = sum_{rows in chunk z} X[row][p] Y[row][q].
@@ -1087,7 +1112,7 @@ void free_pass(MxPass& P) {
 // length comes from the tuning table, else from the wave model (measured
 // first when the tuner may).
 kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, const CUtensorMap& Y, int P, int Q,
-                   int rows, int sym, float* part, int& nz, const CUtensorMap* X_lo = nullptr,
+                   int rows, int alg_rows, int sym, float* part, int& nz, const CUtensorMap* X_lo = nullptr,
                    const CUtensorMap* Y_lo = nullptr) {
     using C = tck::Cfg<tck::GRAM>;
     int p_tiles = (P + 127) / 128, q_tiles = (Q + C::BN - 1) / C::BN;
@@ -1121,10 +1146,14 @@ kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, co
         a.b1 = *Y_lo;
         a.split_all = 1;
     }
-    const double work = 2.0 * (double)tiles * 128 * C::BN * rows;   // algorithmic: one product per entry
+    // the method's work: the n (n + 1) / 2 entries of a symmetric Gram (P x Q
+    // otherwise) over the real rows, one product each; executed: whole tiles
+    // over the padded rows, three products when split
+    const double work = sym ? (double)P * (P + 1) * alg_rows : 2.0 * (double)P * Q * alg_rows;
+    const double exec = 2.0 * (double)tiles * 128 * C::BN * rows * (split ? 3 : 1);
     auto launch = [&](int cl) {
         a.row_chunk = cl;
-        return launch_engine<tck::GRAM>(h, s, a, dim3(tiles, (rows + cl - 1) / cl, 1), KFAC_KC_GRAM, work);
+        return launch_engine<tck::GRAM>(h, s, a, dim3(tiles, (rows + cl - 1) / cl, 1), KFAC_KC_GRAM, work, exec);
     };
 
     int chunk = c.len[c.model];
@@ -1185,6 +1214,7 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
                            MxPass& P, BlockSel sel) {
     MxState* m = MX(h);
     const int L = h->cfg.L, d = h->dims[0], S = P.S;
+    const int split = sel.split_all;     // split-BF16 on every row (else value / Laplacian / time rows only)
     {
         MxLayer& l1 = P.lay[0];
         long long cnt = (long long)P.N_pad * l1.hp;
@@ -1194,7 +1224,7 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
         k_layer1<<<ceil_div_u(cnt / 4, EW), EW, 0, s>>>(m->w.W1f, m->w.W1Qf ? m->w.W1Qf : m->w.W1f, P.Xf, N,
                                                          P.N_pad, d, l1.h, l1.hp, S, h->chw32,
                                                          (h->cfg.op == KFAC_OP_HEAT && S > 2) ? 1 : 0,
-                                                         is_split_all(h) ? 1 : 0, l1.T_hi, l1.T_lo, l1.A0, l1.AD,
+                                                         split, l1.T_hi, l1.T_lo, l1.A0, l1.AD,
                                                          l1.SSQ);
         timer_end(h, KFAC_KC_ELEMENTWISE, s, 2.0 * (double)S * cnt + 16.0 * cnt);
         KFAC_LAUNCH_CHECK(h);
@@ -1203,6 +1233,7 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
         MxLayer& in = P.lay[l - 2];
         MxLayer& out = P.lay[l - 1];
         Args a = base_args(h, P, N);
+        a.split_all = split;
         a.a0 = in.kT_hi;
         a.a1 = in.kT_lo;
         a.b0 = m->w.kW_hi[l - 1];
@@ -1217,8 +1248,11 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
         a.AD = out.AD;
         a.part = m->part;
         const int jb = (out.hp + 127) / 128, pb = P.N_pad / 128;
-        double fl = 2.0 * P.N_pad * (double)out.hp * in.hp;
-        kfac_status_t st = launch_engine<tck::FWD_VALUE>(h, s, a, dim3(jb, pb, 1), KFAC_KC_LAYER_GEMM, 3 * fl);
+        // per Taylor row block: the method's FLOPs (real sizes) and the executed
+        // tensor FLOPs of one product over the padded tile
+        const double alg = 2.0 * N * (double)out.h * in.h;
+        const double fl = 2.0 * P.N_pad * (double)out.hp * in.hp;
+        kfac_status_t st = launch_engine<tck::FWD_VALUE>(h, s, a, dim3(jb, pb, 1), KFAC_KC_LAYER_GEMM, alg, 3 * fl);
         if (st) return st;
         if (S > 1) {
             const int tiles = S - 1;
@@ -1226,17 +1260,17 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
                 a.chunk_len = len;
                 a.n_chunks = (tiles + len - 1) / len;
                 return launch_engine<tck::FWD_TANLAP>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_LAYER_GEMM,
-                                                      fl * (S + 1));
+                                                      alg * (S - 1), fl * (a.split_all ? 3 * (S - 1) : S + 1));
             };
             int len = 0;
-            if ((st = tangent_chunk(h, s, KFAC_TUNE_FWD_TAN, P.N_pad, out.hp, in.hp, tiles, jb * pb, launch, len)))
+            if ((st = tangent_chunk(h, s, KFAC_TUNE_FWD_TAN, split, P.N_pad, out.hp, in.hp, tiles, jb * pb, launch,
+                                    len)))
                 return st;
             if ((st = launch(len))) return st;
             long long cnt = (long long)P.N_pad * out.hp;
             timer_begin(h, KFAC_KC_ELEMENTWISE, s);
             k_lap_finish<<<ceil_div_u(cnt, EW), EW, 0, s>>>(m->part, a.n_chunks, N, P.N_pad, out.h, out.hp, S,
-                                                             out.A0, out.AD, out.SSQ, out.T_hi, out.T_lo,
-                                                             is_split_all(h) ? 1 : 0);
+                                                             out.A0, out.AD, out.SSQ, out.T_hi, out.T_lo, split);
             timer_end(h, KFAC_KC_ELEMENTWISE, s, (4.0 * a.n_chunks + 16.0) * cnt);
             KFAC_LAUNCH_CHECK(h);
         }
@@ -1291,24 +1325,26 @@ kfac_status_t backward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* r
         a.ytan = dn.T_hi;
         a.r = r;
         const int jb = (dn.hp + 127) / 128, pb = P.N_pad / 128;
-        double fl = 2.0 * P.N_pad * (double)up.hp * dn.hp;
+        const double alg = 2.0 * N * (double)up.h * dn.h;
+        const double fl = 2.0 * P.N_pad * (double)up.hp * dn.hp * (a.split_all ? 3 : 1);
         kfac_status_t st;
         if (S > 1) {
-            st = launch_engine<tck::BWD_LAP>(h, s, a, dim3(jb, pb, 1), KFAC_KC_ADJOINT_GEMM, fl);
+            st = launch_engine<tck::BWD_LAP>(h, s, a, dim3(jb, pb, 1), KFAC_KC_ADJOINT_GEMM, alg, fl);
             if (st) return st;
             const int tiles = S - 2;
             auto launch = [&](int len) {
                 a.chunk_len = len;
                 a.n_chunks = (tiles + len - 1) / len;
                 return launch_engine<tck::BWD_TAN>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_ADJOINT_GEMM,
-                                                   fl * (S - 2));
+                                                   alg * (S - 2), fl * (S - 2));
             };
             int len = 0;
-            if ((st = tangent_chunk(h, s, KFAC_TUNE_BWD_TAN, P.N_pad, dn.hp, up.hp, tiles, jb * pb, launch, len)))
+            if ((st = tangent_chunk(h, s, KFAC_TUNE_BWD_TAN, a.split_all, P.N_pad, dn.hp, up.hp, tiles, jb * pb,
+                                    launch, len)))
                 return st;
             if ((st = launch(len))) return st;
         }
-        st = launch_engine<tck::BWD_VALUE>(h, s, a, dim3(jb, pb, 1), KFAC_KC_ADJOINT_GEMM, fl);
+        st = launch_engine<tck::BWD_VALUE>(h, s, a, dim3(jb, pb, 1), KFAC_KC_ADJOINT_GEMM, alg, fl);
         if (st) return st;
     }
     return KFAC_OK;
@@ -1356,11 +1392,14 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
         MxLayer& lb = B.lay[l - 1];
         if (reduce) {
             long long cnt = (long long)I.N_pad * li.hp;
-            k_sum_over_s<<<ceil_div_u(cnt, EW), EW, 0, s>>>(li.Zb, I.N_pad, S, li.hp, 1.f, I.red_g);
+            k_sum_over_s<<<ceil_div_u(cnt, EW), EW, 0, s>>>(li.Zb, sa ? li.Zb_lo : nullptr, I.N_pad, S, li.hp, 1.f,
+                                                             I.red_g, sa ? I.red_g_lo : nullptr);
             KFAC_LAUNCH_CHECK(h);
-            if ((st = gram(h, s, I.gRg[l - 1], I.gRg[l - 1], li.h, li.h, I.N_pad, 1, part_i, zi))) return st;
+            if ((st = gram(h, s, I.gRg[l - 1], I.gRg[l - 1], li.h, li.h, I.N_pad, N, 1, part_i, zi,
+                           sa ? &I.gRg_lo[l - 1] : nullptr, sa ? &I.gRg_lo[l - 1] : nullptr)))
+                return st;
         } else {
-            if ((st = gram(h, s, li.gZb, li.gZb, li.h, li.h, I.rows, 1, part_i, zi, sa ? &li.gZb_lo : nullptr,
+            if ((st = gram(h, s, li.gZb, li.gZb, li.h, li.h, I.rows, S * N, 1, part_i, zi, sa ? &li.gZb_lo : nullptr,
                            sa ? &li.gZb_lo : nullptr)))
                 return st;
         }
@@ -1368,7 +1407,7 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
         k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_i, zi, li.h, 1, nullptr, 1.0 / N, 0.0, 0.0, 0,
                                                          h->fac[KFAC_B_INT][l - 1], beta, h->status);
         KFAC_LAUNCH_CHECK(h);
-        if ((st = gram(h, s, lb.gZb, lb.gZb, lb.h, lb.h, B.rows, 1, part_b, zb, sa ? &lb.gZb_lo : nullptr,
+        if ((st = gram(h, s, lb.gZb, lb.gZb, lb.h, lb.h, B.rows, Nb, 1, part_b, zb, sa ? &lb.gZb_lo : nullptr,
                        sa ? &lb.gZb_lo : nullptr)))
             return st;
         k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_b, zb, lb.h, 1, nullptr, 1.0 / Nb, 0.0, 0.0, 0,
@@ -1384,16 +1423,20 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
         // interior A_l
         if (reduce) {
             long long cnt = (long long)I.N_pad * ti.hp;
-            k_sum_over_s<<<ceil_div_u(cnt, EW), EW, 0, s>>>(ti.T_hi, I.N_pad, S, ti.hp, 1.f / S, I.red_a);
+            k_sum_over_s<<<ceil_div_u(cnt, EW), EW, 0, s>>>(ti.T_hi, sa ? ti.T_lo : nullptr, I.N_pad, S, ti.hp,
+                                                             1.f / S, I.red_a, sa ? I.red_a_lo : nullptr);
             KFAC_LAUNCH_CHECK(h);
-            if ((st = gram(h, s, I.gRa[l - 2], I.gRa[l - 2], hin, hin, I.N_pad, 1, part_i, zi))) return st;
-            k_colsum<<<ceil_div_u(hin, 32), RED_THREADS, 0, s>>>(I.red_a, nullptr, ti.hp, 0, N, hin, cs_i);
+            if ((st = gram(h, s, I.gRa[l - 2], I.gRa[l - 2], hin, hin, I.N_pad, N, 1, part_i, zi,
+                           sa ? &I.gRa_lo[l - 2] : nullptr, sa ? &I.gRa_lo[l - 2] : nullptr)))
+                return st;
+            k_colsum<<<ceil_div_u(hin, 32), RED_THREADS, 0, s>>>(I.red_a, sa ? I.red_a_lo : nullptr, ti.hp, 0, N, hin,
+                                                                  cs_i);
             KFAC_LAUNCH_CHECK(h);
             k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_i, zi, hin, 1, cs_i, 1.0 / N, 1.0 / ((double)N * S),
                                                              1.0 / ((double)S * S), 1, h->fac[KFAC_A_INT][l - 1], beta,
                                                              h->status);
         } else {
-            if ((st = gram(h, s, ti.gT, ti.gT, hin, hin, I.rows, 1, part_i, zi, sa ? &ti.gT_lo : nullptr,
+            if ((st = gram(h, s, ti.gT, ti.gT, hin, hin, I.rows, S * N, 1, part_i, zi, sa ? &ti.gT_lo : nullptr,
                            sa ? &ti.gT_lo : nullptr)))
                 return st;
             k_colsum<<<ceil_div_u(hin, 32), RED_THREADS, 0, s>>>(ti.T_hi, ti.T_lo, ti.hp, 0, N, hin, cs_i);
@@ -1404,7 +1447,7 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
         }
         KFAC_LAUNCH_CHECK(h);
         // boundary A_l
-        if ((st = gram(h, s, tb.gT, tb.gT, hin, hin, B.rows, 1, part_b, zb, sa ? &tb.gT_lo : nullptr,
+        if ((st = gram(h, s, tb.gT, tb.gT, hin, hin, B.rows, Nb, 1, part_b, zb, sa ? &tb.gT_lo : nullptr,
                        sa ? &tb.gT_lo : nullptr)))
             return st;
         k_colsum<<<ceil_div_u(hin, 32), RED_THREADS, 0, s>>>(tb.T_hi, tb.T_lo, tb.hp, 0, Nb, hin, cs_b);
@@ -1417,10 +1460,10 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
             MxLayer& gi = I.lay[l - 1];
             MxLayer& gb = B.lay[l - 1];
             const int hout = gi.h;
-            if ((st = gram(h, s, gi.gGr, ti.gT, hout, hin, I.rows, 0, part_i, zi, sa ? &gi.gGr_lo : nullptr,
+            if ((st = gram(h, s, gi.gGr, ti.gT, hout, hin, I.rows, S * N, 0, part_i, zi, sa ? &gi.gGr_lo : nullptr,
                            sa ? &ti.gT_lo : nullptr)))
                 return st;
-            if ((st = gram(h, s, gb.gGr, tb.gT, hout, hin, B.rows, 0, part_b, zb, sa ? &gb.gGr_lo : nullptr,
+            if ((st = gram(h, s, gb.gGr, tb.gT, hout, hin, B.rows, Nb, 0, part_b, zb, sa ? &gb.gGr_lo : nullptr,
                            sa ? &tb.gT_lo : nullptr)))
                 return st;
             k_colsum<<<ceil_div_u(hout, 32), RED_THREADS, 0, s>>>(gi.Gr, gi.Gr_lo, gi.hp, 0, N, hout, cs_i);
@@ -1558,8 +1601,14 @@ void tc_free(kfac_pinn_handle* h) {
 namespace {
 
 // Forward passes of both terms and their residuals into h->in.r / h->bd.r.
+// trial: a line-search trial loss.  Its forward pass keeps split-BF16 on the
+// rows the residuals read through (value, second-order and heat time rows)
+// and runs the tangent rows in plain BF16 also for a split-everywhere handle:
+// the trial loss only ranks the grid points, and the curvature pass of the
+// step (factors, gradient, direction) stays split on every row.
 kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int,
-                                    int N_int, const double* f, const double* X_bdy, int N_bdy, const double* g) {
+                                    int N_int, const double* f, const double* X_bdy, int N_bdy, const double* g,
+                                    bool trial = false) {
     MxState* m = MX(h);
     kfac_status_t st;
     const int S = m->in.S;
@@ -1572,7 +1621,7 @@ kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const d
     sb.b[0] = 0;
     sb.b[1] = sb.b[2] = 0;
     sb.split_time = 0;
-    sb.split_all = is_split_all(h) ? 1 : 0;
+    sb.split_all = (is_split_all(h) && !trial) ? 1 : 0;
     KFAC_CUDA_TRY(cudaEventRecord(m->fork, s));
     KFAC_CUDA_TRY(cudaStreamWaitEvent(m->side, m->fork, 0));
     st = forward_pass(h, m->side, theta, X_bdy, N_bdy, m->bd, sb);
@@ -1594,7 +1643,7 @@ kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const d
     si.b[1] = 1;
     si.b[2] = 0;
     si.split_time = heat;
-    si.split_all = is_split_all(h) ? 1 : 0;
+    si.split_all = (is_split_all(h) && !trial) ? 1 : 0;
     st = forward_pass(h, s, theta, X_int, N_int, m->in, si);
     if (st == KFAC_OK) {
         k_residual_mx<<<ceil_div_u(N_int, EW), EW, 0, s>>>(m->in.zl, f, h->in.r, N_int, m->in.N_pad, S, 1, h->cT,
@@ -1628,7 +1677,7 @@ kfac_status_t tc_factors(kfac_pinn_handle* h, cudaStream_t s, const double* thet
 kfac_status_t tc_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int, int N_int,
                            const double* f, const double* X_bdy, int N_bdy, const double* g, double* dst) {
     kfac_status_t st;
-    if ((st = forward_and_residuals(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g))) return st;
+    if ((st = forward_and_residuals(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g, true))) return st;
     return fp64_loss_to(h, s, N_int, N_bdy, dst);
 }
 
@@ -1686,8 +1735,11 @@ kfac_status_t tc_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s,
     for (int l = 2; l <= L - 1; l++) {
         MxLayer& ti = I.lay[l - 2];
         MxLayer& gi = I.lay[l - 1];
-        if ((st = gram(h, s, gi.gGr, ti.gT, gi.h, ti.h, I.rows, 0, part, z))) return st;
-        k_colsum<<<ceil_div_u(gi.h, 32), RED_THREADS, 0, s>>>(gi.Gr, nullptr, gi.hp, 0, N, gi.h, cs);
+        const bool sa = is_split_all(h);
+        if ((st = gram(h, s, gi.gGr, ti.gT, gi.h, ti.h, I.rows, S * N, 0, part, z, sa ? &gi.gGr_lo : nullptr,
+                       sa ? &ti.gT_lo : nullptr)))
+            return st;
+        k_colsum<<<ceil_div_u(gi.h, 32), RED_THREADS, 0, s>>>(gi.Gr, sa ? gi.Gr_lo : nullptr, gi.hp, 0, N, gi.h, cs);
         KFAC_LAUNCH_CHECK(h);
         k_grad_reduce<<<ceil_div_u((long long)gi.h * (ti.h + 1), EW), EW, 0, s>>>(part, z, part, 0, gi.h, ti.h, cs, cs,
                                                                                   1.0, 0.0, G + h->woff[l - 1]);
@@ -1743,15 +1795,17 @@ kfac_status_t jvp_pass(kfac_pinn_handle* h, cudaStream_t s, MxPass& P, int N, bo
         a.A0 = out.A0;
         a.YD = out.YD;
         const int jb = (out.hp + 127) / 128, pb = P.N_pad / 128;
+        // two contractions per row block: T dW~^T and dT W^T
+        const double alg = 2.0 * 2.0 * N * (double)out.h * in.h;
         const double fl = 2.0 * 2.0 * P.N_pad * (double)out.hp * in.hp;
-        if ((st = launch_engine<tck::JVP_VALUE>(h, s, a, dim3(jb, pb, 1), KFAC_KC_LAYER_GEMM, fl))) return st;
+        if ((st = launch_engine<tck::JVP_VALUE>(h, s, a, dim3(jb, pb, 1), KFAC_KC_LAYER_GEMM, alg, fl))) return st;
         if (S > 1) {
             a.ytan = out.T_hi;
             a.DAD = m->jdad[l - 1];
             a.part = m->part;
             choose_chunks(S - 1, jb * pb, h->sm_count, a.chunk_len, a.n_chunks);
             if ((st = launch_engine<tck::JVP_TAN>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_LAYER_GEMM,
-                                                  fl * (S - 1))))
+                                                  alg * (S - 1), fl * (S - 1))))
                 return st;
             const long long cnt = (long long)P.N_pad * out.hp;
             k_jvp_lap_finish<<<ceil_div_u(cnt, EW), EW, 0, s>>>(m->part, a.n_chunks, N, P.N_pad, out.h, out.hp, S,
