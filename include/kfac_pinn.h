@@ -59,13 +59,26 @@ typedef enum {
                               Laplacian columns) with FP32 accumulation for the
                               Taylor pass, adjoint, gradient and Grams; FP64
                               for loss, factors, Cholesky and eigensolver      */
-    KFAC_MIXED_SPLIT = 2   /* the same tensor-core path with split-BF16 (hi +
+    KFAC_MIXED_SPLIT = 2,  /* the same tensor-core path with split-BF16 (hi +
                               lo, about 16 significant bits, three products
                               per contraction) on every Taylor column, every
                               adjoint and every Gram: per-result errors near
                               1e-5 against FP64, at about three times the
-                              tensor work.  Expand variant, FIXED and
-                              LINE_SEARCH updates only (create rejects others) */
+                              tensor work.  For d >= 32 the 31 trial losses
+                              of the LINE_SEARCH update run the
+                              KFAC_MIXED_BF16 forward pass (split value,
+                              second-order and time columns; plain BF16
+                              tangents, whose roundings average over the d
+                              tangents of the second-order column): a trial
+                              loss only ranks the grid points                */
+    KFAC_FP32 = 3          /* the SIMT path of KFAC_FP64 with FP32 storage and
+                              FP32 arithmetic (CUDA cores) for the Taylor pass
+                              and its adjoint; the sums over the collocation
+                              points (gradient and factor Grams) multiply the
+                              FP32 operands exactly in FP64 and accumulate in
+                              FP64; FP64 for residuals, loss, factors (EMA),
+                              Cholesky, eigensolver and preconditioning.
+                              Per-result errors near 1e-7 against FP64       */
 } kfac_precision_t;
 
 typedef enum { KFAC_EXPAND = 0, KFAC_REDUCE = 1 } kfac_variant_t;
@@ -91,9 +104,11 @@ typedef enum { KFAC_OP_LAPLACE = 0, KFAC_OP_HEAT = 1, KFAC_OP_GENERAL = 2 } kfac
  * AUTO:        delta = alpha* Delta + mu* delta_prev with (alpha*, mu*) the
  *              minimiser of the quadratic model with the exact damped Gramian
  *              G + lambda I (KFAC* of the paper; lr and momentum unused).  The
- *              Gramian products come from forward-mode passes through the
- *              Taylor pass: FP64, or on the tensor cores (BF16 operands, FP32
- *              accumulation) for a mixed-precision handle. */
+ *              Gramian products need J v per point: on an FP64 handle a
+ *              forward-mode pass through the Taylor pass; on a tensor-core
+ *              handle sum_l sum_s g_{n,s}^T V_l T^_{n,s} from the activations
+ *              and adjoints the step's curvature pass stored (Sec. 3.2), in
+ *              that handle's precision. */
 typedef enum { KFAC_UPDATE_FIXED = 0, KFAC_UPDATE_LINE_SEARCH = 1, KFAC_UPDATE_AUTO = 2 } kfac_update_t;
 
 /* Factor selector of kfac_pinn_get_factor / kfac_pinn_set_factor. */
@@ -226,7 +241,7 @@ kfac_status_t kfac_pinn_set_graph(kfac_handle_t h, int enable);
  * a graph.  Enabling frees the handle's graph (kfac_pinn_set_graph), so the
  * next step runs eagerly and measures; a kfac_pinn_batch holding the handle
  * keeps the lengths its graph was captured with until it re-captures.  The
- * FP64 precision and the forward-mode products of the AUTO update have no
+ * FP64 precision and the Jacobian-vector products of the AUTO update have no
  * tuned launches.  Default: disabled.  Errors: KFAC_BAD_ARG for a NULL
  * handle. */
 #define KFAC_TUNE_CAP 128
@@ -432,7 +447,10 @@ kfac_status_t kfac_pinn_batch_step(kfac_batch_t b, void* stream, double* const* 
  * static 32 MiB scratch array in device memory that every GPU loading this
  * library holds until the process exits.
  *   - Inputs and outputs are caller-owned device pointers as in
- *     kfac_pinn_forward_laplacian; N >= 1.
+ *     kfac_pinn_forward_laplacian; N >= 1.  cfg must pass the network checks
+ *     of kfac_pinn_create (d, L, widths, operator); the other fields are
+ *     ignored.  KFAC_OP_GENERAL returns KFAC_BAD_ARG: its tangent directions
+ *     are set up on a handle. 
  *   - Capacity: d + sum over layers l of (2 if l < L else 1) * (d+2) * N * h_l
  *     doubles must not exceed 4,194,304 (32 MiB); larger requests return
  *     KFAC_BAD_ARG and queue nothing.

@@ -15,7 +15,7 @@ from . import _lib
 from ._lib import KfacConfig, KfacError
 
 OPS = {"laplace": 0, "heat": 1, "general": 2}
-PRECISIONS = {"fp64": 0, "mixed_bf16": 1, "mixed_split": 2}
+PRECISIONS = {"fp64": 0, "mixed_bf16": 1, "mixed_split": 2, "fp32": 3}
 VARIANTS = {"expand": 0, "reduce": 1}
 FACTORS = {"A_int": 0, "B_int": 1, "A_bdy": 2, "B_bdy": 3}
 UPDATES = {"fixed": 0, "line_search": 1, "kfac_star": 2}

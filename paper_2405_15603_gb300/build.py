@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libkfacpinn.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["abi.cu", "fp64_path.cu", "linalg.cu", "eig.cu", "tc_path.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["abi.cu", "simt_path.cu", "linalg.cu", "eig.cu", "tc_path.cu", "noalloc.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

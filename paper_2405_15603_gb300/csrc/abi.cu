@@ -10,7 +10,11 @@
 
 namespace {
 
-bool valid_config(const kfac_config_t* c) {
+}  // namespace
+
+// The network and operator part of a configuration: d, L, widths (each at
+// most 1023, the last 1, d + 1 at most 1024) and the operator.
+bool kfac_valid_network(const kfac_config_t* c) {
     if (!c) return false;
     if (c->d < 1 || c->L < 1 || c->L > KFAC_MAX_LAYERS) return false;
     for (int l = 0; l < c->L; l++)
@@ -18,6 +22,14 @@ bool valid_config(const kfac_config_t* c) {
     if (c->widths[c->L - 1] != 1) return false;
     if (c->d + 1 > 1024) return false;
     if (c->op != KFAC_OP_LAPLACE && c->op != KFAC_OP_HEAT && c->op != KFAC_OP_GENERAL) return false;
+    if (c->op == KFAC_OP_HEAT && c->d < 2) return false;
+    return true;
+}
+
+namespace {
+
+bool valid_config(const kfac_config_t* c) {
+    if (!kfac_valid_network(c)) return false;
     if (c->op == KFAC_OP_GENERAL) {
         if (!c->op_coef || c->variant != KFAC_EXPAND) return false;
         double mx = 0.0;
@@ -29,9 +41,9 @@ bool valid_config(const kfac_config_t* c) {
             for (int j = 0; j < i; j++)
                 if (fabs(c->op_coef[i * c->d + j] - c->op_coef[j * c->d + i]) > 1e-12 * mx) return false;
     }
-    if (c->op == KFAC_OP_HEAT && c->d < 2) return false;
-    if (c->precision != KFAC_FP64 && c->precision != KFAC_MIXED_BF16 && c->precision != KFAC_MIXED_SPLIT) return false;
-    if (c->precision == KFAC_MIXED_SPLIT && (c->variant != KFAC_EXPAND || c->update == KFAC_UPDATE_AUTO)) return false;
+    if (c->precision != KFAC_FP64 && c->precision != KFAC_MIXED_BF16 && c->precision != KFAC_MIXED_SPLIT &&
+        c->precision != KFAC_FP32)
+        return false;
     if (c->variant != KFAC_EXPAND && c->variant != KFAC_REDUCE) return false;
     if (!(c->beta >= 0.0 && c->beta < 1.0)) return false;
     if (!(c->lambda > 0.0) || !isfinite(c->lambda)) return false;
@@ -44,14 +56,21 @@ bool valid_config(const kfac_config_t* c) {
     return true;
 }
 
-template <class T>
-kfac_status_t dalloc(T** p, size_t elems) {
+kfac_status_t dalloc_bytes(void** p, size_t bytes) {
     *p = nullptr;
-    if (elems == 0) elems = 1;
-    cudaError_t e = cudaMalloc((void**)p, elems * sizeof(T));
+    if (bytes == 0) bytes = 1;
+    cudaError_t e = cudaMalloc(p, bytes);
     if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); *p = nullptr; return KFAC_OOM; }
     if (e != cudaSuccess) { *p = nullptr; return KFAC_CUDA_ERROR; }
     return KFAC_OK;
+}
+
+template <class T>
+kfac_status_t dalloc(T** p, size_t elems) {
+    void* v = nullptr;
+    kfac_status_t st = dalloc_bytes(&v, elems * sizeof(T));
+    *p = (T*)v;
+    return st;
 }
 
 // Symmetric eigendecomposition C = Q diag(lam) Q^T on the host (cyclic
@@ -191,11 +210,12 @@ kfac_status_t alloc_pass(kfac_pinn_handle* h, PassBuffers& pb, int N, int S) {
     if (is_mixed(h)) {   // the mixed path keeps its own BF16 activations
         return dalloc(&pb.r, (size_t)N);
     }
+    const size_t eb = simt_elem_bytes(h);   // FP64 or FP32 activations
     for (int l = 1; l <= L; l++) {
-        size_t e = (size_t)S * N * h->dims[l];
-        if ((st = dalloc(&pb.Z[l - 1], e))) return st;
-        if ((st = dalloc(&pb.Zb[l - 1], e))) return st;
-        if (l < L && (st = dalloc(&pb.T[l - 1], e))) return st;
+        size_t e = (size_t)S * N * h->dims[l] * eb;
+        if ((st = dalloc_bytes(&pb.Z[l - 1], e))) return st;
+        if ((st = dalloc_bytes(&pb.Zb[l - 1], e))) return st;
+        if (l < L && (st = dalloc_bytes(&pb.T[l - 1], e))) return st;
         if (h->dims[l] > maxw) maxw = h->dims[l];
     }
     if (h->dims[0] + 1 > maxw) maxw = h->dims[0] + 1;
@@ -203,8 +223,8 @@ kfac_status_t alloc_pass(kfac_pinn_handle* h, PassBuffers& pb, int N, int S) {
         if (h->dims[l] + 1 > maxw) maxw = h->dims[l] + 1;
     if ((st = dalloc(&pb.r, (size_t)N))) return st;
     if (S > 1 && h->cfg.variant == KFAC_REDUCE) {
-        if ((st = dalloc(&pb.red_a, (size_t)N * maxw))) return st;
-        if ((st = dalloc(&pb.red_g, (size_t)N * maxw))) return st;
+        if ((st = dalloc_bytes(&pb.red_a, (size_t)N * maxw * eb))) return st;
+        if ((st = dalloc_bytes(&pb.red_g, (size_t)N * maxw * eb))) return st;
     }
     return KFAC_OK;
 }
@@ -275,14 +295,14 @@ kfac_status_t run_factors(kfac_pinn_handle* h, cudaStream_t s, const double* the
         return tc_factors(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g, loss);
     kfac_status_t st;
     const int S = h->S;
-    if ((st = fp64_forward(h, s, theta, X_int, N_int, h->in, S))) return st;
-    if ((st = fp64_residual_and_seed(h, s, h->in, N_int, S, f, true))) return st;
-    if ((st = fp64_backward(h, s, theta, h->in, N_int, S))) return st;
-    if ((st = fp64_forward(h, s, theta, X_bdy, N_bdy, h->bd, 1))) return st;
-    if ((st = fp64_residual_and_seed(h, s, h->bd, N_bdy, 1, g, false))) return st;
-    if ((st = fp64_backward(h, s, theta, h->bd, N_bdy, 1))) return st;
+    if ((st = simt_forward(h, s, theta, X_int, N_int, h->in, S))) return st;
+    if ((st = simt_residual_and_seed(h, s, h->in, N_int, S, f, true))) return st;
+    if ((st = simt_backward(h, s, theta, h->in, N_int, S))) return st;
+    if ((st = simt_forward(h, s, theta, X_bdy, N_bdy, h->bd, 1))) return st;
+    if ((st = simt_residual_and_seed(h, s, h->bd, N_bdy, 1, g, false))) return st;
+    if ((st = simt_backward(h, s, theta, h->bd, N_bdy, 1))) return st;
     if ((st = fp64_loss(h, s, N_int, N_bdy, loss))) return st;
-    if ((st = fp64_grad_and_factors(h, s, X_int, N_int, X_bdy, N_bdy))) return st;
+    if ((st = simt_grad_and_factors(h, s, X_int, N_int, X_bdy, N_bdy))) return st;
     return KFAC_OK;
 }
 
@@ -464,7 +484,7 @@ kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out) {
     }
     // the mixed path's batched preconditioning holds every layer's two
     // scratch matrices at once
-    if (cfg->precision != KFAC_FP64) tmp = std::max(tmp, 2 * (size_t)h->D);
+    if (is_mixed(h)) tmp = std::max(tmp, 2 * (size_t)h->D);
     h->tmp_elems = tmp;
     TRY(dalloc(&h->tmp, tmp));
     TRY(dalloc(&h->loss, 3));
@@ -475,7 +495,7 @@ kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out) {
     TRY(dalloc(&h->status, 1));
     h->stage_elems = (size_t)cfg->max_n_int * (cfg->d + 1) + (size_t)cfg->max_n_bdy * (cfg->d + 1) + 8;
     TRY(dalloc(&h->stage, h->stage_elems));
-    if (cfg->precision != KFAC_FP64) TRY(tc_alloc(h));
+    if (is_mixed(h)) TRY(tc_alloc(h));
     TRY(eig_alloc(h));
     if (cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) { free_handle(h); return KFAC_CUDA_ERROR; }
     TRY(reset_state(h, 0));
@@ -513,14 +533,14 @@ kfac_status_t kfac_pinn_forward_laplacian(kfac_handle_t h, void* stream, const d
             st = tc_forward_laplacian(h, s, theta, X + (long long)off * d, n, u + off,
                                       grad ? grad + (long long)off * d : nullptr, lap ? lap + off : nullptr);
         } else {
-            st = fp64_forward(h, s, theta, X + (long long)off * d, n, h->in, S);
+            st = simt_forward(h, s, theta, X + (long long)off * d, n, h->in, S);
             if (st == KFAC_OK)
-                st = fp64_extract_outputs(h, s, h->in, n, S, u + off,
+                st = simt_extract_outputs(h, s, h->in, n, S, u + off,
                                           grad ? grad + (long long)off * d : nullptr, lap ? lap + off : nullptr);
         }
         if (st) return st;
     }
-    h->fwd_valid = h->store_forward && h->cfg.precision == KFAC_FP64 && N <= h->cfg.max_n_int;
+    h->fwd_valid = h->store_forward && !is_mixed(h) && N <= h->cfg.max_n_int;
     h->fwd_theta = theta;
     h->fwd_X = X;
     h->fwd_N = N;
@@ -554,7 +574,7 @@ kfac_status_t kfac_pinn_forward_laplacian_backward(kfac_handle_t h, void* stream
                        h->fwd_N == N && N <= h->cfg.max_n_int;
     for (int off = 0; off < N; off += h->cfg.max_n_int) {
         int n = N - off < h->cfg.max_n_int ? N - off : h->cfg.max_n_int;
-        kfac_status_t st = fp64_forward_laplacian_backward(
+        kfac_status_t st = simt_forward_laplacian_backward(
             h, s, theta, X + (long long)off * d, n, du ? du + off : nullptr,
             dgrad ? dgrad + (long long)off * d : nullptr, dlap ? dlap + off : nullptr, dtheta,
             dX ? dX + (long long)off * d : nullptr, off > 0, reuse);

@@ -1,4 +1,5 @@
-// Tiled FP64 SIMT GEMM with operand accessors (FP64 path and linear algebra).
+// Tiled SIMT GEMM with operand accessors (the FP64 and FP32 SIMT paths and
+// the linear algebra).
 //
 // C(p, q) = sum_k A(p, k) B(k, q).  The operands are read through small
 // accessor structs so that one kernel serves the layer GEMMs, the adjoint
@@ -19,26 +20,27 @@ constexpr int GT = 64;     // output tile edge
 constexpr int GK = 16;     // k slice
 constexpr int GTHREADS = 256;
 
-// Plain strided operand: X[i * si + j * sj]
-template <bool FAST_SECOND>
+// Plain strided operand: X[i * si + j * sj] (T: the storage type)
+template <bool FAST_SECOND, class T = double>
 struct Strided {
-    const double* X;
+    const T* X;
     long long si, sj;
     static constexpr bool kfast = FAST_SECOND;   // as A(p, k): second index fast
     static constexpr bool qfast = FAST_SECOND;   // as B(k, q): second index fast
-    KFAC_DEV double operator()(int i, int j) const { return X[(long long)i * si + (long long)j * sj]; }
+    KFAC_DEV T operator()(int i, int j) const { return X[(long long)i * si + (long long)j * sj]; }
 };
 
 // Rows of an activation block with the implicit bias column:
 // element (row, q) = T[row*h + q] for q < h, and for q == h the bias entry,
 // 1 on the value rows (row < N) and 0 elsewhere (the appended row of T^).
+template <class T = double>
 struct ActRows {
-    const double* T;
+    const T* X;
     int h, N;
     static constexpr bool qfast = true;
-    KFAC_DEV double operator()(int row, int q) const {
-        if (q < h) return T[(long long)row * h + q];
-        return row < N ? 1.0 : 0.0;
+    KFAC_DEV T operator()(int row, int q) const {
+        if (q < h) return X[(long long)row * h + q];
+        return row < N ? T(1) : T(0);
     }
 };
 
@@ -63,14 +65,15 @@ struct InputRows {
 };
 
 // Adjoint rows scaled by a per-point weight w[row % N] (w == nullptr: 1).
+template <class T = double>
 struct WeightedRows {
-    const double* G;
+    const T* G;
     int h, N;
     const double* w;
     static constexpr bool qfast = true;
-    KFAC_DEV double operator()(int row, int i) const {
-        double v = G[(long long)row * h + i];
-        if (w) v *= w[row % N];
+    KFAC_DEV T operator()(int row, int i) const {
+        T v = G[(long long)row * h + i];
+        if (w) v *= (T)w[row % N];
         return v;
     }
 };
@@ -80,7 +83,7 @@ template <class R>
 struct Transposed {
     R r;
     static constexpr bool kfast = !R::qfast;
-    KFAC_DEV double operator()(int p, int k) const { return r(k, p); }
+    KFAC_DEV auto operator()(int p, int k) const { return r(k, p); }
 };
 
 // Epilogue writing split-K partials: part[z][p][q]
@@ -93,8 +96,9 @@ struct EpPartial {
 };
 
 // Epilogue: C[p*sp + q*sq] = alpha * v + beta * C  (+ bias[q] on rows p < bias_rows)
+template <class T = double>
 struct EpStore {
-    double* C;
+    T* C;
     long long sp, sq;
     double alpha, beta;
     const double* bias;
@@ -103,14 +107,15 @@ struct EpStore {
     KFAC_DEV void operator()(int p, int q, int, double v) const {
         long long o = (long long)p * sp + (long long)q * sq;
         double r = alpha * v;
-        if (beta != 0.0) r += beta * C[o];
+        if (beta != 0.0) r += beta * (double)C[o];
         if (bias && p < bias_rows) r += bias[(long long)q * bias_stride];
-        C[o] = r;
+        C[o] = (T)r;
     }
 };
 
 // Acc is the arithmetic type of the tile (double, or float where the caller
-// accepts FP32 products); operands are read as double and converted.
+// accepts FP32 products: the FP32 path and the FP32 preconditioning); operands
+// are read through their accessors and converted.
 template <class Acc, class LA, class LB, class EP>
 __global__ void __launch_bounds__(GTHREADS)
 dgemm_tile_kernel(int P, int Q, int K, int kchunk, LA la, LB lb, EP ep) {

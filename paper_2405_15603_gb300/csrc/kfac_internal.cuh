@@ -19,16 +19,18 @@
 // linear map is then one GEMM over M = S*N rows, the value rows are the
 // first block (the only rows that see the bias) and the Laplacian rows the
 // last block.
+// The SIMT path stores them in its precision (double for KFAC_FP64, float
+// for KFAC_FP32: simt_elem_bytes), hence the untyped pointers.
 struct PassBuffers {
     int N;           // capacity in points
     int S;           // shared columns (d + 2 for the interior, 1 for the boundary)
-    double* Z[KFAC_MAX_LAYERS];    // pre-activation outputs Z^{(l)}       (S*N x h_l)
-    double* T[KFAC_MAX_LAYERS];    // post-activation T^{(l)}, l < L       (S*N x h_l)
-    double* Zb[KFAC_MAX_LAYERS];   // adjoints g^{(l)} = dr/dZ^{(l)}       (S*N x h_l)
-    double* r;                     // residuals                            (N)
+    void* Z[KFAC_MAX_LAYERS];      // pre-activation outputs Z^{(l)}       (S*N x h_l)
+    void* T[KFAC_MAX_LAYERS];      // post-activation T^{(l)}, l < L       (S*N x h_l)
+    void* Zb[KFAC_MAX_LAYERS];     // adjoints g^{(l)} = dr/dZ^{(l)}       (S*N x h_l)
+    double* r;                     // residuals, FP64                      (N)
     // reduce-variant scratch: per-point column sums (N x max width)
-    double* red_a;
-    double* red_g;
+    void* red_a;
+    void* red_g;
     // mixed-precision path (bf16 operands, see tc_path.cu)
     void* mx;
 };
@@ -152,9 +154,15 @@ kfac_status_t handle_graph_step(kfac_pinn_handle* h, cudaStream_t s, double* the
                                 const double* f, const double* X_bdy, int N_bdy, const double* g, double* loss);
 void handle_graph_free(kfac_pinn_handle* h);
 
-// The tensor-core path (BF16, or split-BF16 everywhere) vs the FP64 path.
-static inline bool is_mixed(const kfac_pinn_handle* h) { return h->cfg.precision != KFAC_FP64; }
+// The tensor-core path (BF16, or split-BF16 everywhere) vs the SIMT path
+// (FP64 or FP32).
+static inline bool is_mixed(const kfac_pinn_handle* h) {
+    return h->cfg.precision == KFAC_MIXED_BF16 || h->cfg.precision == KFAC_MIXED_SPLIT;
+}
 static inline bool is_split_all(const kfac_pinn_handle* h) { return h->cfg.precision == KFAC_MIXED_SPLIT; }
+
+// The network and operator checks of kfac_pinn_create (abi.cu).
+bool kfac_valid_network(const kfac_config_t* c);
 
 // Device timers: bracket a launch with events when timing is enabled.
 void timer_begin(kfac_pinn_handle* h, int cls, cudaStream_t s);
@@ -166,22 +174,24 @@ void timers_free(kfac_pinn_handle* h);
 static inline unsigned ceil_div_u(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 // ---------------------------------------------------------------------------
-// FP64 path (fp64_path.cu)
+// SIMT path in the handle's precision, FP64 or FP32 (simt_path.cu)
 // ---------------------------------------------------------------------------
-kfac_status_t fp64_forward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+size_t simt_elem_bytes(const kfac_pinn_handle* h);
+kfac_status_t simt_forward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
                            const double* X, int N, PassBuffers& pb, int S);
-kfac_status_t fp64_residual_and_seed(kfac_pinn_handle* h, cudaStream_t s, PassBuffers& pb, int N,
+kfac_status_t simt_residual_and_seed(kfac_pinn_handle* h, cudaStream_t s, PassBuffers& pb, int N,
                                      int S, const double* target, bool interior);
-kfac_status_t fp64_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+kfac_status_t simt_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
                             PassBuffers& pb, int N, int S);
-kfac_status_t fp64_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, const double* X_int,
+kfac_status_t simt_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, const double* X_int,
                                     int N_int, const double* X_bdy, int N_bdy);
+// Loss (Eq. 1) of the FP64 residuals in h->in.r and h->bd.r (both paths)
 kfac_status_t fp64_loss(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N_bdy, double* loss_out);
 kfac_status_t fp64_loss_to(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N_bdy, double* dst);
-kfac_status_t fp64_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int,
+kfac_status_t simt_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int,
                              int N_int, const double* f, const double* X_bdy, int N_bdy, const double* g,
                              double* dst);
-kfac_status_t fp64_jvp(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* v,
+kfac_status_t simt_jvp(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* v,
                        const double* X, int N, PassBuffers& pb, int S, bool interior, double* jv);
 // Automatic learning rate and momentum (linalg.cu), FP64 handles
 kfac_status_t linalg_auto_update(kfac_pinn_handle* h, cudaStream_t s, double* theta, const double* X_int,
@@ -190,11 +200,11 @@ kfac_status_t linalg_auto_update(kfac_pinn_handle* h, cudaStream_t s, double* th
 kfac_status_t linalg_line_search_update(kfac_pinn_handle* h, cudaStream_t s, double* theta, const double* X_int,
                                         int N_int, const double* f, const double* X_bdy, int N_bdy,
                                         const double* g);
-kfac_status_t fp64_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+kfac_status_t simt_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
                                               const double* X, int N, const double* du, const double* dgrad,
                                               const double* dlap, double* dtheta, double* dX, bool accumulate,
                                               bool reuse_forward);
-kfac_status_t fp64_extract_outputs(kfac_pinn_handle* h, cudaStream_t s, PassBuffers& pb, int N,
+kfac_status_t simt_extract_outputs(kfac_pinn_handle* h, cudaStream_t s, PassBuffers& pb, int N,
                                    int S, double* u, double* grad, double* lap);
 
 // ---------------------------------------------------------------------------
@@ -212,7 +222,7 @@ kfac_status_t linalg_precondition(kfac_pinn_handle* h, cudaStream_t s, const dou
 kfac_status_t linalg_update(kfac_pinn_handle* h, cudaStream_t s, double* theta);
 
 // ---------------------------------------------------------------------------
-// Generic FP64 GEMM launchers (gemm_fp64.cu)
+// Generic FP64 GEMM launcher (simt_path.cu)
 // ---------------------------------------------------------------------------
 // C(p, q) = sum_k A(p, k) B(k, q) with strided operands:
 //   A(p, k) = A[p * a_sp + k * a_sk],  B(k, q) = B[k * b_sk + q * b_sq]

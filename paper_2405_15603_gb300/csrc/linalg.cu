@@ -292,6 +292,8 @@ kfac_status_t pgemm_stage(kfac_pinn_handle* h, cudaStream_t s, F desc) {
 }
 
 kfac_status_t precondition_impl(kfac_pinn_handle* h, cudaStream_t s, const double* grad, double* dir) {
+    // FP32 products on the tensor-core precisions (whose 16-bit gradients
+    // dominate the update's error); FP64 on the SIMT precisions
     if (is_mixed(h)) {
         // the four products of every layer as four batched launches; the
         // layers' scratch matrices X1 and Y are laid out one after another
@@ -419,7 +421,7 @@ kfac_status_t linalg_line_search_update(kfac_pinn_handle* h, cudaStream_t s, dou
         KFAC_LAUNCH_CHECK(h);
         double* dst = h->ls_loss + 3 * k;
         kfac_status_t st = mixed ? tc_eval_loss(h, s, h->trial, X_int, N_int, f, X_bdy, N_bdy, g, dst)
-                                 : fp64_eval_loss(h, s, h->trial, X_int, N_int, f, X_bdy, N_bdy, g, dst);
+                                 : simt_eval_loss(h, s, h->trial, X_int, N_int, f, X_bdy, N_bdy, g, dst);
         if (st) return st;
     }
     unsigned ab = blocks < (unsigned)(4 * h->sm_count) ? blocks : (unsigned)(4 * h->sm_count);
@@ -441,15 +443,15 @@ kfac_status_t linalg_auto_update(kfac_pinn_handle* h, cudaStream_t s, double* th
     const int have_prev = h->t > 0;
     kfac_status_t st;
     if (mixed) {
-        // forward-mode products on the tensor cores, from the step's stored forward pass
+        // J v from the step's stored Taylor activations and adjoints, on the tensor cores
         if ((st = tc_residual_jvp(h, s, h->dir, N_int, N_bdy, jDi, jDb))) return st;
         if (have_prev && (st = tc_residual_jvp(h, s, h->delta_prev, N_int, N_bdy, jdi, jdb))) return st;
     } else {
-        if ((st = fp64_jvp(h, s, theta, h->dir, X_int, N_int, h->in, h->S, true, jDi))) return st;
-        if ((st = fp64_jvp(h, s, theta, h->dir, X_bdy, N_bdy, h->bd, 1, false, jDb))) return st;
+        if ((st = simt_jvp(h, s, theta, h->dir, X_int, N_int, h->in, h->S, true, jDi))) return st;
+        if ((st = simt_jvp(h, s, theta, h->dir, X_bdy, N_bdy, h->bd, 1, false, jDb))) return st;
         if (have_prev) {
-            if ((st = fp64_jvp(h, s, theta, h->delta_prev, X_int, N_int, h->in, h->S, true, jdi))) return st;
-            if ((st = fp64_jvp(h, s, theta, h->delta_prev, X_bdy, N_bdy, h->bd, 1, false, jdb))) return st;
+            if ((st = simt_jvp(h, s, theta, h->delta_prev, X_int, N_int, h->in, h->S, true, jdi))) return st;
+            if ((st = simt_jvp(h, s, theta, h->delta_prev, X_bdy, N_bdy, h->bd, 1, false, jdb))) return st;
         }
     }
     k_ks_dots<<<KS_BLOCKS, 256, 0, s>>>(h->dir, h->delta_prev, h->grad, h->D, jDi, jdi, N_int, jDb, jdb, N_bdy,

@@ -56,12 +56,10 @@ extern "C" {
 kfac_status_t kfac_pinn_forward_laplacian_noalloc(const kfac_config_t* cfg, void* stream, const double* theta,
                                                   const double* X, int N, double* u, double* grad, double* lap) {
     if (!cfg || !theta || !X || !u || N < 1) return KFAC_BAD_ARG;
-    if (cfg->d < 1 || cfg->L < 1 || cfg->L > KFAC_MAX_LAYERS) return KFAC_BAD_ARG;
-    if (cfg->op != KFAC_OP_LAPLACE && cfg->op != KFAC_OP_HEAT) return KFAC_BAD_ARG;
-    if (cfg->op == KFAC_OP_HEAT && cfg->d < 2) return KFAC_BAD_ARG;
-    for (int l = 0; l < cfg->L; l++)
-        if (cfg->widths[l] < 1) return KFAC_BAD_ARG;
-    if (cfg->widths[cfg->L - 1] != 1) return KFAC_BAD_ARG;
+    // the network limits of kfac_pinn_create; the general operator (which
+    // needs the coefficient matrix's eigenvectors set up on a handle) is not
+    // available here
+    if (!kfac_valid_network(cfg) || cfg->op == KFAC_OP_GENERAL) return KFAC_BAD_ARG;
 
     // A handle on the host stack describes the network for the FP64 kernels;
     // its buffers point into the static scratch array.
@@ -102,8 +100,8 @@ kfac_status_t kfac_pinn_forward_laplacian_noalloc(const kfac_config_t* cfg, void
     cudaStream_t s = (cudaStream_t)stream;
     k_noalloc_weights<<<(cfg->d + 255) / 256, 256, 0, s>>>(h.chw64, cfg->d, cfg->op == KFAC_OP_HEAT);
     if (cudaGetLastError() != cudaSuccess) return KFAC_CUDA_ERROR;
-    if ((st = fp64_forward(&h, s, theta, X, N, pb, h.S))) return st;
-    return fp64_extract_outputs(&h, s, pb, N, h.S, u, grad, lap);
+    if ((st = simt_forward(&h, s, theta, X, N, pb, h.S))) return st;
+    return simt_extract_outputs(&h, s, pb, N, h.S, u, grad, lap);
 }
 
 }  // extern "C"

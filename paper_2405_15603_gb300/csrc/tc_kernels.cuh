@@ -18,10 +18,11 @@
 //   BWD_TAN     adjoint of tangent rows: abar_i = s1 ybar_i - 4 y_0 y_i ybar_D
 //   BWD_VALUE   adjoint of value rows (uses the tangent cross sums)
 //   GRAM        C = X^T Y over a chunk of rows (factor Grams, weight gradient)
-//   JVP_VALUE   forward-mode derivative of the value rows in direction dW:
-//               da_0 = T_0 dW~^T + dT_0 W^T, dy_0 = s1 da_0
-//   JVP_TAN     tangent rows dy_i = -2 y_0 y_i da_0 + s1 da_i (partial sums of
-//               w_i y_i da_i over the CTA's columns) and the second-order row's da_D
+//   JDOT        residual Jacobian-vector products of a layer (KFAC*): the
+//               rows of T^ V~^T (V~ = (V b_v) a direction shaped like W~)
+//               dotted with the stored adjoint rows g of the same Taylor
+//               column and point, summed over the CTA's columns:
+//               <dr_n/dW~_l, V~> = sum_s g_{n,s}^T V~ T^_{n,s} (Sec. 3.2)
 #pragma once
 #include "tc_common.cuh"
 
@@ -32,8 +33,7 @@ constexpr int BK = 64;
 constexpr int NUM_THREADS = 320;
 constexpr int EPI_WARPS = 8;
 
-enum Mode { FWD_VALUE = 0, FWD_TANLAP = 1, BWD_LAP = 2, BWD_TAN = 3, BWD_VALUE = 4, GRAM = 5, JVP_VALUE = 6,
-            JVP_TAN = 7 };
+enum Mode { FWD_VALUE = 0, FWD_TANLAP = 1, BWD_LAP = 2, BWD_TAN = 3, BWD_VALUE = 4, GRAM = 5, JDOT = 6 };
 
 struct Args {
     CUtensorMap a0, a1, b0, b1;     // operand maps; a1/b1 carry the low BF16 halves
@@ -56,8 +56,9 @@ struct Args {
     float* SSQ;                     // sum of squared tangents
     float* YD;                      // ybar_Delta (BWD)
     float* part;                    // chunk partials / Gram partials
-    const __nv_bfloat16* ytan;      // BWD_TAN: T^{(l-1)} (y_i); JVP_TAN: T^{(l)}
-    float* DAD;                     // JVP_TAN: da_D of the second-order row (YD holds da_0 in the JVP modes)
+    const __nv_bfloat16* ytan;      // BWD_TAN: T^{(l-1)} (y_i)
+    const __nv_bfloat16* g_hi;      // JDOT: adjoint rows g^{(l)} (high half)
+    const __nv_bfloat16* g_lo;      // JDOT: their low halves (split-BF16 everywhere), or nullptr
     const double* r;                // residuals (BWD: for r_n g)
     int* status;
     // split-BF16 on every row (tc_engine<MODE, true>): low halves laid out like the high ones
@@ -75,14 +76,14 @@ struct Cfg {
     // K block fills the slots with two consecutive K blocks (half the barrier
     // round trips for the same bytes in flight: measured 16 % faster for the
     // forward modes); a tile with several products per K block (the split-BF16
-    // terms hi*hi + hi*lo + lo*hi, or the JVP terms T dW + dT W) fills them with
-    // the two A and the two B operands of ONE K block and issues every product
-    // from them, so each operand crosses L2 -> SM once per K block instead of
-    // once per product.  The forward and JVP modes always use two slots; the
+    // terms hi*hi + hi*lo + lo*hi) fills them with the two A and the two B
+    // operands of ONE K block and issues every product from them, so each
+    // operand crosses L2 -> SM once per K block instead of once per product.
+    // The forward and JDOT modes always use two slots; the
     // adjoint modes only when every row is split (one slot and six stages
     // otherwise); the Gram keeps one slot.
     static constexpr bool FUSED =
-        (MODE == FWD_VALUE || MODE == FWD_TANLAP || MODE == JVP_VALUE || MODE == JVP_TAN) ||
+        (MODE == FWD_VALUE || MODE == FWD_TANLAP || MODE == JDOT) ||
         (SPLIT && (MODE == BWD_LAP || MODE == BWD_TAN || MODE == BWD_VALUE));
     static constexpr int SLOTS = FUSED ? 2 : 1;
     static constexpr int STAGES = MN ? 4 : (FUSED ? 3 : 6);
@@ -101,9 +102,9 @@ struct Cfg {
 template <int MODE>
 KFAC_DEV int n_terms(int s, int S, int split_time, int split_all) {
     if (MODE == FWD_VALUE) return 3;
-    if (MODE == JVP_VALUE || MODE == JVP_TAN) return 2;    // T dW~^T + dT W^T
     if (split_all) return 3;                              // hi x hi + hi x lo + lo x hi everywhere
     if (MODE == FWD_TANLAP) return (s == S - 1 || (split_time && s == 1)) ? 3 : 1;
+    if (MODE == JDOT) return (s == 0 || s == S - 1 || (split_time && s == 1)) ? 3 : 1;
     return 1;
 }
 
@@ -112,9 +113,14 @@ KFAC_DEV int lo_block(int s, int S) { return s == 0 ? 0 : (s == S - 1 ? 1 : 2); 
 
 template <int MODE>
 KFAC_DEV void tile_range(const Args& a, int& s_begin, int& s_end) {
-    if (MODE == FWD_VALUE || MODE == BWD_VALUE || MODE == GRAM || MODE == JVP_VALUE) { s_begin = 0; s_end = 1; return; }
+    if (MODE == FWD_VALUE || MODE == BWD_VALUE || MODE == GRAM) { s_begin = 0; s_end = 1; return; }
     if (MODE == BWD_LAP) { s_begin = a.S - 1; s_end = a.S; return; }
-    int last = (MODE == FWD_TANLAP || MODE == JVP_TAN) ? a.S : a.S - 1;   // FWD covers the Laplacian tile too
+    if (MODE == JDOT) {       // every Taylor column, value row block included
+        s_begin = blockIdx.z * a.chunk_len;
+        s_end = min(a.S, s_begin + a.chunk_len);
+        return;
+    }
+    int last = (MODE == FWD_TANLAP) ? a.S : a.S - 1;   // FWD covers the Laplacian tile too
     s_begin = 1 + blockIdx.z * a.chunk_len;
     s_end = min(last, s_begin + a.chunk_len);
 }
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
     }
     if (warp == 0 && lane == 0) {
         tc::prefetch_tmap(&a.a0); tc::prefetch_tmap(&a.b0);
-        if (MODE == FWD_VALUE || MODE == FWD_TANLAP || MODE == JVP_VALUE || MODE == JVP_TAN || SPLIT) {
+        if (MODE == FWD_VALUE || MODE == FWD_TANLAP || MODE == JDOT || SPLIT) {
             tc::prefetch_tmap(&a.a1);
             tc::prefetch_tmap(&a.b1);
         }
@@ -233,12 +239,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                 const int s = s_begin + ti;
                 const int terms = SPLIT ? n_terms<MODE>(s, a.S, a.split_time, 1) : n_terms<MODE>(s, a.S, a.split_time, 0);
                 if constexpr (C::FUSED) {
-                    // rows of the second A operand: the low half (laid out like the high
-                    // half when every row is split, else in its value / Laplacian / time
-                    // block) or, in the JVP modes, dT
-                    const bool jvp = (MODE == JVP_VALUE || MODE == JVP_TAN);
+                    // rows of the second A operand: the low half, laid out like the high
+                    // half when every row is split, else in its value / Laplacian / time block
                     const int arow = s * a.N_pad + p0;
-                    const int arow1 = (SPLIT || jvp) ? arow : (lo_block(s, a.S) * a.N_pad + p0);
+                    const int arow1 = SPLIT ? arow : (lo_block(s, a.S) * a.N_pad + p0);
                     const bool fuse = terms > 1;
                     const int nst = fuse ? a.k_steps : (a.k_steps + 1) / 2;
                     for (int k = 0; k < nst; k++) {
@@ -311,7 +315,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                 const int terms = SPLIT ? n_terms<MODE>(s, a.S, a.split_time, 1) : n_terms<MODE>(s, a.S, a.split_time, 0);
                 bool first = true;
                 if constexpr (C::FUSED) {
-                    const bool jvp = (MODE == JVP_VALUE || MODE == JVP_TAN);
                     const bool fuse = terms > 1;
                     const int nst = fuse ? a.k_steps : (a.k_steps + 1) / 2;
                     for (int k = 0; k < nst; k++) {
@@ -320,13 +323,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                         const uint32_t sa = tc::smem_u32(smem + stage * C::STAGE_BYTES);
                         const uint32_t sb = sa + C::A_BYTES;
                         // (A slot, B slot) of each product: one K block per slot pair when
-                        // not fused; hi*hi, hi*lo, lo*hi (or T dW, dT W) of one K block when fused
-                        const int np = fuse ? (jvp ? 2 : 3) : 2;
+                        // not fused; hi*hi, hi*lo, lo*hi of one K block when fused
+                        const int np = fuse ? 3 : 2;
 #pragma unroll
                         for (int pi = 0; pi < 3; pi++) {
                             if (pi >= np) break;
-                            const uint32_t ua = fuse ? (jvp ? pi : (pi == 2 ? 1u : 0u)) : pi;
-                            const uint32_t ub = fuse ? (jvp ? pi : (pi == 1 ? 1u : 0u)) : pi;
+                            const uint32_t ua = fuse ? (pi == 2 ? 1u : 0u) : pi;
+                            const uint32_t ub = fuse ? (pi == 1 ? 1u : 0u) : pi;
 #pragma unroll
                             for (int w = 0; w < BK / 16; w++) {
                                 const uint64_t ad = tc::smem_desc(sa + ua * C::SLOT_A + w * 32, 16, 1024, tc::LAYOUT_SW128);
@@ -378,10 +381,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
         const long long hp = a.hp_out;
 
         // per-thread state kept across the CTA's tiles
-        constexpr bool STATE = (MODE == FWD_TANLAP || MODE == BWD_TAN || MODE == JVP_TAN);
+        constexpr bool STATE = (MODE == FWD_TANLAP || MODE == BWD_TAN);
         float st1[STATE ? CW : 1];
         float st2[STATE ? CW : 1];
-        __nv_bfloat16 stq[(MODE == BWD_TAN || MODE == JVP_TAN) ? CW : 1];
+        __nv_bfloat16 stq[(MODE == BWD_TAN) ? CW : 1];
+        float jacc = 0.f;                                // JDOT: this thread's partial dot
         if (STATE) {
 #pragma unroll
             for (int c = 0; c < CW; c += 16) {
@@ -393,14 +397,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                 float a0v[16];
                 load16_f32(a.A0 + (long long)n * hp + j0 + c0 + c, a0v);
                 float ydv[16];
-                if (MODE == BWD_TAN || MODE == JVP_TAN) load16_f32(a.YD + (long long)n * hp + j0 + c0 + c, ydv);
+                if (MODE == BWD_TAN) load16_f32(a.YD + (long long)n * hp + j0 + c0 + c, ydv);
 #pragma unroll
                 for (int i = 0; i < 16; i++) {
                     float y0 = tanhf(a0v[i]);
                     st1[c + i] = 1.f - y0 * y0;
                     st2[c + i] = 0.f;
                     if (MODE == BWD_TAN) stq[c + i] = __float2bfloat16_rn(4.f * y0 * ydv[i]);
-                    if (MODE == JVP_TAN) stq[c + i] = __float2bfloat16_rn(-2.f * y0 * ydv[i]);   // -2 y_0 da_0
                 }
             }
         }
@@ -445,32 +448,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                     store16_f32(a.A0 + (long long)n * hp + j, a0v);
                     store16_bf16(a.out_hi + (long long)n * hp + j, hi);
                     store16_bf16(a.out_lo + (long long)n * hp + j, lo);
-                } else if (MODE == JVP_VALUE) {
-                    float da[16], dy[16], a0v[16];
-                    load16_f32(a.A0 + (long long)n * hp + j, a0v);
-#pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        bool valid = live && (j + i < a.n_out);
-                        da[i] = valid ? v[i] + a.bias[j + i] : 0.f;
-                        float y0 = tanhf(a0v[i]);
-                        dy[i] = (1.f - y0 * y0) * da[i];
-                    }
-                    store16_f32(a.YD + (long long)n * hp + j, da);
-                    store16_bf16(a.out_hi + (long long)n * hp + j, dy);
-                } else if (MODE == JVP_TAN) {
-                    if (s == a.S - 1) {
-                        store16_f32(a.DAD + (long long)n * hp + j, v);
-                    } else {
-                        float yi[16], dy[16];
-                        load16_bf16(a.ytan + ((long long)s * a.N_pad + n) * hp + j, yi);
-                        const float wc = a.chw[s - 1];
+                } else if (MODE == JDOT) {
+                    // (T^ V~^T)_{row, j}, the bias of V~ on the value rows, times g_{row, j}
+                    if (live) {
+                        float gh[16], gl[16];
+                        const long long o = ((long long)s * a.N_pad + n) * hp + j;
+                        load16_bf16(a.g_hi + o, gh);
+                        if (a.g_lo) load16_bf16(a.g_lo + o, gl);
 #pragma unroll
                         for (int i = 0; i < 16; i++) {
-                            dy[i] = fmaf(__bfloat162float(stq[c + i]), yi[i], st1[c + i] * v[i]);
-                            st2[c + i] = fmaf(wc * yi[i], v[i], st2[c + i]);
-                            if (!live || j + i >= a.n_out) dy[i] = 0.f;
+                            const float pv = (s == 0) ? v[i] + a.bias[j + i] : v[i];
+                            const float gv = a.g_lo ? gh[i] + gl[i] : gh[i];
+                            jacc = fmaf(pv, gv, jacc);
                         }
-                        store16_bf16(a.out_hi + ((long long)s * a.N_pad + n) * hp + j, dy);
                     }
                 } else if (MODE == FWD_TANLAP) {
                     if (s == a.S - 1) {
@@ -615,6 +605,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                 if (j < a.hp_out)
                     store16_f32(a.part + ((long long)blockIdx.z * a.N_pad + n) * hp + j, st2 + c);
             }
+        }
+        if (MODE == JDOT && !abort_flag) {
+            // one partial per (column chunk, feature tile, column half) and point
+            const long long slot = ((long long)blockIdx.z * gridDim.x + blockIdx.x) * 2 + half;
+            a.part[slot * a.N_pad + n] = jacc;
         }
     }
 

@@ -99,9 +99,8 @@ struct MxState {
     float* Qf;          // general operator: tangent directions (d x d, FP32)
     double* gtan;       // general operator: first-layer tangent gradient sums (h_1 x d)
     float* seed;        // reverse mode: per-point seeds c_{n,s} of the interior pass (S x N_pad)
-    MxWeights dw;       // KFAC*: the direction converted like the weights
+    MxWeights dw;       // KFAC*: a parameter direction converted like the weights
     bool have_dw;
-    float* jdad[KFAC_MAX_LAYERS];   // KFAC*: da_D of the second-order row per hidden layer (N_pad x hp)
     // the boundary pass runs beside the interior pass (they share only the
     // read-only weights): a stream of its own, forked from the caller's and
     // joined back
@@ -603,87 +602,56 @@ __global__ void k_rotate_first(const float* __restrict__ W1f, const float* __res
 }
 
 // ---------------------------------------------------------------------------
-// Forward-mode derivative of the Taylor pass in a parameter direction dW (the
-// residual JVPs of KFAC*); the linearised tanh rule of Eq. 6 in the y-form:
-//   dy_0 = s1 da_0,  dy_i = -2 y_0 y_i da_0 + s1 da_i,
-//   dy_D = s2 da_0 a_D + s1 da_D + s3 da_0 sum_i w_i a_i^2 - 4 y_0 sum_i w_i y_i da_i
+// Residual Jacobian-vector products of KFAC* from the step's stored Taylor
+// pass: J_n v = sum_l <dr_n / dW~_l, V~_l> with dr_n / dW~_l =
+// sum_s g^{(l)}_{n,s} T^^{(l-1)T}_{n,s} (Sec. 3.2), so each layer adds
+// sum_s g_{n,s}^T V~_l T^_{n,s}.  Hidden layers: the JDOT engine mode; the
+// first layer (inputs (x; 1) on the value column, the tangent directions v_m
+// on the tangent columns, 0 on the second-order column) and the last layer
+// (h_L = 1, g = the residual seed c) below.
 // ---------------------------------------------------------------------------
-__global__ void k_jvp_layer1(const float* __restrict__ dW1f, const float* __restrict__ Wt,
-                             const float* __restrict__ dWt, const float* __restrict__ Xf,
-                             const float* __restrict__ A0, const float* __restrict__ SSQ,
-                             const float* __restrict__ chw, int N, int N_pad, int d, int h, int hp, int S, bf16* dT,
-                             float* DA0) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)N_pad * hp) return;
-    const int n = (int)(idx / hp), j = (int)(idx % hp);
+// First layer: jv[n] += g_{n,0}^T (V_1 x_n + b_v) + sum_m g_{n,m}^T V_1 v_m.
+// V1f: the direction's first layer input-major (V1f[k * hp + j], k = d: bias);
+// V1t: its tangent inputs V_1 v_m (V1t[m * hp + j]).  One block per point.
+__global__ void k_jdot_layer1(const float* __restrict__ V1f, const float* __restrict__ V1t,
+                              const float* __restrict__ Xf, const bf16* __restrict__ G, const bf16* __restrict__ G_lo,
+                              int N, int N_pad, int d, int hp, int S, double* jv) {
+    __shared__ double sh[32];
+    const int n = blockIdx.x;
     const long long blk = (long long)N_pad * hp;
-    const bool live = (n < N) && (j < h);
-    float da0 = dW1f[(long long)d * hp + j];
-    for (int k = 0; k < d; k++) da0 = fmaf(dW1f[(long long)k * hp + j], Xf[(long long)n * d + k], da0);
-    da0 = live ? da0 : 0.f;
-    const float y0 = live ? tanhf(A0[idx]) : 0.f;
-    const float s1 = 1.f - y0 * y0;
-    DA0[idx] = da0;
-    dT[idx] = __float2bfloat16_rn(s1 * da0);
-    if (S == 1) return;
-    float P = 0.f;
-    for (int i = 0; i < d; i++) {
-        const float yi = s1 * Wt[(long long)i * hp + j];
-        const float dai = dWt[(long long)i * hp + j];
-        const float dyi = live ? fmaf(-2.f * y0 * yi, da0, s1 * dai) : 0.f;
-        dT[(1 + i) * blk + idx] = __float2bfloat16_rn(dyi);
-        P = fmaf(chw[i] * yi, dai, P);
+    float t = 0.f;
+    for (int j = threadIdx.x; j < hp; j += blockDim.x) {
+        float a0 = V1f[(long long)d * hp + j];
+        for (int k = 0; k < d; k++) a0 = fmaf(V1f[(long long)k * hp + j], Xf[(long long)n * d + k], a0);
+        const long long o = (long long)n * hp + j;
+        float g0 = __bfloat162float(G[o]);
+        if (G_lo) g0 += __bfloat162float(G_lo[o]);
+        t = fmaf(a0, g0, t);
+        if (S > 1)
+            for (int m = 0; m < d; m++) {
+                float g = __bfloat162float(G[(1 + m) * blk + o]);
+                if (G_lo) g += __bfloat162float(G_lo[(1 + m) * blk + o]);
+                t = fmaf(V1t[(long long)m * hp + j], g, t);
+            }
     }
-    const float s3 = -2.f * s1 * (1.f - 3.f * y0 * y0);
-    const float dyD = live ? s3 * da0 * SSQ[idx] - 4.f * y0 * P : 0.f;   // a_D = da_D = 0 at layer 1
-    dT[(S - 1) * blk + idx] = __float2bfloat16_rn(dyD);
+    double v = t;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x % 32 == 0) sh[threadIdx.x / 32] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); w++) tot += sh[w];
+        jv[n] += tot;
+    }
 }
 
-__global__ void k_jvp_lap_finish(const float* __restrict__ part, int n_chunks, int N, int N_pad, int h, int hp,
-                                 int S, const float* __restrict__ A0, const float* __restrict__ AD,
-                                 const float* __restrict__ SSQ, const float* __restrict__ DA0,
-                                 const float* __restrict__ DAD, bf16* dT) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long blk = (long long)N_pad * hp;
-    if (idx >= blk) return;
-    const int n = (int)(idx / hp), j = (int)(idx % hp);
-    float P = 0.f;
-    for (int z = 0; z < n_chunks; z++) P += part[z * blk + idx];
-    const float y0 = tanhf(A0[idx]);
-    const float s1 = 1.f - y0 * y0, s2 = -2.f * y0 * s1, s3 = -2.f * s1 * (1.f - 3.f * y0 * y0);
-    const float da0 = DA0[idx];
-    float dyD = s2 * da0 * AD[idx] + s1 * DAD[idx] + s3 * da0 * SSQ[idx] - 4.f * y0 * P;
-    if (n >= N || j >= h) dyD = 0.f;
-    dT[(S - 1) * blk + idx] = __float2bfloat16_rn(dyD);
-}
-
-// dZ^{(L)} rows of the selected Taylor blocks: T dw_L (+ db_L on value rows) + dT w_L.
-__global__ void k_last_jvp(const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo, const bf16* __restrict__ dT,
-                           const float* __restrict__ wL, const float* __restrict__ dwL, int N_pad, int S, int hp,
-                           BlockSel sel, float* jz) {
-    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-    const int lane = threadIdx.x % 32;
-    const long long nrows = (long long)(sel.nsel ? sel.nsel : S) * N_pad;
-    if (wid >= nrows) return;
-    const int bi = (int)(wid / N_pad), n = (int)(wid % N_pad);
-    const int s = sel.nsel ? sel.b[bi] : bi;
-    wid = (long long)s * N_pad + n;
-    const bf16* row = T_hi + wid * hp;
-    const bf16* drow = dT + wid * hp;
-    const bf16* lrow = nullptr;
-    if (sel.split_all) lrow = T_lo + ((long long)s * N_pad + n) * hp;
-    else if (s == 0) lrow = T_lo + (long long)n * hp;
-    else if (s == S - 1) lrow = T_lo + ((long long)N_pad + n) * hp;
-    else if (s == 1 && sel.split_time) lrow = T_lo + (2LL * N_pad + n) * hp;
-    float acc = 0.f;
-    for (int j = lane; j < hp; j += 32) {
-        float t = __bfloat162float(row[j]);
-        if (lrow) t += __bfloat162float(lrow[j]);
-        acc = fmaf(t, dwL[j], acc);
-        acc = fmaf(__bfloat162float(drow[j]), wL[j], acc);
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) jz[wid] = acc + (s == 0 ? dwL[hp] : 0.f);
+// jv[n] += sum over the JDOT launch's partial slots of part[slot][n].
+__global__ void k_jdot_reduce(const float* __restrict__ part, int slots, int N, int N_pad, double* jv) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double acc = 0.0;
+    for (int z = 0; z < slots; z++) acc += (double)part[(long long)z * N_pad + n];
+    jv[n] += acc;
 }
 
 __global__ void k_residual_jvp_mx(const float* __restrict__ jz, double* jv, int N, int N_pad, int S, int interior,
@@ -727,13 +695,14 @@ __global__ void k_seed_mx(float* seed, int N, int N_pad, int S, const float* __r
 }
 
 // dphi/dW~_L[q] = sum_n sum_s c_{n,s} T^_{n,s}[q]: the hidden rows with their low
-// halves where they have one (value, second-order, heat time), and the bias
-// entry q = h_{L-1} from the value rows.  FP32 partial sums per row group.
+// halves where they have one (value, second-order, heat time; every row at its
+// own block when split_all), and the bias entry q = h_{L-1} from the value
+// rows.  FP32 partial sums per row group.
 __global__ void __launch_bounds__(RED_THREADS) k_last_grad_seeded(const bf16* __restrict__ T_hi,
                                                                   const bf16* __restrict__ T_lo,
                                                                   const float* __restrict__ seed, int N, int N_pad,
                                                                   int hin, int hp, int S, int split_time,
-                                                                  double* grad) {
+                                                                  int split_all, double* grad) {
     __shared__ double shm[32][33];
     const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
     const int q = blockIdx.x * 32 + cl;
@@ -742,7 +711,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_last_grad_seeded(const bf16* __
     if (q < hin) {
         for (int s = 0; s < S; s++) {
             const bf16* lo = nullptr;
-            if (s == 0) lo = T_lo;
+            if (split_all) lo = T_lo + s * blk;
+            else if (s == 0) lo = T_lo;
             else if (s == S - 1) lo = T_lo + blk;
             else if (s == 1 && split_time) lo = T_lo + 2 * blk;
             for (int n = rg; n < N; n += 32) {
@@ -759,11 +729,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_last_grad_seeded(const bf16* __
 }
 
 // dphi/dx_n = W_1^T g^{(1)}_{n,0}: x enters the value column of layer 1 only.
-__global__ void k_dX_mx(const bf16* __restrict__ Zb1, int N, int hp, int h1, int d, const float* __restrict__ W1f,
-                        double* dX) {
+// Zb1_lo: the adjoint's low half (split-BF16 everywhere), or nullptr.
+__global__ void k_dX_mx(const bf16* __restrict__ Zb1, const bf16* __restrict__ Zb1_lo, int N, int hp, int h1, int d,
+                        const float* __restrict__ W1f, double* dX) {
     extern __shared__ float zrow[];
     const int n = blockIdx.x;
-    for (int j = threadIdx.x; j < h1; j += blockDim.x) zrow[j] = __bfloat162float(Zb1[(long long)n * hp + j]);
+    for (int j = threadIdx.x; j < h1; j += blockDim.x) {
+        float z = __bfloat162float(Zb1[(long long)n * hp + j]);
+        if (Zb1_lo) z += __bfloat162float(Zb1_lo[(long long)n * hp + j]);
+        zrow[j] = z;
+    }
     __syncthreads();
     for (int k = threadIdx.x; k < d; k += blockDim.x) {
         float acc = 0.f;
@@ -849,14 +824,8 @@ kfac_status_t launch_engine(kfac_pinn_handle* h, cudaStream_t s, const Args& a, 
                             double exec) {
     if (grid.x == 0 || grid.y == 0 || grid.z == 0) return KFAC_OK;
     timer_begin(h, kclass, s);
-    kfac_status_t st;
-    // the forward-mode JVPs (KFAC*) have no split-everywhere form
-    if constexpr (MODE != tck::JVP_VALUE && MODE != tck::JVP_TAN) {
-        st = a.split_all ? launch_engine_as<MODE, true>(h, s, a, grid) : launch_engine_as<MODE, false>(h, s, a, grid);
-    } else {
-        if (a.split_all) return KFAC_BAD_ARG;
-        st = launch_engine_as<MODE, false>(h, s, a, grid);
-    }
+    kfac_status_t st =
+        a.split_all ? launch_engine_as<MODE, true>(h, s, a, grid) : launch_engine_as<MODE, false>(h, s, a, grid);
     if (st) return st;
     timer_end(h, kclass, s, work, exec);
     KFAC_LAUNCH_CHECK(h);
@@ -1546,8 +1515,6 @@ kfac_status_t tc_alloc(kfac_pinn_handle* h) {
     if (h->cfg.update == KFAC_UPDATE_AUTO) {
         if ((st = alloc_weights(h, m->dw))) return st;
         m->have_dw = true;
-        for (int l = 1; l <= L - 1; l++)
-            if ((st = dal(&m->jdad[l - 1], (size_t)m->in.N_pad * round_up(h->dims[l], 64)))) return st;
     }
     if (h->opQ) {
         const int d = h->dims[0];
@@ -1581,7 +1548,6 @@ void tc_free(kfac_pinn_handle* h) {
     free_pass(m->bd);
     free_weights(m->w);
     if (m->have_dw) free_weights(m->dw);
-    for (int l = 0; l < KFAC_MAX_LAYERS; l++) cudaFree(m->jdad[l]);
     cudaFree(m->Qf);
     cudaFree(m->gtan);
     cudaFree(m->seed);
@@ -1600,12 +1566,20 @@ void tc_free(kfac_pinn_handle* h) {
 
 namespace {
 
+// Input dimension from which a split-everywhere handle runs its line-search
+// trial passes with plain BF16 tangent rows (see forward_and_residuals).
+constexpr int TRIAL_BF16_TANGENTS_MIN_D = 32;
+
 // Forward passes of both terms and their residuals into h->in.r / h->bd.r.
-// trial: a line-search trial loss.  Its forward pass keeps split-BF16 on the
-// rows the residuals read through (value, second-order and heat time rows)
-// and runs the tangent rows in plain BF16 also for a split-everywhere handle:
-// the trial loss only ranks the grid points, and the curvature pass of the
-// step (factors, gradient, direction) stays split on every row.
+// trial: a line-search trial loss.  For d >= TRIAL_BF16_TANGENTS_MIN_D its
+// forward pass keeps split-BF16 on the rows the residuals read through
+// (value, second-order and heat time rows) and runs the tangent rows in plain
+// BF16 also for a split-everywhere handle: the second-order row sums
+// sigma'' a_i^2 over the d tangents, whose independent BF16 roundings average
+// out like 1/sqrt(d) (trial losses within 1e-4 of FP64 at d = 100, 2e-4 at
+// d = 5), and the tangent GEMMs are where that pass spends its time.  The
+// curvature pass of the step (factors, gradient, direction) stays split on
+// every row.
 kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int,
                                     int N_int, const double* f, const double* X_bdy, int N_bdy, const double* g,
                                     bool trial = false) {
@@ -1621,7 +1595,8 @@ kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const d
     sb.b[0] = 0;
     sb.b[1] = sb.b[2] = 0;
     sb.split_time = 0;
-    sb.split_all = (is_split_all(h) && !trial) ? 1 : 0;
+    const int split = (is_split_all(h) && !(trial && h->dims[0] >= TRIAL_BF16_TANGENTS_MIN_D)) ? 1 : 0;
+    sb.split_all = split;
     KFAC_CUDA_TRY(cudaEventRecord(m->fork, s));
     KFAC_CUDA_TRY(cudaStreamWaitEvent(m->side, m->fork, 0));
     st = forward_pass(h, m->side, theta, X_bdy, N_bdy, m->bd, sb);
@@ -1643,7 +1618,7 @@ kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const d
     si.b[1] = 1;
     si.b[2] = 0;
     si.split_time = heat;
-    si.split_all = (is_split_all(h) && !trial) ? 1 : 0;
+    si.split_all = split;
     st = forward_pass(h, s, theta, X_int, N_int, m->in, si);
     if (st == KFAC_OK) {
         k_residual_mx<<<ceil_div_u(N_int, EW), EW, 0, s>>>(m->in.zl, f, h->in.r, N_int, m->in.N_pad, S, 1, h->cT,
@@ -1749,6 +1724,7 @@ kfac_status_t tc_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s,
         MxLayer& ti = I.lay[L - 2];
         k_last_grad_seeded<<<ceil_div_u(ti.h + 1, 32), RED_THREADS, 0, s>>>(ti.T_hi, ti.T_lo, m->seed, N, I.N_pad, ti.h,
                                                                             ti.hp, S, heat && S > 2,
+                                                                            is_split_all(h) ? 1 : 0,
                                                                             G + h->woff[L - 1]);
         KFAC_LAUNCH_CHECK(h);
     }
@@ -1756,7 +1732,8 @@ kfac_status_t tc_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s,
     KFAC_LAUNCH_CHECK(h);
     if (dX) {
         const MxLayer& l1 = I.lay[0];
-        k_dX_mx<<<N, 128, sizeof(float) * l1.hp, s>>>(l1.Zb, N, l1.hp, l1.h, d, m->w.W1f, dX);
+        k_dX_mx<<<N, 128, sizeof(float) * l1.hp, s>>>(l1.Zb, is_split_all(h) ? l1.Zb_lo : nullptr, N, l1.hp, l1.h,
+                                                       d, m->w.W1f, dX);
         KFAC_LAUNCH_CHECK(h);
     }
     return KFAC_OK;
@@ -1766,73 +1743,76 @@ namespace {
 
 // J_theta r . v for one pass whose forward activations at theta are held in P,
 // with the direction v already converted into m->dw.
-kfac_status_t jvp_pass(kfac_pinn_handle* h, cudaStream_t s, MxPass& P, int N, bool interior, double* jv) {
+// J v of one pass (interior or boundary) for the direction converted into
+// m->dw, from the pass's stored activations T^ and adjoints g (the step's
+// curvature pass): jv[n] = sum_l sum_s g^{(l)}_{n,s}^T V~_l T^^{(l-1)}_{n,s}.
+kfac_status_t jdot_pass(kfac_pinn_handle* h, cudaStream_t s, MxPass& P, int N, bool interior, double* jv) {
     MxState* m = MX(h);
     const int L = h->cfg.L, d = h->dims[0], S = P.S;
     const int heat = h->cfg.op == KFAC_OP_HEAT;
+    const int split = is_split_all(h) ? 1 : 0;
     kfac_status_t st;
+    // last layer (h_L = 1, g^{(L)}_{n,s} = c_s): jv = sum_s c_s (v_L . T^_{n,s} + [s = 0] b_v)
     {
-        MxLayer& l1 = P.lay[0];
-        const float* Wt = m->w.W1Qf ? m->w.W1Qf : m->w.W1f;
-        const float* dWt = m->dw.W1Qf ? m->dw.W1Qf : m->dw.W1f;
-        k_jvp_layer1<<<ceil_div_u((long long)P.N_pad * l1.hp, EW), EW, 0, s>>>(
-            m->dw.W1f, Wt, dWt, P.Xf, l1.A0, l1.SSQ, h->chw32, N, P.N_pad, d, l1.h, l1.hp, S, l1.Zb, l1.YD);
+        MxLayer& last = P.lay[L - 2];
+        BlockSel sel;
+        sel.b[0] = sel.b[1] = sel.b[2] = 0;
+        sel.split_time = 0;
+        sel.split_all = split;
+        if (interior) {
+            sel.nsel = heat ? 2 : 1;
+            sel.b[0] = S - 1;
+            sel.b[1] = 1;
+            sel.split_time = heat;
+        } else {
+            sel.nsel = 1;
+        }
+        k_last_fwd<<<ceil_div_u((long long)sel.nsel * P.N_pad * 32, EW), EW, 0, s>>>(last.T_hi, last.T_lo, m->dw.wL,
+                                                                                     P.N_pad, S, last.hp, sel, P.zl);
+        KFAC_LAUNCH_CHECK(h);
+        k_residual_jvp_mx<<<ceil_div_u(N, EW), EW, 0, s>>>(P.zl, jv, N, P.N_pad, S, interior ? 1 : 0, h->cT, h->cD);
         KFAC_LAUNCH_CHECK(h);
     }
+    // hidden layers 2..L-1 on the tensor cores
+    const long long part_cap = (long long)MAX_CHUNKS * m->in.N_pad * m->hp_max;
     for (int l = 2; l <= L - 1; l++) {
-        MxLayer& in = P.lay[l - 2];
-        MxLayer& out = P.lay[l - 1];
+        MxLayer& in = P.lay[l - 2];    // T^{(l-1)}
+        MxLayer& out = P.lay[l - 1];   // g^{(l)}
         Args a = base_args(h, P, N);
         a.a0 = in.kT_hi;
+        a.a1 = in.kT_lo;
         a.b0 = m->dw.kW_hi[l - 1];
-        a.a1 = in.kZb;
-        a.b1 = m->w.kW_hi[l - 1];
+        a.b1 = m->dw.kW_lo[l - 1];
         a.k_steps = in.hp / 64;
         a.n_out = out.h;
         a.hp_out = out.hp;
-        a.out_hi = out.Zb;
         a.bias = m->dw.bias[l - 1];
-        a.A0 = out.A0;
-        a.YD = out.YD;
+        a.g_hi = out.Zb;
+        a.g_lo = split ? out.Zb_lo : nullptr;
+        a.part = m->part;
         const int jb = (out.hp + 127) / 128, pb = P.N_pad / 128;
-        // two contractions per row block: T dW~^T and dT W^T
-        const double alg = 2.0 * 2.0 * N * (double)out.h * in.h;
-        const double fl = 2.0 * 2.0 * P.N_pad * (double)out.hp * in.hp;
-        if ((st = launch_engine<tck::JVP_VALUE>(h, s, a, dim3(jb, pb, 1), KFAC_KC_LAYER_GEMM, alg, fl))) return st;
-        if (S > 1) {
-            a.ytan = out.T_hi;
-            a.DAD = m->jdad[l - 1];
-            a.part = m->part;
-            choose_chunks(S - 1, jb * pb, h->sm_count, a.chunk_len, a.n_chunks);
-            if ((st = launch_engine<tck::JVP_TAN>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_LAYER_GEMM,
-                                                  alg * (S - 1), fl * (S - 1))))
-                return st;
-            const long long cnt = (long long)P.N_pad * out.hp;
-            k_jvp_lap_finish<<<ceil_div_u(cnt, EW), EW, 0, s>>>(m->part, a.n_chunks, N, P.N_pad, out.h, out.hp, S,
-                                                                 out.A0, out.AD, out.SSQ, out.YD, m->jdad[l - 1],
-                                                                 out.Zb);
-            KFAC_LAUNCH_CHECK(h);
-        }
+        choose_chunks(S, jb * pb, h->sm_count, a.chunk_len, a.n_chunks);
+        const int slots = a.n_chunks * jb * 2;
+        if ((long long)slots * P.N_pad > part_cap) return KFAC_BAD_ARG;
+        // three products on split rows (every row when split everywhere; the
+        // value, second-order and time rows otherwise), one on plain BF16 rows
+        const int split_rows = split ? S : (S == 1 ? 1 : (heat && S > 2 ? 3 : 2));
+        const double alg = 2.0 * N * (double)S * out.h * in.h;
+        const double fl = 2.0 * P.N_pad * (double)out.hp * in.hp;
+        if ((st = launch_engine<tck::JDOT>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_LAYER_GEMM, alg,
+                                           fl * (S + 2 * split_rows))))
+            return st;
+        k_jdot_reduce<<<ceil_div_u(N, EW), EW, 0, s>>>(m->part, slots, N, P.N_pad, jv);
+        KFAC_LAUNCH_CHECK(h);
     }
-    MxLayer& last = P.lay[L - 2];
-    BlockSel sel;
-    sel.b[0] = sel.b[1] = sel.b[2] = 0;
-    sel.split_time = 0;
-    sel.split_all = is_split_all(h) ? 1 : 0;
-    if (interior) {
-        sel.nsel = heat ? 2 : 1;
-        sel.b[0] = S - 1;
-        sel.b[1] = 1;
-        sel.split_time = heat;
-    } else {
-        sel.nsel = 1;
+    // first layer
+    {
+        MxLayer& l1 = P.lay[0];
+        const float* V1t = m->dw.W1Qf ? m->dw.W1Qf : m->dw.W1f;
+        k_jdot_layer1<<<N, 256, 0, s>>>(m->dw.W1f, V1t, P.Xf, l1.Zb, split ? l1.Zb_lo : nullptr, N, P.N_pad, d,
+                                        l1.hp, S, jv);
+        KFAC_LAUNCH_CHECK(h);
     }
-    k_last_jvp<<<ceil_div_u((long long)sel.nsel * P.N_pad * 32, EW), EW, 0, s>>>(last.T_hi, last.T_lo, last.Zb,
-                                                                                 m->w.wL, m->dw.wL, P.N_pad, S,
-                                                                                 last.hp, sel, P.zl);
-    KFAC_LAUNCH_CHECK(h);
-    k_residual_jvp_mx<<<ceil_div_u(N, EW), EW, 0, s>>>(P.zl, jv, N, P.N_pad, S, interior ? 1 : 0, h->cT, h->cD);
-    KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }
 
@@ -1844,6 +1824,6 @@ kfac_status_t tc_residual_jvp(kfac_pinn_handle* h, cudaStream_t s, const double*
     if (!m->have_dw) return KFAC_BAD_ARG;
     kfac_status_t st;
     if ((st = convert_weights_into(h, s, v, m->dw))) return st;
-    if ((st = jvp_pass(h, s, m->in, N_int, true, jv_int))) return st;
-    return jvp_pass(h, s, m->bd, N_bdy, false, jv_bdy);
+    if ((st = jdot_pass(h, s, m->in, N_int, true, jv_int))) return st;
+    return jdot_pass(h, s, m->bd, N_bdy, false, jv_bdy);
 }

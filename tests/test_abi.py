@@ -88,7 +88,7 @@ int main(void) {
     V(KFAC_MAX_LAYERS); V(KFAC_TUNE_CAP);
     V(KFAC_OK); V(KFAC_BAD_ARG); V(KFAC_NOT_PD); V(KFAC_NONFINITE); V(KFAC_TIMEOUT); V(KFAC_OOM);
     V(KFAC_CUDA_ERROR); V(KFAC_NOT_READY);
-    V(KFAC_FP64); V(KFAC_MIXED_BF16); V(KFAC_MIXED_SPLIT); V(KFAC_EXPAND); V(KFAC_REDUCE);
+    V(KFAC_FP64); V(KFAC_MIXED_BF16); V(KFAC_MIXED_SPLIT); V(KFAC_FP32); V(KFAC_EXPAND); V(KFAC_REDUCE);
     V(KFAC_OP_LAPLACE); V(KFAC_OP_HEAT); V(KFAC_OP_GENERAL);
     V(KFAC_UPDATE_FIXED); V(KFAC_UPDATE_LINE_SEARCH); V(KFAC_UPDATE_AUTO);
     V(KFAC_A_INT); V(KFAC_B_INT); V(KFAC_A_BDY); V(KFAC_B_BDY);
@@ -126,7 +126,8 @@ def test_ctypes_mirrors_match_the_header(tmp_path):
     for code, name in _lib.STATUS.items():
         assert c[name] == (code,), name
     for name, v in api.PRECISIONS.items():
-        assert c[{"fp64": "KFAC_FP64", "mixed_bf16": "KFAC_MIXED_BF16", "mixed_split": "KFAC_MIXED_SPLIT"}[name]] == (v,)
+        assert c[{"fp64": "KFAC_FP64", "mixed_bf16": "KFAC_MIXED_BF16", "mixed_split": "KFAC_MIXED_SPLIT",
+                  "fp32": "KFAC_FP32"}[name]] == (v,)
     for name, v in api.VARIANTS.items():
         assert c["KFAC_" + name.upper()] == (v,)
     for name, v in api.OPS.items():

@@ -120,16 +120,19 @@ def test_no_hidden_layer_and_single_point():
         assert opt.sync_status() == "KFAC_OK"
 
 
-def test_split_mode_rejects_unsupported_combinations():
-    # split-BF16 everywhere supports the expand variant with the fixed and
-    # line-search updates only
+def test_split_mode_variants_and_updates():
+    # split-BF16 everywhere runs every variant and update rule; the tensor-core
+    # precisions need a hidden layer (create rejects L = 1 for them)
     from paper_2405_15603_gb300.api import KfacError
-    for kw in (dict(variant="reduce"), dict(update="kfac_star")):
+    for prec in ("mixed_split", "mixed_bf16"):
         with pytest.raises(KfacError):
-            _opt(3, (16, 1), precision="mixed_split", max_n_int=8, max_n_bdy=8, **kw)
-    opt = _opt(3, (16, 16, 1), precision="mixed_split", max_n_int=8, max_n_bdy=8, update="line_search")
+            _opt(3, (1,), precision=prec, max_n_int=8, max_n_bdy=8)
     prob = si.poisson_cos_problem(3)
     Xi, f, Xb, g = si.make_batch(prob, 8, 8, seed=3)
-    th = torch.tensor(si.xavier_theta(3, (16, 16, 1), 0), device=DEV)
-    opt.step(th, Xi, f, Xb, g)
-    assert opt.sync_status() == "KFAC_OK"
+    for kw in (dict(update="line_search"), dict(variant="reduce"), dict(update="kfac_star"),
+               dict(variant="reduce", update="kfac_star")):
+        opt = _opt(3, (16, 16, 1), precision="mixed_split", max_n_int=8, max_n_bdy=8, **kw)
+        th = torch.tensor(si.xavier_theta(3, (16, 16, 1), 0), device=DEV)
+        opt.step(th, Xi, f, Xb, g)
+        assert opt.sync_status() == "KFAC_OK", kw
+        assert torch.isfinite(th).all()

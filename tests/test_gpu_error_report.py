@@ -1,19 +1,24 @@
 """Per-result relative error of one KFAC step against the FP64 oracle, for
-both precisions on the configurations the oracle finishes in seconds (the
+every precision on the configurations the oracle finishes in seconds (the
 2-d, 5-d and heat workloads at their full point counts; the 100-d net on a
 small batch).  Run with -s to print the table; the assertions are the
 per-result bounds of each precision:
 
-  FP64:  forward outputs, loss, gradient and factors to 1e-10, the
+  fp64:  forward outputs, loss, gradient and factors to 1e-10, the
          preconditioned direction and the update to 1e-8;
-  mixed_bf16: u and the loss to 1e-3 (split-BF16 value channel), the
-         tangents, Laplacian, gradient and factors to 2e-2 (BF16 tangent and
-         adjoint channels, 8 significant bits); the update is reported, since
-         the damped inverse amplifies factor errors by up to ||dA|| / lambda;
-  mixed_split (split-BF16 on every channel, about 16 bits): every forward
-         output, the loss, the gradient and the factors to 1e-4, the update
-         to 1e-3 on the Poisson problems and 5e-3 on the heat problem, whose
-         damped inverse amplifies the factor differences about 330-fold.
+  fp32 (SIMT FP32, split-K sums in FP64): every forward output, the loss, the
+         gradient and every factor to 1e-4, the update to 1e-3, on every
+         configuration (the heat workload is specified in FP32);
+  mixed_split (split-BF16 on every row, about 16 bits; the benchmarked
+         precision): every forward output, the loss, the gradient and the
+         factors to 1e-4 and the update to 1e-3.  On the heat workload the
+         damped inverse amplifies its ~1e-5 factor differences about 330-fold
+         (update error / factor error), which puts the update at 2.7e-3: that
+         case is an expected failure of the 1e-3 bound (still held to 5e-3),
+         and FP32 is the precision that meets the bound there;
+  mixed_bf16 (BF16 tangent and adjoint rows): u and the loss to 1e-3, the
+         tangents, Laplacian, gradient and factors to 2e-2; the update is
+         reported (it misses the reduced-precision bound by 20-150x).
 """
 import numpy as np
 import pytest
@@ -67,7 +72,7 @@ def errors(prob, widths, N, Nb, precision):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed_bf16", "mixed_split"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed_split", "mixed_bf16"])
 def test_error_report(precision):
     print()
     print(f"relative error per result, {precision}, one step, lambda = 1e-3 (factors: max over the layers)")
@@ -77,22 +82,26 @@ def test_error_report(precision):
         e = errors(prob, widths, N, Nb, precision)
         print(name.ljust(46) + "".join(f"{e[k]:11.2e}" for k in KEYS), flush=True)
         rows.append((name, e))
+    misses = []
     for name, e in rows:
         if precision == "fp64":
             for k in KEYS[:9]:
                 assert e[k] < 1e-10, (name, k, e[k])
             assert e["direction"] < 1e-8 and e["update"] < 1e-8, (name, e)
-        elif precision == "mixed_split":
+        elif precision in ("fp32", "mixed_split"):
             for k in KEYS[:9]:
                 assert e[k] < 1e-4, (name, k, e[k])
-            # the update is the damped Kronecker-sum inverse applied to the
-            # gradient: at lambda = 1e-3 it amplifies the ~1e-5 factor
-            # differences by up to ~330 on the heat problem (measured: update
-            # error / factor error), so 1e-3 holds on the Poisson problems
-            # and 5e-3 bounds the heat problem
-            assert e["update"] < (5e-3 if name.startswith("C4") else 1e-3), (name, e["update"])
+            if precision == "mixed_split" and name.startswith("C4"):
+                assert e["update"] < 5e-3, (name, e["update"])
+                if e["update"] >= 1e-3:
+                    misses.append((name, e["update"]))
+            else:
+                assert e["update"] < 1e-3, (name, e["update"])
         else:
             assert e["u"] < 1e-3 and e["loss"] < 1e-3, (name, e)
             for k in ("grad_u", "lap_u", "gradient", "A_int", "B_int", "A_bdy", "B_bdy"):
                 assert e[k] < 2e-2, (name, k, e[k])
             assert np.isfinite(e["update"])
+    if misses:
+        pytest.xfail(f"split-BF16 update above the 1e-3 bound on the heat workload: {misses} "
+                     "(FP32 meets it there)")
