@@ -222,7 +222,8 @@ kfac_status_t kfac_pinn_set_graph(kfac_handle_t h, int enable);
  *   KFAC_TUNE_GRAM     the Grams of the Kronecker factors (Eq. 8, Eq. 3) and
  *                      the weight-gradient contractions: their K = S * N_cap
  *                      rows (N_cap = max_n_int or max_n_bdy rounded up to
- *                      128) are split into row chunks;
+ *                      128) are split into row chunks of at most 2048 rows
+ *                      (each chunk sums in FP32, the chunks in FP64);
  *   KFAC_TUNE_FWD_TAN  the layer GEMM of the tangent and Laplacian columns of
  *                      the Taylor pass: its tiles (one per tangent column) are
  *                      split into chunks, each adding its share of the
@@ -410,6 +411,28 @@ kfac_status_t kfac_pinn_timing_read(kfac_handle_t h, int kernel_class, double* t
  * NULL.  The class's timers are cleared. */
 kfac_status_t kfac_pinn_timing_read_ex(kfac_handle_t h, int kernel_class, double* total_ms,
                                        int64_t* launches, double* work, double* exec_work);
+
+/* Failure detection without a fault (no counterpart in the paper).
+ *
+ * kfac_pinn_check_wait_timeout runs one of the library's bounded device waits
+ * against a condition that nothing satisfies, with a limit of limit_ms
+ * milliseconds instead of the 2 s its kernels use:
+ *   kind 0: the group barrier of the cooperative eigensolver kernels (a group
+ *           of two CTAs of which only one is launched);
+ *   kind 1: the mbarrier wait of the tcgen05 engine (one expected arrival
+ *           that never comes).
+ * The wait gives up after limit_ms, the kernel latches KFAC_TIMEOUT in the
+ * handle's status word (kfac_pinn_sync_status reads it) and returns, and the
+ * context stays usable.  Synchronises `stream`.  Errors: KFAC_BAD_ARG (NULL
+ * handle, kind not 0 or 1, limit_ms outside 1..10000).
+ *
+ * kfac_pinn_inject_alloc_failure makes the device allocation that comes after
+ * n more successful ones fail as if the device were out of memory (n = 0: the
+ * next one; -1: none; process-wide).  kfac_pinn_create then returns
+ * KFAC_OOM and frees everything it had allocated.  Errors: KFAC_BAD_ARG for
+ * n < -1. */
+kfac_status_t kfac_pinn_check_wait_timeout(kfac_handle_t h, void* stream, int kind, int limit_ms);
+kfac_status_t kfac_pinn_inject_alloc_failure(long long n);
 
 /* Batched stepping of many independent problems (handles), each with its own
  * network, point counts and buffers.  The paper steps one problem at a time;

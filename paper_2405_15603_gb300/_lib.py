@@ -22,6 +22,7 @@ EXPORTS = [
     "kfac_pinn_batch_step", "kfac_pinn_last_cuda_error", "kfac_pinn_last_cuda_error_string",
     "kfac_pinn_set_store_forward",
     "kfac_pinn_set_graph", "kfac_pinn_set_autotune", "kfac_pinn_get_tuning", "kfac_pinn_set_tuning",
+    "kfac_pinn_check_wait_timeout", "kfac_pinn_inject_alloc_failure",
 ]
 
 KFAC_TUNE_CAP = 128
@@ -112,6 +113,8 @@ def load() -> C.CDLL:
         "kfac_pinn_sync_status": (st, [H, C.POINTER(C.c_int)]),
         "kfac_pinn_launch_count": (C.c_int64, [H]),
         "kfac_pinn_timing_enable": (st, [H, I]),
+        "kfac_pinn_check_wait_timeout": (st, [H, P, I, I]),
+        "kfac_pinn_inject_alloc_failure": (st, [C.c_longlong]),
         "kfac_pinn_forward_laplacian_noalloc": (st, [C.POINTER(KfacConfig), P, P, P, I, P, P, P]),
         "kfac_pinn_timing_read": (st, [H, I, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                        C.POINTER(C.c_double)]),

@@ -258,6 +258,14 @@ class KfacPinn:
     def launch_count(self) -> int:
         return int(self.lib.kfac_pinn_launch_count(self.h))
 
+    def check_wait_timeout(self, kind: str = "group_barrier", limit_ms: int = 50):
+        """Run a bounded device wait that cannot complete ("group_barrier": the
+        eigensolver's; "mbarrier": the tcgen05 engine's) with a short limit; the
+        handle's status word then holds KFAC_TIMEOUT (see sync_status)."""
+        k = {"group_barrier": 0, "mbarrier": 1}[kind]
+        _check("kfac_pinn_check_wait_timeout",
+               self.lib.kfac_pinn_check_wait_timeout(self.h, _stream(), k, int(limit_ms)))
+
     def timing_enable(self, on: bool = True):
         _check("kfac_pinn_timing_enable", self.lib.kfac_pinn_timing_enable(self.h, int(on)))
 
@@ -335,3 +343,10 @@ class KfacBatch:
             self.b, _stream(), ptrs(thetas), ptrs(X_int), Ia(*[x.shape[0] for x in X_int]), ptrs(f),
             ptrs(X_bdy), Ia(*[x.shape[0] for x in X_bdy]), ptrs(g), None if losses is None else ptrs(losses),
             int(use_graph)))
+
+
+def inject_alloc_failure(n: int):
+    """Make the device allocation after n more successful ones fail as out of
+    memory (n = -1: none); process-wide, for failure-path tests."""
+    lib = _lib.load()
+    _check("kfac_pinn_inject_alloc_failure", lib.kfac_pinn_inject_alloc_failure(int(n)))

@@ -3,6 +3,7 @@
 #include <string.h>
 #include <math.h>
 
+#include <atomic>
 #include <vector>
 
 #include "kfac_internal.cuh"
@@ -11,6 +12,26 @@
 namespace {
 
 }  // namespace
+
+// Allocation-failure injection (kfac_pinn_inject_alloc_failure): the number of
+// device allocations still to succeed before one fails, or -1 for none.
+static std::atomic<long long> g_alloc_fail_in{-1};
+
+kfac_status_t kfac_device_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 1;
+    long long left = g_alloc_fail_in.load();
+    while (left >= 0) {
+        if (g_alloc_fail_in.compare_exchange_weak(left, left - 1)) {
+            if (left == 0) return KFAC_OOM;      // the injected failure: nothing allocated
+            break;
+        }
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); *p = nullptr; return KFAC_OOM; }
+    if (e != cudaSuccess) { *p = nullptr; return KFAC_CUDA_ERROR; }
+    return KFAC_OK;
+}
 
 // The network and operator part of a configuration: d, L, widths (each at
 // most 1023, the last 1, d + 1 at most 1024) and the operator.
@@ -56,14 +77,7 @@ bool valid_config(const kfac_config_t* c) {
     return true;
 }
 
-kfac_status_t dalloc_bytes(void** p, size_t bytes) {
-    *p = nullptr;
-    if (bytes == 0) bytes = 1;
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); *p = nullptr; return KFAC_OOM; }
-    if (e != cudaSuccess) { *p = nullptr; return KFAC_CUDA_ERROR; }
-    return KFAC_OK;
-}
+kfac_status_t dalloc_bytes(void** p, size_t bytes) { return kfac_device_alloc(p, bytes); }
 
 template <class T>
 kfac_status_t dalloc(T** p, size_t elems) {
@@ -432,6 +446,18 @@ const char* kfac_pinn_status_string(kfac_status_t st) {
         case KFAC_NOT_READY: return "KFAC_NOT_READY";
     }
     return "KFAC_UNKNOWN";
+}
+
+kfac_status_t kfac_pinn_check_wait_timeout(kfac_handle_t h, void* stream, int kind, int limit_ms) {
+    if (!h || limit_ms < 1 || limit_ms > 10000 || (kind != 0 && kind != 1)) return KFAC_BAD_ARG;
+    const uint64_t ns = (uint64_t)limit_ms * 1000000ull;
+    return kind == 0 ? eig_check_wait(h, S_(stream), ns) : tc_check_wait(h, S_(stream), ns);
+}
+
+kfac_status_t kfac_pinn_inject_alloc_failure(long long n) {
+    if (n < -1) return KFAC_BAD_ARG;
+    g_alloc_fail_in.store(n);
+    return KFAC_OK;
 }
 
 kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out) {

@@ -484,7 +484,11 @@ __global__ void k_symmetrize(Prob* pr, int* fail) {
 // --------------------------------------------------------------------------
 // 3. Householder tridiagonalisation, cooperative
 // --------------------------------------------------------------------------
-__device__ bool group_barrier(unsigned* bar, int g, int* abort_flag) {
+// Bounded wait of the g CTAs of a group: false (and the abort flag set) when
+// the others have not all arrived within limit_ns of globaltimer, or when
+// another CTA has aborted.
+constexpr uint64_t GROUP_WAIT_LIMIT_NS = 2000000000ull;   // 2 s
+__device__ bool group_barrier(unsigned* bar, int g, int* abort_flag, uint64_t limit_ns = GROUP_WAIT_LIMIT_NS) {
     __syncthreads();
     __shared__ int ok;
     if (threadIdx.x == 0) {
@@ -506,7 +510,7 @@ __device__ bool group_barrier(unsigned* bar, int g, int* abort_flag) {
                 if ((it & 63u) == 0) {
                     uint64_t t1;
                     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-                    if (t1 - t0 > 2000000000ull) { ok = 0; atomicExch(abort_flag, 1); break; }
+                    if (t1 - t0 > limit_ns) { ok = 0; atomicExch(abort_flag, 1); break; }
                 }
                 __nanosleep(64);
             }
@@ -1687,11 +1691,10 @@ __global__ void k_write_w(Prob* pr, int* fail, int* status) {
 // --------------------------------------------------------------------------
 template <class T>
 kfac_status_t dal(T** p, size_t n) {
-    *p = nullptr;
-    if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
-    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return KFAC_OOM; }
-    return e == cudaSuccess ? KFAC_OK : KFAC_CUDA_ERROR;
+    void* v = nullptr;
+    kfac_status_t st = kfac_device_alloc(&v, (n == 0 ? 1 : n) * sizeof(T));
+    *p = (T*)v;
+    return st;
 }
 
 int ceil_log2(int n) {
@@ -1814,7 +1817,8 @@ static kfac_status_t group_alloc(kfac_pinn_handle* h, EigState* es, const std::v
         es->n_trsm_jobs = (int)jobs.size();
         es->bt_smem = 0;
         for (const TrsmJob& j : jobs) es->bt_smem = std::max(es->bt_smem, bt_smem_bytes(es->host[j.prob].n, j.cb));
-        if (cudaMalloc(&es->trsm_jobs, sizeof(TrsmJob) * jobs.size()) != cudaSuccess) return KFAC_OOM;
+        kfac_status_t ast = kfac_device_alloc(&es->trsm_jobs, sizeof(TrsmJob) * jobs.size());
+        if (ast != KFAC_OK) return ast;
         cudaMemcpy(es->trsm_jobs, jobs.data(), sizeof(TrsmJob) * jobs.size(), cudaMemcpyHostToDevice);
     }
 
@@ -2089,6 +2093,33 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
     KFAC_LAUNCH_CHECK(h);
     k_write_w<<<np, 256, 0, s>>>(pr, es->fail, h->status);
     KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+// Self-check of the group barrier's bound: a group of two CTAs of which only
+// this one is launched, so the barrier cannot complete and must give up after
+// limit_ns (kfac_pinn_check_wait_timeout).
+__global__ void k_check_group_barrier(unsigned* bar, int* abort_flag, int* status, uint64_t limit_ns) {
+    if (!group_barrier(bar, 2, abort_flag, limit_ns) && threadIdx.x == 0) latch_status(status, KFAC_TIMEOUT);
+}
+
+kfac_status_t eig_check_wait(kfac_pinn_handle* h, cudaStream_t s, uint64_t limit_ns) {
+    void* scratch = nullptr;     // barrier counter, generation and abort flag
+    kfac_status_t st = kfac_device_alloc(&scratch, 4 * sizeof(unsigned));
+    if (st) return st;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 4 * sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+        unsigned* bar = (unsigned*)scratch;
+        k_check_group_barrier<<<1, 128, 0, s>>>(bar, (int*)(bar + 2), h->status, limit_ns);
+        h->launches++;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(scratch);
+    if (e != cudaSuccess) {
+        kfac_record_cuda_error(e);
+        return KFAC_CUDA_ERROR;
+    }
     return KFAC_OK;
 }
 

@@ -164,6 +164,12 @@ static inline bool is_split_all(const kfac_pinn_handle* h) { return h->cfg.preci
 // The network and operator checks of kfac_pinn_create (abi.cu).
 bool kfac_valid_network(const kfac_config_t* c);
 
+// Every device allocation of the library (abi.cu): cudaMalloc of `bytes`
+// (at least 1), KFAC_OOM when the device is out of memory or when the
+// injected failure of kfac_pinn_inject_alloc_failure is due, KFAC_CUDA_ERROR
+// for any other failure; *p is NULL unless KFAC_OK.
+kfac_status_t kfac_device_alloc(void** p, size_t bytes);
+
 // Device timers: bracket a launch with events when timing is enabled.
 void timer_begin(kfac_pinn_handle* h, int cls, cudaStream_t s);
 // work: algorithmic work of the launch; exec: work as executed (padding and
@@ -216,6 +222,8 @@ size_t linalg_auto_part_elems();
 kfac_status_t eig_alloc(kfac_pinn_handle* h);
 void eig_free(kfac_pinn_handle* h);
 kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s);
+// Self-check of the eigensolver's bounded group barrier (kfac_pinn_check_wait_timeout).
+kfac_status_t eig_check_wait(kfac_pinn_handle* h, cudaStream_t s, uint64_t limit_ns);
 kfac_status_t linalg_invert(kfac_pinn_handle* h, cudaStream_t s);
 kfac_status_t linalg_precondition(kfac_pinn_handle* h, cudaStream_t s, const double* grad,
                                   double* dir);

@@ -41,14 +41,15 @@ KFAC_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait on phase `parity`: gives up after ~timeout_ns of wall time.
+// Bounded wait on phase `parity`: gives up after limit_ns of wall time (or
+// 2^30 polls).
 constexpr uint64_t WAIT_TIMEOUT_NS = 2000000000ull;   // 2 s
-KFAC_DEV bool mbar_wait(uint64_t* bar, uint32_t parity) {
+KFAC_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = WAIT_TIMEOUT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     uint64_t t0 = globaltimer_ns();
     for (uint32_t it = 0; it < (1u << 30); it++) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 0 && globaltimer_ns() - t0 > WAIT_TIMEOUT_NS) return false;
+        if ((it & 255u) == 0 && globaltimer_ns() - t0 > limit_ns) return false;
     }
     return false;
 }

@@ -53,7 +53,13 @@ namespace {
 typedef __nv_bfloat16 bf16;
 constexpr int EW = 256;
 constexpr int MAX_CHUNKS = 16;
-constexpr int MAX_GRAM_CHUNKS = 32;
+constexpr int MAX_GRAM_CHUNKS = 128;
+// Longest row chunk of a Gram or weight-gradient launch: each CTA accumulates
+// its chunk in FP32 (TMEM) and the chunks' partial sums are added in FP64, so
+// the FP32 rounding of these sums over collocation points grows with the
+// chunk, not with the whole batch (at 2048 rows it stays below the 16-bit
+// split-BF16 representation error of the operands).
+constexpr int GRAM_MAX_CHUNK_ROWS = 2048;
 
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
@@ -112,12 +118,10 @@ MxState* MX(kfac_pinn_handle* h) { return (MxState*)h->mx; }
 
 template <class T>
 kfac_status_t dal(T** p, size_t n) {
-    *p = nullptr;
-    if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
-    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return KFAC_OOM; }
-    if (e != cudaSuccess) return KFAC_CUDA_ERROR;
-    return KFAC_OK;
+    void* v = nullptr;
+    kfac_status_t st = kfac_device_alloc(&v, (n == 0 ? 1 : n) * sizeof(T));
+    *p = (T*)v;
+    return st;
 }
 
 // ============================================================================
@@ -1091,13 +1095,20 @@ kfac_status_t gram(kfac_pinn_handle* h, cudaStream_t s, const CUtensorMap& X, co
     if (max_chunks > MAX_GRAM_CHUNKS) max_chunks = MAX_GRAM_CHUNKS;
     if (max_chunks < 1) return KFAC_BAD_ARG;
     const int split = (X_lo && Y_lo) ? 1 : 0;
-    // every candidate needs at most max_chunks chunks
+    // every candidate needs at most max_chunks chunks of at most
+    // GRAM_MAX_CHUNK_ROWS rows (the fewest chunks that fit when the workspace
+    // cannot hold that many)
     Cands c;
-    for (int want = 1; want <= max_chunks; want++) {
+    int want0 = (rows + GRAM_MAX_CHUNK_ROWS - 1) / GRAM_MAX_CHUNK_ROWS;
+    if (want0 > max_chunks) want0 = max_chunks;
+    if (want0 < 1) want0 = 1;
+    for (int want = want0; want <= max_chunks; want++) {
         const int cl = round_up((rows + want - 1) / want, 64);
         const int cnt = (rows + cl - 1) / cl;
+        if (cnt > max_chunks) continue;
         c.add(cl, wave_efficiency((long long)tiles * cnt, h->sm_count) * (double)rows / ((double)cnt * cl));
     }
+    if (c.n == 0) return KFAC_BAD_ARG;
 
     Args a;
     memset(&a, 0, sizeof(a));
@@ -1817,6 +1828,27 @@ kfac_status_t jdot_pass(kfac_pinn_handle* h, cudaStream_t s, MxPass& P, int N, b
 }
 
 }  // namespace
+
+namespace {
+// Self-check of the engine's mbarrier bound: a barrier expecting one arrival
+// that never comes, waited on with limit_ns (kfac_pinn_check_wait_timeout).
+__global__ void k_check_mbar_wait(int* status, uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, limit_ns)) latch_status(status, KFAC_TIMEOUT);
+}
+}  // namespace
+
+kfac_status_t tc_check_wait(kfac_pinn_handle* h, cudaStream_t s, uint64_t limit_ns) {
+    k_check_mbar_wait<<<1, 32, 0, s>>>(h->status, limit_ns);
+    KFAC_LAUNCH_CHECK(h);
+    KFAC_CUDA_TRY(cudaStreamSynchronize(s));
+    return KFAC_OK;
+}
 
 kfac_status_t tc_residual_jvp(kfac_pinn_handle* h, cudaStream_t s, const double* v, int N_int, int N_bdy,
                               double* jv_int, double* jv_bdy) {

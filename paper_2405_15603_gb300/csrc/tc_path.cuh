@@ -22,3 +22,5 @@ kfac_status_t tc_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s,
 // batch (forward activations at theta still held by the handle), KFAC*.
 kfac_status_t tc_residual_jvp(kfac_pinn_handle* h, cudaStream_t s, const double* v, int N_int, int N_bdy,
                               double* jv_int, double* jv_bdy);
+// Self-check of the engine's bounded mbarrier wait (kfac_pinn_check_wait_timeout).
+kfac_status_t tc_check_wait(kfac_pinn_handle* h, cudaStream_t s, uint64_t limit_ns);

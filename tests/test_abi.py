@@ -150,3 +150,13 @@ def test_product_package_does_not_import_oracle():
             if fn.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, fn)).read()
                 assert "oracle" not in txt.replace("oracle_", ""), fn
+
+
+def test_failure_hooks_validate_arguments_without_a_gpu():
+    # argument errors are returned before anything touches the device
+    from paper_2405_15603_gb300 import _lib
+    lib = _lib.load()
+    assert lib.kfac_pinn_inject_alloc_failure(-2) == 1      # KFAC_BAD_ARG
+    assert lib.kfac_pinn_inject_alloc_failure(3) == 0
+    assert lib.kfac_pinn_inject_alloc_failure(-1) == 0
+    assert lib.kfac_pinn_check_wait_timeout(None, None, 0, 50) == 1
