@@ -846,7 +846,8 @@ def main():
         print(json.dumps(run_many()), flush=True)
         return
     if args.equal_l2:
-        print(json.dumps(run_equal_l2(args.equal_l2, precision=args.precision)), flush=True)
+        print(json.dumps(run_equal_l2(args.equal_l2, every=max(5, args.equal_l2 // 10), precision=args.precision)),
+              flush=True)
         return
     if args.c2:
         print(json.dumps(run_c2()), flush=True)
