@@ -115,6 +115,29 @@ typedef enum { KFAC_UPDATE_FIXED = 0, KFAC_UPDATE_LINE_SEARCH = 1, KFAC_UPDATE_A
 typedef enum { KFAC_A_INT = 0, KFAC_B_INT = 1, KFAC_A_BDY = 2, KFAC_B_BDY = 3 } kfac_factor_t;
 
 #define KFAC_MAX_LAYERS 16
+#define KFAC_MAX_RESIDUALS 8
+
+/* A general interior residual (Sec. 3.3, Eq. 9-10) in place of the operator's
+ * own: M outputs that are polynomials of degree two in the network's Taylor
+ * outputs at each point, z_n = (u, du/dx_1, .., du/dx_d, the operator's
+ * second-order column) in R^S, S = d + 2,
+ *     r_{n,k} = sum_s b[k,s] z_{n,s} + 1/2 sum_{s,t} Q[k,s,t] z_{n,s} z_{n,t} - f_{n,k},
+ * fed into the criterion l(r) = 1/2 r^T W r, so that the interior loss is
+ * (1/N) sum_n l(r_n) and the criterion Hessian of Eq. 10 is Lambda = W.
+ * First-order terms of a linear operator are b on the derivative columns, a
+ * term such as |grad u|^2 is Q on them, M > 1 residuals share one network.
+ * B_Omega = (1/N) sum_{n,s} (J_{Z_{n,s}} r_n)^T W (J_{Z_{n,s}} r_n) is formed by
+ * M adjoint passes seeded with the columns of the Cholesky factor of W (the
+ * outer-product rewrite of Sec. 3.3), the gradient by one more seeded with
+ * W r_n.  The interior data f of every call then holds N x M values,
+ * point-major.  Host pointers, read by kfac_pinn_create only. */
+typedef struct {
+    int M;               /* residual outputs, 1..KFAC_MAX_RESIDUALS                 */
+    const double* b;     /* M x S row-major, b[k * S + s]                            */
+    const double* Q;     /* M x S x S, Q[(k * S + s) * S + t], symmetric in s and t;
+                            NULL: r linear in z                                      */
+    const double* W;     /* M x M symmetric positive definite; NULL: the identity   */
+} kfac_residual_t;
 
 typedef struct {
     int d;                         /* input dimension h_0 (>= 1)                       */
@@ -143,6 +166,11 @@ typedef struct {
     const double* op_coef;         /* GENERAL: host pointer to the d x d coefficient
                                       matrix C (row-major, symmetric), read by
                                       kfac_pinn_create only; otherwise ignored        */
+    const kfac_residual_t* residual; /* NULL: the operator's own residual (Eq. 1);
+                                      else the general residual above (LAPLACE or
+                                      HEAT operator, FP64 or FP32 precision,
+                                      KFAC-expand, FIXED or LINE_SEARCH update;
+                                      create returns KFAC_BAD_ARG otherwise)  */
 } kfac_config_t;
 
 typedef struct kfac_pinn_handle* kfac_handle_t;

@@ -18,8 +18,7 @@ library primitives it uses.  Notation:
     [value, ∂_1, .., ∂_d, Laplacian] (Sec. 3.2; App. C.2 Eq. 20);
   * arrays of per-point matrices have shape (N, rows, S).
 
-Readings taken where the paper is silent or inconsistent (listed in the
-design notes as well):
+Readings taken where the paper is silent or inconsistent:
   * The Laplacian column carries the full Laplacian Δz (main text, Eq. 6),
     not the half-Laplacian of the Taylor coefficients of App. C.
   * The loss is Eq. 1 with 1/(2N) on both terms, also for the heat equation.
@@ -37,6 +36,9 @@ design notes as well):
     B = (1/N) Σ_n ḡ_n ḡ_nᵀ with ḡ_n the sum of the S output gradients.
   * Damping adds λ (or √λ when `damping_sqrt`) times the identity to each
     factor (Sec. 3.4).
+  * General residuals (Sec. 3.3) are taken as polynomials of degree two in
+    the network's Taylor outputs with a quadratic criterion ½ rᵀ W r, so that
+    Λ = W; the PDE map Ψ of Eq. 9 is not otherwise specified.
 """
 from __future__ import annotations
 
@@ -224,8 +226,57 @@ def residual_seed(S: int, op: str, kappa: float, interior: bool) -> np.ndarray:
     return c
 
 
+@dataclass
+class QuadraticResidual:
+    """A PDE residual with M outputs (Sec. 3.3, Eq. 9) that is a polynomial of
+    degree two in the network's Taylor outputs z_n = Z^{(L)}_n = (u, ∂_1 u, ..,
+    ∂_d u, second-order column) ∈ R^S:
+
+        r_{n,k} = Σ_s b[k,s] z_{n,s} + ½ Σ_{s,t} Q[k,s,t] z_{n,s} z_{n,t} - f_{n,k},
+
+    fed into the criterion ℓ(r) = ½ rᵀ W r, whose Hessian Λ(r) = W is constant
+    (W = I: the squared residual of Eq. 1).  First-order terms of a linear
+    operator are b on the first-derivative columns; the |∇u|² of a nonlinear
+    one is Q on them."""
+    b: np.ndarray                     # (M, S)
+    Q: Optional[np.ndarray] = None    # (M, S, S), symmetric in its last two indices
+    W: Optional[np.ndarray] = None    # (M, M) symmetric positive definite; None: identity
+
+    @property
+    def M(self) -> int:
+        return self.b.shape[0]
+
+    def weight(self) -> np.ndarray:
+        return np.eye(self.M) if self.W is None else np.asarray(self.W, dtype=np.float64)
+
+
+def quadratic_residual(res: QuadraticResidual, z: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """r_{n,k} for outputs z (N, S) and data f (N, M): shape (N, M)."""
+    r = z @ res.b.T - np.asarray(f, dtype=np.float64).reshape(z.shape[0], res.M)
+    if res.Q is not None:
+        r = r + 0.5 * np.einsum("ns,kst,nt->nk", z, res.Q, z)
+    return r
+
+
+def quadratic_residual_jacobian(res: QuadraticResidual, z: np.ndarray) -> np.ndarray:
+    """∂r_{n,k}/∂z_{n,s} = b[k,s] + Σ_t Q[k,s,t] z_{n,t}: shape (N, M, S)."""
+    J = np.broadcast_to(res.b[None, :, :], (z.shape[0],) + res.b.shape).copy()
+    if res.Q is not None:
+        J = J + np.einsum("kst,nt->nks", res.Q, z)
+    return J
+
+
 def loss(r_int: np.ndarray, r_bdy: np.ndarray) -> Tuple[float, float, float]:
     li = float((r_int ** 2).sum() / (2.0 * r_int.size))
+    lb = float((r_bdy ** 2).sum() / (2.0 * r_bdy.size))
+    return li + lb, li, lb
+
+
+def loss_general(res: QuadraticResidual, r_int: np.ndarray, r_bdy: np.ndarray) -> Tuple[float, float, float]:
+    """L_Ω = (1/N) Σ_n ℓ(r_n) with ℓ(r) = ½ rᵀ W r (Sec. 3.3), plus the boundary
+    term of Eq. 1."""
+    W = res.weight()
+    li = float(np.einsum("nk,kj,nj->", r_int, W, r_int) / (2.0 * r_int.shape[0]))
     lb = float((r_bdy ** 2).sum() / (2.0 * r_bdy.size))
     return li + lb, li, lb
 
@@ -270,6 +321,9 @@ def taylor_adjoint(Ws: Sequence[np.ndarray], fp: TaylorPass, seed: np.ndarray,
     """Backpropagate the seed c through the Taylor pass (App. B, the backward
     that yields g^{(l)}).  Returns Zbar[l] = g^{(l+1)}, shape (N, h_{l+1}, S).
 
+    seed: c = ∂r_n/∂Z^{(L)}_n, the same row of length S for every point, or
+    one row per point, shape (N, S) (a residual that is nonlinear in the
+    network's outputs, Sec. 3.3).
     Linear layer Z = W̃ T̂: T̄ = W̃ᵀ Z̄ with the bias row dropped.
     Activation layer: `tanh_taylor_adjoint`."""
     L = len(Ws)
@@ -277,7 +331,11 @@ def taylor_adjoint(Ws: Sequence[np.ndarray], fp: TaylorPass, seed: np.ndarray,
     d = fp.T_in[0].shape[1] - 1
     C = operator_matrix(d, op, coef)
     Zbar: List[Optional[np.ndarray]] = [None] * L
-    cur = np.broadcast_to(seed[None, None, :], (N, 1, seed.size)).copy()
+    seed = np.asarray(seed, dtype=np.float64)
+    if seed.ndim == 1:
+        cur = np.broadcast_to(seed[None, None, :], (N, 1, seed.size)).copy()
+    else:
+        cur = seed[:, None, :].copy()
     for l in range(L - 1, -1, -1):
         Zbar[l] = cur
         if l == 0:
@@ -390,6 +448,7 @@ class KfacConfig:
     line_search: bool = False
     kfac_star: bool = False     # automatic learning rate and momentum (KFAC*, Sec. 3.4)
     op_coef: Optional[np.ndarray] = None   # op == "general": symmetric d x d c_ij (App. C.3)
+    residual: Optional[QuadraticResidual] = None   # interior residual of Sec. 3.3 (None: the operator's own)
 
 
 @dataclass
@@ -422,8 +481,51 @@ class StepResult:
     extras: dict = field(default_factory=dict)
 
 
+def curvature_and_gradient_general(cfg: KfacConfig, Ws, X_int, f, X_bdy, g):
+    """The curvature and gradient of a general residual (Sec. 3.3): per residual
+    output k an adjoint pass seeded with ∂r_{n,k}/∂Z^{(L)}_n gives
+    g^{(l)}_{n,s,k} = (J_{Z^{(l)}_{n,s}} r_{n,k})ᵀ, and with Λ = W
+
+        A_Ω = (1/(N S)) Σ_{n,s} T̂_{n,s} T̂_{n,s}ᵀ,
+        B_Ω = (1/N) Σ_{n,s} (J_{Z_{n,s}} r_n)ᵀ Λ (J_{Z_{n,s}} r_n)
+            = (1/N) Σ_{n,s} Σ_{k,k'} W_{k,k'} g_{n,s,k} g_{n,s,k'}ᵀ            (Eq. 10),
+        ∇_{W̃_l} L_Ω = (1/N) Σ_n Σ_k (W r_n)_k J_{W̃_l} r_{n,k}.
+
+    KFAC-expand; the boundary term is the one of Eq. 1."""
+    res = cfg.residual
+    assert cfg.variant == "expand", "the general residual is expand-only"
+    W = res.weight()
+    fp_i = taylor_forward(Ws, X_int, cfg.op, True, cfg.op_coef)
+    z = fp_i.Z[-1][:, 0, :]
+    r_i = quadratic_residual(res, z, f)
+    J = quadratic_residual_jacobian(res, z)
+    zb_k = [taylor_adjoint(Ws, fp_i, J[:, k, :], cfg.op, cfg.op_coef) for k in range(res.M)]
+    fp_b = taylor_forward(Ws, X_bdy, cfg.op, False, cfg.op_coef)
+    r_b = boundary_residual(fp_b, g)
+    zb_b = taylor_adjoint(Ws, fp_b, residual_seed(1, cfg.op, cfg.kappa, False), cfg.op, cfg.op_coef)
+    N = z.shape[0]
+    Wr = r_i @ W                                   # (W r_n)_k, W symmetric
+    Ai, Bi, Ab, Bb, grads = [], [], [], [], []
+    for l in range(len(Ws)):
+        T = fp_i.T_in[l]
+        S = T.shape[2]
+        Tf = np.transpose(T, (0, 2, 1)).reshape(N * S, -1)
+        Ai.append(Tf.T @ Tf / (N * S))
+        Gf = [np.transpose(zb[l], (0, 2, 1)).reshape(N * S, -1) for zb in zb_k]
+        Bi.append(sum(W[k, kk] * (Gf[k].T @ Gf[kk]) for k in range(res.M) for kk in range(res.M)) / N)
+        a, b = factors_expand(fp_b.T_in[l], zb_b[l])
+        Ab.append(a); Bb.append(b)
+        gi = sum(np.tensordot(Wr[:, k], weight_jacobian(zb_k[k][l], T), axes=(0, 0)) for k in range(res.M)) / N
+        gb = np.tensordot(r_b, weight_jacobian(zb_b[l], fp_b.T_in[l]), axes=(0, 0)) / r_b.size
+        grads.append(gi + gb)
+    return dict(fp_i=fp_i, fp_b=fp_b, r_i=r_i, r_b=r_b, zb_i_k=zb_k, zb_b=zb_b, J=J,
+                factors=(Ai, Bi, Ab, Bb), grads=grads, loss=loss_general(res, r_i, r_b))
+
+
 def curvature_and_gradient(cfg: KfacConfig, Ws, X_int, f, X_bdy, g):
     """App. B (without the preconditioner)."""
+    if cfg.residual is not None:
+        return curvature_and_gradient_general(cfg, Ws, X_int, f, X_bdy, g)
     fp_i = taylor_forward(Ws, X_int, cfg.op, True, cfg.op_coef)
     r_i = interior_residual(fp_i, f, cfg.op, cfg.kappa)
     zb_i = taylor_adjoint(Ws, fp_i, residual_seed(fp_i.S, cfg.op, cfg.kappa, True), cfg.op, cfg.op_coef)
@@ -445,9 +547,11 @@ def curvature_and_gradient(cfg: KfacConfig, Ws, X_int, f, X_bdy, g):
 def batch_loss(cfg: KfacConfig, theta: np.ndarray, X_int, f, X_bdy, g) -> Tuple[float, float, float]:
     """Eq. 1 at theta on one batch: forward passes and residuals only."""
     Ws = unpack_theta(theta, cfg.d, cfg.widths)
-    r_i = interior_residual(taylor_forward(Ws, X_int, cfg.op, True, cfg.op_coef), f, cfg.op, cfg.kappa)
+    fp_i = taylor_forward(Ws, X_int, cfg.op, True, cfg.op_coef)
     r_b = boundary_residual(taylor_forward(Ws, X_bdy, cfg.op, False, cfg.op_coef), g)
-    return loss(r_i, r_b)
+    if cfg.residual is not None:
+        return loss_general(cfg.residual, quadratic_residual(cfg.residual, fp_i.Z[-1][:, 0, :], f), r_b)
+    return loss(interior_residual(fp_i, f, cfg.op, cfg.kappa), r_b)
 
 
 LINE_SEARCH_GRID = tuple(2.0 ** -k for k in range(31))   # {2^0, 2^-1, .., 2^-30} (Sec. 3.4)
@@ -470,17 +574,29 @@ def line_search(cfg: KfacConfig, theta: np.ndarray, dhat: np.ndarray, X_int, f, 
 
 def residual_jvp(cg: dict, V: Sequence[np.ndarray]) -> Tuple[np.ndarray, np.ndarray]:
     """J_θ r · v for the interior and boundary residuals: (J_n v) = Σ_l ⟨J_{W̃_l} r_n, V_l⟩
-    with the per-point weight Jacobians of Sec. 3.2 (V_l shaped like W̃_l)."""
-    ji = sum(np.einsum("nij,ij->n", weight_jacobian(cg["zb_i"][l], cg["fp_i"].T_in[l]), V[l])
-             for l in range(len(V)))
+    with the per-point weight Jacobians of Sec. 3.2 (V_l shaped like W̃_l).  A
+    residual with M outputs (Sec. 3.3) gives (N, M) interior products."""
+    if "zb_i_k" in cg:
+        ji = np.stack([sum(np.einsum("nij,ij->n", weight_jacobian(zb[l], cg["fp_i"].T_in[l]), V[l])
+                           for l in range(len(V))) for zb in cg["zb_i_k"]], axis=1)
+    else:
+        ji = sum(np.einsum("nij,ij->n", weight_jacobian(cg["zb_i"][l], cg["fp_i"].T_in[l]), V[l])
+                 for l in range(len(V)))
     jb = sum(np.einsum("nij,ij->n", weight_jacobian(cg["zb_b"][l], cg["fp_b"].T_in[l]), V[l])
              for l in range(len(V)))
     return ji, jb
 
 
-def gramian_bilinear(ja: Tuple[np.ndarray, np.ndarray], jb: Tuple[np.ndarray, np.ndarray]) -> float:
-    """aᵀ G b with G of Eq. 2, from the residual JVPs J a and J b."""
-    return float(ja[0] @ jb[0] / ja[0].size + ja[1] @ jb[1] / ja[1].size)
+def gramian_bilinear(ja: Tuple[np.ndarray, np.ndarray], jb: Tuple[np.ndarray, np.ndarray],
+                     W: Optional[np.ndarray] = None) -> float:
+    """aᵀ G b with G of Eq. 2 (Λ = W for a residual with M outputs, Sec. 3.3),
+    from the residual JVPs J a and J b."""
+    if ja[0].ndim == 2:
+        Wm = np.eye(ja[0].shape[1]) if W is None else W
+        inner = float(np.einsum("nk,kj,nj->", ja[0], Wm, jb[0]) / ja[0].shape[0])
+    else:
+        inner = float(ja[0] @ jb[0] / ja[0].size)
+    return inner + float(ja[1] @ jb[1] / ja[1].size)
 
 
 def kfac_star_coefficients(cfg: KfacConfig, cg: dict, Delta: np.ndarray, delta: Optional[np.ndarray],
@@ -489,15 +605,16 @@ def kfac_star_coefficients(cfg: KfacConfig, cg: dict, Delta: np.ndarray, delta: 
     Gramian G + λI (Sec. 3.4, after Martens & Grosse 2015, Sec. 7).  On the
     first step (δ = 0) the model is minimised over α alone and μ* = 0."""
     lam = cfg.lam
+    W = None if cfg.residual is None else cfg.residual.weight()
     unpack = lambda v: unpack_theta(v, cfg.d, cfg.widths)
     jD = residual_jvp(cg, unpack(Delta))
-    a11 = gramian_bilinear(jD, jD) + lam * float(Delta @ Delta)
+    a11 = gramian_bilinear(jD, jD, W) + lam * float(Delta @ Delta)
     b1 = float(Delta @ grad)
     if delta is None or not np.any(delta):
         return -b1 / a11, 0.0
     jd = residual_jvp(cg, unpack(delta))
-    a12 = gramian_bilinear(jD, jd) + lam * float(Delta @ delta)
-    a22 = gramian_bilinear(jd, jd) + lam * float(delta @ delta)
+    a12 = gramian_bilinear(jD, jd, W) + lam * float(Delta @ delta)
+    a22 = gramian_bilinear(jd, jd, W) + lam * float(delta @ delta)
     b2 = float(delta @ grad)
     alpha, mu = -np.linalg.solve(np.array([[a11, a12], [a12, a22]]), np.array([b1, b2]))
     return float(alpha), float(mu)
@@ -575,9 +692,16 @@ def full_ggn(cfg: KfacConfig, Ws, X_int, f, X_bdy, g) -> np.ndarray:
                 for l in range(len(Ws))]))
         return np.stack(rows)
 
-    Ji = jac_rows(cg["fp_i"], cg["zb_i"])
     Jb = jac_rows(cg["fp_b"], cg["zb_b"])
-    return Ji.T @ Ji / Ji.shape[0] + Jb.T @ Jb / Jb.shape[0]
+    Gb = Jb.T @ Jb / Jb.shape[0]
+    if "zb_i_k" in cg:     # Σ_n J_nᵀ Λ J_n with the rows of J_n per residual output (Sec. 3.3)
+        W = cfg.residual.weight()
+        Jk = [jac_rows(cg["fp_i"], zb) for zb in cg["zb_i_k"]]
+        N = Jk[0].shape[0]
+        Gi = sum(W[k, kk] * (Jk[k].T @ Jk[kk]) for k in range(len(Jk)) for kk in range(len(Jk))) / N
+        return Gi + Gb
+    Ji = jac_rows(cg["fp_i"], cg["zb_i"])
+    return Ji.T @ Ji / Ji.shape[0] + Gb
 
 
 def relative_l2(u: np.ndarray, u_star: np.ndarray) -> float:

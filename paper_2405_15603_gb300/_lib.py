@@ -26,6 +26,7 @@ EXPORTS = [
 ]
 
 KFAC_TUNE_CAP = 128
+KFAC_MAX_RESIDUALS = 8
 
 KERNEL_CLASSES = {0: "layer_gemm", 1: "adjoint_gemm", 2: "gram", 3: "elementwise", 4: "eig", 5: "precond"}
 
@@ -37,8 +38,12 @@ class KfacConfig(C.Structure):
         ("beta", C.c_double), ("lambda_", C.c_double), ("damping_sqrt", C.c_int),
         ("factor_init_identity", C.c_int), ("lr", C.c_double), ("momentum", C.c_double),
         ("max_n_int", C.c_int), ("max_n_bdy", C.c_int), ("update", C.c_int), ("eig_sm_budget", C.c_int),
-        ("op_coef", C.c_void_p),
+        ("op_coef", C.c_void_p), ("residual", C.c_void_p),
     ]
+
+
+class KfacResidual(C.Structure):
+    _fields_ = [("M", C.c_int), ("b", C.c_void_p), ("Q", C.c_void_p), ("W", C.c_void_p)]
 
 
 TUNE_KINDS = {0: "gram", 1: "fwd_tan", 2: "bwd_tan"}

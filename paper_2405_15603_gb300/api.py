@@ -46,9 +46,11 @@ def make_config(d: int, widths: Sequence[int], op: str = "laplace", kappa: float
                 lam: float = 1e-3, damping_sqrt: bool = False, init_identity: bool = False,
                 lr: float = 0.1, momentum: float = 0.0, max_n_int: int = 1024,
                 max_n_bdy: int = 1024, line_search: bool = False, update: str = "fixed",
-                eig_sm_budget: int = 0, op_coef=None) -> KfacConfig:
+                eig_sm_budget: int = 0, op_coef=None, residual=None) -> KfacConfig:
     """line_search=True is shorthand for update="line_search".  op="general" takes
-    the symmetric d x d coefficient matrix op_coef (kept alive on the config)."""
+    the symmetric d x d coefficient matrix op_coef (kept alive on the config).
+    residual: a general interior residual (Sec. 3.3) as a dict with "b" (M x S),
+    optional "Q" (M x S x S) and "W" (M x M); see kfac_residual_t."""
     cfg = KfacConfig()
     cfg.d = d
     cfg.L = len(widths)
@@ -72,6 +74,20 @@ def make_config(d: int, widths: Sequence[int], op: str = "laplace", kappa: float
         arr = np.ascontiguousarray(op_coef, dtype=np.float64)
         cfg._op_coef_keepalive = arr
         cfg.op_coef = arr.ctypes.data
+    if residual is not None:
+        res = _lib.KfacResidual()
+        keep = []
+        b = np.ascontiguousarray(residual["b"], dtype=np.float64)
+        res.M = b.shape[0]
+        res.b = b.ctypes.data
+        keep.append(b)
+        for key in ("Q", "W"):
+            if residual.get(key) is not None:
+                arr = np.ascontiguousarray(residual[key], dtype=np.float64)
+                setattr(res, key, arr.ctypes.data)
+                keep.append(arr)
+        cfg._residual_keepalive = (res, keep)
+        cfg.residual = C.addressof(res)
     return cfg
 
 

@@ -49,6 +49,59 @@ bool kfac_valid_network(const kfac_config_t* c) {
 
 namespace {
 
+// Cholesky factor of the M x M symmetric matrix W (row-major, lower
+// triangle into Lw); false unless W is positive definite.
+bool host_cholesky(const double* W, int M, double* Lw) {
+    for (int i = 0; i < M * M; i++) Lw[i] = 0.0;
+    for (int j = 0; j < M; j++) {
+        double dsum = W[j * M + j];
+        for (int k = 0; k < j; k++) dsum -= Lw[j * M + k] * Lw[j * M + k];
+        if (!(dsum > 0.0) || !isfinite(dsum)) return false;
+        const double ljj = sqrt(dsum);
+        Lw[j * M + j] = ljj;
+        for (int i = j + 1; i < M; i++) {
+            double v = W[i * M + j];
+            for (int k = 0; k < j; k++) v -= Lw[i * M + k] * Lw[j * M + k];
+            Lw[i * M + j] = v / ljj;
+        }
+    }
+    return true;
+}
+
+// The general residual: 1 <= M <= KFAC_MAX_RESIDUALS, finite b, Q symmetric in
+// its last two indices, W symmetric positive definite; the SIMT precisions,
+// the LAPLACE or HEAT operator (coordinate tangents), KFAC-expand, and the
+// FIXED or LINE_SEARCH update.
+bool valid_residual(const kfac_config_t* c) {
+    const kfac_residual_t* r = c->residual;
+    if (r->M < 1 || r->M > KFAC_MAX_RESIDUALS || !r->b) return false;
+    if (c->op != KFAC_OP_LAPLACE && c->op != KFAC_OP_HEAT) return false;
+    if (c->precision != KFAC_FP64 && c->precision != KFAC_FP32) return false;
+    if (c->variant != KFAC_EXPAND || c->update == KFAC_UPDATE_AUTO) return false;
+    const int M = r->M, S = c->d + 2;
+    for (int i = 0; i < M * S; i++)
+        if (!isfinite(r->b[i])) return false;
+    if (r->Q) {
+        for (int k = 0; k < M; k++)
+            for (int a = 0; a < S; a++)
+                for (int b = 0; b < S; b++) {
+                    const double q = r->Q[((size_t)k * S + a) * S + b];
+                    if (!isfinite(q) || fabs(q - r->Q[((size_t)k * S + b) * S + a]) > 1e-12 * (1.0 + fabs(q)))
+                        return false;
+                }
+    }
+    if (r->W) {
+        for (int i = 0; i < M; i++)
+            for (int j = 0; j < M; j++)
+                if (!isfinite(r->W[i * M + j]) || fabs(r->W[i * M + j] - r->W[j * M + i]) >
+                                                       1e-12 * (1.0 + fabs(r->W[i * M + j])))
+                    return false;
+        std::vector<double> Lw((size_t)M * M);
+        if (!host_cholesky(r->W, M, Lw.data())) return false;
+    }
+    return true;
+}
+
 bool valid_config(const kfac_config_t* c) {
     if (!kfac_valid_network(c)) return false;
     if (c->op == KFAC_OP_GENERAL) {
@@ -65,6 +118,7 @@ bool valid_config(const kfac_config_t* c) {
     if (c->precision != KFAC_FP64 && c->precision != KFAC_MIXED_BF16 && c->precision != KFAC_MIXED_SPLIT &&
         c->precision != KFAC_FP32)
         return false;
+    if (c->residual && !valid_residual(c)) return false;
     if (c->variant != KFAC_EXPAND && c->variant != KFAC_REDUCE) return false;
     if (!(c->beta >= 0.0 && c->beta < 1.0)) return false;
     if (!(c->lambda > 0.0) || !isfinite(c->lambda)) return false;
@@ -156,6 +210,29 @@ kfac_status_t setup_operator(kfac_pinn_handle* h) {
         KFAC_CUDA_TRY(cudaMemcpy(h->opQ, Q.data(), sizeof(double) * d * d, cudaMemcpyHostToDevice));
     }
     h->cfg.op_coef = nullptr;           // read only here
+    h->fM = 1;
+    if (h->cfg.residual) {
+        const kfac_residual_t* r = h->cfg.residual;
+        const int M = r->M, S = d + 2;
+        std::vector<double> coef((size_t)M * S + 2 * (size_t)M * M + (r->Q ? (size_t)M * S * S : 0), 0.0);
+        double* b = coef.data();
+        double* W = b + (size_t)M * S;
+        double* Lw = W + (size_t)M * M;
+        for (int i = 0; i < M * S; i++) b[i] = r->b[i];
+        for (int i = 0; i < M; i++) W[i * M + i] = 1.0;
+        if (r->W)
+            for (int i = 0; i < M * M; i++) W[i] = r->W[i];
+        if (!host_cholesky(W, M, Lw)) return KFAC_BAD_ARG;
+        if (r->Q)
+            for (size_t i = 0; i < (size_t)M * S * S; i++) Lw[(size_t)M * M + i] = r->Q[i];
+        if ((st = dalloc(&h->res_coef, coef.size()))) return st;
+        KFAC_CUDA_TRY(cudaMemcpy(h->res_coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice));
+        if ((st = dalloc(&h->res_r, (size_t)h->cfg.max_n_int * M))) return st;
+        h->res_M = M;
+        h->res_has_Q = r->Q ? 1 : 0;
+        h->fM = M;
+    }
+    h->cfg.residual = nullptr;          // read only here
     std::vector<float> wf(w.begin(), w.end());
     if ((st = dalloc(&h->chw64, (size_t)d))) return st;
     if ((st = dalloc(&h->chw32, (size_t)d))) return st;
@@ -194,6 +271,8 @@ void free_handle(kfac_pinn_handle* h) {
     cudaFree(h->opQ);
     cudaFree(h->chw64);
     cudaFree(h->chw32);
+    cudaFree(h->res_coef);
+    cudaFree(h->res_r);
     cudaFree(h->w1q);
     cudaFree(h->w1q2);
     for (int w = 0; w < 4; w++)
@@ -309,6 +388,15 @@ kfac_status_t run_factors(kfac_pinn_handle* h, cudaStream_t s, const double* the
         return tc_factors(h, s, theta, X_int, N_int, f, X_bdy, N_bdy, g, loss);
     kfac_status_t st;
     const int S = h->S;
+    if (h->res_M > 0) {      // general residual: M + 1 seeded interior adjoint passes
+        if ((st = simt_forward(h, s, theta, X_int, N_int, h->in, S))) return st;
+        if ((st = simt_residual_general(h, s, N_int, f))) return st;
+        if ((st = simt_forward(h, s, theta, X_bdy, N_bdy, h->bd, 1))) return st;
+        if ((st = simt_residual_and_seed(h, s, h->bd, N_bdy, 1, g, false))) return st;
+        if ((st = simt_backward(h, s, theta, h->bd, N_bdy, 1))) return st;
+        if ((st = fp64_loss(h, s, N_int, N_bdy, loss))) return st;
+        return simt_backward_and_factors_general(h, s, theta, X_int, N_int, f, X_bdy, N_bdy);
+    }
     if ((st = simt_forward(h, s, theta, X_int, N_int, h->in, S))) return st;
     if ((st = simt_residual_and_seed(h, s, h->in, N_int, S, f, true))) return st;
     if ((st = simt_backward(h, s, theta, h->in, N_int, S))) return st;
@@ -519,7 +607,7 @@ kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out) {
     h->lin_elems = linalg_workspace_elems(h);
     TRY(dalloc(&h->lin, h->lin_elems));
     TRY(dalloc(&h->status, 1));
-    h->stage_elems = (size_t)cfg->max_n_int * (cfg->d + 1) + (size_t)cfg->max_n_bdy * (cfg->d + 1) + 8;
+    h->stage_elems = (size_t)cfg->max_n_int * (cfg->d + h->fM) + (size_t)cfg->max_n_bdy * (cfg->d + 1) + 8;
     TRY(dalloc(&h->stage, h->stage_elems));
     if (is_mixed(h)) TRY(tc_alloc(h));
     TRY(eig_alloc(h));
@@ -716,11 +804,11 @@ kfac_status_t kfac_pinn_step(kfac_handle_t h, void* stream, double* theta,
         const int d = h->dims[0];
         double* xi = h->stage;
         double* fi = xi + (size_t)N_int * d;
-        double* xb = fi + N_int;
+        double* xb = fi + (size_t)N_int * h->fM;
         double* gb = xb + (size_t)N_bdy * d;
         if (X_int != xi) {
             KFAC_CUDA_TRY(cudaMemcpyAsync(xi, X_int, (size_t)N_int * d * sizeof(double), cudaMemcpyDeviceToDevice, s));
-            KFAC_CUDA_TRY(cudaMemcpyAsync(fi, f, (size_t)N_int * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            KFAC_CUDA_TRY(cudaMemcpyAsync(fi, f, (size_t)N_int * h->fM * sizeof(double), cudaMemcpyDeviceToDevice, s));
             KFAC_CUDA_TRY(cudaMemcpyAsync(xb, X_bdy, (size_t)N_bdy * d * sizeof(double), cudaMemcpyDeviceToDevice, s));
             KFAC_CUDA_TRY(cudaMemcpyAsync(gb, g, (size_t)N_bdy * sizeof(double), cudaMemcpyDeviceToDevice, s));
         }
@@ -764,10 +852,10 @@ kfac_status_t kfac_pinn_step_host(kfac_handle_t h, void* stream, double* theta,
     const int d = h->dims[0];
     double* xi = h->stage;
     double* fi = xi + (size_t)N_int * d;
-    double* xb = fi + N_int;
+    double* xb = fi + (size_t)N_int * h->fM;
     double* gb = xb + (size_t)N_bdy * d;
     KFAC_CUDA_TRY(cudaMemcpyAsync(xi, X_int_host, (size_t)N_int * d * sizeof(double), cudaMemcpyHostToDevice, s));
-    KFAC_CUDA_TRY(cudaMemcpyAsync(fi, f_host, (size_t)N_int * sizeof(double), cudaMemcpyHostToDevice, s));
+    KFAC_CUDA_TRY(cudaMemcpyAsync(fi, f_host, (size_t)N_int * h->fM * sizeof(double), cudaMemcpyHostToDevice, s));
     KFAC_CUDA_TRY(cudaMemcpyAsync(xb, X_bdy_host, (size_t)N_bdy * d * sizeof(double), cudaMemcpyHostToDevice, s));
     KFAC_CUDA_TRY(cudaMemcpyAsync(gb, g_host, (size_t)N_bdy * sizeof(double), cudaMemcpyHostToDevice, s));
     if ((st = kfac_pinn_step(h, stream, theta, xi, N_int, fi, xb, N_bdy, gb, h->loss))) return st;

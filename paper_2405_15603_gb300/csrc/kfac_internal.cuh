@@ -60,6 +60,12 @@ struct kfac_pinn_handle {
     // Taylor pass has direction v_m = opQ e_m (opQ == nullptr: e_m) and weight chw[m]
     // in the second-order column (App. C.3)
     double cT, cD;
+    // general interior residual (kfac_residual_t; res_M == 0: the operator's own)
+    int res_M;
+    int res_has_Q;
+    int fM;               // interior data values per point: res_M, or 1
+    double* res_coef;     // b (M x S), W (M x M), L_W (M x M, Cholesky of W), Q (M x S x S)
+    double* res_r;        // residuals r_{n,k} of the last interior pass (max_n_int x M)
     double* opQ;          // d x d row-major (general operator only)
     double* chw64;        // d
     float* chw32;         // d
@@ -199,6 +205,13 @@ kfac_status_t simt_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* 
                              double* dst);
 kfac_status_t simt_jvp(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* v,
                        const double* X, int N, PassBuffers& pb, int S, bool interior, double* jv);
+// General interior residual (Sec. 3.3): r_{n,k} into h->res_r and r_n^T W r_n into
+// h->in.r from the interior pass's outputs; the whole curvature-and-gradient part
+// of a step after both forward passes (M + 1 interior adjoint passes).
+kfac_status_t simt_residual_general(kfac_pinn_handle* h, cudaStream_t s, int N, const double* f);
+kfac_status_t simt_backward_and_factors_general(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                                                const double* X_int, int N_int, const double* f,
+                                                const double* X_bdy, int N_bdy);
 // Automatic learning rate and momentum (linalg.cu), FP64 handles
 kfac_status_t linalg_auto_update(kfac_pinn_handle* h, cudaStream_t s, double* theta, const double* X_int,
                                  int N_int, const double* X_bdy, int N_bdy);

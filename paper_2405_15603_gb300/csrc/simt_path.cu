@@ -200,11 +200,12 @@ __global__ void k_seed(R* __restrict__ ZbL, int N, int S, int interior, double c
 }
 
 // loss[1] = sum r^2 / (2N), loss[2] = sum rb^2 / (2Nb), loss[0] = loss[1] + loss[2].
+// r_sq: r already holds the per-point r_n^T W r_n of a general residual.
 __global__ void k_loss(const double* __restrict__ r, int N, const double* __restrict__ rb, int Nb,
-                       double* __restrict__ loss, int* status) {
+                       double* __restrict__ loss, int* status, int r_sq) {
     __shared__ double sh[2][32];
     double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) a = fma(r[i], r[i], a);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) a = r_sq ? a + r[i] : fma(r[i], r[i], a);
     for (int i = threadIdx.x; i < Nb; i += blockDim.x) b = fma(rb[i], rb[i], b);
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, o);
@@ -371,9 +372,11 @@ kfac_status_t backward_t(kfac_pinn_handle* h, cudaStream_t s, const double* thet
     return KFAC_OK;
 }
 
+// general: the interior adjoint was seeded with W r_n (a general residual), so
+// its rows enter the gradient unweighted, and B_Omega was formed beforehand.
 template <class R, class RowsI, class RowsB>
 kfac_status_t layer_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, int l, RowsI in_i,
-                                     RowsB in_b, int N, int Nb) {
+                                     RowsB in_b, int N, int Nb, bool general) {
     const int S = h->S;
     const int hout = h->dims[l], nin = h->dims[l - 1] + 1;
     const double beta = h->cfg.beta;
@@ -381,7 +384,7 @@ kfac_status_t layer_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, int l,
     kfac_status_t st;
     // Weight gradient: (1/N) sum_rows r_n g_row T^_row^T  +  (1/Nb) sum ...
     {
-        Transposed<WeightedRows<R>> A{WeightedRows<R>{act<R>(h->in.Zb[l - 1]), hout, N, h->in.r}};
+        Transposed<WeightedRows<R>> A{WeightedRows<R>{act<R>(h->in.Zb[l - 1]), hout, N, general ? nullptr : h->in.r}};
         st = reduce_gemm(h, s, hout, nin, S * N, A, in_i, 1.0 / N, gW, 1, hout, 0, 0, 0.0);
         if (st != KFAC_OK) return st;
         Transposed<WeightedRows<R>> Ab{WeightedRows<R>{act<R>(h->bd.Zb[l - 1]), hout, Nb, h->bd.r}};
@@ -393,10 +396,12 @@ kfac_status_t layer_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, int l,
         st = reduce_gemm(h, s, nin, nin, S * N, Transposed<RowsI>{in_i}, in_i, 1.0 / ((double)N * S),
                             h->fac[KFAC_A_INT][l - 1], nin, 1, 0, 1, beta);
         if (st != KFAC_OK) return st;
-        WeightedRows<R> G{act<R>(h->in.Zb[l - 1]), hout, N, nullptr};
-        st = reduce_gemm(h, s, hout, hout, S * N, Transposed<WeightedRows<R>>{G}, G, 1.0 / N,
-                            h->fac[KFAC_B_INT][l - 1], hout, 1, 0, 1, beta);
-        if (st != KFAC_OK) return st;
+        if (!general) {
+            WeightedRows<R> G{act<R>(h->in.Zb[l - 1]), hout, N, nullptr};
+            st = reduce_gemm(h, s, hout, hout, S * N, Transposed<WeightedRows<R>>{G}, G, 1.0 / N,
+                                h->fac[KFAC_B_INT][l - 1], hout, 1, 0, 1, beta);
+            if (st != KFAC_OK) return st;
+        }
     } else {
         // KFAC-reduce: abar_n = (1/S) sum_s T^_{n,s}, gbar_n = sum_s g_{n,s}.
         R* ra = act<R>(h->in.red_a);
@@ -427,17 +432,17 @@ kfac_status_t layer_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, int l,
 
 template <class R>
 kfac_status_t grad_and_factors_t(kfac_pinn_handle* h, cudaStream_t s, const double* X_int, int N_int,
-                                 const double* X_bdy, int N_bdy) {
+                                 const double* X_bdy, int N_bdy, bool general = false) {
     const int L = h->cfg.L, d = h->dims[0];
     for (int l = 1; l <= L; l++) {
         kfac_status_t st;
         if (l == 1) {
             st = layer_grad_and_factors<R>(h, s, 1, InputRows{X_int, d, N_int, h->opQ},
-                                           InputRows{X_bdy, d, N_bdy, h->opQ}, N_int, N_bdy);
+                                           InputRows{X_bdy, d, N_bdy, h->opQ}, N_int, N_bdy, general);
         } else {
             int hin = h->dims[l - 1];
             st = layer_grad_and_factors<R>(h, s, l, ActRows<R>{act<R>(h->in.T[l - 2]), hin, N_int},
-                                           ActRows<R>{act<R>(h->bd.T[l - 2]), hin, N_bdy}, N_int, N_bdy);
+                                           ActRows<R>{act<R>(h->bd.T[l - 2]), hin, N_bdy}, N_int, N_bdy, general);
         }
         if (st != KFAC_OK) return st;
     }
@@ -591,6 +596,132 @@ __global__ void k_extract(const R* __restrict__ ZL, int N, int S, int d, const d
     if (lap) lap[n] = (double)ZL[(long long)(S - 1) * N + n];
 }
 
+// --------------------------------------------------------------------------
+// General interior residual (Sec. 3.3): with z_n = Z^{(L)}_n (S outputs, in the
+// column-block layout ZL[s * N + n]) and the coefficients b (M x S), W, its
+// Cholesky factor L_W (M x M) and Q (M x S x S) one after another in coef,
+//   r_{n,k} = b_k . z_n + 1/2 z_n^T Q_k z_n - f_{n,k},
+//   J_{n,k,s} = dr_{n,k} / dz_{n,s} = b[k,s] + sum_t Q[k,s,t] z_{n,t}.
+// --------------------------------------------------------------------------
+struct ResCoef {
+    const double* b;
+    const double* W;
+    const double* Lw;
+    const double* Q;     // nullptr: linear
+    int M, S;
+};
+
+// r (N x M) and the per-point r_n^T W r_n (rq, N); one thread per point.
+template <class R>
+__global__ void k_residual_general(const R* __restrict__ ZL, const double* __restrict__ f, ResCoef c, int N,
+                                   double* __restrict__ r, double* __restrict__ rq) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double rk[KFAC_MAX_RESIDUALS];
+    for (int k = 0; k < c.M; k++) {
+        double v = -f[(long long)n * c.M + k];
+        for (int s2 = 0; s2 < c.S; s2++) {
+            const double zs = (double)ZL[(long long)s2 * N + n];
+            v = fma(c.b[k * c.S + s2], zs, v);
+            if (c.Q) {
+                const double* q = c.Q + ((long long)k * c.S + s2) * c.S;
+                double qz = 0.0;
+                for (int t = 0; t < c.S; t++) qz = fma(q[t], (double)ZL[(long long)t * N + n], qz);
+                v = fma(0.5 * zs, qz, v);
+            }
+        }
+        rk[k] = v;
+        r[(long long)n * c.M + k] = v;
+    }
+    double acc = 0.0;
+    for (int k = 0; k < c.M; k++)
+        for (int j = 0; j < c.M; j++) acc = fma(rk[k] * c.W[k * c.M + j], rk[j], acc);
+    rq[n] = acc;
+}
+
+// Seed of one interior adjoint pass, Zbar^{(L)}_{n,s} = sum_k w_{n,k} J_{n,k,s}
+// with w_n = L_W[:, mode] (the mode-th term of the outer-product rewrite of
+// Lambda = W, Sec. 3.3) or, for mode = -1, w_n = W r_n (the loss gradient).
+template <class R>
+__global__ void k_seed_general(const R* __restrict__ ZL, const double* __restrict__ r, ResCoef c, int N, int mode,
+                               R* __restrict__ ZbL) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * c.S) return;
+    const int s2 = (int)(idx / N), n = (int)(idx % N);
+    double acc = 0.0;
+    for (int k = 0; k < c.M; k++) {
+        double w;
+        if (mode >= 0) {
+            w = c.Lw[k * c.M + mode];
+        } else {
+            w = 0.0;
+            for (int j = 0; j < c.M; j++) w = fma(c.W[k * c.M + j], r[(long long)n * c.M + j], w);
+        }
+        if (w == 0.0) continue;
+        double J = c.b[k * c.S + s2];
+        if (c.Q) {
+            const double* q = c.Q + ((long long)k * c.S + s2) * c.S;
+            for (int t = 0; t < c.S; t++) J = fma(q[t], (double)ZL[(long long)t * N + n], J);
+        }
+        acc = fma(w, J, acc);
+    }
+    ZbL[idx] = (R)acc;
+}
+
+ResCoef res_coef(const kfac_pinn_handle* h) {
+    ResCoef c;
+    c.M = h->res_M;
+    c.S = h->S;
+    c.b = h->res_coef;
+    c.W = c.b + (size_t)c.M * c.S;
+    c.Lw = c.W + (size_t)c.M * c.M;
+    c.Q = h->res_has_Q ? c.Lw + (size_t)c.M * c.M : nullptr;
+    return c;
+}
+
+template <class R>
+kfac_status_t residual_general_t(kfac_pinn_handle* h, cudaStream_t s, int N, const double* f) {
+    const int L = h->cfg.L;
+    k_residual_general<R><<<ceil_div_u(N, EW_THREADS), EW_THREADS, 0, s>>>(act<R>(h->in.Z[L - 1]), f, res_coef(h),
+                                                                           N, h->res_r, h->in.r);
+    KFAC_LAUNCH_CHECK(h);
+    return KFAC_OK;
+}
+
+// After both forward passes and the boundary adjoint: B_Omega of every layer
+// from M seeded interior adjoint passes (Eq. 10 in the outer-product form,
+// accumulated into the EMA), then the gradient pass and, with it, the
+// gradient, A_Omega, A_bdy and B_bdy of every layer.
+template <class R>
+kfac_status_t backward_and_factors_general_t(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                                             const double* X_int, int N_int, const double* X_bdy, int N_bdy) {
+    const int L = h->cfg.L, S = h->S, M = h->res_M;
+    const double beta = h->cfg.beta;
+    const ResCoef c = res_coef(h);
+    const unsigned sg = ceil_div_u((long long)N_int * S, EW_THREADS);
+    kfac_status_t st;
+    for (int m = 0; m < M; m++) {
+        k_seed_general<R><<<sg, EW_THREADS, 0, s>>>(act<R>(h->in.Z[L - 1]), h->res_r, c, N_int, m,
+                                                    act<R>(h->in.Zb[L - 1]));
+        KFAC_LAUNCH_CHECK(h);
+        if ((st = backward_t<R>(h, s, theta, h->in, N_int, S))) return st;
+        for (int l = 1; l <= L; l++) {
+            const int hout = h->dims[l];
+            WeightedRows<R> G{act<R>(h->in.Zb[l - 1]), hout, N_int, nullptr};
+            // first term: the EMA step; the others add (1 - beta) / N of their Gram
+            st = reduce_gemm(h, s, hout, hout, S * N_int, Transposed<WeightedRows<R>>{G}, G,
+                             m == 0 ? 1.0 / N_int : (1.0 - beta) / N_int, h->fac[KFAC_B_INT][l - 1], hout, 1,
+                             m == 0 ? 0 : 1, m == 0 ? 1 : 0, beta);
+            if (st) return st;
+        }
+    }
+    k_seed_general<R><<<sg, EW_THREADS, 0, s>>>(act<R>(h->in.Z[L - 1]), h->res_r, c, N_int, -1,
+                                                act<R>(h->in.Zb[L - 1]));
+    KFAC_LAUNCH_CHECK(h);
+    if ((st = backward_t<R>(h, s, theta, h->in, N_int, S))) return st;
+    return grad_and_factors_t<R>(h, s, X_int, N_int, X_bdy, N_bdy, true);
+}
+
 inline bool fp32_storage(const kfac_pinn_handle* h) { return h->cfg.precision == KFAC_FP32; }
 
 }  // namespace
@@ -622,7 +753,7 @@ kfac_status_t simt_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, const d
 }
 
 kfac_status_t fp64_loss(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N_bdy, double* loss_out) {
-    k_loss<<<1, 1024, 0, s>>>(h->in.r, N_int, h->bd.r, N_bdy, h->loss, h->status);
+    k_loss<<<1, 1024, 0, s>>>(h->in.r, N_int, h->bd.r, N_bdy, h->loss, h->status, h->res_M > 0);
     KFAC_LAUNCH_CHECK(h);
     if (loss_out && loss_out != h->loss)
         KFAC_CUDA_TRY(cudaMemcpyAsync(loss_out, h->loss, 3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -632,9 +763,20 @@ kfac_status_t fp64_loss(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N_bd
 // Loss of the residuals in h->in.r / h->bd.r written to dst (3 doubles); a
 // non-finite value is recorded, not latched (line-search trials may diverge).
 kfac_status_t fp64_loss_to(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N_bdy, double* dst) {
-    k_loss<<<1, 1024, 0, s>>>(h->in.r, N_int, h->bd.r, N_bdy, dst, nullptr);
+    k_loss<<<1, 1024, 0, s>>>(h->in.r, N_int, h->bd.r, N_bdy, dst, nullptr, h->res_M > 0);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
+}
+
+kfac_status_t simt_residual_general(kfac_pinn_handle* h, cudaStream_t s, int N, const double* f) {
+    return fp32_storage(h) ? residual_general_t<float>(h, s, N, f) : residual_general_t<double>(h, s, N, f);
+}
+
+kfac_status_t simt_backward_and_factors_general(kfac_pinn_handle* h, cudaStream_t s, const double* theta,
+                                                const double* X_int, int N_int, const double*, const double* X_bdy,
+                                                int N_bdy) {
+    return fp32_storage(h) ? backward_and_factors_general_t<float>(h, s, theta, X_int, N_int, X_bdy, N_bdy)
+                           : backward_and_factors_general_t<double>(h, s, theta, X_int, N_int, X_bdy, N_bdy);
 }
 
 kfac_status_t simt_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* theta, const double* X_int,
@@ -642,7 +784,9 @@ kfac_status_t simt_eval_loss(kfac_pinn_handle* h, cudaStream_t s, const double* 
                              double* dst) {
     kfac_status_t st;
     if ((st = simt_forward(h, s, theta, X_int, N_int, h->in, h->S))) return st;
-    if ((st = simt_residual_and_seed(h, s, h->in, N_int, h->S, f, true))) return st;
+    if (h->res_M > 0) st = simt_residual_general(h, s, N_int, f);
+    else st = simt_residual_and_seed(h, s, h->in, N_int, h->S, f, true);
+    if (st) return st;
     if ((st = simt_forward(h, s, theta, X_bdy, N_bdy, h->bd, 1))) return st;
     if ((st = simt_residual_and_seed(h, s, h->bd, N_bdy, 1, g, false))) return st;
     return fp64_loss_to(h, s, N_int, N_bdy, dst);

@@ -79,13 +79,15 @@ int main(void) {
     F(kfac_config_t, beta); F(kfac_config_t, lambda); F(kfac_config_t, damping_sqrt);
     F(kfac_config_t, factor_init_identity); F(kfac_config_t, lr); F(kfac_config_t, momentum);
     F(kfac_config_t, max_n_int); F(kfac_config_t, max_n_bdy); F(kfac_config_t, update);
-    F(kfac_config_t, eig_sm_budget); F(kfac_config_t, op_coef);
+    F(kfac_config_t, eig_sm_budget); F(kfac_config_t, op_coef); F(kfac_config_t, residual);
+    printf("kfac_residual_t %zu\n", sizeof(kfac_residual_t));
+    F(kfac_residual_t, M); F(kfac_residual_t, b); F(kfac_residual_t, Q); F(kfac_residual_t, W);
     printf("kfac_tune_entry_t %zu\n", sizeof(kfac_tune_entry_t));
     F(kfac_tune_entry_t, kind); F(kfac_tune_entry_t, P); F(kfac_tune_entry_t, Q); F(kfac_tune_entry_t, K);
     F(kfac_tune_entry_t, tiles); F(kfac_tune_entry_t, sym); F(kfac_tune_entry_t, split);
     F(kfac_tune_entry_t, chunk); F(kfac_tune_entry_t, model_chunk); F(kfac_tune_entry_t, us);
     F(kfac_tune_entry_t, model_us);
-    V(KFAC_MAX_LAYERS); V(KFAC_TUNE_CAP);
+    V(KFAC_MAX_LAYERS); V(KFAC_TUNE_CAP); V(KFAC_MAX_RESIDUALS);
     V(KFAC_OK); V(KFAC_BAD_ARG); V(KFAC_NOT_PD); V(KFAC_NONFINITE); V(KFAC_TIMEOUT); V(KFAC_OOM);
     V(KFAC_CUDA_ERROR); V(KFAC_NOT_READY);
     V(KFAC_FP64); V(KFAC_MIXED_BF16); V(KFAC_MIXED_SPLIT); V(KFAC_FP32); V(KFAC_EXPAND); V(KFAC_REDUCE);
@@ -114,7 +116,8 @@ def test_ctypes_mirrors_match_the_header(tmp_path):
     for line in filter(None, out):
         key, *vals = line.split()
         c[key] = tuple(int(v) for v in vals)
-    for T, S in (("kfac_config_t", _lib.KfacConfig), ("kfac_tune_entry_t", _lib.KfacTuneEntry)):
+    for T, S in (("kfac_config_t", _lib.KfacConfig), ("kfac_tune_entry_t", _lib.KfacTuneEntry),
+                 ("kfac_residual_t", _lib.KfacResidual)):
         assert c[T] == (C.sizeof(S),), T
         assert [f for f, _ in S._fields_] == [k.split(".")[1].replace("lambda", "lambda_")
                                                for k in c if k.startswith(T + ".")], T
@@ -123,6 +126,7 @@ def test_ctypes_mirrors_match_the_header(tmp_path):
             assert c[f"{T}.{f.rstrip('_')}"] == (desc.offset, desc.size), (T, f)
     assert c["KFAC_MAX_LAYERS"] == (_lib.KFAC_MAX_LAYERS,)
     assert c["KFAC_TUNE_CAP"] == (_lib.KFAC_TUNE_CAP,)
+    assert c["KFAC_MAX_RESIDUALS"] == (_lib.KFAC_MAX_RESIDUALS,)
     for code, name in _lib.STATUS.items():
         assert c[name] == (code,), name
     for name, v in api.PRECISIONS.items():

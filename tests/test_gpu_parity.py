@@ -3,7 +3,9 @@
 Tolerances are normwise relative errors per result.  FP64 path: 1e-10 on the
 Taylor pass, loss, gradient and factors; the preconditioned direction and the
 update go through an inverse whose condition number is up to ‖A‖/λ per
-factor, so they are held to 1e-9 (derivation in the design notes).
+factor (the damped factors have eigenvalues down to λ), which multiplies the
+~1e-14 rounding of the factors and gradient by up to 1e4-1e5 at λ = 1e-3, so
+they are held to 1e-9.
 """
 import numpy as np
 import pytest

@@ -109,3 +109,42 @@ def operator_value(theta: np.ndarray, d: int, widths, X: np.ndarray, coef: np.nd
         H = torch.autograd.functional.hessian(net, torch.as_tensor(x, dtype=torch.float64))
         out.append(float((C * H).sum()))
     return np.array(out)
+
+
+def taylor_outputs_fn(d, widths, op="laplace"):
+    """z(theta_t, x) = (u, du/dx_1, .., du/dx_d, second-order column) by autograd:
+    the Laplacian, or the spatial Laplacian (coordinates 1..d-1) for the heat
+    operator."""
+    def z(theta_t, x):
+        net = mlp_from_flat(theta_t, d, widths)
+        xg = x.clone().requires_grad_(True)
+        u = net(xg)
+        (g,) = torch.autograd.grad(u, xg, create_graph=True)
+        lap = 0.0
+        for i in (range(1, d) if op == "heat" else range(d)):
+            (gi,) = torch.autograd.grad(g[i], xg, create_graph=True)
+            lap = lap + gi[i]
+        return torch.cat([u.reshape(1), g, torch.as_tensor(lap, dtype=torch.float64).reshape(1)])
+    return z
+
+
+def quadratic_residual_rows(theta, d, widths, X, F, b, Q=None, op="laplace"):
+    """r_{n,k} = b_k . z_n + 1/2 z_n^T Q_k z_n - F_{n,k} and their Jacobians
+    J_theta r_{n,k} (N x M x D) by autograd."""
+    zf = taylor_outputs_fn(d, widths, op)
+    bt = torch.as_tensor(b, dtype=torch.float64)
+    Qt = None if Q is None else torch.as_tensor(Q, dtype=torch.float64)
+    rs, Js = [], []
+    for x, f in zip(X, F):
+        th = torch.as_tensor(theta, dtype=torch.float64).clone().requires_grad_(True)
+        z = zf(th, torch.as_tensor(x, dtype=torch.float64))
+        r = bt @ z - torch.as_tensor(f, dtype=torch.float64)
+        if Qt is not None:
+            r = r + 0.5 * torch.einsum("s,kst,t->k", z, Qt, z)
+        rows = []
+        for k in range(r.shape[0]):
+            (jr,) = torch.autograd.grad(r[k], th, retain_graph=True)
+            rows.append(jr.numpy())
+        rs.append(r.detach().numpy())
+        Js.append(np.stack(rows))
+    return np.stack(rs), np.stack(Js)
