@@ -807,6 +807,40 @@ def run_secondary():
     return out
 
 
+def run_profile_step(args):
+    """The benchmark's step for profilers: the warm-up steps (autotuner, graph
+    capture), then one replayed step inside the NVTX range "kfac_step" (for
+    `ncu --nvtx --nvtx-include kfac_step/`) and nothing else.  Prints the
+    step's device time and the library's launch count of that step."""
+    import torch
+    from paper_2405_15603_gb300 import build as _build
+    _build.build()
+    from paper_2405_15603_gb300.api import KfacPinn
+    dev = torch.device("cuda:0")
+    prob, widths = WORKLOAD.prob, WORKLOAD.widths
+    batches = [tuple(torch.tensor(a, device=dev) for a in b) for b in make_batches(args.warmup + 1, 0)]
+    opt = KfacPinn(prob.d, widths, device=str(dev), precision=args.precision, max_n_int=WORKLOAD.n_int,
+                   max_n_bdy=WORKLOAD.n_bdy, **HYPER)
+    opt.set_graph(True)
+    opt.set_autotune(True)
+    theta = torch.tensor(si.xavier_theta(prob.d, widths, 0), device=dev)
+    for k in range(args.warmup):
+        opt.step(theta, *batches[k])
+    torch.cuda.synchronize()
+    n0 = opt.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("kfac_step")
+    e0.record()
+    opt.step(theta, *batches[args.warmup])
+    e1.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    out = {"precision": args.precision, "workload": WORKLOAD_NAME, "ms": round(e0.elapsed_time(e1), 3),
+           "launches": int(opt.launch_count() - n0), "status": opt.sync_status()}
+    opt.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -824,6 +858,8 @@ def main():
                     help="forward vs autodiff Laplacian time and memory (App. C.4) instead of the step bench")
     ap.add_argument("--equal-l2", type=int, default=0, metavar="STEPS",
                     help="L2 error after STEPS steps, mixed vs FP64 (about 17 s per FP64 step)")
+    ap.add_argument("--profile", action="store_true",
+                    help="warm-up steps, then one step inside the NVTX range kfac_step (for ncu)")
     ap.add_argument("--c2", action="store_true",
                     help="5-d Poisson, 1000 KFAC steps per precision, L2 on 10k held-out points")
     ap.add_argument("--no-secondary", action="store_true",
@@ -851,6 +887,9 @@ def main():
         return
     if args.c2:
         print(json.dumps(run_c2()), flush=True)
+        return
+    if args.profile:
+        print(json.dumps(run_profile_step(args)), flush=True)
         return
     if args.steps is None:
         args.steps = 2 if args.precision == "fp64" else 30

@@ -32,7 +32,15 @@ namespace {
 
 constexpr int NB = 64;        // Cholesky / TRSM block
 constexpr int CB_MAX = 32;    // widest TRSM column strip
-constexpr int STRIP_NARROW_FROM = 640;   // factors this large get 16-column strips (TRSM, back-transform)
+// Column-strip widths of the triangular solves and the back-transformation:
+// one CTA per strip, sequential down the strip, so the strips are the
+// parallelism.  Narrower strips for larger factors keep the jobs' FP64 work
+// about equal (n^2 x width) and make the largest factors' strips outnumber the
+// SMs several times over (a 769 factor: 97 strips of 8 columns), so that the
+// last wave of equal jobs leaves few SMs idle.
+constexpr int STRIP_NARROW_FROM = 640;   // factors this large get 8-column strips
+constexpr int STRIP_MEDIUM_FROM = 320;   // these 16, the smaller ones 32
+inline int strip_width(int n) { return n >= STRIP_NARROW_FROM ? 8 : (n >= STRIP_MEDIUM_FROM ? 16 : 32); }
 constexpr int KFAC_MAX_WIDTH_PLUS_ONE = 1024;   // widths <= 1023 and d + 1 <= 1024 (create checks)
 constexpr int MAXP = 2 * KFAC_MAX_LAYERS;
 constexpr double DEPS = 2.220446049250313e-16;
@@ -429,7 +437,8 @@ __global__ void __launch_bounds__(256, 2) k_trsm(Prob* pr, const TrsmJob* jobs, 
     const Prob p = pr[jb.prob];
     if (jb.c0 >= p.n) return;
     const bool failed = fail[jb.prob] != 0;
-    if (jb.cb == 16) trsm_strip<16>(p, jb.c0, mode, failed, sm);
+    if (jb.cb == 8) trsm_strip<8>(p, jb.c0, mode, failed, sm);
+    else if (jb.cb == 16) trsm_strip<16>(p, jb.c0, mode, failed, sm);
     else trsm_strip<32>(p, jb.c0, mode, failed, sm);
 }
 
@@ -1600,10 +1609,11 @@ __global__ void k_dc_copy(const Copy* cp, int n_cp) {
 inline size_t bt_smem_bytes(int n, int W) {
     return sizeof(double) * ((size_t)n * W + 2 * (size_t)n + 9 * (size_t)W);
 }
-// the most any job can ask for: 16 columns of the largest factor, or 32
-// columns of a factor just below the width threshold
+// the most any job can ask for: the widest strip of each width class at the
+// largest factor of that class
 inline size_t bt_smem_max() {
-    return std::max(bt_smem_bytes(KFAC_MAX_WIDTH_PLUS_ONE, 16), bt_smem_bytes(STRIP_NARROW_FROM - 1, 32));
+    return std::max(bt_smem_bytes(KFAC_MAX_WIDTH_PLUS_ONE, 8),
+                    std::max(bt_smem_bytes(STRIP_NARROW_FROM - 1, 16), bt_smem_bytes(STRIP_MEDIUM_FROM - 1, 32)));
 }
 
 // U <- H_0 H_1 .. H_{n-3} U on a strip of W columns held in shared memory.
@@ -1648,7 +1658,9 @@ __device__ void bt_strip(const Prob& p, int c0, double* sm) {
         if (tk == 0.0) continue;                  // uniform
         double dot = 0.0;
         for (int i = rg; i < m; i += RG) dot = fma(v[i], Us[(b + i) * W + cl], dot);
-        if (W == 16) dot += __shfl_xor_sync(0xffffffffu, dot, 16);
+        // lanes l, l + W, .. of a warp hold the same column: fold them
+        if (W <= 16) dot += __shfl_xor_sync(0xffffffffu, dot, 16);
+        if (W <= 8) dot += __shfl_xor_sync(0xffffffffu, dot, 8);
         if (lane < W) part[warp * W + lane] = dot;
         __syncthreads();
         if (warp == 0 && lane < W) {
@@ -1673,7 +1685,8 @@ __global__ void __launch_bounds__(256) k_backtransform(Prob* pr, const TrsmJob* 
     const TrsmJob jb = jobs[blockIdx.x];
     const Prob p = pr[jb.prob];
     if (fail[jb.prob] || jb.c0 >= p.n) return;
-    if (jb.cb == 16) bt_strip<16>(p, jb.c0, bt_sm);
+    if (jb.cb == 8) bt_strip<8>(p, jb.c0, bt_sm);
+    else if (jb.cb == 16) bt_strip<16>(p, jb.c0, bt_sm);
     else bt_strip<32>(p, jb.c0, bt_sm);
 }
 
@@ -1806,7 +1819,7 @@ static kfac_status_t group_alloc(kfac_pinn_handle* h, EigState* es, const std::v
         std::vector<TrsmJob> jobs;
         for (int i = 0; i < es->np; i++) {
             const int n = es->host[i].n;
-            const int cb = n >= STRIP_NARROW_FROM ? 16 : 32;
+            const int cb = strip_width(n);
             for (int c0 = 0; c0 < n; c0 += cb) jobs.push_back(TrsmJob{i, c0, cb});
         }
         std::stable_sort(jobs.begin(), jobs.end(), [&](const TrsmJob& x, const TrsmJob& y) {
