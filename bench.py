@@ -601,9 +601,12 @@ def run_e10(reps=5):
 # ---------------------------------------------------------------------------
 def run_many(steps=10, warmup=3, n_streams=16, count=64, precision="mixed_split"):
     """Aggregate KFAC steps/s of `count` uneven Poisson PINNs stepped as one
-    batch (reduced precision, worker streams, CUDA graph replay), beside the
-    same problems stepped one after another: the same precision on one stream,
-    and the plain FP64 path (one step each, timed after one warm-up step)."""
+    batch in the grouped form (every kernel launched once for all problems
+    over member tables, one batched eigensolve, CUDA graph replay), beside the
+    same batch in the stream form (each problem's own launches on worker
+    streams) and the same problems stepped one after another: the same
+    precision on one stream, and the plain FP64 path (one step each, timed
+    after one warm-up step)."""
     import torch
     from paper_2405_15603_gb300 import build as _build
     _build.build()
@@ -620,21 +623,22 @@ def run_many(steps=10, warmup=3, n_streams=16, count=64, precision="mixed_split"
             for i, m in enumerate(members)]
     cols = [[b[j] for b in bufs] for j in range(4)]
     losses = [torch.zeros(3, dtype=torch.float64, device=dev) for _ in members]
-    batch = KfacBatch(opts, n_streams=n_streams)
-    for _ in range(warmup):                  # eager, capture, replay
-        batch.step(thetas, *cols, losses)
-    torch.cuda.synchronize()
-    l0 = sum(o.launch_count() for o in opts)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        batch.step(thetas, *cols, losses)
-    e1.record()
-    torch.cuda.synchronize()
-    ms_batch = e0.elapsed_time(e1) / steps
-    launches = (sum(o.launch_count() for o in opts) - l0) // steps
+    timed = {}
+    for form in ("streams", "grouped"):
+        batch = KfacBatch(opts, n_streams=n_streams, grouped=(form == "grouped"))
+        for _ in range(warmup):                  # eager, capture, replay
+            batch.step(thetas, *cols, losses)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            batch.step(thetas, *cols, losses)
+        e1.record()
+        torch.cuda.synchronize()
+        timed[form] = (e0.elapsed_time(e1) / steps, batch.launches_per_step())
+        batch.close()
+    ms_batch, launches = timed["grouped"]
     status = sorted({o.sync_status() for o in opts})
-    batch.close()
     # the same problems one after another, mixed precision, one stream
     e0.record()
     for i, o in enumerate(opts):
@@ -667,6 +671,10 @@ def run_many(steps=10, warmup=3, n_streams=16, count=64, precision="mixed_split"
                        "widths": "uniform {32..512}, 2-3 hidden layers", "n_int": "uniform [500, 4000]",
                        "n_bdy": "n_int/4", "n_streams": n_streams, **kw, "graph": True},
             "gpu_launches_per_batch_step": int(launches), "status": status,
+            "form": "grouped: one launch per kernel for all problems (member tables), one batched eigensolve",
+            "streams_form": {"value": round(count / (timed["streams"][0] / 1e3), 3), "unit": "steps/s",
+                             "ms_per_batch_step": round(timed["streams"][0], 4),
+                             "gpu_launches_per_batch_step": int(timed["streams"][1])},
             "mixed_sequential": {"value": round(count / (ms_seq_mixed / 1e3), 3), "unit": "steps/s"},
             "fp64_sequential": {"value": round(count / (ms_fp64 / 1e3), 3), "unit": "steps/s"},
             "speedup_vs_fp64_sequential": round(ms_fp64 / ms_batch, 2)}

@@ -488,6 +488,31 @@ kfac_status_t kfac_pinn_batch_step(kfac_batch_t b, void* stream, double* const* 
                                    const double* const* X_bdy, const int* N_bdy, const double* const* g,
                                    double* const* loss, int use_graph);
 
+/* Grouped form of a batch (no counterpart in the paper: a serving pattern for many
+ * small PINNs).  With enable = 1 the next captured batch step (a call with
+ * use_graph = 1 from the second on) records every handle's step launch by
+ * launch instead of running it, merges the launches of the same kernel
+ * across handles into one grouped launch (each handle's launch keeps its own
+ * grid and arguments, read from a member table in device memory: a block of
+ * the grouped launch computes what the same block of the handle's own launch
+ * computes) and solves the generalized eigenproblems of every factor pair of
+ * every handle (Sec. 3.4) as one batched eigensolve.  The number of launches
+ * of a batch step is then about that of one handle's step, whatever the
+ * number of handles.  Results equal those of kfac_pinn_step on each handle.
+ *   - Every handle must use a tensor-core precision (KFAC_MIXED_BF16 or
+ *     KFAC_MIXED_SPLIT): KFAC_BAD_ARG otherwise.  enable = 0 returns to the
+ *     stream form.  Switching drops the captured graph.
+ *   - Eager calls (the first one, use_graph = 0, timing enabled) run the
+ *     stream form.
+ *   - A handle's own graph mode (kfac_pinn_set_graph) does not apply to its
+ *     steps inside the batch.
+ *
+ * kfac_pinn_batch_launches writes the number of kernel launches of one
+ * replayed batch step (the captured graph's kernels) to *per_step;
+ * KFAC_NOT_READY before a graph has been captured. */
+kfac_status_t kfac_pinn_batch_set_grouped(kfac_batch_t b, int enable);
+kfac_status_t kfac_pinn_batch_launches(kfac_batch_t b, long long* per_step);
+
 /* Allocation-free forward Laplacian.  The paper has no counterpart: this is
  * a service for callers that cannot allocate device memory while they run
  * (code inside another runtime's memory pool or fixed device-memory budget,

@@ -22,7 +22,8 @@ EXPORTS = [
     "kfac_pinn_batch_step", "kfac_pinn_last_cuda_error", "kfac_pinn_last_cuda_error_string",
     "kfac_pinn_set_store_forward",
     "kfac_pinn_set_graph", "kfac_pinn_set_autotune", "kfac_pinn_get_tuning", "kfac_pinn_set_tuning",
-    "kfac_pinn_check_wait_timeout", "kfac_pinn_inject_alloc_failure",
+    "kfac_pinn_check_wait_timeout", "kfac_pinn_inject_alloc_failure", "kfac_pinn_batch_set_grouped",
+    "kfac_pinn_batch_launches",
 ]
 
 KFAC_TUNE_CAP = 128
@@ -115,6 +116,8 @@ def load() -> C.CDLL:
         "kfac_pinn_batch_create": (st, [P, I, I, C.POINTER(C.c_void_p)]),
         "kfac_pinn_batch_destroy": (st, [P]),
         "kfac_pinn_batch_step": (st, [P, P, P, P, P, P, P, P, P, P, I]),
+        "kfac_pinn_batch_set_grouped": (st, [P, I]),
+        "kfac_pinn_batch_launches": (st, [P, C.POINTER(C.c_longlong)]),
         "kfac_pinn_sync_status": (st, [H, C.POINTER(C.c_int)]),
         "kfac_pinn_launch_count": (C.c_int64, [H]),
         "kfac_pinn_timing_enable": (st, [H, I]),

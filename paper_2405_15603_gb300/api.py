@@ -323,15 +323,28 @@ class ForwardLaplacian(torch.autograd.Function):
 
 
 class KfacBatch:
-    """Many KfacPinn problems stepped together (worker streams, CUDA graph replay)."""
+    """Many KfacPinn problems stepped together, replayed as one CUDA graph:
+    their steps on worker streams, or (grouped=True) every kernel launched
+    once for all problems and one batched eigensolve."""
 
-    def __init__(self, problems: Sequence[KfacPinn], n_streams: int = 8):
+    def __init__(self, problems: Sequence[KfacPinn], n_streams: int = 8, grouped: bool = False):
         self.lib = _lib.load()
         self.problems = list(problems)
         hs = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
         self.b = C.c_void_p()
         _check("kfac_pinn_batch_create", self.lib.kfac_pinn_batch_create(hs, len(self.problems), n_streams,
                                                                          C.byref(self.b)))
+        if grouped:
+            _check("kfac_pinn_batch_set_grouped", self.lib.kfac_pinn_batch_set_grouped(self.b, 1))
+
+    def launches_per_step(self):
+        """Kernel launches of one replayed batch step (None before the graph exists)."""
+        n = C.c_longlong()
+        st = self.lib.kfac_pinn_batch_launches(self.b, C.byref(n))
+        if st == 7:      # KFAC_NOT_READY
+            return None
+        _check("kfac_pinn_batch_launches", st)
+        return int(n.value)
 
     def close(self):
         if self.b:

@@ -42,7 +42,6 @@ constexpr int STRIP_NARROW_FROM = 640;   // factors this large get 8-column stri
 constexpr int STRIP_MEDIUM_FROM = 320;   // these 16, the smaller ones 32
 inline int strip_width(int n) { return n >= STRIP_NARROW_FROM ? 8 : (n >= STRIP_MEDIUM_FROM ? 16 : 32); }
 constexpr int KFAC_MAX_WIDTH_PLUS_ONE = 1024;   // widths <= 1023 and d + 1 <= 1024 (create checks)
-constexpr int MAXP = 2 * KFAC_MAX_LAYERS;
 constexpr double DEPS = 2.220446049250313e-16;
 
 struct Prob {
@@ -59,6 +58,8 @@ struct Prob {
     int *mk, *mnrot, *mflip;               // per merge (indexed by block start a)
     double* mrh;
     int final_buf;                         // 0: Qa, 1: Qb holds the D&C result
+    double eps;                            // damping added to both factors' diagonals
+    int* status;                           // status word of the problem's handle
 };
 
 struct Merge {
@@ -102,7 +103,7 @@ struct Level {
 
 struct EigState {
     int np;
-    Prob host[MAXP];
+    std::vector<Prob> host;
     Prob* dev;                  // device copy of host[]
     double* ws;                 // all double workspaces
     int* iws;                   // all int workspaces
@@ -178,14 +179,14 @@ __device__ double block_reduce_max(double v, double* sh) {
 // --------------------------------------------------------------------------
 // 0. damped copies
 // --------------------------------------------------------------------------
-__global__ void k_damp(Prob* pr, double eps, int* fail) {
+__global__ void k_damp(Prob* pr, int* fail) {
     const Prob p = pr[blockIdx.y];
     const int n = p.n;
     if (threadIdx.x == 0 && blockIdx.x == 0) fail[blockIdx.y] = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)n * n;
          i += (long long)gridDim.x * blockDim.x) {
         int r = (int)(i / n), c = (int)(i % n);
-        double e = (r == c) ? eps : 0.0;
+        double e = (r == c) ? p.eps : 0.0;
         p.L[i] = p.P[i] + e;
         p.M[i] = p.Q[i] + e;
     }
@@ -194,7 +195,7 @@ __global__ void k_damp(Prob* pr, double eps, int* fail) {
 // --------------------------------------------------------------------------
 // 1. blocked Cholesky (lower), block k0
 // --------------------------------------------------------------------------
-__global__ void k_chol_diag(Prob* pr, int k0, int* fail, int* status) {
+__global__ void k_chol_diag(Prob* pr, int k0, int* fail) {
     __shared__ double A[NB][NB + 1];
     __shared__ int bad;
     const Prob p = pr[blockIdx.x];
@@ -228,7 +229,7 @@ __global__ void k_chol_diag(Prob* pr, int k0, int* fail, int* status) {
     if (bad) {
         if (threadIdx.x == 0) {
             fail[blockIdx.x] = 1;
-            latch_status(status, KFAC_NOT_PD);
+            latch_status(p.status, KFAC_NOT_PD);
         }
         return;
     }
@@ -562,8 +563,7 @@ __device__ bool wait_row(const unsigned* ready, unsigned k, int* abort_flag) {
 // rank-2 update of owned rows; the owner of row k+1 updates it first and
 // publishes it through a counter, which replaces a second barrier.
 __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, const int* cta_rank,
-                                                 const int* group, unsigned* bars, int* abort_flag, int* status,
-                                                 int* fail) {
+                                                 const int* group, unsigned* bars, int* abort_flag, int* fail) {
     __shared__ double v[1024];
     __shared__ double w[1024];
     __shared__ double sh[40];
@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, 
     // every update must be in place before the diagonal is read
     if (alive && !group_barrier(bar, g, abort_flag)) alive = false;
     if (!alive) {
-        if (threadIdx.x == 0) latch_status(status, KFAC_TIMEOUT);
+        if (threadIdx.x == 0) latch_status(p.status, KFAC_TIMEOUT);
         return;
     }
     if (rank == 0) {
@@ -728,7 +728,7 @@ __host__ __device__ inline long long trc_off(int t, int c, int cl) {
 // cluster at the same column (they all see the same pushed value) and marks
 // the problem failed.
 __global__ void __launch_bounds__(TRC_THREADS, 1) k_chol_cluster(Prob* pr, const int* clu_prob, int lds, int nmax,
-                                                                 int* fail, int* status) {
+                                                                 int* fail) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ double trc_sm[];
@@ -806,7 +806,7 @@ __global__ void __launch_bounds__(TRC_THREADS, 1) k_chol_cluster(Prob* pr, const
     if (!ok) {
         if (c == 0 && tid == 0) {
             fail[pi] = 1;
-            latch_status(status, KFAC_NOT_PD);
+            latch_status(p.status, KFAC_NOT_PD);
         }
         return;
     }
@@ -1690,11 +1690,11 @@ __global__ void __launch_bounds__(256) k_backtransform(Prob* pr, const TrsmJob* 
     else bt_strip<32>(p, jb.c0, bt_sm);
 }
 
-__global__ void k_write_w(Prob* pr, int* fail, int* status) {
+__global__ void k_write_w(Prob* pr, int* fail) {
     const Prob p = pr[blockIdx.x];
     for (int i = threadIdx.x; i < p.n; i += blockDim.x) {
         double v = fail[blockIdx.x] ? 0.0 : p.D[i];
-        if (!isfinite(v)) latch_status(status, KFAC_NONFINITE);
+        if (!isfinite(v)) latch_status(p.status, KFAC_NONFINITE);
         p.w[i] = v;
     }
 }
@@ -1720,29 +1720,33 @@ int ceil_log2(int n) {
 
 static int pair_n(const kfac_pinn_handle* h, int l, int which) { return which == 0 ? h->dims[l - 1] + 1 : h->dims[l]; }
 
-// One group of factor pairs (layer, 0: A / 1: B) solved by one sequence of
-// batched kernels.
+static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es);
+
+// One group of factor pairs (layer, 0: A / 1: B) of one handle solved by one
+// sequence of batched kernels: the problems' workspaces, then the schedule.
 static kfac_status_t group_alloc(kfac_pinn_handle* h, EigState* es, const std::vector<std::pair<int, int>>& pairs) {
     es->np = 0;
-    es->nmax = 0;
     size_t dtot = 0, itot = 0;
     std::vector<int> ns;
     for (const auto& pw : pairs) ns.push_back(pair_n(h, pw.first, pw.second));
     for (int n : ns) {
         dtot += 7 * (size_t)n * n + (size_t)n * NB + 20 * (size_t)n;
         itot += 12 * (size_t)n;
-        es->nmax = std::max(es->nmax, n);
     }
     kfac_status_t st;
     if ((st = dal(&es->ws, dtot))) return st;
     if ((st = dal(&es->iws, itot))) return st;
     double* dp = es->ws;
     int* ip = es->iws;
+    es->host.assign(pairs.size(), Prob());
+    const double eps = h->cfg.damping_sqrt ? sqrt(h->cfg.lambda) : h->cfg.lambda;
     for (const auto& pw : pairs) {
         {
             const int l = pw.first, which = pw.second;
             Prob& p = es->host[es->np++];
             memset(&p, 0, sizeof(p));
+            p.eps = eps;
+            p.status = h->status;
             const int n = which == 0 ? h->dims[l - 1] + 1 : h->dims[l];
             p.n = n;
             p.P = h->fac[which == 0 ? KFAC_A_INT : KFAC_B_INT][l - 1];
@@ -1770,14 +1774,27 @@ static kfac_status_t group_alloc(kfac_pinn_handle* h, EigState* es, const std::v
             p.final_buf = ceil_log2(n) & 1;
         }
     }
+    return group_schedule(h, es);
+}
+
+// The device copy of the problem list es->host and every schedule of the
+// kernel sequence (cooperative groups, triangular-solve jobs, clusters, merge
+// levels).  h0 supplies the device and the SM budget.
+static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es) {
+    kfac_pinn_handle* h = h0;
+    kfac_status_t st;
+    es->np = (int)es->host.size();
+    es->nmax = 0;
+    for (const Prob& p : es->host) es->nmax = std::max(es->nmax, p.n);
     if ((st = dal(&es->dev, (size_t)es->np))) return st;
-    if (cudaMemcpy(es->dev, es->host, sizeof(Prob) * es->np, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(es->dev, es->host.data(), sizeof(Prob) * es->np, cudaMemcpyHostToDevice) != cudaSuccess)
         return KFAC_CUDA_ERROR;
     if ((st = dal(&es->fail, (size_t)es->np))) return st;
     if ((st = dal(&es->bar, 3 * (size_t)es->np))) return st;
     if ((st = dal(&es->abort_flag, 1))) return st;
     cudaMemset(es->fail, 0, sizeof(int) * es->np);
 
+    bool coop_fits = false;
     // cooperative tridiagonalisation: CTAs per problem ~ n^3, two CTAs per SM
     // (one CTA's synchronisation stalls overlap the other's FP64 work)
     {
@@ -1811,7 +1828,8 @@ static kfac_status_t group_alloc(kfac_pinn_handle* h, EigState* es, const std::v
         cudaMemcpy(es->cta_prob, cp.data(), sizeof(int) * cp.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(es->cta_rank, cr.data(), sizeof(int) * cr.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(es->group, g.data(), sizeof(int) * g.size(), cudaMemcpyHostToDevice);
-        if (per_sm * h->sm_count < es->n_cta) return KFAC_BAD_ARG;
+        // (needed only when the cluster kernel below cannot take the problems)
+        coop_fits = per_sm * h->sm_count >= es->n_cta;
     }
 
     // triangular-solve jobs of about equal work, largest first
@@ -1885,6 +1903,7 @@ static kfac_status_t group_alloc(kfac_pinn_handle* h, EigState* es, const std::v
             cudaGetLastError();   // a refused configuration only selects the cooperative kernel
         }
     }
+    if (es->trc_cl == 0 && !coop_fits) return KFAC_BAD_ARG;
 
     // divide-and-conquer schedules, one per merge level
     for (int s = 1; s < es->nmax; s *= 2) {
@@ -1963,6 +1982,8 @@ static kfac_status_t group_alloc(kfac_pinn_handle* h, EigState* es, const std::v
     return cudaGetLastError() == cudaSuccess ? KFAC_OK : KFAC_CUDA_ERROR;
 }
 
+static kfac_status_t eigall_free_streams(EigAll* ea);
+
 static void group_free(EigState* es) {
     if (!es) return;
     cudaFree(es->ws);
@@ -1987,11 +2008,10 @@ static void group_free(EigState* es) {
 static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s) {
     const int np = es->np;
     Prob* pr = es->dev;
-    const double eps = h->cfg.damping_sqrt ? sqrt(h->cfg.lambda) : h->cfg.lambda;
     const int nmax = es->nmax;
     const int nblk = (nmax + NB - 1) / NB;
 
-    k_damp<<<dim3(64, np), 256, 0, s>>>(pr, eps, es->fail);
+    k_damp<<<dim3(64, np), 256, 0, s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
     // 1. Cholesky: one cluster per problem, or the blocked kernels
     if (es->trc_cl > 0) {
@@ -2008,12 +2028,12 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
         lc.attrs = &attr;
         lc.numAttrs = 1;
         KFAC_CUDA_TRY(cudaLaunchKernelEx(&lc, k_chol_cluster, (Prob*)pr, (const int*)es->clu_prob, es->trc_lds, nmax,
-                                         (int*)es->fail, (int*)h->status));
+                                         (int*)es->fail));
         h->launches++;
     }
     for (int kb = 0; es->trc_cl == 0 && kb < nblk; kb++) {
         const int k0 = kb * NB;
-        k_chol_diag<<<np, 256, 0, s>>>(pr, k0, es->fail, h->status);
+        k_chol_diag<<<np, 256, 0, s>>>(pr, k0, es->fail);
         KFAC_LAUNCH_CHECK(h);
         const int rows = nmax - k0 - NB;
         if (rows <= 0) continue;
@@ -2066,7 +2086,7 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
         lc.numAttrs = 1;
         KFAC_CUDA_TRY(cudaLaunchKernelEx(&lc, k_tridiag, (Prob*)pr, (const int*)es->cta_prob,
                                          (const int*)es->cta_rank, (const int*)es->group, (unsigned*)es->bar,
-                                         (int*)es->abort_flag, (int*)h->status, (int*)es->fail));
+                                         (int*)es->abort_flag, (int*)es->fail));
         h->launches++;
     }
     // 4. divide and conquer
@@ -2104,7 +2124,7 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
     KFAC_LAUNCH_CHECK(h);
     k_trsm<<<es->n_trsm_jobs, 256, smem_trsm, s>>>(pr, (const TrsmJob*)es->trsm_jobs, 2, es->fail);
     KFAC_LAUNCH_CHECK(h);
-    k_write_w<<<np, 256, 0, s>>>(pr, es->fail, h->status);
+    k_write_w<<<np, 256, 0, s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }
@@ -2168,17 +2188,23 @@ kfac_status_t eig_alloc(kfac_pinn_handle* h) {
 void eig_free(kfac_pinn_handle* h) {
     EigAll* ea = EA(h);
     if (!ea) return;
-    if (ea->side) cudaStreamSynchronize(ea->side);
+    eigall_free_streams(ea);
     for (int i = 0; i < 2; i++) group_free(ea->g[i]);
-    if (ea->side) cudaStreamDestroy(ea->side);
-    if (ea->fork) cudaEventDestroy(ea->fork);
-    if (ea->join) cudaEventDestroy(ea->join);
     delete ea;
     h->eig = nullptr;
 }
 
-kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
-    EigAll* ea = EA(h);
+static kfac_status_t eigall_free_streams(EigAll* ea) {
+    if (ea->side) cudaStreamSynchronize(ea->side);
+    if (ea->side) cudaStreamDestroy(ea->side);
+    if (ea->fork) cudaEventDestroy(ea->fork);
+    if (ea->join) cudaEventDestroy(ea->join);
+    ea->side = nullptr;
+    ea->fork = ea->join = nullptr;
+    return KFAC_OK;
+}
+
+static kfac_status_t eigall_run(kfac_pinn_handle* h, EigAll* ea, cudaStream_t s) {
     if (ea->ng == 1) return group_run(h, ea->g[0], s);
     if (ea->g[0]->trc_cl == 0 || ea->g[1]->trc_cl == 0) {
         // a cooperative tridiagonalisation needs all its CTAs resident at
@@ -2194,4 +2220,53 @@ kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) {
     if (st == KFAC_OK) st = group_run(h, ea->g[0], s);
     KFAC_CUDA_TRY(cudaStreamWaitEvent(s, ea->join, 0));
     return st;
+}
+
+kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) { return eigall_run(h, EA(h), s); }
+
+// The eigensolves of many handles as one pair of groups over the problems'
+// own workspaces: every factor pair of every handle, the pairs of at least 3/4
+// of the largest size in the first group, the rest in the second.
+kfac_status_t eig_batch_alloc(kfac_pinn_handle* const* hs, int count, void** out) {
+    *out = nullptr;
+    if (count < 1) return KFAC_BAD_ARG;
+    std::vector<Prob> all;
+    for (int i = 0; i < count; i++) {
+        EigAll* ea = EA(hs[i]);
+        if (!ea) return KFAC_BAD_ARG;
+        for (int g = 0; g < ea->ng; g++) all.insert(all.end(), ea->g[g]->host.begin(), ea->g[g]->host.end());
+    }
+    int nmax = 0;
+    for (const Prob& p : all) nmax = std::max(nmax, p.n);
+    std::vector<Prob> big, rest;
+    for (const Prob& p : all) (4 * p.n >= 3 * nmax ? big : rest).push_back(p);
+    EigAll* ea = new EigAll();
+    memset(ea, 0, sizeof(*ea));
+    *out = ea;
+    kfac_status_t st;
+    for (std::vector<Prob>* list : {&big, &rest}) {
+        if (list->empty()) continue;
+        EigState* es = new EigState();
+        ea->g[ea->ng++] = es;
+        es->host = *list;
+        if ((st = group_schedule(hs[0], es))) return st;
+    }
+    if (ea->ng == 2 &&
+        (cudaStreamCreateWithFlags(&ea->side, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&ea->fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&ea->join, cudaEventDisableTiming) != cudaSuccess))
+        return KFAC_CUDA_ERROR;
+    return KFAC_OK;
+}
+
+kfac_status_t eig_batch_run(kfac_pinn_handle* h0, void* eb, cudaStream_t s) {
+    return eigall_run(h0, (EigAll*)eb, s);
+}
+
+void eig_batch_free(void* eb) {
+    EigAll* ea = (EigAll*)eb;
+    if (!ea) return;
+    eigall_free_streams(ea);
+    for (int i = 0; i < 2; i++) group_free(ea->g[i]);
+    delete ea;
 }

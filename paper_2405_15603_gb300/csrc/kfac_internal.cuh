@@ -235,6 +235,11 @@ size_t linalg_auto_part_elems();
 kfac_status_t eig_alloc(kfac_pinn_handle* h);
 void eig_free(kfac_pinn_handle* h);
 kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s);
+// One eigensolve over every factor pair of `count` handles (the grouped batch
+// step): problems on the handles' own workspaces, schedules of their own.
+kfac_status_t eig_batch_alloc(kfac_pinn_handle* const* hs, int count, void** out);
+kfac_status_t eig_batch_run(kfac_pinn_handle* h0, void* eb, cudaStream_t s);
+void eig_batch_free(void* eb);
 // Self-check of the eigensolver's bounded group barrier (kfac_pinn_check_wait_timeout).
 kfac_status_t eig_check_wait(kfac_pinn_handle* h, cudaStream_t s, uint64_t limit_ns);
 kfac_status_t linalg_invert(kfac_pinn_handle* h, cudaStream_t s);

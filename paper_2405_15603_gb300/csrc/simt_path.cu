@@ -10,6 +10,7 @@
 // shared columns of one (point, feature) pair.
 #include "kfac_internal.cuh"
 #include "gemm_simt.cuh"
+#include "group.cuh"
 
 using namespace kfac;
 
@@ -201,29 +202,32 @@ __global__ void k_seed(R* __restrict__ ZbL, int N, int S, int interior, double c
 
 // loss[1] = sum r^2 / (2N), loss[2] = sum rb^2 / (2Nb), loss[0] = loss[1] + loss[2].
 // r_sq: r already holds the per-point r_n^T W r_n of a general residual.
-__global__ void k_loss(const double* __restrict__ r, int N, const double* __restrict__ rb, int Nb,
-                       double* __restrict__ loss, int* status, int r_sq) {
-    __shared__ double sh[2][32];
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) a = r_sq ? a + r[i] : fma(r[i], r[i], a);
-    for (int i = threadIdx.x; i < Nb; i += blockDim.x) b = fma(rb[i], rb[i], b);
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
+struct k_loss {
+    static constexpr int THREADS = 1024;
+    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ r, int N, const double* __restrict__ rb,
+                               int Nb, double* __restrict__ loss, int* status, int r_sq) {
+        __shared__ double sh[2][32];
+        double a = 0.0, b = 0.0;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) a = r_sq ? a + r[i] : fma(r[i], r[i], a);
+        for (int i = threadIdx.x; i < Nb; i += blockDim.x) b = fma(rb[i], rb[i], b);
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        int w = threadIdx.x / 32, l = threadIdx.x % 32;
+        if (l == 0) { sh[0][w] = a; sh[1][w] = b; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double A = 0.0, B = 0.0;
+            for (int i = 0; i < (int)(blockDim.x / 32); i++) { A += sh[0][i]; B += sh[1][i]; }
+            double li = A / (2.0 * N), lb = B / (2.0 * Nb);
+            loss[0] = li + lb;
+            loss[1] = li;
+            loss[2] = lb;
+            if (status && !isfinite(li + lb)) latch_status(status, KFAC_NONFINITE);
+        }
     }
-    int w = threadIdx.x / 32, l = threadIdx.x % 32;
-    if (l == 0) { sh[0][w] = a; sh[1][w] = b; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double A = 0.0, B = 0.0;
-        for (int i = 0; i < (int)(blockDim.x / 32); i++) { A += sh[0][i]; B += sh[1][i]; }
-        double li = A / (2.0 * N), lb = B / (2.0 * Nb);
-        loss[0] = li + lb;
-        loss[1] = li;
-        loss[2] = lb;
-        if (status && !isfinite(li + lb)) latch_status(status, KFAC_NONFINITE);
-    }
-}
+};
 
 // out[p*osp + q*osq] = (accumulate ? out : 0) + scale * sum_z part[z][p][q],
 // or the EMA  out = beta * out + (1 - beta) * scale * sum_z part  when ema.
@@ -753,18 +757,15 @@ kfac_status_t simt_grad_and_factors(kfac_pinn_handle* h, cudaStream_t s, const d
 }
 
 kfac_status_t fp64_loss(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N_bdy, double* loss_out) {
-    k_loss<<<1, 1024, 0, s>>>(h->in.r, N_int, h->bd.r, N_bdy, h->loss, h->status, h->res_M > 0);
-    KFAC_LAUNCH_CHECK(h);
-    if (loss_out && loss_out != h->loss)
-        KFAC_CUDA_TRY(cudaMemcpyAsync(loss_out, h->loss, 3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    KFAC_TRY(KL<k_loss>(h, s, 1, 0, h->in.r, N_int, h->bd.r, N_bdy, h->loss, h->status, h->res_M > 0));
+    if (loss_out && loss_out != h->loss) return group_copy(h, s, loss_out, h->loss, 3 * sizeof(double));
     return KFAC_OK;
 }
 
 // Loss of the residuals in h->in.r / h->bd.r written to dst (3 doubles); a
 // non-finite value is recorded, not latched (line-search trials may diverge).
 kfac_status_t fp64_loss_to(kfac_pinn_handle* h, cudaStream_t s, int N_int, int N_bdy, double* dst) {
-    k_loss<<<1, 1024, 0, s>>>(h->in.r, N_int, h->bd.r, N_bdy, dst, nullptr, h->res_M > 0);
-    KFAC_LAUNCH_CHECK(h);
+    KFAC_TRY(KL<k_loss>(h, s, 1, 0, h->in.r, N_int, h->bd.r, N_bdy, dst, nullptr, h->res_M > 0));
     return KFAC_OK;
 }
 

@@ -55,6 +55,12 @@ KFAC_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = WAIT
 }
 
 // -------------------------------------------------------------------- TMA
+// A tensor map in global memory, written before the launch, made visible to
+// the tensor-map proxy of this thread.
+KFAC_DEV void tmap_acquire(const CUtensorMap* m) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(m))
+                 : "memory");
+}
 KFAC_DEV void prefetch_tmap(const CUtensorMap* m) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
 }

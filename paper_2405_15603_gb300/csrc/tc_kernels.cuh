@@ -25,6 +25,7 @@
 //               <dr_n/dW~_l, V~> = sum_s g_{n,s}^T V~ T^_{n,s} (Sec. 3.2)
 #pragma once
 #include "tc_common.cuh"
+#include "group.cuh"
 
 namespace tck {
 
@@ -112,16 +113,16 @@ KFAC_DEV int n_terms(int s, int S, int split_time, int split_all) {
 KFAC_DEV int lo_block(int s, int S) { return s == 0 ? 0 : (s == S - 1 ? 1 : 2); }
 
 template <int MODE>
-KFAC_DEV void tile_range(const Args& a, int& s_begin, int& s_end) {
+KFAC_DEV void tile_range(const Args& a, uint3 vb, int& s_begin, int& s_end) {
     if (MODE == FWD_VALUE || MODE == BWD_VALUE || MODE == GRAM) { s_begin = 0; s_end = 1; return; }
     if (MODE == BWD_LAP) { s_begin = a.S - 1; s_end = a.S; return; }
     if (MODE == JDOT) {       // every Taylor column, value row block included
-        s_begin = blockIdx.z * a.chunk_len;
+        s_begin = vb.z * a.chunk_len;
         s_end = min(a.S, s_begin + a.chunk_len);
         return;
     }
     int last = (MODE == FWD_TANLAP) ? a.S : a.S - 1;   // FWD covers the Laplacian tile too
-    s_begin = 1 + blockIdx.z * a.chunk_len;
+    s_begin = 1 + vb.z * a.chunk_len;
     s_end = min(last, s_begin + a.chunk_len);
 }
 
@@ -172,8 +173,10 @@ KFAC_DEV void load16_f32(const float* src, float* v) {
 // ---------------------------------------------------------------------------
 // SPLIT (split-BF16 on every row, Args::split_all) is a template parameter so
 // that the plain instantiations keep their register budget.
+// The engine's work for one CTA: vb / vg stand for blockIdx / gridDim of the
+// launch the CTA belongs to (its own, or its member's in a grouped launch).
 template <int MODE, bool SPLIT>
-__global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constant__ Args a) {
+KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
     using C = Cfg<MODE, SPLIT>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -187,9 +190,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
     // ---- tile geometry ----------------------------------------------------
     int p0, j0, s_begin, s_end, k_begin = 0, k_steps;
     if (MODE == GRAM) {
-        // blockIdx.x enumerates the (p, q) output tiles, symmetric ones only
-        // when they touch the upper triangle; blockIdx.y is the row chunk.
-        int t = blockIdx.x, pb = 0, qb = 0, cnt = 0;
+        // vb.x enumerates the (p, q) output tiles, symmetric ones only
+        // when they touch the upper triangle; vb.y is the row chunk.
+        int t = vb.x, pb = 0, qb = 0, cnt = 0;
         int p_tiles = (a.P + BM - 1) / BM;
         for (pb = 0; pb < p_tiles; pb++) {
             int q_first = a.sym ? (pb * BM) / C::BN : 0;
@@ -199,15 +202,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
         }
         p0 = pb * BM;
         j0 = qb * C::BN;
-        k_begin = blockIdx.y * a.row_chunk;
+        k_begin = vb.y * a.row_chunk;
         int k_end = min(a.rows, k_begin + a.row_chunk);
         k_steps = (k_end - k_begin + BK - 1) / BK;
         s_begin = 0; s_end = 1;
     } else {
-        j0 = blockIdx.x * C::BN;
-        p0 = blockIdx.y * BM;
+        j0 = vb.x * C::BN;
+        p0 = vb.y * BM;
         k_steps = a.k_steps;                              // 64-wide K blocks (one-slot modes)
-        tile_range<MODE>(a, s_begin, s_end);
+        tile_range<MODE>(a, vb, s_begin, s_end);
     }
     const int n_tiles = max(0, s_end - s_begin);
 
@@ -424,7 +427,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
                 if (MODE == GRAM) {
                     const int p = p0 + r;
                     if (p < a.P) {
-                        float* dst = a.part + ((long long)blockIdx.y * a.P + p) * a.Q + j;
+                        float* dst = a.part + ((long long)vb.y * a.P + p) * a.Q + j;
                         // float4 stores need 16-byte alignment: Q % 4 == 0
                         if (j + 16 <= a.Q && (a.Q & 3) == 0) store16_f32(dst, v);
                         else for (int i = 0; i < 16 && j + i < a.Q; i++) dst[i] = v[i];
@@ -603,12 +606,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
             for (int c = 0; c < CW; c += 16) {
                 const int j = j0 + c0 + c;
                 if (j < a.hp_out)
-                    store16_f32(a.part + ((long long)blockIdx.z * a.N_pad + n) * hp + j, st2 + c);
+                    store16_f32(a.part + ((long long)vb.z * a.N_pad + n) * hp + j, st2 + c);
             }
         }
         if (MODE == JDOT && !abort_flag) {
             // one partial per (column chunk, feature tile, column half) and point
-            const long long slot = ((long long)blockIdx.z * gridDim.x + blockIdx.x) * 2 + half;
+            const long long slot = ((long long)vb.z * vg.x + vb.x) * 2 + half;
             a.part[slot * a.N_pad + n] = jacc;
         }
     }
@@ -620,6 +623,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constan
         tc::tc_fence_after();
         tc::tmem_dealloc(tbase, C::TMEM_COLS);
     }
+}
+
+template <int MODE, bool SPLIT>
+__global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constant__ Args a) {
+    engine_body<MODE, SPLIT>(a, blockIdx, make_uint3(gridDim.x, gridDim.y, gridDim.z));
+}
+
+// Grouped launch (group.cuh): every member's Args, tensor maps included, in a
+// table in global memory.  The producer thread acquires the maps for the
+// tensor-map proxy before its first TMA through them.
+template <int MODE, bool SPLIT>
+__global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine_group(const __grid_constant__ GroupTab t) {
+    const int m = group_member(t, blockIdx.x);
+    const uint3 g = t.grid[m];
+    const Args& a = *reinterpret_cast<const Args*>(t.packs + (size_t)m * t.stride);
+    if (threadIdx.x == 0) {
+        tc::tmap_acquire(&a.a0);
+        tc::tmap_acquire(&a.a1);
+        tc::tmap_acquire(&a.b0);
+        tc::tmap_acquire(&a.b1);
+    }
+    engine_body<MODE, SPLIT>(a, group_block(blockIdx.x - t.start[m], g), g);
 }
 
 }  // namespace tck

@@ -130,43 +130,55 @@ kfac_status_t dal(T** p, size_t n) {
 
 // theta (FP64, column-stacked W~_l) -> BF16 hi/lo row-major W (hout_p x hin_p),
 // BF16 transposed Wt (hin_p x hout_p), FP32 bias; zero padding.
-__global__ void k_convert_weights(const double* __restrict__ W, int hout, int hin, int hout_p, int hin_p,
-                                  bf16* Whi, bf16* Wlo, bf16* Wt, bf16* Wt_lo, float* bias) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)hout_p * hin_p) return;
-    int i = (int)(idx / hin_p), k = (int)(idx % hin_p);
-    // one FP64 operation per element (the conversion); the split is done in FP32
-    float v = (i < hout && k < hin) ? (float)W[i + (long long)hout * k] : 0.f;
-    bf16 hi = __float2bfloat16_rn(v);
-    bf16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-    Whi[idx] = hi;
-    Wlo[idx] = lo;
-    Wt[(long long)k * hout_p + i] = hi;
-    if (Wt_lo) Wt_lo[(long long)k * hout_p + i] = lo;
-    if (k == 0) bias[i] = (i < hout) ? (float)W[i + (long long)hout * hin] : 0.f;
-}
+struct k_convert_weights {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ W, int hout, int hin, int hout_p,
+                               int hin_p, bf16* Whi, bf16* Wlo, bf16* Wt, bf16* Wt_lo, float* bias) {
+        long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
+        if (idx >= (long long)hout_p * hin_p) return;
+        int i = (int)(idx / hin_p), k = (int)(idx % hin_p);
+        // one FP64 operation per element (the conversion); the split is done in FP32
+        float v = (i < hout && k < hin) ? (float)W[i + (long long)hout * k] : 0.f;
+        bf16 hi = __float2bfloat16_rn(v);
+        bf16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        Whi[idx] = hi;
+        Wlo[idx] = lo;
+        Wt[(long long)k * hout_p + i] = hi;
+        if (Wt_lo) Wt_lo[(long long)k * hout_p + i] = lo;
+        if (k == 0) bias[i] = (i < hout) ? (float)W[i + (long long)hout * hin] : 0.f;
+    }
+};
 
-__global__ void k_convert_last(const double* __restrict__ W, int hin, int hin_p, float* wL) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k > hin_p) return;
-    if (k < hin_p) wL[k] = (k < hin) ? (float)W[k] : 0.f;
-    else wL[k] = (float)W[hin];     // bias at index hin_p
-}
+struct k_convert_last {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ W, int hin, int hin_p, float* wL) {
+        int k = vb.x * blockDim.x + threadIdx.x;
+        if (k > hin_p) return;
+        if (k < hin_p) wL[k] = (k < hin) ? (float)W[k] : 0.f;
+        else wL[k] = (float)W[hin];     // bias at index hin_p
+    }
+};
 
 // First-layer weights in FP32, input-major with the features contiguous.
-__global__ void k_convert_first(const double* __restrict__ W, int h, int hp, int d, float* W1f) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)(d + 1) * hp) return;
-    int k = (int)(idx / hp), j = (int)(idx % hp);
-    W1f[idx] = (j < h) ? (float)W[j + (long long)h * k] : 0.f;
-}
+struct k_convert_first {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ W, int h, int hp, int d, float* W1f) {
+        long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
+        if (idx >= (long long)(d + 1) * hp) return;
+        int k = (int)(idx / hp), j = (int)(idx % hp);
+        W1f[idx] = (j < h) ? (float)W[j + (long long)h * k] : 0.f;
+    }
+};
 
 // Points in FP32 (rows >= N zero).
-__global__ void k_points_f32(const double* __restrict__ X, int N, int N_pad, int d, float* Xf) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)N_pad * d) return;
-    Xf[idx] = (idx < (long long)N * d) ? (float)X[idx] : 0.f;
-}
+struct k_points_f32 {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ X, int N, int N_pad, int d, float* Xf) {
+        long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
+        if (idx >= (long long)N_pad * d) return;
+        Xf[idx] = (idx < (long long)N * d) ? (float)X[idx] : 0.f;
+    }
+};
 
 KFAC_DEV void store4_bf16(bf16* dst, const float* v) {
     __align__(8) __nv_bfloat162 t[2] = {__floats2bfloat162_rn(v[0], v[1]), __floats2bfloat162_rn(v[2], v[3])};
@@ -178,102 +190,109 @@ KFAC_DEV void store4_bf16(bf16* dst, const float* v) {
 // and its Laplacian column is 0; tanh rule of Eq. 6 with channel weights chw
 // (App. C.3).  FP32 arithmetic (the outputs are split-BF16, about 16 bits, at
 // most); one thread per point and 4 consecutive features.
-__global__ void k_layer1(const float* __restrict__ W1f, const float* __restrict__ Wt, const float* __restrict__ Xf,
-                         int N, int N_pad, int d, int h, int hp, int S, const float* __restrict__ chw,
-                         int split_time, int split_all, bf16* T_hi, bf16* T_lo, float* A0, float* AD, float* SSQ) {
-    // low halves: block 0 value, 1 Laplacian, 2 time (heat); every block s at
-    // its own row block when split_all
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int hq = hp / 4;
-    if (idx >= (long long)N_pad * hq) return;
-    const int n = (int)(idx / hq), j = 4 * (int)(idx % hq);
-    const long long o = (long long)n * hp + j;
-    const long long blk = (long long)N_pad * hp;
-    float a0[4], y0[4], s1[4], hi[4], lo[4];
-    bool live[4];
-    {
-        float4 b = *reinterpret_cast<const float4*>(W1f + (long long)d * hp + j);
-        a0[0] = b.x; a0[1] = b.y; a0[2] = b.z; a0[3] = b.w;
-    }
-    for (int k = 0; k < d; k++) {
-        const float x = Xf[(long long)n * d + k];
-        float4 w = *reinterpret_cast<const float4*>(W1f + (long long)k * hp + j);
-        a0[0] = fmaf(w.x, x, a0[0]); a0[1] = fmaf(w.y, x, a0[1]);
-        a0[2] = fmaf(w.z, x, a0[2]); a0[3] = fmaf(w.w, x, a0[3]);
-    }
-    const bool row_live = n < N;
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-        live[q] = row_live && (j + q < h);
-        a0[q] = live[q] ? a0[q] : 0.f;
-        y0[q] = live[q] ? tanhf(a0[q]) : 0.f;
-        s1[q] = live[q] ? 1.f - y0[q] * y0[q] : 0.f;
-        __nv_bfloat16 hb = __float2bfloat16_rn(y0[q]);
-        hi[q] = __bfloat162float(hb);
-        lo[q] = y0[q] - hi[q];
-    }
-    store4_bf16(T_hi + o, hi);
-    store4_bf16(T_lo + o, lo);
-    float ssq[4] = {0.f, 0.f, 0.f, 0.f};
-    if (S == 1) {
-#pragma unroll
-        for (int q = 0; q < 4; q++) live[q] = false;   // no tangents: SSQ = 0
-    }
-    if (S > 1) {
-        for (int i = 0; i < d; i++) {
-            float4 w4 = *reinterpret_cast<const float4*>(Wt + (long long)i * hp + j);
-            const float w[4] = {w4.x, w4.y, w4.z, w4.w};
-            float t[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) t[q] = s1[q] * w[q];
-            store4_bf16(T_hi + (1 + i) * blk + o, t);
-            if (split_all || (i == 0 && split_time)) {     // heat: the time tangent keeps its low half
-                float tl[4];
-#pragma unroll
-                for (int q = 0; q < 4; q++) tl[q] = t[q] - __bfloat162float(__float2bfloat16_rn(t[q]));
-                store4_bf16(T_lo + (split_all ? (1 + i) : 2) * blk + o, tl);
-            }
-            const float wc = chw[i];
-#pragma unroll
-            for (int q = 0; q < 4; q++) ssq[q] = fmaf(wc * w[q], w[q], ssq[q]);
+struct k_layer1 {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ W1f, const float* __restrict__ Wt,
+                               const float* __restrict__ Xf, int N, int N_pad, int d, int h, int hp, int S,
+                               const float* __restrict__ chw, int split_time, int split_all, bf16* T_hi, bf16* T_lo,
+                               float* A0, float* AD, float* SSQ) {
+        // low halves: block 0 value, 1 Laplacian, 2 time (heat); every block s at
+        // its own row block when split_all
+        long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
+        const int hq = hp / 4;
+        if (idx >= (long long)N_pad * hq) return;
+        const int n = (int)(idx / hq), j = 4 * (int)(idx % hq);
+        const long long o = (long long)n * hp + j;
+        const long long blk = (long long)N_pad * hp;
+        float a0[4], y0[4], s1[4], hi[4], lo[4];
+        bool live[4];
+        {
+            float4 b = *reinterpret_cast<const float4*>(W1f + (long long)d * hp + j);
+            a0[0] = b.x; a0[1] = b.y; a0[2] = b.z; a0[3] = b.w;
         }
-        float dh[4], dl[4];
-#pragma unroll
+        for (int k = 0; k < d; k++) {
+            const float x = Xf[(long long)n * d + k];
+            float4 w = *reinterpret_cast<const float4*>(W1f + (long long)k * hp + j);
+            a0[0] = fmaf(w.x, x, a0[0]); a0[1] = fmaf(w.y, x, a0[1]);
+            a0[2] = fmaf(w.z, x, a0[2]); a0[3] = fmaf(w.w, x, a0[3]);
+        }
+        const bool row_live = n < N;
+    #pragma unroll
         for (int q = 0; q < 4; q++) {
-            if (!live[q]) ssq[q] = 0.f;
-            const float yD = -2.f * y0[q] * s1[q] * ssq[q];
-            __nv_bfloat16 hb = __float2bfloat16_rn(yD);
-            dh[q] = __bfloat162float(hb);
-            dl[q] = yD - dh[q];
+            live[q] = row_live && (j + q < h);
+            a0[q] = live[q] ? a0[q] : 0.f;
+            y0[q] = live[q] ? tanhf(a0[q]) : 0.f;
+            s1[q] = live[q] ? 1.f - y0[q] * y0[q] : 0.f;
+            __nv_bfloat16 hb = __float2bfloat16_rn(y0[q]);
+            hi[q] = __bfloat162float(hb);
+            lo[q] = y0[q] - hi[q];
         }
-        store4_bf16(T_hi + (S - 1) * blk + o, dh);
-        store4_bf16(T_lo + (split_all ? S - 1 : 1) * blk + o, dl);
+        store4_bf16(T_hi + o, hi);
+        store4_bf16(T_lo + o, lo);
+        float ssq[4] = {0.f, 0.f, 0.f, 0.f};
+        if (S == 1) {
+    #pragma unroll
+            for (int q = 0; q < 4; q++) live[q] = false;   // no tangents: SSQ = 0
+        }
+        if (S > 1) {
+            for (int i = 0; i < d; i++) {
+                float4 w4 = *reinterpret_cast<const float4*>(Wt + (long long)i * hp + j);
+                const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+                float t[4];
+    #pragma unroll
+                for (int q = 0; q < 4; q++) t[q] = s1[q] * w[q];
+                store4_bf16(T_hi + (1 + i) * blk + o, t);
+                if (split_all || (i == 0 && split_time)) {     // heat: the time tangent keeps its low half
+                    float tl[4];
+    #pragma unroll
+                    for (int q = 0; q < 4; q++) tl[q] = t[q] - __bfloat162float(__float2bfloat16_rn(t[q]));
+                    store4_bf16(T_lo + (split_all ? (1 + i) : 2) * blk + o, tl);
+                }
+                const float wc = chw[i];
+    #pragma unroll
+                for (int q = 0; q < 4; q++) ssq[q] = fmaf(wc * w[q], w[q], ssq[q]);
+            }
+            float dh[4], dl[4];
+    #pragma unroll
+            for (int q = 0; q < 4; q++) {
+                if (!live[q]) ssq[q] = 0.f;
+                const float yD = -2.f * y0[q] * s1[q] * ssq[q];
+                __nv_bfloat16 hb = __float2bfloat16_rn(yD);
+                dh[q] = __bfloat162float(hb);
+                dl[q] = yD - dh[q];
+            }
+            store4_bf16(T_hi + (S - 1) * blk + o, dh);
+            store4_bf16(T_lo + (split_all ? S - 1 : 1) * blk + o, dl);
+        }
+        *reinterpret_cast<float4*>(A0 + o) = make_float4(a0[0], a0[1], a0[2], a0[3]);
+        *reinterpret_cast<float4*>(AD + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(SSQ + o) = make_float4(ssq[0], ssq[1], ssq[2], ssq[3]);
     }
-    *reinterpret_cast<float4*>(A0 + o) = make_float4(a0[0], a0[1], a0[2], a0[3]);
-    *reinterpret_cast<float4*>(AD + o) = make_float4(0.f, 0.f, 0.f, 0.f);
-    *reinterpret_cast<float4*>(SSQ + o) = make_float4(ssq[0], ssq[1], ssq[2], ssq[3]);
-}
+};
 
 // Laplacian row of a hidden layer once all tangent chunks are done:
 // y_D = s1 a_D + s2 sum_{i in C} a_i^2  (Eq. 6).
-__global__ void k_lap_finish(const float* __restrict__ part, int n_chunks, int N, int N_pad, int h, int hp, int S,
-                             const float* __restrict__ A0, const float* __restrict__ AD, float* SSQ, bf16* T_hi,
-                             bf16* T_lo, int split_all) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long blk = (long long)N_pad * hp;
-    if (idx >= blk) return;
-    int n = (int)(idx / hp), j = (int)(idx % hp);
-    float ssq = 0.f;
-    for (int z = 0; z < n_chunks; z++) ssq += part[z * blk + idx];
-    bool live = (n < N) && (j < h);
-    float y0 = tanhf(A0[idx]);
-    float s1 = 1.f - y0 * y0, s2 = -2.f * y0 * s1;
-    float yD = live ? fmaf(s1, AD[idx], s2 * ssq) : 0.f;
-    SSQ[idx] = live ? ssq : 0.f;
-    bf16 hi = __float2bfloat16_rn(yD);
-    T_hi[(S - 1) * blk + idx] = hi;
-    T_lo[(split_all ? S - 1 : 1) * blk + idx] = __float2bfloat16_rn(yD - __bfloat162float(hi));
-}
+struct k_lap_finish {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ part, int n_chunks, int N, int N_pad,
+                               int h, int hp, int S, const float* __restrict__ A0, const float* __restrict__ AD,
+                               float* SSQ, bf16* T_hi, bf16* T_lo, int split_all) {
+        long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
+        const long long blk = (long long)N_pad * hp;
+        if (idx >= blk) return;
+        int n = (int)(idx / hp), j = (int)(idx % hp);
+        float ssq = 0.f;
+        for (int z = 0; z < n_chunks; z++) ssq += part[z * blk + idx];
+        bool live = (n < N) && (j < h);
+        float y0 = tanhf(A0[idx]);
+        float s1 = 1.f - y0 * y0, s2 = -2.f * y0 * s1;
+        float yD = live ? fmaf(s1, AD[idx], s2 * ssq) : 0.f;
+        SSQ[idx] = live ? ssq : 0.f;
+        bf16 hi = __float2bfloat16_rn(yD);
+        T_hi[(S - 1) * blk + idx] = hi;
+        T_lo[(split_all ? S - 1 : 1) * blk + idx] = __float2bfloat16_rn(yD - __bfloat162float(hi));
+    }
+};
 
 // Last linear layer (h_L = 1): z[row] = sum_j T[row][j] w[j] (+ bias on value
 // rows) for the selected Taylor blocks: all of them (nsel == 0) or the nsel
@@ -285,130 +304,144 @@ struct BlockSel {
     int split_time;
     int split_all;      // every block has its low half at its own row block
 };
-__global__ void k_last_fwd(const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo, const float* __restrict__ wL,
-                           int N_pad, int S, int hp, BlockSel sel, float* zl) {
-    long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-    int lane = threadIdx.x % 32;
-    long long nrows = (long long)(sel.nsel ? sel.nsel : S) * N_pad;
-    if (wid >= nrows) return;
-    int bi = (int)(wid / N_pad), n = (int)(wid % N_pad);
-    int s = sel.nsel ? sel.b[bi] : bi;
-    wid = (long long)s * N_pad + n;
-    const bf16* row = T_hi + wid * hp;
-    const bf16* lrow = nullptr;
-    if (sel.split_all) lrow = T_lo + ((long long)s * N_pad + n) * hp;
-    else if (s == 0) lrow = T_lo + (long long)n * hp;
-    else if (s == S - 1) lrow = T_lo + ((long long)N_pad + n) * hp;
-    else if (s == 1 && sel.split_time) lrow = T_lo + (2LL * N_pad + n) * hp;
-    float acc = 0.f;
-    for (int j = lane * 2; j < hp; j += 64) {
-        float2 t = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(row + j));
-        if (lrow) {
-            float2 u = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(lrow + j));
-            t.x += u.x;
-            t.y += u.y;
+struct k_last_fwd {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo,
+                               const float* __restrict__ wL, int N_pad, int S, int hp, BlockSel sel, float* zl) {
+        long long wid = ((long long)vb.x * blockDim.x + threadIdx.x) / 32;
+        int lane = threadIdx.x % 32;
+        long long nrows = (long long)(sel.nsel ? sel.nsel : S) * N_pad;
+        if (wid >= nrows) return;
+        int bi = (int)(wid / N_pad), n = (int)(wid % N_pad);
+        int s = sel.nsel ? sel.b[bi] : bi;
+        wid = (long long)s * N_pad + n;
+        const bf16* row = T_hi + wid * hp;
+        const bf16* lrow = nullptr;
+        if (sel.split_all) lrow = T_lo + ((long long)s * N_pad + n) * hp;
+        else if (s == 0) lrow = T_lo + (long long)n * hp;
+        else if (s == S - 1) lrow = T_lo + ((long long)N_pad + n) * hp;
+        else if (s == 1 && sel.split_time) lrow = T_lo + (2LL * N_pad + n) * hp;
+        float acc = 0.f;
+        for (int j = lane * 2; j < hp; j += 64) {
+            float2 t = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(row + j));
+            if (lrow) {
+                float2 u = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(lrow + j));
+                t.x += u.x;
+                t.y += u.y;
+            }
+            acc = fmaf(t.x, wL[j], acc);
+            acc = fmaf(t.y, wL[j + 1], acc);
         }
-        acc = fmaf(t.x, wL[j], acc);
-        acc = fmaf(t.y, wL[j + 1], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) zl[wid] = acc + (s == 0 ? wL[hp] : 0.f);
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) zl[wid] = acc + (s == 0 ? wL[hp] : 0.f);
-}
+};
 
 // Residuals (Eq. 1): interior r = cT z_t + cD z_D - f, boundary r = u - g.
-__global__ void k_residual_mx(const float* __restrict__ zl, const double* __restrict__ target, double* r, int N,
-                              int N_pad, int S, int interior, double cT, double cD) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    double v;
-    if (!interior) {
-        v = (double)zl[n] - target[n];
-    } else {
-        v = cD * (double)zl[(long long)(S - 1) * N_pad + n];
-        if (cT != 0.0) v += cT * (double)zl[N_pad + n];
-        v -= target[n];
+struct k_residual_mx {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ zl, const double* __restrict__ target,
+                               double* r, int N, int N_pad, int S, int interior, double cT, double cD) {
+        int n = vb.x * blockDim.x + threadIdx.x;
+        if (n >= N) return;
+        double v;
+        if (!interior) {
+            v = (double)zl[n] - target[n];
+        } else {
+            v = cD * (double)zl[(long long)(S - 1) * N_pad + n];
+            if (cT != 0.0) v += cT * (double)zl[N_pad + n];
+            v -= target[n];
+        }
+        r[n] = v;
     }
-    r[n] = v;
-}
+};
 
 // u, grad u (rotated back to the coordinate axes when the tangent directions
 // are the columns of Q) and the second-order column.
-__global__ void k_extract_mx(const float* __restrict__ zl, int N, int N_pad, int S, int d, const float* __restrict__ Qf,
-                             double* u, double* grad, double* lap) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    if (u) u[n] = zl[n];
-    if (grad) {
-        for (int i = 0; i < d; i++) {
-            float g;
-            if (!Qf) {
-                g = zl[(long long)(1 + i) * N_pad + n];
-            } else {
-                g = 0.f;
-                for (int m = 0; m < d; m++) g = fmaf(Qf[(long long)i * d + m], zl[(long long)(1 + m) * N_pad + n], g);
+struct k_extract_mx {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ zl, int N, int N_pad, int S, int d,
+                               const float* __restrict__ Qf, double* u, double* grad, double* lap) {
+        int n = vb.x * blockDim.x + threadIdx.x;
+        if (n >= N) return;
+        if (u) u[n] = zl[n];
+        if (grad) {
+            for (int i = 0; i < d; i++) {
+                float g;
+                if (!Qf) {
+                    g = zl[(long long)(1 + i) * N_pad + n];
+                } else {
+                    g = 0.f;
+                    for (int m = 0; m < d; m++)
+                        g = fmaf(Qf[(long long)i * d + m], zl[(long long)(1 + m) * N_pad + n], g);
+                }
+                grad[(long long)n * d + i] = g;
             }
-            grad[(long long)n * d + i] = g;
         }
+        if (lap) lap[n] = zl[(long long)(S - 1) * N_pad + n];
     }
-    if (lap) lap[n] = zl[(long long)(S - 1) * N_pad + n];
-}
+};
 
 // Adjoint through the last linear layer and the tanh of layer L-1: the
 // incoming T^bar_s = c_s w (h_L = 1, seed c = dr/dZ^{(L)}), then the tanh
 // adjoint (abar_i = s1 ybar_i - 4 y0 y_i ybar_D, ...).  Writes g = Zbar and
 // r_n g for every Taylor row.
-__global__ void k_last_bwd(const float* __restrict__ wL, const bf16* __restrict__ T_hi, const float* __restrict__ A0,
-                           const float* __restrict__ AD, const float* __restrict__ SSQ, const double* __restrict__ r,
-                           int N, int N_pad, int h, int hp, int S, const float* __restrict__ chw, float cT,
-                           float cD, const float* __restrict__ seed, bf16* Zb, bf16* Gr,
-                           const bf16* __restrict__ T_lo, bf16* Zb_lo, bf16* Gr_lo) {
-    // T_lo, Zb_lo, Gr_lo: split-BF16 everywhere (all three, or none)
-    // seed == nullptr: the residual's constant seed c (cT, cD; 1 on the value of a
-    // boundary pass); else c_{n,s} = seed[s * N_pad + n] (reverse mode of the forward
-    // Laplacian).  r == nullptr: Gr = Zb.
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long blk = (long long)N_pad * hp;
-    if (idx >= blk) return;
-    int n = (int)(idx / hp), j = (int)(idx % hp);
-    bool live = (n < N) && (j < h);
-    float w = live ? wL[j] : 0.f;
-    float rn = (n < N) ? (r ? (float)r[n] : 1.f) : 0.f;
-    float y0 = tanhf(A0[idx]);
-    float s1 = 1.f - y0 * y0;
-    const float c0 = seed ? seed[n] : (S == 1 ? 1.f : 0.f);
-    auto put = [&](long long o, float ab) {
-        const bf16 zh = __float2bfloat16_rn(ab), gh = __float2bfloat16_rn(rn * ab);
-        Zb[o] = zh;
-        Gr[o] = gh;
-        if (Zb_lo) {
-            Zb_lo[o] = __float2bfloat16_rn(ab - __bfloat162float(zh));
-            Gr_lo[o] = __float2bfloat16_rn(rn * ab - __bfloat162float(gh));
+struct k_last_bwd {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ wL, const bf16* __restrict__ T_hi,
+                               const float* __restrict__ A0, const float* __restrict__ AD,
+                               const float* __restrict__ SSQ, const double* __restrict__ r, int N, int N_pad, int h,
+                               int hp, int S, const float* __restrict__ chw, float cT, float cD,
+                               const float* __restrict__ seed, bf16* Zb, bf16* Gr, const bf16* __restrict__ T_lo,
+                               bf16* Zb_lo, bf16* Gr_lo) {
+        // T_lo, Zb_lo, Gr_lo: split-BF16 everywhere (all three, or none)
+        // seed == nullptr: the residual's constant seed c (cT, cD; 1 on the value of a
+        // boundary pass); else c_{n,s} = seed[s * N_pad + n] (reverse mode of the forward
+        // Laplacian).  r == nullptr: Gr = Zb.
+        long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
+        const long long blk = (long long)N_pad * hp;
+        if (idx >= blk) return;
+        int n = (int)(idx / hp), j = (int)(idx % hp);
+        bool live = (n < N) && (j < h);
+        float w = live ? wL[j] : 0.f;
+        float rn = (n < N) ? (r ? (float)r[n] : 1.f) : 0.f;
+        float y0 = tanhf(A0[idx]);
+        float s1 = 1.f - y0 * y0;
+        const float c0 = seed ? seed[n] : (S == 1 ? 1.f : 0.f);
+        auto put = [&](long long o, float ab) {
+            const bf16 zh = __float2bfloat16_rn(ab), gh = __float2bfloat16_rn(rn * ab);
+            Zb[o] = zh;
+            Gr[o] = gh;
+            if (Zb_lo) {
+                Zb_lo[o] = __float2bfloat16_rn(ab - __bfloat162float(zh));
+                Gr_lo[o] = __float2bfloat16_rn(rn * ab - __bfloat162float(gh));
+            }
+        };
+        if (S == 1) {
+            put(idx, s1 * c0 * w);
+            return;
         }
-    };
-    if (S == 1) {
-        put(idx, s1 * c0 * w);
-        return;
+        // seed c = dr/dZ^{(L)}: cD on the second-order column, cT on tangent column 1 (time, heat)
+        float yD = (seed ? seed[(long long)(S - 1) * N_pad + n] : cD) * w;
+        float cross = 0.f;
+        for (int s = 1; s < S - 1; s++) {
+            float yi = __bfloat162float(T_hi[s * blk + idx]);
+            if (T_lo) yi += __bfloat162float(T_lo[s * blk + idx]);
+            float ybar = (seed ? seed[(long long)s * N_pad + n] : (s == 1 ? cT : 0.f)) * w;
+            float ab = s1 * ybar;
+            ab -= 4.f * chw[s - 1] * y0 * yi * yD;
+            cross = fmaf(yi, ybar, cross);
+            ab = live ? ab : 0.f;
+            put(s * blk + idx, ab);
+        }
+        float a0b = s1 * c0 * w - 2.f * y0 * cross - 2.f * s1 * (y0 * AD[idx] + (1.f - 3.f * y0 * y0) * SSQ[idx]) * yD;
+        float aDb = s1 * yD;
+        a0b = live ? a0b : 0.f;
+        aDb = live ? aDb : 0.f;
+        put(idx, a0b);
+        put((S - 1) * blk + idx, aDb);
     }
-    // seed c = dr/dZ^{(L)}: cD on the second-order column, cT on tangent column 1 (time, heat)
-    float yD = (seed ? seed[(long long)(S - 1) * N_pad + n] : cD) * w;
-    float cross = 0.f;
-    for (int s = 1; s < S - 1; s++) {
-        float yi = __bfloat162float(T_hi[s * blk + idx]);
-        if (T_lo) yi += __bfloat162float(T_lo[s * blk + idx]);
-        float ybar = (seed ? seed[(long long)s * N_pad + n] : (s == 1 ? cT : 0.f)) * w;
-        float ab = s1 * ybar;
-        ab -= 4.f * chw[s - 1] * y0 * yi * yD;
-        cross = fmaf(yi, ybar, cross);
-        ab = live ? ab : 0.f;
-        put(s * blk + idx, ab);
-    }
-    float a0b = s1 * c0 * w - 2.f * y0 * cross - 2.f * s1 * (y0 * AD[idx] + (1.f - 3.f * y0 * y0) * SSQ[idx]) * yD;
-    float aDb = s1 * yD;
-    a0b = live ? a0b : 0.f;
-    aDb = live ? aDb : 0.f;
-    put(idx, a0b);
-    put((S - 1) * blk + idx, aDb);
-}
+};
 
 // Column reductions run as 32 x 32 thread blocks: lane = column, warp = row
 // group (rows strided by 32), then a deterministic sum over the 32 groups.
@@ -424,186 +457,209 @@ __device__ double reduce_row_groups(double v, double (*sh)[33]) {
 }
 
 // FP64 column sums of rows [row0, row0+nrows) of a BF16 matrix (+ optional lo block).
-__global__ void __launch_bounds__(RED_THREADS) k_colsum(const bf16* __restrict__ X, const bf16* __restrict__ Xlo,
-                                                        int hp, long long row0, int nrows, int ncols, double* out) {
-    __shared__ double sh[32][33];
-    const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
-    const int q = blockIdx.x * 32 + cl;
-    // FP32 partial sums per row group (FP64 arithmetic is scarce on this part),
-    // combined in FP64
-    float acc = 0.f;
-    if (q < ncols)
-        for (int n = rg; n < nrows; n += 32) {
-            float v = __bfloat162float(X[(row0 + n) * hp + q]);
-            if (Xlo) v += __bfloat162float(Xlo[(long long)n * hp + q]);
-            acc += v;
-        }
-    double s = reduce_row_groups((double)acc, sh);
-    if (rg == 0 && q < ncols) out[q] = s;
-}
+struct k_colsum {
+    static constexpr int THREADS = RED_THREADS;
+    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ X, const bf16* __restrict__ Xlo, int hp,
+                               long long row0, int nrows, int ncols, double* out) {
+        __shared__ double sh[32][33];
+        const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
+        const int q = vb.x * 32 + cl;
+        // FP32 partial sums per row group (FP64 arithmetic is scarce on this part),
+        // combined in FP64
+        float acc = 0.f;
+        if (q < ncols)
+            for (int n = rg; n < nrows; n += 32) {
+                float v = __bfloat162float(X[(row0 + n) * hp + q]);
+                if (Xlo) v += __bfloat162float(Xlo[(long long)n * hp + q]);
+                acc += v;
+            }
+        double s = reduce_row_groups((double)acc, sh);
+        if (rg == 0 && q < ncols) out[q] = s;
+    }
+};
 
 // KFAC-reduce per-point sums over the S Taylor columns: out = scale * sum_s X_s.
 // With X_lo (split-BF16 everywhere) the sum runs over hi + lo and is stored
 // split again (out_lo = the rounding remainder of out).
-__global__ void k_sum_over_s(const bf16* __restrict__ X, const bf16* __restrict__ X_lo, int N_pad, int S, int hp,
-                             float scale, bf16* out, bf16* out_lo) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long blk = (long long)N_pad * hp;
-    if (idx >= blk) return;
-    float acc = 0.f;
-    for (int s = 0; s < S; s++) {
-        acc += __bfloat162float(X[s * blk + idx]);
-        if (X_lo) acc += __bfloat162float(X_lo[s * blk + idx]);
+struct k_sum_over_s {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ X, const bf16* __restrict__ X_lo,
+                               int N_pad, int S, int hp, float scale, bf16* out, bf16* out_lo) {
+        long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
+        const long long blk = (long long)N_pad * hp;
+        if (idx >= blk) return;
+        float acc = 0.f;
+        for (int s = 0; s < S; s++) {
+            acc += __bfloat162float(X[s * blk + idx]);
+            if (X_lo) acc += __bfloat162float(X_lo[s * blk + idx]);
+        }
+        const float v = scale * acc;
+        const bf16 hi = __float2bfloat16_rn(v);
+        out[idx] = hi;
+        if (out_lo) out_lo[idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
     }
-    const float v = scale * acc;
-    const bf16 hi = __float2bfloat16_rn(v);
-    out[idx] = hi;
-    if (out_lo) out_lo[idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
-}
+};
 
 // Factor from Gram partials: M[p][q] = sc * sum_z part[z][min][max] (p,q < P),
 // bias row/column sc_b * cs[q], corner `corner`; EMA into the FP64 factor.
-__global__ void k_factor_reduce(const float* __restrict__ part, int nz, int P, int sym, const double* cs, double sc,
-                                double sc_b, double corner, int with_bias, double* fac, double beta, int* status) {
-    int n = P + with_bias;
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)n * n) return;
-    int p = (int)(idx / n), q = (int)(idx % n);
-    double v;
-    if (p < P && q < P) {
-        int a = p, b = q;
-        if (sym && a > b) { a = q; b = p; }
-        double acc = 0.0;
-        for (int z = 0; z < nz; z++) acc += (double)part[((long long)z * P + a) * P + b];
-        v = sc * acc;
-    } else if (p < P) {
-        v = sc_b * cs[p];
-    } else if (q < P) {
-        v = sc_b * cs[q];
-    } else {
-        v = corner;
+struct k_factor_reduce {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ part, int nz, int P, int sym,
+                               const double* cs, double sc, double sc_b, double corner, int with_bias, double* fac,
+                               double beta, int* status) {
+        int n = P + with_bias;
+        long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
+        if (idx >= (long long)n * n) return;
+        int p = (int)(idx / n), q = (int)(idx % n);
+        double v;
+        if (p < P && q < P) {
+            int a = p, b = q;
+            if (sym && a > b) { a = q; b = p; }
+            double acc = 0.0;
+            for (int z = 0; z < nz; z++) acc += (double)part[((long long)z * P + a) * P + b];
+            v = sc * acc;
+        } else if (p < P) {
+            v = sc_b * cs[p];
+        } else if (q < P) {
+            v = sc_b * cs[q];
+        } else {
+            v = corner;
+        }
+        double o = beta * fac[idx] + (1.0 - beta) * v;
+        if (!isfinite(o)) latch_status(status, KFAC_NONFINITE);
+        fac[idx] = o;
     }
-    double o = beta * fac[idx] + (1.0 - beta) * v;
-    if (!isfinite(o)) latch_status(status, KFAC_NONFINITE);
-    fac[idx] = o;
-}
+};
 
 // Weight gradient of a layer from interior and boundary Gram partials:
 // grad[i + P*q] = si * sum part_i[i][q] + sb * sum part_b[i][q] (q < Q), bias
 // column q = Q from the column sums.
-__global__ void k_grad_reduce(const float* __restrict__ pi, int zi, const float* __restrict__ pb, int zb, int P, int Q,
-                              const double* csi, const double* csb, double si, double sb, double* grad) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)P * (Q + 1)) return;
-    int i = (int)(idx / (Q + 1)), q = (int)(idx % (Q + 1));
-    double v;
-    if (q < Q) {
-        double a = 0.0, b = 0.0;
-        for (int z = 0; z < zi; z++) a += (double)pi[((long long)z * P + i) * Q + q];
-        for (int z = 0; z < zb; z++) b += (double)pb[((long long)z * P + i) * Q + q];
-        v = si * a + sb * b;
-    } else {
-        v = si * csi[i] + sb * csb[i];
+struct k_grad_reduce {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ pi, int zi, const float* __restrict__ pb,
+                               int zb, int P, int Q, const double* csi, const double* csb, double si, double sb,
+                               double* grad) {
+        long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
+        if (idx >= (long long)P * (Q + 1)) return;
+        int i = (int)(idx / (Q + 1)), q = (int)(idx % (Q + 1));
+        double v;
+        if (q < Q) {
+            double a = 0.0, b = 0.0;
+            for (int z = 0; z < zi; z++) a += (double)pi[((long long)z * P + i) * Q + q];
+            for (int z = 0; z < zb; z++) b += (double)pb[((long long)z * P + i) * Q + q];
+            v = si * a + sb * b;
+        } else {
+            v = si * csi[i] + sb * csb[i];
+        }
+        grad[i + (long long)P * q] = v;
     }
-    grad[i + (long long)P * q] = v;
-}
+};
 
 // First-layer input factor in closed form (Sec. 3.1: T^(0) has columns
 // (x, e_1..e_d, 0) and bias row (1, 0, .., 0)).
-__global__ void __launch_bounds__(RED_THREADS) k_factor_A1(const float* __restrict__ X, int N, int d, int S,
-                                                           int reduce, int boundary, double* fac, double beta,
-                                                           int* status) {
-    __shared__ double shm[32][33];
-    const int n1 = d + 1;
-    const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
-    const int p = blockIdx.y, q = blockIdx.x * 32 + cl;
-    float acc = 0.f;     // FP32 partial sums per row group, combined in FP64
-    const float sh = (reduce && !boundary) ? 1.f : 0.f;   // reduce: abar = (x + 1, 1) / S
-    if (q < n1)
-        for (int n = rg; n < N; n += 32) {
-            float xp = (p < d) ? X[(long long)n * d + p] + sh : 1.f;
-            float xq = (q < d) ? X[(long long)n * d + q] + sh : 1.f;
-            acc = fmaf(xp, xq, acc);
-        }
-    double tot = reduce_row_groups((double)acc, shm);
-    if (rg != 0 || q >= n1) return;
-    const int idx = p * n1 + q;
-    double v;
-    if (boundary) v = tot / N;
-    else if (reduce) v = tot / ((double)N * S * S);
-    else v = (tot + ((p == q && p < d) ? (double)N : 0.0)) / ((double)N * S);
-    double o = beta * fac[idx] + (1.0 - beta) * v;
-    if (!isfinite(o)) latch_status(status, KFAC_NONFINITE);
-    fac[idx] = o;
-}
+struct k_factor_A1 {
+    static constexpr int THREADS = RED_THREADS;
+    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ X, int N, int d, int S, int reduce,
+                               int boundary, double* fac, double beta, int* status) {
+        __shared__ double shm[32][33];
+        const int n1 = d + 1;
+        const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
+        const int p = vb.y, q = vb.x * 32 + cl;
+        float acc = 0.f;     // FP32 partial sums per row group, combined in FP64
+        const float sh = (reduce && !boundary) ? 1.f : 0.f;   // reduce: abar = (x + 1, 1) / S
+        if (q < n1)
+            for (int n = rg; n < N; n += 32) {
+                float xp = (p < d) ? X[(long long)n * d + p] + sh : 1.f;
+                float xq = (q < d) ? X[(long long)n * d + q] + sh : 1.f;
+                acc = fmaf(xp, xq, acc);
+            }
+        double tot = reduce_row_groups((double)acc, shm);
+        if (rg != 0 || q >= n1) return;
+        const int idx = p * n1 + q;
+        double v;
+        if (boundary) v = tot / N;
+        else if (reduce) v = tot / ((double)N * S * S);
+        else v = (tot + ((p == q && p < d) ? (double)N : 0.0)) / ((double)N * S);
+        double o = beta * fac[idx] + (1.0 - beta) * v;
+        if (!isfinite(o)) latch_status(status, KFAC_NONFINITE);
+        fac[idx] = o;
+    }
+};
 
 // Weight gradient of the first layer:
 //   (1/N) sum_n [ (r g)_{n,0} (x_n, 1)^T + sum_i (r g)_{n,i} (e_i, 0)^T ] + boundary term.
-__global__ void __launch_bounds__(RED_THREADS) k_grad_layer1(const bf16* __restrict__ Gr, const bf16* __restrict__ Grb,
-                                                             const float* __restrict__ X,
-                                                             const float* __restrict__ Xb, int N, int N_pad, int Nb,
-                                                             int d, int h, int hp, int S, double si, double sb,
-                                                             double* grad, double* gtan, const bf16* __restrict__ Gr_lo,
-                                                             const bf16* __restrict__ Grb_lo) {
-    // Gr_lo / Grb_lo: low halves (split-BF16 everywhere), or nullptr
-    // dL/dW~_1[j][k] = si sum_n (r g_{n,0,j} x_{n,k} + sum_m r g_{n,m,j} (v_m)_k) + boundary term (sb);
-    // with gtan the tangent sums t_{j,m} = si sum_n r g_{n,m,j} are written there
-    // (the caller rotates them by the tangent directions), else v_m = e_m.
-    __shared__ double shm[32][33];
-    const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
-    const int k = blockIdx.y, j = blockIdx.x * 32 + cl;
-    const long long blk = (long long)N_pad * hp;
-    float a = 0.f, t = 0.f, b = 0.f;     // FP32 partial sums per row group, combined in FP64
-    if (j < h) {
-        for (int n = rg; n < N; n += 32) {
-            float g0 = __bfloat162float(Gr[(long long)n * hp + j]);
-            if (Gr_lo) g0 += __bfloat162float(Gr_lo[(long long)n * hp + j]);
-            if (k < d) {
-                a = fmaf(g0, X[(long long)n * d + k], a);
-                t += __bfloat162float(Gr[(1 + k) * blk + (long long)n * hp + j]);
-                if (Gr_lo) t += __bfloat162float(Gr_lo[(1 + k) * blk + (long long)n * hp + j]);
-            } else {
-                a += g0;
+struct k_grad_layer1 {
+    static constexpr int THREADS = RED_THREADS;
+    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ Gr, const bf16* __restrict__ Grb,
+                               const float* __restrict__ X, const float* __restrict__ Xb, int N, int N_pad, int Nb,
+                               int d, int h, int hp, int S, double si, double sb, double* grad, double* gtan,
+                               const bf16* __restrict__ Gr_lo, const bf16* __restrict__ Grb_lo) {
+        // Gr_lo / Grb_lo: low halves (split-BF16 everywhere), or nullptr
+        // dL/dW~_1[j][k] = si sum_n (r g_{n,0,j} x_{n,k} + sum_m r g_{n,m,j} (v_m)_k) + boundary term (sb);
+        // with gtan the tangent sums t_{j,m} = si sum_n r g_{n,m,j} are written there
+        // (the caller rotates them by the tangent directions), else v_m = e_m.
+        __shared__ double shm[32][33];
+        const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
+        const int k = vb.y, j = vb.x * 32 + cl;
+        const long long blk = (long long)N_pad * hp;
+        float a = 0.f, t = 0.f, b = 0.f;     // FP32 partial sums per row group, combined in FP64
+        if (j < h) {
+            for (int n = rg; n < N; n += 32) {
+                float g0 = __bfloat162float(Gr[(long long)n * hp + j]);
+                if (Gr_lo) g0 += __bfloat162float(Gr_lo[(long long)n * hp + j]);
+                if (k < d) {
+                    a = fmaf(g0, X[(long long)n * d + k], a);
+                    t += __bfloat162float(Gr[(1 + k) * blk + (long long)n * hp + j]);
+                    if (Gr_lo) t += __bfloat162float(Gr_lo[(1 + k) * blk + (long long)n * hp + j]);
+                } else {
+                    a += g0;
+                }
+            }
+            for (int n = rg; n < Nb; n += 32) {
+                float g0 = __bfloat162float(Grb[(long long)n * hp + j]);
+                if (Grb_lo) g0 += __bfloat162float(Grb_lo[(long long)n * hp + j]);
+                b += (k < d) ? g0 * Xb[(long long)n * d + k] : g0;
             }
         }
-        for (int n = rg; n < Nb; n += 32) {
-            float g0 = __bfloat162float(Grb[(long long)n * hp + j]);
-            if (Grb_lo) g0 += __bfloat162float(Grb_lo[(long long)n * hp + j]);
-            b += (k < d) ? g0 * Xb[(long long)n * d + k] : g0;
+        const double tv = si * (double)t;
+        const double v = si * (double)a + sb * (double)b + (gtan ? 0.0 : tv);
+        const double s = reduce_row_groups(v, shm);
+        if (rg == 0 && j < h) grad[j + (long long)h * k] = s;
+        if (gtan && k < d) {
+            __syncthreads();
+            const double st = reduce_row_groups(tv, shm);
+            if (rg == 0 && j < h) gtan[j + (long long)h * k] = st;
         }
     }
-    const double tv = si * (double)t;
-    const double v = si * (double)a + sb * (double)b + (gtan ? 0.0 : tv);
-    const double s = reduce_row_groups(v, shm);
-    if (rg == 0 && j < h) grad[j + (long long)h * k] = s;
-    if (gtan && k < d) {
-        __syncthreads();
-        const double st = reduce_row_groups(tv, shm);
-        if (rg == 0 && j < h) gtan[j + (long long)h * k] = st;
-    }
-}
+};
 
 // grad[j][k] += sum_m t_{j,m} (v_m)_k for the first layer's input columns k < d.
-__global__ void k_rotate_grad1(const double* __restrict__ gtan, const float* __restrict__ Qf, int h, int d,
-                               double* grad) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)h * d) return;
-    const int j = (int)(idx % h), k = (int)(idx / h);
-    double acc = 0.0;
-    for (int m = 0; m < d; m++) acc += gtan[j + (long long)h * m] * (double)Qf[(long long)k * d + m];
-    grad[j + (long long)h * k] += acc;
-}
+struct k_rotate_grad1 {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ gtan, const float* __restrict__ Qf,
+                               int h, int d, double* grad) {
+        long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
+        if (idx >= (long long)h * d) return;
+        const int j = (int)(idx % h), k = (int)(idx / h);
+        double acc = 0.0;
+        for (int m = 0; m < d; m++) acc += gtan[j + (long long)h * m] * (double)Qf[(long long)k * d + m];
+        grad[j + (long long)h * k] += acc;
+    }
+};
 
 // Tangent inputs of the first layer for the directions v_m = Q e_m: W1Qf[m][j] = sum_k W1f[k][j] Q[k][m].
-__global__ void k_rotate_first(const float* __restrict__ W1f, const float* __restrict__ Qf, int d, int hp,
-                               float* W1Qf) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)d * hp) return;
-    const int m = (int)(idx / hp), j = (int)(idx % hp);
-    float acc = 0.f;
-    for (int k = 0; k < d; k++) acc = fmaf(W1f[(long long)k * hp + j], Qf[(long long)k * d + m], acc);
-    W1Qf[idx] = acc;
-}
+struct k_rotate_first {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ W1f, const float* __restrict__ Qf, int d,
+                               int hp, float* W1Qf) {
+        long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
+        if (idx >= (long long)d * hp) return;
+        const int m = (int)(idx / hp), j = (int)(idx % hp);
+        float acc = 0.f;
+        for (int k = 0; k < d; k++) acc = fmaf(W1f[(long long)k * hp + j], Qf[(long long)k * d + m], acc);
+        W1Qf[idx] = acc;
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Residual Jacobian-vector products of KFAC* from the step's stored Taylor
@@ -617,198 +673,248 @@ __global__ void k_rotate_first(const float* __restrict__ W1f, const float* __res
 // First layer: jv[n] += g_{n,0}^T (V_1 x_n + b_v) + sum_m g_{n,m}^T V_1 v_m.
 // V1f: the direction's first layer input-major (V1f[k * hp + j], k = d: bias);
 // V1t: its tangent inputs V_1 v_m (V1t[m * hp + j]).  One block per point.
-__global__ void k_jdot_layer1(const float* __restrict__ V1f, const float* __restrict__ V1t,
-                              const float* __restrict__ Xf, const bf16* __restrict__ G, const bf16* __restrict__ G_lo,
-                              int N, int N_pad, int d, int hp, int S, double* jv) {
-    __shared__ double sh[32];
-    const int n = blockIdx.x;
-    const long long blk = (long long)N_pad * hp;
-    float t = 0.f;
-    for (int j = threadIdx.x; j < hp; j += blockDim.x) {
-        float a0 = V1f[(long long)d * hp + j];
-        for (int k = 0; k < d; k++) a0 = fmaf(V1f[(long long)k * hp + j], Xf[(long long)n * d + k], a0);
-        const long long o = (long long)n * hp + j;
-        float g0 = __bfloat162float(G[o]);
-        if (G_lo) g0 += __bfloat162float(G_lo[o]);
-        t = fmaf(a0, g0, t);
-        if (S > 1)
-            for (int m = 0; m < d; m++) {
-                float g = __bfloat162float(G[(1 + m) * blk + o]);
-                if (G_lo) g += __bfloat162float(G_lo[(1 + m) * blk + o]);
-                t = fmaf(V1t[(long long)m * hp + j], g, t);
-            }
+struct k_jdot_layer1 {
+    static constexpr int THREADS = 256;
+    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ V1f, const float* __restrict__ V1t,
+                               const float* __restrict__ Xf, const bf16* __restrict__ G,
+                               const bf16* __restrict__ G_lo, int N, int N_pad, int d, int hp, int S, double* jv) {
+        __shared__ double sh[32];
+        const int n = vb.x;
+        const long long blk = (long long)N_pad * hp;
+        float t = 0.f;
+        for (int j = threadIdx.x; j < hp; j += blockDim.x) {
+            float a0 = V1f[(long long)d * hp + j];
+            for (int k = 0; k < d; k++) a0 = fmaf(V1f[(long long)k * hp + j], Xf[(long long)n * d + k], a0);
+            const long long o = (long long)n * hp + j;
+            float g0 = __bfloat162float(G[o]);
+            if (G_lo) g0 += __bfloat162float(G_lo[o]);
+            t = fmaf(a0, g0, t);
+            if (S > 1)
+                for (int m = 0; m < d; m++) {
+                    float g = __bfloat162float(G[(1 + m) * blk + o]);
+                    if (G_lo) g += __bfloat162float(G_lo[(1 + m) * blk + o]);
+                    t = fmaf(V1t[(long long)m * hp + j], g, t);
+                }
+        }
+        double v = t;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x % 32 == 0) sh[threadIdx.x / 32] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < (int)(blockDim.x / 32); w++) tot += sh[w];
+            jv[n] += tot;
+        }
     }
-    double v = t;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x % 32 == 0) sh[threadIdx.x / 32] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot = 0.0;
-        for (int w = 0; w < (int)(blockDim.x / 32); w++) tot += sh[w];
-        jv[n] += tot;
-    }
-}
+};
 
 // jv[n] += sum over the JDOT launch's partial slots of part[slot][n].
-__global__ void k_jdot_reduce(const float* __restrict__ part, int slots, int N, int N_pad, double* jv) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    double acc = 0.0;
-    for (int z = 0; z < slots; z++) acc += (double)part[(long long)z * N_pad + n];
-    jv[n] += acc;
-}
-
-__global__ void k_residual_jvp_mx(const float* __restrict__ jz, double* jv, int N, int N_pad, int S, int interior,
-                                  double cT, double cD) {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    double v;
-    if (!interior) {
-        v = (double)jz[n];
-    } else {
-        v = cD * (double)jz[(long long)(S - 1) * N_pad + n];
-        if (cT != 0.0) v += cT * (double)jz[N_pad + n];
+struct k_jdot_reduce {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ part, int slots, int N, int N_pad,
+                               double* jv) {
+        const int n = vb.x * blockDim.x + threadIdx.x;
+        if (n >= N) return;
+        double acc = 0.0;
+        for (int z = 0; z < slots; z++) acc += (double)part[(long long)z * N_pad + n];
+        jv[n] += acc;
     }
-    jv[n] = v;
-}
+};
+
+struct k_residual_jvp_mx {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ jz, double* jv, int N, int N_pad, int S,
+                               int interior, double cT, double cD) {
+        int n = vb.x * blockDim.x + threadIdx.x;
+        if (n >= N) return;
+        double v;
+        if (!interior) {
+            v = (double)jz[n];
+        } else {
+            v = cD * (double)jz[(long long)(S - 1) * N_pad + n];
+            if (cT != 0.0) v += cT * (double)jz[N_pad + n];
+        }
+        jv[n] = v;
+    }
+};
 
 // Reverse mode of the forward Laplacian: the seed c_{n,s} = dphi/dZ^{(L)}_{n,s} per
 // point, in FP32: the value row takes du, the tangent rows dgrad (rotated into
 // the tangent directions, Q^T dgrad, for a general operator), the last row dlap.
-__global__ void k_seed_mx(float* seed, int N, int N_pad, int S, const float* __restrict__ Qf,
-                          const double* __restrict__ du, const double* __restrict__ dgrad,
-                          const double* __restrict__ dlap) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)S * N_pad) return;
-    const int s = (int)(idx / N_pad), n = (int)(idx % N_pad), d = S - 2;
-    float c = 0.f;
-    if (n < N) {
-        if (s == 0) {
-            c = du ? (float)du[n] : 0.f;
-        } else if (s == S - 1) {
-            c = dlap ? (float)dlap[n] : 0.f;
-        } else if (dgrad) {
-            if (!Qf) {
-                c = (float)dgrad[(long long)n * d + (s - 1)];
-            } else {
-                for (int i = 0; i < d; i++) c = fmaf(Qf[(long long)i * d + (s - 1)], (float)dgrad[(long long)n * d + i], c);
+struct k_seed_mx {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, float* seed, int N, int N_pad, int S, const float* __restrict__ Qf,
+                               const double* __restrict__ du, const double* __restrict__ dgrad,
+                               const double* __restrict__ dlap) {
+        long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
+        if (idx >= (long long)S * N_pad) return;
+        const int s = (int)(idx / N_pad), n = (int)(idx % N_pad), d = S - 2;
+        float c = 0.f;
+        if (n < N) {
+            if (s == 0) {
+                c = du ? (float)du[n] : 0.f;
+            } else if (s == S - 1) {
+                c = dlap ? (float)dlap[n] : 0.f;
+            } else if (dgrad) {
+                if (!Qf) {
+                    c = (float)dgrad[(long long)n * d + (s - 1)];
+                } else {
+                    for (int i = 0; i < d; i++)
+                        c = fmaf(Qf[(long long)i * d + (s - 1)], (float)dgrad[(long long)n * d + i], c);
+                }
             }
         }
+        seed[idx] = c;
     }
-    seed[idx] = c;
-}
+};
 
 // dphi/dW~_L[q] = sum_n sum_s c_{n,s} T^_{n,s}[q]: the hidden rows with their low
 // halves where they have one (value, second-order, heat time; every row at its
 // own block when split_all), and the bias entry q = h_{L-1} from the value
 // rows.  FP32 partial sums per row group.
-__global__ void __launch_bounds__(RED_THREADS) k_last_grad_seeded(const bf16* __restrict__ T_hi,
-                                                                  const bf16* __restrict__ T_lo,
-                                                                  const float* __restrict__ seed, int N, int N_pad,
-                                                                  int hin, int hp, int S, int split_time,
-                                                                  int split_all, double* grad) {
-    __shared__ double shm[32][33];
-    const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
-    const int q = blockIdx.x * 32 + cl;
-    const long long blk = (long long)N_pad * hp;
-    float acc = 0.f;
-    if (q < hin) {
-        for (int s = 0; s < S; s++) {
-            const bf16* lo = nullptr;
-            if (split_all) lo = T_lo + s * blk;
-            else if (s == 0) lo = T_lo;
-            else if (s == S - 1) lo = T_lo + blk;
-            else if (s == 1 && split_time) lo = T_lo + 2 * blk;
-            for (int n = rg; n < N; n += 32) {
-                float t = __bfloat162float(T_hi[s * blk + (long long)n * hp + q]);
-                if (lo) t += __bfloat162float(lo[(long long)n * hp + q]);
-                acc = fmaf(seed[(long long)s * N_pad + n], t, acc);
+struct k_last_grad_seeded {
+    static constexpr int THREADS = RED_THREADS;
+    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo,
+                               const float* __restrict__ seed, int N, int N_pad, int hin, int hp, int S,
+                               int split_time, int split_all, double* grad) {
+        __shared__ double shm[32][33];
+        const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
+        const int q = vb.x * 32 + cl;
+        const long long blk = (long long)N_pad * hp;
+        float acc = 0.f;
+        if (q < hin) {
+            for (int s = 0; s < S; s++) {
+                const bf16* lo = nullptr;
+                if (split_all) lo = T_lo + s * blk;
+                else if (s == 0) lo = T_lo;
+                else if (s == S - 1) lo = T_lo + blk;
+                else if (s == 1 && split_time) lo = T_lo + 2 * blk;
+                for (int n = rg; n < N; n += 32) {
+                    float t = __bfloat162float(T_hi[s * blk + (long long)n * hp + q]);
+                    if (lo) t += __bfloat162float(lo[(long long)n * hp + q]);
+                    acc = fmaf(seed[(long long)s * N_pad + n], t, acc);
+                }
             }
+        } else if (q == hin) {
+            for (int n = rg; n < N; n += 32) acc += seed[n];
         }
-    } else if (q == hin) {
-        for (int n = rg; n < N; n += 32) acc += seed[n];
+        const double tot = reduce_row_groups((double)acc, shm);
+        if (rg == 0 && q <= hin) grad[q] = tot;
     }
-    const double tot = reduce_row_groups((double)acc, shm);
-    if (rg == 0 && q <= hin) grad[q] = tot;
-}
+};
 
 // dphi/dx_n = W_1^T g^{(1)}_{n,0}: x enters the value column of layer 1 only.
 // Zb1_lo: the adjoint's low half (split-BF16 everywhere), or nullptr.
-__global__ void k_dX_mx(const bf16* __restrict__ Zb1, const bf16* __restrict__ Zb1_lo, int N, int hp, int h1, int d,
-                        const float* __restrict__ W1f, double* dX) {
-    extern __shared__ float zrow[];
-    const int n = blockIdx.x;
-    for (int j = threadIdx.x; j < h1; j += blockDim.x) {
-        float z = __bfloat162float(Zb1[(long long)n * hp + j]);
-        if (Zb1_lo) z += __bfloat162float(Zb1_lo[(long long)n * hp + j]);
-        zrow[j] = z;
+struct k_dX_mx {
+    static constexpr int THREADS = 128;
+    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ Zb1, const bf16* __restrict__ Zb1_lo,
+                               int N, int hp, int h1, int d, const float* __restrict__ W1f, double* dX) {
+        extern __shared__ float zrow[];
+        const int n = vb.x;
+        for (int j = threadIdx.x; j < h1; j += blockDim.x) {
+            float z = __bfloat162float(Zb1[(long long)n * hp + j]);
+            if (Zb1_lo) z += __bfloat162float(Zb1_lo[(long long)n * hp + j]);
+            zrow[j] = z;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < d; k += blockDim.x) {
+            float acc = 0.f;
+            for (int j = 0; j < h1; j++) acc = fmaf(zrow[j], W1f[(long long)k * hp + j], acc);
+            dX[(long long)n * d + k] = acc;
+        }
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < d; k += blockDim.x) {
-        float acc = 0.f;
-        for (int j = 0; j < h1; j++) acc = fmaf(zrow[j], W1f[(long long)k * hp + j], acc);
-        dX[(long long)n * d + k] = acc;
+};
+
+struct k_copy_or_add {
+    static constexpr int THREADS = EW;
+    __device__ static void run(uint3 vb, uint3 vg, double* dst, const double* src, long long n, int add) {
+        long long i = (long long)vb.x * blockDim.x + threadIdx.x;
+        if (i < n) dst[i] = add ? dst[i] + src[i] : src[i];
     }
-}
-
-__global__ void k_copy_or_add(double* dst, const double* src, long long n, int add) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = add ? dst[i] + src[i] : src[i];
-}
-
+};
 
 // Last layer: gradient (1/N) sum_{n,s} r_n c_s T^_{n,s} + boundary, and the
 // 1x1 output factors B_L.
-__global__ void k_last_layer_terms(const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo,
-                                   const bf16* __restrict__ Tb_hi, const bf16* __restrict__ Tb_lo,
-                                   const double* __restrict__ r, const double* __restrict__ rb, int N, int N_pad,
-                                   int Nb, int Nb_pad, int h, int hp, int S, double cT, double cD, int reduce,
-                                   double* grad, double* B_int, double* B_bdy, double beta, int* status,
-                                   int split_all) {
-    // low halves of the Laplacian (block 1) and time (block 2) rows, or at the
-    // rows' own blocks when every row is split
-    __shared__ double shm[32][33];
-    const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
-    const int q = blockIdx.x * 32 + cl;
-    const long long blk = (long long)N_pad * hp;
-    double a = 0.0, b = 0.0;
-    if (q < h) {
-        for (int n = rg; n < N; n += 32) {
-            double tD = (double)__bfloat162float(T_hi[(S - 1) * blk + (long long)n * hp + q]) +
-                        (double)__bfloat162float(T_lo[(split_all ? S - 1 : 1) * blk + (long long)n * hp + q]);
-            double v = cD * tD;
-            if (cT != 0.0)     // heat: the time tangent carries its low half (block 2)
-                v += cT * ((double)__bfloat162float(T_hi[blk + (long long)n * hp + q]) +
-                           (double)__bfloat162float(T_lo[(split_all ? 1 : 2) * blk + (long long)n * hp + q]));
-            a += r[n] * v;
+struct k_last_layer_terms {
+    static constexpr int THREADS = RED_THREADS;
+    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo,
+                               const bf16* __restrict__ Tb_hi, const bf16* __restrict__ Tb_lo,
+                               const double* __restrict__ r, const double* __restrict__ rb, int N, int N_pad, int Nb,
+                               int Nb_pad, int h, int hp, int S, double cT, double cD, int reduce, double* grad,
+                               double* B_int, double* B_bdy, double beta, int* status, int split_all) {
+        // low halves of the Laplacian (block 1) and time (block 2) rows, or at the
+        // rows' own blocks when every row is split
+        __shared__ double shm[32][33];
+        const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
+        const int q = vb.x * 32 + cl;
+        const long long blk = (long long)N_pad * hp;
+        double a = 0.0, b = 0.0;
+        if (q < h) {
+            for (int n = rg; n < N; n += 32) {
+                double tD = (double)__bfloat162float(T_hi[(S - 1) * blk + (long long)n * hp + q]) +
+                            (double)__bfloat162float(T_lo[(split_all ? S - 1 : 1) * blk + (long long)n * hp + q]);
+                double v = cD * tD;
+                if (cT != 0.0)     // heat: the time tangent carries its low half (block 2)
+                    v += cT * ((double)__bfloat162float(T_hi[blk + (long long)n * hp + q]) +
+                               (double)__bfloat162float(T_lo[(split_all ? 1 : 2) * blk + (long long)n * hp + q]));
+                a += r[n] * v;
+            }
+            for (int n = rg; n < Nb; n += 32) {
+                double t0 = (double)__bfloat162float(Tb_hi[(long long)n * hp + q]) +
+                            (double)__bfloat162float(Tb_lo[(long long)n * hp + q]);
+                b += rb[n] * t0;
+            }
+        } else if (q == h) {
+            for (int n = rg; n < Nb; n += 32) b += rb[n];   // bias: c_0 = 0 in the interior
         }
-        for (int n = rg; n < Nb; n += 32) {
-            double t0 = (double)__bfloat162float(Tb_hi[(long long)n * hp + q]) +
-                        (double)__bfloat162float(Tb_lo[(long long)n * hp + q]);
-            b += rb[n] * t0;
+        const double s = reduce_row_groups(a / N + b / Nb, shm);
+        if (rg != 0 || q > h) return;
+        grad[q] = s;
+        if (q == 0) {
+            double e = reduce ? (cD + cT) * (cD + cT) : cD * cD + cT * cT;
+            double o1 = beta * B_int[0] + (1.0 - beta) * e;
+            double o2 = beta * B_bdy[0] + (1.0 - beta) * 1.0;
+            if (!isfinite(o1) || !isfinite(o2)) latch_status(status, KFAC_NONFINITE);
+            B_int[0] = o1;
+            B_bdy[0] = o2;
         }
-    } else if (q == h) {
-        for (int n = rg; n < Nb; n += 32) b += rb[n];   // bias: c_0 = 0 in the interior
     }
-    const double s = reduce_row_groups(a / N + b / Nb, shm);
-    if (rg != 0 || q > h) return;
-    grad[q] = s;
-    if (q == 0) {
-        double e = reduce ? (cD + cT) * (cD + cT) : cD * cD + cT * cT;
-        double o1 = beta * B_int[0] + (1.0 - beta) * e;
-        double o2 = beta * B_bdy[0] + (1.0 - beta) * 1.0;
-        if (!isfinite(o1) || !isfinite(o2)) latch_status(status, KFAC_NONFINITE);
-        B_int[0] = o1;
-        B_bdy[0] = o2;
-    }
-}
+};
 
 // ============================================================================
 // Host helpers
 // ============================================================================
+// Grouped launch of the engine over a member table of Args (group.cuh).
+template <int MODE, bool SPLIT>
+cudaError_t launch_engine_group(const GroupTab& t, unsigned blocks, size_t, cudaStream_t s) {
+    using C = tck::Cfg<MODE, SPLIT>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(tck::tc_engine_group<MODE, SPLIT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    tck::tc_engine_group<MODE, SPLIT><<<blocks, tck::NUM_THREADS, C::SMEM, s>>>(t);
+    return cudaGetLastError();
+}
+
 template <int MODE, bool SPLIT>
 kfac_status_t launch_engine_as(kfac_pinn_handle* h, cudaStream_t s, const Args& a, dim3 grid) {
     using C = tck::Cfg<MODE, SPLIT>;
+    if (GroupRecorder* r = group_recorder()) {
+        LaunchRec rec;
+        rec.key = (const void*)tck::tc_engine_group<MODE, SPLIT>;
+        rec.launch = &launch_engine_group<MODE, SPLIT>;
+        rec.grid = make_uint3(grid.x, grid.y, grid.z);
+        rec.smem = C::SMEM;
+        rec.align = (int)alignof(Args);
+        rec.args.resize(sizeof(Args));
+        memcpy(rec.args.data(), &a, sizeof(Args));
+        rec.marker = 0;
+        r->list->push_back(std::move(rec));
+        return KFAC_OK;
+    }
     static bool attr_set = false;
     if (!attr_set) {
         if (cudaFuncSetAttribute(tck::tc_engine<MODE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
@@ -827,6 +933,8 @@ template <int MODE>
 kfac_status_t launch_engine(kfac_pinn_handle* h, cudaStream_t s, const Args& a, dim3 grid, int kclass, double work,
                             double exec) {
     if (grid.x == 0 || grid.y == 0 || grid.z == 0) return KFAC_OK;
+    if (group_recording())
+        return a.split_all ? launch_engine_as<MODE, true>(h, s, a, grid) : launch_engine_as<MODE, false>(h, s, a, grid);
     timer_begin(h, kclass, s);
     kfac_status_t st =
         a.split_all ? launch_engine_as<MODE, true>(h, s, a, grid) : launch_engine_as<MODE, false>(h, s, a, grid);
@@ -916,7 +1024,7 @@ int tune_find(const kfac_pinn_handle* h, const kfac_tune_entry_t& key) {
 }
 
 bool tune_may_measure(const kfac_pinn_handle* h, cudaStream_t s) {
-    if (!h->autotune || h->n_tune >= KFAC_TUNE_CAP) return false;
+    if (!h->autotune || h->n_tune >= KFAC_TUNE_CAP || group_recording()) return false;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
 }
@@ -1165,24 +1273,21 @@ kfac_status_t convert_weights_into(kfac_pinn_handle* h, cudaStream_t s, const do
     for (int l = 2; l <= L - 1; l++) {
         int hout = h->dims[l], hin = h->dims[l - 1];
         int hout_p = round_up(hout, 64), hin_p = round_up(hin, 64);
-        k_convert_weights<<<ceil_div_u((long long)hout_p * hin_p, EW), EW, 0, s>>>(
-            theta + h->woff[l - 1], hout, hin, hout_p, hin_p, w.W_hi[l - 1], w.W_lo[l - 1], w.Wt[l - 1],
-            w.Wt_lo[l - 1], w.bias[l - 1]);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_convert_weights>(h, s, ceil_div_u((long long)hout_p * hin_p, EW), 0, theta + h->woff[l - 1],
+                                       hout, hin, hout_p, hin_p, w.W_hi[l - 1], w.W_lo[l - 1], w.Wt[l - 1],
+                                       w.Wt_lo[l - 1], w.bias[l - 1]));
     }
     {
         const int h1 = h->dims[1], hp1 = round_up(h1, 64), d = h->dims[0];
-        k_convert_first<<<ceil_div_u((long long)(d + 1) * hp1, EW), EW, 0, s>>>(theta + h->woff[0], h1, hp1, d,
-                                                                                 w.W1f);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_convert_first>(h, s, ceil_div_u((long long)(d + 1) * hp1, EW), 0, theta + h->woff[0], h1, hp1,
+                                     d, w.W1f));
         if (w.W1Qf) {
-            k_rotate_first<<<ceil_div_u((long long)d * hp1, EW), EW, 0, s>>>(w.W1f, MX(h)->Qf, d, hp1, w.W1Qf);
-            KFAC_LAUNCH_CHECK(h);
+            KFAC_TRY(KL<k_rotate_first>(h, s, ceil_div_u((long long)d * hp1, EW), 0, w.W1f, MX(h)->Qf, d, hp1,
+                                        w.W1Qf));
         }
     }
     int hin = h->dims[L - 1], hin_p = round_up(hin, 64);
-    k_convert_last<<<ceil_div_u(hin_p + 1, EW), EW, 0, s>>>(theta + h->woff[L - 1], hin, hin_p, w.wL);
-    KFAC_LAUNCH_CHECK(h);
+    KFAC_TRY(KL<k_convert_last>(h, s, ceil_div_u(hin_p + 1, EW), 0, theta + h->woff[L - 1], hin, hin_p, w.wL));
     return KFAC_OK;
 }
 
@@ -1199,15 +1304,11 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
         MxLayer& l1 = P.lay[0];
         long long cnt = (long long)P.N_pad * l1.hp;
         timer_begin(h, KFAC_KC_ELEMENTWISE, s);
-        k_points_f32<<<ceil_div_u((long long)P.N_pad * d, EW), EW, 0, s>>>(X, N, P.N_pad, d, P.Xf);
-        KFAC_LAUNCH_CHECK(h);
-        k_layer1<<<ceil_div_u(cnt / 4, EW), EW, 0, s>>>(m->w.W1f, m->w.W1Qf ? m->w.W1Qf : m->w.W1f, P.Xf, N,
-                                                         P.N_pad, d, l1.h, l1.hp, S, h->chw32,
-                                                         (h->cfg.op == KFAC_OP_HEAT && S > 2) ? 1 : 0,
-                                                         split, l1.T_hi, l1.T_lo, l1.A0, l1.AD,
-                                                         l1.SSQ);
+        KFAC_TRY(KL<k_points_f32>(h, s, ceil_div_u((long long)P.N_pad * d, EW), 0, X, N, P.N_pad, d, P.Xf));
+        KFAC_TRY(KL<k_layer1>(h, s, ceil_div_u(cnt / 4, EW), 0, m->w.W1f, m->w.W1Qf ? m->w.W1Qf : m->w.W1f, P.Xf, N,
+                              P.N_pad, d, l1.h, l1.hp, S, h->chw32, (h->cfg.op == KFAC_OP_HEAT && S > 2) ? 1 : 0,
+                              split, l1.T_hi, l1.T_lo, l1.A0, l1.AD, l1.SSQ));
         timer_end(h, KFAC_KC_ELEMENTWISE, s, 2.0 * (double)S * cnt + 16.0 * cnt);
-        KFAC_LAUNCH_CHECK(h);
     }
     for (int l = 2; l <= L - 1; l++) {
         MxLayer& in = P.lay[l - 2];
@@ -1249,19 +1350,17 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
             if ((st = launch(len))) return st;
             long long cnt = (long long)P.N_pad * out.hp;
             timer_begin(h, KFAC_KC_ELEMENTWISE, s);
-            k_lap_finish<<<ceil_div_u(cnt, EW), EW, 0, s>>>(m->part, a.n_chunks, N, P.N_pad, out.h, out.hp, S,
-                                                             out.A0, out.AD, out.SSQ, out.T_hi, out.T_lo, split);
+            KFAC_TRY(KL<k_lap_finish>(h, s, ceil_div_u(cnt, EW), 0, m->part, a.n_chunks, N, P.N_pad, out.h, out.hp, S,
+                                      out.A0, out.AD, out.SSQ, out.T_hi, out.T_lo, split));
             timer_end(h, KFAC_KC_ELEMENTWISE, s, (4.0 * a.n_chunks + 16.0) * cnt);
-            KFAC_LAUNCH_CHECK(h);
         }
     }
     MxLayer& last = P.lay[L - 2];
     long long threads = (long long)(sel.nsel ? sel.nsel : S) * P.N_pad * 32;
     timer_begin(h, KFAC_KC_ELEMENTWISE, s);
-    k_last_fwd<<<ceil_div_u(threads, EW), EW, 0, s>>>(last.T_hi, last.T_lo, m->w.wL, P.N_pad, S, last.hp, sel,
-                                                       P.zl);
+    KFAC_TRY(KL<k_last_fwd>(h, s, ceil_div_u(threads, EW), 0, last.T_hi, last.T_lo, m->w.wL, P.N_pad, S, last.hp, sel,
+                            P.zl));
     timer_end(h, KFAC_KC_ELEMENTWISE, s, 0.0);
-    KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
 }
 
@@ -1273,11 +1372,10 @@ kfac_status_t backward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* r
         MxLayer& ly = P.lay[L - 2];
         long long cnt = (long long)P.N_pad * ly.hp;
         timer_begin(h, KFAC_KC_ELEMENTWISE, s);
-        k_last_bwd<<<ceil_div_u(cnt, EW), EW, 0, s>>>(m->w.wL, ly.T_hi, ly.A0, ly.AD, ly.SSQ, r, N, P.N_pad, ly.h,
-                                                       ly.hp, S, h->chw32, (float)h->cT, (float)h->cD, seed, ly.Zb,
-                                                       ly.Gr, ly.Zb_lo ? ly.T_lo : nullptr, ly.Zb_lo, ly.Gr_lo);
+        KFAC_TRY(KL<k_last_bwd>(h, s, ceil_div_u(cnt, EW), 0, m->w.wL, ly.T_hi, ly.A0, ly.AD, ly.SSQ, r, N, P.N_pad,
+                                ly.h, ly.hp, S, h->chw32, (float)h->cT, (float)h->cD, seed, ly.Zb, ly.Gr,
+                                ly.Zb_lo ? ly.T_lo : nullptr, ly.Zb_lo, ly.Gr_lo));
         timer_end(h, KFAC_KC_ELEMENTWISE, s, 6.0 * S * (double)cnt);
-        KFAC_LAUNCH_CHECK(h);
     }
     for (int l = L - 1; l >= 2; l--) {
         MxLayer& up = P.lay[l - 1];    // g^{(l)}
@@ -1349,21 +1447,17 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
     // ---- layer 1: closed-form A, gradient from the adjoints ---------------
     {
         int n1 = d + 1;
-        k_factor_A1<<<dim3(ceil_div_u(n1, 32), n1), RED_THREADS, 0, s>>>(I.Xf, N, d, S, reduce, 0, h->fac[KFAC_A_INT][0],
-                                                                          beta, h->status);
-        KFAC_LAUNCH_CHECK(h);
-        k_factor_A1<<<dim3(ceil_div_u(n1, 32), n1), RED_THREADS, 0, s>>>(B.Xf, Nb, d, 1, 0, 1, h->fac[KFAC_A_BDY][0],
-                                                                          beta, h->status);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_factor_A1>(h, s, dim3(ceil_div_u(n1, 32), n1), 0, I.Xf, N, d, S, reduce, 0,
+                                 h->fac[KFAC_A_INT][0], beta, h->status));
+        KFAC_TRY(KL<k_factor_A1>(h, s, dim3(ceil_div_u(n1, 32), n1), 0, B.Xf, Nb, d, 1, 0, 1, h->fac[KFAC_A_BDY][0],
+                                 beta, h->status));
         MxLayer& l1 = I.lay[0];
-        k_grad_layer1<<<dim3(ceil_div_u(l1.h, 32), d + 1), RED_THREADS, 0, s>>>(
-            l1.Gr, B.lay[0].Gr, I.Xf, B.Xf, N, I.N_pad, Nb, d, l1.h, l1.hp, S, 1.0 / N, 1.0 / Nb,
-            h->grad + h->woff[0], m->gtan, l1.Gr_lo, B.lay[0].Gr_lo);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_grad_layer1>(h, s, dim3(ceil_div_u(l1.h, 32), d + 1), 0, l1.Gr, B.lay[0].Gr, I.Xf, B.Xf, N,
+                                   I.N_pad, Nb, d, l1.h, l1.hp, S, 1.0 / N, 1.0 / Nb, h->grad + h->woff[0], m->gtan,
+                                   l1.Gr_lo, B.lay[0].Gr_lo));
         if (m->gtan) {
-            k_rotate_grad1<<<ceil_div_u((long long)l1.h * d, EW), EW, 0, s>>>(m->gtan, m->Qf, l1.h, d,
-                                                                              h->grad + h->woff[0]);
-            KFAC_LAUNCH_CHECK(h);
+            KFAC_TRY(KL<k_rotate_grad1>(h, s, ceil_div_u((long long)l1.h * d, EW), 0, m->gtan, m->Qf, l1.h, d,
+                                        h->grad + h->woff[0]));
         }
     }
     // ---- hidden-layer output factors B_l, l = 1..L-1 -----------------------
@@ -1372,9 +1466,8 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
         MxLayer& lb = B.lay[l - 1];
         if (reduce) {
             long long cnt = (long long)I.N_pad * li.hp;
-            k_sum_over_s<<<ceil_div_u(cnt, EW), EW, 0, s>>>(li.Zb, sa ? li.Zb_lo : nullptr, I.N_pad, S, li.hp, 1.f,
-                                                             I.red_g, sa ? I.red_g_lo : nullptr);
-            KFAC_LAUNCH_CHECK(h);
+            KFAC_TRY(KL<k_sum_over_s>(h, s, ceil_div_u(cnt, EW), 0, li.Zb, sa ? li.Zb_lo : nullptr, I.N_pad, S, li.hp,
+                                      1.f, I.red_g, sa ? I.red_g_lo : nullptr));
             if ((st = gram(h, s, I.gRg[l - 1], I.gRg[l - 1], li.h, li.h, I.N_pad, N, 1, part_i, zi,
                            sa ? &I.gRg_lo[l - 1] : nullptr, sa ? &I.gRg_lo[l - 1] : nullptr)))
                 return st;
@@ -1384,15 +1477,13 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
                 return st;
         }
         long long nn = (long long)li.h * li.h;
-        k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_i, zi, li.h, 1, nullptr, 1.0 / N, 0.0, 0.0, 0,
-                                                         h->fac[KFAC_B_INT][l - 1], beta, h->status);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_factor_reduce>(h, s, ceil_div_u(nn, EW), 0, part_i, zi, li.h, 1, nullptr, 1.0 / N, 0.0, 0.0, 0,
+                                     h->fac[KFAC_B_INT][l - 1], beta, h->status));
         if ((st = gram(h, s, lb.gZb, lb.gZb, lb.h, lb.h, B.rows, Nb, 1, part_b, zb, sa ? &lb.gZb_lo : nullptr,
                        sa ? &lb.gZb_lo : nullptr)))
             return st;
-        k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_b, zb, lb.h, 1, nullptr, 1.0 / Nb, 0.0, 0.0, 0,
-                                                         h->fac[KFAC_B_BDY][l - 1], beta, h->status);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_factor_reduce>(h, s, ceil_div_u(nn, EW), 0, part_b, zb, lb.h, 1, nullptr, 1.0 / Nb, 0.0, 0.0, 0,
+                                     h->fac[KFAC_B_BDY][l - 1], beta, h->status));
     }
     // ---- input factors A_l and gradients of layers 2..L ---------------------
     for (int l = 2; l <= L; l++) {
@@ -1403,38 +1494,32 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
         // interior A_l
         if (reduce) {
             long long cnt = (long long)I.N_pad * ti.hp;
-            k_sum_over_s<<<ceil_div_u(cnt, EW), EW, 0, s>>>(ti.T_hi, sa ? ti.T_lo : nullptr, I.N_pad, S, ti.hp,
-                                                             1.f / S, I.red_a, sa ? I.red_a_lo : nullptr);
-            KFAC_LAUNCH_CHECK(h);
+            KFAC_TRY(KL<k_sum_over_s>(h, s, ceil_div_u(cnt, EW), 0, ti.T_hi, sa ? ti.T_lo : nullptr, I.N_pad, S,
+                                      ti.hp, 1.f / S, I.red_a, sa ? I.red_a_lo : nullptr));
             if ((st = gram(h, s, I.gRa[l - 2], I.gRa[l - 2], hin, hin, I.N_pad, N, 1, part_i, zi,
                            sa ? &I.gRa_lo[l - 2] : nullptr, sa ? &I.gRa_lo[l - 2] : nullptr)))
                 return st;
-            k_colsum<<<ceil_div_u(hin, 32), RED_THREADS, 0, s>>>(I.red_a, sa ? I.red_a_lo : nullptr, ti.hp, 0, N, hin,
-                                                                  cs_i);
-            KFAC_LAUNCH_CHECK(h);
-            k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_i, zi, hin, 1, cs_i, 1.0 / N, 1.0 / ((double)N * S),
-                                                             1.0 / ((double)S * S), 1, h->fac[KFAC_A_INT][l - 1], beta,
-                                                             h->status);
+            KFAC_TRY(KL<k_colsum>(h, s, ceil_div_u(hin, 32), 0, I.red_a, sa ? I.red_a_lo : nullptr, ti.hp, 0, N, hin,
+                                  cs_i));
+            KFAC_TRY(KL<k_factor_reduce>(h, s, ceil_div_u(nn, EW), 0, part_i, zi, hin, 1, cs_i, 1.0 / N,
+                                         1.0 / ((double)N * S), 1.0 / ((double)S * S), 1, h->fac[KFAC_A_INT][l - 1],
+                                         beta, h->status));
         } else {
             if ((st = gram(h, s, ti.gT, ti.gT, hin, hin, I.rows, S * N, 1, part_i, zi, sa ? &ti.gT_lo : nullptr,
                            sa ? &ti.gT_lo : nullptr)))
                 return st;
-            k_colsum<<<ceil_div_u(hin, 32), RED_THREADS, 0, s>>>(ti.T_hi, ti.T_lo, ti.hp, 0, N, hin, cs_i);
-            KFAC_LAUNCH_CHECK(h);
+            KFAC_TRY(KL<k_colsum>(h, s, ceil_div_u(hin, 32), 0, ti.T_hi, ti.T_lo, ti.hp, 0, N, hin, cs_i));
             double sc = 1.0 / ((double)N * S);
-            k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_i, zi, hin, 1, cs_i, sc, sc, 1.0 / S, 1,
-                                                             h->fac[KFAC_A_INT][l - 1], beta, h->status);
+            KFAC_TRY(KL<k_factor_reduce>(h, s, ceil_div_u(nn, EW), 0, part_i, zi, hin, 1, cs_i, sc, sc, 1.0 / S, 1,
+                                         h->fac[KFAC_A_INT][l - 1], beta, h->status));
         }
-        KFAC_LAUNCH_CHECK(h);
         // boundary A_l
         if ((st = gram(h, s, tb.gT, tb.gT, hin, hin, B.rows, Nb, 1, part_b, zb, sa ? &tb.gT_lo : nullptr,
                        sa ? &tb.gT_lo : nullptr)))
             return st;
-        k_colsum<<<ceil_div_u(hin, 32), RED_THREADS, 0, s>>>(tb.T_hi, tb.T_lo, tb.hp, 0, Nb, hin, cs_b);
-        KFAC_LAUNCH_CHECK(h);
-        k_factor_reduce<<<ceil_div_u(nn, EW), EW, 0, s>>>(part_b, zb, hin, 1, cs_b, 1.0 / Nb, 1.0 / Nb, 1.0, 1,
-                                                         h->fac[KFAC_A_BDY][l - 1], beta, h->status);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_colsum>(h, s, ceil_div_u(hin, 32), 0, tb.T_hi, tb.T_lo, tb.hp, 0, Nb, hin, cs_b));
+        KFAC_TRY(KL<k_factor_reduce>(h, s, ceil_div_u(nn, EW), 0, part_b, zb, hin, 1, cs_b, 1.0 / Nb, 1.0 / Nb, 1.0,
+                                     1, h->fac[KFAC_A_BDY][l - 1], beta, h->status));
         // gradient of layer l
         if (l < L) {
             MxLayer& gi = I.lay[l - 1];
@@ -1446,19 +1531,15 @@ kfac_status_t factors_and_grad(kfac_pinn_handle* h, cudaStream_t s, const double
             if ((st = gram(h, s, gb.gGr, tb.gT, hout, hin, B.rows, Nb, 0, part_b, zb, sa ? &gb.gGr_lo : nullptr,
                            sa ? &tb.gT_lo : nullptr)))
                 return st;
-            k_colsum<<<ceil_div_u(hout, 32), RED_THREADS, 0, s>>>(gi.Gr, gi.Gr_lo, gi.hp, 0, N, hout, cs_i);
-            KFAC_LAUNCH_CHECK(h);
-            k_colsum<<<ceil_div_u(hout, 32), RED_THREADS, 0, s>>>(gb.Gr, gb.Gr_lo, gb.hp, 0, Nb, hout, cs_b);
-            KFAC_LAUNCH_CHECK(h);
-            k_grad_reduce<<<ceil_div_u((long long)hout * (hin + 1), EW), EW, 0, s>>>(
-                part_i, zi, part_b, zb, hout, hin, cs_i, cs_b, 1.0 / N, 1.0 / Nb, h->grad + h->woff[l - 1]);
-            KFAC_LAUNCH_CHECK(h);
+            KFAC_TRY(KL<k_colsum>(h, s, ceil_div_u(hout, 32), 0, gi.Gr, gi.Gr_lo, gi.hp, 0, N, hout, cs_i));
+            KFAC_TRY(KL<k_colsum>(h, s, ceil_div_u(hout, 32), 0, gb.Gr, gb.Gr_lo, gb.hp, 0, Nb, hout, cs_b));
+            KFAC_TRY(KL<k_grad_reduce>(h, s, ceil_div_u((long long)hout * (hin + 1), EW), 0, part_i, zi, part_b, zb,
+                                       hout, hin, cs_i, cs_b, 1.0 / N, 1.0 / Nb, h->grad + h->woff[l - 1]));
         } else {
-            k_last_layer_terms<<<ceil_div_u(hin + 1, 32), RED_THREADS, 0, s>>>(
-                ti.T_hi, ti.T_lo, tb.T_hi, tb.T_lo, h->in.r, h->bd.r, N, I.N_pad, Nb, B.N_pad, hin, ti.hp, S,
-                h->cT, h->cD, reduce, h->grad + h->woff[L - 1], h->fac[KFAC_B_INT][L - 1],
-                h->fac[KFAC_B_BDY][L - 1], beta, h->status, sa ? 1 : 0);
-            KFAC_LAUNCH_CHECK(h);
+            KFAC_TRY(KL<k_last_layer_terms>(h, s, ceil_div_u(hin + 1, 32), 0, ti.T_hi, ti.T_lo, tb.T_hi, tb.T_lo,
+                                            h->in.r, h->bd.r, N, I.N_pad, Nb, B.N_pad, hin, ti.hp, S, h->cT, h->cD,
+                                            reduce, h->grad + h->woff[L - 1], h->fac[KFAC_B_INT][L - 1],
+                                            h->fac[KFAC_B_BDY][L - 1], beta, h->status, sa ? 1 : 0));
         }
     }
     return KFAC_OK;
@@ -1612,9 +1693,8 @@ kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const d
     KFAC_CUDA_TRY(cudaStreamWaitEvent(m->side, m->fork, 0));
     st = forward_pass(h, m->side, theta, X_bdy, N_bdy, m->bd, sb);
     if (st == KFAC_OK) {
-        k_residual_mx<<<ceil_div_u(N_bdy, EW), EW, 0, m->side>>>(m->bd.zl, g, h->bd.r, N_bdy, m->bd.N_pad, 1, 0,
-                                                                 h->cT, h->cD);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_residual_mx>(h, m->side, ceil_div_u(N_bdy, EW), 0, m->bd.zl, g, h->bd.r, N_bdy, m->bd.N_pad, 1,
+                                   0, h->cT, h->cD));
     }
     // the join is recorded even after an error, so that s never runs ahead of the side stream
     KFAC_CUDA_TRY(cudaEventRecord(m->join, m->side));
@@ -1632,9 +1712,8 @@ kfac_status_t forward_and_residuals(kfac_pinn_handle* h, cudaStream_t s, const d
     si.split_all = split;
     st = forward_pass(h, s, theta, X_int, N_int, m->in, si);
     if (st == KFAC_OK) {
-        k_residual_mx<<<ceil_div_u(N_int, EW), EW, 0, s>>>(m->in.zl, f, h->in.r, N_int, m->in.N_pad, S, 1, h->cT,
-                                                            h->cD);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_residual_mx>(h, s, ceil_div_u(N_int, EW), 0, m->in.zl, f, h->in.r, N_int, m->in.N_pad, S, 1,
+                                   h->cT, h->cD));
     }
     KFAC_CUDA_TRY(cudaStreamWaitEvent(s, m->join, 0));
     return st;
@@ -1678,9 +1757,8 @@ kfac_status_t tc_forward_laplacian(kfac_pinn_handle* h, cudaStream_t s, const do
     all.split_time = (h->cfg.op == KFAC_OP_HEAT) ? 1 : 0;
     all.split_all = is_split_all(h) ? 1 : 0;
     if ((st = forward_pass(h, s, theta, X, N, m->in, all))) return st;
-    k_extract_mx<<<ceil_div_u(N, EW), EW, 0, s>>>(m->in.zl, N, m->in.N_pad, m->in.S, h->dims[0], m->Qf, u, grad,
-                                                   lap);
-    KFAC_LAUNCH_CHECK(h);
+    KFAC_TRY(KL<k_extract_mx>(h, s, ceil_div_u(N, EW), 0, m->in.zl, N, m->in.N_pad, m->in.S, h->dims[0], m->Qf, u,
+                              grad, lap));
     return KFAC_OK;
 }
 
@@ -1699,8 +1777,8 @@ kfac_status_t tc_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s,
     all.split_time = heat;
     all.split_all = is_split_all(h) ? 1 : 0;
     if ((st = forward_pass(h, s, theta, X, N, I, all))) return st;
-    k_seed_mx<<<ceil_div_u((long long)S * I.N_pad, EW), EW, 0, s>>>(m->seed, N, I.N_pad, S, m->Qf, du, dgrad, dlap);
-    KFAC_LAUNCH_CHECK(h);
+    KFAC_TRY(KL<k_seed_mx>(h, s, ceil_div_u((long long)S * I.N_pad, EW), 0, m->seed, N, I.N_pad, S, m->Qf, du, dgrad,
+                           dlap));
     if ((st = backward_pass(h, s, nullptr, N, I, m->seed))) return st;
     // gradient of every layer into the handle's gradient buffer, then into dtheta
     double* G = h->grad;
@@ -1709,13 +1787,11 @@ kfac_status_t tc_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s,
     int z = 0;
     {
         MxLayer& l1 = I.lay[0];
-        k_grad_layer1<<<dim3(ceil_div_u(l1.h, 32), d + 1), RED_THREADS, 0, s>>>(
-            l1.Gr, l1.Gr, I.Xf, I.Xf, N, I.N_pad, 0, d, l1.h, l1.hp, S, 1.0, 0.0, G + h->woff[0], m->gtan,
-            l1.Gr_lo, l1.Gr_lo);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_grad_layer1>(h, s, dim3(ceil_div_u(l1.h, 32), d + 1), 0, l1.Gr, l1.Gr, I.Xf, I.Xf, N, I.N_pad,
+                                   0, d, l1.h, l1.hp, S, 1.0, 0.0, G + h->woff[0], m->gtan, l1.Gr_lo, l1.Gr_lo));
         if (m->gtan) {
-            k_rotate_grad1<<<ceil_div_u((long long)l1.h * d, EW), EW, 0, s>>>(m->gtan, m->Qf, l1.h, d, G + h->woff[0]);
-            KFAC_LAUNCH_CHECK(h);
+            KFAC_TRY(KL<k_rotate_grad1>(h, s, ceil_div_u((long long)l1.h * d, EW), 0, m->gtan, m->Qf, l1.h, d,
+                                        G + h->woff[0]));
         }
     }
     for (int l = 2; l <= L - 1; l++) {
@@ -1725,27 +1801,20 @@ kfac_status_t tc_forward_laplacian_backward(kfac_pinn_handle* h, cudaStream_t s,
         if ((st = gram(h, s, gi.gGr, ti.gT, gi.h, ti.h, I.rows, S * N, 0, part, z, sa ? &gi.gGr_lo : nullptr,
                        sa ? &ti.gT_lo : nullptr)))
             return st;
-        k_colsum<<<ceil_div_u(gi.h, 32), RED_THREADS, 0, s>>>(gi.Gr, sa ? gi.Gr_lo : nullptr, gi.hp, 0, N, gi.h, cs);
-        KFAC_LAUNCH_CHECK(h);
-        k_grad_reduce<<<ceil_div_u((long long)gi.h * (ti.h + 1), EW), EW, 0, s>>>(part, z, part, 0, gi.h, ti.h, cs, cs,
-                                                                                  1.0, 0.0, G + h->woff[l - 1]);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_colsum>(h, s, ceil_div_u(gi.h, 32), 0, gi.Gr, sa ? gi.Gr_lo : nullptr, gi.hp, 0, N, gi.h, cs));
+        KFAC_TRY(KL<k_grad_reduce>(h, s, ceil_div_u((long long)gi.h * (ti.h + 1), EW), 0, part, z, part, 0, gi.h,
+                                   ti.h, cs, cs, 1.0, 0.0, G + h->woff[l - 1]));
     }
     {
         MxLayer& ti = I.lay[L - 2];
-        k_last_grad_seeded<<<ceil_div_u(ti.h + 1, 32), RED_THREADS, 0, s>>>(ti.T_hi, ti.T_lo, m->seed, N, I.N_pad, ti.h,
-                                                                            ti.hp, S, heat && S > 2,
-                                                                            is_split_all(h) ? 1 : 0,
-                                                                            G + h->woff[L - 1]);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_last_grad_seeded>(h, s, ceil_div_u(ti.h + 1, 32), 0, ti.T_hi, ti.T_lo, m->seed, N, I.N_pad,
+                                        ti.h, ti.hp, S, heat && S > 2, is_split_all(h) ? 1 : 0, G + h->woff[L - 1]));
     }
-    k_copy_or_add<<<ceil_div_u(h->D, EW), EW, 0, s>>>(dtheta, G, h->D, accumulate ? 1 : 0);
-    KFAC_LAUNCH_CHECK(h);
+    KFAC_TRY(KL<k_copy_or_add>(h, s, ceil_div_u(h->D, EW), 0, dtheta, G, h->D, accumulate ? 1 : 0));
     if (dX) {
         const MxLayer& l1 = I.lay[0];
-        k_dX_mx<<<N, 128, sizeof(float) * l1.hp, s>>>(l1.Zb, is_split_all(h) ? l1.Zb_lo : nullptr, N, l1.hp, l1.h,
-                                                       d, m->w.W1f, dX);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_dX_mx>(h, s, N, sizeof(float) * l1.hp, l1.Zb, is_split_all(h) ? l1.Zb_lo : nullptr, N, l1.hp,
+                             l1.h, d, m->w.W1f, dX));
     }
     return KFAC_OK;
 }
@@ -1778,11 +1847,10 @@ kfac_status_t jdot_pass(kfac_pinn_handle* h, cudaStream_t s, MxPass& P, int N, b
         } else {
             sel.nsel = 1;
         }
-        k_last_fwd<<<ceil_div_u((long long)sel.nsel * P.N_pad * 32, EW), EW, 0, s>>>(last.T_hi, last.T_lo, m->dw.wL,
-                                                                                     P.N_pad, S, last.hp, sel, P.zl);
-        KFAC_LAUNCH_CHECK(h);
-        k_residual_jvp_mx<<<ceil_div_u(N, EW), EW, 0, s>>>(P.zl, jv, N, P.N_pad, S, interior ? 1 : 0, h->cT, h->cD);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_last_fwd>(h, s, ceil_div_u((long long)sel.nsel * P.N_pad * 32, EW), 0, last.T_hi, last.T_lo,
+                                m->dw.wL, P.N_pad, S, last.hp, sel, P.zl));
+        KFAC_TRY(KL<k_residual_jvp_mx>(h, s, ceil_div_u(N, EW), 0, P.zl, jv, N, P.N_pad, S, interior ? 1 : 0, h->cT,
+                                       h->cD));
     }
     // hidden layers 2..L-1 on the tensor cores
     const long long part_cap = (long long)MAX_CHUNKS * m->in.N_pad * m->hp_max;
@@ -1813,16 +1881,14 @@ kfac_status_t jdot_pass(kfac_pinn_handle* h, cudaStream_t s, MxPass& P, int N, b
         if ((st = launch_engine<tck::JDOT>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_LAYER_GEMM, alg,
                                            fl * (S + 2 * split_rows))))
             return st;
-        k_jdot_reduce<<<ceil_div_u(N, EW), EW, 0, s>>>(m->part, slots, N, P.N_pad, jv);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_jdot_reduce>(h, s, ceil_div_u(N, EW), 0, m->part, slots, N, P.N_pad, jv));
     }
     // first layer
     {
         MxLayer& l1 = P.lay[0];
         const float* V1t = m->dw.W1Qf ? m->dw.W1Qf : m->dw.W1f;
-        k_jdot_layer1<<<N, 256, 0, s>>>(m->dw.W1f, V1t, P.Xf, l1.Zb, split ? l1.Zb_lo : nullptr, N, P.N_pad, d,
-                                        l1.hp, S, jv);
-        KFAC_LAUNCH_CHECK(h);
+        KFAC_TRY(KL<k_jdot_layer1>(h, s, N, 0, m->dw.W1f, V1t, P.Xf, l1.Zb, split ? l1.Zb_lo : nullptr, N, P.N_pad, d,
+                                   l1.hp, S, jv));
     }
     return KFAC_OK;
 }
