@@ -24,6 +24,7 @@
 #include <math.h>
 #include <vector>
 #include <algorithm>
+#include <map>
 #include <cooperative_groups.h>
 
 #include "kfac_internal.cuh"
@@ -126,15 +127,18 @@ struct EigState {
     int* clu_prob;              // problem of each cluster, largest first
 };
 
-// The factor pairs in up to two groups run on two streams: the largest
-// problems (whose latency-bound stages, such as the cluster
-// tridiagonalisation, hold only part of the GPU) and the rest, which fills the
-// idle SMs meanwhile.
+// The factor pairs form one group per cluster size of the tridiagonalisation
+// (the size follows from n alone: trc_cluster_size), each group one sequence
+// of batched kernels, the groups on streams of their own: the largest
+// problems' latency-bound stages hold only part of the GPU, and the smaller
+// problems fill the idle SMs meanwhile.
+constexpr int MAX_GROUPS = 6;    // cluster sizes 16, 8, 4, 2, 1 and the cooperative kernel
+
 struct EigAll {
-    EigState* g[2];
+    EigState* g[MAX_GROUPS];
     int ng;
-    cudaStream_t side;
-    cudaEvent_t fork, join;
+    cudaStream_t side[MAX_GROUPS - 1];   // groups 1.. run on these, forked from the caller's stream
+    cudaEvent_t fork, join[MAX_GROUPS - 1];
 };
 
 EigAll* EA(kfac_pinn_handle* h) { return (EigAll*)h->eig; }
@@ -668,7 +672,7 @@ __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, 
 }
 
 // The same reduction with the lower triangle of M held in the distributed
-// shared memory of one thread-block cluster per problem (up to 16 CTAs).  CTA
+// shared memory of one thread-block cluster per problem (CL = 1..16 CTAs).  CTA
 // c of the cluster owns rows r = c + CL*t, t = 0, 1, ..., each stored as its
 // columns 0..r, packed one row after another.  Per column k (b = k + 1):
 //   - gather the pivot column x = M[b.., k] from its owners and form the
@@ -689,7 +693,7 @@ __global__ void __launch_bounds__(512) k_tridiag(Prob* pr, const int* cta_prob, 
 // the cluster's barriers are hardware barriers that every CTA reaches in the
 // same order (all control flow is uniform over the cluster).
 constexpr int TRC_THREADS = 512;
-constexpr int TRC_CL = 16;    // CTAs per cluster (a non-portable cluster size)
+constexpr int TRC_CL = 16;    // most CTAs per cluster (a non-portable cluster size)
 constexpr int TRC_RED = TRC_THREADS + 8;   // reduction scratch: one slot per thread + scalars
 constexpr int TRC_TK = TRC_THREADS, TRC_SCALE = TRC_THREADS + 1, TRC_K = TRC_THREADS + 3;
 
@@ -727,12 +731,12 @@ __host__ __device__ inline long long trc_off(int t, int c, int cl) {
 // column.  A pivot that is not positive and finite stops every CTA of the
 // cluster at the same column (they all see the same pushed value) and marks
 // the problem failed.
+template <int CL>
 __global__ void __launch_bounds__(TRC_THREADS, 1) k_chol_cluster(Prob* pr, const int* clu_prob, int lds, int nmax,
                                                                  int* fail) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ double trc_sm[];
-    constexpr int CL = TRC_CL;
     const int c = (int)cl.block_rank();
     const int pi = clu_prob[blockIdx.x / CL];
     const Prob p = pr[pi];
@@ -817,12 +821,12 @@ __global__ void __launch_bounds__(TRC_THREADS, 1) k_chol_cluster(Prob* pr, const
     }
 }
 
+template <int CL>
 __global__ void __launch_bounds__(TRC_THREADS, 1) k_tridiag_cluster(Prob* pr, const int* clu_prob, int lds, int nmax,
                                                                     int rmax, int* fail) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ double trc_sm[];
-    constexpr int CL = TRC_CL;
     const int c = (int)cl.block_rank();
     const int pi = clu_prob[blockIdx.x / CL];
     if (fail[pi]) return;   // uniform over the cluster, before any barrier
@@ -1720,6 +1724,79 @@ int ceil_log2(int n) {
 
 static int pair_n(const kfac_pinn_handle* h, int l, int which) { return which == 0 ? h->dims[l - 1] + 1 : h->dims[l]; }
 
+// Packed triangle length of the CTA that stores the most of an n-problem in a
+// cluster of CL CTAs, and the cluster kernels' shared memory per CTA.
+static int trc_lds(int n, int CL) {
+    int lds = 0;
+    for (int c = 0; c < CL && c < n; c++) lds = std::max(lds, (int)trc_off((n - c + CL - 1) / CL, c, CL));
+    return lds;
+}
+
+static size_t trc_smem_bytes(int lds, int nmax, int CL) {
+    const int rmax = (nmax + CL - 1) / CL;
+    return sizeof(double) * ((size_t)lds + 5 * (size_t)nmax + (size_t)(CL + 1) * rmax + CL + TRC_RED);
+}
+
+// Cluster size of a problem of size n: the largest power of two up to 16 that
+// leaves every CTA at least 16K of the triangle's n^2 / 2 elements (per
+// column, a CTA's FP64 work then outweighs the latency of the cluster
+// barriers, so small problems take few SMs and many of them run side by
+// side), raised until the triangle fits in the cluster's shared memory (0: it
+// does not fit in 16 CTAs).
+static int trc_cluster_size(int n, size_t smem_optin) {
+    int cl = 1;
+    while (2 * cl <= TRC_CL && 2.0 * cl * 32768.0 <= (double)n * n) cl *= 2;
+    while (cl <= TRC_CL && trc_smem_bytes(trc_lds(n, cl), n, cl) > smem_optin) cl *= 2;
+    return cl <= TRC_CL ? cl : 0;
+}
+
+// f(std::integral_constant<int, CL>) for the cluster sizes the kernels are
+// built for.
+template <class F>
+static cudaError_t with_cluster_size(int cl, F&& f) {
+    switch (cl) {
+        case 1: return f(std::integral_constant<int, 1>{});
+        case 2: return f(std::integral_constant<int, 2>{});
+        case 4: return f(std::integral_constant<int, 4>{});
+        case 8: return f(std::integral_constant<int, 8>{});
+        case 16: return f(std::integral_constant<int, 16>{});
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+static cudaError_t trc_cluster_attributes(int cl, int optin) {
+    return with_cluster_size(cl, [&](auto c) {
+        constexpr int C = decltype(c)::value;
+        cudaFuncSetAttribute(k_tridiag_cluster<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(k_tridiag_cluster<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        cudaFuncSetAttribute(k_chol_cluster<C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        return cudaFuncSetAttribute(k_chol_cluster<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    });
+}
+
+static cudaLaunchConfig_t trc_config(cudaLaunchAttribute* attr, int cl, int np, size_t smem, cudaStream_t s) {
+    attr->id = cudaLaunchAttributeClusterDimension;
+    attr->val.clusterDim.x = cl;
+    attr->val.clusterDim.y = 1;
+    attr->val.clusterDim.z = 1;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cl * np);
+    lc.blockDim = dim3(TRC_THREADS);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return lc;
+}
+
+static cudaError_t trc_max_clusters(int cl, int np, size_t smem, int* clusters) {
+    cudaLaunchAttribute attr;
+    const cudaLaunchConfig_t lc = trc_config(&attr, cl, np, smem, nullptr);
+    return with_cluster_size(cl, [&](auto c) {
+        return cudaOccupancyMaxActiveClusters(clusters, k_tridiag_cluster<decltype(c)::value>, &lc);
+    });
+}
+
 static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es);
 
 // One group of factor pairs (layer, 0: A / 1: B) of one handle solved by one
@@ -1853,55 +1930,36 @@ static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es) {
         cudaMemcpy(es->trsm_jobs, jobs.data(), sizeof(TrsmJob) * jobs.size(), cudaMemcpyHostToDevice);
     }
 
-    // cluster tridiagonalisation: one 16-CTA cluster per problem when the
-    // largest problem's lower triangle fits in the cluster's shared memory
+    // cluster tridiagonalisation: one cluster per problem when the problems'
+    // lower triangles fit in the cluster's shared memory (the group's
+    // problems share one cluster size)
     es->trc_cl = 0;
     es->clu_prob = nullptr;
     {
-        const int CL = TRC_CL;
-        int lds = 0;
-        for (int i = 0; i < es->np; i++) {
-            const int n = es->host[i].n;
-            for (int c = 0; c < CL && c < n; c++) {
-                const int R = (n - c + CL - 1) / CL;
-                lds = std::max(lds, (int)trc_off(R, c, CL));
-            }
-        }
-        const int rmax = (es->nmax + CL - 1) / CL;
-        const size_t smem = sizeof(double) * ((size_t)lds + 5 * (size_t)es->nmax + (size_t)(CL + 1) * rmax + CL + TRC_RED);
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-        if (smem <= (size_t)optin) {
-            cudaFuncSetAttribute(k_tridiag_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            cudaFuncSetAttribute(k_tridiag_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-            cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-            cudaLaunchAttribute attr;
-            attr.id = cudaLaunchAttributeClusterDimension;
-            attr.val.clusterDim.x = CL;
-            attr.val.clusterDim.y = 1;
-            attr.val.clusterDim.z = 1;
-            cudaLaunchConfig_t lc = {};
-            lc.gridDim = dim3(CL * es->np);
-            lc.blockDim = dim3(TRC_THREADS);
-            lc.dynamicSmemBytes = smem;
-            lc.attrs = &attr;
-            lc.numAttrs = 1;
-            int clusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&clusters, k_tridiag_cluster, &lc) == cudaSuccess && clusters >= 1) {
-                std::vector<int> order(es->np);
-                for (int i = 0; i < es->np; i++) order[i] = i;
-                std::stable_sort(order.begin(), order.end(),
-                                 [&](int x, int y) { return es->host[x].n > es->host[y].n; });
-                if ((st = dal(&es->clu_prob, order.size()))) return st;
-                cudaMemcpy(es->clu_prob, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice);
-                es->trc_cl = CL;
-                es->trc_lds = lds;
-                es->trc_rmax = rmax;
-                es->trc_smem = smem;
-            }
-            cudaGetLastError();   // a refused configuration only selects the cooperative kernel
+        const int CL = trc_cluster_size(es->nmax, (size_t)optin);
+        int lds = 0, rmax = 0;
+        size_t smem = 0;
+        if (CL > 0) {
+            for (const Prob& p : es->host) lds = std::max(lds, trc_lds(p.n, CL));
+            rmax = (es->nmax + CL - 1) / CL;
+            smem = trc_smem_bytes(lds, es->nmax, CL);
         }
+        int clusters = 0;
+        if (CL > 0 && trc_cluster_attributes(CL, optin) == cudaSuccess &&
+            trc_max_clusters(CL, es->np, smem, &clusters) == cudaSuccess && clusters >= 1) {
+            std::vector<int> order(es->np);
+            for (int i = 0; i < es->np; i++) order[i] = i;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return es->host[x].n > es->host[y].n; });
+            if ((st = dal(&es->clu_prob, order.size()))) return st;
+            cudaMemcpy(es->clu_prob, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice);
+            es->trc_cl = CL;
+            es->trc_lds = lds;
+            es->trc_rmax = rmax;
+            es->trc_smem = smem;
+        }
+        cudaGetLastError();   // a refused configuration only selects the cooperative kernel
     }
     if (es->trc_cl == 0 && !coop_fits) return KFAC_BAD_ARG;
 
@@ -2016,19 +2074,12 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
     // 1. Cholesky: one cluster per problem, or the blocked kernels
     if (es->trc_cl > 0) {
         cudaLaunchAttribute attr;
-        attr.id = cudaLaunchAttributeClusterDimension;
-        attr.val.clusterDim.x = es->trc_cl;
-        attr.val.clusterDim.y = 1;
-        attr.val.clusterDim.z = 1;
-        cudaLaunchConfig_t lc = {};
-        lc.gridDim = dim3(es->trc_cl * np);
-        lc.blockDim = dim3(TRC_THREADS);
-        lc.dynamicSmemBytes = sizeof(double) * ((size_t)es->trc_lds + 3 * (size_t)nmax + 8);
-        lc.stream = s;
-        lc.attrs = &attr;
-        lc.numAttrs = 1;
-        KFAC_CUDA_TRY(cudaLaunchKernelEx(&lc, k_chol_cluster, (Prob*)pr, (const int*)es->clu_prob, es->trc_lds, nmax,
-                                         (int*)es->fail));
+        const cudaLaunchConfig_t lc =
+            trc_config(&attr, es->trc_cl, np, sizeof(double) * ((size_t)es->trc_lds + 3 * (size_t)nmax + 8), s);
+        KFAC_CUDA_TRY(with_cluster_size(es->trc_cl, [&](auto c) {
+            return cudaLaunchKernelEx(&lc, k_chol_cluster<decltype(c)::value>, (Prob*)pr, (const int*)es->clu_prob,
+                                      es->trc_lds, nmax, (int*)es->fail);
+        }));
         h->launches++;
     }
     for (int kb = 0; es->trc_cl == 0 && kb < nblk; kb++) {
@@ -2056,19 +2107,11 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
     // 3. tridiagonalisation: one cluster per problem, or cooperative groups of CTAs
     if (es->trc_cl > 0) {
         cudaLaunchAttribute attr;
-        attr.id = cudaLaunchAttributeClusterDimension;
-        attr.val.clusterDim.x = es->trc_cl;
-        attr.val.clusterDim.y = 1;
-        attr.val.clusterDim.z = 1;
-        cudaLaunchConfig_t lc = {};
-        lc.gridDim = dim3(es->trc_cl * np);
-        lc.blockDim = dim3(TRC_THREADS);
-        lc.dynamicSmemBytes = es->trc_smem;
-        lc.stream = s;
-        lc.attrs = &attr;
-        lc.numAttrs = 1;
-        KFAC_CUDA_TRY(cudaLaunchKernelEx(&lc, k_tridiag_cluster, (Prob*)pr, (const int*)es->clu_prob, es->trc_lds,
-                                         es->nmax, es->trc_rmax, (int*)es->fail));
+        const cudaLaunchConfig_t lc = trc_config(&attr, es->trc_cl, np, es->trc_smem, s);
+        KFAC_CUDA_TRY(with_cluster_size(es->trc_cl, [&](auto c) {
+            return cudaLaunchKernelEx(&lc, k_tridiag_cluster<decltype(c)::value>, (Prob*)pr,
+                                      (const int*)es->clu_prob, es->trc_lds, es->nmax, es->trc_rmax, (int*)es->fail);
+        }));
         h->launches++;
     } else {
         KFAC_CUDA_TRY(cudaMemsetAsync(es->bar, 0, sizeof(unsigned) * 3 * np, s));
@@ -2159,114 +2202,127 @@ kfac_status_t eig_check_wait(kfac_pinn_handle* h, cudaStream_t s, uint64_t limit
 // Factor pairs of size at least 3/4 of the largest form the first group, the
 // rest the second (run on a stream of the handle's own, forked from and joined
 // back into the caller's stream; both are captured when the step is).
+// Class of a factor pair: its cluster size, 0 for the cooperative kernel.
+static int pair_class(int n, const kfac_pinn_handle* h) {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    return trc_cluster_size(n, (size_t)optin);
+}
+
+// The order of the groups: the largest cluster size first (it runs on the
+// caller's stream), the cooperative class last.
+static int class_rank(int cl) { return cl == 0 ? 99 : -cl; }
+
+static kfac_status_t eigall_streams(EigAll* ea) {
+    if (ea->ng < 2) return KFAC_OK;
+    if (cudaEventCreateWithFlags(&ea->fork, cudaEventDisableTiming) != cudaSuccess) return KFAC_CUDA_ERROR;
+    for (int i = 0; i + 1 < ea->ng; i++)
+        if (cudaStreamCreateWithFlags(&ea->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ea->join[i], cudaEventDisableTiming) != cudaSuccess)
+            return KFAC_CUDA_ERROR;
+    return KFAC_OK;
+}
+
 kfac_status_t eig_alloc(kfac_pinn_handle* h) {
     EigAll* ea = new EigAll();
     memset(ea, 0, sizeof(*ea));
     h->eig = ea;
-    int nmax = 0;
+    std::map<int, std::vector<std::pair<int, int>>> byclass;   // class rank -> (layer, which)
     for (int l = 1; l <= h->cfg.L; l++)
-        for (int w = 0; w < 2; w++) nmax = std::max(nmax, pair_n(h, l, w));
-    std::vector<std::pair<int, int>> big, rest;
-    for (int l = 1; l <= h->cfg.L; l++)
-        for (int w = 0; w < 2; w++) (4 * pair_n(h, l, w) >= 3 * nmax ? big : rest).push_back({l, w});
+        for (int w = 0; w < 2; w++) byclass[class_rank(pair_class(pair_n(h, l, w), h))].push_back({l, w});
     kfac_status_t st;
-    ea->g[0] = new EigState();
-    ea->ng = 1;
-    if ((st = group_alloc(h, ea->g[0], big))) return st;
-    if (!rest.empty()) {
-        ea->g[1] = new EigState();
-        ea->ng = 2;
-        if ((st = group_alloc(h, ea->g[1], rest))) return st;
-        if (cudaStreamCreateWithFlags(&ea->side, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ea->fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ea->join, cudaEventDisableTiming) != cudaSuccess)
-            return KFAC_CUDA_ERROR;
+    for (auto& kv : byclass) {
+        EigState* es = new EigState();
+        ea->g[ea->ng++] = es;
+        if ((st = group_alloc(h, es, kv.second))) return st;
     }
-    return KFAC_OK;
+    return eigall_streams(ea);
+}
+
+static void eigall_free(EigAll* ea) {
+    if (!ea) return;
+    eigall_free_streams(ea);
+    for (int i = 0; i < MAX_GROUPS; i++) group_free(ea->g[i]);
+    delete ea;
 }
 
 void eig_free(kfac_pinn_handle* h) {
-    EigAll* ea = EA(h);
-    if (!ea) return;
-    eigall_free_streams(ea);
-    for (int i = 0; i < 2; i++) group_free(ea->g[i]);
-    delete ea;
+    eigall_free(EA(h));
     h->eig = nullptr;
 }
 
 static kfac_status_t eigall_free_streams(EigAll* ea) {
-    if (ea->side) cudaStreamSynchronize(ea->side);
-    if (ea->side) cudaStreamDestroy(ea->side);
+    for (int i = 0; i + 1 < MAX_GROUPS; i++) {
+        if (ea->side[i]) {
+            cudaStreamSynchronize(ea->side[i]);
+            cudaStreamDestroy(ea->side[i]);
+        }
+        if (ea->join[i]) cudaEventDestroy(ea->join[i]);
+        ea->side[i] = nullptr;
+        ea->join[i] = nullptr;
+    }
     if (ea->fork) cudaEventDestroy(ea->fork);
-    if (ea->join) cudaEventDestroy(ea->join);
-    ea->side = nullptr;
-    ea->fork = ea->join = nullptr;
+    ea->fork = nullptr;
     return KFAC_OK;
 }
 
+// Group 0 on s, groups 1.. on the side streams, forked from s and joined back
+// into it (captured with s when s is capturing).
 static kfac_status_t eigall_run(kfac_pinn_handle* h, EigAll* ea, cudaStream_t s) {
     if (ea->ng == 1) return group_run(h, ea->g[0], s);
-    if (ea->g[0]->trc_cl == 0 || ea->g[1]->trc_cl == 0) {
+    bool coop = false;
+    for (int i = 0; i < ea->ng; i++) coop = coop || ea->g[i]->trc_cl == 0;
+    if (coop) {
         // a cooperative tridiagonalisation needs all its CTAs resident at
         // once: nothing runs beside it
-        kfac_status_t st = group_run(h, ea->g[1], s);
-        return st ? st : group_run(h, ea->g[0], s);
+        for (int i = ea->ng - 1; i >= 0; i--) KFAC_TRY(group_run(h, ea->g[i], s));
+        return KFAC_OK;
     }
     KFAC_CUDA_TRY(cudaEventRecord(ea->fork, s));
-    KFAC_CUDA_TRY(cudaStreamWaitEvent(ea->side, ea->fork, 0));
-    kfac_status_t st = group_run(h, ea->g[1], ea->side);
-    // the join is recorded even after an error so that s never runs ahead of side
-    KFAC_CUDA_TRY(cudaEventRecord(ea->join, ea->side));
+    kfac_status_t st = KFAC_OK;
+    for (int i = 1; i < ea->ng; i++) {
+        KFAC_CUDA_TRY(cudaStreamWaitEvent(ea->side[i - 1], ea->fork, 0));
+        if (st == KFAC_OK) st = group_run(h, ea->g[i], ea->side[i - 1]);
+        // the joins are recorded even after an error so that s never runs ahead of a side stream
+        KFAC_CUDA_TRY(cudaEventRecord(ea->join[i - 1], ea->side[i - 1]));
+    }
     if (st == KFAC_OK) st = group_run(h, ea->g[0], s);
-    KFAC_CUDA_TRY(cudaStreamWaitEvent(s, ea->join, 0));
+    for (int i = 1; i < ea->ng; i++) KFAC_CUDA_TRY(cudaStreamWaitEvent(s, ea->join[i - 1], 0));
     return st;
 }
 
 kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) { return eigall_run(h, EA(h), s); }
 
-// The eigensolves of many handles as one pair of groups over the problems'
-// own workspaces: every factor pair of every handle, the pairs of at least 3/4
-// of the largest size in the first group, the rest in the second.
+// The eigensolves of many handles at once over the problems' own workspaces:
+// every factor pair of every handle, one group per cluster size as for a
+// single handle.  A problem is solved by the same kernels with the same
+// cluster size as in its own handle's eigensolve.
 kfac_status_t eig_batch_alloc(kfac_pinn_handle* const* hs, int count, void** out) {
     *out = nullptr;
     if (count < 1) return KFAC_BAD_ARG;
-    std::vector<Prob> all;
+    std::map<int, std::vector<Prob>> byclass;
     for (int i = 0; i < count; i++) {
         EigAll* ea = EA(hs[i]);
         if (!ea) return KFAC_BAD_ARG;
-        for (int g = 0; g < ea->ng; g++) all.insert(all.end(), ea->g[g]->host.begin(), ea->g[g]->host.end());
+        for (int g = 0; g < ea->ng; g++)
+            for (const Prob& p : ea->g[g]->host) byclass[class_rank(pair_class(p.n, hs[0]))].push_back(p);
     }
-    int nmax = 0;
-    for (const Prob& p : all) nmax = std::max(nmax, p.n);
-    std::vector<Prob> big, rest;
-    for (const Prob& p : all) (4 * p.n >= 3 * nmax ? big : rest).push_back(p);
+    if ((int)byclass.size() > MAX_GROUPS) return KFAC_BAD_ARG;
     EigAll* ea = new EigAll();
     memset(ea, 0, sizeof(*ea));
     *out = ea;
     kfac_status_t st;
-    for (std::vector<Prob>* list : {&big, &rest}) {
-        if (list->empty()) continue;
+    for (auto& kv : byclass) {
         EigState* es = new EigState();
         ea->g[ea->ng++] = es;
-        es->host = *list;
+        es->host = kv.second;
         if ((st = group_schedule(hs[0], es))) return st;
     }
-    if (ea->ng == 2 &&
-        (cudaStreamCreateWithFlags(&ea->side, cudaStreamNonBlocking) != cudaSuccess ||
-         cudaEventCreateWithFlags(&ea->fork, cudaEventDisableTiming) != cudaSuccess ||
-         cudaEventCreateWithFlags(&ea->join, cudaEventDisableTiming) != cudaSuccess))
-        return KFAC_CUDA_ERROR;
-    return KFAC_OK;
+    return eigall_streams(ea);
 }
 
 kfac_status_t eig_batch_run(kfac_pinn_handle* h0, void* eb, cudaStream_t s) {
     return eigall_run(h0, (EigAll*)eb, s);
 }
 
-void eig_batch_free(void* eb) {
-    EigAll* ea = (EigAll*)eb;
-    if (!ea) return;
-    eigall_free_streams(ea);
-    for (int i = 0; i < 2; i++) group_free(ea->g[i]);
-    delete ea;
-}
+void eig_batch_free(void* eb) { eigall_free((EigAll*)eb); }

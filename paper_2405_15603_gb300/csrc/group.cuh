@@ -176,9 +176,3 @@ kfac_status_t KL(kfac_pinn_handle* h, cudaStream_t s, dim3 grid, size_t smem, A&
 // Device-to-device copy of `bytes` (a multiple of 8) as a groupable kernel
 // while recording, cudaMemcpyAsync otherwise.
 kfac_status_t group_copy(kfac_pinn_handle* h, cudaStream_t s, void* dst, const void* src, size_t bytes);
-
-#define KFAC_TRY(expr)                  \
-    do {                                \
-        kfac_status_t _st = (expr);     \
-        if (_st != KFAC_OK) return _st; \
-    } while (0)

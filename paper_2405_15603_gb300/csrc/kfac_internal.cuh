@@ -145,6 +145,12 @@ void kfac_record_cuda_error(cudaError_t e);
         }                                                     \
     } while (0)
 
+#define KFAC_TRY(expr)                  \
+    do {                                \
+        kfac_status_t _st = (expr);     \
+        if (_st != KFAC_OK) return _st; \
+    } while (0)
+
 #define KFAC_LAUNCH_CHECK(h)                                  \
     do {                                                      \
         (h)->launches++;                                      \
