@@ -116,6 +116,7 @@ struct EigState {
     int* group;                 // group size per problem
     int n_cta;
     void* trsm_jobs;            // TrsmJob list, largest work first (also the back-transform's)
+    void* trsm_jobs_upper;      // the same jobs ordered by their work in the upper-triangle solve (mode 1)
     int n_trsm_jobs;
     size_t bt_smem;             // back-transform shared memory for the widest job
     std::vector<Level> levels;
@@ -330,7 +331,9 @@ __global__ void __launch_bounds__(256) k_chol_update(Prob* pr, int k0, int* fail
 // --------------------------------------------------------------------------
 // 2/6. column-parallel triangular solves with L
 //   mode 0: X = L^{-1} B,   B = M (row-major),   X -> Qa
-//   mode 1: X = L^{-1} B^T, B = Qa,              X -> M
+//   mode 1: X = L^{-1} B^T, B = Qa,              X -> M   (X is symmetric: only
+//           rows 0..c of column c, the upper triangle, which k_symmetrize
+//           copies to the lower one; a third of the solve's work)
 //   mode 2: X = L^{-T} B,   B = final D&C buffer, X -> V
 // --------------------------------------------------------------------------
 // One column strip [c0, c0 + CB) of a triangular solve with NB x NB blocks.
@@ -354,7 +357,9 @@ __device__ void trsm_strip(const Prob& p, int c0, int mode, bool failed, double*
         return;
     }
     const bool upper = (mode == 2);
-    for (int s = 0; s < nblk; s++) {
+    // mode 1: the row blocks down to the strip's last column
+    const int nrun = (mode == 1) ? min(nblk, (c0 + ncb - 1) / NB + 1) : nblk;
+    for (int s = 0; s < nrun; s++) {
         const int ib = upper ? nblk - 1 - s : s;
         const int r0 = ib * NB, rows = min(NB, n - r0);
         for (int t = threadIdx.x; t < NB * CB; t += blockDim.x) {
@@ -480,6 +485,8 @@ __global__ void __launch_bounds__(256) k_diag_inv(Prob* pr, int* fail) {
     }
 }
 
+// The lower triangle of M = L^{-1} Q L^{-T} from its upper one (the only one
+// the second solve computes).
 __global__ void k_symmetrize(Prob* pr, int* fail) {
     const Prob p = pr[blockIdx.y];
     const int n = p.n;
@@ -487,11 +494,7 @@ __global__ void k_symmetrize(Prob* pr, int* fail) {
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)n * n;
          t += (long long)gridDim.x * blockDim.x) {
         int r = (int)(t / n), c = (int)(t % n);
-        if (r < c) {
-            double a = 0.5 * (p.M[(long long)r * n + c] + p.M[(long long)c * n + r]);
-            p.M[(long long)r * n + c] = a;
-            p.M[(long long)c * n + r] = a;
-        }
+        if (r > c) p.M[(long long)r * n + c] = p.M[(long long)c * n + r];
     }
 }
 
@@ -1928,6 +1931,15 @@ static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es) {
         kfac_status_t ast = kfac_device_alloc(&es->trsm_jobs, sizeof(TrsmJob) * jobs.size());
         if (ast != KFAC_OK) return ast;
         cudaMemcpy(es->trsm_jobs, jobs.data(), sizeof(TrsmJob) * jobs.size(), cudaMemcpyHostToDevice);
+        // the upper-triangle solve of a strip runs down to its last column
+        auto upper_work = [&](const TrsmJob& j) {
+            const double e = std::min(es->host[j.prob].n, j.c0 + j.cb);
+            return e * e * j.cb;
+        };
+        std::stable_sort(jobs.begin(), jobs.end(),
+                         [&](const TrsmJob& x, const TrsmJob& y) { return upper_work(x) > upper_work(y); });
+        if ((ast = kfac_device_alloc(&es->trsm_jobs_upper, sizeof(TrsmJob) * jobs.size())) != KFAC_OK) return ast;
+        cudaMemcpy(es->trsm_jobs_upper, jobs.data(), sizeof(TrsmJob) * jobs.size(), cudaMemcpyHostToDevice);
     }
 
     // cluster tridiagonalisation: one cluster per problem when the problems'
@@ -2055,6 +2067,7 @@ static void group_free(EigState* es) {
     cudaFree(es->group);
     cudaFree(es->clu_prob);
     cudaFree(es->trsm_jobs);
+    cudaFree(es->trsm_jobs_upper);
     for (auto& lv : es->levels) {
         cudaFree(lv.merges);
         cudaFree(lv.gemms);
@@ -2100,7 +2113,7 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
     const int smem_trsm = (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB_MAX + 1));
     k_trsm<<<es->n_trsm_jobs, 256, smem_trsm, s>>>(pr, (const TrsmJob*)es->trsm_jobs, 0, es->fail);
     KFAC_LAUNCH_CHECK(h);
-    k_trsm<<<es->n_trsm_jobs, 256, smem_trsm, s>>>(pr, (const TrsmJob*)es->trsm_jobs, 1, es->fail);
+    k_trsm<<<es->n_trsm_jobs, 256, smem_trsm, s>>>(pr, (const TrsmJob*)es->trsm_jobs_upper, 1, es->fail);
     KFAC_LAUNCH_CHECK(h);
     k_symmetrize<<<dim3(64, np), 256, 0, s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
