@@ -161,6 +161,40 @@ def make_batches(n, seed_base):
 # ---------------------------------------------------------------------------
 # CUDA arm
 # ---------------------------------------------------------------------------
+def profile_traffic(points):
+    """DRAM traffic per step and kernel class from the ncu capture summarised in
+    profiles/ (lines `traffic class=C bytes_per_step=B points=P scales=0|1
+    sha256=H sources=F1,F2`): kept only while the sha256 of the named kernel
+    sources still matches (null once a kernel changed since the capture).
+    Classes whose traffic grows with the point count are scaled from the
+    captured point count P to `points`."""
+    import glob
+    import hashlib
+    import re
+    out = {}
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            m = re.match(r"\s*traffic class=(\w+) bytes_per_step=([\d.e+]+) points=(\d+) scales=([01]) "
+                         r"sha256=([0-9a-f]+) sources=(\S+)", line)
+            if not m:
+                continue
+            h = hashlib.sha256()
+            for f in m.group(6).split(","):
+                fp = os.path.join(ROOT, f)
+                if not os.path.exists(fp):
+                    h = None
+                    break
+                h.update(open(fp, "rb").read())
+            if h is None or h.hexdigest() != m.group(5):
+                continue
+            b = float(m.group(2))
+            if m.group(4) == "1":
+                b *= points / int(m.group(3))
+            out[m.group(1)] = {"bytes": b, "source": os.path.relpath(path, ROOT) +
+                               ("" if m.group(4) == "0" else f" (scaled from {m.group(3)} to {points} points)")}
+    return out
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2405_15603_gb300 import build as _build
@@ -311,6 +345,8 @@ def run_gpu(args, rank, world, local_rank):
     peaks, peak_kind = load_peaks()
     alu = measure_alu_peaks(dev)
 
+    traffic = profile_traffic(WORKLOAD.n_int + WORKLOAD.n_bdy)
+
     def class_roofline(name, rec):
         per_launch_ms = rec["ms"] / max(rec["launches"], 1)
         per_launch_work = rec["work"] / max(rec["launches"], 1)
@@ -339,6 +375,10 @@ def run_gpu(args, rank, world, local_rank):
                "peak_source": peak_src,
                "achieved_is": "the method's work (real sizes, one product per contraction, symmetric "
                               "Grams counted once) per launch / CUDA-event time"}
+        if name in traffic:
+            # DRAM bytes (read + write) per launch from the ncu capture in profiles/
+            out["traffic"] = round(traffic[name]["bytes"] / max(rec["launches"] / K, 1e-12), 1)
+            out["traffic_source"] = traffic[name]["source"]
         if executed is not None and bound == "tensor":
             # the tensor-core work actually issued: padded tiles and the three
             # split-BF16 products per contraction

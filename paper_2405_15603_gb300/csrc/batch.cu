@@ -34,7 +34,7 @@ void group_record_marker() {
 namespace {
 struct k_copy_words {
     static constexpr int THREADS = 256;
-    __device__ static void run(uint3 vb, uint3 vg, unsigned long long* dst, const unsigned long long* src,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, unsigned long long* dst, const unsigned long long* src,
                                long long n) {
         for (long long i = (long long)vb.x * THREADS + threadIdx.x; i < n; i += (long long)vg.x * THREADS)
             dst[i] = src[i];

@@ -5,8 +5,10 @@
 //
 // A groupable kernel is a struct K with
 //     static constexpr int THREADS;                       // block size
-//     __device__ static void run(uint3 vb, uint3 vg, P... args);
-// where vb / vg stand for blockIdx / gridDim of the member's own launch.
+//     __device__ __noinline__ static void run(uint3 vb, uint3 vg, P... args);
+// where vb / vg stand for blockIdx / gridDim of the member's own launch (not
+// inlined, so that the solo and the grouped kernel call one compiled body and
+// round alike).
 // KL<K>(h, s, grid, smem, args...) launches it as an ordinary kernel
 // (k_solo: vb = blockIdx, vg = gridDim), or, while a recorder is active on
 // this host thread, appends the launch (kernel, grid, shared memory and the

@@ -13,7 +13,7 @@ namespace {
 
 struct k_div_kron {
     static constexpr int THREADS = 256;
-    __device__ static void run(uint3 vb, uint3 vg, double* Y, int nb, int na, const double* wb, const double* wa) {
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, double* Y, int nb, int na, const double* wb, const double* wa) {
         long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
         if (idx >= (long long)nb * na) return;
         int p = (int)(idx / na), q = (int)(idx % na);
@@ -24,7 +24,7 @@ struct k_div_kron {
 // delta = lr (mu delta_prev + Delta); theta += delta (Sec. 3.4, fixed learning rate).
 struct k_update {
     static constexpr int THREADS = 256;
-    __device__ static void run(uint3 vb, uint3 vg, double* theta, const double* dir, double* delta_prev, long long D,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, double* theta, const double* dir, double* delta_prev, long long D,
                                double lr, double mom, double* coef) {
         long long i = (long long)vb.x * blockDim.x + threadIdx.x;
         if (i == 0) {
@@ -44,7 +44,7 @@ constexpr int LS_GRID = 31;
 // dhat = mu delta_prev + Delta (delta_prev is zero before the first step).
 struct k_dhat {
     static constexpr int THREADS = 256;
-    __device__ static void run(uint3 vb, uint3 vg, const double* dir, const double* delta_prev, double* dhat,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const double* dir, const double* delta_prev, double* dhat,
                                long long D, double mom) {
         long long i = (long long)vb.x * blockDim.x + threadIdx.x;
         if (i >= D) return;
@@ -54,7 +54,7 @@ struct k_dhat {
 
 struct k_trial {
     static constexpr int THREADS = 256;
-    __device__ static void run(uint3 vb, uint3 vg, const double* theta, const double* dhat, double* trial,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const double* theta, const double* dhat, double* trial,
                                long long D, double alpha) {
         long long i = (long long)vb.x * blockDim.x + threadIdx.x;
         if (i >= D) return;
@@ -81,7 +81,7 @@ __device__ int ls_argmin(const double* ls_loss) {
 // delta = alpha* dhat; theta += delta.
 struct k_ls_apply {
     static constexpr int THREADS = 256;
-    __device__ static void run(uint3 vb, uint3 vg, double* theta, const double* dhat, double* delta_prev, long long D,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, double* theta, const double* dhat, double* delta_prev, long long D,
                                const double* ls_loss, int* status, double mom, double* coef) {
         __shared__ int best;
         if (threadIdx.x == 0) {
@@ -126,7 +126,7 @@ __device__ double ks_block_sum(double v, double* sh) {
 
 struct k_ks_dots {
     static constexpr int THREADS = 256;
-    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ Dl, const double* __restrict__ dl,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const double* __restrict__ Dl, const double* __restrict__ dl,
                                const double* __restrict__ g, long long D, const double* __restrict__ jDi,
                                const double* __restrict__ jdi, int Ni, const double* __restrict__ jDb,
                                const double* __restrict__ jdb, int Nb, int have_prev, double* part) {
@@ -166,7 +166,7 @@ struct k_ks_dots {
 
 struct k_ks_solve {
     static constexpr int THREADS = 32;
-    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ part, int nblocks, int Ni, int Nb,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const double* __restrict__ part, int nblocks, int Ni, int Nb,
                                double lam, int have_prev, double* coef, int* status) {
         __shared__ double tot[KS_Q];
         if (threadIdx.x < KS_Q) {
@@ -210,7 +210,7 @@ struct k_ks_solve {
 // delta = alpha* Delta + mu* delta_prev; theta += delta.
 struct k_ks_apply {
     static constexpr int THREADS = 256;
-    __device__ static void run(uint3 vb, uint3 vg, double* theta, const double* __restrict__ Dl, double* delta_prev,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, double* theta, const double* __restrict__ Dl, double* delta_prev,
                                long long D, const double* __restrict__ coef) {
         long long i = (long long)vb.x * blockDim.x + threadIdx.x;
         if (i >= D || coef[7] != 0.0) return;       // a non-finite model leaves theta unchanged
@@ -245,7 +245,7 @@ struct PBatch {
 
 struct k_pgemm_f32 {
     static constexpr int THREADS = 256;
-    __device__ static void run(uint3 vb, uint3 vg, const PBatch& b) {
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const PBatch& b) {
         __shared__ __align__(16) float As[16][68];
         __shared__ __align__(16) float Bs[16][68];
         int gi = 0;

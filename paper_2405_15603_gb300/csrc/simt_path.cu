@@ -204,7 +204,7 @@ __global__ void k_seed(R* __restrict__ ZbL, int N, int S, int interior, double c
 // r_sq: r already holds the per-point r_n^T W r_n of a general residual.
 struct k_loss {
     static constexpr int THREADS = 1024;
-    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ r, int N, const double* __restrict__ rb,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const double* __restrict__ r, int N, const double* __restrict__ rb,
                                int Nb, double* __restrict__ loss, int* status, int r_sq) {
         __shared__ double sh[2][32];
         double a = 0.0, b = 0.0;

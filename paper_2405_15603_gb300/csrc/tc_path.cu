@@ -132,7 +132,7 @@ kfac_status_t dal(T** p, size_t n) {
 // BF16 transposed Wt (hin_p x hout_p), FP32 bias; zero padding.
 struct k_convert_weights {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ W, int hout, int hin, int hout_p,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const double* __restrict__ W, int hout, int hin, int hout_p,
                                int hin_p, bf16* Whi, bf16* Wlo, bf16* Wt, bf16* Wt_lo, float* bias) {
         long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
         if (idx >= (long long)hout_p * hin_p) return;
@@ -151,7 +151,7 @@ struct k_convert_weights {
 
 struct k_convert_last {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ W, int hin, int hin_p, float* wL) {
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const double* __restrict__ W, int hin, int hin_p, float* wL) {
         int k = vb.x * blockDim.x + threadIdx.x;
         if (k > hin_p) return;
         if (k < hin_p) wL[k] = (k < hin) ? (float)W[k] : 0.f;
@@ -162,7 +162,7 @@ struct k_convert_last {
 // First-layer weights in FP32, input-major with the features contiguous.
 struct k_convert_first {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ W, int h, int hp, int d, float* W1f) {
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const double* __restrict__ W, int h, int hp, int d, float* W1f) {
         long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
         if (idx >= (long long)(d + 1) * hp) return;
         int k = (int)(idx / hp), j = (int)(idx % hp);
@@ -173,7 +173,7 @@ struct k_convert_first {
 // Points in FP32 (rows >= N zero).
 struct k_points_f32 {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ X, int N, int N_pad, int d, float* Xf) {
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const double* __restrict__ X, int N, int N_pad, int d, float* Xf) {
         long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
         if (idx >= (long long)N_pad * d) return;
         Xf[idx] = (idx < (long long)N * d) ? (float)X[idx] : 0.f;
@@ -192,7 +192,7 @@ KFAC_DEV void store4_bf16(bf16* dst, const float* v) {
 // most); one thread per point and 4 consecutive features.
 struct k_layer1 {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ W1f, const float* __restrict__ Wt,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const float* __restrict__ W1f, const float* __restrict__ Wt,
                                const float* __restrict__ Xf, int N, int N_pad, int d, int h, int hp, int S,
                                const float* __restrict__ chw, int split_time, int split_all, bf16* T_hi, bf16* T_lo,
                                float* A0, float* AD, float* SSQ) {
@@ -274,7 +274,7 @@ struct k_layer1 {
 // y_D = s1 a_D + s2 sum_{i in C} a_i^2  (Eq. 6).
 struct k_lap_finish {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ part, int n_chunks, int N, int N_pad,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const float* __restrict__ part, int n_chunks, int N, int N_pad,
                                int h, int hp, int S, const float* __restrict__ A0, const float* __restrict__ AD,
                                float* SSQ, bf16* T_hi, bf16* T_lo, int split_all) {
         long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
@@ -306,7 +306,7 @@ struct BlockSel {
 };
 struct k_last_fwd {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo,
                                const float* __restrict__ wL, int N_pad, int S, int hp, BlockSel sel, float* zl) {
         long long wid = ((long long)vb.x * blockDim.x + threadIdx.x) / 32;
         int lane = threadIdx.x % 32;
@@ -340,7 +340,7 @@ struct k_last_fwd {
 // Residuals (Eq. 1): interior r = cT z_t + cD z_D - f, boundary r = u - g.
 struct k_residual_mx {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ zl, const double* __restrict__ target,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const float* __restrict__ zl, const double* __restrict__ target,
                                double* r, int N, int N_pad, int S, int interior, double cT, double cD) {
         int n = vb.x * blockDim.x + threadIdx.x;
         if (n >= N) return;
@@ -360,7 +360,7 @@ struct k_residual_mx {
 // are the columns of Q) and the second-order column.
 struct k_extract_mx {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ zl, int N, int N_pad, int S, int d,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const float* __restrict__ zl, int N, int N_pad, int S, int d,
                                const float* __restrict__ Qf, double* u, double* grad, double* lap) {
         int n = vb.x * blockDim.x + threadIdx.x;
         if (n >= N) return;
@@ -388,7 +388,7 @@ struct k_extract_mx {
 // r_n g for every Taylor row.
 struct k_last_bwd {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ wL, const bf16* __restrict__ T_hi,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const float* __restrict__ wL, const bf16* __restrict__ T_hi,
                                const float* __restrict__ A0, const float* __restrict__ AD,
                                const float* __restrict__ SSQ, const double* __restrict__ r, int N, int N_pad, int h,
                                int hp, int S, const float* __restrict__ chw, float cT, float cD,
@@ -459,7 +459,7 @@ __device__ double reduce_row_groups(double v, double (*sh)[33]) {
 // FP64 column sums of rows [row0, row0+nrows) of a BF16 matrix (+ optional lo block).
 struct k_colsum {
     static constexpr int THREADS = RED_THREADS;
-    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ X, const bf16* __restrict__ Xlo, int hp,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ X, const bf16* __restrict__ Xlo, int hp,
                                long long row0, int nrows, int ncols, double* out) {
         __shared__ double sh[32][33];
         const int cl = threadIdx.x % 32, rg = threadIdx.x / 32;
@@ -483,7 +483,7 @@ struct k_colsum {
 // split again (out_lo = the rounding remainder of out).
 struct k_sum_over_s {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ X, const bf16* __restrict__ X_lo,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ X, const bf16* __restrict__ X_lo,
                                int N_pad, int S, int hp, float scale, bf16* out, bf16* out_lo) {
         long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
         const long long blk = (long long)N_pad * hp;
@@ -504,7 +504,7 @@ struct k_sum_over_s {
 // bias row/column sc_b * cs[q], corner `corner`; EMA into the FP64 factor.
 struct k_factor_reduce {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ part, int nz, int P, int sym,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const float* __restrict__ part, int nz, int P, int sym,
                                const double* cs, double sc, double sc_b, double corner, int with_bias, double* fac,
                                double beta, int* status) {
         int n = P + with_bias;
@@ -536,7 +536,7 @@ struct k_factor_reduce {
 // column q = Q from the column sums.
 struct k_grad_reduce {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ pi, int zi, const float* __restrict__ pb,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const float* __restrict__ pi, int zi, const float* __restrict__ pb,
                                int zb, int P, int Q, const double* csi, const double* csb, double si, double sb,
                                double* grad) {
         long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
@@ -559,7 +559,7 @@ struct k_grad_reduce {
 // (x, e_1..e_d, 0) and bias row (1, 0, .., 0)).
 struct k_factor_A1 {
     static constexpr int THREADS = RED_THREADS;
-    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ X, int N, int d, int S, int reduce,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const float* __restrict__ X, int N, int d, int S, int reduce,
                                int boundary, double* fac, double beta, int* status) {
         __shared__ double shm[32][33];
         const int n1 = d + 1;
@@ -590,7 +590,7 @@ struct k_factor_A1 {
 //   (1/N) sum_n [ (r g)_{n,0} (x_n, 1)^T + sum_i (r g)_{n,i} (e_i, 0)^T ] + boundary term.
 struct k_grad_layer1 {
     static constexpr int THREADS = RED_THREADS;
-    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ Gr, const bf16* __restrict__ Grb,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ Gr, const bf16* __restrict__ Grb,
                                const float* __restrict__ X, const float* __restrict__ Xb, int N, int N_pad, int Nb,
                                int d, int h, int hp, int S, double si, double sb, double* grad, double* gtan,
                                const bf16* __restrict__ Gr_lo, const bf16* __restrict__ Grb_lo) {
@@ -636,7 +636,7 @@ struct k_grad_layer1 {
 // grad[j][k] += sum_m t_{j,m} (v_m)_k for the first layer's input columns k < d.
 struct k_rotate_grad1 {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const double* __restrict__ gtan, const float* __restrict__ Qf,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const double* __restrict__ gtan, const float* __restrict__ Qf,
                                int h, int d, double* grad) {
         long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
         if (idx >= (long long)h * d) return;
@@ -650,7 +650,7 @@ struct k_rotate_grad1 {
 // Tangent inputs of the first layer for the directions v_m = Q e_m: W1Qf[m][j] = sum_k W1f[k][j] Q[k][m].
 struct k_rotate_first {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ W1f, const float* __restrict__ Qf, int d,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const float* __restrict__ W1f, const float* __restrict__ Qf, int d,
                                int hp, float* W1Qf) {
         long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
         if (idx >= (long long)d * hp) return;
@@ -675,7 +675,7 @@ struct k_rotate_first {
 // V1t: its tangent inputs V_1 v_m (V1t[m * hp + j]).  One block per point.
 struct k_jdot_layer1 {
     static constexpr int THREADS = 256;
-    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ V1f, const float* __restrict__ V1t,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const float* __restrict__ V1f, const float* __restrict__ V1t,
                                const float* __restrict__ Xf, const bf16* __restrict__ G,
                                const bf16* __restrict__ G_lo, int N, int N_pad, int d, int hp, int S, double* jv) {
         __shared__ double sh[32];
@@ -711,7 +711,7 @@ struct k_jdot_layer1 {
 // jv[n] += sum over the JDOT launch's partial slots of part[slot][n].
 struct k_jdot_reduce {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ part, int slots, int N, int N_pad,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const float* __restrict__ part, int slots, int N, int N_pad,
                                double* jv) {
         const int n = vb.x * blockDim.x + threadIdx.x;
         if (n >= N) return;
@@ -723,7 +723,7 @@ struct k_jdot_reduce {
 
 struct k_residual_jvp_mx {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, const float* __restrict__ jz, double* jv, int N, int N_pad, int S,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const float* __restrict__ jz, double* jv, int N, int N_pad, int S,
                                int interior, double cT, double cD) {
         int n = vb.x * blockDim.x + threadIdx.x;
         if (n >= N) return;
@@ -743,7 +743,7 @@ struct k_residual_jvp_mx {
 // the tangent directions, Q^T dgrad, for a general operator), the last row dlap.
 struct k_seed_mx {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, float* seed, int N, int N_pad, int S, const float* __restrict__ Qf,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, float* seed, int N, int N_pad, int S, const float* __restrict__ Qf,
                                const double* __restrict__ du, const double* __restrict__ dgrad,
                                const double* __restrict__ dlap) {
         long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
@@ -774,7 +774,7 @@ struct k_seed_mx {
 // rows.  FP32 partial sums per row group.
 struct k_last_grad_seeded {
     static constexpr int THREADS = RED_THREADS;
-    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo,
                                const float* __restrict__ seed, int N, int N_pad, int hin, int hp, int S,
                                int split_time, int split_all, double* grad) {
         __shared__ double shm[32][33];
@@ -807,7 +807,7 @@ struct k_last_grad_seeded {
 // Zb1_lo: the adjoint's low half (split-BF16 everywhere), or nullptr.
 struct k_dX_mx {
     static constexpr int THREADS = 128;
-    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ Zb1, const bf16* __restrict__ Zb1_lo,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ Zb1, const bf16* __restrict__ Zb1_lo,
                                int N, int hp, int h1, int d, const float* __restrict__ W1f, double* dX) {
         extern __shared__ float zrow[];
         const int n = vb.x;
@@ -827,7 +827,7 @@ struct k_dX_mx {
 
 struct k_copy_or_add {
     static constexpr int THREADS = EW;
-    __device__ static void run(uint3 vb, uint3 vg, double* dst, const double* src, long long n, int add) {
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, double* dst, const double* src, long long n, int add) {
         long long i = (long long)vb.x * blockDim.x + threadIdx.x;
         if (i < n) dst[i] = add ? dst[i] + src[i] : src[i];
     }
@@ -837,7 +837,7 @@ struct k_copy_or_add {
 // 1x1 output factors B_L.
 struct k_last_layer_terms {
     static constexpr int THREADS = RED_THREADS;
-    __device__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo,
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const bf16* __restrict__ T_hi, const bf16* __restrict__ T_lo,
                                const bf16* __restrict__ Tb_hi, const bf16* __restrict__ Tb_lo,
                                const double* __restrict__ r, const double* __restrict__ rb, int N, int N_pad, int Nb,
                                int Nb_pad, int h, int hp, int S, double cT, double cD, int reduce, double* grad,
