@@ -16,8 +16,13 @@ CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libkfacpinn.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["abi.cu", "simt_path.cu", "linalg.cu", "eig.cu", "tc_path.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["abi.cu", "simt_path.cu", "linalg.cu", "eig.cu", "tc_path.cu", "tc_engine.cu", "noalloc.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The tcgen05 engine's kernels are compiled without floating-point
+# contraction: the grouped kernel inlines the same body as the ordinary one,
+# and only with every FMA written out (fmaf) do both copies round alike, which
+# keeps a grouped batch step bit-identical to each problem's own step.
+EXTRA_FLAGS = {"tc_engine.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -29,7 +34,7 @@ def nvcc() -> str:
 
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *EXTRA_FLAGS.get(src, []),
            "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
@@ -45,7 +50,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "kfac_pinn.h")]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "kfac_pinn.h"),
+                                                                 os.path.abspath(__file__)]
     return any(os.path.getmtime(p) > t for p in deps if os.path.exists(p))
 
 

@@ -175,10 +175,12 @@ KFAC_DEV void load16_f32(const float* src, float* v) {
 // that the plain instantiations keep their register budget.
 // The engine's work for one CTA: vb / vg stand for blockIdx / gridDim of the
 // launch the CTA belongs to (its own, or its member's in a grouped launch).
-// Not inlined: the solo and the grouped kernel call one compiled body, so a
-// member of a grouped launch rounds exactly as its own launch would.
+// Inlined into both the solo and the grouped kernel.  Their translation unit
+// (tc_engine.cu) is compiled without floating-point contraction: every FMA is
+// an explicit fmaf, so the two copies round alike and a member of a grouped
+// launch computes exactly what its own launch computes.
 template <int MODE, bool SPLIT>
-__device__ __noinline__ void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
+KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
     using C = Cfg<MODE, SPLIT>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);

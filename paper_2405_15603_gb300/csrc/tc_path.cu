@@ -19,6 +19,7 @@
 
 #include <vector>
 #include "tc_kernels.cuh"
+#include "tc_engine.cuh"
 
 using tck::Args;
 
@@ -884,28 +885,14 @@ struct k_last_layer_terms {
 // ============================================================================
 // Host helpers
 // ============================================================================
-// Grouped launch of the engine over a member table of Args (group.cuh).
+// The engine's launch, or its record while a grouped batch step is recorded.
 template <int MODE, bool SPLIT>
-cudaError_t launch_engine_group(const GroupTab& t, unsigned blocks, size_t, cudaStream_t s) {
-    using C = tck::Cfg<MODE, SPLIT>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tck::tc_engine_group<MODE, SPLIT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    tck::tc_engine_group<MODE, SPLIT><<<blocks, tck::NUM_THREADS, C::SMEM, s>>>(t);
-    return cudaGetLastError();
-}
-
-template <int MODE, bool SPLIT>
-kfac_status_t launch_engine_as(kfac_pinn_handle* h, cudaStream_t s, const Args& a, dim3 grid) {
+kfac_status_t launch_engine_as(kfac_pinn_handle*, cudaStream_t s, const Args& a, dim3 grid) {
     using C = tck::Cfg<MODE, SPLIT>;
     if (GroupRecorder* r = group_recorder()) {
         LaunchRec rec;
-        rec.key = (const void*)tck::tc_engine_group<MODE, SPLIT>;
-        rec.launch = &launch_engine_group<MODE, SPLIT>;
+        rec.key = tck::engine_group_key(MODE, SPLIT);
+        rec.launch = tck::engine_group_launcher(MODE, SPLIT);
         rec.grid = make_uint3(grid.x, grid.y, grid.z);
         rec.smem = C::SMEM;
         rec.align = (int)alignof(Args);
@@ -915,14 +902,11 @@ kfac_status_t launch_engine_as(kfac_pinn_handle* h, cudaStream_t s, const Args& 
         r->list->push_back(std::move(rec));
         return KFAC_OK;
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(tck::tc_engine<MODE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
-            cudaSuccess)
-            return KFAC_CUDA_ERROR;
-        attr_set = true;
+    const cudaError_t e = tck::engine_launch(MODE, SPLIT, a, grid, s);
+    if (e != cudaSuccess) {
+        kfac_record_cuda_error(e);
+        return KFAC_CUDA_ERROR;
     }
-    tck::tc_engine<MODE, SPLIT><<<grid, tck::NUM_THREADS, C::SMEM, s>>>(a);
     return KFAC_OK;
 }
 
