@@ -665,7 +665,12 @@ def run_many(steps=10, warmup=3, n_streams=16, count=64, precision="mixed_split"
     losses = [torch.zeros(3, dtype=torch.float64, device=dev) for _ in members]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     timed = {}
+    th0 = [t.clone() for t in thetas]
     for form in ("streams", "grouped"):
+        for t, t0 in zip(thetas, th0):      # both forms step the same problems from the same start
+            t.copy_(t0)
+        for o in opts:
+            o.reset()
         batch = KfacBatch(opts, n_streams=n_streams, grouped=(form == "grouped"))
         for _ in range(warmup):                  # eager, capture, replay
             batch.step(thetas, *cols, losses)
@@ -675,10 +680,10 @@ def run_many(steps=10, warmup=3, n_streams=16, count=64, precision="mixed_split"
             batch.step(thetas, *cols, losses)
         e1.record()
         torch.cuda.synchronize()
-        timed[form] = (e0.elapsed_time(e1) / steps, batch.launches_per_step())
+        timed[form] = (e0.elapsed_time(e1) / steps, batch.launches_per_step(),
+                       sorted({o.sync_status() for o in opts}))
         batch.close()
-    ms_batch, launches = timed["grouped"]
-    status = sorted({o.sync_status() for o in opts})
+    ms_batch, launches, status = timed["grouped"]
     # the same problems one after another, mixed precision, one stream
     e0.record()
     for i, o in enumerate(opts):
@@ -714,7 +719,8 @@ def run_many(steps=10, warmup=3, n_streams=16, count=64, precision="mixed_split"
             "form": "grouped: one launch per kernel for all problems (member tables), one batched eigensolve",
             "streams_form": {"value": round(count / (timed["streams"][0] / 1e3), 3), "unit": "steps/s",
                              "ms_per_batch_step": round(timed["streams"][0], 4),
-                             "gpu_launches_per_batch_step": int(timed["streams"][1])},
+                             "gpu_launches_per_batch_step": int(timed["streams"][1]),
+                             "status": timed["streams"][2]},
             "mixed_sequential": {"value": round(count / (ms_seq_mixed / 1e3), 3), "unit": "steps/s"},
             "fp64_sequential": {"value": round(count / (ms_fp64 / 1e3), 3), "unit": "steps/s"},
             "speedup_vs_fp64_sequential": round(ms_fp64 / ms_batch, 2)}
