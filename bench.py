@@ -861,6 +861,42 @@ def run_secondary():
     return out
 
 
+def run_profile_many(args, count=64):
+    """The 64-PINN batch for profilers (`--profile --many`): the grouped form's
+    warm-up steps (eager, recorded and captured), then one replayed batch step
+    inside the NVTX range "kfac_step" and nothing else."""
+    import torch
+    from paper_2405_15603_gb300 import build as _build
+    _build.build()
+    from paper_2405_15603_gb300.api import KfacBatch, KfacPinn
+    dev = torch.device("cuda:0")
+    members = si.many_pinns(count, seed=0)
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    kw = dict(lam=1e-3, beta=0.95, lr=0.05, momentum=0.0, init_identity=True, update="fixed",
+              eig_sm_budget=max(8, sm // 8))
+    opts = [KfacPinn(m.d, m.widths, device=str(dev), precision="mixed_split", max_n_int=m.n_int,
+                     max_n_bdy=m.n_bdy, **kw) for m in members]
+    thetas = [torch.tensor(si.xavier_theta(m.d, m.widths, i), device=dev) for i, m in enumerate(members)]
+    bufs = [[torch.tensor(a, device=dev) for a in si.make_batch(m.prob, m.n_int, m.n_bdy, seed=i)]
+            for i, m in enumerate(members)]
+    cols = [[b[j] for b in bufs] for j in range(4)]
+    batch = KfacBatch(opts, n_streams=16, grouped=True)
+    for _ in range(max(args.warmup, 3)):
+        batch.step(thetas, *cols)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("kfac_step")
+    e0.record()
+    batch.step(thetas, *cols)
+    e1.record()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    out = {"workload": f"many_pinns_{count}_seed0", "form": "grouped", "ms": round(e0.elapsed_time(e1), 3),
+           "launches": batch.launches_per_step(), "status": sorted({o.sync_status() for o in opts})}
+    batch.close()
+    return out
+
+
 def run_profile_step(args):
     """The benchmark's step for profilers: the warm-up steps (autotuner, graph
     capture), then one replayed step inside the NVTX range "kfac_step" (for
@@ -931,6 +967,9 @@ def main():
         WORKLOAD_NAME = f"poisson100d_100-768-768-512-512-1_{ni}int_{nb}bdy_resampled"
     if args.e10:
         print(json.dumps(run_e10()), flush=True)
+        return
+    if args.profile and args.many:
+        print(json.dumps(run_profile_many(args)), flush=True)
         return
     if args.many:
         print(json.dumps(run_many()), flush=True)
