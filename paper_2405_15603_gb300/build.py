@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libkfacpinn.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["abi.cu", "simt_path.cu", "linalg.cu", "eig.cu", "tc_path.cu", "tc_engine.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["abi.cu", "simt_path.cu", "linalg.cu", "eig.cu", "tc_path.cu", "tc_engine.cu", "ozaki.cu", "noalloc.cu",
+           "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The tcgen05 engine's kernels are compiled without floating-point
 # contraction: the grouped kernel inlines the same body as the ordinary one,

@@ -28,6 +28,7 @@
 #include <cooperative_groups.h>
 
 #include "kfac_internal.cuh"
+#include "ozaki.cuh"
 
 namespace {
 
@@ -44,6 +45,9 @@ constexpr int STRIP_MEDIUM_FROM = 320;   // these 16, the smaller ones 32
 inline int strip_width(int n) { return n >= STRIP_NARROW_FROM ? 8 : (n >= STRIP_MEDIUM_FROM ? 16 : 32); }
 constexpr int KFAC_MAX_WIDTH_PLUS_ONE = 1024;   // widths <= 1023 and d + 1 <= 1024 (create checks)
 constexpr double DEPS = 2.220446049250313e-16;
+// Block GEMMs of the divide and conquer with a contraction this long or longer
+// run on the tensor cores (ozaki.cu); shorter ones stay on the FP64 cores.
+constexpr int OZ_MIN_K = 128;
 
 struct Prob {
     int n;
@@ -95,8 +99,9 @@ struct Level {
     Merge* merges;     // device
     int n_merges;
     int max_m;
-    Gd* gemms;         // device
+    Gd* gemms;         // device: the block GEMMs below OZ_MIN_K (FP64 CUDA cores)
     int n_gemms, n_tiles;
+    OzPlan* oz;        // the others, on the tensor cores by error-free splitting (ozaki.cu)
     Copy* copies;      // device
     int n_copies, max_copy;
     int roots;         // sum of m over merges
@@ -2022,8 +2027,30 @@ static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es) {
                 gd.push_back(g2);
             }
         }
+        // the block GEMMs with a contraction of at least OZ_MIN_K run as
+        // error-free FP64 emulations on the tensor cores, the rest here
+        std::vector<OzGemm> big;
+        {
+            std::vector<Gd> small;
+            int t2 = 0;
+            for (Gd g : gd) {
+                if (g.K >= OZ_MIN_K) {
+                    big.push_back(OzGemm{g.A, g.ld, g.B, g.ld, g.C, g.ld, g.M, g.N, g.K});
+                    continue;
+                }
+                g.tile0 = t2;
+                t2 += ((g.M + 63) / 64) * ((g.N + 63) / 64);
+                small.push_back(g);
+            }
+            gd.swap(small);
+            tiles = t2;
+        }
         Level lv;
         memset(&lv, 0, sizeof(lv));
+        if (!big.empty() && (st = oz_plan_create(big, es->host[0].status, &lv.oz))) {
+            oz_plan_free(lv.oz);
+            return st;
+        }
         lv.n_merges = (int)mg.size();
         lv.n_gemms = (int)gd.size();
         lv.n_tiles = tiles;
@@ -2069,6 +2096,7 @@ static void group_free(EigState* es) {
     cudaFree(es->trsm_jobs);
     cudaFree(es->trsm_jobs_upper);
     for (auto& lv : es->levels) {
+        oz_plan_free(lv.oz);
         cudaFree(lv.merges);
         cudaFree(lv.gemms);
         cudaFree(lv.copies);
@@ -2166,8 +2194,11 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
             k_dc_rotate_scatter<<<dim3((lv.max_m + RS_COLS - 1) / RS_COLS, lv.n_merges), 256, 0, s>>>(
                 pr, lv.merges, es->fail);
             KFAC_LAUNCH_CHECK(h);
-            k_dc_gemm<<<lv.n_tiles, 256, 0, s>>>(lv.gemms, lv.n_gemms, es->fail);
-            KFAC_LAUNCH_CHECK(h);
+            if (lv.oz) KFAC_TRY(oz_run(h, lv.oz, s));
+            if (lv.n_tiles > 0) {
+                k_dc_gemm<<<lv.n_tiles, 256, 0, s>>>(lv.gemms, lv.n_gemms, es->fail);
+                KFAC_LAUNCH_CHECK(h);
+            }
         }
         if (lv.n_copies > 0) {
             k_dc_copy<<<dim3(ceil_div_u((long long)lv.max_copy * lv.max_copy, 256), lv.n_copies), 256, 0, s>>>(
