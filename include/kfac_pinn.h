@@ -328,10 +328,15 @@ kfac_status_t kfac_pinn_factors(kfac_handle_t h, void* stream, const double* the
  * layer, with A~ = A^ + lambda I (or sqrt(lambda) I), the simultaneous
  * diagonalisation V^T A~_Omega V = I, V^T A~_bdy V = diag(a) through an FP64
  * Cholesky of A~_Omega and an FP64 symmetric eigendecomposition of the
- * whitened A~_bdy; likewise for B.  A factor that is not positive definite
- * latches KFAC_NOT_PD.  Part of the work runs on a stream of the handle's own,
- * forked from `stream` and joined back into it: the call stays ordered with
- * the rest of `stream` (and is captured with it). */
+ * whitened A~_bdy; likewise for B.  The large matrix products of the
+ * decomposition (the whitening with L^{-1}, the final V = L^{-T} U, the
+ * divide-and-conquer updates) are FP64 products emulated on the BF16 tensor
+ * cores by error-free splitting (8 slices of 7 bits, exact FP32 partial sums,
+ * FP64 combination: rounding errors of the order of an FP64 product's).  A
+ * factor that is not positive definite latches KFAC_NOT_PD.  Part of the work
+ * runs on streams of the handle's own, forked from `stream` and joined back
+ * into it: the call stays ordered with the rest of `stream` (and is captured
+ * with it). */
 kfac_status_t kfac_pinn_invert(kfac_handle_t h, void* stream);
 
 /* direction = -(A~_Omega x B~_Omega + A~_bdy x B~_bdy)^{-1} grad per layer,

@@ -5,18 +5,22 @@
 //   1. Cholesky P = L L^T                       (one cluster per problem, as in 3;
 //                                                 blocked diag / panel / trailing
 //                                                 kernels for the largest factors)
-//   2. M = L^{-1} Q L^{-T}                      (two column-parallel TRSMs)
+//   2. M = L^{-1} Q L^{-T}                      (L^{-1} by column-parallel FP64
+//                                                 solves, the two products on the
+//                                                 tensor cores by error-free FP64
+//                                                 emulation, ozaki.cu)
 //   3. Householder tridiagonalisation of M      (one thread-block cluster per
 //      problem with the triangle in distributed shared memory; for factors
 //      too large for it, one cooperative kernel where each problem owns a
 //      group of CTAs that sync through bounded global barriers)
 //   4. divide and conquer on the tridiagonal T  (Cuppen's rank-one tearing,
 //      deflation, secular equation by a safeguarded rational iteration, eigenvectors via the
-//      Gu-Eisenstat recomputed z, block GEMMs per merge level)
+//      Gu-Eisenstat recomputed z, block GEMMs per merge level, the large ones
+//      on the tensor cores, ozaki.cu)
 //   5. back-transformation by the Householder reflectors (column-parallel)
-//   6. V = L^{-T} U                              (TRSM)
-// The factor pairs form two groups (the largest, the rest) whose kernel
-// sequences run on two streams at once.
+//   6. V = L^{-T} U                              (tensor cores, ozaki.cu)
+// The factor pairs form one group per cluster size of steps 1 and 3, whose
+// kernel sequences run on streams of their own at once.
 // Errors (a P that is not positive definite, a barrier that gave up) are
 // latched in the handle's status word; the problem's V and w are then zero.
 #include <stdlib.h>
@@ -57,6 +61,7 @@ struct Prob {
     double* w;
     double *L, *M, *Qa, *Qb, *R, *R2, *H;  // n x n row-major (H: Householder vectors, one per row)
     double* Ld;                            // inverses of the 64 x 64 diagonal blocks of L (n x 64)
+    double* Li;                            // L^{-1}, n x n row-major (zero above the diagonal)
     double *d, *e, *tau, *D, *pbuf, *pbuf2;  // n
     double *Ds, *zs, *dK, *zK, *tauR, *zh, *rc, *rs, *val; // n (per-merge scratch at offset a)
     int *perm, *defl, *Kidx, *org, *rj, *ri, *col;          // n
@@ -122,6 +127,10 @@ struct EigState {
     int n_cta;
     void* trsm_jobs;            // TrsmJob list, largest work first (also the back-transform's)
     void* trsm_jobs_upper;      // the same jobs ordered by their work in the upper-triangle solve (mode 1)
+    void* trsm_jobs_inv;        // ... and in the inverse (mode 3)
+    OzPlan* oz_red1;            // Qa = L^{-1} M                 (tensor cores, ozaki.cu)
+    OzPlan* oz_red2;            // M = Qa L^{-T}
+    OzPlan* oz_back;            // V = L^{-T} U
     int n_trsm_jobs;
     size_t bt_smem;             // back-transform shared memory for the widest job
     std::vector<Level> levels;
@@ -340,6 +349,10 @@ __global__ void __launch_bounds__(256) k_chol_update(Prob* pr, int k0, int* fail
 //           rows 0..c of column c, the upper triangle, which k_symmetrize
 //           copies to the lower one; a third of the solve's work)
 //   mode 2: X = L^{-T} B,   B = final D&C buffer, X -> V
+//   mode 3: X = L^{-1},     B = I,               X -> Li  (each column from the
+//           block of its diagonal down: a third of a full solve's work)
+// The eigensolver uses mode 3 and forms the products with L^{-1} on the
+// tensor cores (ozaki.cu); modes 0-2 solve with L on the FP64 cores.
 // --------------------------------------------------------------------------
 // One column strip [c0, c0 + CB) of a triangular solve with NB x NB blocks.
 template <int CB>
@@ -353,29 +366,35 @@ __device__ void trsm_strip(const Prob& p, int c0, int mode, bool failed, double*
     double* X;
     if (mode == 0) { B = p.M; X = p.Qa; }
     else if (mode == 1) { B = p.Qa; X = p.M; }
-    else { B = p.final_buf ? p.Qb : p.Qa; X = p.V; }
+    else if (mode == 2) { B = p.final_buf ? p.Qb : p.Qa; X = p.V; }
+    else { B = nullptr; X = p.Li; }
     const int ncb = min(CB, n - c0);
     const int nblk = (n + NB - 1) / NB;
     if (failed) {
-        if (mode == 2)
+        if (mode >= 2)
             for (int t = threadIdx.x; t < n * ncb; t += blockDim.x) X[(long long)(t / ncb) * n + c0 + t % ncb] = 0.0;
         return;
     }
     const bool upper = (mode == 2);
-    // mode 1: the row blocks down to the strip's last column
+    // mode 1: the row blocks down to the strip's last column; mode 3 (the
+    // inverse, right-hand side I): from the block of the strip's first column,
+    // the rows above it being zero
     const int nrun = (mode == 1) ? min(nblk, (c0 + ncb - 1) / NB + 1) : nblk;
-    for (int s = 0; s < nrun; s++) {
+    const int s0 = (mode == 3) ? c0 / NB : 0;
+    for (int s = s0; s < nrun; s++) {
         const int ib = upper ? nblk - 1 - s : s;
         const int r0 = ib * NB, rows = min(NB, n - r0);
         for (int t = threadIdx.x; t < NB * CB; t += blockDim.x) {
             int r = t / CB, c = t % CB;
             double v = 0.0;
-            if (r < rows && c < ncb)
-                v = (mode == 1) ? B[(long long)(c0 + c) * n + r0 + r] : B[(long long)(r0 + r) * n + c0 + c];
+            if (r < rows && c < ncb) {
+                if (mode == 3) v = (r0 + r == c0 + c) ? 1.0 : 0.0;
+                else v = (mode == 1) ? B[(long long)(c0 + c) * n + r0 + r] : B[(long long)(r0 + r) * n + c0 + c];
+            }
             acc[r * (CB + 1) + c] = v;
         }
         // subtract the solved blocks
-        for (int kk = 0; kk < s; kk++) {
+        for (int kk = s0; kk < s; kk++) {
             const int kb = upper ? nblk - 1 - kk : kk;
             const int k0 = kb * NB, kr = min(NB, n - k0);
             __syncthreads();
@@ -1704,6 +1723,8 @@ __global__ void __launch_bounds__(256) k_backtransform(Prob* pr, const TrsmJob* 
 
 __global__ void k_write_w(Prob* pr, int* fail) {
     const Prob p = pr[blockIdx.x];
+    if (fail[blockIdx.x])      // a failed problem's V and w are zero
+        for (long long i = threadIdx.x; i < (long long)p.n * p.n; i += blockDim.x) p.V[i] = 0.0;
     for (int i = threadIdx.x; i < p.n; i += blockDim.x) {
         double v = fail[blockIdx.x] ? 0.0 : p.D[i];
         if (!isfinite(v)) latch_status(p.status, KFAC_NONFINITE);
@@ -1815,7 +1836,7 @@ static kfac_status_t group_alloc(kfac_pinn_handle* h, EigState* es, const std::v
     std::vector<int> ns;
     for (const auto& pw : pairs) ns.push_back(pair_n(h, pw.first, pw.second));
     for (int n : ns) {
-        dtot += 7 * (size_t)n * n + (size_t)n * NB + 20 * (size_t)n;
+        dtot += 8 * (size_t)n * n + (size_t)n * NB + 20 * (size_t)n;
         itot += 12 * (size_t)n;
     }
     kfac_status_t st;
@@ -1846,6 +1867,7 @@ static kfac_status_t group_alloc(kfac_pinn_handle* h, EigState* es, const std::v
             p.R = dp; dp += nn;
             p.R2 = dp; dp += nn;
             p.H = dp; dp += nn;
+            p.Li = dp; dp += nn;
             p.Ld = dp; dp += (size_t)n * NB;
             double** dv[] = {&p.d, &p.e, &p.tau, &p.D, &p.pbuf, &p.Ds, &p.zs, &p.dK, &p.zK, &p.tauR, &p.zh,
                              &p.rc, &p.rs, &p.val, &p.mrh};
@@ -1859,6 +1881,10 @@ static kfac_status_t group_alloc(kfac_pinn_handle* h, EigState* es, const std::v
             p.final_buf = ceil_log2(n) & 1;
         }
     }
+    // L^{-1} is written from each column's diagonal block down: the blocks
+    // above stay zero
+    for (const Prob& p : es->host)
+        if (cudaMemset(p.Li, 0, sizeof(double) * (size_t)p.n * p.n) != cudaSuccess) return KFAC_CUDA_ERROR;
     return group_schedule(h, es);
 }
 
@@ -1945,6 +1971,15 @@ static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es) {
                          [&](const TrsmJob& x, const TrsmJob& y) { return upper_work(x) > upper_work(y); });
         if ((ast = kfac_device_alloc(&es->trsm_jobs_upper, sizeof(TrsmJob) * jobs.size())) != KFAC_OK) return ast;
         cudaMemcpy(es->trsm_jobs_upper, jobs.data(), sizeof(TrsmJob) * jobs.size(), cudaMemcpyHostToDevice);
+        // the inverse's strip runs from the block of its first column down
+        auto inv_work = [&](const TrsmJob& j) {
+            const double e = es->host[j.prob].n - (j.c0 / NB) * NB;
+            return e * e * j.cb;
+        };
+        std::stable_sort(jobs.begin(), jobs.end(),
+                         [&](const TrsmJob& x, const TrsmJob& y) { return inv_work(x) > inv_work(y); });
+        if ((ast = kfac_device_alloc(&es->trsm_jobs_inv, sizeof(TrsmJob) * jobs.size())) != KFAC_OK) return ast;
+        cudaMemcpy(es->trsm_jobs_inv, jobs.data(), sizeof(TrsmJob) * jobs.size(), cudaMemcpyHostToDevice);
     }
 
     // cluster tridiagonalisation: one cluster per problem when the problems'
@@ -2066,6 +2101,27 @@ static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es) {
         if (!cp.empty()) cudaMemcpy(lv.copies, cp.data(), sizeof(Copy) * cp.size(), cudaMemcpyHostToDevice);
         es->levels.push_back(lv);
     }
+    // the products with L^{-1} on the tensor cores
+    {
+        std::vector<OzGemm> r1, r2, bk;
+        for (const Prob& p : es->host) {
+            const int n = p.n;
+            OzGemm g;
+            g.M = g.N = g.K = n;
+            g.lda = g.ldb = g.ldc = n;
+            g.A = p.Li; g.B = p.M; g.C = p.Qa; g.ta = false; g.tb = false;      // Qa = L^{-1} M
+            r1.push_back(g);
+            g.A = p.Qa; g.B = p.Li; g.C = p.M; g.ta = false; g.tb = true;       // M = Qa L^{-T}
+            r2.push_back(g);
+            g.A = p.Li; g.B = p.final_buf ? p.Qb : p.Qa; g.C = p.V;             // V = L^{-T} U
+            g.ta = true; g.tb = false;
+            bk.push_back(g);
+        }
+        int* status = es->host[0].status;
+        if ((st = oz_plan_create(r1, status, &es->oz_red1))) return st;
+        if ((st = oz_plan_create(r2, status, &es->oz_red2))) return st;
+        if ((st = oz_plan_create(bk, status, &es->oz_back))) return st;
+    }
     cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB_MAX + 1)));
     cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2095,6 +2151,10 @@ static void group_free(EigState* es) {
     cudaFree(es->clu_prob);
     cudaFree(es->trsm_jobs);
     cudaFree(es->trsm_jobs_upper);
+    cudaFree(es->trsm_jobs_inv);
+    oz_plan_free(es->oz_red1);
+    oz_plan_free(es->oz_red2);
+    oz_plan_free(es->oz_back);
     for (auto& lv : es->levels) {
         oz_plan_free(lv.oz);
         cudaFree(lv.merges);
@@ -2139,10 +2199,11 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
     k_diag_inv<<<dim3(nblk, np), 256, 2 * NB * (NB + 1) * sizeof(double), s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
     const int smem_trsm = (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB_MAX + 1));
-    k_trsm<<<es->n_trsm_jobs, 256, smem_trsm, s>>>(pr, (const TrsmJob*)es->trsm_jobs, 0, es->fail);
+    // L^{-1} on the FP64 cores, then M = L^{-1} Q L^{-T} on the tensor cores
+    k_trsm<<<es->n_trsm_jobs, 256, smem_trsm, s>>>(pr, (const TrsmJob*)es->trsm_jobs_inv, 3, es->fail);
     KFAC_LAUNCH_CHECK(h);
-    k_trsm<<<es->n_trsm_jobs, 256, smem_trsm, s>>>(pr, (const TrsmJob*)es->trsm_jobs_upper, 1, es->fail);
-    KFAC_LAUNCH_CHECK(h);
+    KFAC_TRY(oz_run(h, es->oz_red1, s));
+    KFAC_TRY(oz_run(h, es->oz_red2, s));
     k_symmetrize<<<dim3(64, np), 256, 0, s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
     // 3. tridiagonalisation: one cluster per problem, or cooperative groups of CTAs
@@ -2209,8 +2270,7 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
     // 5. back-transformation, 6. V = L^{-T} U
     k_backtransform<<<es->n_trsm_jobs, 256, es->bt_smem, s>>>(pr, (const TrsmJob*)es->trsm_jobs, es->fail);
     KFAC_LAUNCH_CHECK(h);
-    k_trsm<<<es->n_trsm_jobs, 256, smem_trsm, s>>>(pr, (const TrsmJob*)es->trsm_jobs, 2, es->fail);
-    KFAC_LAUNCH_CHECK(h);
+    KFAC_TRY(oz_run(h, es->oz_back, s));
     k_write_w<<<np, 256, 0, s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;

@@ -15,8 +15,9 @@
 // S = 8 at the level of FP64's own rounding).  The products of one level t
 // share the scale 2^{-tW}, so they form ONE Gram contraction over the stacked
 // slices: X = [a_1; ...; a_{t-1}] (A's slices transposed, (t-1)K x M) and
-// Y = [b_{t-1}; ...; b_1] ((t-1)K x N), on the engine's Gram mode (row chunks
-// of 512 rows, FP32 partials per chunk).  The partials are integers, so their
+// Y = [b_{t-1}; ...; b_1] ((t-1)K x N); all levels of all the plan's products
+// are the members of one grouped launch of the engine's Gram mode (row chunks
+// of 1024 rows, FP32 partials per chunk).  The partials are integers, so their
 // FP64 sums are exact; the levels are combined in FP64 from the smallest.
 // B's slices are stored in reverse order, so that level t's Y is a contiguous
 // tail of them.
@@ -32,8 +33,9 @@ namespace {
 
 constexpr int OZ_W = 7;                 // bits per slice
 constexpr int OZ_S = 8;                 // slices per operand
-constexpr int OZ_CHUNK = 512;           // Gram rows per exact FP32 partial (<= 1024)
+constexpr int OZ_CHUNK = 1024;          // Gram rows per exact FP32 partial: 1024 * 127^2 < 2^24
 constexpr double OZ_SLICE = 128.0;      // 2^W
+static_assert(OZ_W * OZ_S == 56, "the slices cover the 56-bit fixed-point value");
 
 struct OzDev {
     const double* A;
@@ -90,45 +92,56 @@ __device__ __forceinline__ int exponent_above(double m) {
     return e;
 }
 
-// Column scales of the sides whose columns lie along the source's rows (one
-// warp per column; blockIdx.y = 2 g + side).
-__global__ void __launch_bounds__(256) k_oz_exp_contig(const OzDev* g) {
+// Column scales 2^e_c of every side: one warp per column where the column
+// lies along the source's rows (8 columns per block), else 32 columns per
+// block with 8 row groups each (coalesced along the source's rows);
+// blockIdx.y = 2 g + side.
+__global__ void __launch_bounds__(256) k_oz_exponents(const OzDev* g) {
     const OzSide o = side_of(g[blockIdx.y / 2], blockIdx.y % 2);
-    if (!o.csrc) return;
-    const int c = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (c >= o.Cn) return;
+    __shared__ double red[8][33];
     double m = 0.0;
-    for (int r = lane; r < o.R; r += 32) m = fmax(m, fabs(o.src[(long long)c * o.ld + r]));
-    for (int w = 16; w > 0; w >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, w));
-    if (lane == 0) o.e[c] = exponent_above(m);
+    if (o.csrc) {
+        const int c = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
+        if (c >= o.Cn) return;
+        for (int r = lane; r < o.R; r += 32) m = fmax(m, fabs(o.src[(long long)c * o.ld + r]));
+        for (int w = 16; w > 0; w >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, w));
+        if (lane == 0) o.e[c] = exponent_above(m);
+        return;
+    }
+    if (blockIdx.x * 32 >= (unsigned)o.Cn) return;         // uniform over the block
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32, c = blockIdx.x * 32 + tx;
+    if (c < o.Cn)
+        for (int r = ty; r < o.R; r += 8) m = fmax(m, fabs(o.src[(long long)r * o.ld + c]));
+    red[ty][tx] = m;
+    __syncthreads();
+    if (ty == 0 && c < o.Cn) {
+        for (int k = 1; k < 8; k++) m = fmax(m, red[k][tx]);
+        o.e[c] = exponent_above(m);
+    }
 }
 
-// Column scales of the others (one thread per column, coalesced along it).
-__global__ void __launch_bounds__(256) k_oz_exp_strided(const OzDev* g) {
-    const OzSide o = side_of(g[blockIdx.y / 2], blockIdx.y % 2);
-    if (o.csrc) return;
-    const int c = blockIdx.x * 256 + threadIdx.x;
-    if (c >= o.Cn) return;
-    double m = 0.0;
-    for (int r = 0; r < o.R; r++) m = fmax(m, fabs(o.src[(long long)r * o.ld + c]));
-    o.e[c] = exponent_above(m);
+// The slicing of one value: v 2^{56 - e} truncated to an integer (|.| < 2^56,
+// exact in int64) whose 7-bit groups, from the top, are the slices' magnitudes
+// (the same values as repeated truncation of v 2^{-e} in FP64, taken with
+// integer operations).
+__device__ __forceinline__ long long oz_fixed(double v, int e) { return (long long)ldexp(v, 56 - e); }
+
+__device__ __forceinline__ float oz_digit(long long m, int q) {
+    const long long u = m < 0 ? -m : m;
+    const int d = (int)((u >> (49 - OZ_W * q)) & 127);
+    return (float)(m < 0 ? -d : d);
 }
 
 // Slices of a side whose source is laid out like the destination: one
-// thread per element, along c.  Truncation keeps every slice in [-127, 127]
-// and every remainder exact.
+// thread per element, along c.
 __global__ void __launch_bounds__(256) k_oz_slice_direct(const OzDev* g) {
     const OzSide o = side_of(g[blockIdx.z / 2], blockIdx.z % 2);
     if (o.csrc) return;
     const int c = blockIdx.x * 256 + threadIdx.x, r = blockIdx.y;
     if (c >= o.Cp || r >= o.R) return;
-    double x = (c < o.Cn) ? ldexp(side_at(o, r, c), -o.e[c]) : 0.0;
-    for (int q = 0; q < OZ_S; q++) {
-        const double y = x * OZ_SLICE;
-        const double t = trunc(y);
-        x = y - t;
-        o.D[side_dst(o, q, r, c)] = __float2bfloat16_rn((float)t);
-    }
+    const long long m = (c < o.Cn) ? oz_fixed(side_at(o, r, c), o.e[c]) : 0;
+#pragma unroll
+    for (int q = 0; q < OZ_S; q++) o.D[side_dst(o, q, r, c)] = __float2bfloat16_rn(oz_digit(m, q));
 }
 
 // Slices of a side whose source holds c along its rows: a 32 x 32 tile
@@ -138,29 +151,25 @@ __global__ void __launch_bounds__(256) k_oz_slice_transpose(const OzDev* g) {
     if (!o.csrc) return;
     const int c0 = blockIdx.y * 32, r0 = blockIdx.x * 32;
     if (c0 >= o.Cp || r0 >= o.R) return;
-    __shared__ double x[32][33];
+    __shared__ long long x[32][33];
     const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
     for (int cc = ty; cc < 32; cc += 8) {       // read along r (tx)
         const int c = c0 + cc, r = r0 + tx;
-        double v = 0.0;
-        if (c < o.Cn && r < o.R) v = ldexp(side_at(o, r, c), -o.e[c]);
-        x[cc][tx] = v;
+        x[cc][tx] = (c < o.Cn && r < o.R) ? oz_fixed(side_at(o, r, c), o.e[c]) : 0;
     }
     __syncthreads();
-    for (int q = 0; q < OZ_S; q++) {
-        for (int rr = ty; rr < 32; rr += 8) {   // write along c (tx)
-            const int r = r0 + rr, c = c0 + tx;
-            const double y = x[tx][rr] * OZ_SLICE;
-            const double t = trunc(y);
-            x[tx][rr] = y - t;
-            if (r < o.R && c < o.Cp) o.D[side_dst(o, q, r, c)] = __float2bfloat16_rn((float)t);
-        }
-        __syncthreads();
+    for (int rr = ty; rr < 32; rr += 8) {       // write along c (tx)
+        const int r = r0 + rr, c = c0 + tx;
+        if (r >= o.R || c >= o.Cp) continue;
+        const long long m = x[tx][rr];
+#pragma unroll
+        for (int q = 0; q < OZ_S; q++) o.D[side_dst(o, q, r, c)] = __float2bfloat16_rn(oz_digit(m, q));
     }
 }
 
-// C = 2^{ea_i + eb_j} sum_t 2^{-tW} (sum of level t's exact partials), the
-// levels from the smallest.
+// C = 2^{ea_i + eb_j} sum_t 2^{-tW} S_t, S_t the integer sum of level t's
+// exact partials (integer adds), the levels by Horner's rule from the
+// smallest (each step one exact scaling and one rounding FP64 add).
 __global__ void __launch_bounds__(256) k_oz_combine(const OzDev* g) {
     const OzDev d = g[blockIdx.y];
     const long long e = (long long)blockIdx.x * 256 + threadIdx.x;
@@ -169,11 +178,11 @@ __global__ void __launch_bounds__(256) k_oz_combine(const OzDev* g) {
     const long long mn = (long long)d.M * d.N;
     double acc = 0.0;
     for (int l = OZ_S - 1; l >= 0; l--) {
-        double sl = 0.0;
-        for (int c = 0; c < d.chunks[l]; c++) sl += (double)d.part[l][c * mn + e];
-        acc += ldexp(sl, -(l + 2) * OZ_W);
+        long long sl = 0;
+        for (int c = 0; c < d.chunks[l]; c++) sl += (long long)__float2int_rn(d.part[l][c * mn + e]);
+        acc = fma(acc, 1.0 / OZ_SLICE, (double)sl);
     }
-    d.C[(long long)i * d.ldc + j] = ldexp(acc, d.ea[i] + d.eb[j]);
+    d.C[(long long)i * d.ldc + j] = ldexp(acc, d.ea[i] + d.eb[j] - 2 * OZ_W);
 }
 
 int round_up_i(int a, int b) { return (a + b - 1) / b * b; }
@@ -186,9 +195,9 @@ struct OzPlan {
     long long maxMN;
     OzDev* dev;                          // n descriptors
     void* ws;                            // slices, exponents and partials
-    unsigned char* tabs;                 // per level: Args[n], start[n], grid[n]
-    GroupTab tab[OZ_S];
-    unsigned blocks[OZ_S];
+    unsigned char* tabs;                 // the member table: Args, start blocks, grids
+    GroupTab tab;                        // every (product, level) of the grouped Gram launch
+    unsigned blocks;
 };
 
 kfac_status_t oz_plan_create(const std::vector<OzGemm>& gemms, int* status, OzPlan** out) {
@@ -255,53 +264,62 @@ kfac_status_t oz_plan_create(const std::vector<OzGemm>& gemms, int* status, OzPl
     if (cudaMemcpy(p->dev, hd.data(), sizeof(OzDev) * p->n, cudaMemcpyHostToDevice) != cudaSuccess)
         return KFAC_CUDA_ERROR;
 
-    // member tables of the grouped Gram launches, one per level
+    // the member table of the grouped Gram launch: every (product, level),
+    // the members with the most blocks first
     using GC = tck::Cfg<tck::GRAM>;
     const size_t stride = (sizeof(tck::Args) + 63) / 64 * 64;
-    // each level's table starts on a 256-byte boundary (the tensor maps need 64)
-    const size_t per_level = (stride * p->n + 16 * (size_t)p->n + 32 + 255) / 256 * 256;
-    std::vector<unsigned char> host((size_t)OZ_S * per_level + 256, 0);
+    const int nm = p->n * OZ_S;
+    struct Mem {
+        int g, l;
+        unsigned blocks;
+    };
+    std::vector<Mem> mem;
+    for (int g = 0; g < p->n; g++) {
+        const OzDev& d = hd[g];
+        const int tiles = ((d.M + tck::BM - 1) / tck::BM) * ((d.N + GC::BN - 1) / GC::BN);
+        for (int l = 0; l < OZ_S; l++) mem.push_back(Mem{g, l, (unsigned)(tiles * d.chunks[l])});
+    }
+    std::stable_sort(mem.begin(), mem.end(), [](const Mem& x, const Mem& y) { return x.blocks > y.blocks; });
+    const size_t start_off = stride * nm;
+    const size_t grid_off = start_off + (sizeof(unsigned) * nm + 15) / 16 * 16;
+    std::vector<unsigned char> host(grid_off + sizeof(uint3) * nm + 16, 0);
     void* tv = nullptr;
     if ((st = kfac_device_alloc(&tv, host.size()))) return st;
     p->tabs = (unsigned char*)tv;
-    for (int l = 0; l < OZ_S; l++) {
-        const int t = l + 2;
-        const size_t lb = (size_t)l * per_level;
-        const size_t start_off = lb + stride * p->n;
-        const size_t grid_off = start_off + (sizeof(unsigned) * p->n + 15) / 16 * 16;
-        unsigned blocks = 0;
-        for (int g = 0; g < p->n; g++) {
-            const OzDev& d = hd[g];
-            tck::Args a;
-            memset(&a, 0, sizeof(a));
-            const int rows = (t - 1) * d.K;
-            const __nv_bfloat16* ybase = d.Y + (size_t)(OZ_S - t + 1) * d.K * d.Np;
-            if (!tc_make_tmap_2d(&a.a0, d.X, d.Mp, rows, (uint64_t)d.Mp * 2, 64, 64) ||
-                !tc_make_tmap_2d(&a.b0, ybase, d.Np, rows, (uint64_t)d.Np * 2, 64, 64))
-                return KFAC_CUDA_ERROR;
-            a.P = d.M;
-            a.Q = d.N;
-            a.rows = rows;
-            a.row_chunk = OZ_CHUNK;
-            a.sym = 0;
-            a.q_tiles = (d.N + GC::BN - 1) / GC::BN;
-            a.part = d.part[l];
-            a.status = status;
-            const int tiles = ((d.M + tck::BM - 1) / tck::BM) * a.q_tiles;
-            const uint3 grid = make_uint3(tiles, d.chunks[l], 1);
-            memcpy(host.data() + lb + stride * g, &a, sizeof(a));
-            memcpy(host.data() + start_off + sizeof(unsigned) * g, &blocks, sizeof(unsigned));
-            memcpy(host.data() + grid_off + sizeof(uint3) * g, &grid, sizeof(uint3));
-            blocks += (unsigned)tiles * d.chunks[l];
-        }
-        GroupTab& gt = p->tab[l];
-        gt.packs = p->tabs + lb;
-        gt.start = (const unsigned*)(p->tabs + start_off);
-        gt.grid = (const uint3*)(p->tabs + grid_off);
-        gt.n = p->n;
-        gt.stride = (int)stride;
-        p->blocks[l] = blocks;
+    unsigned long long blocks = 0;
+    for (int m = 0; m < nm; m++) {
+        const OzDev& d = hd[mem[m].g];
+        const int l = mem[m].l, t = l + 2;
+        tck::Args a;
+        memset(&a, 0, sizeof(a));
+        const int rows = (t - 1) * d.K;
+        const __nv_bfloat16* ybase = d.Y + (size_t)(OZ_S - t + 1) * d.K * d.Np;
+        if (!tc_make_tmap_2d(&a.a0, d.X, d.Mp, rows, (uint64_t)d.Mp * 2, 64, 64) ||
+            !tc_make_tmap_2d(&a.b0, ybase, d.Np, rows, (uint64_t)d.Np * 2, 64, 64))
+            return KFAC_CUDA_ERROR;
+        a.P = d.M;
+        a.Q = d.N;
+        a.rows = rows;
+        a.row_chunk = OZ_CHUNK;
+        a.sym = 0;
+        a.q_tiles = (d.N + GC::BN - 1) / GC::BN;
+        a.part = d.part[l];
+        a.status = status;
+        const int tiles = ((d.M + tck::BM - 1) / tck::BM) * a.q_tiles;
+        const uint3 grid = make_uint3(tiles, d.chunks[l], 1);
+        const unsigned b0 = (unsigned)blocks;
+        memcpy(host.data() + stride * m, &a, sizeof(a));
+        memcpy(host.data() + start_off + sizeof(unsigned) * m, &b0, sizeof(unsigned));
+        memcpy(host.data() + grid_off + sizeof(uint3) * m, &grid, sizeof(uint3));
+        blocks += (unsigned long long)tiles * d.chunks[l];
     }
+    if (blocks >= (1ull << 31)) return KFAC_BAD_ARG;
+    p->tab.packs = p->tabs;
+    p->tab.start = (const unsigned*)(p->tabs + start_off);
+    p->tab.grid = (const uint3*)(p->tabs + grid_off);
+    p->tab.n = nm;
+    p->tab.stride = (int)stride;
+    p->blocks = (unsigned)blocks;
     if (cudaMemcpy(p->tabs, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return KFAC_CUDA_ERROR;
     return KFAC_OK;
@@ -310,23 +328,18 @@ kfac_status_t oz_plan_create(const std::vector<OzGemm>& gemms, int* status, OzPl
 kfac_status_t oz_run(kfac_pinn_handle* h, OzPlan* p, cudaStream_t s) {
     const int n = p->n;
     const int maxC = std::max(p->maxMp, p->maxNp);
-    k_oz_exp_contig<<<dim3(ceil_div_u(maxC, 8), 2 * n), 256, 0, s>>>(p->dev);
-    KFAC_LAUNCH_CHECK(h);
-    k_oz_exp_strided<<<dim3(ceil_div_u(maxC, 256), 2 * n), 256, 0, s>>>(p->dev);
+    k_oz_exponents<<<dim3(ceil_div_u(maxC, 8), 2 * n), 256, 0, s>>>(p->dev);
     KFAC_LAUNCH_CHECK(h);
     k_oz_slice_direct<<<dim3(ceil_div_u(maxC, 256), p->maxK, 2 * n), 256, 0, s>>>(p->dev);
     KFAC_LAUNCH_CHECK(h);
     k_oz_slice_transpose<<<dim3(ceil_div_u(p->maxK, 32), ceil_div_u(maxC, 32), 2 * n), 256, 0, s>>>(p->dev);
     KFAC_LAUNCH_CHECK(h);
-    const GroupLaunchFn gram = tck::engine_group_launcher(tck::GRAM, false);
-    for (int l = 0; l < OZ_S; l++) {
-        const cudaError_t e = gram(p->tab[l], p->blocks[l], 0, s);
-        if (e != cudaSuccess) {
-            kfac_record_cuda_error(e);
-            return KFAC_CUDA_ERROR;
-        }
-        h->launches++;
+    const cudaError_t e = tck::engine_group_launcher(tck::GRAM, false)(p->tab, p->blocks, 0, s);
+    if (e != cudaSuccess) {
+        kfac_record_cuda_error(e);
+        return KFAC_CUDA_ERROR;
     }
+    h->launches++;
     k_oz_combine<<<dim3(ceil_div_u(p->maxMN, 256), n), 256, 0, s>>>(p->dev);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
