@@ -17,8 +17,9 @@
 //      deflation, secular equation by a safeguarded rational iteration, eigenvectors via the
 //      Gu-Eisenstat recomputed z, block GEMMs per merge level, the large ones
 //      on the tensor cores, ozaki.cu)
-//   5. back-transformation by the Householder reflectors (column-parallel)
-//   6. V = L^{-T} U                              (tensor cores, ozaki.cu)
+//   5. the reflectors' product Q_H = H_0 H_1 ... (column-parallel, applied to
+//      I) and W = L^{-T} Q_H, beside step 4 on a stream of the group's own
+//   6. V = W U = L^{-T} Q_H U                    (tensor cores, ozaki.cu)
 // The factor pairs form one group per cluster size of steps 1 and 3, whose
 // kernel sequences run on streams of their own at once.
 // Errors (a P that is not positive definite, a barrier that gave up) are
@@ -130,7 +131,10 @@ struct EigState {
     void* trsm_jobs_inv;        // ... and in the inverse (mode 3)
     OzPlan* oz_red1;            // Qa = L^{-1} M                 (tensor cores, ozaki.cu)
     OzPlan* oz_red2;            // M = Qa L^{-T}
-    OzPlan* oz_back;            // V = L^{-T} U
+    OzPlan* oz_w;               // W = L^{-T} Q_H (Q_H = the reflectors' product, formed in L; W into H)
+    OzPlan* oz_v;               // V = W U
+    cudaStream_t aux;           // Q_H and W beside the divide and conquer
+    cudaEvent_t ev_fork, ev_join;
     int n_trsm_jobs;
     size_t bt_smem;             // back-transform shared memory for the widest job
     std::vector<Level> levels;
@@ -1653,18 +1657,23 @@ inline size_t bt_smem_max() {
 // resource), then the rank-1 update.  The next reflector is loaded into
 // registers while the current one is applied (two buffers).
 template <int W>
-__device__ void bt_strip(const Prob& p, int c0, double* sm) {
+__device__ void bt_strip(const Prob& p, int c0, double* sm, bool form) {
     constexpr int RG = 256 / W;                  // row groups
     const int n = p.n;
     double* Us = sm;                             // n x W
     double* vb = Us + (size_t)n * W;             // two reflectors of n
     double* part = vb + 2 * (size_t)n;           // 8 x W
     double* tot = part + 8 * W;                  // W
-    double* U = p.final_buf ? p.Qb : p.Qa;
+    // form: Q_H = H_0 H_1 ... applied to I, into L (free once L^{-1} is formed)
+    double* U = form ? p.L : (p.final_buf ? p.Qb : p.Qa);
     const int cl = threadIdx.x % W, rg = threadIdx.x / W;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int c = c0 + cl;
-    for (int i = rg; i < n; i += RG) Us[i * W + cl] = (c < n) ? U[(long long)i * n + c] : 0.0;
+    for (int i = rg; i < n; i += RG)
+        Us[i * W + cl] = (c < n) ? (form ? (i == c ? 1.0 : 0.0) : U[(long long)i * n + c]) : 0.0;
+    // H_k acts on rows > k, so on e_c only when c > k: starting from I, the
+    // reflectors above the strip's last column leave it as it is
+    const int k_top = form ? min(n - 3, min(c0 + W, n) - 2) : n - 3;
     // reflector k occupies H[k][k+1 .. n); at most 4 values per thread (n <= 1024)
     auto fetch = [&](int k, double* r4) {
 #pragma unroll
@@ -1674,8 +1683,8 @@ __device__ void bt_strip(const Prob& p, int c0, double* sm) {
         }
     };
     double nx[4];
-    fetch(n - 3, nx);
-    for (int k = n - 3; k >= 0; k--) {
+    fetch(k_top, nx);
+    for (int k = k_top; k >= 0; k--) {
         const int b = k + 1, m = n - b;
         double* v = vb + (k & 1) * n;
 #pragma unroll
@@ -1710,15 +1719,16 @@ __device__ void bt_strip(const Prob& p, int c0, double* sm) {
 }
 
 // One CTA per back-transformation job (problem, first column, strip width):
-// the widths make the jobs' work about equal, the list is sorted largest first.
-__global__ void __launch_bounds__(256) k_backtransform(Prob* pr, const TrsmJob* jobs, int* fail) {
+// the widths make the jobs' work about equal, the list is sorted largest
+// first.  form: the reflectors' product Q_H itself (applied to I) into L.
+__global__ void __launch_bounds__(256) k_backtransform(Prob* pr, const TrsmJob* jobs, int* fail, int form) {
     extern __shared__ double bt_sm[];
     const TrsmJob jb = jobs[blockIdx.x];
     const Prob p = pr[jb.prob];
     if (fail[jb.prob] || jb.c0 >= p.n) return;
-    if (jb.cb == 8) bt_strip<8>(p, jb.c0, bt_sm);
-    else if (jb.cb == 16) bt_strip<16>(p, jb.c0, bt_sm);
-    else bt_strip<32>(p, jb.c0, bt_sm);
+    if (jb.cb == 8) bt_strip<8>(p, jb.c0, bt_sm, form != 0);
+    else if (jb.cb == 16) bt_strip<16>(p, jb.c0, bt_sm, form != 0);
+    else bt_strip<32>(p, jb.c0, bt_sm, form != 0);
 }
 
 __global__ void k_write_w(Prob* pr, int* fail) {
@@ -2103,7 +2113,7 @@ static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es) {
     }
     // the products with L^{-1} on the tensor cores
     {
-        std::vector<OzGemm> r1, r2, bk;
+        std::vector<OzGemm> r1, r2, wq, vv;
         for (const Prob& p : es->host) {
             const int n = p.n;
             OzGemm g;
@@ -2113,14 +2123,20 @@ static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es) {
             r1.push_back(g);
             g.A = p.Qa; g.B = p.Li; g.C = p.M; g.ta = false; g.tb = true;       // M = Qa L^{-T}
             r2.push_back(g);
-            g.A = p.Li; g.B = p.final_buf ? p.Qb : p.Qa; g.C = p.V;             // V = L^{-T} U
-            g.ta = true; g.tb = false;
-            bk.push_back(g);
+            g.A = p.Li; g.B = p.L; g.C = p.H; g.ta = true; g.tb = false;        // W = L^{-T} Q_H
+            wq.push_back(g);
+            g.A = p.H; g.B = p.final_buf ? p.Qb : p.Qa; g.C = p.V; g.ta = false; // V = W U
+            vv.push_back(g);
         }
         int* status = es->host[0].status;
         if ((st = oz_plan_create(r1, status, &es->oz_red1))) return st;
         if ((st = oz_plan_create(r2, status, &es->oz_red2))) return st;
-        if ((st = oz_plan_create(bk, status, &es->oz_back))) return st;
+        if ((st = oz_plan_create(wq, status, &es->oz_w))) return st;
+        if ((st = oz_plan_create(vv, status, &es->oz_v))) return st;
+        if (cudaStreamCreateWithFlags(&es->aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&es->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&es->ev_join, cudaEventDisableTiming) != cudaSuccess)
+            return KFAC_CUDA_ERROR;
     }
     cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(double) * (NB * (NB + 1) + 2 * NB * (CB_MAX + 1)));
@@ -2154,7 +2170,14 @@ static void group_free(EigState* es) {
     cudaFree(es->trsm_jobs_inv);
     oz_plan_free(es->oz_red1);
     oz_plan_free(es->oz_red2);
-    oz_plan_free(es->oz_back);
+    oz_plan_free(es->oz_w);
+    oz_plan_free(es->oz_v);
+    if (es->aux) {
+        cudaStreamSynchronize(es->aux);
+        cudaStreamDestroy(es->aux);
+    }
+    if (es->ev_fork) cudaEventDestroy(es->ev_fork);
+    if (es->ev_join) cudaEventDestroy(es->ev_join);
     for (auto& lv : es->levels) {
         oz_plan_free(lv.oz);
         cudaFree(lv.merges);
@@ -2234,6 +2257,22 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
                                          (int*)es->abort_flag, (int*)es->fail));
         h->launches++;
     }
+    // 5a. beside the divide and conquer (on the group's own stream): the
+    // reflectors' product Q_H (in L) and W = L^{-T} Q_H (in H), so that the
+    // back-transformation and V = L^{-T} Q_H U become one product afterwards
+    KFAC_CUDA_TRY(cudaEventRecord(es->ev_fork, s));
+    KFAC_CUDA_TRY(cudaStreamWaitEvent(es->aux, es->ev_fork, 0));
+    k_backtransform<<<es->n_trsm_jobs, 256, es->bt_smem, es->aux>>>(pr, (const TrsmJob*)es->trsm_jobs_upper,
+                                                                    es->fail, 1);
+    kfac_status_t st_aux = cudaGetLastError() == cudaSuccess ? KFAC_OK : KFAC_CUDA_ERROR;
+    h->launches++;
+    if (st_aux == KFAC_OK) st_aux = oz_run(h, es->oz_w, es->aux);
+    // the join is recorded even after an error so that s never runs ahead of aux
+    KFAC_CUDA_TRY(cudaEventRecord(es->ev_join, es->aux));
+    if (st_aux) {
+        KFAC_CUDA_TRY(cudaStreamWaitEvent(s, es->ev_join, 0));
+        return st_aux;
+    }
     // 4. divide and conquer
     k_dc_init<<<dim3(64, np), 256, 0, s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
@@ -2267,10 +2306,9 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
             KFAC_LAUNCH_CHECK(h);
         }
     }
-    // 5. back-transformation, 6. V = L^{-T} U
-    k_backtransform<<<es->n_trsm_jobs, 256, es->bt_smem, s>>>(pr, (const TrsmJob*)es->trsm_jobs, es->fail);
-    KFAC_LAUNCH_CHECK(h);
-    KFAC_TRY(oz_run(h, es->oz_back, s));
+    // 5b, 6. V = L^{-T} Q_H U = W U
+    KFAC_CUDA_TRY(cudaStreamWaitEvent(s, es->ev_join, 0));
+    KFAC_TRY(oz_run(h, es->oz_v, s));
     k_write_w<<<np, 256, 0, s>>>(pr, es->fail);
     KFAC_LAUNCH_CHECK(h);
     return KFAC_OK;
