@@ -130,23 +130,41 @@ kfac_status_t dal(T** p, size_t n) {
 // ============================================================================
 
 // theta (FP64, column-stacked W~_l) -> BF16 hi/lo row-major W (hout_p x hin_p),
-// BF16 transposed Wt (hin_p x hout_p), FP32 bias; zero padding.
+// BF16 transposed Wt (hin_p x hout_p), FP32 bias; zero padding.  One 32 x 32
+// tile per block through shared memory, so that the reads (along i) and both
+// layouts' writes are coalesced.
 struct k_convert_weights {
     static constexpr int THREADS = EW;
-    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const double* __restrict__ W, int hout, int hin, int hout_p,
-                               int hin_p, bf16* Whi, bf16* Wlo, bf16* Wt, bf16* Wt_lo, float* bias) {
-        long long idx = (long long)vb.x * blockDim.x + threadIdx.x;
-        if (idx >= (long long)hout_p * hin_p) return;
-        int i = (int)(idx / hin_p), k = (int)(idx % hin_p);
-        // one FP64 operation per element (the conversion); the split is done in FP32
-        float v = (i < hout && k < hin) ? (float)W[i + (long long)hout * k] : 0.f;
-        bf16 hi = __float2bfloat16_rn(v);
-        bf16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        Whi[idx] = hi;
-        Wlo[idx] = lo;
-        Wt[(long long)k * hout_p + i] = hi;
-        if (Wt_lo) Wt_lo[(long long)k * hout_p + i] = lo;
-        if (k == 0) bias[i] = (i < hout) ? (float)W[i + (long long)hout * hin] : 0.f;
+    __device__ __noinline__ static void run(uint3 vb, uint3 vg, const double* __restrict__ W, int hout, int hin,
+                                            int hout_p, int hin_p, bf16* Whi, bf16* Wlo, bf16* Wt, bf16* Wt_lo,
+                                            float* bias) {
+        __shared__ float t[32][33];
+        const int k0 = vb.x * 32, i0 = vb.y * 32;
+        const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+        for (int kk = ty; kk < 32; kk += 8) {       // read along i
+            const int i = i0 + tx, k = k0 + kk;
+            // one FP64 operation per element (the conversion); the split is done in FP32
+            t[kk][tx] = (i < hout && k < hin) ? (float)W[i + (long long)hout * k] : 0.f;
+        }
+        __syncthreads();
+        for (int kk = ty; kk < 32; kk += 8) {       // W^T along i
+            const int i = i0 + tx, k = k0 + kk;
+            if (i >= hout_p || k >= hin_p) continue;
+            const float v = t[kk][tx];
+            const bf16 hi = __float2bfloat16_rn(v);
+            Wt[(long long)k * hout_p + i] = hi;
+            if (Wt_lo) Wt_lo[(long long)k * hout_p + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        }
+        for (int ii = ty; ii < 32; ii += 8) {       // W along k
+            const int i = i0 + ii, k = k0 + tx;
+            if (i >= hout_p || k >= hin_p) continue;
+            const float v = t[tx][ii];
+            const bf16 hi = __float2bfloat16_rn(v);
+            Whi[(long long)i * hin_p + k] = hi;
+            Wlo[(long long)i * hin_p + k] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        }
+        if (k0 == 0 && ty == 0 && i0 + tx < hout_p)
+            bias[i0 + tx] = (i0 + tx < hout) ? (float)W[i0 + tx + (long long)hout * hin] : 0.f;
     }
 };
 
@@ -1257,7 +1275,8 @@ kfac_status_t convert_weights_into(kfac_pinn_handle* h, cudaStream_t s, const do
     for (int l = 2; l <= L - 1; l++) {
         int hout = h->dims[l], hin = h->dims[l - 1];
         int hout_p = round_up(hout, 64), hin_p = round_up(hin, 64);
-        KFAC_TRY(KL<k_convert_weights>(h, s, ceil_div_u((long long)hout_p * hin_p, EW), 0, theta + h->woff[l - 1],
+        KFAC_TRY(KL<k_convert_weights>(h, s, dim3(ceil_div_u(hin_p, 32), ceil_div_u(hout_p, 32)), 0,
+                                       theta + h->woff[l - 1],
                                        hout, hin, hout_p, hin_p, w.W_hi[l - 1], w.W_lo[l - 1], w.Wt[l - 1],
                                        w.Wt_lo[l - 1], w.bias[l - 1]));
     }
