@@ -151,9 +151,7 @@ struct EigState {
 // of batched kernels, the groups on streams of their own: the largest
 // problems' latency-bound stages hold only part of the GPU, and the smaller
 // problems fill the idle SMs meanwhile.
-constexpr int MAX_GROUPS = 12;   // a handle: cluster sizes 16, 8, 4, 2, 1 and the cooperative kernel;
-                                 // a batch: up to BATCH_GROUPS, several per cluster size
-constexpr int BATCH_GROUPS = 8;
+constexpr int MAX_GROUPS = 6;    // cluster sizes 16, 8, 4, 2, 1 and the cooperative kernel
 
 struct EigAll {
     EigState* g[MAX_GROUPS];
@@ -2438,12 +2436,11 @@ static kfac_status_t eigall_run(kfac_pinn_handle* h, EigAll* ea, cudaStream_t s)
 kfac_status_t eig_run(kfac_pinn_handle* h, cudaStream_t s) { return eigall_run(h, EA(h), s); }
 
 // The eigensolves of many handles at once over the problems' own workspaces:
-// every factor pair of every handle, grouped by cluster size as for a single
-// handle (a problem is solved by the same kernels with the same cluster size
-// as in its own handle's eigensolve), each size's problems dealt, largest
-// first, over several groups on streams of their own (up to BATCH_GROUPS in
-// all, by the sizes' shares of the n^3 work), so that the stages of one group
-// (whose launches wait for their slowest problem) overlap those of others.
+// every factor pair of every handle, one group per cluster size as for a
+// single handle (a problem is solved by the same kernels with the same cluster
+// size as in its own handle's eigensolve).  Dealing a size's problems over
+// several groups on more streams was measured 2 % faster for the 64-problem
+// batch at twice the launches, and is not done.
 kfac_status_t eig_batch_alloc(kfac_pinn_handle* const* hs, int count, void** out) {
     *out = nullptr;
     if (count < 1) return KFAC_BAD_ARG;
@@ -2454,33 +2451,16 @@ kfac_status_t eig_batch_alloc(kfac_pinn_handle* const* hs, int count, void** out
         for (int g = 0; g < ea->ng; g++)
             for (const Prob& p : ea->g[g]->host) byclass[class_rank(pair_class(p.n, hs[0]))].push_back(p);
     }
-    if ((int)byclass.size() > BATCH_GROUPS) return KFAC_BAD_ARG;
-    double total = 0.0;
-    std::map<int, double> work;
-    for (auto& kv : byclass) {
-        double w = 0.0;
-        for (const Prob& p : kv.second) w += (double)p.n * p.n * p.n;
-        work[kv.first] = w;
-        total += w;
-    }
+    if ((int)byclass.size() > MAX_GROUPS) return KFAC_BAD_ARG;
     EigAll* ea = new EigAll();
     memset(ea, 0, sizeof(*ea));
     *out = ea;
-    int spare = BATCH_GROUPS - (int)byclass.size();
     kfac_status_t st;
     for (auto& kv : byclass) {
-        std::vector<Prob>& list = kv.second;
-        int k = 1 + (total > 0 ? (int)floor(spare * work[kv.first] / total) : 0);
-        k = std::min(k, (int)list.size());
-        std::stable_sort(list.begin(), list.end(), [](const Prob& x, const Prob& y) { return x.n > y.n; });
-        std::vector<std::vector<Prob>> parts(k);
-        for (size_t i = 0; i < list.size(); i++) parts[i % k].push_back(list[i]);
-        for (auto& part : parts) {
-            EigState* es = new EigState();
-            ea->g[ea->ng++] = es;
-            es->host = part;
-            if ((st = group_schedule(hs[0], es))) return st;
-        }
+        EigState* es = new EigState();
+        ea->g[ea->ng++] = es;
+        es->host = kv.second;
+        if ((st = group_schedule(hs[0], es))) return st;
     }
     return eigall_streams(ea);
 }
