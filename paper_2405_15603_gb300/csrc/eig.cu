@@ -129,7 +129,9 @@ struct EigState {
     void* trsm_jobs;            // TrsmJob list, largest work first (also the back-transform's)
     void* trsm_jobs_upper;      // the same jobs ordered by their work in the upper-triangle solve (mode 1)
     void* trsm_jobs_inv;        // ... and in the inverse (mode 3)
-    OzPlan* oz_red1;            // Qa = L^{-1} M                 (tensor cores, ozaki.cu)
+    OzPlan* oz_inv1;            // T = L21 X11 of the split inverses (tensor cores, ozaki.cu)
+    OzPlan* oz_inv2;            // X21 = -X22 T
+    OzPlan* oz_red1;            // Qa = L^{-1} M
     OzPlan* oz_red2;            // M = Qa L^{-T}
     OzPlan* oz_w;               // W = L^{-T} Q_H (Q_H = the reflectors' product, formed in L; W into H)
     OzPlan* oz_v;               // V = W U
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(256) k_chol_update(Prob* pr, int k0, int* fail
 // --------------------------------------------------------------------------
 // One column strip [c0, c0 + CB) of a triangular solve with NB x NB blocks.
 template <int CB>
-__device__ void trsm_strip(const Prob& p, int c0, int mode, bool failed, double* sm) {
+__device__ void trsm_strip(const Prob& p, int c0, int mode, bool failed, double* sm, int r_end) {
     constexpr int TRSM_RG = 256 / CB;      // row groups of the 256 threads
     double* Lb = sm;                       // NB x (NB+1)
     double* Xk = Lb + NB * (NB + 1);       // NB x (CB+1)
@@ -383,7 +385,8 @@ __device__ void trsm_strip(const Prob& p, int c0, int mode, bool failed, double*
     // mode 1: the row blocks down to the strip's last column; mode 3 (the
     // inverse, right-hand side I): from the block of the strip's first column,
     // the rows above it being zero
-    const int nrun = (mode == 1) ? min(nblk, (c0 + ncb - 1) / NB + 1) : nblk;
+    const int nrun = (mode == 1) ? min(nblk, (c0 + ncb - 1) / NB + 1)
+                                 : (mode == 3 ? min(nblk, (r_end + NB - 1) / NB) : nblk);
     const int s0 = (mode == 3) ? c0 / NB : 0;
     for (int s = s0; s < nrun; s++) {
         const int ib = upper ? nblk - 1 - s : s;
@@ -467,7 +470,13 @@ __device__ void trsm_strip(const Prob& p, int c0, int mode, bool failed, double*
 // others) and the list is sorted by work, largest first.
 struct TrsmJob {
     int prob, c0, cb;
+    int r_end;       // mode 3: rows solved end here (the first diagonal block of a split inverse)
 };
+
+// Factors from this size get L^{-1} as [X11 0; X21 X22]: the diagonal blocks
+// by strip solves, X21 = -X22 (L21 X11) by two emulated products.
+constexpr int INV_SPLIT_FROM = 256;
+inline int inv_split(int n) { return n >= INV_SPLIT_FROM ? (n / 2 + NB - 1) / NB * NB : 0; }
 
 __global__ void __launch_bounds__(256, 2) k_trsm(Prob* pr, const TrsmJob* jobs, int mode, int* fail) {
     extern __shared__ double sm[];
@@ -475,9 +484,9 @@ __global__ void __launch_bounds__(256, 2) k_trsm(Prob* pr, const TrsmJob* jobs, 
     const Prob p = pr[jb.prob];
     if (jb.c0 >= p.n) return;
     const bool failed = fail[jb.prob] != 0;
-    if (jb.cb == 8) trsm_strip<8>(p, jb.c0, mode, failed, sm);
-    else if (jb.cb == 16) trsm_strip<16>(p, jb.c0, mode, failed, sm);
-    else trsm_strip<32>(p, jb.c0, mode, failed, sm);
+    if (jb.cb == 8) trsm_strip<8>(p, jb.c0, mode, failed, sm, jb.r_end);
+    else if (jb.cb == 16) trsm_strip<16>(p, jb.c0, mode, failed, sm, jb.r_end);
+    else trsm_strip<32>(p, jb.c0, mode, failed, sm, jb.r_end);
 }
 
 // Inverse of every 64 x 64 diagonal block of L (lower triangular), one CTA
@@ -1959,7 +1968,7 @@ static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es) {
         for (int i = 0; i < es->np; i++) {
             const int n = es->host[i].n;
             const int cb = strip_width(n);
-            for (int c0 = 0; c0 < n; c0 += cb) jobs.push_back(TrsmJob{i, c0, cb});
+            for (int c0 = 0; c0 < n; c0 += cb) jobs.push_back(TrsmJob{i, c0, cb, n});
         }
         std::stable_sort(jobs.begin(), jobs.end(), [&](const TrsmJob& x, const TrsmJob& y) {
             const double wx = (double)es->host[x.prob].n * es->host[x.prob].n * x.cb;
@@ -1981,9 +1990,14 @@ static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es) {
                          [&](const TrsmJob& x, const TrsmJob& y) { return upper_work(x) > upper_work(y); });
         if ((ast = kfac_device_alloc(&es->trsm_jobs_upper, sizeof(TrsmJob) * jobs.size())) != KFAC_OK) return ast;
         cudaMemcpy(es->trsm_jobs_upper, jobs.data(), sizeof(TrsmJob) * jobs.size(), cudaMemcpyHostToDevice);
-        // the inverse's strip runs from the block of its first column down
+        // the inverse's strip runs from the block of its first column down, in a
+        // split inverse down to the end of the strip's diagonal block
+        for (TrsmJob& j : jobs) {
+            const int n1 = inv_split(es->host[j.prob].n);
+            j.r_end = (n1 > 0 && j.c0 < n1) ? n1 : es->host[j.prob].n;
+        }
         auto inv_work = [&](const TrsmJob& j) {
-            const double e = es->host[j.prob].n - (j.c0 / NB) * NB;
+            const double e = j.r_end - (j.c0 / NB) * NB;
             return e * e * j.cb;
         };
         std::stable_sort(jobs.begin(), jobs.end(),
@@ -2113,9 +2127,25 @@ static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es) {
     }
     // the products with L^{-1} on the tensor cores
     {
-        std::vector<OzGemm> r1, r2, wq, vv;
+        std::vector<OzGemm> r1, r2, wq, vv, i1, i2;
         for (const Prob& p : es->host) {
             const int n = p.n;
+            const int n1 = inv_split(n), n2 = n - n1;
+            if (n1 > 0) {          // T = L21 X11 (into Qa, n2 x n1), X21 = -X22 T
+                OzGemm t;
+                t.A = p.L + (size_t)n1 * n; t.lda = n;
+                t.B = p.Li; t.ldb = n;
+                t.C = p.Qa; t.ldc = n1;
+                t.M = n2; t.N = n1; t.K = n1;
+                i1.push_back(t);
+                OzGemm x;
+                x.A = p.Li + (size_t)n1 * n + n1; x.lda = n;
+                x.B = p.Qa; x.ldb = n1;
+                x.C = p.Li + (size_t)n1 * n; x.ldc = n;
+                x.M = n2; x.N = n1; x.K = n2;
+                x.alpha = -1.0;
+                i2.push_back(x);
+            }
             OzGemm g;
             g.M = g.N = g.K = n;
             g.lda = g.ldb = g.ldc = n;
@@ -2129,6 +2159,10 @@ static kfac_status_t group_schedule(kfac_pinn_handle* h0, EigState* es) {
             vv.push_back(g);
         }
         int* status = es->host[0].status;
+        if (!i1.empty()) {
+            if ((st = oz_plan_create(i1, status, &es->oz_inv1))) return st;
+            if ((st = oz_plan_create(i2, status, &es->oz_inv2))) return st;
+        }
         if ((st = oz_plan_create(r1, status, &es->oz_red1))) return st;
         if ((st = oz_plan_create(r2, status, &es->oz_red2))) return st;
         if ((st = oz_plan_create(wq, status, &es->oz_w))) return st;
@@ -2170,6 +2204,8 @@ static void group_free(EigState* es) {
     cudaFree(es->trsm_jobs_inv);
     oz_plan_free(es->oz_red1);
     oz_plan_free(es->oz_red2);
+    oz_plan_free(es->oz_inv1);
+    oz_plan_free(es->oz_inv2);
     oz_plan_free(es->oz_w);
     oz_plan_free(es->oz_v);
     if (es->aux) {
@@ -2225,6 +2261,10 @@ static kfac_status_t group_run(kfac_pinn_handle* h, EigState* es, cudaStream_t s
     // L^{-1} on the FP64 cores, then M = L^{-1} Q L^{-T} on the tensor cores
     k_trsm<<<es->n_trsm_jobs, 256, smem_trsm, s>>>(pr, (const TrsmJob*)es->trsm_jobs_inv, 3, es->fail);
     KFAC_LAUNCH_CHECK(h);
+    if (es->oz_inv1) {
+        KFAC_TRY(oz_run(h, es->oz_inv1, s));
+        KFAC_TRY(oz_run(h, es->oz_inv2, s));
+    }
     KFAC_TRY(oz_run(h, es->oz_red1, s));
     KFAC_TRY(oz_run(h, es->oz_red2, s));
     k_symmetrize<<<dim3(64, np), 256, 0, s>>>(pr, es->fail);

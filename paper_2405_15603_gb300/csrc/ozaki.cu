@@ -44,6 +44,7 @@ struct OzDev {
     long long lda, ldb, ldc;
     int M, N, K, Mp, Np;
     int ta, tb;                         // A given as A^T (K x M), B as B^T (N x K)
+    double alpha;
     __nv_bfloat16* X;                   // S blocks of K x Mp: slice p of A^T in block p - 1
     __nv_bfloat16* Y;                   // S blocks of K x Np: slice q of B in block S - q
     int* ea;                            // M
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(256) k_oz_combine(const OzDev* g) {
         for (int c = 0; c < d.chunks[l]; c++) sl += (long long)__float2int_rn(d.part[l][c * mn + e]);
         acc = fma(acc, 1.0 / OZ_SLICE, (double)sl);
     }
-    d.C[(long long)i * d.ldc + j] = ldexp(acc, d.ea[i] + d.eb[j] - 2 * OZ_W);
+    d.C[(long long)i * d.ldc + j] = d.alpha * ldexp(acc, d.ea[i] + d.eb[j] - 2 * OZ_W);
 }
 
 int round_up_i(int a, int b) { return (a + b - 1) / b * b; }
@@ -227,6 +228,7 @@ kfac_status_t oz_plan_create(const std::vector<OzGemm>& gemms, int* status, OzPl
         d.A = G.A; d.B = G.B; d.C = G.C;
         d.lda = G.lda; d.ldb = G.ldb; d.ldc = G.ldc;
         d.M = G.M; d.N = G.N; d.K = G.K;
+        d.alpha = G.alpha;
         d.ta = G.ta ? 1 : 0;
         d.tb = G.tb ? 1 : 0;
         d.Mp = round_up_i(G.M, 64);

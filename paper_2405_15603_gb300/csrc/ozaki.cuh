@@ -7,7 +7,7 @@
 #include "kfac_internal.cuh"
 
 // C = A B with A (M x K), B (K x N) and C (M x N) row-major FP64 matrices with
-// leading dimensions lda, ldb, ldc (elements); K <= OZ_MAX_K.  ta: the memory
+// leading dimensions lda, ldb, ldc (elements) (times alpha); K <= OZ_MAX_K.  ta: the memory
 // at A holds A^T (K x M, row-major); tb: the memory at B holds B^T (N x K).
 struct OzGemm {
     const double* A;
@@ -18,6 +18,7 @@ struct OzGemm {
     long long ldc;
     int M, N, K;
     bool ta = false, tb = false;
+    double alpha = 1.0;              // C = alpha A B, alpha a power of two or its negative
 };
 
 constexpr int OZ_MAX_K = 4096;
