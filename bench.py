@@ -208,8 +208,11 @@ def run_gpu(args, rank, world, local_rank):
     seed = replica_seed(rank)
 
     def new_opt(precision):
-        return KfacPinn(prob.d, widths, device=str(dev), precision=precision,
-                        max_n_int=WORKLOAD.n_int, max_n_bdy=WORKLOAD.n_bdy, **HYPER)
+        o = KfacPinn(prob.d, widths, device=str(dev), precision=precision,
+                     max_n_int=WORKLOAD.n_int, max_n_bdy=WORKLOAD.n_bdy, **HYPER)
+        if args.cta_pairs:
+            o.set_cta_pairs(True)
+        return o
 
     def to_dev(batch):
         return tuple(torch.tensor(a, device=dev) for a in batch)
@@ -346,6 +349,8 @@ def run_gpu(args, rank, world, local_rank):
     alu = measure_alu_peaks(dev)
 
     traffic = profile_traffic(WORKLOAD.n_int + WORKLOAD.n_bdy)
+    if args.cta_pairs:
+        traffic.pop("layer_gemm", None)     # the captured counters are the single-CTA kernels'
 
     def class_roofline(name, rec):
         per_launch_ms = rec["ms"] / max(rec["launches"], 1)
@@ -403,6 +408,7 @@ def run_gpu(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD_NAME, "d": prob.d, "widths": list(widths),
                    "n_int": WORKLOAD.n_int, "n_bdy": WORKLOAD.n_bdy, "precision": args.precision,
                    "variant": "expand", **HYPER, "parallelism": f"replicas{world}",
+                   "cta_pairs": bool(args.cta_pairs),
                    "l2": "flushed between steps (256 MiB write outside the step events)"},
         "e2e": e2e, "gpu_launches": int(launches), "graph": "steps replayed as one CUDA graph (kfac_pinn_set_graph)",
         "kernel_timing": "per-launch CUDA events on the launching stream, in a second eager pass of the same "
@@ -913,6 +919,8 @@ def run_profile_step(args):
                    max_n_bdy=WORKLOAD.n_bdy, **HYPER)
     opt.set_graph(True)
     opt.set_autotune(True)
+    if args.cta_pairs:
+        opt.set_cta_pairs(True)
     theta = torch.tensor(si.xavier_theta(prob.d, widths, 0), device=dev)
     for k in range(args.warmup):
         opt.step(theta, *batches[k])
@@ -957,6 +965,8 @@ def main():
                          "Laplacian, 5-d training, many PINNs)")
     ap.add_argument("--many", action="store_true",
                     help="64 uneven PINNs stepped as one batch (CUDA graph) instead of the step bench")
+    ap.add_argument("--cta-pairs", action="store_true",
+                    help="forward layer GEMMs on CTA pairs (kfac_pinn_set_cta_pairs; off by default)")
     ap.add_argument("--points", default=None,
                     help="N_INT,N_BDY override (smaller cases for profiler captures; not the headline)")
     args = ap.parse_args()

@@ -231,6 +231,18 @@ kfac_status_t kfac_pinn_forward_laplacian_backward(kfac_handle_t h, void* stream
  * not grow with N.  Default: disabled. */
 kfac_status_t kfac_pinn_set_store_forward(kfac_handle_t h, int enable);
 
+/* CTA pairs for the forward layer GEMMs of the tensor-core precisions (no
+ * counterpart in the paper: a kernel option).  When enabled, each 128-point
+ * block of the layer GEMMs T^{(l)} = T^{(l-1)} W~_l^T (Sec. 3.1, Eq. 5) runs
+ * with the next point block on a cluster of two CTAs that share one 256-row
+ * tensor-core product, each loading half of the weight tile (an odd number
+ * of point blocks leaves one CTA of the last pair idle).  The products and their
+ * order are the same either way (the results are bit-identical).  No effect on the
+ * FP64 and FP32 precisions.  Default: disabled (on GB300 the pair form fed
+ * 25 % fewer bytes per SM but ran the benchmark's step about 3 % slower).
+ * Errors: KFAC_BAD_ARG for a NULL handle. */
+kfac_status_t kfac_pinn_set_cta_pairs(kfac_handle_t h, int enable);
+
 /* Graph mode for kfac_pinn_step and kfac_pinn_step_host (no counterpart in the
  * paper: a runtime option).  When enabled, a step copies its batch into the
  * handle's staging buffers (device to device; step_host copies there from the

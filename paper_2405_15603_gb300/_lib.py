@@ -21,6 +21,7 @@ EXPORTS = [
     "kfac_pinn_get_update_coefficients", "kfac_pinn_batch_create", "kfac_pinn_batch_destroy",
     "kfac_pinn_batch_step", "kfac_pinn_last_cuda_error", "kfac_pinn_last_cuda_error_string",
     "kfac_pinn_set_store_forward",
+    "kfac_pinn_set_cta_pairs",
     "kfac_pinn_set_graph", "kfac_pinn_set_autotune", "kfac_pinn_get_tuning", "kfac_pinn_set_tuning",
     "kfac_pinn_check_wait_timeout", "kfac_pinn_inject_alloc_failure", "kfac_pinn_batch_set_grouped",
     "kfac_pinn_batch_launches",
@@ -108,6 +109,7 @@ def load() -> C.CDLL:
         "kfac_pinn_get_update_coefficients": (st, [H, P, P]),
         "kfac_pinn_last_cuda_error": (I, []),
         "kfac_pinn_set_store_forward": (st, [H, I]),
+        "kfac_pinn_set_cta_pairs": (st, [H, I]),
         "kfac_pinn_set_graph": (st, [H, I]),
         "kfac_pinn_set_autotune": (st, [H, I]),
         "kfac_pinn_get_tuning": (st, [H, C.POINTER(KfacTuneEntry), I, C.POINTER(C.c_int)]),

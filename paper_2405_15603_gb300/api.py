@@ -154,6 +154,11 @@ class KfacPinn:
         """Reverse mode reuses the last forward pass's activations (same theta, X) instead of recomputing."""
         _check("kfac_pinn_set_store_forward", self.lib.kfac_pinn_set_store_forward(self.h, int(enable)))
 
+    def set_cta_pairs(self, enable: bool = True):
+        """Forward layer GEMMs of the tensor-core precisions on CTA pairs
+        (kfac_pinn_set_cta_pairs; off by default, bit-identical results)."""
+        _check("kfac_pinn_set_cta_pairs", self.lib.kfac_pinn_set_cta_pairs(self.h, int(enable)))
+
     def set_graph(self, enable: bool = True):
         """Run step / step_host as a captured CUDA graph (kfac_pinn_set_graph):
         the batch is staged into the handle's buffers, the second step is

@@ -555,6 +555,7 @@ kfac_status_t kfac_pinn_create(const kfac_config_t* cfg, kfac_handle_t* out) {
     kfac_pinn_handle* h = (kfac_pinn_handle*)calloc(1, sizeof(kfac_pinn_handle));
     if (!h) return KFAC_OOM;
     h->cfg = *cfg;
+    h->cta_pairs = 0;
     KFAC_CUDA_TRY(cudaGetDevice(&h->device));
     KFAC_CUDA_TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
     h->dims[0] = cfg->d;
@@ -706,6 +707,13 @@ kfac_status_t kfac_pinn_set_store_forward(kfac_handle_t h, int enable) {
     if (!h) return KFAC_BAD_ARG;
     h->store_forward = enable ? 1 : 0;
     h->fwd_valid = 0;
+    return KFAC_OK;
+}
+
+kfac_status_t kfac_pinn_set_cta_pairs(kfac_handle_t h, int enable) {
+    if (!h) return KFAC_BAD_ARG;
+    h->cta_pairs = enable ? 1 : 0;
+    handle_graph_free(h);
     return KFAC_OK;
 }
 

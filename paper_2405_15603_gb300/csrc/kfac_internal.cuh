@@ -107,6 +107,9 @@ struct kfac_pinn_handle {
     // reverse mode with stored activations: the interior pass buffers hold the
     // forward Laplacian of (fwd_theta, fwd_X, fwd_N) while fwd_valid is set
     int store_forward;
+    // the forward layer GEMMs of the tensor-core precisions on CTA pairs
+    // (kfac_pinn_set_cta_pairs; off by default)
+    int cta_pairs;
     // graph mode (kfac_pinn_set_graph): a batch of this handle alone; in_graph
     // marks the eager step run inside it (capture or first call)
     int graph_mode;

@@ -5,7 +5,12 @@
 //   warp 1      MMA issuer (one elected lane) + TMEM owner
 //   warps 2..9  epilogue: TMEM -> registers -> fused math -> global
 // Accumulators live in TMEM, double buffered, so the epilogue of one tile
-// overlaps the MMAs of the next.  A CTA walks a short list of output tiles
+// overlaps the MMAs of the next.
+// The forward modes also run on CTA pairs (clusters of two, tc_engine_pair):
+// the two CTAs take consecutive 128-point blocks of the same 128 output
+// features, each loads its own A rows and HALF of the weight rows, and the
+// even CTA issues 256-row MMAs (cta_group::2) over both CTAs' shared memory,
+// so each SM receives 24 KB instead of 32 KB per 64-deep K block of a tile.  A CTA walks a short list of output tiles
 // (e.g. the Taylor columns s of one point block) so that per-(point, feature)
 // state such as tanh'(a_0) or the running sum of squared tangents stays in
 // registers across tiles.
@@ -68,10 +73,12 @@ struct Args {
     const __nv_bfloat16* ytan_lo;   // BWD_TAN: low half of y_i
 };
 
-template <int MODE, bool SPLIT = false>
+template <int MODE, bool SPLIT = false, bool PAIR = false>
 struct Cfg {
+    static_assert(!PAIR || MODE == FWD_VALUE || MODE == FWD_TANLAP, "CTA pairs: forward modes only");
     static constexpr bool MN = (MODE == GRAM);
     static constexpr int BN = MN ? 256 : 128;
+    static constexpr int BN_CTA = PAIR ? BN / 2 : BN;     // weight rows one CTA loads
     // Two-slot stages: a stage holds two A and two B boxes (each one 64-wide K
     // block, one 128-byte-swizzled TMA box).  A tile with a single product per
     // K block fills the slots with two consecutive K blocks (half the barrier
@@ -87,16 +94,18 @@ struct Cfg {
         (MODE == FWD_VALUE || MODE == FWD_TANLAP || MODE == JDOT) ||
         (SPLIT && (MODE == BWD_LAP || MODE == BWD_TAN || MODE == BWD_VALUE));
     static constexpr int SLOTS = FUSED ? 2 : 1;
-    static constexpr int STAGES = MN ? 4 : (FUSED ? 3 : 6);
+    static constexpr int STAGES = MN ? 4 : (PAIR ? 4 : (FUSED ? 3 : 6));
     static constexpr int SLOT_A = BM * BK * 2;
-    static constexpr int SLOT_B = BN * BK * 2;
+    static constexpr int SLOT_B = BN_CTA * BK * 2;
     static constexpr int A_BYTES = SLOTS * SLOT_A;
     static constexpr int B_BYTES = SLOTS * SLOT_B;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
     static constexpr int TMEM_COLS = MN ? 256 : 2 * BN;
     static constexpr int NBUF = MN ? 1 : 2;
-    static constexpr uint32_t IDESC = tc::idesc_bf16(BM, BN, MN ? 1 : 0, MN ? 1 : 0);
+    static constexpr uint32_t IDESC = tc::idesc_bf16(PAIR ? 2 * BM : BM, BN, MN ? 1 : 0, MN ? 1 : 0);
+    // bytes one stage's full barrier waits for (a pair's even CTA counts both CTAs' loads)
+    static constexpr uint32_t TX_BYTES = PAIR ? 2 * STAGE_BYTES : STAGE_BYTES;
 };
 
 // Number of accumulation terms of tile s (split-BF16 on value/Laplacian rows).
@@ -179,9 +188,20 @@ KFAC_DEV void load16_f32(const float* src, float* v) {
 // (tc_engine.cu) is compiled without floating-point contraction: every FMA is
 // an explicit fmaf, so the two copies round alike and a member of a grouped
 // launch computes exactly what its own launch computes.
-template <int MODE, bool SPLIT>
+//
+// PAIR: the CTA is one of a cluster of two (tc_engine_pair).  vb.x is then
+// 2 j + r for feature tile j and rank r in the pair, vb.y the pair of point
+// blocks (2 vb.y + r), so that, as in the single-CTA grid, the CTAs that run
+// together share their point block's rows (in L2) across the feature tiles.  The
+// even CTA's full barriers count both CTAs' TMA bytes and its MMA thread
+// issues the pair MMAs; their commits arrive on the stage and accumulator
+// barriers of both CTAs; both CTAs' epilogue warps arrive on the even CTA's
+// accumulator-empty barriers.  The pair synchronises (barrier.cluster) after
+// the set-up and before leaving, so that neither CTA leaves while the other
+// may still touch its shared memory.
+template <int MODE, bool SPLIT, bool PAIR = false>
 KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
-    using C = Cfg<MODE, SPLIT>;
+    using C = Cfg<MODE, SPLIT, PAIR>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ uint64_t full_bar[C::STAGES], empty_bar[C::STAGES];
@@ -190,6 +210,7 @@ KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
     __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t rank = PAIR ? tc::cluster_ctarank() : 0u;
 
     // ---- tile geometry ----------------------------------------------------
     int p0, j0, s_begin, s_end, k_begin = 0, k_steps;
@@ -211,8 +232,8 @@ KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
         k_steps = (k_end - k_begin + BK - 1) / BK;
         s_begin = 0; s_end = 1;
     } else {
-        j0 = vb.x * C::BN;
-        p0 = vb.y * BM;
+        j0 = (PAIR ? (vb.x >> 1) : vb.x) * C::BN;
+        p0 = (PAIR ? 2 * vb.y + (vb.x & 1) : vb.y) * BM;
         k_steps = a.k_steps;                              // 64-wide K blocks (one-slot modes)
         tile_range<MODE>(a, vb, s_begin, s_end);
     }
@@ -220,7 +241,10 @@ KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < C::STAGES; i++) { tc::mbar_init(&full_bar[i], 1); tc::mbar_init(&empty_bar[i], 1); }
-        for (int i = 0; i < 2; i++) { tc::mbar_init(&acc_full[i], 1); tc::mbar_init(&acc_empty[i], EPI_WARPS); }
+        for (int i = 0; i < 2; i++) {
+            tc::mbar_init(&acc_full[i], 1);
+            tc::mbar_init(&acc_empty[i], PAIR ? 2 * EPI_WARPS : EPI_WARPS);
+        }
         abort_flag = 0;
         tc::fence_mbar_init();
     }
@@ -231,9 +255,13 @@ KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
             tc::prefetch_tmap(&a.b1);
         }
     }
-    if (warp == 1) { tc::tmem_alloc(&tmem_base, C::TMEM_COLS); tc::tmem_relinquish(); }
+    if (warp == 1) {
+        if (PAIR) { tc::tmem_alloc_pair(&tmem_base, C::TMEM_COLS); tc::tmem_relinquish_pair(); }
+        else { tc::tmem_alloc(&tmem_base, C::TMEM_COLS); tc::tmem_relinquish(); }
+    }
     tc::tc_fence_before();
-    __syncthreads();
+    if (PAIR) tc::cluster_sync();
+    else __syncthreads();
     tc::tc_fence_after();
     const uint32_t tbase = tmem_base;
 
@@ -252,23 +280,31 @@ KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
                     const int arow1 = SPLIT ? arow : (lo_block(s, a.S) * a.N_pad + p0);
                     const bool fuse = terms > 1;
                     const int nst = fuse ? a.k_steps : (a.k_steps + 1) / 2;
+                    // weight rows of this CTA (a pair's CTAs load one half each)
+                    const int brow = j0 + (int)rank * C::BN_CTA;
                     for (int k = 0; k < nst; k++) {
                         if (!tc::mbar_wait(&empty_bar[stage], phase ^ 1)) { abort_flag = 1; break; }
                         unsigned char* sa = smem + stage * C::STAGE_BYTES;
                         unsigned char* sb = sa + C::A_BYTES;
-                        tc::mbar_arrive_expect_tx(&full_bar[stage], C::STAGE_BYTES);
+                        // the odd CTA of a pair signals the even CTA's full barrier, armed there
+                        const uint32_t fb = (PAIR && rank != 0) ? tc::mapa_shared(&full_bar[stage], 0) : 0u;
+                        auto load = [&](void* dst, const CUtensorMap* m, int x, int y) {
+                            if (PAIR && rank != 0) tc::tma_load_2d_pair(dst, m, fb, x, y);
+                            else tc::tma_load_2d(dst, m, &full_bar[stage], x, y);
+                        };
+                        if (!PAIR || rank == 0) tc::mbar_arrive_expect_tx(&full_bar[stage], C::TX_BYTES);
                         if (fuse) {      // a0, a1, b0, b1 of K block k
                             const int kx = k * BK;
-                            tc::tma_load_2d(sa, &a.a0, &full_bar[stage], kx, arow);
-                            tc::tma_load_2d(sa + C::SLOT_A, &a.a1, &full_bar[stage], kx, arow1);
-                            tc::tma_load_2d(sb, &a.b0, &full_bar[stage], kx, j0);
-                            tc::tma_load_2d(sb + C::SLOT_B, &a.b1, &full_bar[stage], kx, j0);
+                            load(sa, &a.a0, kx, arow);
+                            load(sa + C::SLOT_A, &a.a1, kx, arow1);
+                            load(sb, &a.b0, kx, brow);
+                            load(sb + C::SLOT_B, &a.b1, kx, brow);
                         } else {         // K blocks 2k and 2k+1 (blocks past K read zeros)
 #pragma unroll
                             for (int u = 0; u < 2; u++) {
                                 const int kx = (2 * k + u) * BK;
-                                tc::tma_load_2d(sa + u * C::SLOT_A, &a.a0, &full_bar[stage], kx, arow);
-                                tc::tma_load_2d(sb + u * C::SLOT_B, &a.b0, &full_bar[stage], kx, j0);
+                                load(sa + u * C::SLOT_A, &a.a0, kx, arow);
+                                load(sb + u * C::SLOT_B, &a.b0, kx, brow);
                             }
                         }
                         if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
@@ -309,7 +345,8 @@ KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
         }
     } else if (warp == 1) {
         // ============================ MMA issuer ============================
-        if (lane == 0) {
+        // (a pair's MMAs are issued by the even CTA alone)
+        if (lane == 0 && (!PAIR || rank == 0)) {
             int stage = 0;
             uint32_t phase = 0;
             for (int ti = 0; ti < n_tiles && !abort_flag; ti++) {
@@ -341,11 +378,13 @@ KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
                             for (int w = 0; w < BK / 16; w++) {
                                 const uint64_t ad = tc::smem_desc(sa + ua * C::SLOT_A + w * 32, 16, 1024, tc::LAYOUT_SW128);
                                 const uint64_t bd = tc::smem_desc(sb + ub * C::SLOT_B + w * 32, 16, 1024, tc::LAYOUT_SW128);
-                                tc::mma_bf16(dcol, ad, bd, C::IDESC, first ? 0u : 1u);
+                                if (PAIR) tc::mma_bf16_pair(dcol, ad, bd, C::IDESC, first ? 0u : 1u);
+                                else tc::mma_bf16(dcol, ad, bd, C::IDESC, first ? 0u : 1u);
                                 first = false;
                             }
                         }
-                        tc::mma_commit(&empty_bar[stage]);
+                        if (PAIR) tc::mma_commit_pair(&empty_bar[stage]);
+                        else tc::mma_commit(&empty_bar[stage]);
                         if (++stage == C::STAGES) { stage = 0; phase ^= 1; }
                     }
                 } else {
@@ -373,7 +412,8 @@ KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
                         }
                     }
                 }
-                tc::mma_commit(&acc_full[buf]);
+                if (PAIR) tc::mma_commit_pair(&acc_full[buf]);
+                else tc::mma_commit(&acc_full[buf]);
             }
         }
     } else {
@@ -386,6 +426,9 @@ KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
         const uint32_t lane_off = ((uint32_t)(q * 32)) << 16;
         const int n = p0 + r;                            // point (FWD/BWD)
         const long long hp = a.hp_out;
+        // the odd CTA of a pair grid whose number of point blocks is odd: it
+        // takes part in the pair's MMAs and barriers but touches no row
+        const bool idle = PAIR && p0 >= a.N_pad;
 
         // per-thread state kept across the CTA's tiles
         constexpr bool STATE = (MODE == FWD_TANLAP || MODE == BWD_TAN);
@@ -396,7 +439,7 @@ KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
         if (STATE) {
 #pragma unroll
             for (int c = 0; c < CW; c += 16) {
-                if (j0 + c0 + c >= a.hp_out) {
+                if (idle || j0 + c0 + c >= a.hp_out) {
 #pragma unroll
                     for (int i = 0; i < 16; i++) { st1[c + i] = 0.f; st2[c + i] = 0.f; }
                     continue;
@@ -424,6 +467,7 @@ KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
             const uint32_t tcol = tbase + lane_off + (uint32_t)(buf * C::BN + c0);
 #pragma unroll
             for (int c = 0; c < CW; c += 16) {
+                if (idle) continue;                          // uniform over the CTA
                 float v[16];
                 tc::tmem_ld16(tcol + c, v);
                 tc::tmem_wait_ld();
@@ -603,9 +647,12 @@ KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
             }
             tc::tc_fence_before();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&acc_empty[buf]);
+            if (lane == 0) {
+                if (PAIR && rank != 0) tc::mbar_arrive_cluster(tc::mapa_shared(&acc_empty[buf], 0));
+                else tc::mbar_arrive(&acc_empty[buf]);
+            }
         }
-        if (STATE && !abort_flag) {
+        if (STATE && !abort_flag && !idle) {
 #pragma unroll
             for (int c = 0; c < CW; c += 16) {
                 const int j = j0 + c0 + c;
@@ -621,17 +668,26 @@ KFAC_DEV void engine_body(const Args& a, const uint3 vb, const uint3 vg) {
     }
 
     tc::tc_fence_before();
-    __syncthreads();
+    if (PAIR) tc::cluster_sync();
+    else __syncthreads();
     if (abort_flag && threadIdx.x == 0) latch_status(a.status, KFAC_TIMEOUT);
     if (warp == 1) {
         tc::tc_fence_after();
-        tc::tmem_dealloc(tbase, C::TMEM_COLS);
+        if (PAIR) tc::tmem_dealloc_pair(tbase, C::TMEM_COLS);
+        else tc::tmem_dealloc(tbase, C::TMEM_COLS);
     }
 }
 
 template <int MODE, bool SPLIT>
 __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine(const __grid_constant__ Args a) {
     engine_body<MODE, SPLIT>(a, blockIdx, make_uint3(gridDim.x, gridDim.y, gridDim.z));
+}
+
+// The forward modes on CTA pairs: grid (2 x feature tiles, point blocks / 2
+// rounded up, column chunks).
+template <int MODE, bool SPLIT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1) tc_engine_pair(const __grid_constant__ Args a) {
+    engine_body<MODE, SPLIT, true>(a, blockIdx, make_uint3(gridDim.x, gridDim.y, gridDim.z));
 }
 
 // Grouped launch (group.cuh): every member's Args, tensor maps included, in a
@@ -649,6 +705,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) tc_engine_group(const __grid_c
         tc::tmap_acquire(&a.b1);
     }
     engine_body<MODE, SPLIT>(a, group_block(blockIdx.x - t.start[m], g), g);
+}
+
+// Grouped launch of CTA-pair members: every member's grid.x is even, so its
+// first flat block is even and each cluster of two holds blocks 2q and
+// 2q + 1 of one member (one feature tile, one pair of point blocks).
+template <int MODE, bool SPLIT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NUM_THREADS, 1)
+    tc_engine_group_pair(const __grid_constant__ GroupTab t) {
+    const int m = group_member(t, blockIdx.x);
+    const uint3 g = t.grid[m];
+    const Args& a = *reinterpret_cast<const Args*>(t.packs + (size_t)m * t.stride);
+    if (threadIdx.x == 0) {
+        tc::tmap_acquire(&a.a0);
+        tc::tmap_acquire(&a.a1);
+        tc::tmap_acquire(&a.b0);
+        tc::tmap_acquire(&a.b1);
+    }
+    engine_body<MODE, SPLIT, true>(a, group_block(blockIdx.x - t.start[m], g), g);
 }
 
 }  // namespace tck

@@ -90,6 +90,7 @@ struct MxWeights {
     CUtensorMap kWt_lo[KFAC_MAX_LAYERS];
     float* bias[KFAC_MAX_LAYERS];
     CUtensorMap kW_hi[KFAC_MAX_LAYERS], kW_lo[KFAC_MAX_LAYERS], kWt[KFAC_MAX_LAYERS];
+    CUtensorMap kWp_hi[KFAC_MAX_LAYERS], kWp_lo[KFAC_MAX_LAYERS];   // 64-row boxes (CTA pairs)
     float* wL;        // last layer weights (h_{L-1}) and bias at [hp]
     float* W1f;       // first layer in FP32, input-major: W1f[k * hp_1 + j] = W~_1[j][k], k = 0..d (d: bias)
     float* W1Qf;      // general operator: tangent inputs W_1 q_m, W1Qf[m * hp_1 + j]
@@ -904,15 +905,16 @@ struct k_last_layer_terms {
 // Host helpers
 // ============================================================================
 // The engine's launch, or its record while a grouped batch step is recorded.
+// pair: the CTA-pair kernel (forward modes; grid.x even).
 template <int MODE, bool SPLIT>
-kfac_status_t launch_engine_as(kfac_pinn_handle*, cudaStream_t s, const Args& a, dim3 grid) {
+kfac_status_t launch_engine_as(kfac_pinn_handle*, cudaStream_t s, const Args& a, dim3 grid, bool pair) {
     using C = tck::Cfg<MODE, SPLIT>;
     if (GroupRecorder* r = group_recorder()) {
         LaunchRec rec;
-        rec.key = tck::engine_group_key(MODE, SPLIT);
-        rec.launch = tck::engine_group_launcher(MODE, SPLIT);
+        rec.key = tck::engine_group_key(MODE, SPLIT, pair);
+        rec.launch = tck::engine_group_launcher(MODE, SPLIT, pair);
         rec.grid = make_uint3(grid.x, grid.y, grid.z);
-        rec.smem = C::SMEM;
+        rec.smem = pair ? (size_t)tck::Cfg<tck::FWD_VALUE, SPLIT, true>::SMEM : (size_t)C::SMEM;
         rec.align = (int)alignof(Args);
         rec.args.resize(sizeof(Args));
         memcpy(rec.args.data(), &a, sizeof(Args));
@@ -920,7 +922,7 @@ kfac_status_t launch_engine_as(kfac_pinn_handle*, cudaStream_t s, const Args& a,
         r->list->push_back(std::move(rec));
         return KFAC_OK;
     }
-    const cudaError_t e = tck::engine_launch(MODE, SPLIT, a, grid, s);
+    const cudaError_t e = tck::engine_launch(MODE, SPLIT, pair, a, grid, s);
     if (e != cudaSuccess) {
         kfac_record_cuda_error(e);
         return KFAC_CUDA_ERROR;
@@ -933,13 +935,14 @@ kfac_status_t launch_engine_as(kfac_pinn_handle*, cudaStream_t s, const Args& a,
 // split-BF16 product).
 template <int MODE>
 kfac_status_t launch_engine(kfac_pinn_handle* h, cudaStream_t s, const Args& a, dim3 grid, int kclass, double work,
-                            double exec) {
+                            double exec, bool pair = false) {
     if (grid.x == 0 || grid.y == 0 || grid.z == 0) return KFAC_OK;
     if (group_recording())
-        return a.split_all ? launch_engine_as<MODE, true>(h, s, a, grid) : launch_engine_as<MODE, false>(h, s, a, grid);
+        return a.split_all ? launch_engine_as<MODE, true>(h, s, a, grid, pair)
+                           : launch_engine_as<MODE, false>(h, s, a, grid, pair);
     timer_begin(h, kclass, s);
-    kfac_status_t st =
-        a.split_all ? launch_engine_as<MODE, true>(h, s, a, grid) : launch_engine_as<MODE, false>(h, s, a, grid);
+    kfac_status_t st = a.split_all ? launch_engine_as<MODE, true>(h, s, a, grid, pair)
+                                   : launch_engine_as<MODE, false>(h, s, a, grid, pair);
     if (st) return st;
     timer_end(h, kclass, s, work, exec);
     KFAC_LAUNCH_CHECK(h);
@@ -1320,8 +1323,13 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
         a.split_all = split;
         a.a0 = in.kT_hi;
         a.a1 = in.kT_lo;
-        a.b0 = m->w.kW_hi[l - 1];
-        a.b1 = m->w.kW_lo[l - 1];
+        const int jb = (out.hp + 127) / 128, pb = P.N_pad / 128;
+        // CTA pairs over consecutive point blocks (grid: 2 x feature tiles,
+        // point-block pairs; an odd count of point blocks leaves one CTA idle)
+        const bool pair = h->cta_pairs != 0;
+        const int pbx = pair ? pb + (pb & 1) : pb;
+        a.b0 = pair ? m->w.kWp_hi[l - 1] : m->w.kW_hi[l - 1];
+        a.b1 = pair ? m->w.kWp_lo[l - 1] : m->w.kW_lo[l - 1];
         a.k_steps = in.hp / 64;
         a.n_out = out.h;
         a.hp_out = out.hp;
@@ -1331,23 +1339,23 @@ kfac_status_t forward_pass(kfac_pinn_handle* h, cudaStream_t s, const double* th
         a.A0 = out.A0;
         a.AD = out.AD;
         a.part = m->part;
-        const int jb = (out.hp + 127) / 128, pb = P.N_pad / 128;
+        auto grid = [&](int z) { return pair ? dim3(2 * jb, pbx / 2, z) : dim3(jb, pb, z); };
         // per Taylor row block: the method's FLOPs (real sizes) and the executed
         // tensor FLOPs of one product over the padded tile
         const double alg = 2.0 * N * (double)out.h * in.h;
         const double fl = 2.0 * P.N_pad * (double)out.hp * in.hp;
-        kfac_status_t st = launch_engine<tck::FWD_VALUE>(h, s, a, dim3(jb, pb, 1), KFAC_KC_LAYER_GEMM, alg, 3 * fl);
+        kfac_status_t st = launch_engine<tck::FWD_VALUE>(h, s, a, grid(1), KFAC_KC_LAYER_GEMM, alg, 3 * fl, pair);
         if (st) return st;
         if (S > 1) {
             const int tiles = S - 1;
             auto launch = [&](int len) {
                 a.chunk_len = len;
                 a.n_chunks = (tiles + len - 1) / len;
-                return launch_engine<tck::FWD_TANLAP>(h, s, a, dim3(jb, pb, a.n_chunks), KFAC_KC_LAYER_GEMM,
-                                                      alg * (S - 1), fl * (a.split_all ? 3 * (S - 1) : S + 1));
+                return launch_engine<tck::FWD_TANLAP>(h, s, a, grid(a.n_chunks), KFAC_KC_LAYER_GEMM,
+                                                      alg * (S - 1), fl * (a.split_all ? 3 * (S - 1) : S + 1), pair);
             };
             int len = 0;
-            if ((st = tangent_chunk(h, s, KFAC_TUNE_FWD_TAN, split, P.N_pad, out.hp, in.hp, tiles, jb * pb, launch,
+            if ((st = tangent_chunk(h, s, KFAC_TUNE_FWD_TAN, split, P.N_pad, out.hp, in.hp, tiles, jb * pbx, launch,
                                     len)))
                 return st;
             if ((st = launch(len))) return st;
@@ -1568,6 +1576,8 @@ kfac_status_t alloc_weights(kfac_pinn_handle* h, MxWeights& w) {
         if ((st = dal(&w.bias[l - 1], (size_t)hout_p))) return st;
         bool ok = tc_make_tmap_2d(&w.kW_hi[l - 1], w.W_hi[l - 1], hin_p, hout_p, hin_p * 2, 64, 128) &&
                   tc_make_tmap_2d(&w.kW_lo[l - 1], w.W_lo[l - 1], hin_p, hout_p, hin_p * 2, 64, 128) &&
+                  tc_make_tmap_2d(&w.kWp_hi[l - 1], w.W_hi[l - 1], hin_p, hout_p, hin_p * 2, 64, 64) &&
+                  tc_make_tmap_2d(&w.kWp_lo[l - 1], w.W_lo[l - 1], hin_p, hout_p, hin_p * 2, 64, 64) &&
                   tc_make_tmap_2d(&w.kWt[l - 1], w.Wt[l - 1], hout_p, hin_p, hout_p * 2, 64, 128);
         if (!ok) return KFAC_CUDA_ERROR;
         if (is_split_all(h)) {
