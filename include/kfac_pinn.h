@@ -240,7 +240,9 @@ kfac_status_t kfac_pinn_set_store_forward(kfac_handle_t h, int enable);
  * order are the same either way (the results are bit-identical).  No effect on the
  * FP64 and FP32 precisions.  Default: disabled (on GB300 the pair form fed
  * 25 % fewer bytes per SM but ran the benchmark's step about 3 % slower).
- * Errors: KFAC_BAD_ARG for a NULL handle. */
+ * Takes effect at the handle's next step (its own captured graph is
+ * dropped); a batch step captured earlier (kfac_pinn_batch_step) keeps the
+ * form it was captured with.  Errors: KFAC_BAD_ARG for a NULL handle. */
 kfac_status_t kfac_pinn_set_cta_pairs(kfac_handle_t h, int enable);
 
 /* Graph mode for kfac_pinn_step and kfac_pinn_step_host (no counterpart in the
