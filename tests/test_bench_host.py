@@ -42,3 +42,25 @@ def test_profile_traffic_keeps_matching_lines_and_drops_stale_ones(tmp_path, mon
     # a changed source drops the line
     _write(root, "src/b.cu", "kernel b, edited\n")
     assert bench.profile_traffic(2560) == {}
+
+
+def test_reference_arm_line(monkeypatch):
+    # the oracle arm's JSON line (run at N = 1 on the host cores), on a
+    # two-point sample so that it takes seconds
+    import json
+
+    monkeypatch.setattr(bench, "REF_SAMPLE", (2, 1))
+
+    class Args:
+        steps, warmup = 1, 0
+
+    out = bench.run_reference(Args, 0, 1)
+    json.dumps(out)
+    assert out["impl"] == "reference" and out["metric"] == bench.METRIC
+    assert out["unit"] == "steps/s" and out["higher_is_better"] is True and out["value"] > 0
+    assert out["config"]["workload"] == bench.WORKLOAD_NAME and out["dtype"] == "f64"
+    assert out["e2e"] == {"value": out["value"], "unit": "steps/s", "h2d_bytes_per_step": 0,
+                          "d2h_bytes_per_step": 0}
+    cb = out["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == out["value"] and cb["cores"] >= 1
+    assert cb["extrapolated"] is True and cb["scale"] == bench.WORKLOAD.n_int // 2 and "sample" in cb
