@@ -64,6 +64,7 @@ def test_null_handle_is_bad_arg(lib):
     assert lib.kfac_pinn_get_tuning(None, None, 0, C.byref(n)) == 1
     assert lib.kfac_pinn_set_tuning(None, None, 0) == 1
     assert lib.kfac_pinn_set_graph(None, 1) == 1
+    assert lib.kfac_pinn_set_cta_pairs(None, 1) == 1
 
 
 _LAYOUT_PROBE = r"""
