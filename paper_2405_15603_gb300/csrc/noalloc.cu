@@ -16,6 +16,8 @@
 // be cleared between calls.
 #include <string.h>
 
+#include <atomic>
+
 #include "kfac_internal.cuh"
 
 namespace {
@@ -26,19 +28,22 @@ constexpr size_t NOALLOC_SCRATCH_DOUBLES = (size_t)4 << 20;
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
 constexpr int MAX_DEVICES = 64;
-double* g_scratch_addr[MAX_DEVICES] = {nullptr};
+std::atomic<double*> g_scratch_addr[MAX_DEVICES];   // static storage: all null
 
 // Device address of the scratch array on the current device, looked up once
 // per device (the host-side symbol is only a stand-in, not a device address).
+// Concurrent first calls may both look it up; they store the same address.
 kfac_status_t scratch_address(double** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return KFAC_CUDA_ERROR;
-    if (!g_scratch_addr[dev]) {
+    double* a = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!a) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return KFAC_CUDA_ERROR;
-        g_scratch_addr[dev] = (double*)p;
+        a = (double*)p;
+        g_scratch_addr[dev].store(a, std::memory_order_release);
     }
-    *out = g_scratch_addr[dev];
+    *out = a;
     return KFAC_OK;
 }
 
