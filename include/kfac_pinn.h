@@ -237,7 +237,10 @@ kfac_status_t kfac_pinn_set_store_forward(kfac_handle_t h, int enable);
  * with the next point block on a cluster of two CTAs that share one 256-row
  * tensor-core product, each loading half of the weight tile (an odd number
  * of point blocks leaves one CTA of the last pair idle).  The products and their
- * order are the same either way (the results are bit-identical).  No effect on the
+ * order are the same either way, so the results are bit-identical whenever the
+ * two forms split the tangent columns into the same chunks (the wave model
+ * counts the idle CTA, so with an odd number of point blocks it may choose
+ * another split, which changes only the rounding of the partial sums).  No effect on the
  * FP64 and FP32 precisions.  Default: disabled (on GB300 the pair form fed
  * 25 % fewer bytes per SM but ran the benchmark's step about 3 % slower).
  * Takes effect at the handle's next step (its own captured graph is

@@ -156,7 +156,7 @@ class KfacPinn:
 
     def set_cta_pairs(self, enable: bool = True):
         """Forward layer GEMMs of the tensor-core precisions on CTA pairs
-        (kfac_pinn_set_cta_pairs; off by default, bit-identical results)."""
+        (kfac_pinn_set_cta_pairs; off by default; the same products in the same order)."""
         _check("kfac_pinn_set_cta_pairs", self.lib.kfac_pinn_set_cta_pairs(self.h, int(enable)))
 
     def set_graph(self, enable: bool = True):
