@@ -15,6 +15,12 @@ def _wrap(name, make):
     return name, make
 
 
+def _with(cfg, **kw):
+    """A copy of an oracle config with some fields replaced."""
+    import dataclasses
+    return dataclasses.replace(cfg, **kw)
+
+
 def _ties_keep_smaller_alpha(cfg, theta, dhat, X_int, f, X_bdy, g):
     losses = [ko.batch_loss(cfg, theta + a * dhat, X_int, f, X_bdy, g) for a in ko.LINE_SEARCH_GRID]
     best = None
@@ -71,6 +77,21 @@ MUTANTS = {
     "generalized eigenvectors not P-normalised": (
         _wrap("generalized_eig", lambda o: lambda P, Q: (2.0 * o(P, Q)[0], o(P, Q)[1])),
         lambda: pins.test_kron_sum_inverse_vs_dense_solve(True)),
+    # Sec. 3.4 (KFAC*): the Gramian products without the boundary term
+    "Gramian products without the boundary term": (
+        _wrap("gramian_bilinear",
+              lambda o: lambda ja, jb, W=None: o((ja[0], 0.0 * ja[1]), (jb[0], 0.0 * jb[1]), W)),
+        pins.test_gramian_products_vs_full_ggn),
+    # Sec. 3.4 (KFAC*): the model's damping term left out of the 2 x 2 system
+    "KFAC* coefficients without damping": (
+        _wrap("kfac_star_coefficients",
+              lambda o: lambda cfg, cg, Delta, delta, grad:
+              o(_with(cfg, lam=0.0), cg, Delta, delta, grad)),
+        pins.test_kfac_star_minimises_quadratic_model),
+    # Algorithm 1: identity initialisation of the EMA ignored
+    "EMA started from zero instead of the identity": (
+        _wrap("init_state", lambda o: lambda cfg: o(_with(cfg, init_identity=False))),
+        pins.test_ema_and_identity_init),
     # App. B: ties resolved towards the smaller learning rate
     "line search keeping the smaller alpha on ties": (
         ("line_search", lambda o: _ties_keep_smaller_alpha),
