@@ -8,6 +8,7 @@ import pytest
 
 from oracle import kfac_oracle as ko
 from tests import test_oracle as pins
+from tests import test_oracle_general_residual as gpins
 
 
 def _wrap(name, make):
@@ -16,7 +17,7 @@ def _wrap(name, make):
 
 
 def _with(cfg, **kw):
-    """A copy of an oracle config with some fields replaced."""
+    """A copy of an oracle dataclass (config, residual) with some fields replaced."""
     import dataclasses
     return dataclasses.replace(cfg, **kw)
 
@@ -92,6 +93,19 @@ MUTANTS = {
     "EMA started from zero instead of the identity": (
         _wrap("init_state", lambda o: lambda cfg: o(_with(cfg, init_identity=False))),
         pins.test_ema_and_identity_init),
+    # Sec. 3.3 (Eq. 9): the quadratic term without its factor 1/2
+    "general residual with the quadratic term doubled": (
+        _wrap("quadratic_residual",
+              lambda o: lambda res, z, f: o(_with(res, Q=None if res.Q is None else 2.0 * res.Q), z, f)),
+        lambda: gpins.test_residual_and_gradient_vs_autograd(True)),
+    # Sec. 3.3: the residual's Jacobian without the quadratic term's part
+    "general residual Jacobian without the quadratic term": (
+        _wrap("quadratic_residual_jacobian", lambda o: lambda res, z: o(_with(res, Q=None), z)),
+        gpins.test_full_ggn_vs_autograd),
+    # Sec. 3.3: the criterion's Hessian W left out of the loss
+    "general loss without the criterion weight": (
+        _wrap("loss_general", lambda o: lambda res, ri, rb: o(_with(res, W=None), ri, rb)),
+        lambda: gpins.test_residual_and_gradient_vs_autograd(False)),
     # App. B: ties resolved towards the smaller learning rate
     "line search keeping the smaller alpha on ties": (
         ("line_search", lambda o: _ties_keep_smaller_alpha),
